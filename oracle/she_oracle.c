@@ -1,0 +1,475 @@
+/*
+ * she_oracle.c -- plain, slow FP64 CPU oracle for the finite-volume
+ * stochastic heat / species diffusion step of Garcia et al.,
+ * "An Introduction to Computational Fluctuating Hydrodynamics" (2024).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference arm of bench.py may load this library.  It shares
+ * no code, header, table or helper with the CUDA library; the two sides were
+ * written independently from the same written specification of the method
+ * and of the noise generator.
+ *
+ * What it computes (all in double precision, one realization at a time):
+ *   - Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and Box-Muller
+ *     (Box & Muller, 1958) normal deviates, addressed by a counter
+ *     (group, step, stream, tag) -- the paper draws iid N(0,1) per face per
+ *     step, Sec. 3, Eq. (3.7); the counter form is this library's reading.
+ *   - one forward-Euler (Euler-Maruyama) step, Sec. 3, Eq. (3.3), with the
+ *     face value as the arithmetic mean of its neighbours (Sec. 3, text
+ *     after Eq. (3.3)), the Dirichlet wall stencil of Eq. (3.8) and the
+ *     sqrt(2) wall-noise factor stated right after it, periodic wrap;
+ *     heat noise proportional to T_face (Eq. (2.12)/(4.9)), species noise
+ *     proportional to sqrt(c_face) (Eq. (4.7)/(4.8)); in 2D/3D the per-axis
+ *     fluxes use independent noises (Eq. (2.11), Kronecker delta over axes).
+ *   - the sampling of Sec. 3, Eq. (3.9): after relaxation, every K steps,
+ *     pooled over realizations: sums of delta = T - T_ref, of delta^2, of
+ *     delta_i*delta_j (equal-time covariance, generalising the one-point
+ *     correlation the paper plots, Eq. (3.10)/(3.13)), and of |hat(delta)_k|^2
+ *     with the unnormalised DFT of Eq. (3.11).
+ *
+ * Counter layout (the paper leaves the random-number source open; this is
+ * the reading both sides implement):
+ *   key      = (seed & 0xffffffff, seed >> 32)
+ *   low face = the face on the low side of cell x along axis a; its normal
+ *              index is g = a*Ncells + lin(x), lin(x) = x0 + n0*(x1 + n1*x2);
+ *              normal g is slot g%4 of Philox(ctr = (g/4, n, stream, 0))
+ *   high wall (1D Dirichlet only: face N) = slot n%4 of
+ *              Philox(ctr = (0, n/4, stream, 2))
+ *   initial perturbation of cell i = slot i%4 of Philox(ctr = (i/4, 0, stream, 1))
+ *   n = absolute 0-based index of the step being taken, stream = realization.
+ *   From u0..u3: U(u) = (u + 0.5) / 2^32, R_a = sqrt(-2 ln U(u0)),
+ *   th_a = 2 pi U(u1), R_b = sqrt(-2 ln U(u2)), th_b = 2 pi U(u3);
+ *   slots 0..3 = R_a cos th_a, R_a sin th_a, R_b cos th_b, R_b sin th_b.
+ *
+ * Parity pins: see tests/test_oracle_*.py (Philox statistical tests, the
+ * deterministic sine/Fourier-mode limit, the exact first/second-moment
+ * recursion of the discrete scheme, closed forms of Eq. (3.10), (3.12),
+ * (3.13) and the species equilibrium of exercise 5).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_HEAT 0
+#define ORC_SPECIES 1
+#define ORC_PERIODIC 0
+#define ORC_DIRICHLET 1
+
+#define ORC_TAG_STEP 0u
+#define ORC_TAG_IC 1u
+#define ORC_TAG_WALL 2u
+
+typedef struct {
+    int32_t dim;           /* 1, 2 or 3 */
+    int32_t n[3];          /* cells per axis (unused axes = 1) */
+    int32_t equation;      /* ORC_HEAT or ORC_SPECIES */
+    int32_t bc;            /* ORC_PERIODIC or ORC_DIRICHLET (Dirichlet: 1D only) */
+    double r;              /* diffusion number kappa*dt/dx^2 (or D*dt/dx^2) */
+    double eps;            /* heat: kB/(rho c_V dV); species: 1/(n0 dV) */
+    double wall_lo, wall_hi; /* T_L, T_R (periodic: both = uniform value) */
+    uint64_t seed;
+    int32_t stochastic;    /* 0: deterministic limit (alpha = 0) */
+    int32_t perturb_ic;    /* 1: add the seeded perturbation to the IC */
+    int32_t stats_interval;/* K */
+    int32_t pad0;
+    int64_t relax_steps;   /* sample at step m (1-based) iff m%K==0 && m>relax */
+    int32_t want_cov;      /* accumulate sum delta_i delta_j */
+    int32_t want_sk;       /* bit0: full DFT over the grid, bit1: per-axis lines */
+} orc_params;
+
+/* ---------------------------------------------------------------- RNG ---- */
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    /* Salmon et al. SC'11: Philox-4x32 with multipliers 0xD2511F53,
+     * 0xCD9E8D57 and Weyl key increments 0x9E3779B9, 0xBB67AE85. */
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t prod0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t prod1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+        uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static double orc_uniform(uint32_t u)
+{
+    return ((double)u + 0.5) / 4294967296.0;
+}
+
+/* The four normals of one counter, Box & Muller (1958), both branches. */
+void orc_normals4(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                  double z[4])
+{
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {c0, c1, c2, c3};
+    uint32_t u[4];
+    orc_philox4x32_10(ctr, key, u);
+    const double two_pi = 6.283185307179586476925286766559;
+    double ra = sqrt(-2.0 * log(orc_uniform(u[0])));
+    double ta = two_pi * orc_uniform(u[1]);
+    double rb = sqrt(-2.0 * log(orc_uniform(u[2])));
+    double tb = two_pi * orc_uniform(u[3]);
+    z[0] = ra * cos(ta);
+    z[1] = ra * sin(ta);
+    z[2] = rb * cos(tb);
+    z[3] = rb * sin(tb);
+}
+
+/* Normal number g of the step/IC stream. */
+double orc_normal(uint64_t seed, uint64_t g, uint32_t step, uint32_t stream, uint32_t tag)
+{
+    double z[4];
+    orc_normals4(seed, (uint32_t)(g / 4u), step, stream, tag, z);
+    return z[g % 4u];
+}
+
+/* Normal of the 1D high (right) Dirichlet wall face at step n. */
+double orc_wall_normal(uint64_t seed, uint32_t step, uint32_t stream)
+{
+    double z[4];
+    orc_normals4(seed, 0u, step / 4u, stream, ORC_TAG_WALL, z);
+    return z[step % 4u];
+}
+
+/* ------------------------------------------------------------ helpers ---- */
+
+static int64_t orc_cells(const orc_params* p)
+{
+    int64_t c = 1;
+    for (int a = 0; a < p->dim; ++a) c *= p->n[a];
+    return c;
+}
+
+/* Deterministic steady profile T_ref (Sec. 3: linear profile between the
+ * walls for Dirichlet, uniform for periodic). */
+void orc_reference_profile(const orc_params* p, double* tref)
+{
+    int64_t nc = orc_cells(p);
+    if (p->dim == 1 && p->bc == ORC_DIRICHLET) {
+        int n = p->n[0];
+        for (int i = 0; i < n; ++i)
+            tref[i] = p->wall_lo + (p->wall_hi - p->wall_lo) * ((double)i + 0.5) / (double)n;
+    } else {
+        for (int64_t i = 0; i < nc; ++i) tref[i] = p->wall_lo;
+    }
+}
+
+/* Initial condition: T_ref plus (optionally) sigma * N(0,1) per cell with
+ * sigma^2 the equilibrium variance at the mid temperature (heat: eps*T^2,
+ * Eq. (3.10); species: eps*c, exercise 5).  Periodic grids conserve the
+ * total, so the perturbation is projected to zero sum. */
+void orc_initial_state(const orc_params* p, uint32_t stream, double* T)
+{
+    int64_t nc = orc_cells(p);
+    orc_reference_profile(p, T);
+    if (!p->perturb_ic) return;
+    double mid = 0.5 * (p->wall_lo + p->wall_hi);
+    double sigma = (p->equation == ORC_HEAT) ? sqrt(p->eps) * fabs(mid) : sqrt(p->eps * fabs(mid));
+    double* pert = (double*)malloc(sizeof(double) * (size_t)nc);
+    double mean = 0.0;
+    for (int64_t i = 0; i < nc; ++i) {
+        pert[i] = sigma * orc_normal(p->seed, (uint64_t)i, 0u, stream, ORC_TAG_IC);
+        mean += pert[i];
+    }
+    mean /= (double)nc;
+    int periodic = (p->bc == ORC_PERIODIC);
+    for (int64_t i = 0; i < nc; ++i) T[i] += pert[i] - (periodic ? mean : 0.0);
+    free(pert);
+}
+
+/* Noise amplitude times face value: heat s*T_f with s = sqrt(2 r eps);
+ * species sqrt(2 r eps max(c_f, 0)). */
+static double orc_flux_amp(const orc_params* p, double face_value)
+{
+    if (!p->stochastic) return 0.0;
+    if (p->equation == ORC_HEAT) return sqrt(2.0 * p->r * p->eps) * face_value;
+    double c = face_value > 0.0 ? face_value : 0.0;
+    return sqrt(2.0 * p->r * p->eps * c);
+}
+
+/* --------------------------------------------------------------- step ---- */
+
+/* One forward-Euler step of Eq. (3.3) in 1D (Dirichlet walls per Eq. (3.8)). */
+static void orc_step_1d(const orc_params* p, uint32_t step, uint32_t stream,
+                        const double* T, double* Tn, double* G /* N+1 */)
+{
+    const int n = p->n[0];
+    const double r = p->r;
+    const int dir = (p->bc == ORC_DIRICHLET);
+    const double sq2 = sqrt(2.0);
+    /* face f = low face of cell f, f = 0..n-1; face n = high wall */
+    for (int f = 0; f < n; ++f) {
+        double tface;
+        double w = 1.0;
+        if (f == 0) {
+            if (dir) { tface = p->wall_lo; w = sq2; }
+            else tface = 0.5 * (T[n - 1] + T[0]);
+        } else {
+            tface = 0.5 * (T[f - 1] + T[f]);
+        }
+        double z = p->stochastic ? orc_normal(p->seed, (uint64_t)f, step, stream, ORC_TAG_STEP) : 0.0;
+        G[f] = w * orc_flux_amp(p, tface) * z;
+    }
+    if (dir) {
+        double z = p->stochastic ? orc_wall_normal(p->seed, step, stream) : 0.0;
+        G[n] = sq2 * orc_flux_amp(p, p->wall_hi) * z;
+    } else {
+        G[n] = G[0];
+    }
+    for (int i = 0; i < n; ++i) {
+        double d;
+        if (dir && i == 0)
+            d = r * (T[1] - 3.0 * T[0] + 2.0 * p->wall_lo);
+        else if (dir && i == n - 1)
+            d = r * (T[n - 2] - 3.0 * T[n - 1] + 2.0 * p->wall_hi);
+        else {
+            double left = T[(i - 1 + n) % n];
+            double right = T[(i + 1) % n];
+            d = r * (right - 2.0 * T[i] + left);
+        }
+        Tn[i] = T[i] + d + (G[i + 1] - G[i]);
+    }
+}
+
+/* One step in 2D/3D, periodic on every axis: per axis the same 1D stencil
+ * and an independent face noise (Eq. (2.11)). */
+static void orc_step_nd(const orc_params* p, uint32_t step, uint32_t stream,
+                        const double* T, double* Tn, double* G /* dim*Ncells */)
+{
+    const int64_t nc = orc_cells(p);
+    int n0 = p->n[0], n1 = p->n[1], n2 = (p->dim == 3) ? p->n[2] : 1;
+    int64_t stride[3] = {1, n0, (int64_t)n0 * n1};
+    int ext[3] = {n0, n1, n2};
+    for (int a = 0; a < p->dim; ++a) {
+        for (int64_t i = 0; i < nc; ++i) {
+            int x[3] = {(int)(i % n0), (int)((i / n0) % n1), (int)(i / ((int64_t)n0 * n1))};
+            int xl = (x[a] - 1 + ext[a]) % ext[a];
+            int64_t il = i + (int64_t)(xl - x[a]) * stride[a];
+            double tface = 0.5 * (T[il] + T[i]);
+            double z = p->stochastic ? orc_normal(p->seed, (uint64_t)a * (uint64_t)nc + (uint64_t)i,
+                                                  step, stream, ORC_TAG_STEP) : 0.0;
+            G[(int64_t)a * nc + i] = orc_flux_amp(p, tface) * z;
+        }
+    }
+    for (int64_t i = 0; i < nc; ++i) {
+        int x[3] = {(int)(i % n0), (int)((i / n0) % n1), (int)(i / ((int64_t)n0 * n1))};
+        double acc = T[i];
+        for (int a = 0; a < p->dim; ++a) {
+            int xl = (x[a] - 1 + ext[a]) % ext[a];
+            int xr = (x[a] + 1) % ext[a];
+            int64_t il = i + (int64_t)(xl - x[a]) * stride[a];
+            int64_t ir = i + (int64_t)(xr - x[a]) * stride[a];
+            acc += p->r * (T[ir] - 2.0 * T[i] + T[il]);
+            acc += G[(int64_t)a * nc + ir] - G[(int64_t)a * nc + i];
+        }
+        Tn[i] = acc;
+    }
+}
+
+/* Public single-step entry: Tn = step(T) at absolute step index `step`. */
+int orc_step(const orc_params* p, uint32_t step, uint32_t stream, const double* T, double* Tn)
+{
+    int64_t nc = orc_cells(p);
+    double* G = (double*)malloc(sizeof(double) * (size_t)(p->dim * nc + 1));
+    if (!G) return -1;
+    if (p->dim == 1) orc_step_1d(p, step, stream, T, Tn, G);
+    else orc_step_nd(p, step, stream, T, Tn, G);
+    free(G);
+    return 0;
+}
+
+/* ----------------------------------------------------------- sampling ---- */
+
+/* Plain DFT of a real vector: out_re/out_im[k] = sum_j v_j e^{-2 pi i j k / n}
+ * (Eq. (3.11)); `stride` walks the input. */
+static void orc_dft_line(const double* v, int64_t stride, int n, double* re, double* im)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int k = 0; k < n; ++k) {
+        double sr = 0.0, si = 0.0;
+        for (int j = 0; j < n; ++j) {
+            long long jk = ((long long)j * k) % n;
+            double ang = two_pi * (double)jk / (double)n;
+            sr += v[(int64_t)j * stride] * cos(ang);
+            si -= v[(int64_t)j * stride] * sin(ang);
+        }
+        re[k] = sr;
+        im[k] = si;
+    }
+}
+
+typedef struct {
+    int64_t n_samples;     /* per realization */
+    double* sum_d;         /* [cells] */
+    double* sum_d2;        /* [cells] */
+    double* sum_dd;        /* [cells*cells] or NULL */
+    double* sum_sk;        /* [cells] |hat delta_k|^2 (full DFT, dim<=2) or NULL */
+    double* sum_sk_axes;   /* [n0+n1+n2] line-averaged per-axis |hat delta|^2 or NULL */
+} orc_acc;
+
+static void orc_sample(const orc_params* p, const double* T, const double* tref, orc_acc* acc,
+                       double* work)
+{
+    int64_t nc = orc_cells(p);
+    double* d = work;                 /* [nc] */
+    for (int64_t i = 0; i < nc; ++i) d[i] = T[i] - tref[i];
+    acc->n_samples += 1;
+    for (int64_t i = 0; i < nc; ++i) {
+        acc->sum_d[i] += d[i];
+        acc->sum_d2[i] += d[i] * d[i];
+    }
+    if (acc->sum_dd) {
+        for (int64_t i = 0; i < nc; ++i)
+            for (int64_t j = 0; j < nc; ++j) acc->sum_dd[i * nc + j] += d[i] * d[j];
+    }
+    if (acc->sum_sk) {
+        /* full multi-dimensional DFT by its definition, Eq. (3.11) per axis */
+        const double two_pi = 6.283185307179586476925286766559;
+        int n0 = p->n[0], n1 = (p->dim >= 2) ? p->n[1] : 1;
+        for (int64_t k = 0; k < nc; ++k) {
+            int k0 = (int)(k % n0), k1 = (int)(k / n0);
+            double sr = 0.0, si = 0.0;
+            for (int64_t j = 0; j < nc; ++j) {
+                int j0 = (int)(j % n0), j1 = (int)(j / n0);
+                double ph = (double)(((long long)j0 * k0) % n0) / (double)n0 +
+                            (double)(((long long)j1 * k1) % n1) / (double)n1;
+                sr += d[j] * cos(two_pi * ph);
+                si -= d[j] * sin(two_pi * ph);
+            }
+            acc->sum_sk[k] += sr * sr + si * si;
+        }
+    }
+    if (acc->sum_sk_axes) {
+        int ext[3] = {p->n[0], p->dim >= 2 ? p->n[1] : 1, p->dim >= 3 ? p->n[2] : 1};
+        int64_t stride[3] = {1, ext[0], (int64_t)ext[0] * ext[1]};
+        int off = 0;
+        double* re = work + nc;
+        double* im = re + 4096;
+        for (int a = 0; a < p->dim; ++a) {
+            int64_t lines = nc / ext[a];
+            for (int64_t l = 0; l < lines; ++l) {
+                /* base cell of line l: the cell with x_a = 0 */
+                int64_t base;
+                if (a == 0) base = l * ext[0];
+                else if (a == 1) base = (l % ext[0]) + (l / ext[0]) * stride[2];
+                else base = l;
+                orc_dft_line(d + base, stride[a], ext[a], re, im);
+                for (int k = 0; k < ext[a]; ++k)
+                    acc->sum_sk_axes[off + k] += (re[k] * re[k] + im[k] * im[k]) / (double)lines;
+            }
+            off += ext[a];
+        }
+    }
+}
+
+/*
+ * Run `nsteps` steps for realizations stream0 .. stream0+R-1, starting at
+ * absolute step `step0`.  `state` ([R][cells]) is read as the starting state
+ * unless `init` is set, in which case it is filled with the initial
+ * condition first; on return it holds the final state.  Accumulator arrays
+ * (pooled over the R realizations, added to, not cleared) may be NULL when
+ * not wanted; n_samples receives the per-realization sample count added.
+ * Returns 0 on success, -1 on allocation failure, -2 on bad arguments.
+ */
+int orc_run(const orc_params* p, int64_t R, uint32_t stream0, uint32_t step0, int64_t nsteps,
+            double* state, int init, int64_t* n_samples, double* sum_d, double* sum_d2,
+            double* sum_dd, double* sum_sk, double* sum_sk_axes)
+{
+    if (p->dim < 1 || p->dim > 3 || R < 0 || nsteps < 0) return -2;
+    if (p->dim > 1 && p->bc != ORC_PERIODIC) return -2;
+    if (sum_sk && p->dim > 2) return -2;
+    int64_t nc = orc_cells(p);
+    int axes_len = p->n[0] + (p->dim >= 2 ? p->n[1] : 0) + (p->dim >= 3 ? p->n[2] : 0);
+    double* tref = (double*)malloc(sizeof(double) * (size_t)nc);
+    if (!tref) return -1;
+    orc_reference_profile(p, tref);
+    int err = 0;
+    int64_t samples_per_real = 0;
+    /* per-realization accumulators, summed in realization order afterwards */
+    double* pd = (double*)calloc((size_t)(R * nc), sizeof(double));
+    double* pd2 = (double*)calloc((size_t)(R * nc), sizeof(double));
+    double* pdd = sum_dd ? (double*)calloc((size_t)(R * nc * nc), sizeof(double)) : NULL;
+    double* psk = sum_sk ? (double*)calloc((size_t)(R * nc), sizeof(double)) : NULL;
+    double* pska = sum_sk_axes ? (double*)calloc((size_t)(R * axes_len), sizeof(double)) : NULL;
+    if ((R > 0 && (!pd || !pd2)) || (sum_dd && R > 0 && !pdd) || (sum_sk && R > 0 && !psk) ||
+        (sum_sk_axes && R > 0 && !pska)) {
+        free(tref); free(pd); free(pd2); free(pdd); free(psk); free(pska);
+        return -1;
+    }
+    for (int64_t m = (int64_t)step0 + 1; m <= (int64_t)step0 + nsteps; ++m)
+        if (p->stats_interval > 0 && m % p->stats_interval == 0 && m > p->relax_steps)
+            samples_per_real++;
+
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t rr = 0; rr < R; ++rr) {
+        double* T = state + rr * nc;
+        double* Tn = (double*)malloc(sizeof(double) * (size_t)nc);
+        double* G = (double*)malloc(sizeof(double) * (size_t)(p->dim * nc + 1));
+        double* work = (double*)malloc(sizeof(double) * (size_t)(nc + 8192));
+        if (!Tn || !G || !work) {
+            free(Tn); free(G); free(work);
+#pragma omp atomic write
+            err = -1;
+            continue;
+        }
+        uint32_t stream = stream0 + (uint32_t)rr;
+        if (init) orc_initial_state(p, stream, T);
+        orc_acc acc;
+        acc.n_samples = 0;
+        acc.sum_d = pd + rr * nc;
+        acc.sum_d2 = pd2 + rr * nc;
+        acc.sum_dd = pdd ? pdd + rr * nc * nc : NULL;
+        acc.sum_sk = psk ? psk + rr * nc : NULL;
+        acc.sum_sk_axes = pska ? pska + rr * axes_len : NULL;
+        for (int64_t s = 0; s < nsteps; ++s) {
+            uint32_t step = step0 + (uint32_t)s;
+            if (p->dim == 1) orc_step_1d(p, step, stream, T, Tn, G);
+            else orc_step_nd(p, step, stream, T, Tn, G);
+            memcpy(T, Tn, sizeof(double) * (size_t)nc);
+            int64_t m = (int64_t)step + 1;
+            if (p->stats_interval > 0 && m % p->stats_interval == 0 && m > p->relax_steps)
+                orc_sample(p, T, tref, &acc, work);
+        }
+        free(Tn); free(G); free(work);
+    }
+    if (!err) {
+        if (n_samples) *n_samples += samples_per_real;
+        for (int64_t rr = 0; rr < R; ++rr) {
+            for (int64_t i = 0; i < nc; ++i) {
+                if (sum_d) sum_d[i] += pd[rr * nc + i];
+                if (sum_d2) sum_d2[i] += pd2[rr * nc + i];
+                if (sum_sk) sum_sk[i] += psk[rr * nc + i];
+            }
+            if (sum_dd)
+                for (int64_t i = 0; i < nc * nc; ++i) sum_dd[i] += pdd[rr * nc * nc + i];
+            if (sum_sk_axes)
+                for (int i = 0; i < axes_len; ++i) sum_sk_axes[i] += pska[rr * axes_len + i];
+        }
+    }
+    free(tref); free(pd); free(pd2); free(pdd); free(psk); free(pska);
+    return err;
+}
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,320 @@
+"""Closed forms and exact moment recursions for the discrete scheme.
+
+TEST INFRASTRUCTURE ONLY.  These formulas pin the C oracle to mathematics
+that is independent of its code path: they never draw a random number and
+never step a sample path.
+
+* Deterministic limit (alpha = 0, Sec. 3): the forward-Euler step with the
+  Dirichlet wall stencil of Eq. (3.8) is diagonalised exactly by the
+  half-shifted sine modes sin(m pi (i+1/2)/N) (the wall stencil is the
+  centred stencil with an antisymmetric ghost cell), eigenvalue
+  1 - 4 r sin^2(m pi / 2N); periodic grids by Fourier modes, eigenvalue
+  1 - 4 r sin^2(pi k / N).
+* Exact first and second moments of the stochastic step.  The face noise is
+  independent of the state at the start of the step (the Ito reading of the
+  scheme, Sec. 3), so with T' = A T + b + sum_f g_f(T) N_f d_f:
+      m' = A m + b
+      C' = A C A^T + sum_f E[g_f^2] d_f d_f^T
+  with E[g_f^2] = 2 r eps w_f^2 ((P_f m + q_f)^2 + P_f C P_f^T) for heat
+  (noise proportional to the face temperature, Eq. (2.12)) and
+  2 r eps w_f^2 (P_f m + q_f) for species (noise proportional to the square
+  root of the face concentration, Eq. (4.7)).  This closure is exact.
+* Stationary covariance of that recursion (discrete Lyapunov equation,
+  the discrete-time analogue of the fluctuation-dissipation relation of
+  the supplement, Eq. (SM1.6)).
+* Closed forms: forward-Euler equilibrium covariance
+  eps T^2 (I + r L / 2)^{-1}, whose r -> 0 limit is eps T^2 I (Eq. (3.10));
+  periodic structure factor eps T^2 N / (1 - r mu_k / 2) whose r -> 0 limit is
+  the flat S_k = eps T^2 N (Eq. (3.12), with the cell volume restored);
+  the non-equilibrium long-range correlation of Eq. (3.13).
+"""
+import numpy as np
+import scipy.linalg
+
+
+# --------------------------------------------------------------- operators --
+
+def laplacian_1d(N, bc):
+    """Matrix L of the second-difference stencil (without the r factor):
+    interior T_{i+1} - 2 T_i + T_{i-1}; Dirichlet end cells -3 on the
+    diagonal (Eq. (3.8), wall values enter through the vector b);
+    periodic wrap."""
+    L = np.zeros((N, N))
+    for i in range(N):
+        L[i, i] = -2.0
+        if i > 0:
+            L[i, i - 1] += 1.0
+        elif bc == "periodic":
+            L[i, N - 1] += 1.0
+        if i < N - 1:
+            L[i, i + 1] += 1.0
+        elif bc == "periodic":
+            L[i, 0] += 1.0
+    if bc == "dirichlet":
+        L[0, 0] = -3.0
+        L[N - 1, N - 1] = -3.0
+    return L
+
+
+def faces_1d(N, bc, wall_lo, wall_hi):
+    """List of faces (P_f, q_f, w2_f, d_f): face value P_f.T + q_f, squared
+    wall weight w_f^2 (2 at Dirichlet walls, Sec. 3), and divergence vector
+    d_f (flux through face f leaves cell f and enters cell f-1, Eq. (3.3))."""
+    out = []
+    nf = N + 1 if bc == "dirichlet" else N
+    for f in range(nf):
+        P = np.zeros(N)
+        d = np.zeros(N)
+        q = 0.0
+        w2 = 1.0
+        if bc == "dirichlet" and f == 0:
+            q, w2 = wall_lo, 2.0
+        elif bc == "dirichlet" and f == N:
+            q, w2 = wall_hi, 2.0
+        else:
+            P[(f - 1) % N] += 0.5
+            P[f % N] += 0.5
+        if f < N:
+            d[f] -= 1.0
+        if f > 0:
+            d[f - 1] += 1.0
+        elif bc == "periodic":
+            d[N - 1] += 1.0
+        out.append((P, q, w2, d))
+    return out
+
+
+def laplacian_nd_periodic(shape):
+    """Periodic second-difference matrix summed over axes; cell index
+    x0 + n0*(x1 + n1*x2) with axis 0 fastest."""
+    n = int(np.prod(shape))
+    L = np.zeros((n, n))
+    dims = list(shape)
+    for i in range(n):
+        x = np.unravel_index(i, tuple(reversed(dims)))[::-1]
+        for a in range(len(dims)):
+            for s in (-1, 1):
+                y = list(x)
+                y[a] = (y[a] + s) % dims[a]
+                j = int(np.ravel_multi_index(tuple(reversed(y)), tuple(reversed(dims))))
+                L[i, j] += 1.0
+            L[i, i] -= 2.0
+    return L
+
+
+def faces_nd_periodic(shape):
+    n = int(np.prod(shape))
+    dims = list(shape)
+    out = []
+    for a in range(len(dims)):
+        for i in range(n):
+            x = np.unravel_index(i, tuple(reversed(dims)))[::-1]
+            y = list(x)
+            y[a] = (y[a] - 1) % dims[a]
+            j = int(np.ravel_multi_index(tuple(reversed(y)), tuple(reversed(dims))))
+            P = np.zeros(n)
+            P[i] += 0.5
+            P[j] += 0.5
+            d = np.zeros(n)
+            d[i] -= 1.0
+            d[j] += 1.0
+            out.append((P, 0.0, 1.0, d))
+    return out
+
+
+def scheme(prob_like):
+    """(A, b, faces, tref) of one forward-Euler step for a problem given as a
+    dict with dim, n, bc, r, eps, wall_lo, wall_hi, equation."""
+    dim = prob_like["dim"]
+    r = prob_like["r"]
+    if dim == 1:
+        N = prob_like["n"][0]
+        bc = prob_like["bc"]
+        L = laplacian_1d(N, bc)
+        b = np.zeros(N)
+        if bc == "dirichlet":
+            b[0] = 2.0 * r * prob_like["wall_lo"]
+            b[-1] = 2.0 * r * prob_like["wall_hi"]
+            x = (np.arange(N) + 0.5) / N
+            tref = prob_like["wall_lo"] + (prob_like["wall_hi"] - prob_like["wall_lo"]) * x
+        else:
+            tref = np.full(N, float(prob_like["wall_lo"]))
+        faces = faces_1d(N, bc, prob_like["wall_lo"], prob_like["wall_hi"])
+    else:
+        shape = tuple(prob_like["n"][:dim])
+        L = laplacian_nd_periodic(shape)
+        b = np.zeros(L.shape[0])
+        tref = np.full(L.shape[0], float(prob_like["wall_lo"]))
+        faces = faces_nd_periodic(shape)
+    A = np.eye(L.shape[0]) + r * L
+    return A, b, faces, tref, L
+
+
+def noise_cov(prob_like, faces, m, C):
+    """sum_f E[g_f^2] d_f d_f^T for mean m and covariance C of the state."""
+    r, eps = prob_like["r"], prob_like["eps"]
+    heat = prob_like.get("equation", "heat") == "heat"
+    n = len(m)
+    Q = np.zeros((n, n))
+    for P, q, w2, d in faces:
+        fm = P @ m + q
+        if heat:
+            e = 2.0 * r * eps * w2 * (fm * fm + P @ C @ P)
+        else:
+            e = 2.0 * r * eps * w2 * fm
+        Q += e * np.outer(d, d)
+    return Q
+
+
+def initial_moments(prob_like, tref):
+    """Mean and covariance of the seeded initial condition: T_ref plus iid
+    sigma*N(0,1) (sigma^2 = eps*T_mid^2 heat, eps*c_mid species), projected
+    to zero sum on periodic grids."""
+    n = len(tref)
+    C = np.zeros((n, n))
+    if prob_like.get("perturb_ic", 1):
+        mid = 0.5 * (prob_like["wall_lo"] + prob_like["wall_hi"])
+        if prob_like.get("equation", "heat") == "heat":
+            s2 = prob_like["eps"] * mid * mid
+        else:
+            s2 = prob_like["eps"] * abs(mid)
+        C = s2 * np.eye(n)
+        if prob_like["dim"] > 1 or prob_like["bc"] == "periodic":
+            Pr = np.eye(n) - np.ones((n, n)) / n
+            C = Pr @ C @ Pr
+    return tref.copy(), C
+
+
+def pooled_expectation(prob_like, nsteps, K, relax, step0=0):
+    """Exact expectation of the pooled sample statistics the oracle and the
+    GPU accumulate over steps step0+1..step0+nsteps (sample at step m iff
+    m % K == 0 and m > relax): returns dict with E[mean delta], E[second
+    moment of delta] (matrix), per-sample list not kept."""
+    A, b, faces, tref, _ = scheme(prob_like)
+    m, C = initial_moments(prob_like, tref)
+    n = len(m)
+    s1 = np.zeros(n)
+    s2 = np.zeros((n, n))
+    cnt = 0
+    for mstep in range(step0 + 1, step0 + nsteps + 1):
+        Q = noise_cov(prob_like, faces, m, C)
+        C = A @ C @ A.T + Q
+        m = A @ m + b
+        if mstep % K == 0 and mstep > relax:
+            dm = m - tref
+            s1 += dm
+            s2 += C + np.outer(dm, dm)
+            cnt += 1
+    return {"count": cnt, "mean_delta": s1 / cnt, "second": s2 / cnt,
+            "final_mean": m, "final_cov": C, "tref": tref}
+
+
+def stationary(prob_like, iters=50):
+    """Stationary mean and covariance of the exact moment recursion: the
+    mean solves m = A m + b; the covariance solves the discrete Lyapunov
+    equation C = A C A^T + Q(m, C), iterated on the (small, O(eps))
+    multiplicative part of Q."""
+    A, b, faces, tref, L = scheme(prob_like)
+    n = len(tref)
+    periodic = prob_like["dim"] > 1 or prob_like["bc"] == "periodic"
+    if periodic:
+        m = tref.copy()
+        Pr = np.eye(n) - np.ones((n, n)) / n
+    else:
+        m = np.linalg.solve(np.eye(n) - A, b)
+        Pr = np.eye(n)
+    C = np.zeros((n, n))
+    # project the zero mode out (the total is conserved on periodic grids)
+    Ap = Pr @ A @ Pr
+    for _ in range(iters):
+        Q = Pr @ noise_cov(prob_like, faces, m, C) @ Pr
+        Cn = scipy.linalg.solve_discrete_lyapunov(Ap, Q)
+        Cn = 0.5 * (Cn + Cn.T)
+        if np.max(np.abs(Cn - C)) <= 1e-15 * max(1.0, np.max(np.abs(Cn))):
+            C = Cn
+            break
+        C = Cn
+    return m, C
+
+
+# ---------------------------------------------------------- closed forms --
+
+def fe_equilibrium_cov(N, bc, r, eps, T):
+    """Linearised forward-Euler equilibrium covariance eps T^2 (I + r L/2)^{-1}
+    (Dirichlet), which tends to eps T^2 I (Eq. (3.10)) as r -> 0; on
+    periodic grids the zero mode is removed."""
+    L = laplacian_1d(N, bc)
+    M = np.eye(N) + 0.5 * r * L
+    if bc == "dirichlet":
+        return eps * T * T * np.linalg.inv(M)
+    Pr = np.eye(N) - np.ones((N, N)) / N
+    return eps * T * T * Pr @ np.linalg.pinv(Pr @ M @ Pr) @ Pr
+
+
+def fe_structure_factor(shape, r, eps_amp):
+    """Periodic forward-Euler structure factor for k != 0:
+    eps_amp * Ncells / (1 - r mu_k / 2), mu_k = sum_axes 4 sin^2(pi k_a/n_a).
+    eps_amp = eps T^2 (heat, linearised) or eps c (species, exact).
+    Array ordered like the cells (axis 0 fastest); entry k = 0 is set to 0."""
+    dims = list(shape)
+    ncell = int(np.prod(dims))
+    grids = np.meshgrid(*[np.arange(n) for n in reversed(dims)], indexing="ij")
+    mu = np.zeros(grids[0].shape)
+    for g, n in zip(grids, reversed(dims)):
+        mu += 4.0 * np.sin(np.pi * g / n) ** 2
+    S = eps_amp * ncell / (1.0 - 0.5 * r * mu)
+    S = S.ravel()
+    S[0] = 0.0
+    return S
+
+
+def fe_structure_factor_transient(shape, r, eps_amp, nsteps):
+    """S_k after n steps from a uniform state: S_inf (1 - lambda_k^{2n}),
+    lambda_k = 1 - r mu_k."""
+    dims = list(shape)
+    grids = np.meshgrid(*[np.arange(n) for n in reversed(dims)], indexing="ij")
+    mu = np.zeros(grids[0].shape)
+    for g, n in zip(grids, reversed(dims)):
+        mu += 4.0 * np.sin(np.pi * g / n) ** 2
+    lam = (1.0 - r * mu).ravel()
+    S = fe_structure_factor(shape, r, eps_amp)
+    return S * (1.0 - lam ** (2 * nsteps))
+
+
+def periodic_variance(N, r, eps_amp):
+    """Pointwise variance on a periodic 1D FE grid: (1/N^2) sum_{k!=0} S_k;
+    tends to eps_amp (1 - 1/N) (the conservation correction of Sec. 3) as r -> 0."""
+    S = fe_structure_factor((N,), r, eps_amp)
+    return S.sum() / (N * N)
+
+
+def long_range_correlation(N, eps, dT):
+    """Non-equilibrium long-range part of Eq. (3.13) in cell units:
+    eps (dT)^2 (i+1/2)(N-j-1/2)/N^3 for i <= j (symmetric)."""
+    x = np.arange(N) + 0.5
+    lo = np.minimum.outer(x, x)
+    hi = np.maximum.outer(x, x)
+    return eps * dT * dT * lo * (N - hi) / N ** 3
+
+
+def sine_mode_solution(N, r, wall_lo, wall_hi, T0, nsteps):
+    """Exact deterministic forward-Euler solution with Dirichlet walls:
+    T^n = T_lin + sum_m b_m lambda_m^n sin(m pi (i+1/2)/N),
+    lambda_m = 1 - 4 r sin^2(m pi/(2N)), b from the initial deviation."""
+    i = np.arange(N)
+    x = (i + 0.5) / N
+    tlin = wall_lo + (wall_hi - wall_lo) * x
+    m = np.arange(1, N + 1)
+    Phi = np.sin(np.pi * np.outer(i + 0.5, m) / N)       # [cell, mode]
+    bm = np.linalg.solve(Phi, np.asarray(T0) - tlin)
+    lam = 1.0 - 4.0 * r * np.sin(m * np.pi / (2.0 * N)) ** 2
+    return tlin + Phi @ (bm * lam ** nsteps)
+
+
+def fourier_mode_solution(N, r, T0, nsteps):
+    """Exact deterministic forward-Euler solution on a periodic grid:
+    each Fourier mode decays by (1 - 4 r sin^2(pi k/N))^n."""
+    k = np.arange(N)
+    lam = 1.0 - 4.0 * r * np.sin(np.pi * k / N) ** 2
+    That = np.fft.fft(np.asarray(T0))
+    return np.real(np.fft.ifft(That * lam ** nsteps))
