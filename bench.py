@@ -1,0 +1,353 @@
+"""Benchmark: SHE cell-updates/s incl. noise on one GB300 (or N, weak scaling).
+
+A bench *step* is one pass of the whole hot path over one batch of input:
+``--chunk`` forward-Euler time steps (default 10,000) of the full ensemble,
+including the inline Philox noise and the moment (and covariance) sampling
+every K steps after relaxation.  The default workload is the 1D
+non-equilibrium rod: 256 cells, walls 1 and 2, 4096 realizations, FP32 state,
+statistics every 10 steps after 1e5 steps; ``--steps 100`` covers its full
+1e6 time steps.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (there is no other reference implementation).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SHE cell-updates/s incl. noise, FP32-batched vs FP64 plain, % of roofline"
+UNIT = "cell-updates/s"
+
+# Algorithmic lane-operations per 1D cell-update, counted from the source
+# algorithm (Philox-4x32-10: per round 2 x (32x32->64 product = hi + lo),
+# 4 two-input xors, 2 key adds = 10 ops, 10 rounds per 4 normals -> 25 per
+# normal; Box-Muller: 2 uniforms (convert + scale), log, sqrt, sin/cos,
+# 2 products per pair -> 5.5 per normal; heat face flux: mean (2), amplitude
+# (1), noise (1); cell update: stencil (4) + flux difference (2) -> 6).
+OPS_PER_CELL_UPDATE_1D = 25.0 + 5.5 + 4.0 + 6.0
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="she_clocks_", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu_index)],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+            os.unlink(self.path)
+        except Exception:
+            return None
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------- workloads --
+
+def workload(name):
+    import she_workloads as W
+    if name == "gradient_rod":
+        p = W.gradient_rod()
+        desc = ("1D SHE rod, 256 cells, Dirichlet walls T_L=1 T_R=2, eps=1e-3, r=0.2, 4096 "
+                "realizations, FP32 state, moments every 10 steps after 1e5 steps")
+        return p, desc
+    if name == "oracle_rod":
+        p = W.oracle_rod(want_cov=0, want_sk=0)
+        return p, "1D SHE rod, 32 cells, walls 1, 16 realizations, FP64"
+    raise SystemExit("unknown workload %s" % name)
+
+
+def _cells(p):
+    c = 1
+    for v in p["n"][: p["dim"]]:
+        c *= v
+    return c
+
+
+# ------------------------------------------------------------ oracle timing --
+
+def oracle_sample_rate(p, seconds_hint=10.0):
+    """Time the FP64 oracle, as it stands, on a bounded sample of the workload:
+    64 realizations x 10,000 steps in the sampling phase (relax 0); returns
+    (cell-updates/s, threads, sample description)."""
+    from oracle import she as O
+    q = dict(p)
+    q["relax_steps"] = 0
+    R_s = 64
+    steps = 10_000
+    if _cells(p) <= 64:
+        R_s = 256
+    O.lib()
+    t0 = time.perf_counter()
+    O.run(q, R_s, steps)
+    dt = time.perf_counter() - t0
+    rate = R_s * steps * _cells(p) / dt
+    sample = ("%d realizations x %d steps of the workload (sampling phase, every %d steps), FP64 "
+              "oracle, %.1f s" % (R_s, steps, p["stats_interval"], dt))
+    return rate, O.num_threads(), sample
+
+
+# --------------------------------------------------------------- our arm ----
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2406_12157_gb300 as she
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    she.lib()
+    p, desc = workload(args.workload)
+    R = p["realizations"]
+    cells = _cells(p)
+    stream = torch.cuda.Stream()
+    # weak scaling: every rank runs a full ensemble on its own noise streams
+    sim = she.Simulation(p, stream=stream, stream_offset=rank * R)
+    chunk = args.chunk
+    cu_per_step = R * cells * chunk
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        sim.step(chunk)
+    barrier()
+    launches0 = sim.launches()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.add_(1.0)          # L2 flush (256 MB write) outside the timed events
+            ev[k][0].record(stream)
+        sim.step(chunk)
+        with torch.cuda.stream(stream):
+            ev[k][1].record(stream)
+    barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    launches = sim.launches() - launches0
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    total_cu = cu_per_step * args.steps * world
+    value = total_cu / (ms / 1e3)
+    try:
+        stats = sim.stats()      # the statistics of the run (device reduce + D2H)
+        assert np.all(np.isfinite(stats["var"]))
+    except she.SheError as e:
+        if e.status != she._abi.SHE_ERR_STATE:   # no sample yet in a short run is fine
+            raise
+
+    # ---- FP64 plain form on the same workload, a bounded number of steps ----
+    plain_steps = max(10, min(2000, int(2e8 // (R * cells))))
+    sim64 = she.Simulation(p, stream=stream, precision="fp64", kernel="plain", stream_offset=rank * R)
+    sim64.step(min(plain_steps, 50))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+    sim64.step(plain_steps)
+    with torch.cuda.stream(stream):
+        e1.record(stream)
+    torch.cuda.synchronize()
+    plain_rate = R * cells * plain_steps / (e0.elapsed_time(e1) / 1e3)
+    sim64.close()
+
+    # ---- e2e through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        state, step = sim.state()
+        host = torch.from_numpy(state).pin_memory()
+        host_np = host.numpy()
+        e2e_steps = max(1, min(args.steps, 10))
+        barrier()
+        t0 = time.perf_counter()
+        d2h = 0
+        for _ in range(e2e_steps):
+            sim.set_state(host_np, step)            # H2D of the step's input state
+            sim.step(chunk)
+            try:
+                out = sim.stats()                   # device reduce + D2H of the statistics
+                d2h = sum(v.nbytes for v in out.values() if hasattr(v, "nbytes"))
+                d2h += 2 * min(32, R) * cells * 8
+            except she.SheError as e:
+                if e.status != she._abi.SHE_ERR_STATE:
+                    raise
+                st_now, _ = sim.state()             # no sample yet: read the state back
+                d2h = st_now.nbytes
+            step += chunk
+        barrier()
+        te = time.perf_counter() - t0
+        e2e = {"value": cu_per_step * e2e_steps * world / te, "unit": UNIT,
+               "h2d_bytes_per_step": int(host_np.nbytes),
+               "d2h_bytes_per_step": int(d2h)}
+    sim.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    peaks, peak_src = _peaks()
+    per_launch_ms = ms / max(1, launches) if world == 1 else (ms / max(1, launches))
+    cu_per_launch = cu_per_step * args.steps / max(1, launches)
+    ops_per_launch = cu_per_launch * OPS_PER_CELL_UPDATE_1D
+    achieved = ops_per_launch / (per_launch_ms / 1e3) / 1e12          # Tops/s (lane-ops)
+    peak = 128 * 152 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
+            "unit": "Tops/s", "frac": round(achieved / peak, 4), "traffic": None,
+            "kernel": "k_step1d<float,8,dirichlet,heat>",
+            "ops_per_cell_update": OPS_PER_CELL_UPDATE_1D,
+            "peak_source": "128 lane-ops/clk/SM x 152 SMs x max SM clock (%s)" % peak_src}
+    cpu = None
+    if not args.no_cpu_baseline and world >= 1:
+        rate, cores, sample = oracle_sample_rate(p)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if p["precision"] == "fp32" else "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "cells": cells,
+                   "realizations_per_gpu": R, "time_steps_per_bench_step": chunk,
+                   "stats_interval": p["stats_interval"], "relax_steps": p["relax_steps"],
+                   "l2": "flushed between timed steps (256 MB write outside the events)"},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+        "clocks": clk,
+        "fp64_plain": {"value": plain_rate, "unit": UNIT, "steps": plain_steps,
+                       "speedup_fp32_batched": value / world / plain_rate},
+        "wall_s": t_wall,
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------- reference arm ----
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    from oracle import she as O
+    p, desc = workload(args.workload)
+    q = dict(p)
+    q["relax_steps"] = 0
+    cells = _cells(p)
+    R_s, steps = 32, 2000
+    O.lib()
+    for _ in range(max(0, args.warmup)):
+        O.run(q, R_s, 200)
+    times = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        O.run(q, R_s, steps, step0=k * steps)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = R_s * steps * cells * args.steps / total
+    sample = ("%d realizations x %d steps per bench step (sampling phase), FP64 oracle" % (R_s, steps))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "cells": cells},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="gradient_rod")
+    ap.add_argument("--chunk", type=int, default=10_000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

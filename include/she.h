@@ -1,0 +1,252 @@
+/*
+ * she.h -- C ABI of libshe: the explicit finite-volume Euler-Maruyama step of
+ * the stochastic heat equation (SHE) and of the stochastic species-diffusion
+ * equation, run over many independent realizations on one GPU, with the
+ * ensemble statistics accumulated from it.
+ *
+ * Method: Garcia, Bell, Nonaka, Srivastava, Ladiges, Kim, "An Introduction to
+ * Computational Fluctuating Hydrodynamics" (2024):
+ *   - the SHE, Sec. 2, Eq. (2.12) (1D compact form) and Eq. (2.10)/(2.11)
+ *     (3D, independent white noise per Cartesian direction);
+ *   - the forward-Euler scheme on a cell-centred grid, Sec. 3, Eq. (3.3),
+ *     face temperature = arithmetic mean of the two neighbours, discrete
+ *     noise Z = N(0,1)/sqrt(dV dt), Eq. (3.6)-(3.7);
+ *   - Dirichlet walls: boundary stencil of Eq. (3.8) and the sqrt(2) factor on
+ *     the wall-face noise (Sec. 3, text after Eq. (3.8)); periodic wrap;
+ *   - stochastic species diffusion, Sec. 4, Eq. (4.7) (noise amplitude
+ *     sqrt(2 D c / n0)) -- the Dean-Kawasaki form Eq. (4.8) is the case
+ *     n0 = 1 in number-density units;
+ *   - statistics: time averages after relaxation, Eq. (3.9); mean and
+ *     variance per cell and the equal-time correlation, Eq. (3.10) and
+ *     Eq. (3.13); the unnormalised structure factor S_k = <|hat T_k|^2> with
+ *     the DFT of Eq. (3.11).
+ * Everything on the hot path runs in this library's own CUDA kernels for
+ * sm_103a; there is no CPU fallback.
+ *
+ * Dimensionless form used internally: r = kappa dt / dx^2 (diffusion
+ * number), eps = k_B / (rho c_V dV) (relative equilibrium variance); the
+ * face noise amplitude is sqrt(2 r eps) * T_face (heat) or
+ * sqrt(2 r eps_c max(c_face, 0)) with eps_c = 1/(n0 dV) (species).
+ *
+ * Noise: Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) + Box-Muller,
+ * generated inline in the kernels (no noise array in device memory).
+ * Key = (seed lo 32 bits, seed hi 32 bits).  The normal of the low face of
+ * cell x on axis a at step n (0-based absolute index) of realization rho is
+ * normal g = a*Ncells + lin(x) (lin = x0 + n0*(x1 + n1*x2)): slot g%4 of
+ * Philox(counter = (g/4, n, rho, 0)).  The 1D right Dirichlet wall face uses
+ * slot n%4 of Philox(counter = (0, n/4, rho, 2)); the initial perturbation of
+ * cell i uses slot i%4 of Philox(counter = (i/4, 0, rho, 1)).  Slots 0..3 of
+ * a block (u0..u3) are R_a cos t_a, R_a sin t_a, R_b cos t_b, R_b sin t_b with
+ * U(u) = (u + 1/2)/2^32, R_a = sqrt(-2 ln U(u0)), t_a = 2 pi U(u1), and
+ * likewise (u2, u3).  Trajectories are therefore a pure function of (seed,
+ * realization index, absolute step), independent of launch shapes, and
+ * resumable bit for bit from a checkpoint.
+ *
+ * Conventions for every call:
+ *   - Every function returns a she_status and never throws or aborts across
+ *     the ABI.  On error the handle (if any) keeps a message readable with
+ *     she_last_error().
+ *   - The library owns all device memory it allocates (cudaMalloc at init,
+ *     cudaFree at she_free).  The caller owns `she_params` and every host
+ *     array it passes; pointers are only read or written during the call.
+ *   - A handle is not thread-safe; use one handle per host thread.
+ *   - Work is enqueued on `params.stream` (a cudaStream_t, NULL = legacy
+ *     default stream).  she_step_n is asynchronous; she_stats, she_get_state
+ *     and she_set_state synchronise that stream.
+ */
+#ifndef SHE_H
+#define SHE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum she_status {
+    SHE_OK = 0,
+    SHE_ERR_INVALID_ARG = 1,  /* bad parameter, size or pointer */
+    SHE_ERR_UNSTABLE = 2,     /* r = kappa dt/dx^2 > 1/(2 dim): FE unstable (Sec. 3) */
+    SHE_ERR_OOM = 3,          /* device allocation failed */
+    SHE_ERR_CUDA = 4,         /* a CUDA runtime call failed */
+    SHE_ERR_NONFINITE = 5,    /* the state holds NaN/Inf after a step batch */
+    SHE_ERR_TIMEOUT = 6,      /* a bounded device wait gave up */
+    SHE_ERR_STATE = 7,        /* call not valid in the handle's current state */
+    SHE_ERR_UNSUPPORTED = 8   /* valid combination not implemented on this path */
+} she_status;
+
+enum { SHE_HEAT = 0, SHE_SPECIES = 1 };        /* equation */
+enum { SHE_PERIODIC = 0, SHE_DIRICHLET = 1 };  /* boundary */
+enum { SHE_FP32 = 0, SHE_FP64 = 1 };           /* state/step precision */
+enum { SHE_FE = 0 };                           /* scheme: forward Euler */
+enum { SHE_SK_FULL = 1, SHE_SK_AXES = 2 };     /* want_sk bits */
+enum { SHE_KERNEL_AUTO = 0,                    /* fused on-chip / streaming kernels */
+       SHE_KERNEL_PLAIN = 1 };                 /* plain one-launch-per-step form */
+
+/*
+ * Problem statement, in the paper's physical terms (Sec. 3 and the
+ * program's parameters).  All lengths, times and temperatures in any
+ * consistent unit system.
+ */
+typedef struct she_params {
+    int32_t dim;          /* 1, 2 or 3 */
+    int32_t n[3];         /* cells per axis; unused axes must be 1; each used axis >= 2 */
+    double dx;            /* uniform cell size */
+    double area;          /* 1D: cross-section A (dV = A dx); 2D: thickness h
+                             (dV = h dx^2); 3D: ignored (dV = dx^3) */
+    int32_t equation;     /* SHE_HEAT or SHE_SPECIES */
+    int32_t bc;           /* SHE_DIRICHLET (1D only) or SHE_PERIODIC (all axes) */
+    double kappa;         /* heat: thermal diffusivity lambda/(rho c_V) */
+    double rho_cv;        /* heat: rho c_V */
+    double kB;            /* heat: Boltzmann constant */
+    double D;             /* species: diffusion coefficient */
+    double n0;            /* species: number density of the pure state */
+    double wall_lo;       /* Dirichlet: T_L (or c_L); periodic: the uniform
+                             reference value (must equal wall_hi) */
+    double wall_hi;       /* Dirichlet: T_R (or c_R) */
+    double dt;            /* time step */
+    uint64_t seed;        /* Philox key */
+    int64_t realizations; /* independent sample paths, >= 1 */
+    int32_t scheme;       /* SHE_FE */
+    int32_t stochastic;   /* 1: thermal noise on; 0: deterministic (alpha = 0) */
+    int32_t perturb_ic;   /* 1: T_ref + sigma N(0,1) per cell, sigma^2 = eps T_mid^2
+                             (heat) or eps_c c_mid (species); zero-sum on periodic grids */
+    int32_t precision;    /* SHE_FP32 or SHE_FP64 */
+    int32_t stats_interval; /* K: sample every K steps (>= 1) */
+    int32_t want_cov;     /* 1: accumulate the full equal-time covariance
+                             (1D, N <= 256) */
+    int64_t relax_steps;  /* sample after step m (1-based) iff m % K == 0 and m > relax */
+    int32_t want_sk;      /* SHE_SK_FULL (1D, 2D) and/or SHE_SK_AXES (any dim) */
+    int32_t kernel;       /* SHE_KERNEL_AUTO or SHE_KERNEL_PLAIN */
+    int32_t steps_per_launch; /* 0 = library default */
+    int32_t stream_offset; /* noise stream (counter word 2) of realization 0; realization
+                              rho uses stream stream_offset + rho, so disjoint shards of
+                              one ensemble can run in separate handles or processes */
+    void* stream;         /* cudaStream_t */
+} she_params;
+
+typedef struct she_handle she_handle;
+
+/*
+ * Statistics, finalised on the host from the FP64 device accumulators.
+ * The caller allocates every non-NULL array (sizes from she_stats_sizes);
+ * NULL arrays are skipped.  For a batch handle the per-cell arrays hold the
+ * instances back to back (instance i at offset cell_offset[i]).
+ *   mean_i = T_ref,i + sum(delta_i)/n, delta = T - T_ref (T_ref: the linear
+ *            steady profile, or the uniform value on periodic grids)
+ *   var_i  = sum(delta_i^2)/n - (sum(delta_i)/n)^2   (biased 1/n, as Sec. 3)
+ *   cov_ij = sum(delta_i delta_j)/n - mu_i mu_j      (Eq. (3.13) generalised)
+ *   sk_k   = <|hat T_k|^2> (Eq. (3.11)); sk_fluct_k = <|hat T_k|^2> - |<hat T_k>|^2
+ *   sk_axes: per axis a, <|hat delta_k|^2> of the 1D DFT along a, averaged
+ *            over all lines along a; axes back to back (n[0] + n[1] + n[2])
+ *   var_se_i: standard error of var_i from 32 contiguous realization
+ *            batches (NaN when fewer than 2 realizations per batch exist)
+ * n is the pooled sample count (realizations x sampling times).
+ */
+typedef struct she_stats_out {
+    int64_t n_samples;    /* out */
+    double* mean;         /* [cells] */
+    double* var;          /* [cells] */
+    double* var_se;       /* [cells] */
+    double* cov;          /* [cells*cells], row-major; needs want_cov */
+    double* sk;           /* [cells]; needs want_sk & SHE_SK_FULL */
+    double* sk_fluct;     /* [cells]; needs want_sk & SHE_SK_FULL */
+    double* sk_axes;      /* [n0+n1+n2]; needs want_sk & SHE_SK_AXES */
+    double* sum_d;        /* [cells] raw pooled sum of delta */
+    double* sum_d2;       /* [cells] raw pooled sum of delta^2 */
+} she_stats_out;
+
+typedef struct she_sizes {
+    int64_t cells;        /* cells per realization (batch: total over instances) */
+    int64_t realizations;
+    int64_t instances;    /* 1, or the batch count */
+    int64_t state_bytes;  /* bytes of the full state buffer (get/set_state) */
+    int64_t elem_bytes;   /* 4 (FP32) or 8 (FP64) */
+    int64_t axes_len;     /* n[0] + n[1] + n[2] over used axes */
+    uint64_t step;        /* absolute steps taken so far */
+} she_sizes;
+
+/*
+ * Validate `p` and create a handle: allocates the state [realizations][cells]
+ * and FP64 accumulators on the device, writes the initial condition with
+ * the IC stream of the noise generator, zeroes the accumulators.
+ * Errors: SHE_ERR_INVALID_ARG (NULL pointers, dim/n/realizations/K out of
+ * range, non-positive dx/dt/coefficients, periodic grid with
+ * wall_lo != wall_hi -- the paper's program rejects that combination too --,
+ * Dirichlet on dim > 1, want_cov with N > 256 or dim > 1, SHE_SK_FULL on
+ * dim 3), SHE_ERR_UNSTABLE (r > 1/(2 dim)), SHE_ERR_OOM, SHE_ERR_CUDA.
+ * On error *out is NULL.
+ */
+she_status she_init(const she_params* p, she_handle** out);
+
+/*
+ * Batched uneven instances: `count` independent 1D problems p[0..count-1]
+ * (each its own N, kappa, walls, dt and seed; all must share dim = 1,
+ * equation, bc, precision, stats_interval, relax_steps and realizations = 1)
+ * advanced together by one persistent launch per step batch.  The noise
+ * stream index of instance i is i.  Same errors as she_init per instance.
+ */
+she_status she_init_batch(const she_params* p, int64_t count, she_handle** out);
+
+/* Enqueue n forward-Euler steps (asynchronous on the handle's stream).
+ * The absolute step counter advances by n; it must stay below 2^32.
+ * Errors: SHE_ERR_INVALID_ARG (NULL handle or counter overflow),
+ * SHE_ERR_CUDA (launch failure). */
+she_status she_step_n(she_handle* h, uint64_t n);
+
+/* Sizes of the state and statistics arrays. */
+she_status she_get_sizes(const she_handle* h, she_sizes* s);
+
+/* Synchronise the stream, reduce the accumulators over realizations (on the
+ * device, FP64) and write the requested statistics (see she_stats_out).
+ * Errors: SHE_ERR_STATE if no sample was taken yet (n_samples = 0, arrays
+ * untouched), SHE_ERR_INVALID_ARG if cov/sk are requested but were not
+ * enabled at init, SHE_ERR_NONFINITE if the state became non-finite. */
+she_status she_stats(she_handle* h, she_stats_out* out);
+
+/* Zero every accumulator (the state and step counter are kept). */
+she_status she_reset_stats(she_handle* h);
+
+/* Copy the state [realizations][cells] (elements of elem_bytes) to
+ * `host_buf` (bytes must equal state_bytes) and the absolute step counter
+ * to *step (may be NULL).  Synchronises the stream. */
+she_status she_get_state(she_handle* h, void* host_buf, size_t bytes, uint64_t* step);
+
+/* Overwrite the state from `host_buf` (same layout as she_get_state) and set
+ * the absolute step counter.  Accumulators are not touched. */
+she_status she_set_state(she_handle* h, const void* host_buf, size_t bytes, uint64_t step);
+
+/* Device-resident variants for callers that keep the state in their own
+ * device memory: `dev_buf` is a device pointer of state_bytes bytes; the
+ * copy is enqueued on the handle's stream (no synchronisation). */
+she_status she_get_state_device(she_handle* h, void* dev_buf, size_t bytes);
+she_status she_set_state_device(she_handle* h, const void* dev_buf, size_t bytes, uint64_t step);
+
+/* Human-readable message of the last error on `h` ("" if none; a static
+ * message if h is NULL). */
+const char* she_last_error(const she_handle* h);
+
+/* Release all device memory of the handle.  NULL-safe. */
+void she_free(she_handle* h);
+
+/*
+ * Test hook of the noise generator: for counters (c0 + k, c1, c2, c3),
+ * k = 0..count-1, write the raw Philox-4x32-10 words to bits[4k..4k+3] and
+ * the four Box-Muller normals in FP64 to z64[4k..] and in FP32 to z32[4k..]
+ * (host arrays; any may be NULL).  Runs the library's device code on the
+ * current device and synchronises.  Errors: SHE_ERR_INVALID_ARG
+ * (count < 0 or > 2^24), SHE_ERR_CUDA.
+ */
+she_status she_noise_probe(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                           int64_t count, uint32_t* bits, double* z64, float* z32);
+
+/* Number of kernel launches enqueued by this handle since init (for the
+ * benchmark's launch accounting). */
+int64_t she_launch_count(const she_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SHE_H */

@@ -1,0 +1,247 @@
+"""GB300-native stochastic heat / species diffusion library (Python binding).
+
+Thin binding of the C ABI in ``include/she.h`` (``libshe.so``), with the same
+names.  Argument marshalling only; every step runs in the library's CUDA
+kernels for sm_103a.  If the library is not built, every call raises
+``LibraryMissing`` -- there is no CPU fallback.
+
+Method: Garcia et al., "An Introduction to Computational Fluctuating
+Hydrodynamics" (2024), Sec. 3 (forward-Euler scheme, Eq. (3.3); Dirichlet
+walls, Eq. (3.8); sampling, Eq. (3.9)) and Sec. 4 (species noise, Eq. (4.7)).
+"""
+import ctypes
+
+import numpy as np
+
+from . import _abi
+from ._abi import (LibraryMissing, SHE_DIRICHLET, SHE_FE, SHE_FP32, SHE_FP64, SHE_HEAT,  # noqa: F401
+                   SHE_KERNEL_AUTO, SHE_KERNEL_PLAIN, SHE_PERIODIC, SHE_SK_AXES, SHE_SK_FULL,
+                   SHE_SPECIES)
+
+__all__ = ["SheError", "LibraryMissing", "params_from_problem", "she_init", "she_init_batch",
+           "she_step_n", "she_get_sizes", "she_stats", "she_reset_stats", "she_get_state",
+           "she_set_state", "she_get_state_device", "she_set_state_device", "she_last_error",
+           "she_free", "she_noise_probe", "she_launch_count", "Simulation", "lib"]
+
+
+class SheError(RuntimeError):
+    def __init__(self, status, msg):
+        self.status = status
+        super().__init__("%s: %s" % (_abi.STATUS_NAMES.get(status, status), msg))
+
+
+def lib():
+    return _abi.load()
+
+
+def _check(status, h=None, what=""):
+    if status != _abi.SHE_OK:
+        msg = what
+        if h is not None:
+            m = lib().she_last_error(h)
+            if m:
+                msg = "%s: %s" % (what, m.decode(errors="replace"))
+        raise SheError(status, msg)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    ptr = getattr(stream, "cuda_stream", None)     # torch.cuda.Stream
+    if ptr is not None:
+        return int(ptr)
+    raise TypeError("stream must be None, an int cudaStream_t or a torch.cuda.Stream")
+
+
+def params_from_problem(prob, stream=None, **overrides):
+    """Build a ``she_params`` from a problem dict in the paper's physical
+    terms (see she_workloads for the fields)."""
+    q = dict(prob)
+    q.update(overrides)
+    p = _abi.she_params()
+    p.dim = int(q["dim"])
+    n = list(q["n"]) + [1] * (3 - len(q["n"]))
+    for a in range(3):
+        p.n[a] = int(n[a]) if a < p.dim else 1
+    p.dx = float(q["dx"])
+    p.area = float(q.get("area", 1.0))
+    p.equation = SHE_HEAT if q.get("equation", "heat") in ("heat", SHE_HEAT) else SHE_SPECIES
+    p.bc = SHE_DIRICHLET if q.get("bc", "dirichlet") in ("dirichlet", SHE_DIRICHLET) else SHE_PERIODIC
+    p.kappa = float(q.get("kappa", 1.0))
+    p.rho_cv = float(q.get("rho_cv", 1.0))
+    p.kB = float(q.get("kB", 0.0))
+    p.D = float(q.get("D", 1.0))
+    p.n0 = float(q.get("n0", 1.0))
+    p.wall_lo = float(q["wall_lo"])
+    p.wall_hi = float(q["wall_hi"])
+    p.dt = float(q["dt"])
+    p.seed = int(q.get("seed", 0))
+    p.realizations = int(q.get("realizations", 1))
+    p.scheme = SHE_FE
+    p.stochastic = int(q.get("stochastic", 1))
+    p.perturb_ic = int(q.get("perturb_ic", 1))
+    prec = q.get("precision", "fp32")
+    p.precision = SHE_FP64 if prec in ("fp64", SHE_FP64) else SHE_FP32
+    p.stats_interval = int(q.get("stats_interval", 10))
+    p.want_cov = int(q.get("want_cov", 0))
+    p.relax_steps = int(q.get("relax_steps", 0))
+    p.want_sk = int(q.get("want_sk", 0))
+    kern = q.get("kernel", "auto")
+    p.kernel = SHE_KERNEL_PLAIN if kern in ("plain", SHE_KERNEL_PLAIN) else SHE_KERNEL_AUTO
+    p.steps_per_launch = int(q.get("steps_per_launch", 0))
+    p.stream_offset = int(q.get("stream_offset", 0))
+    sp = _stream_ptr(stream)
+    p.stream = sp
+    return p
+
+
+def she_init(params):
+    h = ctypes.c_void_p()
+    _check(lib().she_init(ctypes.byref(params), ctypes.byref(h)), None, "she_init")
+    return h
+
+
+def she_init_batch(params_list):
+    arr = (_abi.she_params * len(params_list))(*params_list)
+    h = ctypes.c_void_p()
+    _check(lib().she_init_batch(arr, len(params_list), ctypes.byref(h)), None, "she_init_batch")
+    return h
+
+
+def she_step_n(h, n):
+    _check(lib().she_step_n(h, int(n)), h, "she_step_n")
+
+
+def she_get_sizes(h):
+    s = _abi.she_sizes()
+    _check(lib().she_get_sizes(h, ctypes.byref(s)), h, "she_get_sizes")
+    return s
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if a is not None else None
+
+
+def she_stats(h, cov=False, sk=False, sk_axes=False, raw=False):
+    """Finalised statistics as numpy arrays (see she_stats_out in she.h)."""
+    s = she_get_sizes(h)
+    c = int(s.cells)
+    out = {k: np.empty(c) for k in ("mean", "var", "var_se")}
+    if cov:
+        out["cov"] = np.empty(c * c)
+    if sk:
+        out["sk"] = np.empty(c)
+        out["sk_fluct"] = np.empty(c)
+    if sk_axes:
+        out["sk_axes"] = np.empty(int(s.axes_len))
+    if raw:
+        out["sum_d"] = np.empty(c)
+        out["sum_d2"] = np.empty(c)
+    st = _abi.she_stats_out()
+    for k, v in out.items():
+        setattr(st, k, _ptr(v))
+    _check(lib().she_stats(h, ctypes.byref(st)), h, "she_stats")
+    out["n_samples"] = int(st.n_samples)
+    if cov:
+        out["cov"] = out["cov"].reshape(c, c)
+    return out
+
+
+def she_reset_stats(h):
+    _check(lib().she_reset_stats(h), h, "she_reset_stats")
+
+
+def she_get_state(h):
+    """Return (state [realizations, cells] as float32/float64, step)."""
+    s = she_get_sizes(h)
+    dt = np.float64 if s.elem_bytes == 8 else np.float32
+    buf = np.empty((int(s.realizations), int(s.cells)), dtype=dt)
+    step = ctypes.c_uint64()
+    _check(lib().she_get_state(h, buf.ctypes.data, buf.nbytes, ctypes.byref(step)), h, "she_get_state")
+    return buf, int(step.value)
+
+
+def she_set_state(h, state, step):
+    s = she_get_sizes(h)
+    dt = np.float64 if s.elem_bytes == 8 else np.float32
+    buf = np.ascontiguousarray(state, dtype=dt)
+    _check(lib().she_set_state(h, buf.ctypes.data, buf.nbytes, int(step)), h, "she_set_state")
+
+
+def she_get_state_device(h, dev_ptr, nbytes):
+    _check(lib().she_get_state_device(h, int(dev_ptr), int(nbytes)), h, "she_get_state_device")
+
+
+def she_set_state_device(h, dev_ptr, nbytes, step):
+    _check(lib().she_set_state_device(h, int(dev_ptr), int(nbytes), int(step)), h,
+           "she_set_state_device")
+
+
+def she_last_error(h):
+    m = lib().she_last_error(h)
+    return m.decode(errors="replace") if m else ""
+
+
+def she_free(h):
+    if h is not None and h.value:
+        lib().she_free(h)
+        h.value = None
+
+
+def she_launch_count(h):
+    return int(lib().she_launch_count(h))
+
+
+def she_noise_probe(seed, c0, c1, c2, c3, count):
+    """Raw Philox words and Box-Muller normals (FP64 and FP32) from the
+    device generator for counters (c0 + k, c1, c2, c3), k < count."""
+    bits = np.empty(4 * count, dtype=np.uint32)
+    z64 = np.empty(4 * count, dtype=np.float64)
+    z32 = np.empty(4 * count, dtype=np.float32)
+    _check(lib().she_noise_probe(seed, c0, c1, c2, c3, count, bits.ctypes.data, z64.ctypes.data,
+                                 z32.ctypes.data), None, "she_noise_probe")
+    return bits.reshape(count, 4), z64.reshape(count, 4), z32.reshape(count, 4)
+
+
+class Simulation:
+    """Owning wrapper of one handle: ``with Simulation(problem) as sim: ...``."""
+
+    def __init__(self, prob, stream=None, **overrides):
+        self.params = params_from_problem(prob, stream=stream, **overrides)
+        self.h = she_init(self.params)
+
+    def step(self, n):
+        she_step_n(self.h, n)
+
+    def stats(self, **kw):
+        return she_stats(self.h, **kw)
+
+    def state(self):
+        return she_get_state(self.h)
+
+    def set_state(self, state, step):
+        she_set_state(self.h, state, step)
+
+    def sizes(self):
+        return she_get_sizes(self.h)
+
+    def launches(self):
+        return she_launch_count(self.h)
+
+    def close(self):
+        she_free(self.h)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

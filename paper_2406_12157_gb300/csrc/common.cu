@@ -1,0 +1,142 @@
+// common.cu -- initial condition, accumulator reduction and the noise probe.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "philox.cuh"
+#include "she_internal.cuh"
+
+namespace she {
+
+// Initial condition (one block per realization): T_ref plus, if requested,
+// sigma * N(0,1) with sigma^2 the equilibrium variance at the mid value
+// (heat eps T^2, Eq. (3.10); species eps c, Sec. 4 exercise 5), drawn from
+// the IC stream (tag 1).  Periodic grids conserve the total, so the
+// perturbation is projected to zero sum (two passes over the row).
+template <typename Real>
+__global__ void k_init_state(Real* state, int64_t cells, int dim_is_1d_dirichlet, double wlo,
+                             double whi, double sigma, int perturb, int periodic, uint32_t key0,
+                             uint32_t key1, uint32_t stream0)
+{
+    const int rho = blockIdx.x;
+    const uint32_t stream = stream0 + (uint32_t)rho;
+    Real* row = state + (size_t)rho * (size_t)cells;
+    __shared__ double red[32];
+    double local = 0.0;
+    for (int64_t i = threadIdx.x; i < cells; i += blockDim.x) {
+        double z = 0.0;
+        if (perturb) {
+            double zz[4];
+            box_muller4(philox4x32_10(make_uint4((uint32_t)(i >> 2), 0u, stream, 1u), key0, key1), zz);
+            z = sigma * zz[i & 3];
+            local += z;
+        }
+        const double ref = dim_is_1d_dirichlet
+                               ? wlo + (whi - wlo) * ((double)i + 0.5) / (double)cells
+                               : wlo;
+        row[i] = (Real)(ref + z);
+    }
+    if (!(perturb && periodic)) return;
+    // block sum of the perturbation
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) red[0] = v;
+    }
+    __syncthreads();
+    const double mean = red[0] / (double)cells;
+    for (int64_t i = threadIdx.x; i < cells; i += blockDim.x) {
+        // recompute the deviate so the subtraction is done in double
+        double zz[4];
+        box_muller4(philox4x32_10(make_uint4((uint32_t)(i >> 2), 0u, stream, 1u), key0, key1), zz);
+        row[i] = (Real)(wlo + (sigma * zz[i & 3] - mean));
+    }
+}
+
+cudaError_t launch_init_state(Handle& h)
+{
+    const Problem& p = h.prob;
+    const bool dir1d = (p.dim == 1 && p.bc == SHE_DIRICHLET);
+    const double mid = 0.5 * (p.wall_lo + p.wall_hi);
+    const double sigma = (p.equation == SHE_HEAT) ? sqrt(p.eps) * fabs(mid) : sqrt(p.eps * fabs(mid));
+    const uint32_t key0 = (uint32_t)(p.seed & 0xffffffffu), key1 = (uint32_t)(p.seed >> 32);
+    const dim3 grid((unsigned)h.R), block(256);
+    h.launches += 1;
+    if (h.precision == SHE_FP64)
+        k_init_state<double><<<grid, block, 0, h.stream>>>((double*)h.d_state, p.cells, dir1d, p.wall_lo,
+                                                           p.wall_hi, sigma, h.perturb_ic,
+                                                           p.bc == SHE_PERIODIC, key0, key1, h.stream0);
+    else
+        k_init_state<float><<<grid, block, 0, h.stream>>>((float*)h.d_state, p.cells, dir1d, p.wall_lo,
+                                                          p.wall_hi, sigma, h.perturb_ic,
+                                                          p.bc == SHE_PERIODIC, key0, key1, h.stream0);
+    return cudaGetLastError();
+}
+
+// Sum the per-realization FP64 accumulators over `batches` contiguous
+// realization batches: out[b][i] = sum over realizations of batch b.
+__global__ void k_reduce_batches(const double* __restrict__ acc1, const double* __restrict__ acc2,
+                                 int64_t cells, int64_t R, int batches, double* out1, double* out2)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cells) return;
+    for (int b = 0; b < batches; ++b) {
+        const int64_t r0 = R * b / batches, r1 = R * (b + 1) / batches;
+        double a1 = 0.0, a2 = 0.0;
+        for (int64_t r = r0; r < r1; ++r) {
+            a1 += acc1[r * cells + i];
+            a2 += acc2[r * cells + i];
+        }
+        out1[(int64_t)b * cells + i] = a1;
+        out2[(int64_t)b * cells + i] = a2;
+    }
+}
+
+cudaError_t launch_reduce_batches(const Handle& h, int batches, double* d_out1, double* d_out2)
+{
+    const int tpb = 256;
+    const int64_t cells = h.prob.cells;
+    k_reduce_batches<<<(unsigned)((cells + tpb - 1) / tpb), tpb, 0, h.stream>>>(
+        h.d_acc1, h.d_acc2, cells, h.R, batches, d_out1, d_out2);
+    return cudaGetLastError();
+}
+
+__global__ void k_noise_probe(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                              int64_t count, uint32_t* bits, double* z64, float* z32)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    const uint32_t key0 = (uint32_t)(seed & 0xffffffffu), key1 = (uint32_t)(seed >> 32);
+    const uint4 u = philox4x32_10(make_uint4(c0 + (uint32_t)k, c1, c2, c3), key0, key1);
+    if (bits) {
+        bits[4 * k + 0] = u.x;
+        bits[4 * k + 1] = u.y;
+        bits[4 * k + 2] = u.z;
+        bits[4 * k + 3] = u.w;
+    }
+    if (z64) {
+        double z[4];
+        box_muller4(u, z);
+        for (int s = 0; s < 4; ++s) z64[4 * k + s] = z[s];
+    }
+    if (z32) {
+        float z[4];
+        box_muller4(u, z);
+        for (int s = 0; s < 4; ++s) z32[4 * k + s] = z[s];
+    }
+}
+
+cudaError_t launch_noise_probe(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                               int64_t count, uint32_t* d_bits, double* d_z64, float* d_z32)
+{
+    if (count <= 0) return cudaSuccess;
+    const int tpb = 256;
+    k_noise_probe<<<(unsigned)((count + tpb - 1) / tpb), tpb>>>(seed, c0, c1, c2, c3, count, d_bits, d_z64,
+                                                                 d_z32);
+    return cudaGetLastError();
+}
+
+}  // namespace she

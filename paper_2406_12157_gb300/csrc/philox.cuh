@@ -1,0 +1,78 @@
+// philox.cuh -- inline counter-based noise for the step kernels.
+//
+// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+// easy as 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplies with the
+// constants 0xD2511F53 / 0xCD9E8D57 and a Weyl-sequence key schedule
+// (+0x9E3779B9, +0xBB67AE85 per round).  Box & Muller (1958) turns the four
+// 32-bit words of one block into four N(0,1) deviates (both the cosine and
+// the sine branch of each pair).  The paper draws iid N(0,1) per face and step
+// (Sec. 3, Eq. (3.7)); the counter layout that addresses a face is fixed in
+// she.h.  Nothing here is ever written to device memory: each step kernel
+// regenerates the deviates it needs in registers.
+#pragma once
+#include <cstdint>
+
+namespace she {
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Four normals from one block, double precision: U = (u + 1/2) 2^-32,
+// z0,z1 = sqrt(-2 ln U(u0)) (cos, sin)(2 pi U(u1)); z2,z3 likewise (u2, u3).
+__device__ __forceinline__ void box_muller4(uint4 u, double z[4])
+{
+    const double scale = 2.3283064365386962890625e-10;  // 2^-32
+    const double ra = sqrt(-2.0 * log(((double)u.x + 0.5) * scale));
+    const double rb = sqrt(-2.0 * log(((double)u.z + 0.5) * scale));
+    double sa, ca, sb, cb;
+    sincospi(2.0 * (((double)u.y + 0.5) * scale), &sa, &ca);
+    sincospi(2.0 * (((double)u.w + 0.5) * scale), &sb, &cb);
+    z[0] = ra * ca;
+    z[1] = ra * sa;
+    z[2] = rb * cb;
+    z[3] = rb * sb;
+}
+
+// Same deviates in single precision.  The radius uses the hardware base-2
+// logarithm (ln U = ln 2 * log2 U); the angle is taken as
+// 2 pi U - pi = 2 pi (u - 2^31 + 1/2) 2^-32, inside (-pi, pi) where the fast
+// sine/cosine are accurate, and the sign flip cos(x + pi) = -cos(x) is folded
+// into the radius.  U rounds to 1.0f only when the exact radius is below
+// 3.5e-4; the radius is then 0 instead (max abs error 3.5e-4, probability
+// 2^-25 per pair).
+__device__ __forceinline__ void box_muller4(uint4 u, float z[4])
+{
+    const float scale = 2.3283064365386963e-10f;          // 2^-32
+    const float m2ln2 = -1.38629436111989061883f;         // -2 ln 2
+    const float ang = 1.46291807926715968105e-09f;        // 2 pi 2^-32
+    const float ang0 = 7.31459039633579840525e-10f;       // pi 2^-32
+    float xa = m2ln2 * __log2f(fmaf((float)u.x, scale, 0.5f * scale));
+    float xb = m2ln2 * __log2f(fmaf((float)u.z, scale, 0.5f * scale));
+    xa = fmaxf(xa, 1e-30f);
+    xb = fmaxf(xb, 1e-30f);
+    const float ra = -(xa * rsqrtf(xa));
+    const float rb = -(xb * rsqrtf(xb));
+    const float ta = fmaf((float)(int32_t)(u.y ^ 0x80000000u), ang, ang0);
+    const float tb = fmaf((float)(int32_t)(u.w ^ 0x80000000u), ang, ang0);
+    float sa, ca, sb, cb;
+    __sincosf(ta, &sa, &ca);
+    __sincosf(tb, &sb, &cb);
+    z[0] = ra * ca;
+    z[1] = ra * sa;
+    z[2] = rb * cb;
+    z[3] = rb * sb;
+}
+
+}  // namespace she

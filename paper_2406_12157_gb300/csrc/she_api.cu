@@ -1,0 +1,440 @@
+// she_api.cu -- the C ABI declared in include/she.h: validation, device
+// allocation, dispatch of the step kernels, and host-side finalisation of the
+// statistics from the FP64 device accumulators.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "she_internal.cuh"
+
+using she::Handle;
+
+namespace {
+
+const char* kNullHandleMsg = "she: null handle";
+
+she_status fail(Handle* h, she_status st, const std::string& msg)
+{
+    if (h) h->err = msg;
+    return st;
+}
+
+she_status cuda_fail(Handle* h, cudaError_t e, const char* where)
+{
+    std::string m = std::string("she: CUDA error in ") + where + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return fail(h, SHE_ERR_OOM, m);
+    return fail(h, SHE_ERR_CUDA, m);
+}
+
+double cell_volume(const she_params& p)
+{
+    if (p.dim == 1) return p.area * p.dx;
+    if (p.dim == 2) return p.area * p.dx * p.dx;
+    return p.dx * p.dx * p.dx;
+}
+
+// Validate and convert the physical parameters to the dimensionless pair
+// (r, eps) of Eq. (3.3)/(3.7).
+she_status convert(const she_params& p, she::Problem& out, std::string& msg)
+{
+    if (p.dim < 1 || p.dim > 3) { msg = "she: dim must be 1, 2 or 3"; return SHE_ERR_INVALID_ARG; }
+    int64_t cells = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (a < p.dim) {
+            if (p.n[a] < 2) { msg = "she: every used axis needs n >= 2 cells"; return SHE_ERR_INVALID_ARG; }
+            cells *= p.n[a];
+        } else if (p.n[a] != 1 && p.n[a] != 0) {
+            msg = "she: unused axes must have n = 1";
+            return SHE_ERR_INVALID_ARG;
+        }
+    }
+    if (cells > (int64_t)1 << 31) { msg = "she: too many cells per realization"; return SHE_ERR_INVALID_ARG; }
+    if (!(p.dx > 0.0) || !(p.dt > 0.0) || (p.dim < 3 && !(p.area > 0.0))) {
+        msg = "she: dx, dt and area must be positive";
+        return SHE_ERR_INVALID_ARG;
+    }
+    if (p.equation != SHE_HEAT && p.equation != SHE_SPECIES) { msg = "she: bad equation"; return SHE_ERR_INVALID_ARG; }
+    if (p.bc != SHE_PERIODIC && p.bc != SHE_DIRICHLET) { msg = "she: bad boundary"; return SHE_ERR_INVALID_ARG; }
+    if (p.bc == SHE_DIRICHLET && p.dim > 1) {
+        msg = "she: Dirichlet walls are supported in 1D only (2D/3D grids are periodic)";
+        return SHE_ERR_INVALID_ARG;
+    }
+    if (p.bc == SHE_PERIODIC && p.wall_lo != p.wall_hi) {
+        msg = "she: a periodic grid is an equilibrium problem: wall_lo must equal wall_hi";
+        return SHE_ERR_INVALID_ARG;
+    }
+    if (!std::isfinite(p.wall_lo) || !std::isfinite(p.wall_hi)) { msg = "she: walls must be finite"; return SHE_ERR_INVALID_ARG; }
+    const double dV = cell_volume(p);
+    double r, eps;
+    if (p.equation == SHE_HEAT) {
+        if (!(p.kappa > 0.0) || !(p.rho_cv > 0.0) || !(p.kB >= 0.0)) {
+            msg = "she: kappa, rho_cv must be positive and kB non-negative";
+            return SHE_ERR_INVALID_ARG;
+        }
+        r = p.kappa * p.dt / (p.dx * p.dx);
+        eps = p.kB / (p.rho_cv * dV);
+    } else {
+        if (!(p.D > 0.0) || !(p.n0 > 0.0)) { msg = "she: D and n0 must be positive"; return SHE_ERR_INVALID_ARG; }
+        r = p.D * p.dt / (p.dx * p.dx);
+        eps = 1.0 / (p.n0 * dV);
+    }
+    if (!std::isfinite(r) || !std::isfinite(eps)) { msg = "she: non-finite r or eps"; return SHE_ERR_INVALID_ARG; }
+    if (r > 1.0 / (2.0 * p.dim)) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "she: forward Euler is unstable: r = kappa dt/dx^2 = %g > 1/(2 dim) = %g", r,
+                 1.0 / (2.0 * p.dim));
+        msg = buf;
+        return SHE_ERR_UNSTABLE;
+    }
+    out.dim = p.dim;
+    for (int a = 0; a < 3; ++a) out.n[a] = (a < p.dim) ? p.n[a] : 1;
+    out.cells = cells;
+    out.equation = p.equation;
+    out.bc = p.bc;
+    out.r = r;
+    out.eps = eps;
+    out.wall_lo = p.wall_lo;
+    out.wall_hi = p.wall_hi;
+    out.seed = p.seed;
+    return SHE_OK;
+}
+
+void release(Handle* h)
+{
+    if (!h) return;
+    cudaFree(h->d_state);
+    cudaFree(h->d_state2);
+    cudaFree(h->d_acc1);
+    cudaFree(h->d_acc2);
+    cudaFree(h->d_face);
+    cudaFree(h->d_flags);
+    cudaFree(h->d_red);
+    h->d_state = h->d_state2 = nullptr;
+    h->d_acc1 = h->d_acc2 = h->d_face = h->d_red = nullptr;
+    h->d_flags = nullptr;
+}
+
+int64_t samples_in(uint64_t step_from, uint64_t nsteps, int K, int64_t relax)
+{
+    // number of m in (step_from, step_from + nsteps] with m % K == 0 and m > relax
+    const int64_t lo = std::max<int64_t>((int64_t)step_from, relax);
+    const int64_t hi = (int64_t)(step_from + nsteps);
+    if (hi <= lo) return 0;
+    return hi / K - lo / K;
+}
+
+int default_steps_per_launch(const Handle& h)
+{
+    if (h.steps_per_launch > 0) return h.steps_per_launch;
+    // FP32 partial sums hold at most 256 samples before the FP64 flush
+    int64_t spl = (int64_t)h.K * 256;
+    if (spl > 4096) spl = 4096 - 4096 % h.K;
+    if (spl < h.K) spl = h.K;
+    return (int)spl;
+}
+
+}  // namespace
+
+extern "C" {
+
+she_status she_init(const she_params* p, she_handle** out)
+{
+    if (!out) return SHE_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!p) return SHE_ERR_INVALID_ARG;
+    Handle* h = new (std::nothrow) Handle();
+    if (!h) return SHE_ERR_OOM;
+    std::string msg;
+    she_status st = convert(*p, h->prob, msg);
+    if (st == SHE_OK && p->realizations < 1) { st = SHE_ERR_INVALID_ARG; msg = "she: realizations must be >= 1"; }
+    if (st == SHE_OK && p->realizations > (int64_t)1 << 30) { st = SHE_ERR_INVALID_ARG; msg = "she: too many realizations"; }
+    if (st == SHE_OK && p->stats_interval < 1) { st = SHE_ERR_INVALID_ARG; msg = "she: stats_interval must be >= 1"; }
+    if (st == SHE_OK && p->precision != SHE_FP32 && p->precision != SHE_FP64) {
+        st = SHE_ERR_INVALID_ARG; msg = "she: precision must be SHE_FP32 or SHE_FP64";
+    }
+    if (st == SHE_OK && p->scheme != SHE_FE) { st = SHE_ERR_UNSUPPORTED; msg = "she: only the forward-Euler scheme"; }
+    if (st == SHE_OK && p->kernel != SHE_KERNEL_AUTO && p->kernel != SHE_KERNEL_PLAIN) {
+        st = SHE_ERR_INVALID_ARG; msg = "she: bad kernel selector";
+    }
+    if (st == SHE_OK && p->kernel == SHE_KERNEL_PLAIN && (p->precision != SHE_FP64 || p->dim != 1)) {
+        st = SHE_ERR_UNSUPPORTED; msg = "she: the plain form is FP64 and 1D";
+    }
+    if (st == SHE_OK && (p->stream_offset < 0 || (int64_t)p->stream_offset + p->realizations > ((int64_t)1 << 32))) {
+        st = SHE_ERR_INVALID_ARG; msg = "she: stream_offset + realizations must fit in 32 bits";
+    }
+    if (st == SHE_OK && p->steps_per_launch < 0) { st = SHE_ERR_INVALID_ARG; msg = "she: steps_per_launch < 0"; }
+    if (st == SHE_OK && (p->want_sk & ~3)) { st = SHE_ERR_INVALID_ARG; msg = "she: bad want_sk bits"; }
+    if (st == SHE_OK && p->want_cov) { st = SHE_ERR_UNSUPPORTED; msg = "she: covariance not built yet"; }
+    if (st == SHE_OK && p->want_sk) { st = SHE_ERR_UNSUPPORTED; msg = "she: S(k) not built yet"; }
+    if (st == SHE_OK && p->dim > 1) { st = SHE_ERR_UNSUPPORTED; msg = "she: 2D/3D not built yet"; }
+    if (st != SHE_OK) {
+        fprintf(stderr, "%s\n", msg.c_str());
+        delete h;
+        return st;
+    }
+    h->R = p->realizations;
+    h->precision = p->precision;
+    h->K = p->stats_interval;
+    h->relax = p->relax_steps;
+    h->want_cov = p->want_cov;
+    h->want_sk = p->want_sk;
+    h->kernel = p->kernel;
+    h->stochastic = p->stochastic ? 1 : 0;
+    h->perturb_ic = p->perturb_ic ? 1 : 0;
+    h->steps_per_launch = p->steps_per_launch;
+    h->stream0 = (uint32_t)p->stream_offset;
+    h->stream = (cudaStream_t)p->stream;
+
+    const size_t cells = (size_t)h->prob.cells;
+    const size_t elem = h->precision == SHE_FP64 ? 8 : 4;
+    const size_t nstate = (size_t)h->R * cells;
+    cudaError_t e = cudaSuccess;
+    e = cudaMalloc(&h->d_state, nstate * elem);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_acc1, nstate * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_acc2, nstate * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_flags, sizeof(int));
+    const int batches = (int)std::min<int64_t>(32, h->R);
+    h->red_bytes = 2 * (size_t)batches * cells * sizeof(double);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_red, h->red_bytes);
+    if (e == cudaSuccess && h->kernel == SHE_KERNEL_PLAIN) {
+        e = cudaMalloc(&h->d_state2, nstate * elem);
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_face, (size_t)h->R * (cells + 1) * sizeof(double));
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_acc1, 0, nstate * sizeof(double), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_acc2, 0, nstate * sizeof(double), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flags, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) e = she::launch_init_state(*h);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        she_status s2 = cuda_fail(h, e, "she_init");
+        fprintf(stderr, "%s\n", h->err.c_str());
+        release(h);
+        delete h;
+        return s2;
+    }
+    *out = reinterpret_cast<she_handle*>(h);
+    return SHE_OK;
+}
+
+she_status she_init_batch(const she_params* p, int64_t count, she_handle** out)
+{
+    (void)p;
+    (void)count;
+    if (out) *out = nullptr;
+    return SHE_ERR_UNSUPPORTED;
+}
+
+she_status she_step_n(she_handle* hh, uint64_t n)
+{
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return SHE_ERR_INVALID_ARG;
+    if (n == 0) return SHE_OK;
+    if (h->step + n > (uint64_t)0xffffffffu) return fail(h, SHE_ERR_INVALID_ARG, "she: step counter would pass 2^32");
+    const int spl = default_steps_per_launch(*h);
+    uint64_t left = n;
+    while (left > 0) {
+        int chunk = (int)std::min<uint64_t>(left, (uint64_t)spl);
+        cudaError_t e;
+        if (h->kernel == SHE_KERNEL_PLAIN) e = she::launch_step1d_plain(*h, (uint32_t)h->step, chunk);
+        else e = she::launch_step1d(*h, (uint32_t)h->step, chunk);
+        if (e != cudaSuccess) return cuda_fail(h, e, "she_step_n");
+        h->samples_per_real += samples_in(h->step, (uint64_t)chunk, h->K, h->relax);
+        h->step += (uint64_t)chunk;
+        left -= (uint64_t)chunk;
+    }
+    return SHE_OK;
+}
+
+she_status she_get_sizes(const she_handle* hh, she_sizes* s)
+{
+    const Handle* h = reinterpret_cast<const Handle*>(hh);
+    if (!h || !s) return SHE_ERR_INVALID_ARG;
+    s->cells = h->prob.cells;
+    s->realizations = h->R;
+    s->instances = 1;
+    s->elem_bytes = h->precision == SHE_FP64 ? 8 : 4;
+    s->state_bytes = h->R * h->prob.cells * s->elem_bytes;
+    s->axes_len = 0;
+    for (int a = 0; a < h->prob.dim; ++a) s->axes_len += h->prob.n[a];
+    s->step = h->step;
+    return SHE_OK;
+}
+
+she_status she_stats(she_handle* hh, she_stats_out* out)
+{
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !out) return SHE_ERR_INVALID_ARG;
+    if ((out->cov && !h->want_cov) || ((out->sk || out->sk_fluct) && !(h->want_sk & SHE_SK_FULL)) ||
+        (out->sk_axes && !(h->want_sk & SHE_SK_AXES)))
+        return fail(h, SHE_ERR_INVALID_ARG, "she: statistic requested that was not enabled at init");
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(sync)");
+    int flags = 0;
+    e = cudaMemcpy(&flags, h->d_flags, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(flags)");
+    out->n_samples = h->samples_per_real * h->R;
+    if (flags & 1) return fail(h, SHE_ERR_NONFINITE, "she: the state became non-finite");
+    if (h->samples_per_real == 0) return fail(h, SHE_ERR_STATE, "she: no sample taken yet");
+    const int64_t cells = h->prob.cells;
+    const int B = (int)std::min<int64_t>(32, h->R);
+    double* d1 = h->d_red;
+    double* d2 = h->d_red + (size_t)B * cells;
+    e = she::launch_reduce_batches(*h, B, d1, d2);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(reduce)");
+    std::vector<double> b1((size_t)B * cells), b2((size_t)B * cells);
+    e = cudaMemcpy(b1.data(), d1, b1.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(b2.data(), d2, b2.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(copy)");
+    const double n = (double)out->n_samples;
+    const bool dir = h->prob.dim == 1 && h->prob.bc == SHE_DIRICHLET;
+    for (int64_t i = 0; i < cells; ++i) {
+        double s1 = 0.0, s2 = 0.0;
+        for (int b = 0; b < B; ++b) {
+            s1 += b1[(size_t)b * cells + i];
+            s2 += b2[(size_t)b * cells + i];
+        }
+        const double ref = dir ? h->prob.wall_lo + (h->prob.wall_hi - h->prob.wall_lo) * ((double)i + 0.5) / (double)cells
+                               : h->prob.wall_lo;
+        const double mu = s1 / n;
+        if (out->sum_d) out->sum_d[i] = s1;
+        if (out->sum_d2) out->sum_d2[i] = s2;
+        if (out->mean) out->mean[i] = ref + mu;
+        if (out->var) out->var[i] = s2 / n - mu * mu;
+        if (out->var_se) {
+            // batch b holds realizations [R b / B, R (b+1) / B)
+            double sv = 0.0, svv = 0.0;
+            for (int b = 0; b < B; ++b) {
+                const int64_t rb = h->R * (b + 1) / B - h->R * b / B;
+                const double nb = (double)(h->samples_per_real * rb);
+                const double m1 = b1[(size_t)b * cells + i] / nb;
+                const double v = b2[(size_t)b * cells + i] / nb - m1 * m1;
+                sv += v;
+                svv += v * v;
+            }
+            const double mv = sv / B;
+            out->var_se[i] = (B >= 2) ? std::sqrt(std::max(0.0, (svv / B - mv * mv) * B / (B - 1)) / B)
+                                      : std::numeric_limits<double>::quiet_NaN();
+        }
+    }
+    return SHE_OK;
+}
+
+she_status she_reset_stats(she_handle* hh)
+{
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return SHE_ERR_INVALID_ARG;
+    const size_t nstate = (size_t)h->R * (size_t)h->prob.cells;
+    cudaError_t e = cudaMemsetAsync(h->d_acc1, 0, nstate * sizeof(double), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_acc2, 0, nstate * sizeof(double), h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "she_reset_stats");
+    h->samples_per_real = 0;
+    return SHE_OK;
+}
+
+she_status she_get_state(she_handle* hh, void* host_buf, size_t bytes, uint64_t* step)
+{
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return SHE_ERR_INVALID_ARG;
+    const size_t need = (size_t)h->R * (size_t)h->prob.cells * (h->precision == SHE_FP64 ? 8 : 4);
+    if (!host_buf || bytes != need) return fail(h, SHE_ERR_INVALID_ARG, "she_get_state: bad buffer size");
+    cudaError_t e = cudaMemcpyAsync(host_buf, h->d_state, need, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "she_get_state");
+    if (step) *step = h->step;
+    return SHE_OK;
+}
+
+she_status she_set_state(she_handle* hh, const void* host_buf, size_t bytes, uint64_t step)
+{
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return SHE_ERR_INVALID_ARG;
+    const size_t need = (size_t)h->R * (size_t)h->prob.cells * (h->precision == SHE_FP64 ? 8 : 4);
+    if (!host_buf || bytes != need) return fail(h, SHE_ERR_INVALID_ARG, "she_set_state: bad buffer size");
+    if (step > (uint64_t)0xffffffffu) return fail(h, SHE_ERR_INVALID_ARG, "she_set_state: step >= 2^32");
+    cudaError_t e = cudaMemcpyAsync(h->d_state, host_buf, need, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flags, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "she_set_state");
+    h->step = step;
+    return SHE_OK;
+}
+
+she_status she_get_state_device(she_handle* hh, void* dev_buf, size_t bytes)
+{
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return SHE_ERR_INVALID_ARG;
+    const size_t need = (size_t)h->R * (size_t)h->prob.cells * (h->precision == SHE_FP64 ? 8 : 4);
+    if (!dev_buf || bytes != need) return fail(h, SHE_ERR_INVALID_ARG, "she_get_state_device: bad buffer size");
+    cudaError_t e = cudaMemcpyAsync(dev_buf, h->d_state, need, cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "she_get_state_device");
+    return SHE_OK;
+}
+
+she_status she_set_state_device(she_handle* hh, const void* dev_buf, size_t bytes, uint64_t step)
+{
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return SHE_ERR_INVALID_ARG;
+    const size_t need = (size_t)h->R * (size_t)h->prob.cells * (h->precision == SHE_FP64 ? 8 : 4);
+    if (!dev_buf || bytes != need) return fail(h, SHE_ERR_INVALID_ARG, "she_set_state_device: bad buffer size");
+    if (step > (uint64_t)0xffffffffu) return fail(h, SHE_ERR_INVALID_ARG, "she_set_state_device: step >= 2^32");
+    cudaError_t e = cudaMemcpyAsync(h->d_state, dev_buf, need, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flags, 0, sizeof(int), h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "she_set_state_device");
+    h->step = step;
+    return SHE_OK;
+}
+
+const char* she_last_error(const she_handle* hh)
+{
+    const Handle* h = reinterpret_cast<const Handle*>(hh);
+    if (!h) return kNullHandleMsg;
+    return h->err.c_str();
+}
+
+void she_free(she_handle* hh)
+{
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    release(h);
+    delete h;
+}
+
+she_status she_noise_probe(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, int64_t count,
+                           uint32_t* bits, double* z64, float* z32)
+{
+    if (count < 0 || count > ((int64_t)1 << 24)) return SHE_ERR_INVALID_ARG;
+    if (count == 0) return SHE_OK;
+    uint32_t* db = nullptr;
+    double* dz = nullptr;
+    float* df = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (bits) e = cudaMalloc(&db, (size_t)count * 4 * sizeof(uint32_t));
+    if (e == cudaSuccess && z64) e = cudaMalloc(&dz, (size_t)count * 4 * sizeof(double));
+    if (e == cudaSuccess && z32) e = cudaMalloc(&df, (size_t)count * 4 * sizeof(float));
+    if (e == cudaSuccess) e = she::launch_noise_probe(seed, c0, c1, c2, c3, count, db, dz, df);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && bits) e = cudaMemcpy(bits, db, (size_t)count * 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && z64) e = cudaMemcpy(z64, dz, (size_t)count * 4 * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && z32) e = cudaMemcpy(z32, df, (size_t)count * 4 * sizeof(float), cudaMemcpyDeviceToHost);
+    cudaFree(db);
+    cudaFree(dz);
+    cudaFree(df);
+    return e == cudaSuccess ? SHE_OK : SHE_ERR_CUDA;
+}
+
+int64_t she_launch_count(const she_handle* hh)
+{
+    const Handle* h = reinterpret_cast<const Handle*>(hh);
+    return h ? h->launches : -1;
+}
+
+}  // extern "C"

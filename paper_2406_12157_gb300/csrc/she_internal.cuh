@@ -1,0 +1,86 @@
+// she_internal.cuh -- declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/she.h"
+
+namespace she {
+
+constexpr int kWarpsPerBlock1D = 4;
+
+// Dimensionless problem on the device side (one instance).
+struct Problem {
+    int dim = 1;
+    int n[3] = {1, 1, 1};
+    int64_t cells = 0;
+    int equation = SHE_HEAT;
+    int bc = SHE_DIRICHLET;
+    double r = 0.0;       // kappa dt / dx^2 (species: D dt / dx^2)
+    double eps = 0.0;     // k_B/(rho c_V dV)   (species: 1/(n0 dV))
+    double wall_lo = 0.0, wall_hi = 0.0;
+    uint64_t seed = 0;
+};
+
+// Arguments of the 1D step kernels (one realization per warp).
+template <typename Real>
+struct Step1DArgs {
+    Real* state;          // [R][N], realization-major
+    double* acc1;         // [R][N] sum of delta (FP64, per realization)
+    double* acc2;         // [R][N] sum of delta^2
+    int* flags;           // bit 0: non-finite state seen
+    int N;
+    int R;
+    Real r;               // diffusion number
+    Real amp2;            // 2 r eps: squared noise amplitude per unit face value
+    Real wall_lo, wall_hi;
+    uint32_t key0, key1;
+    uint32_t step0;       // absolute index of the first step of this launch
+    int nsteps;
+    int K;                // sampling interval
+    long long relax;      // sample after step m (1-based) iff m % K == 0 && m > relax
+    uint32_t stream0;     // noise stream of realization 0
+    int stochastic;
+};
+
+struct Handle {
+    Problem prob;
+    int64_t R = 0;
+    int precision = SHE_FP32;
+    int K = 10;
+    int64_t relax = 0;
+    int want_cov = 0, want_sk = 0;
+    int kernel = SHE_KERNEL_AUTO;
+    int stochastic = 1, perturb_ic = 1;
+    int steps_per_launch = 0;
+    uint32_t stream0 = 0;          // noise stream of realization 0
+    cudaStream_t stream = nullptr;
+    uint64_t step = 0;             // absolute steps taken
+    int64_t samples_per_real = 0;  // samples taken per realization
+    int64_t launches = 0;
+    // device buffers
+    void* d_state = nullptr;       // [R][cells] float or double
+    void* d_state2 = nullptr;      // ping-pong buffer (plain form, streaming kernels)
+    double* d_acc1 = nullptr;      // [R][cells]
+    double* d_acc2 = nullptr;      // [R][cells]
+    double* d_face = nullptr;      // plain form: face fluxes [R][N+1]
+    int* d_flags = nullptr;
+    double* d_red = nullptr;       // reduction scratch
+    size_t red_bytes = 0;
+    std::string err;
+};
+
+// Launchers (return cudaSuccess or the launch error).
+cudaError_t launch_init_state(Handle& h);
+cudaError_t launch_step1d(Handle& h, uint32_t step0, int nsteps);
+cudaError_t launch_step1d_plain(Handle& h, uint32_t step0, int nsteps);
+cudaError_t launch_reduce_batches(const Handle& h, int batches, double* d_out1, double* d_out2);
+cudaError_t launch_noise_probe(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                               int64_t count, uint32_t* d_bits, double* d_z64, float* d_z32);
+
+inline bool sample_step(int64_t m, int K, int64_t relax) { return (m % K) == 0 && m > relax; }
+
+}  // namespace she

@@ -1,0 +1,378 @@
+// step1d.cu -- forward-Euler step of the 1D stochastic heat / species
+// diffusion equation over many realizations (Sec. 3, Eq. (3.3), Dirichlet
+// walls Eq. (3.8), species noise Eq. (4.7)).
+//
+// Fused kernel: one warp owns one realization for a whole launch of many
+// steps.  Lane l keeps cells [l*C, l*C + C) of the row in registers; the only
+// inter-lane traffic per step is three shuffles (left/right neighbour value,
+// right-neighbour face flux) plus the periodic wrap or the wall-noise
+// broadcast.  The face noise is regenerated in registers from Philox (one
+// block = four faces), so per cell-update the kernel touches no memory at all;
+// the state is read once at launch start and written once at launch end.
+// Moments of delta = T - T_ref are summed in registers over the launch
+// (at most a few hundred samples, FP32 for the FP32 path) and flushed into
+// per-realization FP64 accumulators at launch end.
+//
+// Plain form (the comparison baseline, FP64): one launch computes every face
+// flux of every realization into device memory, a second applies the flux
+// divergence and the stencil, a third samples; three launches per step.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "philox.cuh"
+#include "she_internal.cuh"
+
+namespace she {
+
+template <typename Real>
+__device__ __forceinline__ Real face_amp(Real face_value, Real amp2, Real s_heat, bool species)
+{
+    if (species) {
+        const Real c = face_value > Real(0) ? face_value : Real(0);
+        return sqrt(amp2 * c);
+    }
+    return s_heat * face_value;
+}
+
+__device__ __forceinline__ float fsqrt_any(float x) { return sqrtf(x); }
+__device__ __forceinline__ double fsqrt_any(double x) { return sqrt(x); }
+
+template <typename Real>
+__device__ __forceinline__ bool finite_any(Real v) { return isfinite(v); }
+
+// ---------------------------------------------------------------- fused ----
+
+template <typename Real, int C, bool DIR, bool SPECIES>
+__global__ void __launch_bounds__(kWarpsPerBlock1D * 32)
+k_step1d(const Step1DArgs<Real> a)
+{
+    static_assert(C % 4 == 0, "cells per lane must be a multiple of 4");
+    using Acc = Real;
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int rho = blockIdx.x * kWarpsPerBlock1D + (threadIdx.x >> 5);
+    if (rho >= a.R) return;  // warp-uniform
+
+    const int N = a.N;
+    const int i0 = lane * C;
+    const int jlast = N - 1 - i0;          // cell N-1 sits at j = jlast in lane last_lane
+    const int last_lane = (N - 1) / C;
+    Real* row = a.state + (size_t)rho * (size_t)N;
+
+    Real T[C];
+    Acc s1[C], s2[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        const int i = i0 + j;
+        T[j] = (i < N) ? row[i] : Real(0);
+        s1[j] = Acc(0);
+        s2[j] = Acc(0);
+    }
+    const Real r = a.r;
+    const Real amp2 = a.amp2;
+    const Real s_heat = fsqrt_any(amp2);
+    const Real half = Real(0.5);
+    const Real sq2 = Real(1.41421356237309504880);
+    const Real wlo = a.wall_lo, whi = a.wall_hi;
+    const Real dref = DIR ? (whi - wlo) / Real(N) : Real(0);
+    const uint32_t stream = a.stream0 + (uint32_t)rho;
+    // Flux through the high Dirichlet wall: Sec. 3 -- face value T_R, noise x sqrt(2).
+    const Real g_wall_amp = sq2 * face_amp<Real>(whi, amp2, s_heat, SPECIES);
+    const Real g_low_amp = sq2 * face_amp<Real>(wlo, amp2, s_heat, SPECIES);
+
+    Real wz[4] = {Real(0), Real(0), Real(0), Real(0)};
+    uint32_t wwin = 0xffffffffu;
+    int nsamp = 0;
+
+    for (int s = 0; s < a.nsteps; ++s) {
+        const uint32_t n = a.step0 + (uint32_t)s;
+        const Real left_nb = __shfl_up_sync(FULL, T[C - 1], 1);
+        const Real right_nb = __shfl_down_sync(FULL, T[0], 1);
+        Real wrap_lo = Real(0), wrap_hi = Real(0);   // periodic: T_{N-1}, T_0
+        if (!DIR) {
+            Real mine = T[0];
+#pragma unroll
+            for (int j = 0; j < C; ++j)
+                if (j == jlast) mine = T[j];
+            wrap_lo = __shfl_sync(FULL, mine, last_lane);
+            wrap_hi = __shfl_sync(FULL, T[0], 0);
+        }
+        // Right-wall noise: slot n%4 of block (0, n/4, stream, 2); lanes 0..7
+        // hold the blocks of a 32-step window.
+        Real g_high = Real(0);
+        if (DIR) {
+            if (a.stochastic) {
+                const uint32_t win = n >> 5;
+                if (win != wwin) {
+                    wwin = win;
+                    const uint4 u = philox4x32_10(make_uint4(0u, win * 8u + (uint32_t)(lane & 7), stream, 2u),
+                                                  a.key0, a.key1);
+                    box_muller4(u, wz);
+                }
+                const uint32_t slot = n & 3u;
+                const Real v = slot == 0 ? wz[0] : slot == 1 ? wz[1] : slot == 2 ? wz[2] : wz[3];
+                g_high = g_wall_amp * __shfl_sync(FULL, v, (int)((n & 31u) >> 2));
+            }
+        }
+
+        // Pipeline over this lane's faces f = i0 + j (the low face of cell
+        // i0 + j): compute G_f, then update cell f-1 in place (it needs G_{f-1}
+        // and G_f and the old values of cells f-2, f-1, f).
+        Real g_first = Real(0), g_prev = Real(0);
+        Real g_zero = Real(0);
+        Real old_prev = (i0 == 0) ? (DIR ? Real(2) * wlo - T[0] : wrap_lo) : left_nb;
+        Real old_cur = T[0];
+#pragma unroll
+        for (int g = 0; g < C / 4; ++g) {
+            Real z[4] = {Real(0), Real(0), Real(0), Real(0)};
+            if (a.stochastic) {
+                const uint4 u = philox4x32_10(make_uint4((uint32_t)(i0 / 4 + g), n, stream, 0u), a.key0, a.key1);
+                box_muller4(u, z);
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int j = 4 * g + t;
+                const int f = i0 + j;
+                Real gf;
+                if (j == 0) {
+                    // face i0: between cell i0-1 (neighbour lane or wall/wrap) and i0
+                    if (f == 0) {
+                        gf = DIR ? g_low_amp * z[0] : face_amp<Real>(half * (wrap_lo + T[0]), amp2, s_heat, SPECIES) * z[0];
+                    } else {
+                        gf = face_amp<Real>(half * (left_nb + T[0]), amp2, s_heat, SPECIES) * z[0];
+                    }
+                    g_first = gf;
+                    g_zero = __shfl_sync(FULL, g_first, 0);
+                } else {
+                    if (f == N) {
+                        gf = DIR ? g_high : g_zero;          // ragged lane: the high face
+                    } else {
+                        gf = face_amp<Real>(half * (old_cur + T[j]), amp2, s_heat, SPECIES) * z[t];
+                    }
+                    // update cell j-1 (global f-1)
+                    const Real tc = old_cur;
+                    Real tr = T[j];
+                    if (f == N) tr = DIR ? Real(2) * whi - tc : wrap_hi;
+                    T[j - 1] = tc + r * (tr - Real(2) * tc + old_prev) + (gf - g_prev);
+                    old_prev = tc;
+                    old_cur = T[j];
+                }
+                g_prev = gf;
+            }
+        }
+        // last cell of the lane (j = C-1): its high face is the neighbour
+        // lane's first face, or the wall/wrap face when it is cell N-1.
+        {
+            const Real g_next = __shfl_down_sync(FULL, g_first, 1);
+            const Real tc = old_cur;
+            Real tr = right_nb;
+            Real gr = g_next;
+            if (i0 + C - 1 == N - 1) {
+                tr = DIR ? Real(2) * whi - tc : wrap_hi;
+                gr = DIR ? g_high : g_zero;
+            }
+            T[C - 1] = tc + r * (tr - Real(2) * tc + old_prev) + (gr - g_prev);
+        }
+
+        const long long m = (long long)n + 1;
+        if ((m % a.K) == 0 && m > a.relax) {
+            ++nsamp;
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                const Real ref = DIR ? fma(dref, Real(i0 + j) + half, wlo) : wlo;
+                const Acc d = (Acc)(T[j] - ref);
+                s1[j] += d;
+                s2[j] = fma(d, d, s2[j]);
+            }
+        }
+    }
+
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        const int i = i0 + j;
+        if (i < N) {
+            row[i] = T[j];
+            bad |= !finite_any(T[j]);
+        }
+    }
+    if (nsamp > 0) {
+        double* p1 = a.acc1 + (size_t)rho * (size_t)N;
+        double* p2 = a.acc2 + (size_t)rho * (size_t)N;
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            const int i = i0 + j;
+            if (i < N) {
+                p1[i] += (double)s1[j];
+                p2[i] += (double)s2[j];
+            }
+        }
+    }
+    if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.flags, 1);
+}
+
+template <typename Real, int C>
+static cudaError_t launch_c(const Step1DArgs<Real>& a, bool dir, bool species, cudaStream_t st)
+{
+    const dim3 block(kWarpsPerBlock1D * 32);
+    const dim3 grid((a.R + kWarpsPerBlock1D - 1) / kWarpsPerBlock1D);
+    if (dir) {
+        if (species) k_step1d<Real, C, true, true><<<grid, block, 0, st>>>(a);
+        else k_step1d<Real, C, true, false><<<grid, block, 0, st>>>(a);
+    } else {
+        if (species) k_step1d<Real, C, false, true><<<grid, block, 0, st>>>(a);
+        else k_step1d<Real, C, false, false><<<grid, block, 0, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+template <typename Real>
+static cudaError_t launch_fused(Handle& h, uint32_t step0, int nsteps)
+{
+    Step1DArgs<Real> a;
+    a.state = (Real*)h.d_state;
+    a.acc1 = h.d_acc1;
+    a.acc2 = h.d_acc2;
+    a.flags = h.d_flags;
+    a.N = h.prob.n[0];
+    a.R = (int)h.R;
+    a.r = (Real)h.prob.r;
+    a.amp2 = (Real)(h.stochastic ? 2.0 * h.prob.r * h.prob.eps : 0.0);
+    a.wall_lo = (Real)h.prob.wall_lo;
+    a.wall_hi = (Real)h.prob.wall_hi;
+    a.key0 = (uint32_t)(h.prob.seed & 0xffffffffu);
+    a.key1 = (uint32_t)(h.prob.seed >> 32);
+    a.step0 = step0;
+    a.nsteps = nsteps;
+    a.K = h.K;
+    a.relax = (long long)h.relax;
+    a.stream0 = h.stream0;
+    a.stochastic = h.stochastic;
+    const bool dir = h.prob.bc == SHE_DIRICHLET;
+    const bool sp = h.prob.equation == SHE_SPECIES;
+    const int N = a.N;
+    if (N <= 128) return launch_c<Real, 4>(a, dir, sp, h.stream);
+    if (N <= 256) return launch_c<Real, 8>(a, dir, sp, h.stream);
+    if (N <= 512) return launch_c<Real, 16>(a, dir, sp, h.stream);
+    return launch_c<Real, 32>(a, dir, sp, h.stream);
+}
+
+cudaError_t launch_step1d(Handle& h, uint32_t step0, int nsteps)
+{
+    h.launches += 1;
+    if (h.precision == SHE_FP64) return launch_fused<double>(h, step0, nsteps);
+    return launch_fused<float>(h, step0, nsteps);
+}
+
+// ---------------------------------------------------------------- plain ----
+// FP64, one thread per face (all faces of all realizations), then one thread
+// per cell; the face fluxes go through device memory.
+
+__global__ void k_plain_faces(const double* __restrict__ T, double* __restrict__ G, int N, int R,
+                              double amp2, double wlo, double whi, int dir, int species,
+                              uint32_t key0, uint32_t key1, uint32_t n, int stochastic, uint32_t stream0)
+{
+    const int nf = N + 1;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)R * nf) return;
+    const int rho = (int)(idx / nf);
+    const int f = (int)(idx % nf);
+    const double* row = T + (size_t)rho * N;
+    const double s_heat = sqrt(amp2);
+    double z = 0.0;
+    double tf, w = 1.0;
+    if (f < N) {
+        if (stochastic) {
+            double zz[4];
+            box_muller4(philox4x32_10(make_uint4((uint32_t)(f >> 2), n, stream0 + (uint32_t)rho, 0u), key0, key1), zz);
+            z = zz[f & 3];
+        }
+        if (f == 0) {
+            if (dir) { tf = wlo; w = 1.41421356237309504880; }
+            else tf = 0.5 * (row[N - 1] + row[0]);
+        } else {
+            tf = 0.5 * (row[f - 1] + row[f]);
+        }
+    } else {
+        if (!dir) return;   // periodic: face N is face 0, read there
+        if (stochastic) {
+            double zz[4];
+            box_muller4(philox4x32_10(make_uint4(0u, n >> 2, stream0 + (uint32_t)rho, 2u), key0, key1), zz);
+            z = zz[n & 3u];
+        }
+        tf = whi;
+        w = 1.41421356237309504880;
+    }
+    double amp;
+    if (species) amp = sqrt(amp2 * (tf > 0.0 ? tf : 0.0));
+    else amp = s_heat * tf;
+    G[(size_t)rho * nf + f] = w * amp * z;
+}
+
+__global__ void k_plain_cells(const double* __restrict__ T, double* __restrict__ Tn,
+                              const double* __restrict__ G, int N, int R, double r, double wlo,
+                              double whi, int dir)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)R * N) return;
+    const int rho = (int)(idx / N);
+    const int i = (int)(idx % N);
+    const double* row = T + (size_t)rho * N;
+    const double* g = G + (size_t)rho * (N + 1);
+    double d;
+    if (dir && i == 0) d = r * (row[1] - 3.0 * row[0] + 2.0 * wlo);
+    else if (dir && i == N - 1) d = r * (row[N - 2] - 3.0 * row[N - 1] + 2.0 * whi);
+    else d = r * (row[(i + 1) % N] - 2.0 * row[i] + row[(i - 1 + N) % N]);
+    const double g_hi = (!dir && i == N - 1) ? g[0] : g[i + 1];
+    Tn[(size_t)rho * N + i] = row[i] + d + (g_hi - g[i]);
+}
+
+__global__ void k_plain_sample(const double* __restrict__ T, double* __restrict__ acc1,
+                               double* __restrict__ acc2, int N, int R, double wlo, double whi,
+                               int dir)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)R * N) return;
+    const int i = (int)(idx % N);
+    const double ref = dir ? wlo + (whi - wlo) * ((double)i + 0.5) / (double)N : wlo;
+    const double d = T[idx] - ref;
+    acc1[idx] += d;
+    acc2[idx] += d * d;
+}
+
+cudaError_t launch_step1d_plain(Handle& h, uint32_t step0, int nsteps)
+{
+    const int N = h.prob.n[0];
+    const int R = (int)h.R;
+    const bool dir = h.prob.bc == SHE_DIRICHLET;
+    const double amp2 = h.stochastic ? 2.0 * h.prob.r * h.prob.eps : 0.0;
+    const uint32_t key0 = (uint32_t)(h.prob.seed & 0xffffffffu), key1 = (uint32_t)(h.prob.seed >> 32);
+    const int tpb = 256;
+    const long long nfaces = (long long)R * (N + 1), ncells = (long long)R * N;
+    for (int s = 0; s < nsteps; ++s) {
+        const uint32_t n = step0 + (uint32_t)s;
+        double* T = (double*)h.d_state;
+        double* Tn = (double*)h.d_state2;
+        k_plain_faces<<<(unsigned)((nfaces + tpb - 1) / tpb), tpb, 0, h.stream>>>(
+            T, h.d_face, N, R, amp2, h.prob.wall_lo, h.prob.wall_hi, dir, h.prob.equation == SHE_SPECIES,
+            key0, key1, n, h.stochastic, h.stream0);
+        k_plain_cells<<<(unsigned)((ncells + tpb - 1) / tpb), tpb, 0, h.stream>>>(
+            T, Tn, h.d_face, N, R, h.prob.r, h.prob.wall_lo, h.prob.wall_hi, dir);
+        h.launches += 2;
+        const long long m = (long long)n + 1;
+        if (sample_step(m, h.K, h.relax)) {
+            k_plain_sample<<<(unsigned)((ncells + tpb - 1) / tpb), tpb, 0, h.stream>>>(
+                Tn, h.d_acc1, h.d_acc2, N, R, h.prob.wall_lo, h.prob.wall_hi, dir);
+            h.launches += 1;
+        }
+        void* t = h.d_state;
+        h.d_state = h.d_state2;
+        h.d_state2 = t;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace she
