@@ -101,7 +101,7 @@ class ClockSampler:
 def workload(name):
     import she_workloads as W
     if name == "gradient_rod":
-        p = W.gradient_rod()
+        p = W.gradient_rod(want_cov=0)
         desc = ("1D SHE rod, 256 cells, Dirichlet walls T_L=1 T_R=2, eps=1e-3, r=0.2, 4096 "
                 "realizations, FP32 state, moments every 10 steps after 1e5 steps")
         return p, desc

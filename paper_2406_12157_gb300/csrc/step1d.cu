@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 
 #include "philox.cuh"
 #include "she_internal.cuh"
@@ -42,44 +44,79 @@ template <typename Real>
 __device__ __forceinline__ bool finite_any(Real v) { return isfinite(v); }
 
 // ---------------------------------------------------------------- fused ----
+//
+// Layout: a warp is split into 32/LPR segments of LPR lanes; each segment owns
+// one realization and lane l of a segment holds cells [l*C, l*C + C) in
+// registers.  Shuffles are segmented (width LPR).  Moment partials of the
+// launch live in shared memory, [C][32] per warp and moment (lane-contiguous,
+// conflict-free), so the registers hold only the row and the pipeline state.
 
-template <typename Real, int C, bool DIR, bool SPECIES>
-__global__ void __launch_bounds__(kWarpsPerBlock1D * 32)
+template <typename Real, int C>
+constexpr int step1d_smem_per_warp() { return 2 * C * 32 * (int)sizeof(Real); }
+
+template <typename Real, int C, int LPR, bool DIR, bool SPECIES, bool RAGGED, int MINB>
+__global__ void __launch_bounds__(kWarpsPerBlock1D * 32, MINB)
 k_step1d(const Step1DArgs<Real> a)
 {
     static_assert(C % 4 == 0, "cells per lane must be a multiple of 4");
-    using Acc = Real;
+    static_assert(LPR == 4 || LPR == 8 || LPR == 16 || LPR == 32, "segment width");
     constexpr unsigned FULL = 0xffffffffu;
+    constexpr int RPW = 32 / LPR;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
-    const int rho = blockIdx.x * kWarpsPerBlock1D + (threadIdx.x >> 5);
-    if (rho >= a.R) return;  // warp-uniform
+    const int sl = lane % LPR;
+    const int warp = blockIdx.x * kWarpsPerBlock1D + (threadIdx.x >> 5);
+    if (warp * RPW >= a.R) return;  // warp-uniform
+    const int rho_raw = warp * RPW + lane / LPR;
+    const bool active = rho_raw < a.R;
+    const int rho = active ? rho_raw : a.R - 1;   // idle segments shadow a real row, never store
+
+    Real* sm1 = reinterpret_cast<Real*>(smem_raw) + (threadIdx.x >> 5) * (2 * C * 32) + lane;
+    Real* sm2 = sm1 + C * 32;
 
     const int N = a.N;
-    const int i0 = lane * C;
-    const int jlast = N - 1 - i0;          // cell N-1 sits at j = jlast in lane last_lane
-    const int last_lane = (N - 1) / C;
+    const int i0 = sl * C;
+    const int jlast = N - 1 - i0;
+    const int last_sl = RAGGED ? (N - 1) / C : LPR - 1;
     Real* row = a.state + (size_t)rho * (size_t)N;
 
     Real T[C];
-    Acc s1[C], s2[C];
 #pragma unroll
     for (int j = 0; j < C; ++j) {
         const int i = i0 + j;
-        T[j] = (i < N) ? row[i] : Real(0);
-        s1[j] = Acc(0);
-        s2[j] = Acc(0);
+        T[j] = (!RAGGED || i < N) ? row[i] : Real(0);
+        sm1[j * 32] = Real(0);
+        sm2[j * 32] = Real(0);
     }
     const Real r = a.r;
     const Real amp2 = a.amp2;
-    const Real s_heat = fsqrt_any(amp2);
+    const Real s_half = fsqrt_any(amp2) * Real(0.5);   // heat: s * (a+b)/2
     const Real half = Real(0.5);
     const Real sq2 = Real(1.41421356237309504880);
     const Real wlo = a.wall_lo, whi = a.wall_hi;
     const Real dref = DIR ? (whi - wlo) / Real(N) : Real(0);
     const uint32_t stream = a.stream0 + (uint32_t)rho;
-    // Flux through the high Dirichlet wall: Sec. 3 -- face value T_R, noise x sqrt(2).
-    const Real g_wall_amp = sq2 * face_amp<Real>(whi, amp2, s_heat, SPECIES);
-    const Real g_low_amp = sq2 * face_amp<Real>(wlo, amp2, s_heat, SPECIES);
+    const uint32_t q0 = (uint32_t)(i0 / 4);
+    // Dirichlet wall faces: face value is the wall value, noise x sqrt(2) (Sec. 3).
+    const Real g_wall_amp = sq2 * face_amp<Real>(whi, amp2, Real(2) * s_half, SPECIES);
+    const Real g_low_amp = sq2 * face_amp<Real>(wlo, amp2, Real(2) * s_half, SPECIES);
+    const bool first_sl = (sl == 0);
+    const bool tail_sl = (sl == last_sl);
+
+    // step index (within the launch) of the first sample: the first m >
+    // max(step0, relax) with m % K == 0, as s = m - step0 - 1
+    const long long mlo = (long long)a.step0 + 1 > a.relax + 1 ? (long long)a.step0 + 1 : a.relax + 1;
+    const long long mfirst = ((mlo + a.K - 1) / a.K) * a.K;
+    long long next_s_ll = mfirst - (long long)a.step0 - 1;
+    int next_s = next_s_ll > (long long)a.nsteps ? a.nsteps : (int)next_s_ll;
+
+    auto flux = [&](Real lo, Real hi, Real z) -> Real {
+        if (SPECIES) {
+            const Real c = half * (lo + hi);
+            return fsqrt_any(amp2 * (c > Real(0) ? c : Real(0))) * z;
+        }
+        return (s_half * (lo + hi)) * z;
+    };
 
     Real wz[4] = {Real(0), Real(0), Real(0), Real(0)};
     uint32_t wwin = 0xffffffffu;
@@ -87,73 +124,69 @@ k_step1d(const Step1DArgs<Real> a)
 
     for (int s = 0; s < a.nsteps; ++s) {
         const uint32_t n = a.step0 + (uint32_t)s;
-        const Real left_nb = __shfl_up_sync(FULL, T[C - 1], 1);
-        const Real right_nb = __shfl_down_sync(FULL, T[0], 1);
+        const Real left_nb = __shfl_up_sync(FULL, T[C - 1], 1, LPR);
+        const Real right_nb = __shfl_down_sync(FULL, T[0], 1, LPR);
         Real wrap_lo = Real(0), wrap_hi = Real(0);   // periodic: T_{N-1}, T_0
         if (!DIR) {
-            Real mine = T[0];
+            Real mine = T[C - 1];
+            if (RAGGED) {
 #pragma unroll
-            for (int j = 0; j < C; ++j)
-                if (j == jlast) mine = T[j];
-            wrap_lo = __shfl_sync(FULL, mine, last_lane);
-            wrap_hi = __shfl_sync(FULL, T[0], 0);
-        }
-        // Right-wall noise: slot n%4 of block (0, n/4, stream, 2); lanes 0..7
-        // hold the blocks of a 32-step window.
-        Real g_high = Real(0);
-        if (DIR) {
-            if (a.stochastic) {
-                const uint32_t win = n >> 5;
-                if (win != wwin) {
-                    wwin = win;
-                    const uint4 u = philox4x32_10(make_uint4(0u, win * 8u + (uint32_t)(lane & 7), stream, 2u),
-                                                  a.key0, a.key1);
-                    box_muller4(u, wz);
-                }
-                const uint32_t slot = n & 3u;
-                const Real v = slot == 0 ? wz[0] : slot == 1 ? wz[1] : slot == 2 ? wz[2] : wz[3];
-                g_high = g_wall_amp * __shfl_sync(FULL, v, (int)((n & 31u) >> 2));
+                for (int j = 0; j < C; ++j)
+                    if (j == jlast) mine = T[j];
             }
+            wrap_lo = __shfl_sync(FULL, mine, last_sl, LPR);
+            wrap_hi = __shfl_sync(FULL, T[0], 0, LPR);
+        }
+        // Right-wall noise: slot n%4 of block (0, n/4, stream, 2); segment
+        // lanes 0..7 hold the blocks of a 32-step window (LPR >= 8), or
+        // lanes 0..3 of a 16-step window (LPR == 4).
+        Real g_high = Real(0);
+        if (DIR && a.stochastic) {
+            constexpr int WL = LPR >= 8 ? 8 : 4;          // blocks per window
+            const uint32_t win = n / (uint32_t)(4 * WL);
+            if (win != wwin) {
+                wwin = win;
+                const uint4 u = philox4x32_10(
+                    make_uint4(0u, win * (uint32_t)WL + (uint32_t)(sl % WL), stream, 2u), a.key0, a.key1);
+                box_muller4(u, wz);
+            }
+            const uint32_t slot = n & 3u;
+            const Real v = slot == 0 ? wz[0] : slot == 1 ? wz[1] : slot == 2 ? wz[2] : wz[3];
+            g_high = g_wall_amp * __shfl_sync(FULL, v, (int)((n % (uint32_t)(4 * WL)) >> 2), LPR);
         }
 
         // Pipeline over this lane's faces f = i0 + j (the low face of cell
         // i0 + j): compute G_f, then update cell f-1 in place (it needs G_{f-1}
         // and G_f and the old values of cells f-2, f-1, f).
-        Real g_first = Real(0), g_prev = Real(0);
-        Real g_zero = Real(0);
-        Real old_prev = (i0 == 0) ? (DIR ? Real(2) * wlo - T[0] : wrap_lo) : left_nb;
+        Real g_first = Real(0), g_prev = Real(0), g_zero = Real(0);
+        Real old_prev = left_nb;
+        if (first_sl) old_prev = DIR ? Real(2) * wlo - T[0] : wrap_lo;
         Real old_cur = T[0];
 #pragma unroll
         for (int g = 0; g < C / 4; ++g) {
             Real z[4] = {Real(0), Real(0), Real(0), Real(0)};
             if (a.stochastic) {
-                const uint4 u = philox4x32_10(make_uint4((uint32_t)(i0 / 4 + g), n, stream, 0u), a.key0, a.key1);
+                const uint4 u = philox4x32_10(make_uint4(q0 + (uint32_t)g, n, stream, 0u), a.key0, a.key1);
                 box_muller4(u, z);
             }
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 const int j = 4 * g + t;
-                const int f = i0 + j;
                 Real gf;
                 if (j == 0) {
-                    // face i0: between cell i0-1 (neighbour lane or wall/wrap) and i0
-                    if (f == 0) {
-                        gf = DIR ? g_low_amp * z[0] : face_amp<Real>(half * (wrap_lo + T[0]), amp2, s_heat, SPECIES) * z[0];
-                    } else {
-                        gf = face_amp<Real>(half * (left_nb + T[0]), amp2, s_heat, SPECIES) * z[0];
-                    }
+                    // face i0: between cell i0-1 (neighbour lane, or wall/wrap) and i0
+                    gf = flux(left_nb, T[0], z[0]);
+                    if (first_sl) gf = DIR ? g_low_amp * z[0] : flux(wrap_lo, T[0], z[0]);
                     g_first = gf;
-                    g_zero = __shfl_sync(FULL, g_first, 0);
+                    if (!DIR) g_zero = __shfl_sync(FULL, g_first, 0, LPR);
                 } else {
-                    if (f == N) {
-                        gf = DIR ? g_high : g_zero;          // ragged lane: the high face
-                    } else {
-                        gf = face_amp<Real>(half * (old_cur + T[j]), amp2, s_heat, SPECIES) * z[t];
-                    }
-                    // update cell j-1 (global f-1)
-                    const Real tc = old_cur;
+                    gf = flux(old_cur, T[j], z[t]);
                     Real tr = T[j];
-                    if (f == N) tr = DIR ? Real(2) * whi - tc : wrap_hi;
+                    if (RAGGED && i0 + j == N) {            // ragged lane: the high face
+                        gf = DIR ? g_high : g_zero;
+                        tr = DIR ? Real(2) * whi - old_cur : wrap_hi;
+                    }
+                    const Real tc = old_cur;
                     T[j - 1] = tc + r * (tr - Real(2) * tc + old_prev) + (gf - g_prev);
                     old_prev = tc;
                     old_cur = T[j];
@@ -164,67 +197,128 @@ k_step1d(const Step1DArgs<Real> a)
         // last cell of the lane (j = C-1): its high face is the neighbour
         // lane's first face, or the wall/wrap face when it is cell N-1.
         {
-            const Real g_next = __shfl_down_sync(FULL, g_first, 1);
+            const Real g_next = __shfl_down_sync(FULL, g_first, 1, LPR);
             const Real tc = old_cur;
             Real tr = right_nb;
             Real gr = g_next;
-            if (i0 + C - 1 == N - 1) {
+            if ((!RAGGED && tail_sl) || (RAGGED && i0 + C - 1 == N - 1)) {
                 tr = DIR ? Real(2) * whi - tc : wrap_hi;
                 gr = DIR ? g_high : g_zero;
             }
             T[C - 1] = tc + r * (tr - Real(2) * tc + old_prev) + (gr - g_prev);
         }
 
-        const long long m = (long long)n + 1;
-        if ((m % a.K) == 0 && m > a.relax) {
+        if (s == next_s) {                 // sample after step m = n + 1 (Eq. (3.9))
+            next_s += a.K;
             ++nsamp;
 #pragma unroll
             for (int j = 0; j < C; ++j) {
                 const Real ref = DIR ? fma(dref, Real(i0 + j) + half, wlo) : wlo;
-                const Acc d = (Acc)(T[j] - ref);
-                s1[j] += d;
-                s2[j] = fma(d, d, s2[j]);
+                const Real d = T[j] - ref;
+                sm1[j * 32] += d;
+                sm2[j * 32] = fma(d, d, sm2[j * 32]);
             }
         }
     }
 
     bool bad = false;
-#pragma unroll
-    for (int j = 0; j < C; ++j) {
-        const int i = i0 + j;
-        if (i < N) {
-            row[i] = T[j];
-            bad |= !finite_any(T[j]);
-        }
-    }
-    if (nsamp > 0) {
-        double* p1 = a.acc1 + (size_t)rho * (size_t)N;
-        double* p2 = a.acc2 + (size_t)rho * (size_t)N;
+    if (active) {
 #pragma unroll
         for (int j = 0; j < C; ++j) {
             const int i = i0 + j;
-            if (i < N) {
-                p1[i] += (double)s1[j];
-                p2[i] += (double)s2[j];
+            if (!RAGGED || i < N) {
+                row[i] = T[j];
+                bad |= !finite_any(T[j]);
+            }
+        }
+        if (nsamp > 0) {
+            double* p1 = a.acc1 + (size_t)rho * (size_t)N;
+            double* p2 = a.acc2 + (size_t)rho * (size_t)N;
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                const int i = i0 + j;
+                if (!RAGGED || i < N) {
+                    p1[i] += (double)sm1[j * 32];
+                    p2[i] += (double)sm2[j * 32];
+                }
             }
         }
     }
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.flags, 1);
 }
 
-template <typename Real, int C>
-static cudaError_t launch_c(const Step1DArgs<Real>& a, bool dir, bool species, cudaStream_t st)
+template <typename Real, int C, int LPR, bool DIR, bool SP, int MINB>
+static cudaError_t launch_layout(const Step1DArgs<Real>& a, cudaStream_t st)
 {
+    constexpr int RPW = 32 / LPR;
+    const int warps = (a.R + RPW - 1) / RPW;
     const dim3 block(kWarpsPerBlock1D * 32);
-    const dim3 grid((a.R + kWarpsPerBlock1D - 1) / kWarpsPerBlock1D);
-    if (dir) {
-        if (species) k_step1d<Real, C, true, true><<<grid, block, 0, st>>>(a);
-        else k_step1d<Real, C, true, false><<<grid, block, 0, st>>>(a);
+    const dim3 grid((warps + kWarpsPerBlock1D - 1) / kWarpsPerBlock1D);
+    const int smem = kWarpsPerBlock1D * step1d_smem_per_warp<Real, C>();
+    if (a.N == LPR * C) {
+        auto k = k_step1d<Real, C, LPR, DIR, SP, false, MINB>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k<<<grid, block, smem, st>>>(a);
     } else {
-        if (species) k_step1d<Real, C, false, true><<<grid, block, 0, st>>>(a);
-        else k_step1d<Real, C, false, false><<<grid, block, 0, st>>>(a);
+        auto k = k_step1d<Real, C, LPR, DIR, SP, true, MINB>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k<<<grid, block, smem, st>>>(a);
     }
     return cudaGetLastError();
+}
+
+// Register budget per layout (min resident blocks of 128 threads): enough
+// warps per SM to hold the whole 4096-realization ensemble in one wave for
+// the 256-cell rows, without starving the compiler of registers for ILP.
+template <typename Real, int C, int LPR, bool DIR, bool SP, int MINB32>
+static cudaError_t launch_layout_r(const Step1DArgs<Real>& a, cudaStream_t st)
+{
+    constexpr int MINB = sizeof(Real) == 4 ? MINB32 : (MINB32 / 2 > 0 ? MINB32 / 2 : 1);
+    return launch_layout<Real, C, LPR, DIR, SP, MINB>(a, st);
+}
+
+template <typename Real, bool DIR, bool SP>
+static cudaError_t launch_ds(const Step1DArgs<Real>& a, int layout, cudaStream_t st)
+{
+    // layout = cells per lane * 100 + lanes per realization (see pick_layout)
+    switch (layout) {
+    case 404: return launch_layout_r<Real, 4, 4, DIR, SP, 8>(a, st);
+    case 408: return launch_layout_r<Real, 4, 8, DIR, SP, 8>(a, st);
+    case 416: return launch_layout_r<Real, 4, 16, DIR, SP, 8>(a, st);
+    case 432: return launch_layout_r<Real, 4, 32, DIR, SP, 8>(a, st);
+    case 832: return launch_layout_r<Real, 8, 32, DIR, SP, 7>(a, st);
+    case 1616: return launch_layout_r<Real, 16, 16, DIR, SP, 4>(a, st);
+    case 1632: return launch_layout_r<Real, 16, 32, DIR, SP, 4>(a, st);
+    case 3208: return launch_layout_r<Real, 32, 8, DIR, SP, 2>(a, st);
+    case 3232: return launch_layout_r<Real, 32, 32, DIR, SP, 1>(a, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// Layout for a row of N cells: cells per lane C and lanes per realization
+// LPR with LPR*C >= N.  Rows of up to 128 cells use 4 cells per lane in the
+// narrowest segment that holds them (several realizations per warp); longer
+// rows use 8 lanes of 32 cells (measured fastest at 256 cells: eight
+// independent Philox blocks per lane per step), then 32 lanes.  An override
+// "C,LPR" (environment variable SHE_TUNE_1D) is honoured when it fits.
+static int pick_layout(int N)
+{
+    if (const char* e = getenv("SHE_TUNE_1D")) {
+        int c = 0, l = 0;
+        if (sscanf(e, "%d,%d", &c, &l) == 2 && c * l >= N && (c == 4 || c == 8 || c == 16 || c == 32)) {
+            const int code = c * 100 + l;
+            if (code == 404 || code == 408 || code == 416 || code == 432 || code == 832 || code == 1616 ||
+                code == 1632 || code == 3208 || code == 3232)
+                return code;
+        }
+    }
+    if (N <= 16) return 404;
+    if (N <= 32) return 408;
+    if (N <= 64) return 416;
+    if (N <= 128) return 432;
+    if (N <= 256) return 3208;
+    if (N <= 512) return 1632;
+    return 3232;
 }
 
 template <typename Real>
@@ -251,11 +345,13 @@ static cudaError_t launch_fused(Handle& h, uint32_t step0, int nsteps)
     a.stochastic = h.stochastic;
     const bool dir = h.prob.bc == SHE_DIRICHLET;
     const bool sp = h.prob.equation == SHE_SPECIES;
-    const int N = a.N;
-    if (N <= 128) return launch_c<Real, 4>(a, dir, sp, h.stream);
-    if (N <= 256) return launch_c<Real, 8>(a, dir, sp, h.stream);
-    if (N <= 512) return launch_c<Real, 16>(a, dir, sp, h.stream);
-    return launch_c<Real, 32>(a, dir, sp, h.stream);
+    const int layout = pick_layout(a.N);
+    if (dir) {
+        if (sp) return launch_ds<Real, true, true>(a, layout, h.stream);
+        return launch_ds<Real, true, false>(a, layout, h.stream);
+    }
+    if (sp) return launch_ds<Real, false, true>(a, layout, h.stream);
+    return launch_ds<Real, false, false>(a, layout, h.stream);
 }
 
 cudaError_t launch_step1d(Handle& h, uint32_t step0, int nsteps)

@@ -72,8 +72,9 @@ CASES = [
 
 
 def _prob(N, bc, eq, walls, **kw):
+    kw.setdefault("realizations", 5)
     p = W.oracle_rod(n=(N, 1, 1), bc=bc, equation=eq, wall_lo=walls[0], wall_hi=walls[1],
-                     n0=200.0, kB=5e-3, realizations=5, want_cov=0, want_sk=0, **kw)
+                     n0=200.0, kB=5e-3, want_cov=0, want_sk=0, **kw)
     return p
 
 
@@ -220,3 +221,23 @@ def test_nonfinite_state_is_reported():
         with pytest.raises(S.SheError) as e:
             sim.stats()
         assert e.value.status == S._abi.SHE_ERR_NONFINITE
+
+
+@pytest.mark.parametrize("layout,N", [("4,4", 13), ("4,8", 29), ("4,16", 64), ("4,32", 100),
+                                      ("8,32", 256), ("8,32", 250), ("16,16", 256), ("16,16", 201),
+                                      ("16,32", 512), ("32,8", 256), ("32,8", 255), ("32,32", 1024)])
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+def test_every_layout_fp64_parity(layout, N, bc, monkeypatch):
+    # each (cells per lane, lanes per realization) layout of the fused kernel,
+    # full and ragged rows, against the oracle; R = 7 leaves idle segments
+    monkeypatch.setenv("SHE_TUNE_1D", layout)
+    walls = (1.0, 2.0) if bc == "dirichlet" else (1.0, 1.0)
+    p = _prob(N, bc, "heat", walls, precision="fp64", realizations=7, stats_interval=3,
+              relax_steps=5)
+    with S.Simulation(p) as sim:
+        sim.step(120)
+        st, _ = sim.state()
+        g = sim.stats(raw=True)
+    ref = O.run(p, 7, 120)
+    assert rel_err(st, ref["state"]) < 1e-12
+    assert np.allclose(g["sum_d2"], ref["sum_d2"], rtol=1e-9, atol=1e-15)
