@@ -101,9 +101,10 @@ class ClockSampler:
 def workload(name):
     import she_workloads as W
     if name == "gradient_rod":
-        p = W.gradient_rod(want_cov=0)
+        p = W.gradient_rod()
         desc = ("1D SHE rod, 256 cells, Dirichlet walls T_L=1 T_R=2, eps=1e-3, r=0.2, 4096 "
-                "realizations, FP32 state, moments every 10 steps after 1e5 steps")
+                "realizations, FP32 state, moments and full 256x256 equal-time covariance "
+                "(tcgen05) every 10 steps after 1e5 steps")
         return p, desc
     if name == "oracle_rod":
         p = W.oracle_rod(want_cov=0, want_sk=0)
@@ -159,6 +160,8 @@ def run_ours(args):
         dist.init_process_group("nccl")
     she.lib()
     p, desc = workload(args.workload)
+    if args.relax is not None:          # profile the sampling phase from the start
+        p["relax_steps"] = args.relax
     R = p["realizations"]
     cells = _cells(p)
     stream = torch.cuda.Stream()
@@ -203,7 +206,7 @@ def run_ours(args):
     total_cu = cu_per_step * args.steps * world
     value = total_cu / (ms / 1e3)
     try:
-        stats = sim.stats()      # the statistics of the run (device reduce + D2H)
+        stats = sim.stats(cov=bool(p.get("want_cov")))   # device reduce + D2H
         assert np.all(np.isfinite(stats["var"]))
     except she.SheError as e:
         if e.status != she._abi.SHE_ERR_STATE:   # no sample yet in a short run is fine
@@ -211,7 +214,8 @@ def run_ours(args):
 
     # ---- FP64 plain form on the same workload, a bounded number of steps ----
     plain_steps = max(10, min(2000, int(2e8 // (R * cells))))
-    sim64 = she.Simulation(p, stream=stream, precision="fp64", kernel="plain", stream_offset=rank * R)
+    sim64 = she.Simulation(p, stream=stream, precision="fp64", kernel="plain", stream_offset=rank * R,
+                           want_cov=0, want_sk=0)
     sim64.step(min(plain_steps, 50))
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -238,9 +242,9 @@ def run_ours(args):
             sim.set_state(host_np, step)            # H2D of the step's input state
             sim.step(chunk)
             try:
-                out = sim.stats()                   # device reduce + D2H of the statistics
+                out = sim.stats(cov=bool(p.get("want_cov")))   # device reduce + D2H
                 d2h = sum(v.nbytes for v in out.values() if hasattr(v, "nbytes"))
-                d2h += 2 * min(32, R) * cells * 8
+                d2h += 2 * min(32, R) * cells * 8 + (cells * cells * 8 if p.get("want_cov") else 0)
             except she.SheError as e:
                 if e.status != she._abi.SHE_ERR_STATE:
                     raise
@@ -266,7 +270,7 @@ def run_ours(args):
     peak = 128 * 152 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
             "unit": "Tops/s", "frac": round(achieved / peak, 4), "traffic": None,
-            "kernel": "k_step1d<float,8,dirichlet,heat>",
+            "kernel": "k_step1d_cov<32,8,dirichlet,heat>" if p.get("want_cov") else "k_step1d<float,32,8,dirichlet,heat>",
             "ops_per_cell_update": OPS_PER_CELL_UPDATE_1D,
             "peak_source": "128 lane-ops/clk/SM x 152 SMs x max SM clock (%s)" % peak_src}
     cpu = None
@@ -340,6 +344,8 @@ def main():
     ap.add_argument("--chunk", type=int, default=10_000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--relax", type=int, default=None,
+                    help="override the workload's relaxation steps (profiling the sampling phase)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -241,6 +241,16 @@ void she_free(she_handle* h);
 she_status she_noise_probe(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                            int64_t count, uint32_t* bits, double* z64, float* z32);
 
+/*
+ * Test hook of the tensor-core covariance path: C = X^T X for a host matrix
+ * X [K][N] (row-major FP32, K <= 32 samples, 1 <= N <= 256 cells) computed by
+ * the library's tcgen05 kernel (bf16 hi/lo split, three MMAs, FP32
+ * accumulation in tensor memory); C is a host [N][N] FP64 array.  Errors:
+ * SHE_ERR_INVALID_ARG (sizes), SHE_ERR_TIMEOUT (the MMA completion wait gave
+ * up), SHE_ERR_CUDA.
+ */
+she_status she_syrk_probe(const float* X, int32_t K, int32_t N, double* C);
+
 /* Number of kernel launches enqueued by this handle since init (for the
  * benchmark's launch accounting). */
 int64_t she_launch_count(const she_handle* h);

@@ -21,7 +21,7 @@ from ._abi import (LibraryMissing, SHE_DIRICHLET, SHE_FE, SHE_FP32, SHE_FP64, SH
 __all__ = ["SheError", "LibraryMissing", "params_from_problem", "she_init", "she_init_batch",
            "she_step_n", "she_get_sizes", "she_stats", "she_reset_stats", "she_get_state",
            "she_set_state", "she_get_state_device", "she_set_state_device", "she_last_error",
-           "she_free", "she_noise_probe", "she_launch_count", "Simulation", "lib"]
+           "she_free", "she_noise_probe", "she_launch_count", "she_syrk_probe", "Simulation", "lib"]
 
 
 class SheError(RuntimeError):
@@ -203,6 +203,16 @@ def she_noise_probe(seed, c0, c1, c2, c3, count):
     _check(lib().she_noise_probe(seed, c0, c1, c2, c3, count, bits.ctypes.data, z64.ctypes.data,
                                  z32.ctypes.data), None, "she_noise_probe")
     return bits.reshape(count, 4), z64.reshape(count, 4), z32.reshape(count, 4)
+
+
+def she_syrk_probe(X):
+    """C = X^T X (FP64 result) for X [K <= 32, N <= 256] via the library's
+    tcgen05 covariance kernel (bf16 hi/lo split, FP32 accumulation)."""
+    Xf = np.ascontiguousarray(X, dtype=np.float32)
+    K, N = Xf.shape
+    C = np.empty((N, N), dtype=np.float64)
+    _check(lib().she_syrk_probe(Xf.ctypes.data, K, N, C.ctypes.data), None, "she_syrk_probe")
+    return C
 
 
 class Simulation:

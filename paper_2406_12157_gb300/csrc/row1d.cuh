@@ -1,0 +1,183 @@
+// row1d.cuh -- one forward-Euler step of a 1D row held in registers by a
+// segment of LPR lanes (C cells per lane), shared by the 1D step kernels.
+//
+// Method (Sec. 3): T_i' = T_i + r (T_{i+1} - 2 T_i + T_{i-1}) + G_{i+1} - G_i,
+// Eq. (3.3), with the face flux G_f = amp(T_face) N_f, T_face the mean of the
+// two neighbours, amp = sqrt(2 r eps) T_face for heat (Eq. (2.12)) and
+// sqrt(2 r eps max(c_face, 0)) for species (Eq. (4.7)); Dirichlet walls use
+// the stencil of Eq. (3.8) (a ghost cell 2 T_wall - T_edge) and a wall face
+// with value T_wall and noise x sqrt(2); periodic rows wrap.  The normals come
+// from the counter layout in she.h.
+#pragma once
+#include <cstdint>
+
+#include "philox.cuh"
+#include "she_internal.cuh"
+
+namespace she {
+
+__device__ __forceinline__ float fsqrt_any(float x) { return sqrtf(x); }
+__device__ __forceinline__ double fsqrt_any(double x) { return sqrt(x); }
+
+template <typename Real>
+__device__ __forceinline__ bool finite_any(Real v) { return isfinite(v); }
+
+template <typename Real>
+__device__ __forceinline__ Real face_amp(Real face_value, Real amp2, Real s_heat, bool species)
+{
+    if (species) {
+        const Real c = face_value > Real(0) ? face_value : Real(0);
+        return fsqrt_any(amp2 * c);
+    }
+    return s_heat * face_value;
+}
+
+template <typename Real, int C, int LPR, bool DIR, bool SPECIES, bool RAGGED>
+struct Row1D {
+    static_assert(C % 4 == 0, "cells per lane must be a multiple of 4");
+    static_assert(LPR == 4 || LPR == 8 || LPR == 16 || LPR == 32, "segment width");
+    static constexpr unsigned FULL = 0xffffffffu;
+
+    int N, i0, jlast, last_sl;
+    bool first_sl, tail_sl;
+    Real r, amp2, s_half, wlo, whi, g_wall_amp, g_low_amp;
+    uint32_t stream, q0, key0, key1;
+    int stochastic;
+    Real wz[4];
+    uint32_t wwin;
+
+    __device__ __forceinline__ void init(const Step1DArgs<Real>& a, int sl, int rho)
+    {
+        N = a.N;
+        i0 = sl * C;
+        jlast = N - 1 - i0;
+        last_sl = RAGGED ? (N - 1) / C : LPR - 1;
+        first_sl = (sl == 0);
+        tail_sl = (sl == last_sl);
+        r = a.r;
+        amp2 = a.amp2;
+        s_half = fsqrt_any(amp2) * Real(0.5);
+        wlo = a.wall_lo;
+        whi = a.wall_hi;
+        const Real sq2 = Real(1.41421356237309504880);
+        g_wall_amp = sq2 * face_amp<Real>(whi, amp2, Real(2) * s_half, SPECIES);
+        g_low_amp = sq2 * face_amp<Real>(wlo, amp2, Real(2) * s_half, SPECIES);
+        stream = a.stream0 + (uint32_t)rho;
+        q0 = (uint32_t)(i0 / 4);
+        key0 = a.key0;
+        key1 = a.key1;
+        stochastic = a.stochastic;
+        wz[0] = wz[1] = wz[2] = wz[3] = Real(0);
+        wwin = 0xffffffffu;
+    }
+
+    __device__ __forceinline__ Real flux(Real lo, Real hi, Real z) const
+    {
+        if (SPECIES) {
+            const Real c = Real(0.5) * (lo + hi);
+            return fsqrt_any(amp2 * (c > Real(0) ? c : Real(0))) * z;
+        }
+        return (s_half * (lo + hi)) * z;
+    }
+
+    // advance the row T by the step with absolute index n
+    __device__ __forceinline__ void step(Real (&T)[C], uint32_t n)
+    {
+        const Real left_nb = __shfl_up_sync(FULL, T[C - 1], 1, LPR);
+        const Real right_nb = __shfl_down_sync(FULL, T[0], 1, LPR);
+        Real wrap_lo = Real(0), wrap_hi = Real(0);   // periodic: T_{N-1}, T_0
+        if (!DIR) {
+            Real mine = T[C - 1];
+            if (RAGGED) {
+#pragma unroll
+                for (int j = 0; j < C; ++j)
+                    if (j == jlast) mine = T[j];
+            }
+            wrap_lo = __shfl_sync(FULL, mine, last_sl, LPR);
+            wrap_hi = __shfl_sync(FULL, T[0], 0, LPR);
+        }
+        // Right-wall noise: slot n%4 of block (0, n/4, stream, 2); segment
+        // lanes 0..WL-1 hold the blocks of a 4*WL-step window.
+        Real g_high = Real(0);
+        if (DIR && stochastic) {
+            constexpr int WL = LPR >= 8 ? 8 : 4;
+            const int sl = i0 / C;
+            const uint32_t win = n / (uint32_t)(4 * WL);
+            if (win != wwin) {
+                wwin = win;
+                const uint4 u = philox4x32_10(
+                    make_uint4(0u, win * (uint32_t)WL + (uint32_t)(sl % WL), stream, 2u), key0, key1);
+                box_muller4(u, wz);
+            }
+            const uint32_t slot = n & 3u;
+            const Real v = slot == 0 ? wz[0] : slot == 1 ? wz[1] : slot == 2 ? wz[2] : wz[3];
+            g_high = g_wall_amp * __shfl_sync(FULL, v, (int)((n % (uint32_t)(4 * WL)) >> 2), LPR);
+        }
+
+        // Pipeline over this lane's faces f = i0 + j (the low face of cell
+        // i0 + j): compute G_f, then update cell f-1 in place (it needs G_{f-1}
+        // and G_f and the old values of cells f-2, f-1, f).
+        Real g_first = Real(0), g_prev = Real(0), g_zero = Real(0);
+        Real old_prev = left_nb;
+        if (first_sl) old_prev = DIR ? Real(2) * wlo - T[0] : wrap_lo;
+        Real old_cur = T[0];
+#pragma unroll
+        for (int g = 0; g < C / 4; ++g) {
+            Real z[4] = {Real(0), Real(0), Real(0), Real(0)};
+            if (stochastic) {
+                const uint4 u = philox4x32_10(make_uint4(q0 + (uint32_t)g, n, stream, 0u), key0, key1);
+                box_muller4(u, z);
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int j = 4 * g + t;
+                Real gf;
+                if (j == 0) {
+                    // face i0: between cell i0-1 (neighbour lane, or wall/wrap) and i0
+                    gf = flux(left_nb, T[0], z[0]);
+                    if (first_sl) gf = DIR ? g_low_amp * z[0] : flux(wrap_lo, T[0], z[0]);
+                    g_first = gf;
+                    if (!DIR) g_zero = __shfl_sync(FULL, g_first, 0, LPR);
+                } else {
+                    gf = flux(old_cur, T[j], z[t]);
+                    Real tr = T[j];
+                    if (RAGGED && i0 + j == N) {            // ragged lane: the high face
+                        gf = DIR ? g_high : g_zero;
+                        tr = DIR ? Real(2) * whi - old_cur : wrap_hi;
+                    }
+                    const Real tc = old_cur;
+                    T[j - 1] = tc + r * (tr - Real(2) * tc + old_prev) + (gf - g_prev);
+                    old_prev = tc;
+                    old_cur = T[j];
+                }
+                g_prev = gf;
+            }
+        }
+        // last cell of the lane (j = C-1): its high face is the neighbour
+        // lane's first face, or the wall/wrap face when it is cell N-1.
+        {
+            const Real g_next = __shfl_down_sync(FULL, g_first, 1, LPR);
+            const Real tc = old_cur;
+            Real tr = right_nb;
+            Real gr = g_next;
+            if ((!RAGGED && tail_sl) || (RAGGED && i0 + C - 1 == N - 1)) {
+                tr = DIR ? Real(2) * whi - tc : wrap_hi;
+                gr = DIR ? g_high : g_zero;
+            }
+            T[C - 1] = tc + r * (tr - Real(2) * tc + old_prev) + (gr - g_prev);
+        }
+    }
+};
+
+// Step index (within a launch starting at absolute step step0) of the first
+// sample: the first m > max(step0, relax) with m % K == 0, as s = m - step0 - 1;
+// nsteps if there is none in the launch.
+__device__ __forceinline__ int first_sample_index(uint32_t step0, long long relax, int K, int nsteps)
+{
+    const long long mlo = (long long)step0 + 1 > relax + 1 ? (long long)step0 + 1 : relax + 1;
+    const long long mfirst = ((mlo + K - 1) / K) * K;
+    const long long s = mfirst - (long long)step0 - 1;
+    return s > (long long)nsteps ? nsteps : (int)s;
+}
+
+}  // namespace she

@@ -115,6 +115,9 @@ void release(Handle* h)
     cudaFree(h->d_face);
     cudaFree(h->d_flags);
     cudaFree(h->d_red);
+    cudaFree(h->d_cov_partial);
+    cudaFree(h->d_cov_red);
+    h->d_cov_partial = h->d_cov_red = nullptr;
     h->d_state = h->d_state2 = nullptr;
     h->d_acc1 = h->d_acc2 = h->d_face = h->d_red = nullptr;
     h->d_flags = nullptr;
@@ -170,8 +173,19 @@ she_status she_init(const she_params* p, she_handle** out)
     }
     if (st == SHE_OK && p->steps_per_launch < 0) { st = SHE_ERR_INVALID_ARG; msg = "she: steps_per_launch < 0"; }
     if (st == SHE_OK && (p->want_sk & ~3)) { st = SHE_ERR_INVALID_ARG; msg = "she: bad want_sk bits"; }
-    if (st == SHE_OK && p->want_cov) { st = SHE_ERR_UNSUPPORTED; msg = "she: covariance not built yet"; }
-    if (st == SHE_OK && p->want_sk) { st = SHE_ERR_UNSUPPORTED; msg = "she: S(k) not built yet"; }
+    // 1D: the structure factor is the DFT of the pooled covariance (exact), so
+    // SHE_SK_FULL implies the covariance accumulation.
+    const bool need_cov = p->want_cov || (p->dim == 1 && (p->want_sk & SHE_SK_FULL));
+    if (st == SHE_OK && need_cov && (p->dim != 1 || p->n[0] > 256)) {
+        st = SHE_ERR_INVALID_ARG; msg = "she: the covariance needs a 1D grid of at most 256 cells";
+    }
+    if (st == SHE_OK && need_cov && (p->precision != SHE_FP32 || p->kernel != SHE_KERNEL_AUTO)) {
+        st = SHE_ERR_UNSUPPORTED; msg = "she: the tensor-core covariance runs on the FP32 fused path";
+    }
+    if (st == SHE_OK && (p->want_sk & SHE_SK_AXES) && p->dim == 1) {
+        st = SHE_ERR_INVALID_ARG; msg = "she: SHE_SK_AXES is for 2D/3D grids (use SHE_SK_FULL in 1D)";
+    }
+    if (st == SHE_OK && p->want_sk && p->dim > 1) { st = SHE_ERR_UNSUPPORTED; msg = "she: S(k) not built yet"; }
     if (st == SHE_OK && p->dim > 1) { st = SHE_ERR_UNSUPPORTED; msg = "she: 2D/3D not built yet"; }
     if (st != SHE_OK) {
         fprintf(stderr, "%s\n", msg.c_str());
@@ -182,7 +196,7 @@ she_status she_init(const she_params* p, she_handle** out)
     h->precision = p->precision;
     h->K = p->stats_interval;
     h->relax = p->relax_steps;
-    h->want_cov = p->want_cov;
+    h->want_cov = need_cov ? 1 : 0;
     h->want_sk = p->want_sk;
     h->kernel = p->kernel;
     h->stochastic = p->stochastic ? 1 : 0;
@@ -205,6 +219,17 @@ she_status she_init(const she_params* p, she_handle** out)
     if (e == cudaSuccess && h->kernel == SHE_KERNEL_PLAIN) {
         e = cudaMalloc(&h->d_state2, nstate * elem);
         if (e == cudaSuccess) e = cudaMalloc(&h->d_face, (size_t)h->R * (cells + 1) * sizeof(double));
+    }
+    if (e == cudaSuccess && h->want_cov) {
+        int dev = 0, sms = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        h->cov_ctas = sms > 0 ? sms : 1;
+        const size_t nn = cells * cells;
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_cov_partial, (size_t)h->cov_ctas * nn * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_cov_red, nn * sizeof(double));
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(h->d_cov_partial, 0, (size_t)h->cov_ctas * nn * sizeof(double), h->stream);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_acc1, 0, nstate * sizeof(double), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_acc2, 0, nstate * sizeof(double), h->stream);
@@ -241,10 +266,12 @@ she_status she_step_n(she_handle* hh, uint64_t n)
     while (left > 0) {
         int chunk = (int)std::min<uint64_t>(left, (uint64_t)spl);
         cudaError_t e;
+        const int64_t ns = samples_in(h->step, (uint64_t)chunk, h->K, h->relax);
         if (h->kernel == SHE_KERNEL_PLAIN) e = she::launch_step1d_plain(*h, (uint32_t)h->step, chunk);
+        else if (h->want_cov) e = she::launch_step1d_cov(*h, (uint32_t)h->step, chunk, ns > 0);
         else e = she::launch_step1d(*h, (uint32_t)h->step, chunk);
         if (e != cudaSuccess) return cuda_fail(h, e, "she_step_n");
-        h->samples_per_real += samples_in(h->step, (uint64_t)chunk, h->K, h->relax);
+        h->samples_per_real += ns;
         h->step += (uint64_t)chunk;
         left -= (uint64_t)chunk;
     }
@@ -280,6 +307,7 @@ she_status she_stats(she_handle* hh, she_stats_out* out)
     if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(flags)");
     out->n_samples = h->samples_per_real * h->R;
     if (flags & 1) return fail(h, SHE_ERR_NONFINITE, "she: the state became non-finite");
+    if (flags & 2) return fail(h, SHE_ERR_TIMEOUT, "she: a bounded tensor-core completion wait gave up");
     if (h->samples_per_real == 0) return fail(h, SHE_ERR_STATE, "she: no sample taken yet");
     const int64_t cells = h->prob.cells;
     const int B = (int)std::min<int64_t>(32, h->R);
@@ -294,19 +322,22 @@ she_status she_stats(she_handle* hh, she_stats_out* out)
     if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(copy)");
     const double n = (double)out->n_samples;
     const bool dir = h->prob.dim == 1 && h->prob.bc == SHE_DIRICHLET;
+    std::vector<double> mu((size_t)cells), ref((size_t)cells);
     for (int64_t i = 0; i < cells; ++i) {
         double s1 = 0.0, s2 = 0.0;
         for (int b = 0; b < B; ++b) {
             s1 += b1[(size_t)b * cells + i];
             s2 += b2[(size_t)b * cells + i];
         }
-        const double ref = dir ? h->prob.wall_lo + (h->prob.wall_hi - h->prob.wall_lo) * ((double)i + 0.5) / (double)cells
-                               : h->prob.wall_lo;
-        const double mu = s1 / n;
+        const double ref_i = dir ? h->prob.wall_lo + (h->prob.wall_hi - h->prob.wall_lo) * ((double)i + 0.5) / (double)cells
+                                 : h->prob.wall_lo;
+        const double mu_i = s1 / n;
+        mu[(size_t)i] = mu_i;
+        ref[(size_t)i] = ref_i;
         if (out->sum_d) out->sum_d[i] = s1;
         if (out->sum_d2) out->sum_d2[i] = s2;
-        if (out->mean) out->mean[i] = ref + mu;
-        if (out->var) out->var[i] = s2 / n - mu * mu;
+        if (out->mean) out->mean[i] = ref_i + mu_i;
+        if (out->var) out->var[i] = s2 / n - mu_i * mu_i;
         if (out->var_se) {
             // batch b holds realizations [R b / B, R (b+1) / B)
             double sv = 0.0, svv = 0.0;
@@ -323,6 +354,49 @@ she_status she_stats(she_handle* hh, she_stats_out* out)
                                       : std::numeric_limits<double>::quiet_NaN();
         }
     }
+    if (h->want_cov && (out->cov || out->sk || out->sk_fluct)) {
+        const int64_t N = cells;
+        e = she::launch_reduce_cov(*h, h->d_cov_red);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        std::vector<double> S((size_t)(N * N));
+        if (e == cudaSuccess) e = cudaMemcpy(S.data(), h->d_cov_red, S.size() * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(cov)");
+        // second moment of delta, symmetrised: M2 = (S + S^T) / (2 n)
+        std::vector<double> M2((size_t)(N * N));
+        for (int64_t i = 0; i < N; ++i)
+            for (int64_t j = 0; j < N; ++j)
+                M2[(size_t)(i * N + j)] = 0.5 * (S[(size_t)(i * N + j)] + S[(size_t)(j * N + i)]) / n;
+        if (out->cov)
+            for (int64_t i = 0; i < N; ++i)
+                for (int64_t j = 0; j < N; ++j)
+                    out->cov[i * N + j] = M2[(size_t)(i * N + j)] - mu[(size_t)i] * mu[(size_t)j];
+        if (out->sk || out->sk_fluct) {
+            // S_k = <|hat T_k|^2> (Eq. (3.11)) from the pooled moments:
+            // <|hat delta_k|^2> = sum_{j,l} M2_jl cos(2 pi (j - l) k / N)
+            const double two_pi = 6.283185307179586476925286766559;
+            std::vector<double> cs((size_t)N), sn((size_t)N);
+            for (int64_t t = 0; t < N; ++t) {
+                cs[(size_t)t] = std::cos(two_pi * (double)t / (double)N);
+                sn[(size_t)t] = std::sin(two_pi * (double)t / (double)N);
+            }
+            for (int64_t k = 0; k < N; ++k) {
+                double dd = 0.0, mr = 0.0, mi = 0.0, rr = 0.0, ri = 0.0;
+                for (int64_t j = 0; j < N; ++j) {
+                    const size_t ph = (size_t)((j * k) % N);
+                    mr += mu[(size_t)j] * cs[ph];
+                    mi -= mu[(size_t)j] * sn[ph];
+                    rr += ref[(size_t)j] * cs[ph];
+                    ri -= ref[(size_t)j] * sn[ph];
+                    for (int64_t l = 0; l < N; ++l) {
+                        const size_t d = (size_t)((((j - l) * k) % N + N) % N);
+                        dd += M2[(size_t)(j * N + l)] * cs[d];
+                    }
+                }
+                if (out->sk_fluct) out->sk_fluct[k] = dd - (mr * mr + mi * mi);
+                if (out->sk) out->sk[k] = rr * rr + ri * ri + 2.0 * (rr * mr + ri * mi) + dd;
+            }
+        }
+    }
     return SHE_OK;
 }
 
@@ -333,6 +407,10 @@ she_status she_reset_stats(she_handle* hh)
     const size_t nstate = (size_t)h->R * (size_t)h->prob.cells;
     cudaError_t e = cudaMemsetAsync(h->d_acc1, 0, nstate * sizeof(double), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_acc2, 0, nstate * sizeof(double), h->stream);
+    if (e == cudaSuccess && h->d_cov_partial)
+        e = cudaMemsetAsync(h->d_cov_partial, 0,
+                            (size_t)h->cov_ctas * (size_t)h->prob.cells * (size_t)h->prob.cells * sizeof(double),
+                            h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "she_reset_stats");
     h->samples_per_real = 0;
     return SHE_OK;
@@ -429,6 +507,30 @@ she_status she_noise_probe(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
     cudaFree(dz);
     cudaFree(df);
     return e == cudaSuccess ? SHE_OK : SHE_ERR_CUDA;
+}
+
+she_status she_syrk_probe(const float* X, int32_t K, int32_t N, double* C)
+{
+    if (!X || !C || K < 1 || K > 32 || N < 1 || N > 256) return SHE_ERR_INVALID_ARG;
+    float* dX = nullptr;
+    double* dC = nullptr;
+    int* dErr = nullptr;
+    cudaError_t e = cudaMalloc(&dX, (size_t)K * N * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&dC, (size_t)N * N * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&dErr, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(dX, X, (size_t)K * N * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(dC, 0, (size_t)N * N * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(dErr, 0, sizeof(int));
+    if (e == cudaSuccess) e = she::launch_syrk_probe(dX, K, N, dC, dErr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&herr, dErr, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(C, dC, (size_t)N * N * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(dX);
+    cudaFree(dC);
+    cudaFree(dErr);
+    if (e != cudaSuccess) return SHE_ERR_CUDA;
+    return herr ? SHE_ERR_TIMEOUT : SHE_OK;
 }
 
 int64_t she_launch_count(const she_handle* hh)

@@ -46,6 +46,14 @@ struct Step1DArgs {
     int stochastic;
 };
 
+// Extra arguments of the fused covariance kernel.
+struct CovArgs {
+    double* partial;      // [G][N][N] per-CTA FP64 partial sums of delta delta^T
+    int r_begin;          // first realization of this wave
+    int r_count;          // realizations in this wave (<= 32 per CTA)
+    int has_samples;      // the launch takes at least one sample
+};
+
 struct Handle {
     Problem prob;
     int64_t R = 0;
@@ -69,6 +77,9 @@ struct Handle {
     double* d_face = nullptr;      // plain form: face fluxes [R][N+1]
     int* d_flags = nullptr;
     double* d_red = nullptr;       // reduction scratch
+    double* d_cov_partial = nullptr;  // [cov_ctas][N][N] FP64 partial covariance sums
+    double* d_cov_red = nullptr;   // [N][N] reduced
+    int cov_ctas = 0;              // CTAs (one per SM) of the fused covariance kernel
     size_t red_bytes = 0;
     std::string err;
 };
@@ -77,7 +88,10 @@ struct Handle {
 cudaError_t launch_init_state(Handle& h);
 cudaError_t launch_step1d(Handle& h, uint32_t step0, int nsteps);
 cudaError_t launch_step1d_plain(Handle& h, uint32_t step0, int nsteps);
+cudaError_t launch_step1d_cov(Handle& h, uint32_t step0, int nsteps, bool has_samples);
+cudaError_t launch_reduce_cov(const Handle& h, double* d_out);
 cudaError_t launch_reduce_batches(const Handle& h, int batches, double* d_out1, double* d_out2);
+cudaError_t launch_syrk_probe(const float* d_X, int K, int N, double* d_C, int* d_err);
 cudaError_t launch_noise_probe(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                int64_t count, uint32_t* d_bits, double* d_z64, float* d_z32);
 

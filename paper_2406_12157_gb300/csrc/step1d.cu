@@ -23,25 +23,10 @@
 #include <cstdlib>
 
 #include "philox.cuh"
+#include "row1d.cuh"
 #include "she_internal.cuh"
 
 namespace she {
-
-template <typename Real>
-__device__ __forceinline__ Real face_amp(Real face_value, Real amp2, Real s_heat, bool species)
-{
-    if (species) {
-        const Real c = face_value > Real(0) ? face_value : Real(0);
-        return sqrt(amp2 * c);
-    }
-    return s_heat * face_value;
-}
-
-__device__ __forceinline__ float fsqrt_any(float x) { return sqrtf(x); }
-__device__ __forceinline__ double fsqrt_any(double x) { return sqrt(x); }
-
-template <typename Real>
-__device__ __forceinline__ bool finite_any(Real v) { return isfinite(v); }
 
 // ---------------------------------------------------------------- fused ----
 //
@@ -58,8 +43,6 @@ template <typename Real, int C, int LPR, bool DIR, bool SPECIES, bool RAGGED, in
 __global__ void __launch_bounds__(kWarpsPerBlock1D * 32, MINB)
 k_step1d(const Step1DArgs<Real> a)
 {
-    static_assert(C % 4 == 0, "cells per lane must be a multiple of 4");
-    static_assert(LPR == 4 || LPR == 8 || LPR == 16 || LPR == 32, "segment width");
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int RPW = 32 / LPR;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -74,12 +57,11 @@ k_step1d(const Step1DArgs<Real> a)
     Real* sm1 = reinterpret_cast<Real*>(smem_raw) + (threadIdx.x >> 5) * (2 * C * 32) + lane;
     Real* sm2 = sm1 + C * 32;
 
+    Row1D<Real, C, LPR, DIR, SPECIES, RAGGED> rowst;
+    rowst.init(a, sl, rho);
     const int N = a.N;
     const int i0 = sl * C;
-    const int jlast = N - 1 - i0;
-    const int last_sl = RAGGED ? (N - 1) / C : LPR - 1;
     Real* row = a.state + (size_t)rho * (size_t)N;
-
     Real T[C];
 #pragma unroll
     for (int j = 0; j < C; ++j) {
@@ -88,126 +70,14 @@ k_step1d(const Step1DArgs<Real> a)
         sm1[j * 32] = Real(0);
         sm2[j * 32] = Real(0);
     }
-    const Real r = a.r;
-    const Real amp2 = a.amp2;
-    const Real s_half = fsqrt_any(amp2) * Real(0.5);   // heat: s * (a+b)/2
     const Real half = Real(0.5);
-    const Real sq2 = Real(1.41421356237309504880);
-    const Real wlo = a.wall_lo, whi = a.wall_hi;
-    const Real dref = DIR ? (whi - wlo) / Real(N) : Real(0);
-    const uint32_t stream = a.stream0 + (uint32_t)rho;
-    const uint32_t q0 = (uint32_t)(i0 / 4);
-    // Dirichlet wall faces: face value is the wall value, noise x sqrt(2) (Sec. 3).
-    const Real g_wall_amp = sq2 * face_amp<Real>(whi, amp2, Real(2) * s_half, SPECIES);
-    const Real g_low_amp = sq2 * face_amp<Real>(wlo, amp2, Real(2) * s_half, SPECIES);
-    const bool first_sl = (sl == 0);
-    const bool tail_sl = (sl == last_sl);
-
-    // step index (within the launch) of the first sample: the first m >
-    // max(step0, relax) with m % K == 0, as s = m - step0 - 1
-    const long long mlo = (long long)a.step0 + 1 > a.relax + 1 ? (long long)a.step0 + 1 : a.relax + 1;
-    const long long mfirst = ((mlo + a.K - 1) / a.K) * a.K;
-    long long next_s_ll = mfirst - (long long)a.step0 - 1;
-    int next_s = next_s_ll > (long long)a.nsteps ? a.nsteps : (int)next_s_ll;
-
-    auto flux = [&](Real lo, Real hi, Real z) -> Real {
-        if (SPECIES) {
-            const Real c = half * (lo + hi);
-            return fsqrt_any(amp2 * (c > Real(0) ? c : Real(0))) * z;
-        }
-        return (s_half * (lo + hi)) * z;
-    };
-
-    Real wz[4] = {Real(0), Real(0), Real(0), Real(0)};
-    uint32_t wwin = 0xffffffffu;
+    const Real wlo = a.wall_lo;
+    const Real dref = DIR ? (a.wall_hi - a.wall_lo) / Real(N) : Real(0);
+    int next_s = first_sample_index(a.step0, a.relax, a.K, a.nsteps);
     int nsamp = 0;
 
     for (int s = 0; s < a.nsteps; ++s) {
-        const uint32_t n = a.step0 + (uint32_t)s;
-        const Real left_nb = __shfl_up_sync(FULL, T[C - 1], 1, LPR);
-        const Real right_nb = __shfl_down_sync(FULL, T[0], 1, LPR);
-        Real wrap_lo = Real(0), wrap_hi = Real(0);   // periodic: T_{N-1}, T_0
-        if (!DIR) {
-            Real mine = T[C - 1];
-            if (RAGGED) {
-#pragma unroll
-                for (int j = 0; j < C; ++j)
-                    if (j == jlast) mine = T[j];
-            }
-            wrap_lo = __shfl_sync(FULL, mine, last_sl, LPR);
-            wrap_hi = __shfl_sync(FULL, T[0], 0, LPR);
-        }
-        // Right-wall noise: slot n%4 of block (0, n/4, stream, 2); segment
-        // lanes 0..7 hold the blocks of a 32-step window (LPR >= 8), or
-        // lanes 0..3 of a 16-step window (LPR == 4).
-        Real g_high = Real(0);
-        if (DIR && a.stochastic) {
-            constexpr int WL = LPR >= 8 ? 8 : 4;          // blocks per window
-            const uint32_t win = n / (uint32_t)(4 * WL);
-            if (win != wwin) {
-                wwin = win;
-                const uint4 u = philox4x32_10(
-                    make_uint4(0u, win * (uint32_t)WL + (uint32_t)(sl % WL), stream, 2u), a.key0, a.key1);
-                box_muller4(u, wz);
-            }
-            const uint32_t slot = n & 3u;
-            const Real v = slot == 0 ? wz[0] : slot == 1 ? wz[1] : slot == 2 ? wz[2] : wz[3];
-            g_high = g_wall_amp * __shfl_sync(FULL, v, (int)((n % (uint32_t)(4 * WL)) >> 2), LPR);
-        }
-
-        // Pipeline over this lane's faces f = i0 + j (the low face of cell
-        // i0 + j): compute G_f, then update cell f-1 in place (it needs G_{f-1}
-        // and G_f and the old values of cells f-2, f-1, f).
-        Real g_first = Real(0), g_prev = Real(0), g_zero = Real(0);
-        Real old_prev = left_nb;
-        if (first_sl) old_prev = DIR ? Real(2) * wlo - T[0] : wrap_lo;
-        Real old_cur = T[0];
-#pragma unroll
-        for (int g = 0; g < C / 4; ++g) {
-            Real z[4] = {Real(0), Real(0), Real(0), Real(0)};
-            if (a.stochastic) {
-                const uint4 u = philox4x32_10(make_uint4(q0 + (uint32_t)g, n, stream, 0u), a.key0, a.key1);
-                box_muller4(u, z);
-            }
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int j = 4 * g + t;
-                Real gf;
-                if (j == 0) {
-                    // face i0: between cell i0-1 (neighbour lane, or wall/wrap) and i0
-                    gf = flux(left_nb, T[0], z[0]);
-                    if (first_sl) gf = DIR ? g_low_amp * z[0] : flux(wrap_lo, T[0], z[0]);
-                    g_first = gf;
-                    if (!DIR) g_zero = __shfl_sync(FULL, g_first, 0, LPR);
-                } else {
-                    gf = flux(old_cur, T[j], z[t]);
-                    Real tr = T[j];
-                    if (RAGGED && i0 + j == N) {            // ragged lane: the high face
-                        gf = DIR ? g_high : g_zero;
-                        tr = DIR ? Real(2) * whi - old_cur : wrap_hi;
-                    }
-                    const Real tc = old_cur;
-                    T[j - 1] = tc + r * (tr - Real(2) * tc + old_prev) + (gf - g_prev);
-                    old_prev = tc;
-                    old_cur = T[j];
-                }
-                g_prev = gf;
-            }
-        }
-        // last cell of the lane (j = C-1): its high face is the neighbour
-        // lane's first face, or the wall/wrap face when it is cell N-1.
-        {
-            const Real g_next = __shfl_down_sync(FULL, g_first, 1, LPR);
-            const Real tc = old_cur;
-            Real tr = right_nb;
-            Real gr = g_next;
-            if ((!RAGGED && tail_sl) || (RAGGED && i0 + C - 1 == N - 1)) {
-                tr = DIR ? Real(2) * whi - tc : wrap_hi;
-                gr = DIR ? g_high : g_zero;
-            }
-            T[C - 1] = tc + r * (tr - Real(2) * tc + old_prev) + (gr - g_prev);
-        }
-
+        rowst.step(T, a.step0 + (uint32_t)s);
         if (s == next_s) {                 // sample after step m = n + 1 (Eq. (3.9))
             next_s += a.K;
             ++nsamp;

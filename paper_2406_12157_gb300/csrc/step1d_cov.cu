@@ -1,0 +1,378 @@
+// step1d_cov.cu -- 1D forward-Euler step fused with the equal-time
+// covariance on the tensor cores (FP32 state, rows of up to 256 cells).
+//
+// Persistent launch, one CTA per SM.  CTA g owns at most 32 realizations; its
+// warps step them exactly as the moments-only kernel does (row1d.cuh).  At
+// every sampling step (Eq. (3.9)) each realization's centred snapshot
+// delta = T - T_ref is split into bf16 hi + lo and written, cells contiguous,
+// into one of two swizzled shared-memory operand buffers (row k = the CTA's
+// k-th realization, rows of absent realizations stay zero).  One thread then
+// issues C += hi^T hi + hi^T lo + lo^T hi as tcgen05 MMAs (M = 128 cells per
+// half, N = the padded row, K = 32 realizations) into an FP32 accumulator in
+// tensor memory and commits to the buffer's mbarrier; the warps go on
+// stepping while the tensor core works.  A buffer is rewritten only after the
+// MMAs that read it completed (bounded wait).  At launch end the accumulator
+// is added into the CTA's FP64 partial covariance in device memory.
+// The covariance generalises the one-point correlation the paper samples
+// (Sec. 3, Eq. (3.13)); every entry is an FP32 sum over at most
+// 32 x (samples per launch) products before the FP64 flush.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "philox.cuh"
+#include "row1d.cuh"
+#include "she_internal.cuh"
+#include "tc05.cuh"
+
+namespace she {
+
+using namespace tc05;
+
+constexpr uint32_t kOpLBO = 1024;           // neighbouring 64-cell atoms
+constexpr uint32_t kOpSBO = 4096;           // neighbouring 8-realization groups
+constexpr int kOpBytes = 16384;             // 32 realizations x 256 cells x bf16
+constexpr uint32_t kWaitTries = 1u << 20;   // bounded mbarrier waits
+
+template <int C>
+constexpr int cov_smem_bytes(int warps)
+{
+    return 1024 /* alignment slack */ + 4 * kOpBytes /* 2 stages x (hi, lo) */ + 64 /* barriers, flags */ +
+           warps * 2 * C * 32 * 4 /* moment partials */;
+}
+
+template <int C, int LPR, bool DIR, bool SPECIES, bool RAGGED>
+__global__ void __launch_bounds__(32 * LPR, 1)
+k_step1d_cov(const Step1DArgs<float> a, const CovArgs c)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int RPW = 32 / LPR;
+    constexpr int NBUF = 2;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // stage b: hi at base + 2b * kOpBytes, lo right after it
+    auto op_hi = [&](int b) { return base + 2 * b * kOpBytes; };
+    auto op_lo = [&](int b) { return base + (2 * b + 1) * kOpBytes; };
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + 4 * kOpBytes);   // [2]: snapshot written
+    uint64_t* empty = full + 2;                                           // [2]: MMAs done reading
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(empty + 2);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+    float* mom = reinterpret_cast<float*>(base + 4 * kOpBytes + 64);
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int sl = lane % LPR;
+    const int g = blockIdx.x;
+    // realizations of this CTA inside the wave [r_begin, r_begin + r_count)
+    const int rb = c.r_begin + (int)((long long)c.r_count * g / gridDim.x);
+    const int re = c.r_begin + (int)((long long)c.r_count * (g + 1) / gridDim.x);
+    const int count = re - rb;
+    // warps 0..LPR-2 step realizations (slots warp*RPW + segment); the last
+    // warp issues the MMAs
+    constexpr int MMA_WARP = LPR - 1;
+    const bool is_mma_warp = (warp == MMA_WARP);
+    const int slot = warp * RPW + lane / LPR;
+    const bool active = !is_mma_warp && slot < count;
+    const bool warp_active = !is_mma_warp && warp * RPW < count;
+    const int active_warps = (count + RPW - 1) / RPW;
+    const int rho = active ? rb + slot : (count > 0 ? rb : 0);
+
+    float* sm1 = mom + warp * (2 * C * 32) + lane;
+    float* sm2 = sm1 + C * 32;
+
+    // zero both operand stages (rows of absent realizations stay zero)
+    for (int i = threadIdx.x; i < 4 * kOpBytes / 16; i += blockDim.x)
+        reinterpret_cast<uint4*>(base)[i] = make_uint4(0u, 0u, 0u, 0u);
+
+    const int N = a.N;
+    const int Mh = (N + 127) / 128;
+    const int Nm = ((N + 15) / 16) * 16;
+    uint32_t ncols = 32;
+    while ((int)ncols < Mh * Nm) ncols <<= 1;
+    const bool use_tc = c.has_samples != 0;
+    if (threadIdx.x == 0) {
+        *abort_flag = 0;
+        if (use_tc) {
+            for (int b = 0; b < NBUF; ++b) {
+                mbar_init(&full[b], (uint32_t)active_warps);
+                mbar_init(&empty[b], 1);
+            }
+            fence_mbar_init();
+        }
+    }
+    if (use_tc && warp == 0) {
+        tmem_alloc(tslot, ncols);
+        tmem_relinquish();
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tbase = use_tc ? *tslot : 0u;
+
+    Row1D<float, C, LPR, DIR, SPECIES, RAGGED> rowst;
+    rowst.init(a, sl, rho);
+    const int i0 = sl * C;
+    float* row = a.state + (size_t)rho * (size_t)N;
+    float T[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        const int i = i0 + j;
+        T[j] = (!RAGGED || i < N) ? row[i] : 0.0f;
+        sm1[j * 32] = 0.0f;
+        sm2[j * 32] = 0.0f;
+    }
+    const float wlo = a.wall_lo;
+    const float dref = DIR ? (a.wall_hi - a.wall_lo) / (float)N : 0.0f;
+    int next_s = first_sample_index(a.step0, a.relax, a.K, a.nsteps);
+    int nsnap = 0;
+    const uint32_t idesc = idesc_bf16_f32(128, Nm, true, true);
+
+    if (is_mma_warp) {
+        // MMA issue: one thread, once every stepping warp wrote the snapshot
+        if (use_tc && lane == 0) {
+            int ns = 0;
+            for (int s = next_s; s < a.nsteps; s += a.K) ++ns;
+            for (int sn = 0; sn < ns && !*abort_flag; ++sn) {
+                const int b = sn & 1;
+                if (!mbar_wait_sleep_bounded(&full[b], (uint32_t)((sn >> 1) & 1), kWaitTries)) {
+                    *abort_flag = 1;
+                    atomicOr(a.flags, 2);
+                    break;
+                }
+                fence_after_sync();
+                const uint32_t hb = smem_u32(op_hi(b)), lb = smem_u32(op_lo(b));
+                for (int h = 0; h < Mh; ++h) {
+                    const uint32_t dt = tbase + (uint32_t)(h * Nm);
+                    const uint32_t moff = (uint32_t)h * 2u * kOpLBO;
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {        // K = 32 slots = 2 x 16
+                        const uint32_t koff = (uint32_t)kk * 2u * kOpSBO;
+                        const uint64_t a_hi = desc_sw128(hb + koff + moff, kOpLBO, kOpSBO);
+                        const uint64_t a_lo = desc_sw128(lb + koff + moff, kOpLBO, kOpSBO);
+                        const uint64_t b_hi = desc_sw128(hb + koff, kOpLBO, kOpSBO);
+                        const uint64_t b_lo = desc_sw128(lb + koff, kOpLBO, kOpSBO);
+                        mma_bf16(dt, a_hi, b_hi, idesc, (sn > 0 || kk > 0) ? 1u : 0u);
+                        mma_bf16(dt, a_hi, b_lo, idesc, 1u);
+                        mma_bf16(dt, a_lo, b_hi, idesc, 1u);
+                    }
+                }
+                mma_commit(&empty[b]);
+            }
+            nsnap = ns;
+        }
+        nsnap = __shfl_sync(FULL, nsnap, 0);
+    } else
+    for (int s = 0; s < a.nsteps; ++s) {
+        if (warp_active) rowst.step(T, a.step0 + (uint32_t)s);
+        if (s != next_s) continue;
+        next_s += a.K;
+        const int b = nsnap & 1;
+        if (warp_active) {
+            bool ok = true;
+            const bool tc_on = use_tc && !*abort_flag;
+            if (tc_on && nsnap >= 2) {
+                // buffer b was last read by the MMAs of snapshot nsnap-2
+                if (lane == 0)
+                    ok = mbar_wait_sleep_bounded(&empty[b], (uint32_t)(((nsnap >> 1) - 1) & 1), kWaitTries);
+                ok = __shfl_sync(FULL, ok ? 1 : 0, 0) != 0;
+            }
+            const bool write = tc_on && ok && active;
+            // eight cells at a time: delta, moment partials, bf16 hi/lo split,
+            // one 16-byte chunk of each operand (four-cell halves for C = 4)
+            constexpr int G8 = C >= 8 ? 8 : 4;
+#pragma unroll
+            for (int j0 = 0; j0 < C; j0 += G8) {
+                float d[G8];
+#pragma unroll
+                for (int t = 0; t < G8; ++t) {
+                    const int j = j0 + t;
+                    const float ref = DIR ? fmaf(dref, (float)(i0 + j) + 0.5f, wlo) : wlo;
+                    d[t] = T[j] - ref;
+                    sm1[j * 32] += d[t];
+                    sm2[j * 32] = fmaf(d[t], d[t], sm2[j * 32]);
+                    if (RAGGED && i0 + j >= N) d[t] = 0.0f;
+                }
+                if (write) {
+                    uint32_t hw[G8 / 2], lw[G8 / 2];
+#pragma unroll
+                    for (int q = 0; q < G8 / 2; ++q) split_bf16x2(d[2 * q], d[2 * q + 1], hw[q], lw[q]);
+                    const uint32_t off = sw128_mn_offset(slot, i0 + j0, kOpLBO, kOpSBO);
+                    if (G8 == 8) {
+                        *reinterpret_cast<uint4*>(op_hi(b) + off) = make_uint4(hw[0], hw[1], hw[2 % (G8 / 2)], hw[3 % (G8 / 2)]);
+                        *reinterpret_cast<uint4*>(op_lo(b) + off) = make_uint4(lw[0], lw[1], lw[2 % (G8 / 2)], lw[3 % (G8 / 2)]);
+                    } else {
+                        *reinterpret_cast<uint2*>(op_hi(b) + off) = make_uint2(hw[0], hw[1]);
+                        *reinterpret_cast<uint2*>(op_lo(b) + off) = make_uint2(lw[0], lw[1]);
+                    }
+                }
+            }
+            if (tc_on) {
+                if (!ok && lane == 0) {
+                    *abort_flag = 1;
+                    atomicOr(a.flags, 2);
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full[b]);
+            }
+        }
+        ++nsnap;
+    }
+
+    // state and moment partials
+    bool bad = false;
+    if (active) {
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            const int i = i0 + j;
+            if (!RAGGED || i < N) {
+                row[i] = T[j];
+                bad |= !finite_any(T[j]);
+            }
+        }
+        if (nsnap > 0) {
+            double* p1 = a.acc1 + (size_t)rho * (size_t)N;
+            double* p2 = a.acc2 + (size_t)rho * (size_t)N;
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                const int i = i0 + j;
+                if (!RAGGED || i < N) {
+                    p1[i] += (double)sm1[j * 32];
+                    p2[i] += (double)sm2[j * 32];
+                }
+            }
+        }
+    }
+    if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.flags, 1);
+
+    if (use_tc) {
+        __syncthreads();
+        // the last commit covers every MMA issued before it
+        bool done = true;
+        if (nsnap > 0 && !*abort_flag) {
+            const int ls = nsnap - 1;
+            done = mbar_wait_sleep_bounded(&empty[ls & 1], (uint32_t)((ls >> 1) & 1), kWaitTries);
+        }
+        const int all_done = __syncthreads_and(done ? 1 : 0);
+        const bool aborted = *abort_flag != 0;
+        fence_after_sync();
+        if (!all_done) {
+            if (threadIdx.x == 0) atomicOr(a.flags, 2);
+        } else if (!aborted && nsnap > 0 && warp < 4) {
+            double* P = c.partial + (size_t)g * (size_t)N * (size_t)N;
+            for (int h = 0; h < Mh; ++h) {
+                const int rowi = h * 128 + 32 * warp + lane;
+                for (int c0 = 0; c0 < Nm; c0 += 32) {
+                    float v[32];
+                    tmem_ld_32x32b_x32(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(h * Nm + c0), v);
+                    if (rowi < N) {
+#pragma unroll
+                        for (int t = 0; t < 32; ++t) {
+                            const int col = c0 + t;
+                            if (col < N) P[(size_t)col * N + rowi] += (double)v[t];
+                        }
+                    }
+                }
+            }
+        }
+        fence_before_sync();
+        __syncthreads();
+        if (warp == 0) tmem_dealloc(tbase, ncols);
+    }
+}
+
+template <int C, int LPR, bool DIR, bool SP>
+static cudaError_t launch_cov_layout(const Step1DArgs<float>& a, const CovArgs& c, int grid, cudaStream_t st)
+{
+    const int smem = cov_smem_bytes<C>(LPR);
+    if (a.N == C * LPR) {
+        auto k = k_step1d_cov<C, LPR, DIR, SP, false>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k<<<grid, 32 * LPR, smem, st>>>(a, c);
+    } else {
+        auto k = k_step1d_cov<C, LPR, DIR, SP, true>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k<<<grid, 32 * LPR, smem, st>>>(a, c);
+    }
+    return cudaGetLastError();
+}
+
+// realization slots per CTA of the layout chosen for N: (warps - 1) x (32 / LPR)
+static int cov_slots_per_cta(int N)
+{
+    const int lpr = N <= 16 ? 4 : N <= 32 ? 8 : N <= 64 ? 16 : N <= 128 ? 32 : 8;
+    return (lpr - 1) * (32 / lpr);
+}
+
+template <bool DIR, bool SP>
+static cudaError_t launch_cov_ds(const Step1DArgs<float>& a, const CovArgs& c, int grid, cudaStream_t st)
+{
+    const int N = a.N;
+    if (N <= 16) return launch_cov_layout<4, 4, DIR, SP>(a, c, grid, st);
+    if (N <= 32) return launch_cov_layout<4, 8, DIR, SP>(a, c, grid, st);
+    if (N <= 64) return launch_cov_layout<4, 16, DIR, SP>(a, c, grid, st);
+    if (N <= 128) return launch_cov_layout<4, 32, DIR, SP>(a, c, grid, st);
+    return launch_cov_layout<32, 8, DIR, SP>(a, c, grid, st);
+}
+
+cudaError_t launch_step1d_cov(Handle& h, uint32_t step0, int nsteps, bool has_samples)
+{
+    Step1DArgs<float> a;
+    a.state = (float*)h.d_state;
+    a.acc1 = h.d_acc1;
+    a.acc2 = h.d_acc2;
+    a.flags = h.d_flags;
+    a.N = h.prob.n[0];
+    a.R = (int)h.R;
+    a.r = (float)h.prob.r;
+    a.amp2 = (float)(h.stochastic ? 2.0 * h.prob.r * h.prob.eps : 0.0);
+    a.wall_lo = (float)h.prob.wall_lo;
+    a.wall_hi = (float)h.prob.wall_hi;
+    a.key0 = (uint32_t)(h.prob.seed & 0xffffffffu);
+    a.key1 = (uint32_t)(h.prob.seed >> 32);
+    a.step0 = step0;
+    a.nsteps = nsteps;
+    a.K = h.K;
+    a.relax = (long long)h.relax;
+    a.stream0 = h.stream0;
+    a.stochastic = h.stochastic;
+    const bool dir = h.prob.bc == SHE_DIRICHLET;
+    const bool sp = h.prob.equation == SHE_SPECIES;
+    // waves of at most (stepper warps x realizations per warp) per CTA
+    const int G = h.cov_ctas;
+    const int64_t per_wave = (int64_t)cov_slots_per_cta(a.N) * G;
+    for (int64_t rb = 0; rb < h.R; rb += per_wave) {
+        CovArgs c;
+        c.partial = h.d_cov_partial;
+        c.r_begin = (int)rb;
+        c.r_count = (int)std::min<int64_t>(per_wave, h.R - rb);
+        c.has_samples = has_samples ? 1 : 0;
+        const int grid = (int)std::min<int64_t>(G, c.r_count);
+        cudaError_t e;
+        if (dir) e = sp ? launch_cov_ds<true, true>(a, c, grid, h.stream) : launch_cov_ds<true, false>(a, c, grid, h.stream);
+        else e = sp ? launch_cov_ds<false, true>(a, c, grid, h.stream) : launch_cov_ds<false, false>(a, c, grid, h.stream);
+        h.launches += 1;
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Sum the per-CTA FP64 partial covariances: out[i] = sum_g partial[g][i].
+__global__ void k_reduce_partials(const double* __restrict__ partial, int64_t n, int G, double* __restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int g = 0; g < G; ++g) s += partial[(int64_t)g * n + i];
+    out[i] = s;
+}
+
+cudaError_t launch_reduce_cov(const Handle& h, double* d_out)
+{
+    const int64_t n = (int64_t)h.prob.n[0] * h.prob.n[0];
+    k_reduce_partials<<<(unsigned)((n + 255) / 256), 256, 0, h.stream>>>(h.d_cov_partial, n, h.cov_ctas, d_out);
+    return cudaGetLastError();
+}
+
+}  // namespace she

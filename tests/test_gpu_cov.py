@@ -1,0 +1,71 @@
+"""GPU checks of the tensor-core covariance kernel (tcgen05, bf16 hi/lo
+split, FP32 accumulation in tensor memory) against the FP64 product.
+
+The split keeps ~16 significant bits per product: the error of one entry of
+X^T X is bounded by about 2^-15 * sum_k |x_ki x_kj|; the tolerance below is
+that bound with margin."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2406_12157_gb300 as S  # noqa: E402
+
+
+@pytest.mark.parametrize("N", [1, 16, 32, 100, 128, 129, 200, 256])
+@pytest.mark.parametrize("K", [1, 27, 32])
+def test_syrk_probe_matches_fp64(N, K):
+    rng = np.random.default_rng(N * 100 + K)
+    X = rng.normal(0.0, 0.03, size=(K, N)).astype(np.float32)
+    X64 = X.astype(np.float64)
+    ref = X64.T @ X64
+    bound = np.abs(X64).T @ np.abs(X64)
+    C = S.she_syrk_probe(X)
+    assert np.all(np.abs(C - ref) <= 4.0 * 2.0 ** -16 * bound + 1e-30)
+
+
+import she_workloads as W  # noqa: E402
+from oracle import she as O  # noqa: E402
+
+
+def _cov_case(N, R, steps, walls=(1.0, 2.0), bc="dirichlet", K=10, sk=True):
+    p = W.gradient_rod(n=(N, 1, 1), realizations=R, relax_steps=0, stats_interval=K,
+                       wall_lo=walls[0], wall_hi=walls[1], bc=bc, want_cov=1, want_sk=int(sk))
+    with S.Simulation(p) as sim:
+        sim.step(steps)
+        g = sim.stats(cov=True, sk=sk)
+    o = O.finalize(p, O.run(p, R, steps, want_cov=1, want_sk=int(sk)))
+    return p, g, o
+
+
+@pytest.mark.parametrize("N,R,steps", [(16, 40, 200), (32, 400, 300), (100, 300, 200),
+                                       (200, 300, 120), (256, 200, 150), (32, 5000, 60)])
+def test_fused_covariance_matches_oracle(N, R, steps):
+    # small grids, several realizations per CTA, ragged rows, one or two
+    # 128-cell halves, and (R = 5000 > 32 x SMs) two realization waves
+    p, g, o = _cov_case(N, R, steps)
+    assert g["n_samples"] == o["n"]
+    scale = np.max(np.diag(o["cov"]))
+    assert np.max(np.abs(g["cov"] - o["cov"])) < 2e-4 * scale
+    # diagonal of the tensor-core covariance vs the CUDA-core variance
+    assert np.max(np.abs(np.diag(g["cov"]) - g["var"])) < 2e-4 * scale
+    assert np.max(np.abs(g["sk_fluct"] - o["sk_fluct"])) < 2e-4 * np.max(o["sk_fluct"])
+    assert np.allclose(g["sk"], o["sk"], rtol=1e-6, atol=2e-4 * np.max(o["sk_fluct"]))
+
+
+def test_fused_covariance_periodic():
+    p, g, o = _cov_case(64, 300, 200, walls=(1.0, 1.0), bc="periodic")
+    scale = np.max(np.diag(o["cov"]))
+    assert np.max(np.abs(g["cov"] - o["cov"])) < 2e-4 * scale
+    assert np.max(np.abs(g["sk_fluct"] - o["sk_fluct"])) < 2e-4 * np.max(o["sk_fluct"])
+
+
+def test_full_size_covariance_matches_oracle():
+    # 256 cells x 4096 realizations, the benchmark's launch shape, 10 snapshots
+    p, g, o = _cov_case(256, 4096, 100, sk=False)
+    scale = np.max(np.diag(o["cov"]))
+    assert np.max(np.abs(g["cov"] - o["cov"])) < 2e-4 * scale
