@@ -122,16 +122,14 @@ def _cells(p):
 # ------------------------------------------------------------ oracle timing --
 
 def oracle_sample_rate(p, seconds_hint=10.0):
-    """Time the FP64 oracle, as it stands, on a bounded sample of the workload:
-    64 realizations x 10,000 steps in the sampling phase (relax 0); returns
-    (cell-updates/s, threads, sample description)."""
+    """Time the FP64 oracle, as it stands, on a bounded sample of the workload
+    (about 2.6e9 cell-updates in the sampling phase, relax 0, i.e. ~10 s on 16
+    cores); returns (cell-updates/s, threads, sample description)."""
     from oracle import she as O
     q = dict(p)
     q["relax_steps"] = 0
-    R_s = 64
     steps = 10_000
-    if _cells(p) <= 64:
-        R_s = 256
+    R_s = max(16, min(p["realizations"], int(2.6e9 // (steps * _cells(p)))))
     O.lib()
     t0 = time.perf_counter()
     O.run(q, R_s, steps)
