@@ -251,6 +251,36 @@ she_status she_noise_probe(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
  */
 she_status she_syrk_probe(const float* X, int32_t K, int32_t N, double* C);
 
+/*
+ * One plain FP64 forward-Euler step that allocates nothing.  The paper has no
+ * counterpart: this is a service entry point for callers that cannot call
+ * cudaMalloc -- code that runs while a CUDA graph is being captured, callers
+ * whose device memory is entirely pre-reserved by their own allocator or
+ * memory budget, and real-time loops that forbid allocation (and the device
+ * synchronisation it can imply) after start-up.  The caller owns the state.
+ *
+ * Advances the 1D rows T_in [realizations][N] (device pointer, FP64) by the
+ * step with absolute index `step` into T_out (device pointer, same shape,
+ * must not alias T_in), with the physics, noise stream and plain two-kernel
+ * form of a handle created with kernel = SHE_KERNEL_PLAIN (same results);
+ * no sampling.  Uses from `p`: dim (must be 1), n, dx, area, equation, bc,
+ * kappa, rho_cv, kB, D, n0, walls, dt, seed, realizations, stochastic,
+ * precision (must be SHE_FP64), stream_offset, stream.
+ * The face fluxes go to one fixed device array of SHE_NOALLOC_MAX_FACES
+ * doubles (8 MiB, held by every GPU that loads the library until the process
+ * exits); realizations * (N + 1) above that is rejected with
+ * SHE_ERR_INVALID_ARG (and a message on stderr).  All calls on one GPU share
+ * that array and it keeps the last call's contents (every entry a call reads
+ * it first writes, so nothing needs clearing); calls whose kernels overlap on
+ * the same GPU, e.g. issued on different streams, race -- issue them on one
+ * stream.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Asynchronous on
+ * p->stream.  Errors: SHE_ERR_INVALID_ARG, SHE_ERR_UNSTABLE, SHE_ERR_CUDA.
+ */
+#define SHE_NOALLOC_MAX_FACES (1 << 20)
+she_status she_step_plain_noalloc(const she_params* p, const double* T_in, double* T_out, uint64_t step);
+
 /* Number of kernel launches enqueued by this handle since init (for the
  * benchmark's launch accounting). */
 int64_t she_launch_count(const she_handle* h);

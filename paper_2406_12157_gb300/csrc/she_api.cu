@@ -11,9 +11,16 @@
 #include <string>
 #include <vector>
 
+#include <mutex>
+
 #include "she_internal.cuh"
 
 using she::Handle;
+
+// Face-flux scratch of she_step_plain_noalloc: a file-scope device array, so
+// that entry point never allocates.  Every GPU that loads the library holds
+// these SHE_NOALLOC_MAX_FACES doubles (8 MiB) until the process exits.
+static __device__ __align__(256) double g_noalloc_faces[SHE_NOALLOC_MAX_FACES];
 
 namespace {
 
@@ -484,6 +491,54 @@ void she_free(she_handle* hh)
     else cudaDeviceSynchronize();
     release(h);
     delete h;
+}
+
+she_status she_step_plain_noalloc(const she_params* p, const double* T_in, double* T_out, uint64_t step)
+{
+    // Device address of the scratch array, looked up once per device (the
+    // host-side name g_noalloc_faces is only a stand-in for the symbol).
+    static std::mutex mu;
+    static double* addr[64] = {nullptr};
+    if (!p || !T_in || !T_out || T_in == T_out) return SHE_ERR_INVALID_ARG;
+    she::Problem prob;
+    std::string msg;
+    she_status st = convert(*p, prob, msg);
+    if (st != SHE_OK) {
+        fprintf(stderr, "%s\n", msg.c_str());
+        return st;
+    }
+    if (p->dim != 1 || p->realizations < 1 || p->precision != SHE_FP64 || step > (uint64_t)0xffffffffu ||
+        p->stream_offset < 0 || (int64_t)p->stream_offset + p->realizations > ((int64_t)1 << 32)) {
+        fprintf(stderr, "she_step_plain_noalloc: needs dim 1, FP64, realizations >= 1, step < 2^32\n");
+        return SHE_ERR_INVALID_ARG;
+    }
+    const int64_t faces = p->realizations * (int64_t)(prob.n[0] + 1);
+    if (faces > (int64_t)SHE_NOALLOC_MAX_FACES) {
+        fprintf(stderr,
+                "she_step_plain_noalloc: realizations * (N + 1) = %lld face fluxes exceed the fixed scratch "
+                "of %d\n",
+                (long long)faces, (int)SHE_NOALLOC_MAX_FACES);
+        return SHE_ERR_INVALID_ARG;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 64) return SHE_ERR_CUDA;
+    double* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!addr[dev]) {
+            e = cudaGetSymbolAddress((void**)&addr[dev], g_noalloc_faces);
+            if (e != cudaSuccess) {
+                addr[dev] = nullptr;
+                return SHE_ERR_CUDA;
+            }
+        }
+        scratch = addr[dev];
+    }
+    e = she::launch_plain_step_scratch(prob, (int)p->realizations, T_in, T_out, scratch, (uint32_t)step,
+                                       (uint32_t)p->stream_offset, p->stochastic ? 1 : 0,
+                                       (cudaStream_t)p->stream);
+    return e == cudaSuccess ? SHE_OK : SHE_ERR_CUDA;
 }
 
 she_status she_noise_probe(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, int64_t count,

@@ -88,6 +88,8 @@ struct Handle {
 cudaError_t launch_init_state(Handle& h);
 cudaError_t launch_step1d(Handle& h, uint32_t step0, int nsteps);
 cudaError_t launch_step1d_plain(Handle& h, uint32_t step0, int nsteps);
+cudaError_t launch_plain_step_scratch(const Problem& p, int R, const double* T, double* Tn, double* G,
+                                      uint32_t n, uint32_t stream0, int stochastic, cudaStream_t st);
 cudaError_t launch_step1d_cov(Handle& h, uint32_t step0, int nsteps, bool has_samples);
 cudaError_t launch_reduce_cov(const Handle& h, double* d_out);
 cudaError_t launch_reduce_batches(const Handle& h, int batches, double* d_out1, double* d_out2);

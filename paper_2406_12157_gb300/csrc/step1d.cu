@@ -307,6 +307,26 @@ __global__ void k_plain_sample(const double* __restrict__ T, double* __restrict_
     acc2[idx] += d * d;
 }
 
+// One plain FP64 step of R rows from T into Tn with the face fluxes in the
+// caller-provided device buffer G (at least R * (N + 1) doubles).  Used by
+// the entry point that allocates nothing; the handle path above keeps its own.
+cudaError_t launch_plain_step_scratch(const Problem& p, int R, const double* T, double* Tn, double* G,
+                                      uint32_t n, uint32_t stream0, int stochastic, cudaStream_t st)
+{
+    const int N = p.n[0];
+    const bool dir = p.bc == SHE_DIRICHLET;
+    const double amp2 = stochastic ? 2.0 * p.r * p.eps : 0.0;
+    const uint32_t key0 = (uint32_t)(p.seed & 0xffffffffu), key1 = (uint32_t)(p.seed >> 32);
+    const int tpb = 256;
+    const long long nfaces = (long long)R * (N + 1), ncells = (long long)R * N;
+    k_plain_faces<<<(unsigned)((nfaces + tpb - 1) / tpb), tpb, 0, st>>>(
+        T, G, N, R, amp2, p.wall_lo, p.wall_hi, dir, p.equation == SHE_SPECIES, key0, key1, n, stochastic,
+        stream0);
+    k_plain_cells<<<(unsigned)((ncells + tpb - 1) / tpb), tpb, 0, st>>>(T, Tn, G, N, R, p.r, p.wall_lo,
+                                                                        p.wall_hi, dir);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_step1d_plain(Handle& h, uint32_t step0, int nsteps)
 {
     const int N = h.prob.n[0];
