@@ -124,6 +124,9 @@ void release(Handle* h)
     cudaFree(h->d_red);
     cudaFree(h->d_cov_partial);
     cudaFree(h->d_cov_red);
+    cudaFree(h->d_m1);
+    cudaFree(h->d_m2);
+    h->d_m1 = h->d_m2 = nullptr;
     h->d_cov_partial = h->d_cov_red = nullptr;
     h->d_state = h->d_state2 = nullptr;
     h->d_acc1 = h->d_acc2 = h->d_face = h->d_red = nullptr;
@@ -193,7 +196,18 @@ she_status she_init(const she_params* p, she_handle** out)
         st = SHE_ERR_INVALID_ARG; msg = "she: SHE_SK_AXES is for 2D/3D grids (use SHE_SK_FULL in 1D)";
     }
     if (st == SHE_OK && p->want_sk && p->dim > 1) { st = SHE_ERR_UNSUPPORTED; msg = "she: S(k) not built yet"; }
-    if (st == SHE_OK && p->dim > 1) { st = SHE_ERR_UNSUPPORTED; msg = "she: 2D/3D not built yet"; }
+    if (st == SHE_OK && p->dim == 3 && !(p->n[0] == 128 || p->n[0] == 256 || p->n[0] == 512)) {
+        st = SHE_ERR_UNSUPPORTED; msg = "she: 3D grids need nx = 128, 256 or 512";
+    }
+    if (st == SHE_OK && p->dim == 3 && 3 * h->prob.cells >= ((int64_t)1 << 32)) {
+        st = SHE_ERR_INVALID_ARG; msg = "she: 3 x cells must stay below 2^32 (noise index)";
+    }
+    if (st == SHE_OK && p->dim == 2 && (p->n[0] % 4 != 0 || p->n[0] > 512)) {
+        st = SHE_ERR_UNSUPPORTED; msg = "she: 2D grids need nx a multiple of 4 and at most 512";
+    }
+    if (st == SHE_OK && p->dim > 1 && p->kernel != SHE_KERNEL_AUTO) {
+        st = SHE_ERR_UNSUPPORTED; msg = "she: the plain form is 1D";
+    }
     if (st != SHE_OK) {
         fprintf(stderr, "%s\n", msg.c_str());
         delete h;
@@ -223,6 +237,15 @@ she_status she_init(const she_params* p, she_handle** out)
     const int batches = (int)std::min<int64_t>(32, h->R);
     h->red_bytes = 2 * (size_t)batches * cells * sizeof(double);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_red, h->red_bytes);
+    if (e == cudaSuccess && h->prob.dim > 1) {
+        e = cudaMalloc(&h->d_state2, nstate * elem);
+        if (e == cudaSuccess && h->precision == SHE_FP32) {
+            e = cudaMalloc(&h->d_m1, nstate * sizeof(float));
+            if (e == cudaSuccess) e = cudaMalloc(&h->d_m2, nstate * sizeof(float));
+            if (e == cudaSuccess) e = cudaMemsetAsync(h->d_m1, 0, nstate * sizeof(float), h->stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(h->d_m2, 0, nstate * sizeof(float), h->stream);
+        }
+    }
     if (e == cudaSuccess && h->kernel == SHE_KERNEL_PLAIN) {
         e = cudaMalloc(&h->d_state2, nstate * elem);
         if (e == cudaSuccess) e = cudaMalloc(&h->d_face, (size_t)h->R * (cells + 1) * sizeof(double));
@@ -274,7 +297,9 @@ she_status she_step_n(she_handle* hh, uint64_t n)
         int chunk = (int)std::min<uint64_t>(left, (uint64_t)spl);
         cudaError_t e;
         const int64_t ns = samples_in(h->step, (uint64_t)chunk, h->K, h->relax);
-        if (h->kernel == SHE_KERNEL_PLAIN) e = she::launch_step1d_plain(*h, (uint32_t)h->step, chunk);
+        if (h->prob.dim == 2) e = she::launch_step2d(*h, (uint32_t)h->step, chunk);
+        else if (h->prob.dim == 3) e = she::launch_step3d(*h, (uint32_t)h->step, chunk);
+        else if (h->kernel == SHE_KERNEL_PLAIN) e = she::launch_step1d_plain(*h, (uint32_t)h->step, chunk);
         else if (h->want_cov) e = she::launch_step1d_cov(*h, (uint32_t)h->step, chunk, ns > 0);
         else e = she::launch_step1d(*h, (uint32_t)h->step, chunk);
         if (e != cudaSuccess) return cuda_fail(h, e, "she_step_n");
@@ -318,6 +343,10 @@ she_status she_stats(she_handle* hh, she_stats_out* out)
     if (h->samples_per_real == 0) return fail(h, SHE_ERR_STATE, "she: no sample taken yet");
     const int64_t cells = h->prob.cells;
     const int B = (int)std::min<int64_t>(32, h->R);
+    if (h->d_m1 && h->partial_samples > 0) {
+        e = she::launch_flush_moments(*h);
+        if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(flush)");
+    }
     double* d1 = h->d_red;
     double* d2 = h->d_red + (size_t)B * cells;
     e = she::launch_reduce_batches(*h, B, d1, d2);
@@ -414,6 +443,9 @@ she_status she_reset_stats(she_handle* hh)
     const size_t nstate = (size_t)h->R * (size_t)h->prob.cells;
     cudaError_t e = cudaMemsetAsync(h->d_acc1, 0, nstate * sizeof(double), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_acc2, 0, nstate * sizeof(double), h->stream);
+    if (e == cudaSuccess && h->d_m1) e = cudaMemsetAsync(h->d_m1, 0, nstate * sizeof(float), h->stream);
+    if (e == cudaSuccess && h->d_m2) e = cudaMemsetAsync(h->d_m2, 0, nstate * sizeof(float), h->stream);
+    h->partial_samples = 0;
     if (e == cudaSuccess && h->d_cov_partial)
         e = cudaMemsetAsync(h->d_cov_partial, 0,
                             (size_t)h->cov_ctas * (size_t)h->prob.cells * (size_t)h->prob.cells * sizeof(double),

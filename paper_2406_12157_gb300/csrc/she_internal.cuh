@@ -46,6 +46,38 @@ struct Step1DArgs {
     int stochastic;
 };
 
+// Arguments of the 2D step kernel (one step per launch).
+template <typename Real>
+struct Step2DArgs {
+    const Real* T;        // [R][ny][nx] old state
+    Real* Tn;             // [R][ny][nx] new state
+    Real* m1;             // [R][cells] moment partial sums (FP32 partials, or the FP64 accumulators)
+    Real* m2;
+    int* flags;
+    int nx, ny, R;
+    int H;                // rows per band
+    int tiles;            // bands per realization
+    Real r, amp2, ref;
+    uint32_t key0, key1, step, stream0;
+    int stochastic;
+    int sample;           // this step is a sampling step
+};
+
+// Arguments of the 3D step kernel (one step per launch).
+template <typename Real>
+struct Step3DArgs {
+    const Real* T;        // [R][nz][ny][nx] old state
+    Real* Tn;
+    Real* m1;             // [R][cells] moment partial sums
+    Real* m2;
+    int* flags;
+    int nx, ny, nz, R;
+    Real r, amp2, ref;
+    uint32_t key0, key1, step, stream0;
+    int stochastic;
+    int sample;
+};
+
 // Extra arguments of the fused covariance kernel.
 struct CovArgs {
     double* partial;      // [G][N][N] per-CTA FP64 partial sums of delta delta^T
@@ -77,6 +109,9 @@ struct Handle {
     double* d_face = nullptr;      // plain form: face fluxes [R][N+1]
     int* d_flags = nullptr;
     double* d_red = nullptr;       // reduction scratch
+    float* d_m1 = nullptr;         // 2D/3D FP32: per-realization moment partials [R][cells]
+    float* d_m2 = nullptr;
+    int partial_samples = 0;       // samples held in d_m1/d_m2 since the last flush
     double* d_cov_partial = nullptr;  // [cov_ctas][N][N] FP64 partial covariance sums
     double* d_cov_red = nullptr;   // [N][N] reduced
     int cov_ctas = 0;              // CTAs (one per SM) of the fused covariance kernel
@@ -92,6 +127,9 @@ cudaError_t launch_plain_step_scratch(const Problem& p, int R, const double* T, 
                                       uint32_t n, uint32_t stream0, int stochastic, cudaStream_t st);
 cudaError_t launch_step1d_cov(Handle& h, uint32_t step0, int nsteps, bool has_samples);
 cudaError_t launch_reduce_cov(const Handle& h, double* d_out);
+cudaError_t launch_step2d(Handle& h, uint32_t step0, int nsteps);
+cudaError_t launch_step3d(Handle& h, uint32_t step0, int nsteps);
+cudaError_t launch_flush_moments(Handle& h);
 cudaError_t launch_reduce_batches(const Handle& h, int batches, double* d_out1, double* d_out2);
 cudaError_t launch_syrk_probe(const float* d_X, int K, int N, double* d_C, int* d_err);
 cudaError_t launch_noise_probe(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,

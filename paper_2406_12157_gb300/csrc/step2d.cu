@@ -1,0 +1,265 @@
+// step2d.cu -- forward-Euler step of the 2D stochastic heat / species
+// diffusion equation on a periodic grid, many realizations (Sec. 3, Eq. (3.3)
+// applied per axis with independent face noises, Eq. (2.11); species noise
+// Eq. (4.7)).
+//
+// One launch = one step (the state streams through L2/HBM, ping-pong
+// buffers).  A segment of LPR lanes owns a band of H rows of one realization
+// across the full row width (lane l holds x-cells [l*C, l*C + C)) and marches
+// down the band keeping rows y-1, y, y+1 and the low y-face fluxes of rows y
+// and y+1 in registers; x-neighbours and x-face fluxes cross lanes by
+// segmented shuffles with periodic wrap.  Each face flux is computed from its
+// own Philox slot (normal g = axis * Ncells + x + nx * y), so the row shared
+// by two bands is computed identically by both.  Per cell-update the kernel
+// reads the old value once (plus one halo row per band) and writes the new
+// value once: ~8 bytes of traffic; the noise never touches memory.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "philox.cuh"
+#include "row1d.cuh"
+#include "she_internal.cuh"
+
+namespace she {
+
+template <typename Real, int C, int LPR, bool SPECIES, bool RAGGED>
+__global__ void __launch_bounds__(128)
+k_step2d(const Step2DArgs<Real> a)
+{
+    static_assert(C % 4 == 0, "cells per lane must be a multiple of 4");
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int SPW = 32 / LPR;                     // segments per warp
+    const int lane = threadIdx.x & 31;
+    const int sl = lane % LPR;
+    const int warp = blockIdx.x * 4 + (threadIdx.x >> 5);
+    const int nseg = a.R * a.tiles;
+    if (warp * SPW >= nseg) return;                   // warp-uniform
+    const int seg_raw = warp * SPW + lane / LPR;
+    const bool active = seg_raw < nseg;
+    const int seg = active ? seg_raw : nseg - 1;
+    const int rho = seg / a.tiles;
+    const int tile = seg % a.tiles;
+    const int nx = a.nx, ny = a.ny;
+    const int y0 = tile * a.H;
+    const int y1 = min(y0 + a.H, ny);
+    const int i0 = sl * C;
+    const int jlast = nx - 1 - i0;
+    const int last_sl = RAGGED ? (nx - 1) / C : LPR - 1;
+    const int64_t ncell = (int64_t)nx * ny;
+    const Real* Tin = a.T + (size_t)rho * (size_t)ncell;
+    Real* Tout = a.Tn + (size_t)rho * (size_t)ncell;
+    const uint32_t stream = a.stream0 + (uint32_t)rho;
+    const Real r = a.r, amp2 = a.amp2, half = Real(0.5);
+    const Real s_half = fsqrt_any(amp2) * half;
+    const uint32_t n = a.step;
+
+    auto flux = [&](Real lo, Real hi, Real z) -> Real {
+        if (SPECIES) {
+            const Real c = half * (lo + hi);
+            return fsqrt_any(amp2 * (c > Real(0) ? c : Real(0))) * z;
+        }
+        return (s_half * (lo + hi)) * z;
+    };
+    auto load_row = [&](int y, Real (&v)[C]) {
+        const int yy = (y + ny) % ny;
+        const Real* p = Tin + (size_t)yy * nx;
+#pragma unroll
+        for (int j = 0; j < C; ++j) v[j] = (!RAGGED || i0 + j < nx) ? p[i0 + j] : Real(0);
+    };
+    // low y-face fluxes of row y (between rows y-1 and y)
+    auto yflux = [&](int y, const Real (&lo)[C], const Real (&hi)[C], Real (&g)[C]) {
+        const int yy = (y + ny) % ny;
+        const uint32_t gbase = (uint32_t)(ncell + (int64_t)nx * yy + i0);    // normal index of cell i0
+#pragma unroll
+        for (int q = 0; q < C / 4; ++q) {
+            Real z[4] = {Real(0), Real(0), Real(0), Real(0)};
+            if (a.stochastic) box_muller4(philox4x32_10(make_uint4(gbase / 4u + (uint32_t)q, n, stream, 0u), a.key0, a.key1), z);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) g[4 * q + t] = flux(lo[4 * q + t], hi[4 * q + t], z[t]);
+        }
+    };
+
+    Real prev[C], cur[C], nxt[C], gy_cur[C], gy_nxt[C];
+    load_row(y0 - 1, prev);
+    load_row(y0, cur);
+    yflux(y0, prev, cur, gy_cur);
+    const Real ref = a.ref;
+
+    for (int y = y0; y < y1; ++y) {
+        load_row(y + 1, nxt);
+        yflux(y + 1, cur, nxt, gy_nxt);
+        // x-direction of row y (periodic): neighbours and low x-face fluxes
+        const Real left_nb = __shfl_up_sync(FULL, cur[C - 1], 1, LPR);
+        const Real right_nb = __shfl_down_sync(FULL, cur[0], 1, LPR);
+        Real mine = cur[C - 1];
+        if (RAGGED) {
+#pragma unroll
+            for (int j = 0; j < C; ++j)
+                if (j == jlast) mine = cur[j];
+        }
+        const Real wrap_lo = __shfl_sync(FULL, mine, last_sl, LPR);     // T(nx-1, y)
+        const Real wrap_hi = __shfl_sync(FULL, cur[0], 0, LPR);         // T(0, y)
+        Real gx[C];
+        const uint32_t gxbase = (uint32_t)((int64_t)nx * y + i0);
+#pragma unroll
+        for (int q = 0; q < C / 4; ++q) {
+            Real z[4] = {Real(0), Real(0), Real(0), Real(0)};
+            if (a.stochastic) box_muller4(philox4x32_10(make_uint4(gxbase / 4u + (uint32_t)q, n, stream, 0u), a.key0, a.key1), z);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int j = 4 * q + t;
+                Real lo = (j == 0) ? left_nb : cur[j - 1];
+                if (j == 0 && sl == 0) lo = wrap_lo;
+                gx[j] = flux(lo, cur[j], z[t]);
+            }
+        }
+        const Real g_next = __shfl_down_sync(FULL, gx[0], 1, LPR);
+        const Real g_zero = __shfl_sync(FULL, gx[0], 0, LPR);
+        Real out[C];
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            const int i = i0 + j;
+            Real left = (j == 0) ? left_nb : cur[j - 1];
+            if (j == 0 && sl == 0) left = wrap_lo;
+            Real right = (j == C - 1) ? right_nb : cur[j + 1];
+            Real ghi = (j == C - 1) ? g_next : gx[j + 1];
+            if ((!RAGGED && j == C - 1 && sl == LPR - 1) || (RAGGED && i == nx - 1)) {
+                right = wrap_hi;
+                ghi = g_zero;
+            }
+            const Real c = cur[j];
+            out[j] = c + r * ((left + right) + (prev[j] + nxt[j]) - Real(4) * c) + (ghi - gx[j]) +
+                     (gy_nxt[j] - gy_cur[j]);
+        }
+        if (active) {
+            Real* po = Tout + (size_t)y * nx;
+            bool bad = false;
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                if (!RAGGED || i0 + j < nx) {
+                    po[i0 + j] = out[j];
+                    bad |= !finite_any(out[j]);
+                }
+            }
+            if (bad) atomicOr(a.flags, 1);
+            if (a.sample) {
+                Real* p1 = a.m1 + (size_t)rho * (size_t)ncell + (size_t)y * nx;
+                Real* p2 = a.m2 + (size_t)rho * (size_t)ncell + (size_t)y * nx;
+#pragma unroll
+                for (int j = 0; j < C; ++j) {
+                    if (!RAGGED || i0 + j < nx) {
+                        const Real d = out[j] - ref;
+                        p1[i0 + j] += d;
+                        p2[i0 + j] = fma(d, d, p2[i0 + j]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            prev[j] = cur[j];
+            cur[j] = nxt[j];
+            gy_cur[j] = gy_nxt[j];
+        }
+    }
+}
+
+// FP32 moment partials -> FP64 accumulators, then clear the partials.
+__global__ void k_flush_moments(float* m1, float* m2, double* acc1, double* acc2, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    acc1[i] += (double)m1[i];
+    acc2[i] += (double)m2[i];
+    m1[i] = 0.0f;
+    m2[i] = 0.0f;
+}
+
+cudaError_t launch_flush_moments(Handle& h)
+{
+    if (!h.d_m1) return cudaSuccess;
+    const int64_t n = h.R * h.prob.cells;
+    k_flush_moments<<<(unsigned)((n + 255) / 256), 256, 0, h.stream>>>(h.d_m1, h.d_m2, h.d_acc1, h.d_acc2, n);
+    h.launches += 1;
+    h.partial_samples = 0;
+    return cudaGetLastError();
+}
+
+template <typename Real, int C, int LPR, bool SP>
+static cudaError_t launch2d_layout(const Step2DArgs<Real>& a, cudaStream_t st)
+{
+    constexpr int SPW = 32 / LPR;
+    const int64_t segs = (int64_t)a.R * a.tiles;
+    const int64_t warps = (segs + SPW - 1) / SPW;
+    const dim3 grid((unsigned)((warps + 3) / 4)), block(128);
+    if (a.nx == C * LPR) k_step2d<Real, C, LPR, SP, false><<<grid, block, 0, st>>>(a);
+    else k_step2d<Real, C, LPR, SP, true><<<grid, block, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename Real, bool SP>
+static cudaError_t launch2d_sp(const Step2DArgs<Real>& a, cudaStream_t st)
+{
+    const int nx = a.nx;
+    if (nx <= 16) return launch2d_layout<Real, 4, 4, SP>(a, st);
+    if (nx <= 32) return launch2d_layout<Real, 4, 8, SP>(a, st);
+    if (nx <= 64) return launch2d_layout<Real, 4, 16, SP>(a, st);
+    if (nx <= 128) return launch2d_layout<Real, 4, 32, SP>(a, st);
+    if (nx <= 256) return launch2d_layout<Real, 8, 32, SP>(a, st);
+    return launch2d_layout<Real, 16, 32, SP>(a, st);
+}
+
+template <typename Real>
+static cudaError_t launch2d_real(Handle& h, uint32_t step0, int nsteps)
+{
+    Step2DArgs<Real> a;
+    a.nx = h.prob.n[0];
+    a.ny = h.prob.n[1];
+    a.R = (int)h.R;
+    a.H = std::min(16, a.ny);
+    a.tiles = (a.ny + a.H - 1) / a.H;
+    a.r = (Real)h.prob.r;
+    a.amp2 = (Real)(h.stochastic ? 2.0 * h.prob.r * h.prob.eps : 0.0);
+    a.ref = (Real)h.prob.wall_lo;
+    a.key0 = (uint32_t)(h.prob.seed & 0xffffffffu);
+    a.key1 = (uint32_t)(h.prob.seed >> 32);
+    a.stream0 = h.stream0;
+    a.stochastic = h.stochastic;
+    a.flags = h.d_flags;
+    const bool sp = h.prob.equation == SHE_SPECIES;
+    for (int s = 0; s < nsteps; ++s) {
+        const uint32_t n = step0 + (uint32_t)s;
+        a.T = (const Real*)h.d_state;
+        a.Tn = (Real*)h.d_state2;
+        a.step = n;
+        a.sample = sample_step((int64_t)n + 1, h.K, h.relax) ? 1 : 0;
+        if (sizeof(Real) == 8) {
+            a.m1 = (Real*)h.d_acc1;
+            a.m2 = (Real*)h.d_acc2;
+        } else {
+            a.m1 = (Real*)h.d_m1;
+            a.m2 = (Real*)h.d_m2;
+        }
+        cudaError_t e = sp ? launch2d_sp<Real, true>(a, h.stream) : launch2d_sp<Real, false>(a, h.stream);
+        h.launches += 1;
+        if (e != cudaSuccess) return e;
+        std::swap(h.d_state, h.d_state2);
+        if (a.sample && sizeof(Real) == 4) {
+            if (++h.partial_samples >= 256) {
+                e = launch_flush_moments(h);
+                if (e != cudaSuccess) return e;
+            }
+        }
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_step2d(Handle& h, uint32_t step0, int nsteps)
+{
+    if (h.precision == SHE_FP64) return launch2d_real<double>(h, step0, nsteps);
+    return launch2d_real<float>(h, step0, nsteps);
+}
+
+}  // namespace she

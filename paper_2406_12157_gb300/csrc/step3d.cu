@@ -1,0 +1,278 @@
+// step3d.cu -- forward-Euler step of the 3D stochastic heat / species
+// diffusion equation on a periodic grid, many realizations (Sec. 2,
+// Eq. (2.10)-(2.11): independent white noise per Cartesian direction;
+// Sec. 3, Eq. (3.3) applied per axis).
+//
+// One launch = one step; the state streams through HBM (ping-pong buffers).
+// A CTA owns Y consecutive x-rows (one warp each, lane l holds x-cells
+// [l*C, l*C + C)) of one realization and marches a band of z-planes:
+//   * z-neighbours and the low z-face fluxes stay in registers (rows z-1, z,
+//     z+1 of the warp's own x-row);
+//   * x-neighbours and x-face fluxes cross lanes by shuffles (periodic wrap);
+//   * y-neighbours and y-face fluxes are exchanged through shared memory:
+//     each warp publishes its row of plane z and the flux of its low y-face;
+//     the two halo rows (y0-1, y0+Y) are read from memory and the top y-face
+//     of the tile is computed by the last warp.
+// Every face flux comes from its own Philox slot (normal g = axis * Ncells +
+// x + nx * (y + ny * z)), so faces on tile edges computed by two CTAs agree.
+// Per cell-update: 4 bytes read + 4 bytes written (+ (Y+2)/Y and (H+2)/H
+// halo factors), three normals, no noise array.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "philox.cuh"
+#include "row1d.cuh"
+#include "she_internal.cuh"
+
+namespace she {
+
+constexpr int kY3 = 8;          // x-rows (warps) per CTA
+constexpr int kH3 = 32;         // z-planes per band
+
+template <typename Real, int C, bool SPECIES>
+__global__ void __launch_bounds__(kY3 * 32)
+k_step3d(const Step3DArgs<Real> a)
+{
+    static_assert(C % 4 == 0, "cells per lane must be a multiple of 4");
+    constexpr unsigned FULL = 0xffffffffu;
+    // smem: 2 stages x [(Y + 2) rows of T + (Y + 1) rows of y-face flux] x nx
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Real* sm = reinterpret_cast<Real*>(smem_raw);
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int stage_elems = (2 * kY3 + 3) * nx;
+
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    const int ytiles = (ny + kY3 - 1) / kY3;
+    const int zbands = (nz + kH3 - 1) / kH3;
+    int b = blockIdx.x;
+    const int zb = b % zbands;
+    b /= zbands;
+    const int yt = b % ytiles;
+    const int rho = b / ytiles;
+    const int y0 = yt * kY3;
+    const int y = y0 + w;
+    const bool row_active = y < ny;          // warps past the grid edge only help with halos
+    const int yc = row_active ? y : ny - 1;
+    const int z0 = zb * kH3, z1 = min(z0 + kH3, nz);
+    const int i0 = lane * C;
+    const int64_t ncell = (int64_t)nx * ny * nz;
+    const Real* Tin = a.T + (size_t)rho * (size_t)ncell;
+    Real* Tout = a.Tn + (size_t)rho * (size_t)ncell;
+    const uint32_t stream = a.stream0 + (uint32_t)rho;
+    const Real r = a.r, amp2 = a.amp2, half = Real(0.5);
+    const Real s_half = fsqrt_any(amp2) * half;
+    const uint32_t n = a.step;
+    const int yl = (y0 - 1 + ny) % ny;                 // halo rows
+    const int yh = min(y0 + kY3, ny) % ny;
+    const int nrows = min(kY3, ny - y0);               // rows of this tile
+
+    auto flux = [&](Real lo, Real hi, Real z) -> Real {
+        if (SPECIES) {
+            const Real c = half * (lo + hi);
+            return fsqrt_any(amp2 * (c > Real(0) ? c : Real(0))) * z;
+        }
+        return (s_half * (lo + hi)) * z;
+    };
+    auto row_ptr = [&](int yy, int zz) -> const Real* {
+        return Tin + ((size_t)((zz + nz) % nz) * ny + (size_t)yy) * nx;
+    };
+    auto load_row = [&](int yy, int zz, Real (&v)[C]) {
+        const Real* p = row_ptr(yy, zz) + i0;
+#pragma unroll
+        for (int j = 0; j < C; ++j) v[j] = p[j];
+    };
+    // fluxes of C faces from two rows of values, noise block base g0 (multiple of 4)
+    auto face_row = [&](const Real (&lo)[C], const Real (&hi)[C], uint32_t g0, Real (&g)[C]) {
+#pragma unroll
+        for (int q = 0; q < C / 4; ++q) {
+            Real z[4] = {Real(0), Real(0), Real(0), Real(0)};
+            if (a.stochastic) box_muller4(philox4x32_10(make_uint4(g0 / 4u + (uint32_t)q, n, stream, 0u), a.key0, a.key1), z);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) g[4 * q + t] = flux(lo[4 * q + t], hi[4 * q + t], z[t]);
+        }
+    };
+    auto lin = [&](int yy, int zz) -> uint32_t {
+        return (uint32_t)((((int64_t)((zz + nz) % nz) * ny + yy) * nx) + i0);
+    };
+
+    Real prev[C], cur[C], nxt[C], gz_cur[C], gz_nxt[C];
+    load_row(yc, z0 - 1, prev);
+    load_row(yc, z0, cur);
+    face_row(prev, cur, (uint32_t)(2 * ncell) + lin(yc, z0), gz_cur);
+
+    for (int z = z0; z < z1; ++z) {
+        Real* st = sm + (size_t)(z & 1) * stage_elems;
+        Real* srow = st;                                  // rows 0..Y+1: y0-1 .. y0+Y
+        Real* sgy = st + (kY3 + 2) * nx;                  // rows 0..Y: low y-faces of y0 .. y0+Y
+        load_row(yc, z + 1, nxt);
+        face_row(cur, nxt, (uint32_t)(2 * ncell) + lin(yc, z + 1), gz_nxt);
+        // publish this warp's row of plane z; warps 0 and 1 fetch the halo rows
+        if (row_active) {
+#pragma unroll
+            for (int j = 0; j < C; ++j) srow[(size_t)(w + 1) * nx + i0 + j] = cur[j];
+        }
+        if (w == 0 || w == 1) {
+            Real hv[C];
+            load_row(w == 0 ? yl : yh, z, hv);
+            Real* dst = srow + (size_t)(w == 0 ? 0 : nrows + 1) * nx;
+#pragma unroll
+            for (int j = 0; j < C; ++j) dst[i0 + j] = hv[j];
+        }
+        __syncthreads();
+        // low y-face of this row (between y-1 and y); warp 0 also does the
+        // top face of the tile (between the last row and the high halo)
+        {
+            Real lo[C], g[C];
+#pragma unroll
+            for (int j = 0; j < C; ++j) lo[j] = srow[(size_t)w * nx + i0 + j];
+            if (row_active) {
+                face_row(lo, cur, (uint32_t)ncell + lin(y, z), g);
+#pragma unroll
+                for (int j = 0; j < C; ++j) sgy[(size_t)w * nx + i0 + j] = g[j];
+            }
+            if (w == 0) {
+                Real lo2[C], hi2[C];
+#pragma unroll
+                for (int j = 0; j < C; ++j) {
+                    lo2[j] = srow[(size_t)nrows * nx + i0 + j];
+                    hi2[j] = srow[(size_t)(nrows + 1) * nx + i0 + j];
+                }
+                face_row(lo2, hi2, (uint32_t)ncell + lin(yh, z), g);
+#pragma unroll
+                for (int j = 0; j < C; ++j) sgy[(size_t)nrows * nx + i0 + j] = g[j];
+            }
+        }
+        __syncthreads();
+        if (row_active) {
+            // x-direction (periodic, the warp holds the whole row)
+            const Real left_nb = __shfl_up_sync(FULL, cur[C - 1], 1);
+            const Real right_nb = __shfl_down_sync(FULL, cur[0], 1);
+            const Real wrap_lo = __shfl_sync(FULL, cur[C - 1], 31);
+            const Real wrap_hi = __shfl_sync(FULL, cur[0], 0);
+            Real gx[C];
+            {
+                Real lo[C];
+#pragma unroll
+                for (int j = 0; j < C; ++j) lo[j] = (j == 0) ? (lane == 0 ? wrap_lo : left_nb) : cur[j - 1];
+                face_row(lo, cur, lin(y, z), gx);
+            }
+            const Real g_next = __shfl_down_sync(FULL, gx[0], 1);
+            const Real g_zero = __shfl_sync(FULL, gx[0], 0);
+            Real out[C];
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                Real left = (j == 0) ? (lane == 0 ? wrap_lo : left_nb) : cur[j - 1];
+                Real right = (j == C - 1) ? (lane == 31 ? wrap_hi : right_nb) : cur[j + 1];
+                Real ghi = (j == C - 1) ? (lane == 31 ? g_zero : g_next) : gx[j + 1];
+                const Real down = srow[(size_t)w * nx + i0 + j];
+                const Real up = srow[(size_t)(w + 2) * nx + i0 + j];
+                const Real gyl = sgy[(size_t)w * nx + i0 + j];
+                const Real gyh = sgy[(size_t)(w + 1) * nx + i0 + j];
+                const Real c = cur[j];
+                out[j] = c + r * ((left + right) + (down + up) + (prev[j] + nxt[j]) - Real(6) * c) +
+                         (ghi - gx[j]) + (gyh - gyl) + (gz_nxt[j] - gz_cur[j]);
+            }
+            Real* po = Tout + ((size_t)z * ny + y) * nx + i0;
+            bool bad = false;
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                po[j] = out[j];
+                bad |= !finite_any(out[j]);
+            }
+            if (bad) atomicOr(a.flags, 1);
+            if (a.sample) {
+                const size_t off = (size_t)rho * (size_t)ncell + ((size_t)z * ny + y) * nx + i0;
+#pragma unroll
+                for (int j = 0; j < C; ++j) {
+                    const Real d = out[j] - a.ref;
+                    a.m1[off + j] += d;
+                    a.m2[off + j] = fma(d, d, a.m2[off + j]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            prev[j] = cur[j];
+            cur[j] = nxt[j];
+            gz_cur[j] = gz_nxt[j];
+        }
+    }
+}
+
+template <typename Real, int C, bool SP>
+static cudaError_t launch3d_layout(const Step3DArgs<Real>& a, cudaStream_t st)
+{
+    const int ytiles = (a.ny + kY3 - 1) / kY3, zbands = (a.nz + kH3 - 1) / kH3;
+    const int64_t blocks = (int64_t)a.R * ytiles * zbands;
+    const int smem = 2 * (2 * kY3 + 3) * a.nx * (int)sizeof(Real);
+    auto k = k_step3d<Real, C, SP>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k<<<(unsigned)blocks, kY3 * 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename Real, bool SP>
+static cudaError_t launch3d_sp(const Step3DArgs<Real>& a, cudaStream_t st)
+{
+    switch (a.nx) {
+    case 128: return launch3d_layout<Real, 4, SP>(a, st);
+    case 256: return launch3d_layout<Real, 8, SP>(a, st);
+    case 512: return launch3d_layout<Real, 16, SP>(a, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename Real>
+static cudaError_t launch3d_real(Handle& h, uint32_t step0, int nsteps)
+{
+    Step3DArgs<Real> a;
+    a.nx = h.prob.n[0];
+    a.ny = h.prob.n[1];
+    a.nz = h.prob.n[2];
+    a.R = (int)h.R;
+    a.r = (Real)h.prob.r;
+    a.amp2 = (Real)(h.stochastic ? 2.0 * h.prob.r * h.prob.eps : 0.0);
+    a.ref = (Real)h.prob.wall_lo;
+    a.key0 = (uint32_t)(h.prob.seed & 0xffffffffu);
+    a.key1 = (uint32_t)(h.prob.seed >> 32);
+    a.stream0 = h.stream0;
+    a.stochastic = h.stochastic;
+    a.flags = h.d_flags;
+    const bool sp = h.prob.equation == SHE_SPECIES;
+    for (int s = 0; s < nsteps; ++s) {
+        const uint32_t n = step0 + (uint32_t)s;
+        a.T = (const Real*)h.d_state;
+        a.Tn = (Real*)h.d_state2;
+        a.step = n;
+        a.sample = sample_step((int64_t)n + 1, h.K, h.relax) ? 1 : 0;
+        if (sizeof(Real) == 8) {
+            a.m1 = (Real*)h.d_acc1;
+            a.m2 = (Real*)h.d_acc2;
+        } else {
+            a.m1 = (Real*)h.d_m1;
+            a.m2 = (Real*)h.d_m2;
+        }
+        cudaError_t e = sp ? launch3d_sp<Real, true>(a, h.stream) : launch3d_sp<Real, false>(a, h.stream);
+        h.launches += 1;
+        if (e != cudaSuccess) return e;
+        std::swap(h.d_state, h.d_state2);
+        if (a.sample && sizeof(Real) == 4) {
+            if (++h.partial_samples >= 256) {
+                e = launch_flush_moments(h);
+                if (e != cudaSuccess) return e;
+            }
+        }
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_step3d(Handle& h, uint32_t step0, int nsteps)
+{
+    if (h.precision == SHE_FP64) return launch3d_real<double>(h, step0, nsteps);
+    return launch3d_real<float>(h, step0, nsteps);
+}
+
+}  // namespace she
