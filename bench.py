@@ -98,18 +98,46 @@ class ClockSampler:
 
 # --------------------------------------------------------------- workloads --
 
+# Per workload: problem, description, default time steps per bench step, the
+# dominant kernel, and its algorithmic work per cell-update counted from the
+# source algorithm: lane-ops (Philox 25 and Box-Muller 5.5 per normal; face
+# flux 4 heat / 7 species per face; update 6 (1D) / 9 (2D) / 11 (3D)) and
+# HBM bytes (state read + write, 8 B, plus the FP32 moment read-modify-write,
+# 16 B per sample, on the streaming 2D/3D paths; the 1D path keeps its rows
+# on chip for a whole launch).
+WORKLOADS = {
+    "gradient_rod": dict(
+        make=lambda W: W.gradient_rod(),
+        desc=("1D SHE rod, 256 cells, Dirichlet walls T_L=1 T_R=2, eps=1e-3, r=0.2, 4096 "
+              "realizations, FP32 state, moments and full 256x256 equal-time covariance "
+              "(tcgen05) every 10 steps after 1e5 steps"),
+        chunk=10_000, ops=25.0 + 5.5 + 4.0 + 6.0, bytes=None,
+        kernel="k_step1d_cov<32,8,dirichlet,heat>"),
+    "species_2d": dict(
+        make=lambda W: W.species_2d(want_sk=0),
+        desc=("2D stochastic species diffusion, 256x256 periodic, D=1, r=0.1, eps_c=1e-3, c=1 + "
+              "zero-sum perturbation, 256 realizations, FP32, moments every 10 steps after 1e4"),
+        chunk=1000, ops=2 * (25.0 + 5.5 + 7.0) + 9.0, bytes=8.0 + 16.0 / 10,
+        kernel="k_step2d<float,8,32,species>"),
+    "cube_3d": dict(
+        make=lambda W: W.cube_3d(want_sk=0),
+        desc=("3D SHE 256^3 periodic, T0=1, r=0.1, eps=1e-3, 8 realizations, FP32, HBM-streaming "
+              "stencil, moments every 10 steps"),
+        chunk=100, ops=3 * (25.0 + 5.5 + 4.0) + 11.0, bytes=8.0 + 16.0 / 10,
+        kernel="k_step3d<float,8,heat>"),
+    "oracle_rod": dict(
+        make=lambda W: W.oracle_rod(want_cov=0, want_sk=0),
+        desc="1D SHE rod, 32 cells, walls 1, 16 realizations, FP64",
+        chunk=10_000, ops=25.0 + 5.5 + 4.0 + 6.0, bytes=None, kernel="k_step1d<double,4,8>"),
+}
+
+
 def workload(name):
     import she_workloads as W
-    if name == "gradient_rod":
-        p = W.gradient_rod()
-        desc = ("1D SHE rod, 256 cells, Dirichlet walls T_L=1 T_R=2, eps=1e-3, r=0.2, 4096 "
-                "realizations, FP32 state, moments and full 256x256 equal-time covariance "
-                "(tcgen05) every 10 steps after 1e5 steps")
-        return p, desc
-    if name == "oracle_rod":
-        p = W.oracle_rod(want_cov=0, want_sk=0)
-        return p, "1D SHE rod, 32 cells, walls 1, 16 realizations, FP64"
-    raise SystemExit("unknown workload %s" % name)
+    if name not in WORKLOADS:
+        raise SystemExit("unknown workload %s" % name)
+    w = WORKLOADS[name]
+    return w["make"](W), w["desc"]
 
 
 def _cells(p):
@@ -128,15 +156,18 @@ def oracle_sample_rate(p, seconds_hint=10.0):
     from oracle import she as O
     q = dict(p)
     q["relax_steps"] = 0
-    steps = 10_000
-    R_s = max(16, min(p["realizations"], int(2.6e9 // (steps * _cells(p)))))
+    cells = _cells(p)
+    R_s = min(p["realizations"], 1024 if cells <= 4096 else 16)
+    steps = int(max(10, min(10_000, 2.6e9 // (R_s * cells))))
+    q["want_sk"] = 0 if p["dim"] > 1 else q.get("want_sk", 0)
     O.lib()
     t0 = time.perf_counter()
     O.run(q, R_s, steps)
     dt = time.perf_counter() - t0
     rate = R_s * steps * _cells(p) / dt
-    sample = ("%d realizations x %d steps of the workload (sampling phase, every %d steps), FP64 "
-              "oracle, %.1f s" % (R_s, steps, p["stats_interval"], dt))
+    sample = ("%d realizations x %d steps of the workload (sampling phase, every %d steps%s), "
+              "FP64 oracle, %.1f s" % (R_s, steps, p["stats_interval"],
+                                       ", covariance" if q.get("want_cov") else "", dt))
     return rate, O.num_threads(), sample
 
 
@@ -165,7 +196,8 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     # weak scaling: every rank runs a full ensemble on its own noise streams
     sim = she.Simulation(p, stream=stream, stream_offset=rank * R)
-    chunk = args.chunk
+    wl = WORKLOADS[args.workload]
+    chunk = args.chunk if args.chunk else wl["chunk"]
     cu_per_step = R * cells * chunk
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -212,7 +244,11 @@ def run_ours(args):
 
     # ---- FP64 plain form on the same workload, a bounded number of steps ----
     plain_steps = max(10, min(2000, int(2e8 // (R * cells))))
-    sim64 = she.Simulation(p, stream=stream, precision="fp64", kernel="plain", stream_offset=rank * R,
+    p64 = dict(p)
+    # 1D: the plain three-launches-per-step FP64 form; 2D/3D (streaming
+    # kernels already launch once per step): the same kernel in FP64
+    kind64 = "plain" if p["dim"] == 1 else "auto"
+    sim64 = she.Simulation(p64, stream=stream, precision="fp64", kernel=kind64, stream_offset=rank * R,
                            want_cov=0, want_sk=0)
     sim64.step(min(plain_steps, 50))
     torch.cuda.synchronize()
@@ -223,7 +259,7 @@ def run_ours(args):
     with torch.cuda.stream(stream):
         e1.record(stream)
     torch.cuda.synchronize()
-    plain_rate = R * cells * plain_steps / (e0.elapsed_time(e1) / 1e3)
+    plain_rate = (p64["realizations"] * _cells(p64)) * plain_steps / (e0.elapsed_time(e1) / 1e3)
     sim64.close()
 
     # ---- e2e through the C ABI with host buffers ----
@@ -261,16 +297,20 @@ def run_ours(args):
             dist.destroy_process_group()
         return
     peaks, peak_src = _peaks()
-    per_launch_ms = ms / max(1, launches) if world == 1 else (ms / max(1, launches))
     cu_per_launch = cu_per_step * args.steps / max(1, launches)
-    ops_per_launch = cu_per_launch * OPS_PER_CELL_UPDATE_1D
+    per_launch_ms = ms / max(1, launches)
+    ops_per_launch = cu_per_launch * wl["ops"]
     achieved = ops_per_launch / (per_launch_ms / 1e3) / 1e12          # Tops/s (lane-ops)
     peak = 128 * 152 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
             "unit": "Tops/s", "frac": round(achieved / peak, 4), "traffic": None,
-            "kernel": "k_step1d_cov<32,8,dirichlet,heat>" if p.get("want_cov") else "k_step1d<float,32,8,dirichlet,heat>",
-            "ops_per_cell_update": OPS_PER_CELL_UPDATE_1D,
+            "kernel": wl["kernel"], "ops_per_cell_update": wl["ops"],
             "peak_source": "128 lane-ops/clk/SM x 152 SMs x max SM clock (%s)" % peak_src}
+    if wl["bytes"]:
+        gbs = cu_per_launch * wl["bytes"] / (per_launch_ms / 1e3) / 1e9
+        roof["hbm"] = {"achieved": round(gbs, 1), "peak": peaks.get("hbm_gbs", 6800.0),
+                       "unit": "GB/s", "frac": round(gbs / peaks.get("hbm_gbs", 6800.0), 4),
+                       "bytes_per_cell_update": wl["bytes"]}
     cpu = None
     if not args.no_cpu_baseline and world >= 1:
         rate, cores, sample = oracle_sample_rate(p)
@@ -287,6 +327,7 @@ def run_ours(args):
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clk,
         "fp64_plain": {"value": plain_rate, "unit": UNIT, "steps": plain_steps,
+                       "form": "plain FP64 (3 launches/step)" if kind64 == "plain" else "same kernel in FP64",
                        "speedup_fp32_batched": value / world / plain_rate},
         "wall_s": t_wall,
     }
@@ -339,7 +380,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="gradient_rod")
-    ap.add_argument("--chunk", type=int, default=10_000)
+    ap.add_argument("--chunk", type=int, default=0,
+                    help="time steps per bench step (default: per workload)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--relax", type=int, default=None,

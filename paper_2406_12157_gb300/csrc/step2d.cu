@@ -24,8 +24,10 @@
 
 namespace she {
 
+// 7 resident blocks of 4 warps per SM for the FP32 8-cell layout: the
+// 256 x 256 x 256 ensemble (4096 bands of 16 rows) fits in one wave
 template <typename Real, int C, int LPR, bool SPECIES, bool RAGGED>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, (sizeof(Real) == 4 && C <= 8) ? 7 : 1)
 k_step2d(const Step2DArgs<Real> a)
 {
     static_assert(C % 4 == 0, "cells per lane must be a multiple of 4");
@@ -81,14 +83,15 @@ k_step2d(const Step2DArgs<Real> a)
         }
     };
 
-    Real prev[C], cur[C], nxt[C], gy_cur[C], gy_nxt[C];
+    Real prev[C], cur[C], nxt[C], nn[C], gy_cur[C], gy_nxt[C];
     load_row(y0 - 1, prev);
     load_row(y0, cur);
+    load_row(y0 + 1, nxt);
     yflux(y0, prev, cur, gy_cur);
     const Real ref = a.ref;
 
     for (int y = y0; y < y1; ++y) {
-        load_row(y + 1, nxt);
+        load_row(y + 2, nn);                          // prefetch, used next row
         yflux(y + 1, cur, nxt, gy_nxt);
         // x-direction of row y (periodic): neighbours and low x-face fluxes
         const Real left_nb = __shfl_up_sync(FULL, cur[C - 1], 1, LPR);
@@ -161,6 +164,7 @@ k_step2d(const Step2DArgs<Real> a)
         for (int j = 0; j < C; ++j) {
             prev[j] = cur[j];
             cur[j] = nxt[j];
+            nxt[j] = nn[j];
             gy_cur[j] = gy_nxt[j];
         }
     }

@@ -31,8 +31,41 @@ namespace she {
 constexpr int kY3 = 8;          // x-rows (warps) per CTA
 constexpr int kH3 = 32;         // z-planes per band
 
+// 16-byte moves of C consecutive values (C % 4 == 0, 16-byte aligned)
+template <int C>
+__device__ __forceinline__ void vload(const float* p, float (&v)[C])
+{
+#pragma unroll
+    for (int k = 0; k < C / 4; ++k) {
+        const float4 f = reinterpret_cast<const float4*>(p)[k];
+        v[4 * k] = f.x; v[4 * k + 1] = f.y; v[4 * k + 2] = f.z; v[4 * k + 3] = f.w;
+    }
+}
+template <int C>
+__device__ __forceinline__ void vstore(float* p, const float (&v)[C])
+{
+#pragma unroll
+    for (int k = 0; k < C / 4; ++k)
+        reinterpret_cast<float4*>(p)[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+}
+template <int C>
+__device__ __forceinline__ void vload(const double* p, double (&v)[C])
+{
+#pragma unroll
+    for (int k = 0; k < C / 2; ++k) {
+        const double2 f = reinterpret_cast<const double2*>(p)[k];
+        v[2 * k] = f.x; v[2 * k + 1] = f.y;
+    }
+}
+template <int C>
+__device__ __forceinline__ void vstore(double* p, const double (&v)[C])
+{
+#pragma unroll
+    for (int k = 0; k < C / 2; ++k) reinterpret_cast<double2*>(p)[k] = make_double2(v[2 * k], v[2 * k + 1]);
+}
+
 template <typename Real, int C, bool SPECIES>
-__global__ void __launch_bounds__(kY3 * 32)
+__global__ void __launch_bounds__(kY3 * 32, sizeof(Real) == 4 ? 3 : 1)
 k_step3d(const Step3DArgs<Real> a)
 {
     static_assert(C % 4 == 0, "cells per lane must be a multiple of 4");
@@ -79,11 +112,7 @@ k_step3d(const Step3DArgs<Real> a)
     auto row_ptr = [&](int yy, int zz) -> const Real* {
         return Tin + ((size_t)((zz + nz) % nz) * ny + (size_t)yy) * nx;
     };
-    auto load_row = [&](int yy, int zz, Real (&v)[C]) {
-        const Real* p = row_ptr(yy, zz) + i0;
-#pragma unroll
-        for (int j = 0; j < C; ++j) v[j] = p[j];
-    };
+    auto load_row = [&](int yy, int zz, Real (&v)[C]) { vload<C>(row_ptr(yy, zz) + i0, v); };
     // fluxes of C faces from two rows of values, noise block base g0 (multiple of 4)
     auto face_row = [&](const Real (&lo)[C], const Real (&hi)[C], uint32_t g0, Real (&g)[C]) {
 #pragma unroll
@@ -110,39 +139,28 @@ k_step3d(const Step3DArgs<Real> a)
         load_row(yc, z + 1, nxt);
         face_row(cur, nxt, (uint32_t)(2 * ncell) + lin(yc, z + 1), gz_nxt);
         // publish this warp's row of plane z; warps 0 and 1 fetch the halo rows
-        if (row_active) {
-#pragma unroll
-            for (int j = 0; j < C; ++j) srow[(size_t)(w + 1) * nx + i0 + j] = cur[j];
-        }
+        if (row_active) vstore<C>(srow + (size_t)(w + 1) * nx + i0, cur);
         if (w == 0 || w == 1) {
             Real hv[C];
             load_row(w == 0 ? yl : yh, z, hv);
-            Real* dst = srow + (size_t)(w == 0 ? 0 : nrows + 1) * nx;
-#pragma unroll
-            for (int j = 0; j < C; ++j) dst[i0 + j] = hv[j];
+            vstore<C>(srow + (size_t)(w == 0 ? 0 : nrows + 1) * nx + i0, hv);
         }
         __syncthreads();
         // low y-face of this row (between y-1 and y); warp 0 also does the
         // top face of the tile (between the last row and the high halo)
         {
             Real lo[C], g[C];
-#pragma unroll
-            for (int j = 0; j < C; ++j) lo[j] = srow[(size_t)w * nx + i0 + j];
+            vload<C>(srow + (size_t)w * nx + i0, lo);
             if (row_active) {
                 face_row(lo, cur, (uint32_t)ncell + lin(y, z), g);
-#pragma unroll
-                for (int j = 0; j < C; ++j) sgy[(size_t)w * nx + i0 + j] = g[j];
+                vstore<C>(sgy + (size_t)w * nx + i0, g);
             }
             if (w == 0) {
                 Real lo2[C], hi2[C];
-#pragma unroll
-                for (int j = 0; j < C; ++j) {
-                    lo2[j] = srow[(size_t)nrows * nx + i0 + j];
-                    hi2[j] = srow[(size_t)(nrows + 1) * nx + i0 + j];
-                }
+                vload<C>(srow + (size_t)nrows * nx + i0, lo2);
+                vload<C>(srow + (size_t)(nrows + 1) * nx + i0, hi2);
                 face_row(lo2, hi2, (uint32_t)ncell + lin(yh, z), g);
-#pragma unroll
-                for (int j = 0; j < C; ++j) sgy[(size_t)nrows * nx + i0 + j] = g[j];
+                vstore<C>(sgy + (size_t)nrows * nx + i0, g);
             }
         }
         __syncthreads();
@@ -161,36 +179,39 @@ k_step3d(const Step3DArgs<Real> a)
             }
             const Real g_next = __shfl_down_sync(FULL, gx[0], 1);
             const Real g_zero = __shfl_sync(FULL, gx[0], 0);
-            Real out[C];
+            Real out[C], down[C], up[C], gyl[C], gyh[C];
+            vload<C>(srow + (size_t)w * nx + i0, down);
+            vload<C>(srow + (size_t)(w + 2) * nx + i0, up);
+            vload<C>(sgy + (size_t)w * nx + i0, gyl);
+            vload<C>(sgy + (size_t)(w + 1) * nx + i0, gyh);
 #pragma unroll
             for (int j = 0; j < C; ++j) {
                 Real left = (j == 0) ? (lane == 0 ? wrap_lo : left_nb) : cur[j - 1];
                 Real right = (j == C - 1) ? (lane == 31 ? wrap_hi : right_nb) : cur[j + 1];
                 Real ghi = (j == C - 1) ? (lane == 31 ? g_zero : g_next) : gx[j + 1];
-                const Real down = srow[(size_t)w * nx + i0 + j];
-                const Real up = srow[(size_t)(w + 2) * nx + i0 + j];
-                const Real gyl = sgy[(size_t)w * nx + i0 + j];
-                const Real gyh = sgy[(size_t)(w + 1) * nx + i0 + j];
                 const Real c = cur[j];
-                out[j] = c + r * ((left + right) + (down + up) + (prev[j] + nxt[j]) - Real(6) * c) +
-                         (ghi - gx[j]) + (gyh - gyl) + (gz_nxt[j] - gz_cur[j]);
+                out[j] = c + r * ((left + right) + (down[j] + up[j]) + (prev[j] + nxt[j]) - Real(6) * c) +
+                         (ghi - gx[j]) + (gyh[j] - gyl[j]) + (gz_nxt[j] - gz_cur[j]);
             }
             Real* po = Tout + ((size_t)z * ny + y) * nx + i0;
+            vstore<C>(po, out);
             bool bad = false;
 #pragma unroll
-            for (int j = 0; j < C; ++j) {
-                po[j] = out[j];
-                bad |= !finite_any(out[j]);
-            }
+            for (int j = 0; j < C; ++j) bad |= !finite_any(out[j]);
             if (bad) atomicOr(a.flags, 1);
             if (a.sample) {
                 const size_t off = (size_t)rho * (size_t)ncell + ((size_t)z * ny + y) * nx + i0;
+                Real s1[C], s2[C];
+                vload<C>(a.m1 + off, s1);
+                vload<C>(a.m2 + off, s2);
 #pragma unroll
                 for (int j = 0; j < C; ++j) {
                     const Real d = out[j] - a.ref;
-                    a.m1[off + j] += d;
-                    a.m2[off + j] = fma(d, d, a.m2[off + j]);
+                    s1[j] += d;
+                    s2[j] = fma(d, d, s2[j]);
                 }
+                vstore<C>(a.m1 + off, s1);
+                vstore<C>(a.m2 + off, s2);
             }
         }
 #pragma unroll
