@@ -127,6 +127,9 @@ void release(Handle* h)
     cudaFree(h->d_m1);
     cudaFree(h->d_m2);
     h->d_m1 = h->d_m2 = nullptr;
+    cudaFree(h->d_axes_partial);
+    cudaFree(h->d_axes_red);
+    h->d_axes_partial = h->d_axes_red = nullptr;
     h->d_cov_partial = h->d_cov_red = nullptr;
     h->d_state = h->d_state2 = nullptr;
     h->d_acc1 = h->d_acc2 = h->d_face = h->d_red = nullptr;
@@ -195,7 +198,13 @@ she_status she_init(const she_params* p, she_handle** out)
     if (st == SHE_OK && (p->want_sk & SHE_SK_AXES) && p->dim == 1) {
         st = SHE_ERR_INVALID_ARG; msg = "she: SHE_SK_AXES is for 2D/3D grids (use SHE_SK_FULL in 1D)";
     }
-    if (st == SHE_OK && p->want_sk && p->dim > 1) { st = SHE_ERR_UNSUPPORTED; msg = "she: S(k) not built yet"; }
+    if (st == SHE_OK && (p->want_sk & SHE_SK_FULL) && p->dim > 1) {
+        st = SHE_ERR_UNSUPPORTED; msg = "she: the full multi-dimensional S(k) is not built; use SHE_SK_AXES";
+    }
+    if (st == SHE_OK && (p->want_sk & SHE_SK_AXES) &&
+        (p->precision != SHE_FP32 || p->n[0] > 256 || p->n[1] > 256 || (p->dim == 3 && p->n[2] > 256))) {
+        st = SHE_ERR_UNSUPPORTED; msg = "she: per-axis S(k) runs on the FP32 path with at most 256 cells per axis";
+    }
     if (st == SHE_OK && p->dim == 3 && !(p->n[0] == 128 || p->n[0] == 256 || p->n[0] == 512)) {
         st = SHE_ERR_UNSUPPORTED; msg = "she: 3D grids need nx = 128, 256 or 512";
     }
@@ -249,6 +258,17 @@ she_status she_init(const she_params* p, she_handle** out)
     if (e == cudaSuccess && h->kernel == SHE_KERNEL_PLAIN) {
         e = cudaMalloc(&h->d_state2, nstate * elem);
         if (e == cudaSuccess) e = cudaMalloc(&h->d_face, (size_t)h->R * (cells + 1) * sizeof(double));
+    }
+    if (e == cudaSuccess && (h->want_sk & SHE_SK_AXES)) {
+        int dev = 0, sms = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        h->cov_ctas = sms > 0 ? sms : 1;
+        const size_t per = (size_t)h->prob.dim * 65536;
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_axes_partial, per * (size_t)h->cov_ctas * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_axes_red, per * sizeof(double));
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(h->d_axes_partial, 0, per * (size_t)h->cov_ctas * sizeof(double), h->stream);
     }
     if (e == cudaSuccess && h->want_cov) {
         int dev = 0, sms = 0;
@@ -390,6 +410,34 @@ she_status she_stats(she_handle* hh, she_stats_out* out)
                                       : std::numeric_limits<double>::quiet_NaN();
         }
     }
+    if (out->sk_axes) {
+        // S_a(k) = sum_{j,l} G_a[j][l] cos(2 pi (j - l) k / n_a) / (lines_a n)
+        e = she::launch_reduce_axes(*h, h->d_axes_red);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        std::vector<double> Gs((size_t)h->prob.dim * 65536);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(Gs.data(), h->d_axes_red, Gs.size() * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(sk_axes)");
+        const double two_pi = 6.283185307179586476925286766559;
+        int off = 0;
+        for (int ax = 0; ax < h->prob.dim; ++ax) {
+            const int na = h->prob.n[ax];
+            const double lines = (double)(cells / na);
+            const double* Gm = Gs.data() + (size_t)ax * 65536;
+            std::vector<double> diag_sum((size_t)na, 0.0);   // sum over j of G[j][(j + d) mod n]
+            for (int j = 0; j < na; ++j)
+                for (int l = 0; l < na; ++l)
+                    diag_sum[(size_t)(((l - j) % na + na) % na)] +=
+                        0.5 * (Gm[(size_t)j * na + l] + Gm[(size_t)l * na + j]);
+            for (int k = 0; k < na; ++k) {
+                double acc = 0.0;
+                for (int d = 0; d < na; ++d)
+                    acc += diag_sum[(size_t)d] * std::cos(two_pi * (double)(((long long)d * k) % na) / (double)na);
+                out->sk_axes[off + k] = acc / (lines * n);
+            }
+            off += na;
+        }
+    }
     if (h->want_cov && (out->cov || out->sk || out->sk_fluct)) {
         const int64_t N = cells;
         e = she::launch_reduce_cov(*h, h->d_cov_red);
@@ -446,6 +494,9 @@ she_status she_reset_stats(she_handle* hh)
     if (e == cudaSuccess && h->d_m1) e = cudaMemsetAsync(h->d_m1, 0, nstate * sizeof(float), h->stream);
     if (e == cudaSuccess && h->d_m2) e = cudaMemsetAsync(h->d_m2, 0, nstate * sizeof(float), h->stream);
     h->partial_samples = 0;
+    if (e == cudaSuccess && h->d_axes_partial)
+        e = cudaMemsetAsync(h->d_axes_partial, 0,
+                            (size_t)h->prob.dim * 65536 * (size_t)h->cov_ctas * sizeof(double), h->stream);
     if (e == cudaSuccess && h->d_cov_partial)
         e = cudaMemsetAsync(h->d_cov_partial, 0,
                             (size_t)h->cov_ctas * (size_t)h->prob.cells * (size_t)h->prob.cells * sizeof(double),

@@ -78,6 +78,15 @@ struct Step3DArgs {
     int sample;
 };
 
+// Arguments of the per-axis line-covariance kernel (S(k) along each axis).
+struct AxesArgs {
+    const float* T;       // [R][nz][ny][nx] state after the sampling step
+    double* partial;      // [naxes][G][256*256] per-CTA FP64 partial line covariances
+    int* flags;
+    int nx, ny, nz, naxes, R;
+    float ref;
+};
+
 // Extra arguments of the fused covariance kernel.
 struct CovArgs {
     double* partial;      // [G][N][N] per-CTA FP64 partial sums of delta delta^T
@@ -115,6 +124,8 @@ struct Handle {
     double* d_cov_partial = nullptr;  // [cov_ctas][N][N] FP64 partial covariance sums
     double* d_cov_red = nullptr;   // [N][N] reduced
     int cov_ctas = 0;              // CTAs (one per SM) of the fused covariance kernel
+    double* d_axes_partial = nullptr;  // [dim][cov_ctas][256*256] per-axis line covariances
+    double* d_axes_red = nullptr;      // [dim][256*256] reduced
     size_t red_bytes = 0;
     std::string err;
 };
@@ -130,6 +141,8 @@ cudaError_t launch_reduce_cov(const Handle& h, double* d_out);
 cudaError_t launch_step2d(Handle& h, uint32_t step0, int nsteps);
 cudaError_t launch_step3d(Handle& h, uint32_t step0, int nsteps);
 cudaError_t launch_flush_moments(Handle& h);
+cudaError_t launch_axes_syrk(Handle& h);
+cudaError_t launch_reduce_axes(const Handle& h, double* d_out);
 cudaError_t launch_reduce_batches(const Handle& h, int batches, double* d_out1, double* d_out2);
 cudaError_t launch_syrk_probe(const float* d_X, int K, int N, double* d_C, int* d_err);
 cudaError_t launch_noise_probe(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,

@@ -280,6 +280,10 @@ static cudaError_t launch3d_real(Handle& h, uint32_t step0, int nsteps)
         h.launches += 1;
         if (e != cudaSuccess) return e;
         std::swap(h.d_state, h.d_state2);
+        if (a.sample && (h.want_sk & SHE_SK_AXES)) {
+            e = launch_axes_syrk(h);
+            if (e != cudaSuccess) return e;
+        }
         if (a.sample && sizeof(Real) == 4) {
             if (++h.partial_samples >= 256) {
                 e = launch_flush_moments(h);

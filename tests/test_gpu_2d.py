@@ -25,8 +25,10 @@ GRIDS = [(8, 6), (12, 5), (16, 16), (20, 33), (64, 48), (132, 7), (256, 20), (26
 
 def _p(nx, ny, eq, **kw):
     kw.setdefault("realizations", 3)
-    return W.species_2d(n=(nx, ny, 1), equation=eq, n0=200.0, kB=3e-3, wall_lo=1.3, wall_hi=1.3,
-                        stats_interval=3, relax_steps=10, want_sk=0, **kw)
+    kw.setdefault("stats_interval", 3)
+    kw.setdefault("relax_steps", 10)
+    kw.setdefault("want_sk", 0)
+    return W.species_2d(n=(nx, ny, 1), equation=eq, n0=200.0, kB=3e-3, wall_lo=1.3, wall_hi=1.3, **kw)
 
 
 @pytest.mark.parametrize("nx,ny", GRIDS)
@@ -84,3 +86,15 @@ def test_total_conserved_2d():
         sim.step(100)
         x1, _ = sim.state()
     assert np.max(np.abs(x1.sum(axis=1) - x0.sum(axis=1))) < 1e-10 * x0.shape[1]
+
+
+@pytest.mark.parametrize("nx,ny", [(16, 16), (132, 7), (256, 20), (64, 256)])
+def test_per_axis_structure_factor_2d(nx, ny):
+    p = _p(nx, ny, "species", precision="fp32", want_sk=2, stats_interval=2, relax_steps=0)
+    with S.Simulation(p) as sim:
+        sim.step(20)
+        g = sim.stats(sk_axes=True)
+    o = O.finalize(p, O.run(p, 3, 20, want_sk=2))
+    assert g["n_samples"] == o["n"]
+    ref = o["sk_axes"]
+    assert np.max(np.abs(g["sk_axes"] - ref)) < 2e-4 * np.max(np.abs(ref))

@@ -26,8 +26,11 @@ GRIDS = [(128, 2, 2), (128, 9, 5), (256, 16, 3), (128, 8, 40), (512, 3, 2)]
 
 def _p(shape, eq, **kw):
     kw.setdefault("realizations", 2)
+    kw.setdefault("stats_interval", 2)
+    kw.setdefault("relax_steps", 3)
+    kw.setdefault("want_sk", 0)
     return W.cube_3d(n=shape, equation=eq, n0=150.0, kB=4e-3, wall_lo=1.2, wall_hi=1.2,
-                     perturb_ic=1, stats_interval=2, relax_steps=3, want_sk=0, **kw)
+                     perturb_ic=1, **kw)
 
 
 @pytest.mark.parametrize("shape", GRIDS)
@@ -84,3 +87,18 @@ def test_total_conserved_3d():
         sim.step(30)
         x1, _ = sim.state()
     assert np.max(np.abs(x1.sum(axis=1) - x0.sum(axis=1))) < 1e-10 * x0.shape[1]
+
+
+@pytest.mark.parametrize("shape", [(128, 8, 40), (256, 16, 3), (128, 3, 130)])
+def test_per_axis_structure_factor_3d(shape):
+    # S(k) along x, y and z from the tensor-core line covariance vs the
+    # oracle's direct line DFTs (Eq. (3.11)) on the same trajectories
+    p = _p(shape, "heat", precision="fp32", want_sk=2, stats_interval=3, relax_steps=0)
+    with S.Simulation(p) as sim:
+        sim.step(9)
+        g = sim.stats(sk_axes=True)
+    o = O.finalize(p, O.run(p, 2, 9, want_sk=2))
+    assert g["n_samples"] == o["n"]
+    ref = o["sk_axes"]
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(g["sk_axes"] - ref)) < 2e-4 * scale
