@@ -125,6 +125,12 @@ WORKLOADS = {
               "stencil, moments every 10 steps"),
         chunk=100, ops=3 * (25.0 + 5.5 + 4.0) + 11.0, bytes=8.0 + 16.0 / 10,
         kernel="k_step3d<float,8,heat>"),
+    "batched_rods": dict(
+        make=lambda W: W.batched_rods(count=10_000, seed=0),
+        desc=("10,000 uneven 1D SHE rods, N log-uniform in [16, 2048], kappa U[0.5, 2], walls U[1, 3], "
+              "r = 0.2 each, per-instance seeds, FP32, moments every 10 steps after 1e4, one CUDA-graph "
+              "launch per step batch"),
+        chunk=2560, ops=25.0 + 5.5 + 4.0 + 6.0, bytes=None, kernel="k_step1d_batch<*>"),
     "oracle_rod": dict(
         make=lambda W: W.oracle_rod(want_cov=0, want_sk=0),
         desc="1D SHE rod, 32 cells, walls 1, 16 realizations, FP64",
@@ -189,13 +195,23 @@ def run_ours(args):
         dist.init_process_group("nccl")
     she.lib()
     p, desc = workload(args.workload)
-    if args.relax is not None:          # profile the sampling phase from the start
-        p["relax_steps"] = args.relax
-    R = p["realizations"]
-    cells = _cells(p)
+    batch = isinstance(p, list)
+    if batch:
+        probs = [dict(q, relax_steps=args.relax) if args.relax is not None else q for q in p]
+        p = probs[0]
+        R = 1
+        cells = sum(q["n"][0] for q in probs)
+    else:
+        if args.relax is not None:          # profile the sampling phase from the start
+            p["relax_steps"] = args.relax
+        R = p["realizations"]
+        cells = _cells(p)
     stream = torch.cuda.Stream()
     # weak scaling: every rank runs a full ensemble on its own noise streams
-    sim = she.Simulation(p, stream=stream, stream_offset=rank * R)
+    if batch:
+        sim = she.BatchSimulation(probs, stream=stream, stream_offset=rank * len(probs))
+    else:
+        sim = she.Simulation(p, stream=stream, stream_offset=rank * R)
     wl = WORKLOADS[args.workload]
     chunk = args.chunk if args.chunk else wl["chunk"]
     cu_per_step = R * cells * chunk
@@ -248,6 +264,8 @@ def run_ours(args):
     # 1D: the plain three-launches-per-step FP64 form; 2D/3D (streaming
     # kernels already launch once per step): the same kernel in FP64
     kind64 = "plain" if p["dim"] == 1 else "auto"
+    if batch:     # same total cells as 256-cell rows in the plain FP64 form
+        p64 = dict(p, n=(256, 1, 1), realizations=max(1, cells // 256))
     sim64 = she.Simulation(p64, stream=stream, precision="fp64", kernel=kind64, stream_offset=rank * R,
                            want_cov=0, want_sk=0)
     sim64.step(min(plain_steps, 50))
@@ -264,7 +282,7 @@ def run_ours(args):
 
     # ---- e2e through the C ABI with host buffers ----
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not batch:
         state, step = sim.state()
         host = torch.from_numpy(state).pin_memory()
         host_np = host.numpy()

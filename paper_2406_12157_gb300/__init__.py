@@ -21,7 +21,7 @@ from ._abi import (LibraryMissing, SHE_DIRICHLET, SHE_FE, SHE_FP32, SHE_FP64, SH
 __all__ = ["SheError", "LibraryMissing", "params_from_problem", "she_init", "she_init_batch",
            "she_step_n", "she_get_sizes", "she_stats", "she_reset_stats", "she_get_state",
            "she_set_state", "she_get_state_device", "she_set_state_device", "she_last_error",
-           "she_free", "she_noise_probe", "she_launch_count", "she_syrk_probe", "Simulation", "lib"]
+           "she_free", "she_noise_probe", "she_launch_count", "she_syrk_probe", "Simulation", "BatchSimulation", "lib"]
 
 
 class SheError(RuntimeError):
@@ -213,6 +213,53 @@ def she_syrk_probe(X):
     C = np.empty((N, N), dtype=np.float64)
     _check(lib().she_syrk_probe(Xf.ctypes.data, K, N, C.ctypes.data), None, "she_syrk_probe")
     return C
+
+
+class BatchSimulation:
+    """Owning wrapper of a batch handle of uneven 1D instances
+    (``she_init_batch``): ``with BatchSimulation(problems) as b: ...``.
+    The state and per-cell statistics are the instances back to back."""
+
+    def __init__(self, problems, stream=None, **overrides):
+        self.params = [params_from_problem(q, stream=stream, **overrides) for q in problems]
+        self.offsets = []
+        off = 0
+        for q in problems:
+            self.offsets.append(off)
+            off += int(q["n"][0])
+        self.h = she_init_batch(self.params)
+
+    def step(self, n):
+        she_step_n(self.h, n)
+
+    def stats(self, **kw):
+        return she_stats(self.h, **kw)
+
+    def state(self):
+        st, step = she_get_state(self.h)
+        return st.reshape(-1), step
+
+    def set_state(self, state, step):
+        she_set_state(self.h, np.asarray(state).reshape(1, -1), step)
+
+    def launches(self):
+        return she_launch_count(self.h)
+
+    def close(self):
+        she_free(self.h)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Simulation:

@@ -46,29 +46,37 @@ struct Row1D {
     Real wz[4];
     uint32_t wwin;
 
-    __device__ __forceinline__ void init(const Step1DArgs<Real>& a, int sl, int rho)
+    // per-row problem: cells, diffusion number, squared noise amplitude per
+    // unit face value (2 r eps), wall values, noise stream and key
+    __device__ __forceinline__ void init_vals(int N_, Real r_, Real amp2_, Real wlo_, Real whi_, uint32_t stream_,
+                                              uint32_t key0_, uint32_t key1_, int stochastic_, int sl)
     {
-        N = a.N;
+        N = N_;
         i0 = sl * C;
         jlast = N - 1 - i0;
         last_sl = RAGGED ? (N - 1) / C : LPR - 1;
         first_sl = (sl == 0);
         tail_sl = (sl == last_sl);
-        r = a.r;
-        amp2 = a.amp2;
+        r = r_;
+        amp2 = amp2_;
         s_half = fsqrt_any(amp2) * Real(0.5);
-        wlo = a.wall_lo;
-        whi = a.wall_hi;
+        wlo = wlo_;
+        whi = whi_;
         const Real sq2 = Real(1.41421356237309504880);
         g_wall_amp = sq2 * face_amp<Real>(whi, amp2, Real(2) * s_half, SPECIES);
         g_low_amp = sq2 * face_amp<Real>(wlo, amp2, Real(2) * s_half, SPECIES);
-        stream = a.stream0 + (uint32_t)rho;
+        stream = stream_;
         q0 = (uint32_t)(i0 / 4);
-        key0 = a.key0;
-        key1 = a.key1;
-        stochastic = a.stochastic;
+        key0 = key0_;
+        key1 = key1_;
+        stochastic = stochastic_;
         wz[0] = wz[1] = wz[2] = wz[3] = Real(0);
         wwin = 0xffffffffu;
+    }
+
+    __device__ __forceinline__ void init(const Step1DArgs<Real>& a, int sl, int rho)
+    {
+        init_vals(a.N, a.r, a.amp2, a.wall_lo, a.wall_hi, a.stream0 + (uint32_t)rho, a.key0, a.key1, a.stochastic, sl);
     }
 
     __device__ __forceinline__ Real flux(Real lo, Real hi, Real z) const

@@ -3,6 +3,7 @@
 // statistics from the FP64 device accumulators.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -130,6 +131,13 @@ void release(Handle* h)
     cudaFree(h->d_axes_partial);
     cudaFree(h->d_axes_red);
     h->d_axes_partial = h->d_axes_red = nullptr;
+    she::destroy_batch_graphs(*h);
+    cudaFree(h->d_inst);
+    cudaFree(h->d_step);
+    cudaFree(h->d_class_list);
+    h->d_inst = nullptr;
+    h->d_step = nullptr;
+    h->d_class_list = nullptr;
     h->d_cov_partial = h->d_cov_red = nullptr;
     h->d_state = h->d_state2 = nullptr;
     h->d_acc1 = h->d_acc2 = h->d_face = h->d_red = nullptr;
@@ -143,6 +151,16 @@ int64_t samples_in(uint64_t step_from, uint64_t nsteps, int K, int64_t relax)
     const int64_t hi = (int64_t)(step_from + nsteps);
     if (hi <= lo) return 0;
     return hi / K - lo / K;
+}
+
+// T_ref of packed cell i of a batch handle
+double batch_ref(const Handle& h, int64_t i)
+{
+    const auto it = std::upper_bound(h.inst_off.begin(), h.inst_off.end(), i);
+    const size_t k = (size_t)(it - h.inst_off.begin()) - 1;
+    const int64_t j = i - h.inst_off[k];
+    if (h.prob.bc != SHE_DIRICHLET) return h.inst_wlo[k];
+    return h.inst_wlo[k] + (h.inst_whi[k] - h.inst_wlo[k]) * ((double)j + 0.5) / (double)h.inst_n[k];
 }
 
 int default_steps_per_launch(const Handle& h)
@@ -299,10 +317,111 @@ she_status she_init(const she_params* p, she_handle** out)
 
 she_status she_init_batch(const she_params* p, int64_t count, she_handle** out)
 {
-    (void)p;
-    (void)count;
-    if (out) *out = nullptr;
-    return SHE_ERR_UNSUPPORTED;
+    if (!out) return SHE_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!p || count < 1 || count > ((int64_t)1 << 24)) return SHE_ERR_INVALID_ARG;
+    Handle* h = new (std::nothrow) Handle();
+    if (!h) return SHE_ERR_OOM;
+    std::vector<she::InstanceDesc> desc((size_t)count);
+    std::vector<float> sigma((size_t)count);
+    std::vector<std::vector<int>> lists(she::kNumBatchClasses);
+    int64_t total = 0;
+    std::string msg;
+    she_status st = SHE_OK;
+    for (int64_t i = 0; i < count && st == SHE_OK; ++i) {
+        const she_params& q = p[i];
+        she::Problem pr;
+        st = convert(q, pr, msg);
+        if (st != SHE_OK) break;
+        if (q.dim != 1 || q.realizations != 1 || q.equation != p[0].equation || q.bc != p[0].bc ||
+            q.precision != SHE_FP32 || q.stats_interval != p[0].stats_interval || q.stats_interval < 1 ||
+            q.relax_steps != p[0].relax_steps || q.stochastic != p[0].stochastic ||
+            q.perturb_ic != p[0].perturb_ic || q.kernel != SHE_KERNEL_AUTO || q.want_cov || q.want_sk ||
+            q.scheme != SHE_FE || pr.n[0] > 2048) {
+            st = SHE_ERR_INVALID_ARG;
+            msg = "she_init_batch: instances must be 1D, FP32, one realization each, N <= 2048, and share "
+                  "equation, boundary, stats_interval, relax_steps, stochastic and perturb_ic";
+            break;
+        }
+        she::InstanceDesc& d = desc[(size_t)i];
+        d.off = total;
+        d.N = pr.n[0];
+        d.r = (float)pr.r;
+        d.amp2 = (float)(q.stochastic ? 2.0 * pr.r * pr.eps : 0.0);
+        d.wlo = (float)pr.wall_lo;
+        d.whi = (float)pr.wall_hi;
+        d.wlo_d = pr.wall_lo;
+        d.whi_d = pr.wall_hi;
+        d.key0 = (uint32_t)(pr.seed & 0xffffffffu);
+        d.key1 = (uint32_t)(pr.seed >> 32);
+        d.stream = (uint32_t)p[0].stream_offset + (uint32_t)i;
+        const double mid = 0.5 * (pr.wall_lo + pr.wall_hi);
+        sigma[(size_t)i] = (float)(pr.equation == SHE_HEAT ? std::sqrt(pr.eps) * std::fabs(mid)
+                                                           : std::sqrt(pr.eps * std::fabs(mid)));
+        lists[(size_t)she::batch_class_of(d.N)].push_back((int)i);
+        total += d.N;
+        if (i == 0) h->prob = pr;
+    }
+    if (st != SHE_OK) {
+        fprintf(stderr, "%s\n", msg.c_str());
+        delete h;
+        return st;
+    }
+    h->is_batch = true;
+    h->instances = count;
+    h->R = 1;
+    h->prob.n[0] = (int)std::min<int64_t>(total, INT32_MAX);
+    h->prob.cells = total;
+    h->precision = SHE_FP32;
+    h->K = p[0].stats_interval;
+    h->relax = p[0].relax_steps;
+    h->stochastic = p[0].stochastic ? 1 : 0;
+    h->perturb_ic = p[0].perturb_ic ? 1 : 0;
+    h->steps_per_launch = p[0].steps_per_launch;
+    h->stream = (cudaStream_t)p[0].stream;
+    std::vector<int> flat;
+    for (int c = 0; c < she::kNumBatchClasses; ++c) {
+        h->class_start[c] = (int)flat.size();
+        h->class_count[c] = (int)lists[(size_t)c].size();
+        flat.insert(flat.end(), lists[(size_t)c].begin(), lists[(size_t)c].end());
+    }
+    for (int64_t i = 0; i < count; ++i) {
+        h->inst_off.push_back(desc[(size_t)i].off);
+        h->inst_n.push_back(desc[(size_t)i].N);
+        h->inst_wlo.push_back(desc[(size_t)i].wlo_d);
+        h->inst_whi.push_back(desc[(size_t)i].whi_d);
+    }
+    float* d_sigma = nullptr;
+    cudaError_t e = cudaMalloc(&h->d_state, (size_t)total * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_acc1, (size_t)total * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_acc2, (size_t)total * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_flags, sizeof(int));
+    h->red_bytes = 2 * (size_t)total * sizeof(double);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_red, h->red_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_inst, desc.size() * sizeof(she::InstanceDesc));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_step, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_class_list, flat.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&d_sigma, sigma.size() * sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h->d_inst, desc.data(), desc.size() * sizeof(she::InstanceDesc), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_class_list, flat.data(), flat.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_sigma, sigma.data(), sigma.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(h->d_step, 0, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_acc1, 0, (size_t)total * sizeof(double), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_acc2, 0, (size_t)total * sizeof(double), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flags, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) e = she::launch_init_batch(*h, d_sigma);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(d_sigma);
+    if (e != cudaSuccess) {
+        she_status s2 = cuda_fail(h, e, "she_init_batch");
+        fprintf(stderr, "%s\n", h->err.c_str());
+        release(h);
+        delete h;
+        return s2;
+    }
+    *out = reinterpret_cast<she_handle*>(h);
+    return SHE_OK;
 }
 
 she_status she_step_n(she_handle* hh, uint64_t n)
@@ -317,7 +436,8 @@ she_status she_step_n(she_handle* hh, uint64_t n)
         int chunk = (int)std::min<uint64_t>(left, (uint64_t)spl);
         cudaError_t e;
         const int64_t ns = samples_in(h->step, (uint64_t)chunk, h->K, h->relax);
-        if (h->prob.dim == 2) e = she::launch_step2d(*h, (uint32_t)h->step, chunk);
+        if (h->is_batch) e = she::launch_batch(*h, chunk);
+        else if (h->prob.dim == 2) e = she::launch_step2d(*h, (uint32_t)h->step, chunk);
         else if (h->prob.dim == 3) e = she::launch_step3d(*h, (uint32_t)h->step, chunk);
         else if (h->kernel == SHE_KERNEL_PLAIN) e = she::launch_step1d_plain(*h, (uint32_t)h->step, chunk);
         else if (h->want_cov) e = she::launch_step1d_cov(*h, (uint32_t)h->step, chunk, ns > 0);
@@ -336,7 +456,7 @@ she_status she_get_sizes(const she_handle* hh, she_sizes* s)
     if (!h || !s) return SHE_ERR_INVALID_ARG;
     s->cells = h->prob.cells;
     s->realizations = h->R;
-    s->instances = 1;
+    s->instances = h->instances;
     s->elem_bytes = h->precision == SHE_FP64 ? 8 : 4;
     s->state_bytes = h->R * h->prob.cells * s->elem_bytes;
     s->axes_len = 0;
@@ -385,8 +505,9 @@ she_status she_stats(she_handle* hh, she_stats_out* out)
             s1 += b1[(size_t)b * cells + i];
             s2 += b2[(size_t)b * cells + i];
         }
-        const double ref_i = dir ? h->prob.wall_lo + (h->prob.wall_hi - h->prob.wall_lo) * ((double)i + 0.5) / (double)cells
-                                 : h->prob.wall_lo;
+        double ref_i = dir ? h->prob.wall_lo + (h->prob.wall_hi - h->prob.wall_lo) * ((double)i + 0.5) / (double)cells
+                           : h->prob.wall_lo;
+        if (h->is_batch) ref_i = batch_ref(*h, i);
         const double mu_i = s1 / n;
         mu[(size_t)i] = mu_i;
         ref[(size_t)i] = ref_i;
@@ -528,6 +649,8 @@ she_status she_set_state(she_handle* hh, const void* host_buf, size_t bytes, uin
     if (step > (uint64_t)0xffffffffu) return fail(h, SHE_ERR_INVALID_ARG, "she_set_state: step >= 2^32");
     cudaError_t e = cudaMemcpyAsync(h->d_state, host_buf, need, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flags, 0, sizeof(int), h->stream);
+    const uint32_t st32 = (uint32_t)step;
+    if (e == cudaSuccess && h->d_step) e = cudaMemcpyAsync(h->d_step, &st32, sizeof(uint32_t), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "she_set_state");
     h->step = step;
@@ -554,6 +677,11 @@ she_status she_set_state_device(she_handle* hh, const void* dev_buf, size_t byte
     if (step > (uint64_t)0xffffffffu) return fail(h, SHE_ERR_INVALID_ARG, "she_set_state_device: step >= 2^32");
     cudaError_t e = cudaMemcpyAsync(h->d_state, dev_buf, need, cudaMemcpyDeviceToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flags, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess && h->d_step) {
+        const uint32_t st32 = (uint32_t)step;
+        e = cudaMemcpyAsync(h->d_step, &st32, sizeof(uint32_t), cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(h, e, "she_set_state_device");
     h->step = step;
     return SHE_OK;

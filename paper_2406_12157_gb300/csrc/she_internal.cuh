@@ -87,6 +87,41 @@ struct AxesArgs {
     float ref;
 };
 
+// One instance of a batch of uneven 1D problems.
+struct InstanceDesc {
+    int64_t off;          // first cell in the packed state / accumulators
+    int N;                // cells
+    float r, amp2;        // diffusion number, 2 r eps
+    float wlo, whi;       // walls (FP32, the step)
+    double wlo_d, whi_d;  // walls (FP64, the initial condition)
+    uint32_t key0, key1;  // Philox key (the instance's seed)
+    uint32_t stream;      // noise stream (counter word 2)
+};
+
+struct BatchArgs {
+    float* state;         // packed [total cells]
+    double* acc1;
+    double* acc2;
+    int* flags;
+    const InstanceDesc* inst;
+    const uint32_t* d_step;   // absolute index of the first step of the launch
+    int nsteps;
+    int K;
+    long long relax;
+    int stochastic;
+};
+
+constexpr int kNumBatchClasses = 8;
+
+struct BatchGraph {
+    int nsteps = 0;
+    int kernels = 0;
+    cudaGraphExec_t exec = nullptr;
+    BatchArgs args;
+    const int* lists[kNumBatchClasses];
+    int counts[kNumBatchClasses];
+};
+
 // Extra arguments of the fused covariance kernel.
 struct CovArgs {
     double* partial;      // [G][N][N] per-CTA FP64 partial sums of delta delta^T
@@ -124,6 +159,18 @@ struct Handle {
     double* d_cov_partial = nullptr;  // [cov_ctas][N][N] FP64 partial covariance sums
     double* d_cov_red = nullptr;   // [N][N] reduced
     int cov_ctas = 0;              // CTAs (one per SM) of the fused covariance kernel
+    // batch of uneven 1D instances
+    bool is_batch = false;
+    int64_t instances = 1;
+    InstanceDesc* d_inst = nullptr;
+    uint32_t* d_step = nullptr;        // device-side step counter read by the batch kernels
+    int* d_class_list = nullptr;       // instance ids grouped by layout class
+    int class_start[kNumBatchClasses] = {0};
+    int class_count[kNumBatchClasses] = {0};
+    std::vector<BatchGraph> batch_graphs;
+    std::vector<int64_t> inst_off;     // host copies for the statistics
+    std::vector<int> inst_n;
+    std::vector<double> inst_wlo, inst_whi;
     double* d_axes_partial = nullptr;  // [dim][cov_ctas][256*256] per-axis line covariances
     double* d_axes_red = nullptr;      // [dim][256*256] reduced
     size_t red_bytes = 0;
@@ -142,6 +189,10 @@ cudaError_t launch_step2d(Handle& h, uint32_t step0, int nsteps);
 cudaError_t launch_step3d(Handle& h, uint32_t step0, int nsteps);
 cudaError_t launch_flush_moments(Handle& h);
 cudaError_t launch_axes_syrk(Handle& h);
+int batch_class_of(int N);
+cudaError_t launch_batch(Handle& h, int nsteps);
+cudaError_t launch_init_batch(Handle& h, const float* d_sigma);
+void destroy_batch_graphs(Handle& h);
 cudaError_t launch_reduce_axes(const Handle& h, double* d_out);
 cudaError_t launch_reduce_batches(const Handle& h, int batches, double* d_out1, double* d_out2);
 cudaError_t launch_syrk_probe(const float* d_X, int K, int N, double* d_C, int* d_err);
