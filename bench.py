@@ -114,15 +114,16 @@ WORKLOADS = {
         chunk=10_000, ops=25.0 + 5.5 + 4.0 + 6.0, bytes=None,
         kernel="k_step1d_cov<32,8,dirichlet,heat>"),
     "species_2d": dict(
-        make=lambda W: W.species_2d(want_sk=0),
+        make=lambda W: W.species_2d(want_sk=1),
         desc=("2D stochastic species diffusion, 256x256 periodic, D=1, r=0.1, eps_c=1e-3, c=1 + "
-              "zero-sum perturbation, 256 realizations, FP32, moments every 10 steps after 1e4"),
+              "zero-sum perturbation, 256 realizations, FP32, moments and the full 2D S(k) "
+              "(two-stage DFT-as-GEMM on tcgen05) every 10 steps after 1e4"),
         chunk=1000, ops=2 * (25.0 + 5.5 + 7.0) + 9.0, bytes=8.0 + 16.0 / 10,
         kernel="k_step2d<float,8,32,species>"),
     "cube_3d": dict(
-        make=lambda W: W.cube_3d(want_sk=0),
+        make=lambda W: W.cube_3d(want_sk=2),
         desc=("3D SHE 256^3 periodic, T0=1, r=0.1, eps=1e-3, 8 realizations, FP32, HBM-streaming "
-              "stencil, moments every 10 steps"),
+              "stencil, moments and S(k) along x, y, z (line covariance on tcgen05) every 10 steps"),
         chunk=100, ops=3 * (25.0 + 5.5 + 4.0) + 11.0, bytes=8.0 + 16.0 / 10,
         kernel="k_step3d<float,8,heat>"),
     "batched_rods": dict(
@@ -252,7 +253,8 @@ def run_ours(args):
     total_cu = cu_per_step * args.steps * world
     value = total_cu / (ms / 1e3)
     try:
-        stats = sim.stats(cov=bool(p.get("want_cov")))   # device reduce + D2H
+        stats = sim.stats(cov=bool(p.get("want_cov")), sk=bool(p.get("want_sk", 0) & 1),
+                          sk_axes=bool(p.get("want_sk", 0) & 2))          # device reduce + D2H
         assert np.all(np.isfinite(stats["var"]))
     except she.SheError as e:
         if e.status != she._abi.SHE_ERR_STATE:   # no sample yet in a short run is fine
@@ -294,7 +296,8 @@ def run_ours(args):
             sim.set_state(host_np, step)            # H2D of the step's input state
             sim.step(chunk)
             try:
-                out = sim.stats(cov=bool(p.get("want_cov")))   # device reduce + D2H
+                out = sim.stats(cov=bool(p.get("want_cov")), sk=bool(p.get("want_sk", 0) & 1),
+                                sk_axes=bool(p.get("want_sk", 0) & 2))      # device reduce + D2H
                 d2h = sum(v.nbytes for v in out.values() if hasattr(v, "nbytes"))
                 d2h += 2 * min(32, R) * cells * 8 + (cells * cells * 8 if p.get("want_cov") else 0)
             except she.SheError as e:

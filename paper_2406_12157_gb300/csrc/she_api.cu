@@ -131,6 +131,14 @@ void release(Handle* h)
     cudaFree(h->d_axes_partial);
     cudaFree(h->d_axes_red);
     h->d_axes_partial = h->d_axes_red = nullptr;
+    cudaFree(h->d_sk_w);
+    cudaFree(h->d_sk_c);
+    cudaFree(h->d_sk_s);
+    cudaFree(h->d_sk_partial);
+    cudaFree(h->d_sk_acc);
+    h->d_sk_w = h->d_sk_c = h->d_sk_s = nullptr;
+    h->d_sk_partial = nullptr;
+    h->d_sk_acc = nullptr;
     she::destroy_batch_graphs(*h);
     cudaFree(h->d_inst);
     cudaFree(h->d_step);
@@ -216,8 +224,12 @@ she_status she_init(const she_params* p, she_handle** out)
     if (st == SHE_OK && (p->want_sk & SHE_SK_AXES) && p->dim == 1) {
         st = SHE_ERR_INVALID_ARG; msg = "she: SHE_SK_AXES is for 2D/3D grids (use SHE_SK_FULL in 1D)";
     }
-    if (st == SHE_OK && (p->want_sk & SHE_SK_FULL) && p->dim > 1) {
-        st = SHE_ERR_UNSUPPORTED; msg = "she: the full multi-dimensional S(k) is not built; use SHE_SK_AXES";
+    if (st == SHE_OK && (p->want_sk & SHE_SK_FULL) && p->dim == 3) {
+        st = SHE_ERR_INVALID_ARG; msg = "she: the full S(k) is for 1D and 2D grids; use SHE_SK_AXES in 3D";
+    }
+    if (st == SHE_OK && (p->want_sk & SHE_SK_FULL) && p->dim == 2 &&
+        (p->precision != SHE_FP32 || p->n[0] % 2 != 0 || p->n[0] > 256 || p->n[1] > 256)) {
+        st = SHE_ERR_UNSUPPORTED; msg = "she: the 2D S(k) runs on the FP32 path with even nx <= 256 and ny <= 256";
     }
     if (st == SHE_OK && (p->want_sk & SHE_SK_AXES) &&
         (p->precision != SHE_FP32 || p->n[0] > 256 || p->n[1] > 256 || (p->dim == 3 && p->n[2] > 256))) {
@@ -287,6 +299,25 @@ she_status she_init(const she_params* p, she_handle** out)
         if (e == cudaSuccess) e = cudaMalloc(&h->d_axes_red, per * sizeof(double));
         if (e == cudaSuccess)
             e = cudaMemsetAsync(h->d_axes_partial, 0, per * (size_t)h->cov_ctas * sizeof(double), h->stream);
+    }
+    if (e == cudaSuccess && h->prob.dim == 2 && (h->want_sk & SHE_SK_FULL)) {
+        int dev = 0, sms = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        h->sk_ctas = (int)std::min<int64_t>(sms > 0 ? sms : 1, h->R);
+        const size_t img = 256 * 1024;     // each constant image set
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_sk_w, img);
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_sk_c, img);
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_sk_s, img);
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_sk_partial, (size_t)h->sk_ctas * 256 * 129 * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_sk_acc, 256 * 129 * sizeof(double));
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->d_sk_w, 0, img, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->d_sk_c, 0, img, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->d_sk_s, 0, img, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(h->d_sk_partial, 0, (size_t)h->sk_ctas * 256 * 129 * sizeof(float), h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->d_sk_acc, 0, 256 * 129 * sizeof(double), h->stream);
+        if (e == cudaSuccess) e = she::launch_sk2d_tables(*h);
     }
     if (e == cudaSuccess && h->want_cov) {
         int dev = 0, sms = 0;
@@ -559,6 +590,52 @@ she_status she_stats(she_handle* hh, she_stats_out* out)
             off += na;
         }
     }
+    if (h->prob.dim == 2 && (out->sk || out->sk_fluct)) {
+        e = she::launch_sk2d_flush(*h);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        std::vector<double> acc(256 * 129);
+        if (e == cudaSuccess) e = cudaMemcpy(acc.data(), h->d_sk_acc, acc.size() * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(sk2d)");
+        const int nx = h->prob.n[0], ny = h->prob.n[1];
+        // hat mu (2D DFT of the mean delta), separably: rows then columns
+        const double two_pi = 6.283185307179586476925286766559;
+        std::vector<double> rr((size_t)cells), ri((size_t)cells), mr((size_t)cells), mi((size_t)cells);
+        for (int y = 0; y < ny; ++y)
+            for (int kx = 0; kx < nx; ++kx) {
+                double sr = 0.0, si = 0.0;
+                for (int x = 0; x < nx; ++x) {
+                    const double ang = two_pi * (double)(((long long)kx * x) % nx) / nx;
+                    sr += mu[(size_t)y * nx + x] * std::cos(ang);
+                    si -= mu[(size_t)y * nx + x] * std::sin(ang);
+                }
+                rr[(size_t)y * nx + kx] = sr;
+                ri[(size_t)y * nx + kx] = si;
+            }
+        for (int ky = 0; ky < ny; ++ky)
+            for (int kx = 0; kx < nx; ++kx) {
+                double sr = 0.0, si = 0.0;
+                for (int y = 0; y < ny; ++y) {
+                    const double ang = two_pi * (double)(((long long)ky * y) % ny) / ny;
+                    const double c = std::cos(ang), sn = std::sin(ang);
+                    const double ar = rr[(size_t)y * nx + kx], ai = ri[(size_t)y * nx + kx];
+                    sr += ar * c + ai * sn;
+                    si += ai * c - ar * sn;
+                }
+                mr[(size_t)ky * nx + kx] = sr;
+                mi[(size_t)ky * nx + kx] = si;
+            }
+        const double refsum = h->prob.wall_lo * (double)cells;     // hat T_ref: only k = 0
+        for (int ky = 0; ky < ny; ++ky)
+            for (int kx = 0; kx < nx; ++kx) {
+                double d2;
+                if (kx <= nx / 2) d2 = acc[(size_t)ky * 129 + kx] / n;
+                else d2 = acc[(size_t)((ny - ky) % ny) * 129 + (nx - kx)] / n;
+                const size_t k = (size_t)ky * nx + kx;
+                const double m2 = mr[k] * mr[k] + mi[k] * mi[k];
+                if (out->sk_fluct) out->sk_fluct[k] = d2 - m2;
+                if (out->sk) out->sk[k] = (k == 0 ? refsum * refsum + 2.0 * refsum * mr[0] : 0.0) + d2;
+            }
+    }
     if (h->want_cov && (out->cov || out->sk || out->sk_fluct)) {
         const int64_t N = cells;
         e = she::launch_reduce_cov(*h, h->d_cov_red);
@@ -615,6 +692,10 @@ she_status she_reset_stats(she_handle* hh)
     if (e == cudaSuccess && h->d_m1) e = cudaMemsetAsync(h->d_m1, 0, nstate * sizeof(float), h->stream);
     if (e == cudaSuccess && h->d_m2) e = cudaMemsetAsync(h->d_m2, 0, nstate * sizeof(float), h->stream);
     h->partial_samples = 0;
+    if (e == cudaSuccess && h->d_sk_partial)
+        e = cudaMemsetAsync(h->d_sk_partial, 0, (size_t)h->sk_ctas * 256 * 129 * sizeof(float), h->stream);
+    if (e == cudaSuccess && h->d_sk_acc) e = cudaMemsetAsync(h->d_sk_acc, 0, 256 * 129 * sizeof(double), h->stream);
+    h->sk_partial_samples = 0;
     if (e == cudaSuccess && h->d_axes_partial)
         e = cudaMemsetAsync(h->d_axes_partial, 0,
                             (size_t)h->prob.dim * 65536 * (size_t)h->cov_ctas * sizeof(double), h->stream);

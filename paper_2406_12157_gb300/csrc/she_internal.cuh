@@ -87,6 +87,18 @@ struct AxesArgs {
     float ref;
 };
 
+// Arguments of the full 2D structure-factor kernel.
+struct Sk2dArgs {
+    const float* T;       // [R][ny][nx]
+    float* partial;       // [G][256][129] FP32 per-CTA sums of |hat delta|^2 (kx <= nx/2)
+    const unsigned char* wimg;   // row-DFT operand images
+    const unsigned char* cimg;   // column cos images
+    const unsigned char* simg;   // column sin images
+    int* flags;
+    int nx, ny, R;
+    float ref;
+};
+
 // One instance of a batch of uneven 1D problems.
 struct InstanceDesc {
     int64_t off;          // first cell in the packed state / accumulators
@@ -171,6 +183,13 @@ struct Handle {
     std::vector<int64_t> inst_off;     // host copies for the statistics
     std::vector<int> inst_n;
     std::vector<double> inst_wlo, inst_whi;
+    unsigned char* d_sk_w = nullptr;   // 2D S(k): constant operand images
+    unsigned char* d_sk_c = nullptr;
+    unsigned char* d_sk_s = nullptr;
+    float* d_sk_partial = nullptr;     // [sk_ctas][256][129]
+    double* d_sk_acc = nullptr;        // [256][129]
+    int sk_ctas = 0;
+    int sk_partial_samples = 0;
     double* d_axes_partial = nullptr;  // [dim][cov_ctas][256*256] per-axis line covariances
     double* d_axes_red = nullptr;      // [dim][256*256] reduced
     size_t red_bytes = 0;
@@ -189,6 +208,9 @@ cudaError_t launch_step2d(Handle& h, uint32_t step0, int nsteps);
 cudaError_t launch_step3d(Handle& h, uint32_t step0, int nsteps);
 cudaError_t launch_flush_moments(Handle& h);
 cudaError_t launch_axes_syrk(Handle& h);
+cudaError_t launch_sk2d_tables(Handle& h);
+cudaError_t launch_sk2d(Handle& h);
+cudaError_t launch_sk2d_flush(Handle& h);
 int batch_class_of(int N);
 cudaError_t launch_batch(Handle& h, int nsteps);
 cudaError_t launch_init_batch(Handle& h, const float* d_sigma);

@@ -254,6 +254,10 @@ static cudaError_t launch2d_real(Handle& h, uint32_t step0, int nsteps)
             e = launch_axes_syrk(h);
             if (e != cudaSuccess) return e;
         }
+        if (a.sample && (h.want_sk & SHE_SK_FULL)) {
+            e = launch_sk2d(h);
+            if (e != cudaSuccess) return e;
+        }
         if (a.sample && sizeof(Real) == 4) {
             if (++h.partial_samples >= 256) {
                 e = launch_flush_moments(h);

@@ -98,3 +98,20 @@ def test_per_axis_structure_factor_2d(nx, ny):
     assert g["n_samples"] == o["n"]
     ref = o["sk_axes"]
     assert np.max(np.abs(g["sk_axes"] - ref)) < 2e-4 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("nx,ny,R", [(16, 12, 6), (64, 48, 4), (256, 16, 3), (132, 20, 3)])
+def test_full_structure_factor_2d(nx, ny, R):
+    # S(kx, ky) from the two-stage tcgen05 DFT vs the oracle's 2D DFT by its
+    # definition (Eq. (3.11) along both axes) on the same trajectories
+    p = _p(nx, ny, "species", precision="fp32", want_sk=1, stats_interval=3, relax_steps=0,
+           realizations=R)
+    with S.Simulation(p) as sim:
+        sim.step(12)
+        g = sim.stats(sk=True)
+    o = O.finalize(p, O.run(p, R, 12, want_sk=1))
+    assert g["n_samples"] == o["n"]
+    scale = np.max(np.abs(o["sk_fluct"][1:]))
+    assert np.max(np.abs(g["sk_fluct"] - o["sk_fluct"])) < 2e-4 * scale
+    assert np.allclose(g["sk"][1:], o["sk"][1:], rtol=0, atol=2e-4 * scale)
+    assert abs(g["sk"][0] - o["sk"][0]) < 1e-6 * abs(o["sk"][0])
