@@ -281,6 +281,17 @@ she_status she_syrk_probe(const float* X, int32_t K, int32_t N, double* C);
 #define SHE_NOALLOC_MAX_FACES (1 << 20)
 she_status she_step_plain_noalloc(const she_params* p, const double* T_in, double* T_out, uint64_t step);
 
+/*
+ * Test hook of the failure path of the bounded device waits (the paper has
+ * no counterpart): a kernel waits on an mbarrier that nothing completes,
+ * giving up after max_tries sleeping try_wait rounds (1 .. 2^20), exactly as
+ * the tensor-core kernels do before they flag SHE_ERR_TIMEOUT.  Returns
+ * SHE_ERR_TIMEOUT when the wait gave up (the expected outcome), SHE_OK if it
+ * completed, SHE_ERR_INVALID_ARG or SHE_ERR_CUDA.  The GPU context stays
+ * usable: nothing traps or spins forever.
+ */
+she_status she_wait_probe(uint32_t max_tries);
+
 /* Number of kernel launches enqueued by this handle since init (for the
  * benchmark's launch accounting). */
 int64_t she_launch_count(const she_handle* h);

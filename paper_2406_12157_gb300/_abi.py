@@ -34,7 +34,7 @@ SHE_KERNEL_AUTO, SHE_KERNEL_PLAIN = 0, 1
 EXPORTS = ["she_init", "she_init_batch", "she_step_n", "she_get_sizes", "she_stats",
            "she_reset_stats", "she_get_state", "she_set_state", "she_get_state_device",
            "she_set_state_device", "she_last_error", "she_free", "she_noise_probe",
-           "she_launch_count", "she_syrk_probe", "she_step_plain_noalloc"]
+           "she_launch_count", "she_syrk_probe", "she_step_plain_noalloc", "she_wait_probe"]
 
 
 class she_params(ctypes.Structure):
@@ -152,6 +152,8 @@ def load(path=None):
     L.she_step_plain_noalloc.argtypes = [ctypes.POINTER(she_params), ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_uint64]
     L.she_step_plain_noalloc.restype = ctypes.c_int
+    L.she_wait_probe.argtypes = [ctypes.c_uint32]
+    L.she_wait_probe.restype = ctypes.c_int
     L.she_launch_count.argtypes = [H]
     L.she_launch_count.restype = ctypes.c_int64
     if path is None:

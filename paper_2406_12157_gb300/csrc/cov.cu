@@ -115,6 +115,26 @@ __global__ void __launch_bounds__(128) k_syrk_probe(const float* __restrict__ X,
     if (threadIdx.x < 32) tmem_dealloc(tbase, ncols);
 }
 
+// Failure-path check of the bounded waits: one thread waits on a fresh
+// mbarrier that nothing arrives on, with the same bounded sleeping wait the
+// tensor-core kernels use, and records whether it gave up.
+__global__ void k_wait_probe(uint32_t max_tries, int* result)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *result = mbar_wait_sleep_bounded(&bar, 0u, max_tries) ? 0 : 1;
+}
+
+cudaError_t launch_wait_probe(uint32_t max_tries, int* d_result)
+{
+    k_wait_probe<<<1, 32>>>(max_tries, d_result);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_syrk_probe(const float* d_X, int K, int N, double* d_C, int* d_err)
 {
     const int smem = 2 * kCovOperandBytes + 1024 + 64;

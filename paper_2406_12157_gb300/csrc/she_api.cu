@@ -880,6 +880,21 @@ she_status she_syrk_probe(const float* X, int32_t K, int32_t N, double* C)
     return herr ? SHE_ERR_TIMEOUT : SHE_OK;
 }
 
+she_status she_wait_probe(uint32_t max_tries)
+{
+    if (max_tries < 1 || max_tries > (1u << 20)) return SHE_ERR_INVALID_ARG;
+    int* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(d, 0, sizeof(int));
+    if (e == cudaSuccess) e = she::launch_wait_probe(max_tries, d);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int r = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&r, d, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return SHE_ERR_CUDA;
+    return r ? SHE_ERR_TIMEOUT : SHE_OK;
+}
+
 int64_t she_launch_count(const she_handle* hh)
 {
     const Handle* h = reinterpret_cast<const Handle*>(hh);

@@ -69,3 +69,11 @@ def test_full_size_covariance_matches_oracle():
     p, g, o = _cov_case(256, 4096, 100, sk=False)
     scale = np.max(np.diag(o["cov"]))
     assert np.max(np.abs(g["cov"] - o["cov"])) < 2e-4 * scale
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    # a wait on a barrier nothing completes gives up and reports it
+    assert S.lib().she_wait_probe(64) == S._abi.SHE_ERR_TIMEOUT
+    # the context is still usable afterwards
+    X = np.ones((4, 16), dtype=np.float32)
+    assert np.allclose(S.she_syrk_probe(X), 4.0)
