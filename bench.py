@@ -205,6 +205,8 @@ def run_ours(args):
     else:
         if args.relax is not None:          # profile the sampling phase from the start
             p["relax_steps"] = args.relax
+        if args.realizations:
+            p["realizations"] = args.realizations
         R = p["realizations"]
         cells = _cells(p)
     stream = torch.cuda.Stream()
@@ -405,6 +407,8 @@ def main():
                     help="time steps per bench step (default: per workload)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--realizations", type=int, default=None,
+                    help="override the workload's realizations (small ncu captures)")
     ap.add_argument("--relax", type=int, default=None,
                     help="override the workload's relaxation steps (profiling the sampling phase)")
     args = ap.parse_args()

@@ -172,9 +172,12 @@ k_axes_syrk(const AxesArgs a)
                     float v[32];
                     if (have && p0 + 32 <= n) {
                         const float4* src = reinterpret_cast<const float4*>(X + (size_t)row * nx + p0);
+                        float4 f8[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) f8[q] = __ldg(src + q);
 #pragma unroll
                         for (int q = 0; q < 8; ++q) {
-                            const float4 f = src[q];
+                            const float4 f = f8[q];
                             v[4 * q] = f.x - a.ref; v[4 * q + 1] = f.y - a.ref;
                             v[4 * q + 2] = f.z - a.ref; v[4 * q + 3] = f.w - a.ref;
                         }
@@ -203,17 +206,19 @@ k_axes_syrk(const AxesArgs a)
                     const size_t lbase = (axis == 1) ? (size_t)other * nx * ny + (xin ? x : 0)
                                                      : (size_t)other * nx + (xin ? x : 0);
                     const int p0 = 32 * warp;
+                    // all 32 loads of this thread first (independent, coalesced
+                    // across the lanes), then split and store
+                    float v[32];
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        const int pp = p0 + q;
+                        v[q] = (xin && pp < n) ? __ldg(X + lbase + (size_t)pp * ge.stride) - a.ref : 0.0f;
+                    }
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
-                        float v[8];
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const int p = p0 + 8 * c + q;
-                            v[q] = (xin && p < n) ? X[lbase + (size_t)p * ge.stride] - a.ref : 0.0f;
-                        }
                         uint32_t hw[4], lw[4];
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) split_bf16x2(v[2 * q], v[2 * q + 1], hw[q], lw[q]);
+                        for (int q = 0; q < 4; ++q) split_bf16x2(v[8 * c + 2 * q], v[8 * c + 2 * q + 1], hw[q], lw[q]);
                         const uint32_t off = sw128_mn_offset(lane, p0 + 8 * c, kLBO, kSBO);
                         *reinterpret_cast<uint4*>(dh + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
                         *reinterpret_cast<uint4*>(dl + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);

@@ -111,10 +111,25 @@ __device__ __forceinline__ void mma3(uint32_t d, uint32_t ahi, uint32_t alo, uin
     mma_bf16(d, desc_sw128(alo, lbo_a, sbo_a), desc_sw128(bhi, lbo_b, sbo_b), idesc, 1u);
 }
 
-__device__ __forceinline__ void copy16(unsigned char* dst, const unsigned char* src, int bytes)
+// block-wide 16-byte copy global -> shared, eight loads in flight per thread
+__device__ __forceinline__ void copy16(unsigned char* dst, const unsigned char* __restrict__ src, int bytes)
 {
-    for (int i = threadIdx.x; i < bytes / 16; i += blockDim.x)
-        reinterpret_cast<uint4*>(dst)[i] = reinterpret_cast<const uint4*>(src)[i];
+    const int n16 = bytes / 16;
+    const uint4* s = reinterpret_cast<const uint4*>(src);
+    uint4* d = reinterpret_cast<uint4*>(dst);
+    for (int i0 = threadIdx.x; i0 < n16; i0 += 8 * blockDim.x) {
+        uint4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i < n16) v[u] = __ldg(s + i);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i < n16) d[i] = v[u];
+        }
+    }
 }
 
 // One CTA per realization (grid-stride), 256 threads.
@@ -170,22 +185,33 @@ k_sk2d(const Sk2dArgs a)
                 unsigned char* a1h = r1;
                 unsigned char* a1l = r1 + kA;
                 unsigned char* wh = r1 + 2 * kA;
-                // delta^T chunk: k = x - 64 kc, mn = y; thread: fixed x, 8 consecutive y per chunk
-                for (int it = tid; it < kKC * 32; it += blockDim.x) {
-                    const int kl = it % kKC, y8 = it / kKC;
-                    const int x = kc * kKC + kl;
-                    float v[8];
+                // delta^T chunk: k = x - 64 kc, mn = y; a thread owns a fixed x and
+                // eight 8-row groups (64 independent loads first, then stores)
+                for (int it0 = tid; it0 < kKC * 32; it0 += 8 * blockDim.x) {
+                    float v[8][8];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const int y = 8 * y8 + q;
-                        v[q] = (x < nx && y < ny) ? X[(size_t)y * nx + x] - a.ref : 0.0f;
+                    for (int u = 0; u < 8; ++u) {
+                        const int it = it0 + u * blockDim.x;
+                        const int kl = it % kKC, y8 = it / kKC;
+                        const int x = kc * kKC + kl;
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const int y = 8 * y8 + q;
+                            v[u][q] = (it < kKC * 32 && x < nx && y < ny) ? __ldg(X + (size_t)y * nx + x) - a.ref : 0.0f;
+                        }
                     }
-                    uint32_t hw[4], lw[4];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) split_bf16x2(v[2 * q], v[2 * q + 1], hw[q], lw[q]);
-                    const uint32_t off = sw128_mn_offset(kl, 8 * y8, kLBO, kSBO_A);
-                    *reinterpret_cast<uint4*>(a1h + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                    *reinterpret_cast<uint4*>(a1l + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    for (int u = 0; u < 8; ++u) {
+                        const int it = it0 + u * blockDim.x;
+                        if (it >= kKC * 32) continue;
+                        const int kl = it % kKC, y8 = it / kKC;
+                        uint32_t hw[4], lw[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) split_bf16x2(v[u][2 * q], v[u][2 * q + 1], hw[q], lw[q]);
+                        const uint32_t off = sw128_mn_offset(kl, 8 * y8, kLBO, kSBO_A);
+                        *reinterpret_cast<uint4*>(a1h + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        *reinterpret_cast<uint4*>(a1l + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    }
                 }
                 copy16(wh, a.wimg + (size_t)(blk * 4 + kc) * 2 * kBW, 2 * kBW);
                 fence_proxy_async_smem();
