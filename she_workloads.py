@@ -9,7 +9,7 @@ nondimensional units with dx = 1 and a unit cell volume, so k_B (heat) or
 1/n0 (species) *is* the relative equilibrium variance eps, and kappa*dt (or
 D*dt) *is* the diffusion number r.
 
-Workloads (shaped like the paper's runs, Sec. 3, Figs. 2-6, and the five
+Workloads (shaped like the paper's runs, Sec. 3, Figs. 2-6, and the
 configurations this library is measured on):
 
 * ``oracle_rod``     1D, 32 cells, Dirichlet walls T = 1, eps = 1e-3,

@@ -54,6 +54,17 @@ def test_noise_bits_and_normals_match_oracle():
         assert np.quantile(d, 0.999) < 2e-5
 
 
+def test_device_philox_known_answers():
+    # the published Philox-4x32-10 known answers (Salmon et al., SC'11)
+    kats = [((0, 0, 0, 0), (0, 0), [0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8]),
+            ((0xffffffff,) * 4, (0xffffffff, 0xffffffff), [0x408f276d, 0x41c83b0e, 0xa20bc7c6, 0x6d5451fd]),
+            ((0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344), (0xa4093822, 0x299f31d0),
+             [0xd16cfe09, 0x94fdcceb, 0x5001e420, 0x24126ea1])]
+    for ctr, key, out in kats:
+        bits, _, _ = S.she_noise_probe(key[0] | (key[1] << 32), *ctr, 1)
+        assert [int(x) for x in bits[0]] == out
+
+
 # ------------------------------------------------------------ trajectories --
 
 CASES = [
@@ -137,7 +148,7 @@ def test_fp32_statistics_match_oracle():
     assert np.all(np.isfinite(g["var_se"])) and np.all(g["var_se"] > 0)
 
 
-def test_fp64_statistics_match_oracle_config1():
+def test_fp64_statistics_match_oracle_32_cells():
     p = W.oracle_rod(want_cov=0, want_sk=0)   # 32 cells, 16 realizations, FP64
     with S.Simulation(p) as sim:
         sim.step(p["steps"])
@@ -209,6 +220,23 @@ def test_stats_before_any_sample_is_a_state_error():
         with pytest.raises(S.SheError) as e:
             sim.stats()
         assert e.value.status == S._abi.SHE_ERR_STATE
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_zero_steps_is_a_no_op(dim):
+    if dim == 1:
+        p = _prob(40, "dirichlet", "heat", (1.0, 2.0), precision="fp32")
+    elif dim == 2:
+        p = W.species_2d(n=(16, 8, 1), realizations=2, relax_steps=0, want_sk=0)
+    else:
+        p = W.cube_3d(n=(128, 8, 4), realizations=2, want_sk=0)
+    with S.Simulation(p) as sim:
+        x0, s0 = sim.state()
+        n0 = sim.launches()
+        sim.step(0)
+        x1, s1 = sim.state()
+        assert s1 == s0 == 0 and sim.launches() == n0
+        assert np.array_equal(x0, x1)
 
 
 def test_nonfinite_state_is_reported():

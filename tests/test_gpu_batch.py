@@ -69,7 +69,7 @@ def test_batch_one_step_fp32_parity():
         assert rel_err(got[off:off + n].astype(np.float64), ref) < 2e-5
 
 
-def test_config4_sampled_one_percent():
+def test_ten_thousand_rods_sampled_one_percent():
     # 10,000 instances, N log-uniform in [16, 2048]; 1 % checked against the oracle
     probs = W.batched_rods(count=10_000, seed=0)
     steps = 200

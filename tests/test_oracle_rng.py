@@ -2,12 +2,13 @@
 
 The paper draws iid N(0,1) per face and step (Sec. 3, Eq. (3.7)); the
 generator is this library's choice.  The oracle's generator is pinned here by
-properties the mathematics fixes -- independent of its code: uniformity of the
-raw 32-bit words, the N(0,1) law of the deviates (moments and a KS test
-against scipy's normal CDF), independence between slots and neighbouring
-counters, and the structure of a 4-round-free counter map (distinct counters
-give distinct blocks).  The GPU generator is compared against this one bit for
-bit in the GPU tests, and against NVIDIA cuRAND's Philox4_32_10 there.
+the known-answer vectors its authors publish for Philox-4x32-10 (Salmon,
+Moraes, Dror, Shaw, SC'11, Random123 distribution) and by properties the
+mathematics fixes -- independent of its code: uniformity of the raw 32-bit
+words, the N(0,1) law of the deviates (moments and a KS test against scipy's
+normal CDF), independence between slots and neighbouring counters, and
+distinct blocks for distinct counters.  The GPU generator is compared against
+this one bit for bit in the GPU tests.
 """
 import numpy as np
 import pytest
@@ -19,6 +20,22 @@ from oracle import she
 def _blocks(n, seed=0, c1=0, c2=0, c3=0):
     return np.array([she.philox([i, c1, c2, c3], [seed & 0xFFFFFFFF, seed >> 32])
                      for i in range(n)], dtype=np.uint64)
+
+
+# (counter, key) -> output of Philox-4x32-10, the published known answers
+KNOWN_ANSWERS = [
+    ([0x00000000, 0x00000000, 0x00000000, 0x00000000], [0x00000000, 0x00000000],
+     [0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8]),
+    ([0xffffffff, 0xffffffff, 0xffffffff, 0xffffffff], [0xffffffff, 0xffffffff],
+     [0x408f276d, 0x41c83b0e, 0xa20bc7c6, 0x6d5451fd]),
+    ([0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344], [0xa4093822, 0x299f31d0],
+     [0xd16cfe09, 0x94fdcceb, 0x5001e420, 0x24126ea1]),
+]
+
+
+@pytest.mark.parametrize("ctr,key,out", KNOWN_ANSWERS)
+def test_philox_known_answers(ctr, key, out):
+    assert [int(x) for x in she.philox(ctr, key)] == out
 
 
 def test_philox_words_uniform():
