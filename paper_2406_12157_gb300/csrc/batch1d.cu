@@ -38,7 +38,7 @@ k_step1d_batch(const BatchArgs a, const int* __restrict__ list, int count)
     float* sm1 = reinterpret_cast<float*>(smem_raw) + (threadIdx.x >> 5) * (2 * C * 32) + lane;
     float* sm2 = sm1 + C * 32;
 
-    Row1D<float, C, LPR, DIR, SPECIES, true> rowst;
+    Row1D<float, C, LPR, DIR, SPECIES, true, false> rowst;
     rowst.init_vals(d.N, d.r, d.amp2, d.wlo, d.whi, d.stream, d.key0, d.key1, a.stochastic, sl);
     const uint32_t step0 = *a.d_step;
     const int N = d.N;

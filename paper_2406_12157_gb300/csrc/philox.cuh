@@ -14,6 +14,42 @@
 
 namespace she {
 
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;   // Weyl increments of the key schedule
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+// The ten round keys of one key (k0 + i W0, k1 + i W1, i = 0..9), filled on
+// the host and passed inside a __grid_constant__ kernel parameter, so that
+// every round reads its key as a constant operand instead of re-deriving it.
+struct RoundKeys {
+    uint32_t k0[10];
+    uint32_t k1[10];
+};
+
+inline RoundKeys make_round_keys(uint64_t seed)
+{
+    RoundKeys rk;
+    uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
+    for (int i = 0; i < 10; ++i) {
+        rk.k0[i] = k0;
+        rk.k1[i] = k1;
+        k0 += kPhiloxW0;
+        k1 += kPhiloxW1;
+    }
+    return rk;
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const RoundKeys& rk)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c.x;   // 32x32 -> 64
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk.k0[round], (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ rk.k1[round], (uint32_t)p0);
+    }
+    return c;
+}
+
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
 {
 #pragma unroll
@@ -23,8 +59,8 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
         const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
         const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
         c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
+        k0 += kPhiloxW0;
+        k1 += kPhiloxW1;
     }
     return c;
 }

@@ -32,7 +32,10 @@ __device__ __forceinline__ Real face_amp(Real face_value, Real amp2, Real s_heat
     return s_heat * face_value;
 }
 
-template <typename Real, int C, int LPR, bool DIR, bool SPECIES, bool RAGGED>
+// RK: the noise key comes as precomputed round keys (a kernel parameter of
+// the single-problem kernels); otherwise as (key0, key1) (per-instance keys
+// of the batch kernel).
+template <typename Real, int C, int LPR, bool DIR, bool SPECIES, bool RAGGED, bool RK = true>
 struct Row1D {
     static_assert(C % 4 == 0, "cells per lane must be a multiple of 4");
     static_assert(LPR == 4 || LPR == 8 || LPR == 16 || LPR == 32, "segment width");
@@ -42,6 +45,7 @@ struct Row1D {
     bool first_sl, tail_sl;
     Real r, amp2, s_half, wlo, whi, g_wall_amp, g_low_amp;
     uint32_t stream, q0, key0, key1;
+    const RoundKeys* rk;
     int stochastic;
     Real wz[4];
     uint32_t wwin;
@@ -69,6 +73,7 @@ struct Row1D {
         q0 = (uint32_t)(i0 / 4);
         key0 = key0_;
         key1 = key1_;
+        rk = nullptr;
         stochastic = stochastic_;
         wz[0] = wz[1] = wz[2] = wz[3] = Real(0);
         wwin = 0xffffffffu;
@@ -77,6 +82,13 @@ struct Row1D {
     __device__ __forceinline__ void init(const Step1DArgs<Real>& a, int sl, int rho)
     {
         init_vals(a.N, a.r, a.amp2, a.wall_lo, a.wall_hi, a.stream0 + (uint32_t)rho, a.key0, a.key1, a.stochastic, sl);
+        rk = &a.rk;
+    }
+
+    __device__ __forceinline__ uint4 noise_block(uint4 ctr) const
+    {
+        if constexpr (RK) return philox4x32_10(ctr, *rk);
+        else return philox4x32_10(ctr, key0, key1);
     }
 
     __device__ __forceinline__ Real flux(Real lo, Real hi, Real z) const
@@ -113,8 +125,7 @@ struct Row1D {
             const uint32_t win = n / (uint32_t)(4 * WL);
             if (win != wwin) {
                 wwin = win;
-                const uint4 u = philox4x32_10(
-                    make_uint4(0u, win * (uint32_t)WL + (uint32_t)(sl % WL), stream, 2u), key0, key1);
+                const uint4 u = noise_block(make_uint4(0u, win * (uint32_t)WL + (uint32_t)(sl % WL), stream, 2u));
                 box_muller4(u, wz);
             }
             const uint32_t slot = n & 3u;
@@ -133,7 +144,7 @@ struct Row1D {
         for (int g = 0; g < C / 4; ++g) {
             Real z[4] = {Real(0), Real(0), Real(0), Real(0)};
             if (stochastic) {
-                const uint4 u = philox4x32_10(make_uint4(q0 + (uint32_t)g, n, stream, 0u), key0, key1);
+                const uint4 u = noise_block(make_uint4(q0 + (uint32_t)g, n, stream, 0u));
                 box_muller4(u, z);
             }
 #pragma unroll

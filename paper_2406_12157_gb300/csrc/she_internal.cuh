@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/she.h"
+#include "philox.cuh"
 
 namespace she {
 
@@ -38,6 +39,7 @@ struct Step1DArgs {
     Real amp2;            // 2 r eps: squared noise amplitude per unit face value
     Real wall_lo, wall_hi;
     uint32_t key0, key1;
+    RoundKeys rk;         // round keys of (key0, key1)
     uint32_t step0;       // absolute index of the first step of this launch
     int nsteps;
     int K;                // sampling interval
@@ -59,6 +61,7 @@ struct Step2DArgs {
     int tiles;            // bands per realization
     Real r, amp2, ref;
     uint32_t key0, key1, step, stream0;
+    RoundKeys rk;         // round keys of (key0, key1)
     int stochastic;
     int sample;           // this step is a sampling step
 };
@@ -74,6 +77,7 @@ struct Step3DArgs {
     int nx, ny, nz, R;
     Real r, amp2, ref;
     uint32_t key0, key1, step, stream0;
+    RoundKeys rk;         // round keys of (key0, key1)
     int stochastic;
     int sample;
 };

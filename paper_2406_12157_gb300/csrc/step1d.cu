@@ -41,7 +41,7 @@ constexpr int step1d_smem_per_warp() { return 2 * C * 32 * (int)sizeof(Real); }
 
 template <typename Real, int C, int LPR, bool DIR, bool SPECIES, bool RAGGED, int MINB>
 __global__ void __launch_bounds__(kWarpsPerBlock1D * 32, MINB)
-k_step1d(const Step1DArgs<Real> a)
+k_step1d(const __grid_constant__ Step1DArgs<Real> a)
 {
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int RPW = 32 / LPR;
@@ -207,6 +207,7 @@ static cudaError_t launch_fused(Handle& h, uint32_t step0, int nsteps)
     a.wall_hi = (Real)h.prob.wall_hi;
     a.key0 = (uint32_t)(h.prob.seed & 0xffffffffu);
     a.key1 = (uint32_t)(h.prob.seed >> 32);
+    a.rk = make_round_keys(h.prob.seed);
     a.step0 = step0;
     a.nsteps = nsteps;
     a.K = h.K;

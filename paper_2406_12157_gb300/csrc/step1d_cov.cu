@@ -44,7 +44,7 @@ constexpr int cov_smem_bytes(int warps)
 
 template <int C, int LPR, bool DIR, bool SPECIES, bool RAGGED>
 __global__ void __launch_bounds__(32 * LPR, 1)
-k_step1d_cov(const Step1DArgs<float> a, const CovArgs c)
+k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
 {
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int RPW = 32 / LPR;
@@ -331,6 +331,7 @@ cudaError_t launch_step1d_cov(Handle& h, uint32_t step0, int nsteps, bool has_sa
     a.wall_hi = (float)h.prob.wall_hi;
     a.key0 = (uint32_t)(h.prob.seed & 0xffffffffu);
     a.key1 = (uint32_t)(h.prob.seed >> 32);
+    a.rk = make_round_keys(h.prob.seed);
     a.step0 = step0;
     a.nsteps = nsteps;
     a.K = h.K;

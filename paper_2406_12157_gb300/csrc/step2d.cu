@@ -28,7 +28,7 @@ namespace she {
 // 256 x 256 x 256 ensemble (4096 bands of 16 rows) fits in one wave
 template <typename Real, int C, int LPR, bool SPECIES, bool RAGGED>
 __global__ void __launch_bounds__(128, (sizeof(Real) == 4 && C <= 8) ? 7 : 1)
-k_step2d(const Step2DArgs<Real> a)
+k_step2d(const __grid_constant__ Step2DArgs<Real> a)
 {
     static_assert(C % 4 == 0, "cells per lane must be a multiple of 4");
     constexpr unsigned FULL = 0xffffffffu;
@@ -77,7 +77,7 @@ k_step2d(const Step2DArgs<Real> a)
 #pragma unroll
         for (int q = 0; q < C / 4; ++q) {
             Real z[4] = {Real(0), Real(0), Real(0), Real(0)};
-            if (a.stochastic) box_muller4(philox4x32_10(make_uint4(gbase / 4u + (uint32_t)q, n, stream, 0u), a.key0, a.key1), z);
+            if (a.stochastic) box_muller4(philox4x32_10(make_uint4(gbase / 4u + (uint32_t)q, n, stream, 0u), a.rk), z);
 #pragma unroll
             for (int t = 0; t < 4; ++t) g[4 * q + t] = flux(lo[4 * q + t], hi[4 * q + t], z[t]);
         }
@@ -109,7 +109,7 @@ k_step2d(const Step2DArgs<Real> a)
 #pragma unroll
         for (int q = 0; q < C / 4; ++q) {
             Real z[4] = {Real(0), Real(0), Real(0), Real(0)};
-            if (a.stochastic) box_muller4(philox4x32_10(make_uint4(gxbase / 4u + (uint32_t)q, n, stream, 0u), a.key0, a.key1), z);
+            if (a.stochastic) box_muller4(philox4x32_10(make_uint4(gxbase / 4u + (uint32_t)q, n, stream, 0u), a.rk), z);
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 const int j = 4 * q + t;
@@ -229,6 +229,7 @@ static cudaError_t launch2d_real(Handle& h, uint32_t step0, int nsteps)
     a.ref = (Real)h.prob.wall_lo;
     a.key0 = (uint32_t)(h.prob.seed & 0xffffffffu);
     a.key1 = (uint32_t)(h.prob.seed >> 32);
+    a.rk = make_round_keys(h.prob.seed);
     a.stream0 = h.stream0;
     a.stochastic = h.stochastic;
     a.flags = h.d_flags;

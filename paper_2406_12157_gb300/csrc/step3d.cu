@@ -66,7 +66,7 @@ __device__ __forceinline__ void vstore(double* p, const double (&v)[C])
 
 template <typename Real, int C, bool SPECIES>
 __global__ void __launch_bounds__(kY3 * 32, sizeof(Real) == 4 ? 3 : 1)
-k_step3d(const Step3DArgs<Real> a)
+k_step3d(const __grid_constant__ Step3DArgs<Real> a)
 {
     static_assert(C % 4 == 0, "cells per lane must be a multiple of 4");
     constexpr unsigned FULL = 0xffffffffu;
@@ -118,7 +118,7 @@ k_step3d(const Step3DArgs<Real> a)
 #pragma unroll
         for (int q = 0; q < C / 4; ++q) {
             Real z[4] = {Real(0), Real(0), Real(0), Real(0)};
-            if (a.stochastic) box_muller4(philox4x32_10(make_uint4(g0 / 4u + (uint32_t)q, n, stream, 0u), a.key0, a.key1), z);
+            if (a.stochastic) box_muller4(philox4x32_10(make_uint4(g0 / 4u + (uint32_t)q, n, stream, 0u), a.rk), z);
 #pragma unroll
             for (int t = 0; t < 4; ++t) g[4 * q + t] = flux(lo[4 * q + t], hi[4 * q + t], z[t]);
         }
@@ -259,6 +259,7 @@ static cudaError_t launch3d_real(Handle& h, uint32_t step0, int nsteps)
     a.ref = (Real)h.prob.wall_lo;
     a.key0 = (uint32_t)(h.prob.seed & 0xffffffffu);
     a.key1 = (uint32_t)(h.prob.seed >> 32);
+    a.rk = make_round_keys(h.prob.seed);
     a.stream0 = h.stream0;
     a.stochastic = h.stochastic;
     a.flags = h.d_flags;
