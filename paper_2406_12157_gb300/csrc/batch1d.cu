@@ -1,93 +1,36 @@
 // batch1d.cu -- many uneven 1D instances (their own N, kappa, walls, seed)
-// advanced together (Sec. 3, Eq. (3.3) and Eq. (3.8) per instance).
+// advanced together (Sec. 3, Eq. (3.3) and Eq. (3.8) per instance): the
+// host planner of the persistent batch kernel (batch1d_kernel.cuh), its
+// CUDA graph, and the initial condition.
 //
-// Instances are grouped into layout classes by N (the (cells per lane, lanes
-// per segment) table of the single-problem kernel, plus 64 cells x 32 lanes
-// up to 2048 cells); one segment steps one instance for a whole launch,
-// reading its cells, diffusion number, amplitude, walls, key and noise
-// stream from an instance table.  The per-class launches of a step batch are
-// one CUDA graph: the classes are independent branches and a final node
-// advances the device-side step counter every kernel reads, so the graph is
-// replayed unchanged for every batch of the same length.
+// Planning (once, at she_init_batch): every instance gets the layout class
+// of the smallest capacity that holds it; a class's instances are cut into
+// units of 32 / LPR and the units into chunks of one per warp of a block; a
+// chunk costs about (C + 2)^1.1 lane-step slots per step (C cells per lane
+// plus the per-step shuffles), independent of how many of its segments are
+// used.  Chunks are sorted by cost and each goes to the resident block with
+// the least load so far (longest processing time first), which leaves every
+// block within a few per cent of the mean load.  A step
+// batch is one CUDA graph of two nodes: the persistent kernel, then a
+// one-thread kernel that advances the device-side step counter the kernel
+// reads, so the same graph is replayed for every batch of the same length.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
+#include <functional>
+#include <queue>
+#include <utility>
+#include <vector>
 
-#include "philox.cuh"
-#include "row1d.cuh"
-#include "she_internal.cuh"
+#include "batch1d_kernel.cuh"
 
 namespace she {
 
-template <int C, int LPR, bool DIR, bool SPECIES>
-__global__ void __launch_bounds__(kWarpsPerBlock1D * 32)
-k_step1d_batch(const BatchArgs a, const int* __restrict__ list, int count)
+void* batch_kernel_dirichlet(bool species)
 {
-    constexpr unsigned FULL = 0xffffffffu;
-    constexpr int RPW = 32 / LPR;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31;
-    const int sl = lane % LPR;
-    const int warp = blockIdx.x * kWarpsPerBlock1D + (threadIdx.x >> 5);
-    if (warp * RPW >= count) return;
-    const int seg_raw = warp * RPW + lane / LPR;
-    const bool active = seg_raw < count;
-    const int id = list[active ? seg_raw : count - 1];
-    const InstanceDesc d = a.inst[id];
-    float* sm1 = reinterpret_cast<float*>(smem_raw) + (threadIdx.x >> 5) * (2 * C * 32) + lane;
-    float* sm2 = sm1 + C * 32;
-
-    Row1D<float, C, LPR, DIR, SPECIES, true, false> rowst;
-    rowst.init_vals(d.N, d.r, d.amp2, d.wlo, d.whi, d.stream, d.key0, d.key1, a.stochastic, sl);
-    const uint32_t step0 = *a.d_step;
-    const int N = d.N;
-    const int i0 = sl * C;
-    float* row = a.state + d.off;
-    float T[C];
-#pragma unroll
-    for (int j = 0; j < C; ++j) {
-        T[j] = (i0 + j < N) ? row[i0 + j] : 0.0f;
-        sm1[j * 32] = 0.0f;
-        sm2[j * 32] = 0.0f;
-    }
-    const float dref = DIR ? (d.whi - d.wlo) / (float)N : 0.0f;
-    int next_s = first_sample_index(step0, a.relax, a.K, a.nsteps);
-    int nsamp = 0;
-    for (int s = 0; s < a.nsteps; ++s) {
-        rowst.step(T, step0 + (uint32_t)s);
-        if (s == next_s) {
-            next_s += a.K;
-            ++nsamp;
-#pragma unroll
-            for (int j = 0; j < C; ++j) {
-                const float ref = DIR ? fmaf(dref, (float)(i0 + j) + 0.5f, d.wlo) : d.wlo;
-                const float dd = T[j] - ref;
-                sm1[j * 32] += dd;
-                sm2[j * 32] = fmaf(dd, dd, sm2[j * 32]);
-            }
-        }
-    }
-    bool bad = false;
-    if (active) {
-#pragma unroll
-        for (int j = 0; j < C; ++j) {
-            if (i0 + j < N) {
-                row[i0 + j] = T[j];
-                bad |= !finite_any(T[j]);
-            }
-        }
-        if (nsamp > 0) {
-#pragma unroll
-            for (int j = 0; j < C; ++j) {
-                if (i0 + j < N) {
-                    a.acc1[d.off + i0 + j] += (double)sm1[j * 32];
-                    a.acc2[d.off + i0 + j] += (double)sm2[j * 32];
-                }
-            }
-        }
-    }
-    if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.flags, 1);
+    return species ? (void*)k_step1d_batch<true, true> : (void*)k_step1d_batch<true, false>;
 }
 
 __global__ void k_advance_step(uint32_t* d_step, uint32_t n)
@@ -115,42 +58,104 @@ __global__ void k_init_batch(float* state, const InstanceDesc* __restrict__ inst
     }
 }
 
-// classes: code = C * 100 + LPR
-static const int kBatchClasses[] = {404, 408, 416, 432, 3208, 1632, 3232, 6432};
-static const int kBatchClassMaxN[] = {16, 32, 64, 128, 256, 512, 1024, 2048};
+struct BatchClassInfo {
+    int max_n, C, LPR;
+};
 
-int batch_class_of(int N)
+static const BatchClassInfo kBatchClassTable[kNumBatchClasses] = {
+#define SHE_BATCH_ROW(idx, max_n, C, LPR) {max_n, C, LPR},
+    SHE_BATCH_CLASSES(SHE_BATCH_ROW)
+#undef SHE_BATCH_ROW
+};
+
+static int batch_class_of(int N)
 {
     for (int c = 0; c < kNumBatchClasses; ++c)
-        if (N <= kBatchClassMaxN[c]) return c;
+        if (N <= kBatchClassTable[c].max_n) return c;
     return -1;
 }
 
-template <int C, int LPR, bool DIR, bool SP>
-static void* batch_kernel_ptr() { return (void*)k_step1d_batch<C, LPR, DIR, SP>; }
+static void* batch_kernel(bool dir, bool sp) { return dir ? batch_kernel_dirichlet(sp) : batch_kernel_periodic(sp); }
 
-template <bool DIR, bool SP>
-static void* batch_kernel_for(int cls, int& C, int& LPR)
+static int batch_smem_bytes() { return kBatchWarps * 2 * kBatchMaxC * 32 * (int)sizeof(float); }
+
+cudaError_t setup_batch(Handle& h, const std::vector<InstanceDesc>& desc)
 {
-    const int code = kBatchClasses[cls];
-    C = code / 100;
-    LPR = code % 100;
-    switch (code) {
-    case 404: return batch_kernel_ptr<4, 4, DIR, SP>();
-    case 408: return batch_kernel_ptr<4, 8, DIR, SP>();
-    case 416: return batch_kernel_ptr<4, 16, DIR, SP>();
-    case 432: return batch_kernel_ptr<4, 32, DIR, SP>();
-    case 3208: return batch_kernel_ptr<32, 8, DIR, SP>();
-    case 1632: return batch_kernel_ptr<16, 32, DIR, SP>();
-    case 3232: return batch_kernel_ptr<32, 32, DIR, SP>();
-    default: return batch_kernel_ptr<64, 32, DIR, SP>();
+    // instances by class
+    std::vector<std::vector<int>> byc(kNumBatchClasses);
+    for (size_t i = 0; i < desc.size(); ++i) {
+        const int c = batch_class_of(desc[i].N);
+        if (c < 0) return cudaErrorInvalidValue;
+        byc[(size_t)c].push_back((int)i);
     }
-}
-
-static void* batch_kernel(bool dir, bool sp, int cls, int& C, int& LPR)
-{
-    if (dir) return sp ? batch_kernel_for<true, true>(cls, C, LPR) : batch_kernel_for<true, false>(cls, C, LPR);
-    return sp ? batch_kernel_for<false, true>(cls, C, LPR) : batch_kernel_for<false, false>(cls, C, LPR);
+    // units, the instance list (unit by unit), and chunks of kBatchWarps
+    // units of one class; a chunk costs (C + 2)^1.1 lane-step slots per step
+    // (measured: the per-cell cost grows slowly with the unrolled row length)
+    std::vector<int> list;
+    std::vector<BatchUnit> chunks;          // [nchunks][kBatchWarps]
+    std::vector<double> cost;
+    for (int c = 0; c < kNumBatchClasses; ++c) {
+        const int rpw = 32 / kBatchClassTable[c].LPR;
+        const auto& ids = byc[(size_t)c];
+        const size_t nunits = (ids.size() + (size_t)rpw - 1) / (size_t)rpw;
+        for (size_t u0 = 0; u0 < nunits; u0 += kBatchWarps) {
+            for (int w = 0; w < kBatchWarps; ++w) {
+                BatchUnit u = {c, (int)list.size(), 0, 0};
+                const size_t k = (u0 + (size_t)w) * (size_t)rpw;
+                if (k < ids.size()) {
+                    u.count = (int)std::min<size_t>((size_t)rpw, ids.size() - k);
+                    for (int t = 0; t < u.count; ++t) list.push_back(ids[k + (size_t)t]);
+                }
+                chunks.push_back(u);
+            }
+            cost.push_back(std::pow((double)(kBatchClassTable[c].C + 2), 1.1));
+        }
+    }
+    const size_t nchunks = cost.size();
+    // resident blocks of the persistent kernel
+    const bool dir = h.prob.bc == SHE_DIRICHLET, sp = h.prob.equation == SHE_SPECIES;
+    void* fn = batch_kernel(dir, sp);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, batch_smem_bytes());
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBatchWarps * 32,
+                                                           (size_t)batch_smem_bytes())) != cudaSuccess)
+        return e;
+    const int blocks = (int)std::max<size_t>(1, std::min<size_t>((size_t)sms * (size_t)std::max(1, per_sm), nchunks));
+    // longest chunk first onto the least loaded block
+    std::vector<int> order(nchunks);
+    for (size_t i = 0; i < nchunks; ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[(size_t)x] > cost[(size_t)y]; });
+    std::priority_queue<std::pair<double, int>, std::vector<std::pair<double, int>>,
+                        std::greater<std::pair<double, int>>> heap;
+    for (int b = 0; b < blocks; ++b) heap.push({0.0, b});
+    std::vector<std::vector<int>> per_block((size_t)blocks);
+    for (int k : order) {
+        auto top = heap.top();
+        heap.pop();
+        per_block[(size_t)top.second].push_back(k);
+        heap.push({top.first + cost[(size_t)k], top.second});
+    }
+    std::vector<BatchUnit> bunits;
+    std::vector<int> bbegin;
+    for (int b = 0; b < blocks; ++b) {
+        bbegin.push_back((int)(bunits.size() / kBatchWarps));
+        for (int k : per_block[(size_t)b])
+            for (int w = 0; w < kBatchWarps; ++w) bunits.push_back(chunks[(size_t)k * kBatchWarps + (size_t)w]);
+    }
+    bbegin.push_back((int)(bunits.size() / kBatchWarps));
+    h.batch_blocks = blocks;
+    e = cudaMalloc(&h.d_class_list, std::max<size_t>(1, list.size()) * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&h.d_units, std::max<size_t>(1, bunits.size()) * sizeof(BatchUnit));
+    if (e == cudaSuccess) e = cudaMalloc(&h.d_block_begin, bbegin.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(h.d_class_list, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h.d_units, bunits.data(), bunits.size() * sizeof(BatchUnit), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h.d_block_begin, bbegin.data(), bbegin.size() * sizeof(int), cudaMemcpyHostToDevice);
+    return e;
 }
 
 // Build (once per step-batch length) and launch the graph of one step batch.
@@ -169,6 +174,9 @@ cudaError_t launch_batch(Handle& h, int nsteps)
         bg->args.acc2 = h.d_acc2;
         bg->args.flags = h.d_flags;
         bg->args.inst = h.d_inst;
+        bg->args.list = h.d_class_list;
+        bg->args.units = h.d_units;
+        bg->args.block_begin = h.d_block_begin;
         bg->args.d_step = h.d_step;
         bg->args.nsteps = nsteps;
         bg->args.K = h.K;
@@ -177,30 +185,17 @@ cudaError_t launch_batch(Handle& h, int nsteps)
         cudaGraph_t graph;
         e = cudaGraphCreate(&graph, 0);
         if (e != cudaSuccess) return e;
-        std::vector<cudaGraphNode_t> nodes;
         const bool dir = h.prob.bc == SHE_DIRICHLET, sp = h.prob.equation == SHE_SPECIES;
-        for (int c = 0; c < kNumBatchClasses; ++c) {
-            if (h.class_count[c] == 0) continue;
-            int C = 0, LPR = 0;
-            void* fn = batch_kernel(dir, sp, c, C, LPR);
-            const int rpw = 32 / LPR;
-            const int warps = (h.class_count[c] + rpw - 1) / rpw;
-            const int smem = kWarpsPerBlock1D * 2 * C * 32 * (int)sizeof(float);
-            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            if (e != cudaSuccess) break;
-            bg->lists[c] = h.d_class_list + h.class_start[c];
-            bg->counts[c] = h.class_count[c];
-            void* params[3] = {(void*)&bg->args, (void*)&bg->lists[c], (void*)&bg->counts[c]};
+        cudaGraphNode_t knode;
+        {
+            void* params[1] = {(void*)&bg->args};
             cudaKernelNodeParams kp = {};
-            kp.func = fn;
-            kp.gridDim = dim3((unsigned)((warps + kWarpsPerBlock1D - 1) / kWarpsPerBlock1D));
-            kp.blockDim = dim3(kWarpsPerBlock1D * 32);
-            kp.sharedMemBytes = (unsigned)smem;
+            kp.func = batch_kernel(dir, sp);
+            kp.gridDim = dim3((unsigned)h.batch_blocks);
+            kp.blockDim = dim3(kBatchWarps * 32);
+            kp.sharedMemBytes = (unsigned)batch_smem_bytes();
             kp.kernelParams = params;
-            cudaGraphNode_t node;
-            e = cudaGraphAddKernelNode(&node, graph, nullptr, 0, &kp);
-            if (e != cudaSuccess) break;
-            nodes.push_back(node);
+            e = cudaGraphAddKernelNode(&knode, graph, nullptr, 0, &kp);
         }
         if (e == cudaSuccess) {
             uint32_t n = (uint32_t)nsteps;
@@ -211,8 +206,8 @@ cudaError_t launch_batch(Handle& h, int nsteps)
             kp.blockDim = dim3(32);
             kp.kernelParams = params;
             cudaGraphNode_t node;
-            e = cudaGraphAddKernelNode(&node, graph, nodes.empty() ? nullptr : nodes.data(), nodes.size(), &kp);
-            bg->kernels = (int)nodes.size() + 1;
+            e = cudaGraphAddKernelNode(&node, graph, &knode, 1, &kp);
+            bg->kernels = 2;
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&bg->exec, graph, 0);
         cudaGraphDestroy(graph);

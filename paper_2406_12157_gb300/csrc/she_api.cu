@@ -143,9 +143,13 @@ void release(Handle* h)
     cudaFree(h->d_inst);
     cudaFree(h->d_step);
     cudaFree(h->d_class_list);
+    cudaFree(h->d_units);
+    cudaFree(h->d_block_begin);
     h->d_inst = nullptr;
     h->d_step = nullptr;
     h->d_class_list = nullptr;
+    h->d_units = nullptr;
+    h->d_block_begin = nullptr;
     h->d_cov_partial = h->d_cov_red = nullptr;
     h->d_state = h->d_state2 = nullptr;
     h->d_acc1 = h->d_acc2 = h->d_face = h->d_red = nullptr;
@@ -355,7 +359,6 @@ she_status she_init_batch(const she_params* p, int64_t count, she_handle** out)
     if (!h) return SHE_ERR_OOM;
     std::vector<she::InstanceDesc> desc((size_t)count);
     std::vector<float> sigma((size_t)count);
-    std::vector<std::vector<int>> lists(she::kNumBatchClasses);
     int64_t total = 0;
     std::string msg;
     she_status st = SHE_OK;
@@ -389,7 +392,6 @@ she_status she_init_batch(const she_params* p, int64_t count, she_handle** out)
         const double mid = 0.5 * (pr.wall_lo + pr.wall_hi);
         sigma[(size_t)i] = (float)(pr.equation == SHE_HEAT ? std::sqrt(pr.eps) * std::fabs(mid)
                                                            : std::sqrt(pr.eps * std::fabs(mid)));
-        lists[(size_t)she::batch_class_of(d.N)].push_back((int)i);
         total += d.N;
         if (i == 0) h->prob = pr;
     }
@@ -410,12 +412,6 @@ she_status she_init_batch(const she_params* p, int64_t count, she_handle** out)
     h->perturb_ic = p[0].perturb_ic ? 1 : 0;
     h->steps_per_launch = p[0].steps_per_launch;
     h->stream = (cudaStream_t)p[0].stream;
-    std::vector<int> flat;
-    for (int c = 0; c < she::kNumBatchClasses; ++c) {
-        h->class_start[c] = (int)flat.size();
-        h->class_count[c] = (int)lists[(size_t)c].size();
-        flat.insert(flat.end(), lists[(size_t)c].begin(), lists[(size_t)c].end());
-    }
     for (int64_t i = 0; i < count; ++i) {
         h->inst_off.push_back(desc[(size_t)i].off);
         h->inst_n.push_back(desc[(size_t)i].N);
@@ -431,11 +427,10 @@ she_status she_init_batch(const she_params* p, int64_t count, she_handle** out)
     if (e == cudaSuccess) e = cudaMalloc(&h->d_red, h->red_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_inst, desc.size() * sizeof(she::InstanceDesc));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_step, sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_class_list, flat.size() * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&d_sigma, sigma.size() * sizeof(float));
     if (e == cudaSuccess)
         e = cudaMemcpy(h->d_inst, desc.data(), desc.size() * sizeof(she::InstanceDesc), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(h->d_class_list, flat.data(), flat.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = she::setup_batch(*h, desc);
     if (e == cudaSuccess) e = cudaMemcpy(d_sigma, sigma.data(), sigma.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(h->d_step, 0, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_acc1, 0, (size_t)total * sizeof(double), h->stream);

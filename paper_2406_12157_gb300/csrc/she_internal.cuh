@@ -114,12 +114,24 @@ struct InstanceDesc {
     uint32_t stream;      // noise stream (counter word 2)
 };
 
+// A work unit of the batch kernel: up to 32 / LPR instances of one layout
+// class, stepped together by one warp (one segment each).
+struct BatchUnit {
+    int cls;              // layout class (index into the class table of batch1d)
+    int first;            // first entry of the unit's instances in the instance list
+    int count;            // instances in the unit (1 .. 32 / LPR)
+    int pad;
+};
+
 struct BatchArgs {
     float* state;         // packed [total cells]
     double* acc1;
     double* acc2;
     int* flags;
     const InstanceDesc* inst;
+    const int* list;          // instance ids, unit by unit
+    const BatchUnit* units;   // [chunks][kBatchWarps]: chunk k runs one unit per warp of a block
+    const int* block_begin;   // chunks of block b: [block_begin[b], block_begin[b + 1])
     const uint32_t* d_step;   // absolute index of the first step of the launch
     int nsteps;
     int K;
@@ -127,15 +139,15 @@ struct BatchArgs {
     int stochastic;
 };
 
-constexpr int kNumBatchClasses = 8;
+constexpr int kNumBatchClasses = 18;
+constexpr int kBatchMaxC = 64;        // cells per lane of the largest class
+constexpr int kBatchWarps = 8;        // warps per block of the batch kernel (one block per SM)
 
 struct BatchGraph {
     int nsteps = 0;
     int kernels = 0;
     cudaGraphExec_t exec = nullptr;
     BatchArgs args;
-    const int* lists[kNumBatchClasses];
-    int counts[kNumBatchClasses];
 };
 
 // Extra arguments of the fused covariance kernel.
@@ -180,9 +192,10 @@ struct Handle {
     int64_t instances = 1;
     InstanceDesc* d_inst = nullptr;
     uint32_t* d_step = nullptr;        // device-side step counter read by the batch kernels
-    int* d_class_list = nullptr;       // instance ids grouped by layout class
-    int class_start[kNumBatchClasses] = {0};
-    int class_count[kNumBatchClasses] = {0};
+    int* d_class_list = nullptr;       // instance ids, unit by unit
+    BatchUnit* d_units = nullptr;      // work units, [chunks][kBatchWarps]
+    int* d_block_begin = nullptr;      // [batch_blocks + 1]
+    int batch_blocks = 0;              // resident blocks of the persistent batch kernel
     std::vector<BatchGraph> batch_graphs;
     std::vector<int64_t> inst_off;     // host copies for the statistics
     std::vector<int> inst_n;
@@ -215,7 +228,9 @@ cudaError_t launch_axes_syrk(Handle& h);
 cudaError_t launch_sk2d_tables(Handle& h);
 cudaError_t launch_sk2d(Handle& h);
 cudaError_t launch_sk2d_flush(Handle& h);
-int batch_class_of(int N);
+cudaError_t setup_batch(Handle& h, const std::vector<InstanceDesc>& desc);
+void* batch_kernel_dirichlet(bool species);
+void* batch_kernel_periodic(bool species);
 cudaError_t launch_batch(Handle& h, int nsteps);
 cudaError_t launch_init_batch(Handle& h, const float* d_sigma);
 void destroy_batch_graphs(Handle& h);
