@@ -119,13 +119,21 @@ WORKLOADS = {
               "zero-sum perturbation, 256 realizations, FP32, moments and the full 2D S(k) "
               "(two-stage DFT-as-GEMM on tcgen05) every 10 steps after 1e4"),
         chunk=1000, ops=2 * (25.0 + 5.5 + 7.0) + 9.0, bytes=8.0 + 16.0 / 10,
-        kernel="k_step2d<float,8,32,species>"),
+        kernel="k_step2d<float,8,32,species>",
+        # per realization and sample: row DFT (ny x nx x nx MAC) + column DFTs
+        # (2 x ny x ny x nx MAC), 3 split products, 2 flop per MAC
+        stats_kernel="k_sk2d", stats_flop=lambda p: 3 * 2 * (p["n"][1] * p["n"][0] ** 2
+                                                           + 2 * p["n"][1] ** 2 * p["n"][0])),
     "cube_3d": dict(
         make=lambda W: W.cube_3d(want_sk=2),
         desc=("3D SHE 256^3 periodic, T0=1, r=0.1, eps=1e-3, 8 realizations, FP32, HBM-streaming "
               "stencil, moments and S(k) along x, y, z (line covariance on tcgen05) every 10 steps"),
         chunk=100, ops=3 * (25.0 + 5.5 + 4.0) + 11.0, bytes=8.0 + 16.0 / 10,
-        kernel="k_step3d<float,8,heat>"),
+        kernel="k_step3d<float,8,heat>",
+        # per realization and sample: for each axis a SYRK over all lines
+        # (cells / n_a lines x n_a^2 MAC), 3 split products, 2 flop per MAC
+        stats_kernel="k_axes_syrk", stats_flop=lambda p: 3 * 2 * sum(
+            (p["n"][0] * p["n"][1] * p["n"][2] // p["n"][a]) * p["n"][a] ** 2 for a in range(3))),
     "batched_rods": dict(
         make=lambda W: W.batched_rods(count=10_000, seed=0),
         desc=("10,000 uneven 1D SHE rods, N log-uniform in [16, 2048], kappa U[0.5, 2], walls U[1, 3], "
@@ -234,6 +242,7 @@ def run_ours(args):
           for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
+    sim.profile(True)            # event pair around every library launch, on its stream
     barrier()
     t_wall0 = time.perf_counter()
     for k in range(args.steps):
@@ -246,6 +255,8 @@ def run_ours(args):
     barrier()
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
+    prof = sim.profile_read()
+    sim.profile(False)
     launches = sim.launches() - launches0
     ms = sum(a.elapsed_time(b) for a, b in ev)
     if dist is not None:
@@ -320,20 +331,37 @@ def run_ours(args):
             dist.destroy_process_group()
         return
     peaks, peak_src = _peaks()
-    cu_per_launch = cu_per_step * args.steps / max(1, launches)
-    per_launch_ms = ms / max(1, launches)
+    # the dominant (step) kernel alone: its launches and their summed device
+    # time, from the event pairs the library recorded in the timed region
+    step_launches = max(1, prof["step_launches"])
+    cu_per_launch = cu_per_step * args.steps / step_launches
+    per_launch_ms = prof["step_ms"] / step_launches if prof["step_launches"] else ms / max(1, launches)
     ops_per_launch = cu_per_launch * wl["ops"]
     achieved = ops_per_launch / (per_launch_ms / 1e3) / 1e12          # Tops/s (lane-ops)
     peak = 128 * 152 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
             "unit": "Tops/s", "frac": round(achieved / peak, 4), "traffic": None,
             "kernel": wl["kernel"], "ops_per_cell_update": wl["ops"],
+            "launches": prof["step_launches"], "ms_per_launch": round(per_launch_ms, 5),
+            "cell_updates_per_launch": cu_per_launch,
+            "share_of_timed_region": round(prof["step_ms"] / ms, 4) if ms > 0 else None,
             "peak_source": "128 lane-ops/clk/SM x 152 SMs x max SM clock (%s)" % peak_src}
     if wl["bytes"]:
         gbs = cu_per_launch * wl["bytes"] / (per_launch_ms / 1e3) / 1e9
         roof["hbm"] = {"achieved": round(gbs, 1), "peak": peaks.get("hbm_gbs", 6800.0),
                        "unit": "GB/s", "frac": round(gbs / peaks.get("hbm_gbs", 6800.0), 4),
                        "bytes_per_cell_update": wl["bytes"]}
+    if prof["stats_launches"] and wl.get("stats_flop"):
+        # tensor-core statistics kernels (S(k)), one region per sampling step
+        flop = wl["stats_flop"](p) * (R if not batch else 1)
+        tf = flop / (prof["stats_ms"] / prof["stats_launches"] / 1e3) / 1e12
+        bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0))
+        roof["stats"] = {"bound": "tensor", "kernel": wl["stats_kernel"], "achieved": round(tf, 2),
+                         "peak": bf16, "unit": "TFLOP/s", "frac": round(tf / bf16, 4),
+                         "flop_per_launch": flop, "launches": prof["stats_launches"],
+                         "ms_per_launch": round(prof["stats_ms"] / prof["stats_launches"], 5),
+                         "share_of_timed_region": round(prof["stats_ms"] / ms, 4) if ms > 0 else None,
+                         "peak_source": "bf16_tflops_sustained (%s); the BF16x3 split counts 3 products" % peak_src}
     cpu = None
     if not args.no_cpu_baseline and world >= 1:
         rate, cores, sample = oracle_sample_rate(p)

@@ -296,6 +296,23 @@ she_status she_wait_probe(uint32_t max_tries);
  * benchmark's launch accounting). */
 int64_t she_launch_count(const she_handle* h);
 
+/* Per-kernel device timing, a measurement hook with no counterpart in the
+ * paper.  she_profile(h, 1) starts recording a CUDA event pair on the
+ * handle's stream around every kernel launch (or graph launch) that
+ * she_step_n issues, tagged SHE_PROF_STEP for the step kernels (the fused 1D
+ * kernels and the plain form, the 2D/3D streaming kernels, the batch graph)
+ * or SHE_PROF_STATS for the statistics kernels run between steps (S(k),
+ * moment flushes); she_profile(h, 0) stops and discards what was recorded.
+ * The events add a few microseconds per launch.
+ * she_profile_read synchronizes the handle's stream and writes, per tag, the
+ * summed device time in milliseconds and the number of timed launches since
+ * profiling started or was last read, then clears them.  Any output pointer
+ * may be NULL.  Errors: SHE_ERR_INVALID_ARG (NULL handle), SHE_ERR_CUDA. */
+enum { SHE_PROF_STEP = 0, SHE_PROF_STATS = 1 };
+she_status she_profile(she_handle* h, int enable);
+she_status she_profile_read(she_handle* h, double* step_ms, int64_t* step_launches, double* stats_ms,
+                            int64_t* stats_launches);
+
 #ifdef __cplusplus
 }
 #endif

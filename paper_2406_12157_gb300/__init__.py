@@ -21,7 +21,8 @@ from ._abi import (LibraryMissing, SHE_DIRICHLET, SHE_FE, SHE_FP32, SHE_FP64, SH
 __all__ = ["SheError", "LibraryMissing", "params_from_problem", "she_init", "she_init_batch",
            "she_step_n", "she_get_sizes", "she_stats", "she_reset_stats", "she_get_state",
            "she_set_state", "she_get_state_device", "she_set_state_device", "she_last_error",
-           "she_free", "she_noise_probe", "she_launch_count", "she_syrk_probe", "Simulation", "BatchSimulation", "lib"]
+           "she_free", "she_noise_probe", "she_launch_count", "she_syrk_probe", "she_profile",
+           "she_profile_read", "Simulation", "BatchSimulation", "lib"]
 
 
 class SheError(RuntimeError):
@@ -194,6 +195,21 @@ def she_launch_count(h):
     return int(lib().she_launch_count(h))
 
 
+def she_profile(h, enable):
+    _check(lib().she_profile(h, 1 if enable else 0), h, "she_profile")
+
+
+def she_profile_read(h):
+    """Device time (ms) and launch counts of the step and statistics kernels
+    timed since profiling started or was last read."""
+    sm, sn = ctypes.c_double(), ctypes.c_int64()
+    tm, tn = ctypes.c_double(), ctypes.c_int64()
+    _check(lib().she_profile_read(h, ctypes.byref(sm), ctypes.byref(sn), ctypes.byref(tm), ctypes.byref(tn)),
+           h, "she_profile_read")
+    return {"step_ms": sm.value, "step_launches": int(sn.value), "stats_ms": tm.value,
+            "stats_launches": int(tn.value)}
+
+
 def she_noise_probe(seed, c0, c1, c2, c3, count):
     """Raw Philox words and Box-Muller normals (FP64 and FP32) from the
     device generator for counters (c0 + k, c1, c2, c3), k < count."""
@@ -245,6 +261,12 @@ class BatchSimulation:
     def launches(self):
         return she_launch_count(self.h)
 
+    def profile(self, enable=True):
+        she_profile(self.h, enable)
+
+    def profile_read(self):
+        return she_profile_read(self.h)
+
     def close(self):
         she_free(self.h)
 
@@ -286,6 +308,12 @@ class Simulation:
 
     def launches(self):
         return she_launch_count(self.h)
+
+    def profile(self, enable=True):
+        she_profile(self.h, enable)
+
+    def profile_read(self):
+        return she_profile_read(self.h)
 
     def close(self):
         she_free(self.h)

@@ -34,7 +34,8 @@ SHE_KERNEL_AUTO, SHE_KERNEL_PLAIN = 0, 1
 EXPORTS = ["she_init", "she_init_batch", "she_step_n", "she_get_sizes", "she_stats",
            "she_reset_stats", "she_get_state", "she_set_state", "she_get_state_device",
            "she_set_state_device", "she_last_error", "she_free", "she_noise_probe",
-           "she_launch_count", "she_syrk_probe", "she_step_plain_noalloc", "she_wait_probe"]
+           "she_launch_count", "she_syrk_probe", "she_step_plain_noalloc", "she_wait_probe",
+           "she_profile", "she_profile_read"]
 
 
 class she_params(ctypes.Structure):
@@ -156,6 +157,11 @@ def load(path=None):
     L.she_wait_probe.restype = ctypes.c_int
     L.she_launch_count.argtypes = [H]
     L.she_launch_count.restype = ctypes.c_int64
+    L.she_profile.argtypes = [H, ctypes.c_int]
+    L.she_profile.restype = ctypes.c_int
+    L.she_profile_read.argtypes = [H, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+    L.she_profile_read.restype = ctypes.c_int
     if path is None:
         _LIB = L
     return L

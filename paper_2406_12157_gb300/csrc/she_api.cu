@@ -140,6 +140,9 @@ void release(Handle* h)
     h->d_sk_partial = nullptr;
     h->d_sk_acc = nullptr;
     she::destroy_batch_graphs(*h);
+    for (cudaEvent_t ev : h->prof_events) cudaEventDestroy(ev);
+    h->prof_events.clear();
+    h->prof_tags.clear();
     cudaFree(h->d_inst);
     cudaFree(h->d_step);
     cudaFree(h->d_class_list);
@@ -462,17 +465,26 @@ she_status she_step_n(she_handle* hh, uint64_t n)
         int chunk = (int)std::min<uint64_t>(left, (uint64_t)spl);
         cudaError_t e;
         const int64_t ns = samples_in(h->step, (uint64_t)chunk, h->K, h->relax);
-        if (h->is_batch) e = she::launch_batch(*h, chunk);
-        else if (h->prob.dim == 2) e = she::launch_step2d(*h, (uint32_t)h->step, chunk);
-        else if (h->prob.dim == 3) e = she::launch_step3d(*h, (uint32_t)h->step, chunk);
-        else if (h->kernel == SHE_KERNEL_PLAIN) e = she::launch_step1d_plain(*h, (uint32_t)h->step, chunk);
-        else if (h->want_cov) e = she::launch_step1d_cov(*h, (uint32_t)h->step, chunk, ns > 0);
-        else e = she::launch_step1d(*h, (uint32_t)h->step, chunk);
-        if (e != cudaSuccess) return cuda_fail(h, e, "she_step_n");
+        if (h->prob.dim == 2 && !h->is_batch) e = she::launch_step2d(*h, (uint32_t)h->step, chunk);
+        else if (h->prob.dim == 3 && !h->is_batch) e = she::launch_step3d(*h, (uint32_t)h->step, chunk);
+        else {
+            // 1D and batch: the chunk is one launch (or one graph, or the
+            // plain form's launches), timed as one step region
+            she::prof_mark(*h, SHE_PROF_STEP);
+            if (h->is_batch) e = she::launch_batch(*h, chunk);
+            else if (h->kernel == SHE_KERNEL_PLAIN) e = she::launch_step1d_plain(*h, (uint32_t)h->step, chunk);
+            else if (h->want_cov) e = she::launch_step1d_cov(*h, (uint32_t)h->step, chunk, ns > 0);
+            else e = she::launch_step1d(*h, (uint32_t)h->step, chunk);
+        }
+        if (e != cudaSuccess) {
+            she::prof_close(*h);
+            return cuda_fail(h, e, "she_step_n");
+        }
         h->samples_per_real += ns;
         h->step += (uint64_t)chunk;
         left -= (uint64_t)chunk;
     }
+    she::prof_close(*h);
     return SHE_OK;
 }
 
@@ -894,6 +906,43 @@ int64_t she_launch_count(const she_handle* hh)
 {
     const Handle* h = reinterpret_cast<const Handle*>(hh);
     return h ? h->launches : -1;
+}
+
+she_status she_profile(she_handle* hh, int enable)
+{
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return SHE_ERR_INVALID_ARG;
+    h->prof_on = enable != 0;
+    h->prof_tags.clear();
+    h->prof_open = -1;
+    h->prof_count[0] = h->prof_count[1] = 0;
+    return SHE_OK;
+}
+
+she_status she_profile_read(she_handle* hh, double* step_ms, int64_t* step_launches, double* stats_ms,
+                            int64_t* stats_launches)
+{
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return SHE_ERR_INVALID_ARG;
+    she::prof_close(*h);
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "she_profile_read");
+    double ms[2] = {0.0, 0.0};
+    for (size_t i = 1; i < h->prof_tags.size(); ++i) {
+        const int tag = h->prof_tags[i];
+        if (tag < 0 || tag > 1) continue;
+        float t = 0.0f;
+        e = cudaEventElapsedTime(&t, h->prof_events[i - 1], h->prof_events[i]);
+        if (e != cudaSuccess) return cuda_fail(h, e, "she_profile_read");
+        ms[tag] += (double)t;
+    }
+    if (step_ms) *step_ms = ms[0];
+    if (step_launches) *step_launches = h->prof_count[0];
+    if (stats_ms) *stats_ms = ms[1];
+    if (stats_launches) *stats_launches = h->prof_count[1];
+    h->prof_tags.clear();
+    h->prof_count[0] = h->prof_count[1] = 0;
+    return SHE_OK;
 }
 
 }  // extern "C"

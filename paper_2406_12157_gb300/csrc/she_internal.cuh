@@ -210,8 +210,56 @@ struct Handle {
     double* d_axes_partial = nullptr;  // [dim][cov_ctas][256*256] per-axis line covariances
     double* d_axes_red = nullptr;      // [dim][256*256] reduced
     size_t red_bytes = 0;
+    // per-kernel device timing (she_profile): a timeline of events on the
+    // stream; prof_tags[i] is the kind of the interval that event i closes
+    // (-1: not the library's), recorded only where the kind changes
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_events;   // pool, reused after each read
+    std::vector<int> prof_tags;
+    int prof_open = -1;                     // kind of the interval now open
+    int64_t prof_count[2] = {0, 0};         // launches per kind
     std::string err;
 };
+
+// Timeline helpers of she_profile.  prof_mark(h, kind) precedes every launch
+// of the given kind (SHE_PROF_STEP / SHE_PROF_STATS); an event is recorded
+// only when the kind differs from the open interval's.  prof_close ends the
+// open interval (at the end of every she_step_n, so that work the caller
+// enqueues between calls is never counted).  Event-pool failures turn
+// profiling off rather than failing the step.
+inline void prof_record(Handle& h, int closing_kind)
+{
+    const size_t i = h.prof_tags.size();
+    if (h.prof_events.size() <= i) {
+        cudaEvent_t ev;
+        if (cudaEventCreate(&ev) != cudaSuccess) {
+            h.prof_on = false;
+            return;
+        }
+        h.prof_events.push_back(ev);
+    }
+    if (cudaEventRecord(h.prof_events[i], h.stream) != cudaSuccess) {
+        h.prof_on = false;
+        return;
+    }
+    h.prof_tags.push_back(closing_kind);
+}
+
+inline void prof_mark(Handle& h, int kind)
+{
+    if (!h.prof_on) return;
+    h.prof_count[kind] += 1;
+    if (h.prof_open == kind) return;
+    prof_record(h, h.prof_open);
+    h.prof_open = kind;
+}
+
+inline void prof_close(Handle& h)
+{
+    if (!h.prof_on || h.prof_open < 0) return;
+    prof_record(h, h.prof_open);
+    h.prof_open = -1;
+}
 
 // Launchers (return cudaSuccess or the launch error).
 cudaError_t launch_init_state(Handle& h);

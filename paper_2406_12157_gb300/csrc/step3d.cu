@@ -277,16 +277,19 @@ static cudaError_t launch3d_real(Handle& h, uint32_t step0, int nsteps)
             a.m1 = (Real*)h.d_m1;
             a.m2 = (Real*)h.d_m2;
         }
+        prof_mark(h, SHE_PROF_STEP);
         cudaError_t e = sp ? launch3d_sp<Real, true>(a, h.stream) : launch3d_sp<Real, false>(a, h.stream);
         h.launches += 1;
         if (e != cudaSuccess) return e;
         std::swap(h.d_state, h.d_state2);
         if (a.sample && (h.want_sk & SHE_SK_AXES)) {
+            prof_mark(h, SHE_PROF_STATS);
             e = launch_axes_syrk(h);
             if (e != cudaSuccess) return e;
         }
         if (a.sample && sizeof(Real) == 4) {
             if (++h.partial_samples >= 256) {
+                prof_mark(h, SHE_PROF_STATS);
                 e = launch_flush_moments(h);
                 if (e != cudaSuccess) return e;
             }

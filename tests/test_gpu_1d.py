@@ -239,6 +239,27 @@ def test_zero_steps_is_a_no_op(dim):
         assert np.array_equal(x0, x1)
 
 
+def test_profile_times_step_kernels():
+    p = _prob(256, "dirichlet", "heat", (1.0, 2.0), precision="fp32", realizations=64, relax_steps=0)
+    with S.Simulation(p, steps_per_launch=500) as sim:
+        sim.profile(True)
+        sim.step(2000)
+        pr = sim.profile_read()
+        assert pr["step_launches"] == 4 and pr["step_ms"] > 0.0
+        assert pr["stats_launches"] == 0
+        assert sim.profile_read()["step_launches"] == 0      # read clears
+        sim.profile(False)
+        sim.step(500)
+        assert sim.profile_read()["step_launches"] == 0
+    p2 = W.species_2d(n=(64, 32, 1), realizations=2, relax_steps=0, stats_interval=5, want_sk=1)
+    with S.Simulation(p2) as sim:
+        sim.profile(True)
+        sim.step(20)
+        pr = sim.profile_read()
+        assert pr["step_launches"] == 20 and pr["stats_launches"] == 4
+        assert pr["step_ms"] > 0.0 and pr["stats_ms"] > 0.0
+
+
 def test_nonfinite_state_is_reported():
     p = _prob(32, "dirichlet", "heat", (1.0, 1.0), precision="fp32")
     with S.Simulation(p) as sim:
