@@ -121,9 +121,10 @@ WORKLOADS = {
         chunk=1000, ops=2 * (25.0 + 5.5 + 7.0) + 9.0, bytes=8.0 + 16.0 / 10,
         kernel="k_step2d<float,8,32,species>",
         # per realization and sample: row DFT (ny x nx x nx MAC) + column DFTs
-        # (2 x ny x ny x nx MAC), 3 split products, 2 flop per MAC
+        # for the 128 rows ky < 128 (2 x 128 x ny x nx MAC; the other rows
+        # follow from the real-field symmetry), 3 split products, 2 flop per MAC
         stats_kernel="k_sk2d", stats_flop=lambda p: 3 * 2 * (p["n"][1] * p["n"][0] ** 2
-                                                           + 2 * p["n"][1] ** 2 * p["n"][0])),
+                                                           + 2 * 128 * p["n"][1] * p["n"][0])),
     "cube_3d": dict(
         make=lambda W: W.cube_3d(want_sk=2),
         desc=("3D SHE 256^3 periodic, T0=1, r=0.1, eps=1e-3, 8 realizations, FP32, HBM-streaming "

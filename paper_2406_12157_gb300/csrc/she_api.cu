@@ -135,6 +135,8 @@ void release(Handle* h)
     cudaFree(h->d_sk_c);
     cudaFree(h->d_sk_s);
     cudaFree(h->d_sk_partial);
+    cudaFree(h->d_sk_scratch);
+    h->d_sk_scratch = nullptr;
     cudaFree(h->d_sk_acc);
     h->d_sk_w = h->d_sk_c = h->d_sk_s = nullptr;
     h->d_sk_partial = nullptr;
@@ -317,6 +319,8 @@ she_status she_init(const she_params* p, she_handle** out)
         if (e == cudaSuccess) e = cudaMalloc(&h->d_sk_c, img);
         if (e == cudaSuccess) e = cudaMalloc(&h->d_sk_s, img);
         if (e == cudaSuccess) e = cudaMalloc(&h->d_sk_partial, (size_t)h->sk_ctas * 256 * 129 * sizeof(float));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&h->d_sk_scratch, (size_t)h->sk_ctas * she::sk2d_scratch_bytes_per_cta());
         if (e == cudaSuccess) e = cudaMalloc(&h->d_sk_acc, 256 * 129 * sizeof(double));
         if (e == cudaSuccess) e = cudaMemsetAsync(h->d_sk_w, 0, img, h->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(h->d_sk_c, 0, img, h->stream);

@@ -98,6 +98,7 @@ struct Sk2dArgs {
     const unsigned char* wimg;   // row-DFT operand images
     const unsigned char* cimg;   // column cos images
     const unsigned char* simg;   // column sin images
+    unsigned char* scratch;      // [G][256 KB] split delta of the realization in work
     int* flags;
     int nx, ny, R;
     float ref;
@@ -203,7 +204,8 @@ struct Handle {
     unsigned char* d_sk_w = nullptr;   // 2D S(k): constant operand images
     unsigned char* d_sk_c = nullptr;
     unsigned char* d_sk_s = nullptr;
-    float* d_sk_partial = nullptr;     // [sk_ctas][256][129]
+    float* d_sk_partial = nullptr;     // [sk_ctas][129][256] (kx major)
+    unsigned char* d_sk_scratch = nullptr;  // [sk_ctas][256 KB] split delta images
     double* d_sk_acc = nullptr;        // [256][129]
     int sk_ctas = 0;
     int sk_partial_samples = 0;
@@ -276,6 +278,7 @@ cudaError_t launch_axes_syrk(Handle& h);
 cudaError_t launch_sk2d_tables(Handle& h);
 cudaError_t launch_sk2d(Handle& h);
 cudaError_t launch_sk2d_flush(Handle& h);
+size_t sk2d_scratch_bytes_per_cta();
 cudaError_t setup_batch(Handle& h, const std::vector<InstanceDesc>& desc);
 void* batch_kernel_dirichlet(bool species);
 void* batch_kernel_periodic(bool species);

@@ -100,7 +100,7 @@ def test_per_axis_structure_factor_2d(nx, ny):
     assert np.max(np.abs(g["sk_axes"] - ref)) < 2e-4 * np.max(np.abs(ref))
 
 
-@pytest.mark.parametrize("nx,ny,R", [(16, 12, 6), (64, 48, 4), (256, 16, 3), (132, 20, 3)])
+@pytest.mark.parametrize("nx,ny,R", [(16, 12, 6), (64, 48, 4), (256, 16, 3), (132, 20, 3), (16, 256, 2), (32, 255, 2)])
 def test_full_structure_factor_2d(nx, ny, R):
     # S(kx, ky) from the two-stage tcgen05 DFT vs the oracle's 2D DFT by its
     # definition (Eq. (3.11) along both axes) on the same trajectories
