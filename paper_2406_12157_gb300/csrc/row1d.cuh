@@ -16,8 +16,46 @@
 
 namespace she {
 
-__device__ __forceinline__ float fsqrt_any(float x) { return sqrtf(x); }
+// Square root of a noise amplitude.  Single precision takes x * rsqrt(x)
+// (relative error a few 1e-7, far inside the FP32 step tolerance, and a
+// fraction of the instructions of the correctly rounded sqrtf), with an exact
+// 0 at x <= 0; double precision keeps the correctly rounded sqrt.
+__device__ __forceinline__ float fsqrt_any(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
 __device__ __forceinline__ double fsqrt_any(double x) { return sqrt(x); }
+
+// 16-byte moves of C consecutive values (C % 4 == 0, 16-byte aligned)
+template <int C>
+__device__ __forceinline__ void vload(const float* p, float (&v)[C])
+{
+#pragma unroll
+    for (int k = 0; k < C / 4; ++k) {
+        const float4 f = reinterpret_cast<const float4*>(p)[k];
+        v[4 * k] = f.x; v[4 * k + 1] = f.y; v[4 * k + 2] = f.z; v[4 * k + 3] = f.w;
+    }
+}
+template <int C>
+__device__ __forceinline__ void vstore(float* p, const float (&v)[C])
+{
+#pragma unroll
+    for (int k = 0; k < C / 4; ++k)
+        reinterpret_cast<float4*>(p)[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+}
+template <int C>
+__device__ __forceinline__ void vload(const double* p, double (&v)[C])
+{
+#pragma unroll
+    for (int k = 0; k < C / 2; ++k) {
+        const double2 f = reinterpret_cast<const double2*>(p)[k];
+        v[2 * k] = f.x; v[2 * k + 1] = f.y;
+    }
+}
+template <int C>
+__device__ __forceinline__ void vstore(double* p, const double (&v)[C])
+{
+#pragma unroll
+    for (int k = 0; k < C / 2; ++k) reinterpret_cast<double2*>(p)[k] = make_double2(v[2 * k], v[2 * k + 1]);
+}
+
 
 template <typename Real>
 __device__ __forceinline__ bool finite_any(Real v) { return isfinite(v); }

@@ -24,10 +24,11 @@
 
 namespace she {
 
-// 7 resident blocks of 4 warps per SM for the FP32 8-cell layout: the
-// 256 x 256 x 256 ensemble (4096 bands of 16 rows) fits in one wave
+// 6 resident blocks of 4 warps per SM for the FP32 8-cell layout (85
+// registers, no spills in the row loop; measured faster than 7 blocks at 72
+// registers although the 256 x 256 x 256 ensemble then takes 1.1 waves)
 template <typename Real, int C, int LPR, bool SPECIES, bool RAGGED>
-__global__ void __launch_bounds__(128, (sizeof(Real) == 4 && C <= 8) ? 7 : 1)
+__global__ void __launch_bounds__(128, (sizeof(Real) == 4 && C <= 8) ? 6 : 1)
 k_step2d(const __grid_constant__ Step2DArgs<Real> a)
 {
     static_assert(C % 4 == 0, "cells per lane must be a multiple of 4");
@@ -67,6 +68,10 @@ k_step2d(const __grid_constant__ Step2DArgs<Real> a)
     auto load_row = [&](int y, Real (&v)[C]) {
         const int yy = (y + ny) % ny;
         const Real* p = Tin + (size_t)yy * nx;
+        if (!RAGGED) {                    // nx % 4 == 0: 16-byte aligned runs
+            vload<C>(p + i0, v);
+            return;
+        }
 #pragma unroll
         for (int j = 0; j < C; ++j) v[j] = (!RAGGED || i0 + j < nx) ? p[i0 + j] : Real(0);
     };
@@ -139,10 +144,11 @@ k_step2d(const __grid_constant__ Step2DArgs<Real> a)
         if (active) {
             Real* po = Tout + (size_t)y * nx;
             bool bad = false;
+            if (!RAGGED) vstore<C>(po + i0, out);
 #pragma unroll
             for (int j = 0; j < C; ++j) {
                 if (!RAGGED || i0 + j < nx) {
-                    po[i0 + j] = out[j];
+                    if (RAGGED) po[i0 + j] = out[j];
                     bad |= !finite_any(out[j]);
                 }
             }
@@ -150,12 +156,26 @@ k_step2d(const __grid_constant__ Step2DArgs<Real> a)
             if (a.sample) {
                 Real* p1 = a.m1 + (size_t)rho * (size_t)ncell + (size_t)y * nx;
                 Real* p2 = a.m2 + (size_t)rho * (size_t)ncell + (size_t)y * nx;
+                if (!RAGGED) {
+                    Real s1[C], s2[C];
+                    vload<C>(p1 + i0, s1);
+                    vload<C>(p2 + i0, s2);
 #pragma unroll
-                for (int j = 0; j < C; ++j) {
-                    if (!RAGGED || i0 + j < nx) {
+                    for (int j = 0; j < C; ++j) {
                         const Real d = out[j] - ref;
-                        p1[i0 + j] += d;
-                        p2[i0 + j] = fma(d, d, p2[i0 + j]);
+                        s1[j] += d;
+                        s2[j] = fma(d, d, s2[j]);
+                    }
+                    vstore<C>(p1 + i0, s1);
+                    vstore<C>(p2 + i0, s2);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < C; ++j) {
+                        if (i0 + j < nx) {
+                            const Real d = out[j] - ref;
+                            p1[i0 + j] += d;
+                            p2[i0 + j] = fma(d, d, p2[i0 + j]);
+                        }
                     }
                 }
             }

@@ -31,39 +31,6 @@ namespace she {
 constexpr int kY3 = 8;          // x-rows (warps) per CTA
 constexpr int kH3 = 32;         // z-planes per band
 
-// 16-byte moves of C consecutive values (C % 4 == 0, 16-byte aligned)
-template <int C>
-__device__ __forceinline__ void vload(const float* p, float (&v)[C])
-{
-#pragma unroll
-    for (int k = 0; k < C / 4; ++k) {
-        const float4 f = reinterpret_cast<const float4*>(p)[k];
-        v[4 * k] = f.x; v[4 * k + 1] = f.y; v[4 * k + 2] = f.z; v[4 * k + 3] = f.w;
-    }
-}
-template <int C>
-__device__ __forceinline__ void vstore(float* p, const float (&v)[C])
-{
-#pragma unroll
-    for (int k = 0; k < C / 4; ++k)
-        reinterpret_cast<float4*>(p)[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
-}
-template <int C>
-__device__ __forceinline__ void vload(const double* p, double (&v)[C])
-{
-#pragma unroll
-    for (int k = 0; k < C / 2; ++k) {
-        const double2 f = reinterpret_cast<const double2*>(p)[k];
-        v[2 * k] = f.x; v[2 * k + 1] = f.y;
-    }
-}
-template <int C>
-__device__ __forceinline__ void vstore(double* p, const double (&v)[C])
-{
-#pragma unroll
-    for (int k = 0; k < C / 2; ++k) reinterpret_cast<double2*>(p)[k] = make_double2(v[2 * k], v[2 * k + 1]);
-}
-
 template <typename Real, int C, bool SPECIES>
 __global__ void __launch_bounds__(kY3 * 32, sizeof(Real) == 4 ? 3 : 1)
 k_step3d(const __grid_constant__ Step3DArgs<Real> a)
