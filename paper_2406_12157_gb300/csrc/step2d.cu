@@ -24,9 +24,9 @@
 
 namespace she {
 
-// 6 resident blocks of 4 warps per SM for the FP32 8-cell layout (85
-// registers, no spills in the row loop; measured faster than 7 blocks at 72
-// registers although the 256 x 256 x 256 ensemble then takes 1.1 waves)
+// 6 resident blocks of 4 warps per SM for the FP32 8-cell layout (80
+// registers; measured faster than 7 blocks at 72 registers, which spill,
+// although the 256 x 256 x 256 ensemble then takes 1.1 waves)
 template <typename Real, int C, int LPR, bool SPECIES, bool RAGGED>
 __global__ void __launch_bounds__(128, (sizeof(Real) == 4 && C <= 8) ? 6 : 1)
 k_step2d(const __grid_constant__ Step2DArgs<Real> a)
