@@ -112,7 +112,10 @@ WORKLOADS = {
               "realizations, FP32 state, moments and full 256x256 equal-time covariance "
               "(tcgen05) every 10 steps after 1e5 steps"),
         chunk=10_000, ops=25.0 + 5.5 + 4.0 + 6.0, bytes=None,
-        kernel="k_step1d_cov<32,8,dirichlet,heat>"),
+        kernel="k_step1d_cov<32,8,dirichlet,heat>",
+        # DRAM read + write of one launch (2560 steps, mostly the per-CTA
+        # covariance flush), ncu capture in profiles/k_step1d_cov_gradient_rod.md
+        traffic=dict(bytes=100.748032e6 + 40.257024e6, realizations=4096)),
     "species_2d": dict(
         make=lambda W: W.species_2d(want_sk=1),
         desc=("2D stochastic species diffusion, 256x256 periodic, D=1, r=0.1, eps_c=1e-3, c=1 + "
@@ -120,6 +123,7 @@ WORKLOADS = {
               "(two-stage DFT-as-GEMM on tcgen05) every 10 steps after 1e4"),
         chunk=1000, ops=2 * (25.0 + 5.5 + 7.0) + 9.0, bytes=8.0 + 16.0 / 10,
         kernel="k_step2d<float,8,32,species>",
+        traffic=dict(bytes=73.059328e6 + 23.921152e6, realizations=256),   # profiles/k_step2d_species_2d.md
         # per realization and sample: row DFT (ny x nx x nx MAC) + column DFTs
         # for the 128 rows ky < 128 (2 x 128 x ny x nx MAC; the other rows
         # follow from the real-field symmetry), 3 split products, 2 flop per MAC
@@ -131,6 +135,7 @@ WORKLOADS = {
               "stencil, moments and S(k) along x, y, z (line covariance on tcgen05) every 10 steps"),
         chunk=100, ops=3 * (25.0 + 5.5 + 4.0) + 11.0, bytes=8.0 + 16.0 / 10,
         kernel="k_step3d<float,8,heat>",
+        traffic=dict(bytes=142.575872e6 + 91.134208e6, realizations=2),    # profiles/k_step3d_cube_3d.md
         # per realization and sample: for each axis a SYRK over all lines
         # (cells / n_a lines x n_a^2 MAC), 3 split products, 2 flop per MAC
         stats_kernel="k_axes_syrk", stats_flop=lambda p: 3 * 2 * sum(
@@ -140,7 +145,8 @@ WORKLOADS = {
         desc=("10,000 uneven 1D SHE rods, N log-uniform in [16, 2048], kappa U[0.5, 2], walls U[1, 3], "
               "r = 0.2 each, per-instance seeds, FP32, moments every 10 steps after 1e4, one CUDA-graph "
               "launch per step batch"),
-        chunk=2560, ops=25.0 + 5.5 + 4.0 + 6.0, bytes=None, kernel="k_step1d_batch<*>"),
+        chunk=2560, ops=25.0 + 5.5 + 4.0 + 6.0, bytes=None, kernel="k_step1d_batch<*>",
+        traffic=dict(bytes=18.150656e6 + 0.032256e6, realizations=1)),    # profiles/k_step1d_batch_batched_rods.md
     "oracle_rod": dict(
         make=lambda W: W.oracle_rod(want_cov=0, want_sk=0),
         desc="1D SHE rod, 32 cells, walls 1, 16 realizations, FP64",
@@ -332,6 +338,12 @@ def run_ours(args):
             dist.destroy_process_group()
         return
     peaks, peak_src = _peaks()
+    # DRAM bytes per launch of the dominant kernel from its ncu capture;
+    # where the capture ran fewer realizations, scaled by the units a launch
+    # processes (the traffic grows in proportion)
+    traffic = None
+    if wl.get("traffic"):
+        traffic = wl["traffic"]["bytes"] * (R / wl["traffic"]["realizations"] if not batch else 1.0)
     # the dominant (step) kernel alone: its launches and their summed device
     # time, from the event pairs the library recorded in the timed region
     step_launches = max(1, prof["step_launches"])
@@ -341,7 +353,7 @@ def run_ours(args):
     achieved = ops_per_launch / (per_launch_ms / 1e3) / 1e12          # Tops/s (lane-ops)
     peak = 128 * 152 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
-            "unit": "Tops/s", "frac": round(achieved / peak, 4), "traffic": None,
+            "unit": "Tops/s", "frac": round(achieved / peak, 4), "traffic": traffic,
             "kernel": wl["kernel"], "ops_per_cell_update": wl["ops"],
             "launches": prof["step_launches"], "ms_per_launch": round(per_launch_ms, 5),
             "cell_updates_per_launch": cu_per_launch,
