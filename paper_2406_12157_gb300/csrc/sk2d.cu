@@ -237,17 +237,22 @@ k_sk2d(const Sk2dArgs a)
         // independent loads, then the stores (kXK * 32 = 4 x blockDim items)
         const int kl = tid % kXK, y8b = tid / kXK;
         for (int kc0 = 0; kc0 < n1; kc0 += 2) {
+            // every load is issued unconditionally (from a clamped address) and
+            // masked afterwards, so that all 64 are in flight together
             float v[2][4][8];
 #pragma unroll
             for (int t = 0; t < 2; ++t) {
                 const int x = (kc0 + t) * kXK + kl;
+                const bool okx = kc0 + t < n1 && x < nx;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int y8 = y8b + u * (256 / kXK);
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         const int y = 8 * y8 + q;
-                        v[t][u][q] = (kc0 + t < n1 && x < nx && y < ny) ? __ldg(X + (size_t)y * nx + x) - a.ref : 0.0f;
+                        const bool ok = okx && y < ny;
+                        const float val = __ldg(X + (ok ? (size_t)y * nx + x : (size_t)0));
+                        v[t][u][q] = ok ? val - a.ref : 0.0f;
                     }
                 }
             }

@@ -103,15 +103,14 @@ k_step3d(const __grid_constant__ Step3DArgs<Real> a)
         Real* st = sm + (size_t)(z & 1) * stage_elems;
         Real* srow = st;                                  // rows 0..Y+1: y0-1 .. y0+Y
         Real* sgy = st + (kY3 + 2) * nx;                  // rows 0..Y: low y-faces of y0 .. y0+Y
+        // warps 0 and 1 fetch the halo rows first (their latency overlaps the z faces)
+        Real hv[C];
+        if (w == 0 || w == 1) load_row(w == 0 ? yl : yh, z, hv);
         load_row(yc, z + 1, nxt);
         face_row(cur, nxt, (uint32_t)(2 * ncell) + lin(yc, z + 1), gz_nxt);
-        // publish this warp's row of plane z; warps 0 and 1 fetch the halo rows
+        // publish this warp's row of plane z and the halo rows
         if (row_active) vstore<C>(srow + (size_t)(w + 1) * nx + i0, cur);
-        if (w == 0 || w == 1) {
-            Real hv[C];
-            load_row(w == 0 ? yl : yh, z, hv);
-            vstore<C>(srow + (size_t)(w == 0 ? 0 : nrows + 1) * nx + i0, hv);
-        }
+        if (w == 0 || w == 1) vstore<C>(srow + (size_t)(w == 0 ? 0 : nrows + 1) * nx + i0, hv);
         __syncthreads();
         // low y-face of this row (between y-1 and y); warp 0 also does the
         // top face of the tile (between the last row and the high halo)
