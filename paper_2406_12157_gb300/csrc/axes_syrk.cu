@@ -207,12 +207,16 @@ k_axes_syrk(const AxesArgs a)
                                                      : (size_t)other * nx + (xin ? x : 0);
                     const int p0 = 32 * warp;
                     // all 32 loads of this thread first (independent, coalesced
-                    // across the lanes), then split and store
+                    // across the lanes), then split and store; each load is
+                    // issued unconditionally from a clamped address and masked
+                    // afterwards, so that all 32 are in flight together
                     float v[32];
 #pragma unroll
                     for (int q = 0; q < 32; ++q) {
                         const int pp = p0 + q;
-                        v[q] = (xin && pp < n) ? __ldg(X + lbase + (size_t)pp * ge.stride) - a.ref : 0.0f;
+                        const bool ok = xin && pp < n;
+                        const float val = __ldg(X + lbase + (ok ? (size_t)pp * ge.stride : (size_t)0));
+                        v[q] = ok ? val - a.ref : 0.0f;
                     }
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
