@@ -120,7 +120,7 @@ struct Row1D {
     __device__ __forceinline__ void init(const Step1DArgs<Real>& a, int sl, int rho)
     {
         init_vals(a.N, a.r, a.amp2, a.wall_lo, a.wall_hi, a.stream0 + (uint32_t)rho, a.key0, a.key1, a.stochastic, sl);
-        rk = &a.rk;
+        if constexpr (RK) rk = &a.rk;
     }
 
     __device__ __forceinline__ uint4 noise_block(uint4 ctr) const

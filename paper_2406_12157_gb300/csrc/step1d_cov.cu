@@ -110,7 +110,7 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
     fence_after_sync();
     const uint32_t tbase = use_tc ? *tslot : 0u;
 
-    Row1D<float, C, LPR, DIR, SPECIES, RAGGED> rowst;
+    Row1D<float, C, LPR, DIR, SPECIES, RAGGED, false> rowst;   // keys in registers: measured faster here
     rowst.init(a, sl, rho);
     const int i0 = sl * C;
     float* row = a.state + (size_t)rho * (size_t)N;
