@@ -113,8 +113,9 @@ WORKLOADS = {
               "(tcgen05) every 10 steps after 1e5 steps"),
         chunk=10_000, ops=25.0 + 5.5 + 4.0 + 6.0, bytes=None,
         kernel="k_step1d_cov<32,8,dirichlet,heat>",
-        # DRAM read + write of one launch: set from the kernel's next capture
-        traffic=None),
+        # DRAM read + write of one launch (2560 steps, mostly the per-CTA
+        # covariance flush), ncu capture in profiles/k_step1d_cov_gradient_rod.md
+        traffic=dict(bytes=100.882176e6 + 40.192000e6, realizations=4096)),
     "species_2d": dict(
         make=lambda W: W.species_2d(want_sk=1),
         desc=("2D stochastic species diffusion, 256x256 periodic, D=1, r=0.1, eps_c=1e-3, c=1 + "

@@ -44,10 +44,10 @@ using namespace tc05;
 namespace {
 constexpr int kB = 64;                 // packed columns per column-stage block
 constexpr int kXK = 32;                // x rows (K) per row-stage chunk
-constexpr int kYK = 32;                // y rows (K) per column-stage chunk
+constexpr int kYK = 64;                // y rows (K) per column-stage chunk
 constexpr int kRA = 16384;             // row-stage A image: 256 (MN = y) x 32 (K = x) bf16
 constexpr int kRW = 16384;             // row-stage B image: 256 (MN = p) x 32 (K = x) bf16
-constexpr int kCA = 8192;              // column-stage A image: 128 (MN = ky) x 32 (K = y) bf16
+constexpr int kCA = 16384;             // column-stage A image: 128 (MN = ky) x 64 (K = y) bf16
 constexpr int kY = 32768;              // Y block image: 64 (MN = p) x 256 (K = y) bf16
 constexpr int kBuf = 2 * kRA + 2 * kRW;   // one operand buffer: 64 KB
 constexpr uint32_t kLBO = 1024;
@@ -61,7 +61,7 @@ constexpr uint32_t kTries2 = 1u << 20;
 // (eight 32-column x chunks, hi then lo, in the row-stage operand layout)
 size_t sk2d_scratch_bytes_per_cta() { return (size_t)8 * 2 * kRA; }
 
-// ---- constant images: W chunks [kc] (256 KB) and C/S chunks [kc] (128 KB) ----
+// ---- constant images: W chunks [kc] (256 KB) and C/S chunks [kc] (128 KB each) ----
 
 __global__ void k_sk2d_tables(int nx, int ny, unsigned char* wimg, unsigned char* cimg, unsigned char* simg)
 {
@@ -89,8 +89,8 @@ __global__ void k_sk2d_tables(int nx, int ny, unsigned char* wimg, unsigned char
         *reinterpret_cast<unsigned short*>(base + off) = h;
         *reinterpret_cast<unsigned short*>(base + kRW + off) = l;
     }
-    // C and S: 8 y chunks of [K = 32 y][MN = 128 ky]
-    if (t < 8 * kYK * 128) {
+    // C and S: 256 / kYK y chunks of [K = kYK y][MN = 128 ky]
+    if (t < 256 * 128) {
         const int ky = t % 128;
         const int k_local = (t / 128) % kYK;
         const int kc = t / (128 * kYK);
@@ -132,7 +132,7 @@ __device__ __forceinline__ void mma3(uint32_t d, uint32_t ahi, uint32_t alo, uin
 // chunks into the CTA's global scratch; (2) one thread drives a stream of
 // operand chunks through two 64 KB shared-memory buffers: the eight row-stage
 // x chunks (split delta + W), then for each block of 64 packed columns its
-// eight column-stage y chunks (C and S); the copy of chunk c + 1 is issued as
+// four column-stage y chunks (C and S); the copy of chunk c + 1 is issued as
 // soon as the MMAs of chunk c - 1 have released its buffer.  Before a
 // block's column stage all eight warps drain its D1 columns into the Y
 // operand image; after it they fold |hat delta|^2 into the CTA's partial
@@ -400,7 +400,7 @@ __global__ void k_sk2d_flush(float* partial, double* acc, int G)
 
 cudaError_t launch_sk2d_tables(Handle& h)
 {
-    const int total = 8 * kXK * 256;                // >= 8 * kYK * 128
+    const int total = 8 * kXK * 256;                // >= 256 * 128
     k_sk2d_tables<<<(total + 255) / 256, 256, 0, h.stream>>>(h.prob.n[0], h.prob.n[1], h.d_sk_w, h.d_sk_c, h.d_sk_s);
     h.launches += 1;
     return cudaGetLastError();
