@@ -258,7 +258,7 @@ k_axes_syrk(const AxesArgs a)
 #pragma unroll
                         for (int t = 0; t < 32; ++t) {
                             const int col = c0 + t;
-                            if (col < n) P[(size_t)col * n + rowi] += (double)v[t];
+                            if (col < n) atomicAdd(&P[(size_t)col * n + rowi], (double)v[t]);
                         }
                     }
                 }

@@ -88,8 +88,8 @@ __device__ __forceinline__ void batch_unit(const BatchArgs& a, int first, int co
 #pragma unroll
             for (int j = 0; j < C; ++j) {
                 if (i0 + j < N) {
-                    a.acc1[d.off + i0 + j] += (double)sm1[j * 32];
-                    a.acc2[d.off + i0 + j] += (double)sm2[j * 32];
+                    atomicAdd(&a.acc1[d.off + i0 + j], (double)sm1[j * 32]);
+                    atomicAdd(&a.acc2[d.off + i0 + j], (double)sm2[j * 32]);
                 }
             }
         }

@@ -13,6 +13,12 @@ namespace she {
 
 constexpr int kWarpsPerBlock1D = 4;
 
+// Accumulator flushes (per-CTA partials, per-realization moments) add into
+// FP64 device memory with atomicAdd whose result is unused (a fire-and-forget
+// reduction): each address has a single writer per launch, so the sums equal
+// a plain read-modify-write, but the reductions do not wait on one another
+// the way a loop of dependent `+=` through possibly-aliased pointers does.
+
 // Dimensionless problem on the device side (one instance).
 struct Problem {
     int dim = 1;

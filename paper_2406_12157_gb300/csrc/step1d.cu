@@ -108,8 +108,8 @@ k_step1d(const __grid_constant__ Step1DArgs<Real> a)
             for (int j = 0; j < C; ++j) {
                 const int i = i0 + j;
                 if (!RAGGED || i < N) {
-                    p1[i] += (double)sm1[j * 32];
-                    p2[i] += (double)sm2[j * 32];
+                    atomicAdd(&p1[i], (double)sm1[j * 32]);
+                    atomicAdd(&p2[i], (double)sm2[j * 32]);
                 }
             }
         }

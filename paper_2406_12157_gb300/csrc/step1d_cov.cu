@@ -238,8 +238,8 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
             for (int j = 0; j < C; ++j) {
                 const int i = i0 + j;
                 if (!RAGGED || i < N) {
-                    p1[i] += (double)sm1[j * 32];
-                    p2[i] += (double)sm2[j * 32];
+                    atomicAdd(&p1[i], (double)sm1[j * 32]);
+                    atomicAdd(&p2[i], (double)sm2[j * 32]);
                 }
             }
         }
@@ -270,7 +270,7 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
 #pragma unroll
                         for (int t = 0; t < 32; ++t) {
                             const int col = c0 + t;
-                            if (col < N) P[(size_t)col * N + rowi] += (double)v[t];
+                            if (col < N) atomicAdd(&P[(size_t)col * N + rowi], (double)v[t]);
                         }
                     }
                 }
