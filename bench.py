@@ -390,7 +390,7 @@ def run_ours(args):
                          "share_of_timed_region": round(prof["stats_ms"] / ms, 4) if ms > 0 else None,
                          "peak_source": "bf16_tflops_sustained (%s); the BF16x3 split counts 3 products" % peak_src}
     cpu = None
-    if not args.no_cpu_baseline and world >= 1:
+    if not args.no_cpu_baseline and world == 1:     # rank 0 at N = 1 only
         rate, cores, sample = oracle_sample_rate(probs if batch else p)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
     line = {
