@@ -115,7 +115,7 @@ WORKLOADS = {
         kernel="k_step1d_cov<32,8,dirichlet,heat>",
         # DRAM read + write of one launch (2560 steps, mostly the per-CTA
         # covariance flush), ncu capture in profiles/k_step1d_cov_gradient_rod.md
-        traffic=dict(bytes=100.882176e6 + 40.192000e6, realizations=4096)),
+        traffic=dict(bytes=100.737792e6 + 40.631040e6, realizations=4096)),
     "species_2d": dict(
         make=lambda W: W.species_2d(want_sk=1),
         desc=("2D stochastic species diffusion, 256x256 periodic, D=1, r=0.1, eps_c=1e-3, c=1 + "
@@ -146,7 +146,7 @@ WORKLOADS = {
               "r = 0.2 each, per-instance seeds, FP32, moments every 10 steps after 1e4, one CUDA-graph "
               "launch per step batch"),
         chunk=2560, ops=25.0 + 5.5 + 4.0 + 6.0, bytes=None, kernel="k_step1d_batch<*>",
-        traffic=dict(bytes=18.150656e6 + 0.032256e6, realizations=1)),    # profiles/k_step1d_batch_batched_rods.md
+        traffic=dict(bytes=17.875968e6 + 0.063232e6, realizations=1)),    # profiles/k_step1d_batch_batched_rods.md
     "oracle_rod": dict(
         make=lambda W: W.oracle_rod(want_cov=0, want_sk=0),
         desc="1D SHE rod, 32 cells, walls 1, 16 realizations, FP64",
