@@ -318,7 +318,7 @@ def run_ours(args):
 
     # ---- e2e through the C ABI with host buffers ----
     e2e = None
-    if not args.no_e2e and not batch:
+    if not args.no_e2e:
         state, step = sim.state()
         host = torch.from_numpy(state).pin_memory()
         host_np = host.numpy()
