@@ -23,6 +23,10 @@ namespace she {
 __device__ __forceinline__ float fsqrt_any(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
 __device__ __forceinline__ double fsqrt_any(double x) { return sqrt(x); }
 
+// i mod n for i in [-n, 2n): periodic neighbour indices are at most one
+// period out of range, so a compare and an add replace the integer division
+__device__ __forceinline__ int wrap_once(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
 // 16-byte moves of C consecutive values (C % 4 == 0, 16-byte aligned)
 template <int C>
 __device__ __forceinline__ void vload(const float* p, float (&v)[C])

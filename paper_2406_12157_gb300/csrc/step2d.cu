@@ -66,7 +66,7 @@ k_step2d(const __grid_constant__ Step2DArgs<Real> a)
         return (s_half * (lo + hi)) * z;
     };
     auto load_row = [&](int y, Real (&v)[C]) {
-        const int yy = (y + ny) % ny;
+        const int yy = wrap_once(y, ny);
         const Real* p = Tin + (size_t)yy * nx;
         if (!RAGGED) {                    // nx % 4 == 0: 16-byte aligned runs
             vload<C>(p + i0, v);
@@ -77,7 +77,7 @@ k_step2d(const __grid_constant__ Step2DArgs<Real> a)
     };
     // low y-face fluxes of row y (between rows y-1 and y)
     auto yflux = [&](int y, const Real (&lo)[C], const Real (&hi)[C], Real (&g)[C]) {
-        const int yy = (y + ny) % ny;
+        const int yy = wrap_once(y, ny);
         const uint32_t gbase = (uint32_t)(ncell + (int64_t)nx * yy + i0);    // normal index of cell i0
 #pragma unroll
         for (int q = 0; q < C / 4; ++q) {

@@ -77,7 +77,7 @@ k_step3d(const __grid_constant__ Step3DArgs<Real> a)
         return (s_half * (lo + hi)) * z;
     };
     auto row_ptr = [&](int yy, int zz) -> const Real* {
-        return Tin + ((size_t)((zz + nz) % nz) * ny + (size_t)yy) * nx;
+        return Tin + ((size_t)wrap_once(zz, nz) * ny + (size_t)yy) * nx;
     };
     auto load_row = [&](int yy, int zz, Real (&v)[C]) { vload<C>(row_ptr(yy, zz) + i0, v); };
     // fluxes of C faces from two rows of values, noise block base g0 (multiple of 4)
@@ -91,7 +91,7 @@ k_step3d(const __grid_constant__ Step3DArgs<Real> a)
         }
     };
     auto lin = [&](int yy, int zz) -> uint32_t {
-        return (uint32_t)((((int64_t)((zz + nz) % nz) * ny + yy) * nx) + i0);
+        return (uint32_t)((((int64_t)wrap_once(zz, nz) * ny + yy) * nx) + i0);
     };
 
     Real prev[C], cur[C], nxt[C], gz_cur[C], gz_nxt[C];
