@@ -127,6 +127,10 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
     int next_s = first_sample_index(a.step0, a.relax, a.K, a.nsteps);
     int nsnap = 0;
     const uint32_t idesc = idesc_bf16_f32(128, Nm, true, true);
+    // C is symmetric: the second 128-row half (rows 128..) needs only columns
+    // 128.. (N = Nm - 128, whose B operand is the A operand itself); the
+    // lower-left block is the transpose of the first half's upper-right one
+    const uint32_t idesc1 = Mh > 1 ? idesc_bf16_f32(128, Nm - 128, true, true) : idesc;
 
     if (is_mma_warp) {
         // MMA issue: one thread, once every stepping warp wrote the snapshot
@@ -145,16 +149,19 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
                 for (int h = 0; h < Mh; ++h) {
                     const uint32_t dt = tbase + (uint32_t)(h * Nm);
                     const uint32_t moff = (uint32_t)h * 2u * kOpLBO;
+                    const uint32_t id = h == 0 ? idesc : idesc1;
 #pragma unroll
                     for (int kk = 0; kk < 2; ++kk) {        // K = 32 slots = 2 x 16
                         const uint32_t koff = (uint32_t)kk * 2u * kOpSBO;
                         const uint64_t a_hi = desc_sw128(hb + koff + moff, kOpLBO, kOpSBO);
                         const uint64_t a_lo = desc_sw128(lb + koff + moff, kOpLBO, kOpSBO);
-                        const uint64_t b_hi = desc_sw128(hb + koff, kOpLBO, kOpSBO);
-                        const uint64_t b_lo = desc_sw128(lb + koff, kOpLBO, kOpSBO);
-                        mma_bf16(dt, a_hi, b_hi, idesc, (sn > 0 || kk > 0) ? 1u : 0u);
-                        mma_bf16(dt, a_hi, b_lo, idesc, 1u);
-                        mma_bf16(dt, a_lo, b_hi, idesc, 1u);
+                        const uint64_t b_hi = desc_sw128(hb + koff + moff, kOpLBO, kOpSBO);   // columns from 128 h
+                        const uint64_t b_lo = desc_sw128(lb + koff + moff, kOpLBO, kOpSBO);
+                        const uint64_t b0_hi = desc_sw128(hb + koff, kOpLBO, kOpSBO);         // all columns
+                        const uint64_t b0_lo = desc_sw128(lb + koff, kOpLBO, kOpSBO);
+                        mma_bf16(dt, a_hi, h == 0 ? b0_hi : b_hi, id, (sn > 0 || kk > 0) ? 1u : 0u);
+                        mma_bf16(dt, a_hi, h == 0 ? b0_lo : b_lo, id, 1u);
+                        mma_bf16(dt, a_lo, h == 0 ? b0_hi : b_hi, id, 1u);
                     }
                 }
                 mma_commit(&empty[b]);
@@ -263,14 +270,20 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
             double* P = c.partial + (size_t)g * (size_t)N * (size_t)N;
             for (int h = 0; h < Mh; ++h) {
                 const int rowi = h * 128 + 32 * warp + lane;
-                for (int c0 = 0; c0 < Nm; c0 += 32) {
+                const int cbase = h * 128;                   // first column held by half h
+                const int ncol = Nm - cbase;
+                for (int c0 = 0; c0 < ncol; c0 += 32) {
                     float v[32];
                     tmem_ld_32x32b_x32(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(h * Nm + c0), v);
                     if (rowi < N) {
 #pragma unroll
                         for (int t = 0; t < 32; ++t) {
-                            const int col = c0 + t;
-                            if (col < N) atomicAdd(&P[(size_t)col * N + rowi], (double)v[t]);
+                            const int col = cbase + c0 + t;
+                            if (c0 + t < ncol && col < N) {
+                                atomicAdd(&P[(size_t)col * N + rowi], (double)v[t]);
+                                if (h == 0 && Mh > 1 && col >= 128)      // the mirrored lower-left entry
+                                    atomicAdd(&P[(size_t)rowi * N + col], (double)v[t]);
+                            }
                         }
                     }
                 }

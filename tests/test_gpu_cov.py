@@ -43,7 +43,7 @@ def _cov_case(N, R, steps, walls=(1.0, 2.0), bc="dirichlet", K=10, sk=True):
 
 
 @pytest.mark.parametrize("N,R,steps", [(16, 40, 200), (32, 400, 300), (100, 300, 200),
-                                       (200, 300, 120), (256, 200, 150), (32, 5000, 60)])
+                                       (130, 300, 120), (200, 300, 120), (256, 200, 150), (32, 5000, 60)])
 def test_fused_covariance_matches_oracle(N, R, steps):
     # small grids, several realizations per CTA, ragged rows, one or two
     # 128-cell halves, and (R = 5000 > 32 x SMs) two realization waves
