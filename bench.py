@@ -115,7 +115,7 @@ WORKLOADS = {
         kernel="k_step1d_cov<32,8,dirichlet,heat>",
         # DRAM read + write of one launch (2560 steps, mostly the per-CTA
         # covariance flush), ncu capture in profiles/k_step1d_cov_gradient_rod.md
-        traffic=dict(bytes=100.737792e6 + 40.631040e6, realizations=4096)),
+        traffic=dict(bytes=100.751360e6 + 42.191360e6, realizations=4096)),
     "species_2d": dict(
         make=lambda W: W.species_2d(want_sk=1),
         desc=("2D stochastic species diffusion, 256x256 periodic, D=1, r=0.1, eps_c=1e-3, c=1 + "
@@ -123,7 +123,7 @@ WORKLOADS = {
               "(two-stage DFT-as-GEMM on tcgen05) every 10 steps after 1e4"),
         chunk=1000, ops=2 * (25.0 + 5.5 + 7.0) + 9.0, bytes=8.0 + 16.0 / 10,
         kernel="k_step2d<float,8,32,species>",
-        traffic=None,    # kernel changed since its capture: set from the next one
+        traffic=dict(bytes=72.768512e6 + 23.187200e6, realizations=256),   # profiles/k_step2d_species_2d.md
         # per realization and sample: row DFT (ny x nx x nx MAC) + column DFTs
         # for the 128 rows ky < 128 (2 x 128 x ny x nx MAC; the other rows
         # follow from the real-field symmetry), 3 split products, 2 flop per MAC
@@ -135,7 +135,7 @@ WORKLOADS = {
               "stencil, moments and S(k) along x, y, z (line covariance on tcgen05) every 10 steps"),
         chunk=100, ops=3 * (25.0 + 5.5 + 4.0) + 11.0, bytes=8.0 + 16.0 / 10,
         kernel="k_step3d<float,8,heat>",
-        traffic=None,    # kernel changed since its capture: set from the next one
+        traffic=dict(bytes=143.190784e6 + 94.754048e6, realizations=2),    # profiles/k_step3d_cube_3d.md
         # per realization and sample: for each axis a SYRK over all lines
         # (cells / n_a lines x n_a^2 MAC), 3 split products, 2 flop per MAC
         stats_kernel="k_axes_syrk", stats_flop=lambda p: 3 * 2 * sum(
