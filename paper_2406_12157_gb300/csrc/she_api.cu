@@ -227,8 +227,8 @@ she_status she_init(const she_params* p, she_handle** out)
     if (st == SHE_OK && need_cov && (p->dim != 1 || p->n[0] > 256)) {
         st = SHE_ERR_INVALID_ARG; msg = "she: the covariance needs a 1D grid of at most 256 cells";
     }
-    if (st == SHE_OK && need_cov && (p->precision != SHE_FP32 || p->kernel != SHE_KERNEL_AUTO)) {
-        st = SHE_ERR_UNSUPPORTED; msg = "she: the tensor-core covariance runs on the FP32 fused path";
+    if (st == SHE_OK && need_cov && p->precision == SHE_FP32 && p->kernel != SHE_KERNEL_AUTO) {
+        st = SHE_ERR_UNSUPPORTED; msg = "she: the FP32 covariance runs on the fused tensor-core path";
     }
     if (st == SHE_OK && (p->want_sk & SHE_SK_AXES) && p->dim == 1) {
         st = SHE_ERR_INVALID_ARG; msg = "she: SHE_SK_AXES is for 2D/3D grids (use SHE_SK_FULL in 1D)";
@@ -334,7 +334,8 @@ she_status she_init(const she_params* p, she_handle** out)
         int dev = 0, sms = 0;
         e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        h->cov_ctas = sms > 0 ? sms : 1;
+        // FP32: one partial per CTA of the fused kernel; FP64: one partial
+        h->cov_ctas = h->precision == SHE_FP64 ? 1 : (sms > 0 ? sms : 1);
         const size_t nn = cells * cells;
         if (e == cudaSuccess) e = cudaMalloc(&h->d_cov_partial, (size_t)h->cov_ctas * nn * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc(&h->d_cov_red, nn * sizeof(double));
@@ -465,8 +466,20 @@ she_status she_step_n(she_handle* hh, uint64_t n)
     if (h->step + n > (uint64_t)0xffffffffu) return fail(h, SHE_ERR_INVALID_ARG, "she: step counter would pass 2^32");
     const int spl = default_steps_per_launch(*h);
     uint64_t left = n;
+    // FP64 with the covariance: every launch ends at a sampling step, after
+    // which the FP64 covariance kernel reads the state
+    const bool cov64 = h->want_cov && h->precision == SHE_FP64 && !h->is_batch;
     while (left > 0) {
         int chunk = (int)std::min<uint64_t>(left, (uint64_t)spl);
+        bool ends_on_sample = false;
+        if (cov64) {
+            const uint64_t lo = std::max<uint64_t>(h->step + 1, (uint64_t)(h->relax + 1));
+            const uint64_t m = (lo + (uint64_t)h->K - 1) / (uint64_t)h->K * (uint64_t)h->K;   // next sample
+            if (m - h->step <= (uint64_t)chunk) {
+                chunk = (int)(m - h->step);
+                ends_on_sample = true;
+            }
+        }
         cudaError_t e;
         const int64_t ns = samples_in(h->step, (uint64_t)chunk, h->K, h->relax);
         if (h->prob.dim == 2 && !h->is_batch) e = she::launch_step2d(*h, (uint32_t)h->step, chunk);
@@ -477,8 +490,12 @@ she_status she_step_n(she_handle* hh, uint64_t n)
             she::prof_mark(*h, SHE_PROF_STEP);
             if (h->is_batch) e = she::launch_batch(*h, chunk);
             else if (h->kernel == SHE_KERNEL_PLAIN) e = she::launch_step1d_plain(*h, (uint32_t)h->step, chunk);
-            else if (h->want_cov) e = she::launch_step1d_cov(*h, (uint32_t)h->step, chunk, ns > 0);
+            else if (h->want_cov && !cov64) e = she::launch_step1d_cov(*h, (uint32_t)h->step, chunk, ns > 0);
             else e = she::launch_step1d(*h, (uint32_t)h->step, chunk);
+            if (e == cudaSuccess && ends_on_sample) {
+                she::prof_mark(*h, SHE_PROF_STATS);
+                e = she::launch_cov_fp64(*h);
+            }
         }
         if (e != cudaSuccess) {
             she::prof_close(*h);

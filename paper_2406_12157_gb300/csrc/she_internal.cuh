@@ -277,6 +277,7 @@ cudaError_t launch_plain_step_scratch(const Problem& p, int R, const double* T, 
                                       uint32_t n, uint32_t stream0, int stochastic, cudaStream_t st);
 cudaError_t launch_step1d_cov(Handle& h, uint32_t step0, int nsteps, bool has_samples);
 cudaError_t launch_reduce_cov(const Handle& h, double* d_out);
+cudaError_t launch_cov_fp64(Handle& h);
 cudaError_t launch_step2d(Handle& h, uint32_t step0, int nsteps);
 cudaError_t launch_step3d(Handle& h, uint32_t step0, int nsteps);
 cudaError_t launch_flush_moments(Handle& h);

@@ -362,4 +362,47 @@ cudaError_t launch_step1d_plain(Handle& h, uint32_t step0, int nsteps)
     return cudaSuccess;
 }
 
+// ------------------------------------------------------- FP64 covariance ----
+//
+// The FP64 paths accumulate the equal-time covariance (the generalisation of
+// the one-point correlation of Sec. 3, Eq. (3.13)) on the CUDA cores, exactly
+// in FP64: after every sampling step, C[i][j] += sum_r delta[r][i] delta[r][j]
+// with delta = T - T_ref, as 16 x 16 output tiles that stage 16-realization
+// slices of delta in shared memory.  C is stored column-major like the FP32
+// tensor-core partials ([j][i]; symmetric), one partial.
+
+__global__ void __launch_bounds__(256) k_cov_fp64(const double* __restrict__ T, int R, int N, double wlo,
+                                                  double dref, int dir, double* __restrict__ C)
+{
+    __shared__ double si[16][17], sj[16][17];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i = blockIdx.y * 16 + ty, j = blockIdx.x * 16 + tx;
+    const int li = blockIdx.y * 16 + tx, lj = blockIdx.x * 16 + tx;   // columns this thread loads
+    const double refi = dir ? fma(dref, (double)li + 0.5, wlo) : wlo;
+    const double refj = dir ? fma(dref, (double)lj + 0.5, wlo) : wlo;
+    double acc = 0.0;
+    for (int r0 = 0; r0 < R; r0 += 16) {
+        const int r = r0 + ty;
+        si[ty][tx] = (r < R && li < N) ? T[(size_t)r * N + li] - refi : 0.0;
+        sj[ty][tx] = (r < R && lj < N) ? T[(size_t)r * N + lj] - refj : 0.0;
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) acc = fma(si[k][ty], sj[k][tx], acc);
+        __syncthreads();
+    }
+    if (i < N && j < N) C[(size_t)j * N + i] += acc;
+}
+
+cudaError_t launch_cov_fp64(Handle& h)
+{
+    const int N = h.prob.n[0];
+    const bool dir = h.prob.bc == SHE_DIRICHLET;
+    const double dref = dir ? (h.prob.wall_hi - h.prob.wall_lo) / (double)N : 0.0;
+    const dim3 grid((unsigned)((N + 15) / 16), (unsigned)((N + 15) / 16)), block(16, 16);
+    k_cov_fp64<<<grid, block, 0, h.stream>>>((const double*)h.d_state, (int)h.R, N, h.prob.wall_lo, dref,
+                                             dir ? 1 : 0, h.d_cov_partial);
+    h.launches += 1;
+    return cudaGetLastError();
+}
+
 }  // namespace she

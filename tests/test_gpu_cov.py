@@ -32,10 +32,10 @@ import she_workloads as W  # noqa: E402
 from oracle import she as O  # noqa: E402
 
 
-def _cov_case(N, R, steps, walls=(1.0, 2.0), bc="dirichlet", K=10, sk=True):
-    p = W.gradient_rod(n=(N, 1, 1), realizations=R, relax_steps=0, stats_interval=K,
-                       wall_lo=walls[0], wall_hi=walls[1], bc=bc, want_cov=1, want_sk=int(sk))
-    with S.Simulation(p) as sim:
+def _cov_case(N, R, steps, walls=(1.0, 2.0), bc="dirichlet", K=10, sk=True, relax=0, **kw):
+    p = W.gradient_rod(n=(N, 1, 1), realizations=R, relax_steps=relax, stats_interval=K,
+                       wall_lo=walls[0], wall_hi=walls[1], bc=bc, want_cov=1, want_sk=int(sk), **kw)
+    with S.Simulation(p, **({"steps_per_launch": 37} if kw.get("precision") == "fp64" else {})) as sim:
         sim.step(steps)
         g = sim.stats(cov=True, sk=sk)
     o = O.finalize(p, O.run(p, R, steps, want_cov=1, want_sk=int(sk)))
@@ -77,3 +77,17 @@ def test_bounded_wait_times_out_and_context_survives():
     # the context is still usable afterwards
     X = np.ones((4, 16), dtype=np.float32)
     assert np.allclose(S.she_syrk_probe(X), 4.0)
+
+
+@pytest.mark.parametrize("N,R,steps,bc,kernel", [(16, 40, 203, "dirichlet", "auto"), (130, 70, 157, "dirichlet", "auto"),
+                                                 (256, 33, 90, "periodic", "auto"), (48, 20, 95, "dirichlet", "plain")])
+def test_fp64_covariance_matches_oracle_exactly(N, R, steps, bc, kernel):
+    # FP64 state and FP64 covariance (CUDA cores): the same sample paths as
+    # the oracle, so the pooled covariance and S(k) agree to rounding order
+    walls = (1.0, 2.0) if bc == "dirichlet" else (1.5, 1.5)
+    p, g, o = _cov_case(N, R, steps, walls=walls, bc=bc, K=7, relax=23, precision="fp64", kernel=kernel)
+    assert g["n_samples"] == o["n"]
+    scale = np.max(np.diag(o["cov"]))
+    assert np.max(np.abs(g["cov"] - o["cov"])) < 1e-10 * scale
+    assert np.max(np.abs(np.diag(g["cov"]) - g["var"])) < 1e-10 * scale
+    assert np.max(np.abs(g["sk_fluct"] - o["sk_fluct"])) < 1e-10 * np.max(o["sk_fluct"])
