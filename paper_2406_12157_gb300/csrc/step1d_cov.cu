@@ -42,6 +42,50 @@ constexpr int cov_smem_bytes(int warps)
            warps * 2 * C * 32 * 4 /* moment partials */;
 }
 
+// The MMA warp's loop (one thread): for every snapshot of the launch, wait
+// until the stepping warps wrote it, issue C += hi^T hi + hi^T lo + lo^T hi
+// over the upper half of C and commit to the buffer's `empty` barrier.
+// Returns the number of snapshots.  Kept out of line so that the stepping
+// loop of the kernel compiles as it does without the tensor-core code
+// (measured: inlined, the sampling launches are about 1 % slower).
+__device__ __noinline__ int cov_mma_issue(unsigned char* base, uint64_t* full, uint64_t* empty,
+                                          volatile int* abort_flag, int* flags, uint32_t tbase, int Mh, int Nm,
+                                          uint32_t idesc, uint32_t idesc1, int next_s, int nsteps, int K)
+{
+    int ns = 0;
+    for (int s = next_s; s < nsteps; s += K) ++ns;
+    for (int sn = 0; sn < ns && !*abort_flag; ++sn) {
+        const int b = sn & 1;
+        if (!mbar_wait_sleep_bounded(&full[b], (uint32_t)((sn >> 1) & 1), kWaitTries)) {
+            *abort_flag = 1;
+            atomicOr(flags, 2);
+            break;
+        }
+        fence_after_sync();
+        const uint32_t hb = smem_u32(base + 2 * b * kOpBytes), lb = smem_u32(base + (2 * b + 1) * kOpBytes);
+        for (int h = 0; h < Mh; ++h) {
+            const uint32_t dt = tbase + (uint32_t)(h * Nm);
+            const uint32_t moff = (uint32_t)h * 2u * kOpLBO;
+            const uint32_t id = h == 0 ? idesc : idesc1;
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk) {        // K = 32 slots = 2 x 16
+                const uint32_t koff = (uint32_t)kk * 2u * kOpSBO;
+                const uint64_t a_hi = desc_sw128(hb + koff + moff, kOpLBO, kOpSBO);
+                const uint64_t a_lo = desc_sw128(lb + koff + moff, kOpLBO, kOpSBO);
+                // B: all columns for the first half, columns from 128 h after it
+                const uint32_t boff = h == 0 ? 0u : moff;
+                const uint64_t b_hi = desc_sw128(hb + koff + boff, kOpLBO, kOpSBO);
+                const uint64_t b_lo = desc_sw128(lb + koff + boff, kOpLBO, kOpSBO);
+                mma_bf16(dt, a_hi, b_hi, id, (sn > 0 || kk > 0) ? 1u : 0u);
+                mma_bf16(dt, a_hi, b_lo, id, 1u);
+                mma_bf16(dt, a_lo, b_hi, id, 1u);
+            }
+        }
+        mma_commit(&empty[b]);
+    }
+    return ns;
+}
+
 template <int C, int LPR, bool DIR, bool SPECIES, bool RAGGED>
 __global__ void __launch_bounds__(32 * LPR, 1)
 k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
@@ -134,40 +178,9 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
 
     if (is_mma_warp) {
         // MMA issue: one thread, once every stepping warp wrote the snapshot
-        if (use_tc && lane == 0) {
-            int ns = 0;
-            for (int s = next_s; s < a.nsteps; s += a.K) ++ns;
-            for (int sn = 0; sn < ns && !*abort_flag; ++sn) {
-                const int b = sn & 1;
-                if (!mbar_wait_sleep_bounded(&full[b], (uint32_t)((sn >> 1) & 1), kWaitTries)) {
-                    *abort_flag = 1;
-                    atomicOr(a.flags, 2);
-                    break;
-                }
-                fence_after_sync();
-                const uint32_t hb = smem_u32(op_hi(b)), lb = smem_u32(op_lo(b));
-                for (int h = 0; h < Mh; ++h) {
-                    const uint32_t dt = tbase + (uint32_t)(h * Nm);
-                    const uint32_t moff = (uint32_t)h * 2u * kOpLBO;
-                    const uint32_t id = h == 0 ? idesc : idesc1;
-#pragma unroll
-                    for (int kk = 0; kk < 2; ++kk) {        // K = 32 slots = 2 x 16
-                        const uint32_t koff = (uint32_t)kk * 2u * kOpSBO;
-                        const uint64_t a_hi = desc_sw128(hb + koff + moff, kOpLBO, kOpSBO);
-                        const uint64_t a_lo = desc_sw128(lb + koff + moff, kOpLBO, kOpSBO);
-                        const uint64_t b_hi = desc_sw128(hb + koff + moff, kOpLBO, kOpSBO);   // columns from 128 h
-                        const uint64_t b_lo = desc_sw128(lb + koff + moff, kOpLBO, kOpSBO);
-                        const uint64_t b0_hi = desc_sw128(hb + koff, kOpLBO, kOpSBO);         // all columns
-                        const uint64_t b0_lo = desc_sw128(lb + koff, kOpLBO, kOpSBO);
-                        mma_bf16(dt, a_hi, h == 0 ? b0_hi : b_hi, id, (sn > 0 || kk > 0) ? 1u : 0u);
-                        mma_bf16(dt, a_hi, h == 0 ? b0_lo : b_lo, id, 1u);
-                        mma_bf16(dt, a_lo, h == 0 ? b0_hi : b_hi, id, 1u);
-                    }
-                }
-                mma_commit(&empty[b]);
-            }
-            nsnap = ns;
-        }
+        if (use_tc && lane == 0)
+            nsnap = cov_mma_issue(base, full, empty, abort_flag, a.flags, tbase, Mh, Nm, idesc, idesc1, next_s,
+                                  a.nsteps, a.K);
         nsnap = __shfl_sync(FULL, nsnap, 0);
     } else
     for (int s = 0; s < a.nsteps; ++s) {
