@@ -115,7 +115,7 @@ WORKLOADS = {
         kernel="k_step1d_cov<32,8,dirichlet,heat>",
         # DRAM read + write of one launch (2560 steps, mostly the per-CTA
         # covariance flush), ncu capture in profiles/k_step1d_cov_gradient_rod.md
-        traffic=dict(bytes=100.751360e6 + 42.191360e6, realizations=4096)),
+        traffic=dict(bytes=100.744192e6 + 41.423616e6, realizations=4096)),
     "species_2d": dict(
         make=lambda W: W.species_2d(want_sk=1),
         desc=("2D stochastic species diffusion, 256x256 periodic, D=1, r=0.1, eps_c=1e-3, c=1 + "
