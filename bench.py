@@ -123,7 +123,7 @@ WORKLOADS = {
               "(two-stage DFT-as-GEMM on tcgen05) every 10 steps after 1e4"),
         chunk=1000, ops=2 * (25.0 + 5.5 + 7.0) + 9.0, bytes=8.0 + 16.0 / 10,
         kernel="k_step2d<float,8,32,species>",
-        traffic=dict(bytes=72.768512e6 + 23.187200e6, realizations=256),   # profiles/k_step2d_species_2d.md
+        traffic=dict(bytes=74.679552e6 + 23.367168e6, realizations=256),   # profiles/k_step2d_species_2d.md
         # per realization and sample: row DFT (ny x nx x nx MAC) + column DFTs
         # for the 128 rows ky < 128 (2 x 128 x ny x nx MAC; the other rows
         # follow from the real-field symmetry), 3 split products, 2 flop per MAC
@@ -146,7 +146,7 @@ WORKLOADS = {
               "r = 0.2 each, per-instance seeds, FP32, moments every 10 steps after 1e4, one CUDA-graph "
               "launch per step batch"),
         chunk=2560, ops=25.0 + 5.5 + 4.0 + 6.0, bytes=None, kernel="k_step1d_batch<*>",
-        traffic=dict(bytes=17.875968e6 + 0.063232e6, realizations=1)),    # profiles/k_step1d_batch_batched_rods.md
+        traffic=dict(bytes=17.868800e6 + 0.052480e6, realizations=1)),    # profiles/k_step1d_batch_batched_rods.md
     "oracle_rod": dict(
         make=lambda W: W.oracle_rod(want_cov=0, want_sk=0),
         desc="1D SHE rod, 32 cells, walls 1, 16 realizations, FP64",

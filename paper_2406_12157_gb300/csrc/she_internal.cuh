@@ -64,7 +64,8 @@ struct Step2DArgs {
     int* flags;
     int nx, ny, R;
     int H;                // rows per band
-    int tiles;            // bands per realization
+    int tiles;            // bands per realization; 0: balanced row runs
+    int nseg;             // balanced row runs in this launch (tiles == 0)
     Real r, amp2, ref;
     uint32_t key0, key1, step, stream0;
     RoundKeys rk;         // round keys of (key0, key1)

@@ -37,23 +37,35 @@ k_step2d(const __grid_constant__ Step2DArgs<Real> a)
     const int lane = threadIdx.x & 31;
     const int sl = lane % LPR;
     const int warp = blockIdx.x * 4 + (threadIdx.x >> 5);
-    const int nseg = a.R * a.tiles;
+    // a.tiles > 0: segment = (realization, band of a.H rows); a.tiles == 0
+    // (one segment per warp only): segment = a balanced run of the R * ny
+    // realization-major rows, which may cross into the next realization
+    const bool balanced = LPR == 32 && a.tiles == 0;
+    const int nseg = balanced ? a.nseg : a.R * a.tiles;
     if (warp * SPW >= nseg) return;                   // warp-uniform
     const int seg_raw = warp * SPW + lane / LPR;
     const bool active = seg_raw < nseg;
     const int seg = active ? seg_raw : nseg - 1;
-    const int rho = seg / a.tiles;
-    const int tile = seg % a.tiles;
     const int nx = a.nx, ny = a.ny;
-    const int y0 = tile * a.H;
-    const int y1 = min(y0 + a.H, ny);
+    int rho, y_first, left;                           // first row (rho, y_first) and row count
+    if (balanced) {
+        const int64_t total = (int64_t)a.R * ny;
+        const int64_t rbeg = total * seg / nseg;
+        rho = (int)(rbeg / ny);
+        y_first = (int)(rbeg - (int64_t)rho * ny);
+        left = (int)(total * (seg + 1) / nseg - rbeg);
+    } else {
+        rho = seg / a.tiles;
+        y_first = (seg % a.tiles) * a.H;
+        left = min(a.H, ny - y_first);
+    }
     const int i0 = sl * C;
     const int jlast = nx - 1 - i0;
     const int last_sl = RAGGED ? (nx - 1) / C : LPR - 1;
     const int64_t ncell = (int64_t)nx * ny;
-    const Real* Tin = a.T + (size_t)rho * (size_t)ncell;
-    Real* Tout = a.Tn + (size_t)rho * (size_t)ncell;
-    const uint32_t stream = a.stream0 + (uint32_t)rho;
+    const Real* Tin = a.T;                            // set per band below
+    Real* Tout = a.Tn;
+    uint32_t stream = a.stream0;
     const Real r = a.r, amp2 = a.amp2, half = Real(0.5);
     const Real s_half = fsqrt_any(amp2) * half;
     const uint32_t n = a.step;
@@ -88,104 +100,113 @@ k_step2d(const __grid_constant__ Step2DArgs<Real> a)
         }
     };
 
-    Real prev[C], cur[C], nxt[C], nn[C], gy_cur[C], gy_nxt[C];
-    load_row(y0 - 1, prev);
-    load_row(y0, cur);
-    load_row(y0 + 1, nxt);
-    yflux(y0, prev, cur, gy_cur);
-    const Real ref = a.ref;
+    for (; left > 0; ++rho, y_first = 0) {           // one band per realization touched
+        const int y0 = y_first;
+        const int y1 = min(ny, y0 + left);
+        left -= y1 - y0;
+        Tin = a.T + (size_t)rho * (size_t)ncell;
+        Tout = a.Tn + (size_t)rho * (size_t)ncell;
+        stream = a.stream0 + (uint32_t)rho;
 
-    for (int y = y0; y < y1; ++y) {
-        load_row(y + 2, nn);                          // prefetch, used next row
-        yflux(y + 1, cur, nxt, gy_nxt);
-        // x-direction of row y (periodic): neighbours and low x-face fluxes
-        const Real left_nb = __shfl_up_sync(FULL, cur[C - 1], 1, LPR);
-        const Real right_nb = __shfl_down_sync(FULL, cur[0], 1, LPR);
-        Real mine = cur[C - 1];
-        if (RAGGED) {
+        Real prev[C], cur[C], nxt[C], nn[C], gy_cur[C], gy_nxt[C];
+        load_row(y0 - 1, prev);
+        load_row(y0, cur);
+        load_row(y0 + 1, nxt);
+        yflux(y0, prev, cur, gy_cur);
+        const Real ref = a.ref;
+
+        for (int y = y0; y < y1; ++y) {
+            load_row(y + 2, nn);                          // prefetch, used next row
+            yflux(y + 1, cur, nxt, gy_nxt);
+            // x-direction of row y (periodic): neighbours and low x-face fluxes
+            const Real left_nb = __shfl_up_sync(FULL, cur[C - 1], 1, LPR);
+            const Real right_nb = __shfl_down_sync(FULL, cur[0], 1, LPR);
+            Real mine = cur[C - 1];
+            if (RAGGED) {
 #pragma unroll
-            for (int j = 0; j < C; ++j)
-                if (j == jlast) mine = cur[j];
-        }
-        const Real wrap_lo = __shfl_sync(FULL, mine, last_sl, LPR);     // T(nx-1, y)
-        const Real wrap_hi = __shfl_sync(FULL, cur[0], 0, LPR);         // T(0, y)
-        Real gx[C];
-        const uint32_t gxbase = (uint32_t)((int64_t)nx * y + i0);
-#pragma unroll
-        for (int q = 0; q < C / 4; ++q) {
-            Real z[4] = {Real(0), Real(0), Real(0), Real(0)};
-            if (a.stochastic) box_muller4(philox4x32_10(make_uint4(gxbase / 4u + (uint32_t)q, n, stream, 0u), a.rk), z);
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int j = 4 * q + t;
-                Real lo = (j == 0) ? left_nb : cur[j - 1];
-                if (j == 0 && sl == 0) lo = wrap_lo;
-                gx[j] = flux(lo, cur[j], z[t]);
+                for (int j = 0; j < C; ++j)
+                    if (j == jlast) mine = cur[j];
             }
-        }
-        const Real g_next = __shfl_down_sync(FULL, gx[0], 1, LPR);
-        const Real g_zero = __shfl_sync(FULL, gx[0], 0, LPR);
-        Real out[C];
+            const Real wrap_lo = __shfl_sync(FULL, mine, last_sl, LPR);     // T(nx-1, y)
+            const Real wrap_hi = __shfl_sync(FULL, cur[0], 0, LPR);         // T(0, y)
+            Real gx[C];
+            const uint32_t gxbase = (uint32_t)((int64_t)nx * y + i0);
 #pragma unroll
-        for (int j = 0; j < C; ++j) {
-            const int i = i0 + j;
-            Real left = (j == 0) ? left_nb : cur[j - 1];
-            if (j == 0 && sl == 0) left = wrap_lo;
-            Real right = (j == C - 1) ? right_nb : cur[j + 1];
-            Real ghi = (j == C - 1) ? g_next : gx[j + 1];
-            if ((!RAGGED && j == C - 1 && sl == LPR - 1) || (RAGGED && i == nx - 1)) {
-                right = wrap_hi;
-                ghi = g_zero;
-            }
-            const Real c = cur[j];
-            out[j] = c + r * ((left + right) + (prev[j] + nxt[j]) - Real(4) * c) + (ghi - gx[j]) +
-                     (gy_nxt[j] - gy_cur[j]);
-        }
-        if (active) {
-            Real* po = Tout + (size_t)y * nx;
-            bool bad = false;
-            if (!RAGGED) vstore<C>(po + i0, out);
+            for (int q = 0; q < C / 4; ++q) {
+                Real z[4] = {Real(0), Real(0), Real(0), Real(0)};
+                if (a.stochastic) box_muller4(philox4x32_10(make_uint4(gxbase / 4u + (uint32_t)q, n, stream, 0u), a.rk), z);
 #pragma unroll
-            for (int j = 0; j < C; ++j) {
-                if (!RAGGED || i0 + j < nx) {
-                    if (RAGGED) po[i0 + j] = out[j];
-                    bad |= !finite_any(out[j]);
+                for (int t = 0; t < 4; ++t) {
+                    const int j = 4 * q + t;
+                    Real lo = (j == 0) ? left_nb : cur[j - 1];
+                    if (j == 0 && sl == 0) lo = wrap_lo;
+                    gx[j] = flux(lo, cur[j], z[t]);
                 }
             }
-            if (bad) atomicOr(a.flags, 1);
-            if (a.sample) {
-                Real* p1 = a.m1 + (size_t)rho * (size_t)ncell + (size_t)y * nx;
-                Real* p2 = a.m2 + (size_t)rho * (size_t)ncell + (size_t)y * nx;
-                if (!RAGGED) {
-                    Real s1[C], s2[C];
-                    vload<C>(p1 + i0, s1);
-                    vload<C>(p2 + i0, s2);
+            const Real g_next = __shfl_down_sync(FULL, gx[0], 1, LPR);
+            const Real g_zero = __shfl_sync(FULL, gx[0], 0, LPR);
+            Real out[C];
 #pragma unroll
-                    for (int j = 0; j < C; ++j) {
-                        const Real d = out[j] - ref;
-                        s1[j] += d;
-                        s2[j] = fma(d, d, s2[j]);
+            for (int j = 0; j < C; ++j) {
+                const int i = i0 + j;
+                Real left = (j == 0) ? left_nb : cur[j - 1];
+                if (j == 0 && sl == 0) left = wrap_lo;
+                Real right = (j == C - 1) ? right_nb : cur[j + 1];
+                Real ghi = (j == C - 1) ? g_next : gx[j + 1];
+                if ((!RAGGED && j == C - 1 && sl == LPR - 1) || (RAGGED && i == nx - 1)) {
+                    right = wrap_hi;
+                    ghi = g_zero;
+                }
+                const Real c = cur[j];
+                out[j] = c + r * ((left + right) + (prev[j] + nxt[j]) - Real(4) * c) + (ghi - gx[j]) +
+                         (gy_nxt[j] - gy_cur[j]);
+            }
+            if (active) {
+                Real* po = Tout + (size_t)y * nx;
+                bool bad = false;
+                if (!RAGGED) vstore<C>(po + i0, out);
+#pragma unroll
+                for (int j = 0; j < C; ++j) {
+                    if (!RAGGED || i0 + j < nx) {
+                        if (RAGGED) po[i0 + j] = out[j];
+                        bad |= !finite_any(out[j]);
                     }
-                    vstore<C>(p1 + i0, s1);
-                    vstore<C>(p2 + i0, s2);
-                } else {
+                }
+                if (bad) atomicOr(a.flags, 1);
+                if (a.sample) {
+                    Real* p1 = a.m1 + (size_t)rho * (size_t)ncell + (size_t)y * nx;
+                    Real* p2 = a.m2 + (size_t)rho * (size_t)ncell + (size_t)y * nx;
+                    if (!RAGGED) {
+                        Real s1[C], s2[C];
+                        vload<C>(p1 + i0, s1);
+                        vload<C>(p2 + i0, s2);
 #pragma unroll
-                    for (int j = 0; j < C; ++j) {
-                        if (i0 + j < nx) {
+                        for (int j = 0; j < C; ++j) {
                             const Real d = out[j] - ref;
-                            p1[i0 + j] += d;
-                            p2[i0 + j] = fma(d, d, p2[i0 + j]);
+                            s1[j] += d;
+                            s2[j] = fma(d, d, s2[j]);
+                        }
+                        vstore<C>(p1 + i0, s1);
+                        vstore<C>(p2 + i0, s2);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < C; ++j) {
+                            if (i0 + j < nx) {
+                                const Real d = out[j] - ref;
+                                p1[i0 + j] += d;
+                                p2[i0 + j] = fma(d, d, p2[i0 + j]);
+                            }
                         }
                     }
                 }
             }
-        }
 #pragma unroll
-        for (int j = 0; j < C; ++j) {
-            prev[j] = cur[j];
-            cur[j] = nxt[j];
-            nxt[j] = nn[j];
-            gy_cur[j] = gy_nxt[j];
+            for (int j = 0; j < C; ++j) {
+                prev[j] = cur[j];
+                cur[j] = nxt[j];
+                nxt[j] = nn[j];
+                gy_cur[j] = gy_nxt[j];
+            }
         }
     }
 }
@@ -211,14 +232,39 @@ cudaError_t launch_flush_moments(Handle& h)
     return cudaGetLastError();
 }
 
+// Resident warps of one kernel instance on this device (0 if unknown).
+template <typename K>
+static int resident_warps(K kernel)
+{
+    int dev = 0, sms = 0, blocks = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, 128, 0) != cudaSuccess)
+        return 0;
+    return sms * blocks * 4;
+}
+
+// One warp per segment (LPR = 32): the R * ny rows are split into as many
+// balanced runs as there are resident warps (but runs of at least 16 rows),
+// so the launch is a single full wave; a partial second wave of bands would
+// otherwise run at a fraction of the SM's issue rate.
 template <typename Real, int C, int LPR, bool SP>
-static cudaError_t launch2d_layout(const Step2DArgs<Real>& a, cudaStream_t st)
+static cudaError_t launch2d_layout(Step2DArgs<Real> a, cudaStream_t st)
 {
     constexpr int SPW = 32 / LPR;
-    const int64_t segs = (int64_t)a.R * a.tiles;
+    const bool ragged = a.nx != C * LPR;
+    if (LPR == 32) {
+        static const int slots[2] = {resident_warps(k_step2d<Real, C, LPR, SP, false>),
+                                     resident_warps(k_step2d<Real, C, LPR, SP, true>)};
+        const int64_t rows = (int64_t)a.R * a.ny;
+        const int64_t runs = std::min<int64_t>(slots[ragged] > 0 ? slots[ragged] : 1, (rows + 15) / 16);
+        a.tiles = 0;
+        a.nseg = (int)runs;
+    }
+    const int64_t segs = a.tiles > 0 ? (int64_t)a.R * a.tiles : a.nseg;
     const int64_t warps = (segs + SPW - 1) / SPW;
     const dim3 grid((unsigned)((warps + 3) / 4)), block(128);
-    if (a.nx == C * LPR) k_step2d<Real, C, LPR, SP, false><<<grid, block, 0, st>>>(a);
+    if (!ragged) k_step2d<Real, C, LPR, SP, false><<<grid, block, 0, st>>>(a);
     else k_step2d<Real, C, LPR, SP, true><<<grid, block, 0, st>>>(a);
     return cudaGetLastError();
 }
@@ -244,6 +290,7 @@ static cudaError_t launch2d_real(Handle& h, uint32_t step0, int nsteps)
     a.R = (int)h.R;
     a.H = std::min(16, a.ny);
     a.tiles = (a.ny + a.H - 1) / a.H;
+    a.nseg = 0;
     a.r = (Real)h.prob.r;
     a.amp2 = (Real)(h.stochastic ? 2.0 * h.prob.r * h.prob.eps : 0.0);
     a.ref = (Real)h.prob.wall_lo;
