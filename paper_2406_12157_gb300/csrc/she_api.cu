@@ -132,13 +132,12 @@ void release(Handle* h)
     cudaFree(h->d_axes_red);
     h->d_axes_partial = h->d_axes_red = nullptr;
     cudaFree(h->d_sk_w);
-    cudaFree(h->d_sk_c);
-    cudaFree(h->d_sk_s);
+    cudaFree(h->d_sk_a);
     cudaFree(h->d_sk_partial);
     cudaFree(h->d_sk_scratch);
     h->d_sk_scratch = nullptr;
     cudaFree(h->d_sk_acc);
-    h->d_sk_w = h->d_sk_c = h->d_sk_s = nullptr;
+    h->d_sk_w = h->d_sk_a = nullptr;
     h->d_sk_partial = nullptr;
     h->d_sk_acc = nullptr;
     she::destroy_batch_graphs(*h);
@@ -316,15 +315,13 @@ she_status she_init(const she_params* p, she_handle** out)
         h->sk_ctas = (int)std::min<int64_t>(sms > 0 ? sms : 1, h->R);
         const size_t img = 256 * 1024;     // each constant image set
         if (e == cudaSuccess) e = cudaMalloc(&h->d_sk_w, img);
-        if (e == cudaSuccess) e = cudaMalloc(&h->d_sk_c, img);
-        if (e == cudaSuccess) e = cudaMalloc(&h->d_sk_s, img);
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_sk_a, img);
         if (e == cudaSuccess) e = cudaMalloc(&h->d_sk_partial, (size_t)h->sk_ctas * 256 * 129 * sizeof(float));
         if (e == cudaSuccess)
             e = cudaMalloc(&h->d_sk_scratch, (size_t)h->sk_ctas * she::sk2d_scratch_bytes_per_cta());
         if (e == cudaSuccess) e = cudaMalloc(&h->d_sk_acc, 256 * 129 * sizeof(double));
         if (e == cudaSuccess) e = cudaMemsetAsync(h->d_sk_w, 0, img, h->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(h->d_sk_c, 0, img, h->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(h->d_sk_s, 0, img, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->d_sk_a, 0, img, h->stream);
         if (e == cudaSuccess)
             e = cudaMemsetAsync(h->d_sk_partial, 0, (size_t)h->sk_ctas * 256 * 129 * sizeof(float), h->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(h->d_sk_acc, 0, 256 * 129 * sizeof(double), h->stream);

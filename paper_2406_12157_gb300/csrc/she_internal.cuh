@@ -102,10 +102,9 @@ struct AxesArgs {
 struct Sk2dArgs {
     const float* T;       // [R][ny][nx]
     float* partial;       // [G][256][129] FP32 per-CTA sums of |hat delta|^2 (kx <= nx/2)
-    const unsigned char* wimg;   // row-DFT operand images
-    const unsigned char* cimg;   // column cos images
-    const unsigned char* simg;   // column sin images
-    unsigned char* scratch;      // [G][256 KB] split delta of the realization in work
+    const unsigned char* wimg;   // row-stage B images (W)
+    const unsigned char* aimg;   // column-stage A images ([C; S])
+    unsigned char* scratch;      // [G][512 KB] split delta and split D1 of the realization in work
     int* flags;
     int nx, ny, R;
     float ref;
@@ -208,11 +207,10 @@ struct Handle {
     std::vector<int64_t> inst_off;     // host copies for the statistics
     std::vector<int> inst_n;
     std::vector<double> inst_wlo, inst_whi;
-    unsigned char* d_sk_w = nullptr;   // 2D S(k): constant operand images
-    unsigned char* d_sk_c = nullptr;
-    unsigned char* d_sk_s = nullptr;
+    unsigned char* d_sk_w = nullptr;   // 2D S(k): constant operand images (W; [C; S])
+    unsigned char* d_sk_a = nullptr;
     float* d_sk_partial = nullptr;     // [sk_ctas][129][256] (kx major)
-    unsigned char* d_sk_scratch = nullptr;  // [sk_ctas][256 KB] split delta images
+    unsigned char* d_sk_scratch = nullptr;  // [sk_ctas][512 KB] split delta and split D1 images
     double* d_sk_acc = nullptr;        // [256][129]
     int sk_ctas = 0;
     int sk_partial_samples = 0;
