@@ -18,6 +18,7 @@ from . import build as _build
 
 HEAT, SPECIES = 0, 1
 PERIODIC, DIRICHLET = 0, 1
+FE, PC = 0, 1
 
 
 class OrcParams(ctypes.Structure):
@@ -34,7 +35,7 @@ class OrcParams(ctypes.Structure):
         ("stochastic", ctypes.c_int32),
         ("perturb_ic", ctypes.c_int32),
         ("stats_interval", ctypes.c_int32),
-        ("pad0", ctypes.c_int32),
+        ("scheme", ctypes.c_int32),
         ("relax_steps", ctypes.c_int64),
         ("want_cov", ctypes.c_int32),
         ("want_sk", ctypes.c_int32),
@@ -124,6 +125,7 @@ def to_params(prob):
     p.stochastic = int(prob.get("stochastic", 1))
     p.perturb_ic = int(prob.get("perturb_ic", 1))
     p.stats_interval = int(prob.get("stats_interval", 10))
+    p.scheme = PC if prob.get("scheme", "fe") == "pc" else FE
     p.relax_steps = int(prob.get("relax_steps", 0))
     p.want_cov = int(prob.get("want_cov", 0))
     p.want_sk = int(prob.get("want_sk", 0))
@@ -179,7 +181,8 @@ def initial_state(prob, stream):
 
 
 def step(prob, state, step_index, stream):
-    """One forward-Euler step (Eq. (3.3)) of one realization from `state`."""
+    """One step of one realization from `state`: forward Euler (Eq. (3.3)) or,
+    with ``prob["scheme"] == "pc"``, the predictor-corrector scheme of Sec. 3."""
     p = to_params(prob)
     T = np.ascontiguousarray(state, dtype=np.float64)
     out = np.zeros_like(T)

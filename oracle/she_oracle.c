@@ -21,6 +21,12 @@
  *     heat noise proportional to T_face (Eq. (2.12)/(4.9)), species noise
  *     proportional to sqrt(c_face) (Eq. (4.7)/(4.8)); in 2D/3D the per-axis
  *     fluxes use independent noises (Eq. (2.11), Kronecker delta over axes).
+ *   - or one predictor-corrector step (Sec. 3, the trapezoidal scheme
+ *     written after Eq. (3.3), and the SCHEME_FLAG branch of the paper's
+ *     program in its supplement): the forward-Euler step as predictor T*,
+ *     then the corrector (T + T* + D(T*) + div G(T*)) / 2 with the face
+ *     values and stencil on T* and the SAME face normals (noise constant over
+ *     the step); walls keep their wall value and sqrt(2) factor.
  *   - the sampling of Sec. 3, Eq. (3.9): after relaxation, every K steps,
  *     pooled over realizations: sums of delta = T - T_ref, of delta^2, of
  *     delta_i*delta_j (equal-time covariance, generalising the one-point
@@ -60,6 +66,9 @@
 #define ORC_PERIODIC 0
 #define ORC_DIRICHLET 1
 
+#define ORC_FE 0
+#define ORC_PC 1
+
 #define ORC_TAG_STEP 0u
 #define ORC_TAG_IC 1u
 #define ORC_TAG_WALL 2u
@@ -76,7 +85,7 @@ typedef struct {
     int32_t stochastic;    /* 0: deterministic limit (alpha = 0) */
     int32_t perturb_ic;    /* 1: add the seeded perturbation to the IC */
     int32_t stats_interval;/* K */
-    int32_t pad0;
+    int32_t scheme;        /* ORC_FE or ORC_PC */
     int64_t relax_steps;   /* sample at step m (1-based) iff m%K==0 && m>relax */
     int32_t want_cov;      /* accumulate sum delta_i delta_j */
     int32_t want_sk;       /* bit0: full DFT over the grid, bit1: per-axis lines */
@@ -204,33 +213,70 @@ static double orc_flux_amp(const orc_params* p, double face_value)
 
 /* --------------------------------------------------------------- step ---- */
 
-/* One forward-Euler step of Eq. (3.3) in 1D (Dirichlet walls per Eq. (3.8)). */
-static void orc_step_1d(const orc_params* p, uint32_t step, uint32_t stream,
-                        const double* T, double* Tn, double* G /* N+1 */)
+/* Work arrays of one realization's step. */
+typedef struct {
+    double* Z;      /* [dim*cells + 1] normals of the step's faces (wall weight folded in) */
+    double* G;      /* [dim*cells + 1] stochastic face fluxes */
+    double* inc;    /* [cells] increment D + (G_hi - G_lo) */
+    double* Ts;     /* [cells] predictor state */
+} orc_work;
+
+static int orc_work_alloc(const orc_params* p, orc_work* w)
+{
+    int64_t nc = orc_cells(p);
+    w->Z = (double*)malloc(sizeof(double) * (size_t)(p->dim * nc + 1));
+    w->G = (double*)malloc(sizeof(double) * (size_t)(p->dim * nc + 1));
+    w->inc = (double*)malloc(sizeof(double) * (size_t)nc);
+    w->Ts = (double*)malloc(sizeof(double) * (size_t)nc);
+    return (w->Z && w->G && w->inc && w->Ts) ? 0 : -1;
+}
+
+static void orc_work_free(orc_work* w)
+{
+    free(w->Z); free(w->G); free(w->inc); free(w->Ts);
+}
+
+/* The step's face normals, drawn once (both stages of the predictor-corrector
+ * scheme reuse them, Sec. 3).  1D: Z[f] for the low face of cell f, times
+ * sqrt(2) at a Dirichlet wall (Eq. (3.8)), Z[n] the high wall; 2D/3D:
+ * Z[a*cells + i] for the low face of cell i on axis a (Eq. (2.11)). */
+static void orc_step_normals(const orc_params* p, uint32_t step, uint32_t stream, double* Z)
+{
+    const int64_t nc = orc_cells(p);
+    if (!p->stochastic) {
+        for (int64_t i = 0; i < p->dim * nc + 1; ++i) Z[i] = 0.0;
+        return;
+    }
+    if (p->dim == 1) {
+        const int n = p->n[0];
+        const int dir = (p->bc == ORC_DIRICHLET);
+        for (int f = 0; f < n; ++f) {
+            Z[f] = orc_normal(p->seed, (uint64_t)f, step, stream, ORC_TAG_STEP);
+            if (f == 0 && dir) Z[f] *= sqrt(2.0);
+        }
+        Z[n] = dir ? sqrt(2.0) * orc_wall_normal(p->seed, step, stream) : Z[0];
+        return;
+    }
+    for (int64_t g = 0; g < p->dim * nc; ++g) Z[g] = orc_normal(p->seed, (uint64_t)g, step, stream, ORC_TAG_STEP);
+    Z[p->dim * nc] = 0.0;
+}
+
+/* Increment of Eq. (3.3) in 1D from state T and face normals Z: the
+ * deterministic stencil (Dirichlet end cells per Eq. (3.8)) plus the
+ * divergence of the stochastic flux G_f = amp(T_f) Z_f, with the wall value
+ * as face value at a Dirichlet wall. */
+static void orc_increment_1d(const orc_params* p, const double* T, const double* Z, double* G, double* inc)
 {
     const int n = p->n[0];
     const double r = p->r;
     const int dir = (p->bc == ORC_DIRICHLET);
-    const double sq2 = sqrt(2.0);
-    /* face f = low face of cell f, f = 0..n-1; face n = high wall */
     for (int f = 0; f < n; ++f) {
         double tface;
-        double w = 1.0;
-        if (f == 0) {
-            if (dir) { tface = p->wall_lo; w = sq2; }
-            else tface = 0.5 * (T[n - 1] + T[0]);
-        } else {
-            tface = 0.5 * (T[f - 1] + T[f]);
-        }
-        double z = p->stochastic ? orc_normal(p->seed, (uint64_t)f, step, stream, ORC_TAG_STEP) : 0.0;
-        G[f] = w * orc_flux_amp(p, tface) * z;
+        if (f == 0) tface = dir ? p->wall_lo : 0.5 * (T[n - 1] + T[0]);
+        else tface = 0.5 * (T[f - 1] + T[f]);
+        G[f] = orc_flux_amp(p, tface) * Z[f];
     }
-    if (dir) {
-        double z = p->stochastic ? orc_wall_normal(p->seed, step, stream) : 0.0;
-        G[n] = sq2 * orc_flux_amp(p, p->wall_hi) * z;
-    } else {
-        G[n] = G[0];
-    }
+    G[n] = dir ? orc_flux_amp(p, p->wall_hi) * Z[n] : G[0];
     for (int i = 0; i < n; ++i) {
         double d;
         if (dir && i == 0)
@@ -242,14 +288,13 @@ static void orc_step_1d(const orc_params* p, uint32_t step, uint32_t stream,
             double right = T[(i + 1) % n];
             d = r * (right - 2.0 * T[i] + left);
         }
-        Tn[i] = T[i] + d + (G[i + 1] - G[i]);
+        inc[i] = d + (G[i + 1] - G[i]);
     }
 }
 
-/* One step in 2D/3D, periodic on every axis: per axis the same 1D stencil
- * and an independent face noise (Eq. (2.11)). */
-static void orc_step_nd(const orc_params* p, uint32_t step, uint32_t stream,
-                        const double* T, double* Tn, double* G /* dim*Ncells */)
+/* The same in 2D/3D, periodic on every axis: per axis the 1D stencil and an
+ * independent face noise (Eq. (2.11)), summed over the axes. */
+static void orc_increment_nd(const orc_params* p, const double* T, const double* Z, double* G, double* inc)
 {
     const int64_t nc = orc_cells(p);
     int n0 = p->n[0], n1 = p->n[1], n2 = (p->dim == 3) ? p->n[2] : 1;
@@ -261,14 +306,12 @@ static void orc_step_nd(const orc_params* p, uint32_t step, uint32_t stream,
             int xl = (x[a] - 1 + ext[a]) % ext[a];
             int64_t il = i + (int64_t)(xl - x[a]) * stride[a];
             double tface = 0.5 * (T[il] + T[i]);
-            double z = p->stochastic ? orc_normal(p->seed, (uint64_t)a * (uint64_t)nc + (uint64_t)i,
-                                                  step, stream, ORC_TAG_STEP) : 0.0;
-            G[(int64_t)a * nc + i] = orc_flux_amp(p, tface) * z;
+            G[(int64_t)a * nc + i] = orc_flux_amp(p, tface) * Z[(int64_t)a * nc + i];
         }
     }
     for (int64_t i = 0; i < nc; ++i) {
         int x[3] = {(int)(i % n0), (int)((i / n0) % n1), (int)(i / ((int64_t)n0 * n1))};
-        double acc = T[i];
+        double acc = 0.0;
         for (int a = 0; a < p->dim; ++a) {
             int xl = (x[a] - 1 + ext[a]) % ext[a];
             int xr = (x[a] + 1) % ext[a];
@@ -277,20 +320,44 @@ static void orc_step_nd(const orc_params* p, uint32_t step, uint32_t stream,
             acc += p->r * (T[ir] - 2.0 * T[i] + T[il]);
             acc += G[(int64_t)a * nc + ir] - G[(int64_t)a * nc + i];
         }
-        Tn[i] = acc;
+        inc[i] = acc;
     }
+}
+
+static void orc_increment(const orc_params* p, const double* T, orc_work* w)
+{
+    if (p->dim == 1) orc_increment_1d(p, T, w->Z, w->G, w->inc);
+    else orc_increment_nd(p, T, w->Z, w->G, w->inc);
+}
+
+/* One step at absolute index `step`.  Forward Euler (Eq. (3.3)):
+ * Tn = T + inc(T).  Predictor-corrector (Sec. 3): the predictor
+ * T* = T + inc(T) and the corrector Tn = (T + T* + inc(T*)) / 2, where
+ * inc(T*) evaluates the stencil and the face values on T* with the SAME face
+ * normals as the predictor (noise constant over the step). */
+static void orc_advance(const orc_params* p, uint32_t step, uint32_t stream, const double* T, double* Tn,
+                        orc_work* w)
+{
+    const int64_t nc = orc_cells(p);
+    orc_step_normals(p, step, stream, w->Z);
+    orc_increment(p, T, w);
+    if (p->scheme != ORC_PC) {
+        for (int64_t i = 0; i < nc; ++i) Tn[i] = T[i] + w->inc[i];
+        return;
+    }
+    for (int64_t i = 0; i < nc; ++i) w->Ts[i] = T[i] + w->inc[i];
+    orc_increment(p, w->Ts, w);
+    for (int64_t i = 0; i < nc; ++i) Tn[i] = 0.5 * (T[i] + w->Ts[i] + w->inc[i]);
 }
 
 /* Public single-step entry: Tn = step(T) at absolute step index `step`. */
 int orc_step(const orc_params* p, uint32_t step, uint32_t stream, const double* T, double* Tn)
 {
-    int64_t nc = orc_cells(p);
-    double* G = (double*)malloc(sizeof(double) * (size_t)(p->dim * nc + 1));
-    if (!G) return -1;
-    if (p->dim == 1) orc_step_1d(p, step, stream, T, Tn, G);
-    else orc_step_nd(p, step, stream, T, Tn, G);
-    free(G);
-    return 0;
+    orc_work w;
+    int rc = orc_work_alloc(p, &w);
+    if (rc == 0) orc_advance(p, step, stream, T, Tn, &w);
+    orc_work_free(&w);
+    return rc;
 }
 
 /* ----------------------------------------------------------- sampling ---- */
@@ -392,6 +459,7 @@ int orc_run(const orc_params* p, int64_t R, uint32_t stream0, uint32_t step0, in
 {
     if (p->dim < 1 || p->dim > 3 || R < 0 || nsteps < 0) return -2;
     if (p->dim > 1 && p->bc != ORC_PERIODIC) return -2;
+    if (p->scheme != ORC_FE && p->scheme != ORC_PC) return -2;
     if (sum_sk && p->dim > 2) return -2;
     int64_t nc = orc_cells(p);
     int axes_len = p->n[0] + (p->dim >= 2 ? p->n[1] : 0) + (p->dim >= 3 ? p->n[2] : 0);
@@ -419,10 +487,11 @@ int orc_run(const orc_params* p, int64_t R, uint32_t stream0, uint32_t step0, in
     for (int64_t rr = 0; rr < R; ++rr) {
         double* T = state + rr * nc;
         double* Tn = (double*)malloc(sizeof(double) * (size_t)nc);
-        double* G = (double*)malloc(sizeof(double) * (size_t)(p->dim * nc + 1));
         double* work = (double*)malloc(sizeof(double) * (size_t)(nc + 8192));
-        if (!Tn || !G || !work) {
-            free(Tn); free(G); free(work);
+        orc_work ws;
+        int wrc = orc_work_alloc(p, &ws);
+        if (!Tn || !work || wrc != 0) {
+            free(Tn); free(work); orc_work_free(&ws);
 #pragma omp atomic write
             err = -1;
             continue;
@@ -438,14 +507,13 @@ int orc_run(const orc_params* p, int64_t R, uint32_t stream0, uint32_t step0, in
         acc.sum_sk_axes = pska ? pska + rr * axes_len : NULL;
         for (int64_t s = 0; s < nsteps; ++s) {
             uint32_t step = step0 + (uint32_t)s;
-            if (p->dim == 1) orc_step_1d(p, step, stream, T, Tn, G);
-            else orc_step_nd(p, step, stream, T, Tn, G);
+            orc_advance(p, step, stream, T, Tn, &ws);
             memcpy(T, Tn, sizeof(double) * (size_t)nc);
             int64_t m = (int64_t)step + 1;
             if (p->stats_interval > 0 && m % p->stats_interval == 0 && m > p->relax_steps)
                 orc_sample(p, T, tref, &acc, work);
         }
-        free(Tn); free(G); free(work);
+        free(Tn); free(work); orc_work_free(&ws);
     }
     if (!err) {
         if (n_samples) *n_samples += samples_per_real;

@@ -22,6 +22,20 @@ never step a sample path.
 * Stationary covariance of that recursion (discrete Lyapunov equation,
   the discrete-time analogue of the fluctuation-dissipation relation of
   the supplement, Eq. (SM1.6)).
+* Predictor-corrector scheme (Sec. 3: the forward-Euler step as predictor
+  T*, then T' = (T + T* + D(T*) + div G(T*)) / 2 with the same face noise).
+  With F_N = A + sum_f s_f N_f d_f P_f^T and g_N = b + sum_f s_f N_f q_f d_f
+  the heat step is T* = F_N T + g_N and T' = (I + F_N^2) T / 2 +
+  (I + F_N) g_N / 2: affine in T with coefficients polynomial (degree <= 2)
+  in the step's normals, which are independent of T.  The first two moments
+  therefore propagate exactly, and tensor Gauss-Hermite quadrature with 3
+  nodes per face (exact to degree 5 per variable) evaluates the expectations
+  exactly; applied to forward Euler it reproduces the closed recursion above.
+  Deterministic modes are amplified by 1 - x + x^2/2 (Heun) instead of 1 - x,
+  x = r mu; with additive noise the stationary structure factor is
+  eps T^2 N (2 - x) / (2 - x + x^2/2), an O(x^2) deviation from the flat
+  value where forward Euler's is O(x) (the error orders the paper states in
+  its exercises, Sec. 6).
 * Closed forms: forward-Euler equilibrium covariance
   eps T^2 (I + r L / 2)^{-1}, whose r -> 0 limit is eps T^2 I (Eq. (3.10));
   periodic structure factor eps T^2 N / (1 - r mu_k / 2) whose r -> 0 limit is
@@ -297,7 +311,14 @@ def long_range_correlation(N, eps, dT):
     return eps * dT * dT * lo * (N - hi) / N ** 3
 
 
-def sine_mode_solution(N, r, wall_lo, wall_hi, T0, nsteps):
+def amplification(x, scheme="fe"):
+    """Deterministic factor per step of a mode with eigenvalue -x of r L:
+    forward Euler 1 - x; predictor-corrector (Heun) 1 - x + x^2/2."""
+    x = np.asarray(x, dtype=float)
+    return 1.0 - x + (0.5 * x * x if scheme == "pc" else 0.0)
+
+
+def sine_mode_solution(N, r, wall_lo, wall_hi, T0, nsteps, scheme="fe"):
     """Exact deterministic forward-Euler solution with Dirichlet walls:
     T^n = T_lin + sum_m b_m lambda_m^n sin(m pi (i+1/2)/N),
     lambda_m = 1 - 4 r sin^2(m pi/(2N)), b from the initial deviation."""
@@ -307,14 +328,139 @@ def sine_mode_solution(N, r, wall_lo, wall_hi, T0, nsteps):
     m = np.arange(1, N + 1)
     Phi = np.sin(np.pi * np.outer(i + 0.5, m) / N)       # [cell, mode]
     bm = np.linalg.solve(Phi, np.asarray(T0) - tlin)
-    lam = 1.0 - 4.0 * r * np.sin(m * np.pi / (2.0 * N)) ** 2
+    lam = amplification(4.0 * r * np.sin(m * np.pi / (2.0 * N)) ** 2, scheme)
     return tlin + Phi @ (bm * lam ** nsteps)
 
 
-def fourier_mode_solution(N, r, T0, nsteps):
-    """Exact deterministic forward-Euler solution on a periodic grid:
-    each Fourier mode decays by (1 - 4 r sin^2(pi k/N))^n."""
+def fourier_mode_solution(N, r, T0, nsteps, scheme="fe"):
+    """Exact deterministic solution on a periodic grid: each Fourier mode is
+    multiplied per step by the scheme's amplification of
+    x = 4 r sin^2(pi k/N)."""
     k = np.arange(N)
-    lam = 1.0 - 4.0 * r * np.sin(np.pi * k / N) ** 2
+    lam = amplification(4.0 * r * np.sin(np.pi * k / N) ** 2, scheme)
     That = np.fft.fft(np.asarray(T0))
     return np.real(np.fft.ifft(That * lam ** nsteps))
+
+
+def structure_factor(shape, r, eps_amp, scheme="fe"):
+    """Periodic structure factor for k != 0 with additive noise (the
+    linearised heat equation; exact for species): forward Euler
+    eps_amp N / (1 - x/2), predictor-corrector eps_amp N (2 - x) /
+    (2 - x + x^2/2), x = r mu_k (derivation: per mode T' = g T + h eta with
+    g = 1 - x + x^2/2 and h = 1 - x/2, so S = h^2 sigma^2 / (1 - g^2)).
+    Entry k = 0 is set to 0; cells ordered with axis 0 fastest."""
+    dims = list(shape)
+    ncell = int(np.prod(dims))
+    grids = np.meshgrid(*[np.arange(n) for n in reversed(dims)], indexing="ij")
+    mu = np.zeros(grids[0].shape)
+    for g, n in zip(grids, reversed(dims)):
+        mu += 4.0 * np.sin(np.pi * g / n) ** 2
+    x = r * mu
+    if scheme == "pc":
+        S = eps_amp * ncell * (2.0 - x) / (2.0 - x + 0.5 * x * x)
+    else:
+        S = eps_amp * ncell / (1.0 - 0.5 * x)
+    S = S.ravel()
+    S[0] = 0.0
+    return S
+
+
+# ------------------------------------------- exact moments by quadrature --
+
+def gauss_hermite(nvars, npts):
+    """Tensor Gauss-Hermite rule for nvars independent N(0,1) variables:
+    (weights [Q], nodes [Q, nvars]); exact for polynomials of degree
+    <= 2 npts - 1 in each variable."""
+    x, w = np.polynomial.hermite_e.hermegauss(npts)
+    w = w / np.sqrt(2.0 * np.pi)
+    grids = np.meshgrid(*([np.arange(npts)] * nvars), indexing="ij")
+    idx = np.stack([g.ravel() for g in grids], axis=1)
+    return np.prod(w[idx], axis=1), x[idx]
+
+
+def _increment(prob_like, Aminus, b, faces, T, z):
+    """D(T) + div G(T) for face normals z (wall weights applied here)."""
+    r, eps = prob_like["r"], prob_like["eps"]
+    heat = prob_like.get("equation", "heat") == "heat"
+    out = Aminus @ T + b
+    for (P, q, w2, d), zf in zip(faces, z):
+        fv = P @ T + q
+        amp = np.sqrt(2.0 * r * eps * w2) * fv if heat else np.sqrt(2.0 * r * eps * w2 * max(fv, 0.0))
+        out = out + amp * zf * d
+    return out
+
+
+def step_map(prob_like, T, z, ops=None):
+    """One step from state T with face normals z: forward Euler, or the
+    predictor-corrector scheme when prob_like["scheme"] == "pc"."""
+    A, b, faces, _, _ = ops if ops is not None else scheme(prob_like)
+    Am = A - np.eye(len(b))
+    Ts = T + _increment(prob_like, Am, b, faces, T, z)
+    if prob_like.get("scheme", "fe") != "pc":
+        return Ts
+    return 0.5 * (T + Ts + _increment(prob_like, Am, b, faces, Ts, z))
+
+
+def affine_step(prob_like, z, ops=None):
+    """Heat only: (F, g) with step(T) = F T + g for face normals z."""
+    A, b, faces, _, _ = ops if ops is not None else scheme(prob_like)
+    r, eps = prob_like["r"], prob_like["eps"]
+    F = A.copy()
+    g = b.copy()
+    for (P, q, w2, d), zf in zip(faces, z):
+        s = np.sqrt(2.0 * r * eps * w2) * zf
+        F += s * np.outer(d, P)
+        g += s * q * d
+    if prob_like.get("scheme", "fe") == "pc":
+        I = np.eye(len(b))
+        return 0.5 * (I + F @ F), 0.5 * (I + F) @ g
+    return F, g
+
+
+def pooled_expectation_quadrature(prob_like, nsteps, K, relax, step0=0):
+    """Exact expectation of the pooled statistics (as pooled_expectation) for
+    the heat equation under either scheme, propagating E[T] and E[T T^T]
+    through the affine random step with 3-node Gauss-Hermite quadrature over
+    the faces (exact: the integrands have degree <= 4 per normal)."""
+    assert prob_like.get("equation", "heat") == "heat"
+    ops = scheme(prob_like)
+    tref = ops[3]
+    nf = len(ops[2])
+    W, Z = gauss_hermite(nf, 3)
+    maps = [affine_step(prob_like, z, ops) for z in Z]
+    EF = sum(w * F for w, (F, g) in zip(W, maps))
+    Eg = sum(w * g for w, (F, g) in zip(W, maps))
+    m, C = initial_moments(prob_like, tref)
+    S = C + np.outer(m, m)
+    n = len(m)
+    s1 = np.zeros(n)
+    s2 = np.zeros((n, n))
+    cnt = 0
+    for mstep in range(step0 + 1, step0 + nsteps + 1):
+        Sn = np.zeros((n, n))
+        for w, (F, g) in zip(W, maps):
+            Fm = F @ m
+            Sn += w * (F @ S @ F.T + np.outer(Fm, g) + np.outer(g, Fm) + np.outer(g, g))
+        m = EF @ m + Eg
+        S = 0.5 * (Sn + Sn.T)
+        if mstep % K == 0 and mstep > relax:
+            s1 += m - tref
+            s2 += S - np.outer(m, tref) - np.outer(tref, m) + np.outer(tref, tref)
+            cnt += 1
+    C = S - np.outer(m, m)
+    return {"count": cnt, "mean_delta": s1 / cnt, "second": s2 / cnt,
+            "final_mean": m, "final_cov": C, "tref": tref}
+
+
+def first_step_quadrature(prob_like, T0, npts):
+    """Mean and covariance of one step from the fixed state T0 by npts-node
+    Gauss-Hermite quadrature over the faces (exact for heat with npts >= 2;
+    for species the integrand is smooth where the face values stay positive,
+    and the rule converges rapidly in npts)."""
+    ops = scheme(prob_like)
+    W, Z = gauss_hermite(len(ops[2]), npts)
+    T0 = np.asarray(T0, dtype=float)
+    vals = np.array([step_map(prob_like, T0, z, ops) for z in Z])
+    mean = W @ vals
+    dev = vals - mean
+    return mean, (dev * W[:, None]).T @ dev

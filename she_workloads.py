@@ -43,7 +43,7 @@ def _base(**kw):
         "dt": 0.2, "seed": 0, "realizations": 16,
         "stochastic": 1, "perturb_ic": 1, "stats_interval": 10,
         "relax_steps": 0, "want_cov": 0, "want_sk": 0,
-        "precision": "fp64", "steps": 10_000,
+        "precision": "fp64", "steps": 10_000, "scheme": "fe",
     }
     p.update(kw)
     return p
