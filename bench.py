@@ -112,10 +112,20 @@ WORKLOADS = {
               "realizations, FP32 state, moments and full 256x256 equal-time covariance "
               "(tcgen05) every 10 steps after 1e5 steps"),
         chunk=10_000, ops=25.0 + 5.5 + 4.0 + 6.0, bytes=None,
-        kernel="k_step1d_cov<32,8,dirichlet,heat>",
+        kernel="k_step1d_cov<16,16,dirichlet,heat>",
         # DRAM read + write of one launch (2560 steps, mostly the per-CTA
         # covariance flush), ncu capture in profiles/k_step1d_cov_gradient_rod.md
-        traffic=dict(bytes=100.744192e6 + 41.423616e6, realizations=4096)),
+        traffic=dict(bytes=100.734208e6 + 41.664512e6, realizations=4096)),
+    "gradient_rod_pc": dict(
+        make=lambda W: W.gradient_rod(scheme="pc"),
+        desc=("the gradient_rod configuration (1D SHE rod, 256 cells, walls 1 and 2, eps=1e-3, r=0.2, "
+              "4096 realizations, FP32, moments and the 256x256 covariance on tcgen05 every 10 steps "
+              "after 1e5) stepped by the predictor-corrector scheme of Sec. 3"),
+        # one normal per face as forward Euler, the face flux and update twice
+        # (predictor, corrector on T*), and the trapezoid (T + T* + inc) / 2
+        chunk=10_000, ops=25.0 + 5.5 + 2 * (4.0 + 6.0) + 3.0, bytes=None,
+        kernel="k_step1d_cov<16,16,dirichlet,heat,pc>",
+        traffic=dict(bytes=100.739072e6 + 41.579008e6, realizations=4096)),   # profiles/k_step1d_cov_pc_gradient_rod_pc.md
     "species_2d": dict(
         make=lambda W: W.species_2d(want_sk=1),
         desc=("2D stochastic species diffusion, 256x256 periodic, D=1, r=0.1, eps_c=1e-3, c=1 + "
@@ -299,7 +309,7 @@ def run_ours(args):
     p64 = dict(p)
     # 1D: the plain three-launches-per-step FP64 form; 2D/3D (streaming
     # kernels already launch once per step): the same kernel in FP64
-    kind64 = "plain" if p["dim"] == 1 else "auto"
+    kind64 = "plain" if p["dim"] == 1 and p.get("scheme", "fe") == "fe" else "auto"
     if batch:     # same total cells as 256-cell rows in the plain FP64 form
         p64 = dict(p, n=(256, 1, 1), realizations=max(1, cells // 256))
     sim64 = she.Simulation(p64, stream=stream, precision="fp64", kernel=kind64, stream_offset=rank * R,

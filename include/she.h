@@ -11,6 +11,10 @@
  *   - the forward-Euler scheme on a cell-centred grid, Sec. 3, Eq. (3.3),
  *     face temperature = arithmetic mean of the two neighbours, discrete
  *     noise Z = N(0,1)/sqrt(dV dt), Eq. (3.6)-(3.7);
+ *   - the predictor-corrector scheme, Sec. 3 (the trapezoidal scheme written
+ *     after Eq. (3.3)): the forward-Euler step as predictor T*, then
+ *     T' = (T + T* + D(T*) + div G(T*)) / 2 with the face values and the
+ *     stencil on T* and the same face noise (1D, fused kernels only);
  *   - Dirichlet walls: boundary stencil of Eq. (3.8) and the sqrt(2) factor on
  *     the wall-face noise (Sec. 3, text after Eq. (3.8)); periodic wrap;
  *   - stochastic species diffusion, Sec. 4, Eq. (4.7) (noise amplitude
@@ -79,7 +83,7 @@ typedef enum she_status {
 enum { SHE_HEAT = 0, SHE_SPECIES = 1 };        /* equation */
 enum { SHE_PERIODIC = 0, SHE_DIRICHLET = 1 };  /* boundary */
 enum { SHE_FP32 = 0, SHE_FP64 = 1 };           /* state/step precision */
-enum { SHE_FE = 0 };                           /* scheme: forward Euler */
+enum { SHE_FE = 0, SHE_PC = 1 };               /* scheme: forward Euler, predictor-corrector */
 enum { SHE_SK_FULL = 1, SHE_SK_AXES = 2 };     /* want_sk bits */
 enum { SHE_KERNEL_AUTO = 0,                    /* fused on-chip / streaming kernels */
        SHE_KERNEL_PLAIN = 1 };                 /* plain one-launch-per-step form */
@@ -108,7 +112,8 @@ typedef struct she_params {
     double dt;            /* time step */
     uint64_t seed;        /* Philox key */
     int64_t realizations; /* independent sample paths, >= 1 */
-    int32_t scheme;       /* SHE_FE */
+    int32_t scheme;       /* SHE_FE, or SHE_PC (dim 1, kernel auto, N <= 512;
+                             otherwise SHE_ERR_UNSUPPORTED) */
     int32_t stochastic;   /* 1: thermal noise on; 0: deterministic (alpha = 0) */
     int32_t perturb_ic;   /* 1: T_ref + sigma N(0,1) per cell, sigma^2 = eps T_mid^2
                              (heat) or eps_c c_mid (species); zero-sum on periodic grids */
@@ -265,7 +270,7 @@ she_status she_syrk_probe(const float* X, int32_t K, int32_t N, double* C);
  * form of a handle created with kernel = SHE_KERNEL_PLAIN (same results);
  * no sampling.  Uses from `p`: dim (must be 1), n, dx, area, equation, bc,
  * kappa, rho_cv, kB, D, n0, walls, dt, seed, realizations, stochastic,
- * precision (must be SHE_FP64), stream_offset, stream.
+ * precision (must be SHE_FP64), scheme (must be SHE_FE), stream_offset, stream.
  * The face fluxes go to one fixed device array of SHE_NOALLOC_MAX_FACES
  * doubles (8 MiB, held by every GPU that loads the library until the process
  * exits); realizations * (N + 1) above that is rejected with

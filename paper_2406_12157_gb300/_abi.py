@@ -27,6 +27,7 @@ SHE_HEAT, SHE_SPECIES = 0, 1
 SHE_PERIODIC, SHE_DIRICHLET = 0, 1
 SHE_FP32, SHE_FP64 = 0, 1
 SHE_FE = 0
+SHE_PC = 1
 SHE_SK_FULL, SHE_SK_AXES = 1, 2
 SHE_KERNEL_AUTO, SHE_KERNEL_PLAIN = 0, 1
 

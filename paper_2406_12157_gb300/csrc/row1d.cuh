@@ -1,5 +1,6 @@
-// row1d.cuh -- one forward-Euler step of a 1D row held in registers by a
-// segment of LPR lanes (C cells per lane), shared by the 1D step kernels.
+// row1d.cuh -- one forward-Euler or predictor-corrector step of a 1D row
+// held in registers by a segment of LPR lanes (C cells per lane), shared by
+// the 1D step kernels.
 //
 // Method (Sec. 3): T_i' = T_i + r (T_{i+1} - 2 T_i + T_{i-1}) + G_{i+1} - G_i,
 // Eq. (3.3), with the face flux G_f = amp(T_face) N_f, T_face the mean of the
@@ -142,7 +143,29 @@ struct Row1D {
         return (s_half * (lo + hi)) * z;
     }
 
-    // advance the row T by the step with absolute index n
+    // Flux through the right Dirichlet wall at step n (0 if periodic or
+    // deterministic): its normal is slot n%4 of block (0, n/4, stream, 2);
+    // segment lanes 0..WL-1 hold the blocks of a 4*WL-step window.
+    __device__ __forceinline__ Real high_wall_flux(uint32_t n)
+    {
+        Real g_high = Real(0);
+        if (DIR && stochastic) {
+            constexpr int WL = LPR >= 8 ? 8 : 4;
+            const int sl = i0 / C;
+            const uint32_t win = n / (uint32_t)(4 * WL);
+            if (win != wwin) {
+                wwin = win;
+                const uint4 u = noise_block(make_uint4(0u, win * (uint32_t)WL + (uint32_t)(sl % WL), stream, 2u));
+                box_muller4(u, wz);
+            }
+            const uint32_t slot = n & 3u;
+            const Real v = slot == 0 ? wz[0] : slot == 1 ? wz[1] : slot == 2 ? wz[2] : wz[3];
+            g_high = g_wall_amp * __shfl_sync(FULL, v, (int)((n % (uint32_t)(4 * WL)) >> 2), LPR);
+        }
+        return g_high;
+    }
+
+    // advance the row T by the forward-Euler step with absolute index n
     __device__ __forceinline__ void step(Real (&T)[C], uint32_t n)
     {
         const Real left_nb = __shfl_up_sync(FULL, T[C - 1], 1, LPR);
@@ -158,22 +181,7 @@ struct Row1D {
             wrap_lo = __shfl_sync(FULL, mine, last_sl, LPR);
             wrap_hi = __shfl_sync(FULL, T[0], 0, LPR);
         }
-        // Right-wall noise: slot n%4 of block (0, n/4, stream, 2); segment
-        // lanes 0..WL-1 hold the blocks of a 4*WL-step window.
-        Real g_high = Real(0);
-        if (DIR && stochastic) {
-            constexpr int WL = LPR >= 8 ? 8 : 4;
-            const int sl = i0 / C;
-            const uint32_t win = n / (uint32_t)(4 * WL);
-            if (win != wwin) {
-                wwin = win;
-                const uint4 u = noise_block(make_uint4(0u, win * (uint32_t)WL + (uint32_t)(sl % WL), stream, 2u));
-                box_muller4(u, wz);
-            }
-            const uint32_t slot = n & 3u;
-            const Real v = slot == 0 ? wz[0] : slot == 1 ? wz[1] : slot == 2 ? wz[2] : wz[3];
-            g_high = g_wall_amp * __shfl_sync(FULL, v, (int)((n % (uint32_t)(4 * WL)) >> 2), LPR);
-        }
+        const Real g_high = high_wall_flux(n);
 
         // Pipeline over this lane's faces f = i0 + j (the low face of cell
         // i0 + j): compute G_f, then update cell f-1 in place (it needs G_{f-1}
@@ -227,6 +235,91 @@ struct Row1D {
             }
             T[C - 1] = tc + r * (tr - Real(2) * tc + old_prev) + (gr - g_prev);
         }
+    }
+
+    // inc = D(X) + G_hi(X) - G_lo(X) of every cell of the lane, the face
+    // fluxes built from X with this step's normals z (the wall fluxes g_low
+    // at the left Dirichlet wall and g_high at the right one do not depend on
+    // X).  Cells of a ragged lane beyond N get values that are never used.
+    __device__ __forceinline__ void increment(const Real (&X)[C], const Real (&z)[C], Real g_high,
+                                              Real (&inc)[C]) const
+    {
+        const Real left_nb = __shfl_up_sync(FULL, X[C - 1], 1, LPR);
+        const Real right_nb = __shfl_down_sync(FULL, X[0], 1, LPR);
+        Real wrap_lo = Real(0), wrap_hi = Real(0);   // periodic: X_{N-1}, X_0
+        if (!DIR) {
+            Real mine = X[C - 1];
+            if (RAGGED) {
+#pragma unroll
+                for (int j = 0; j < C; ++j)
+                    if (j == jlast) mine = X[j];
+            }
+            wrap_lo = __shfl_sync(FULL, mine, last_sl, LPR);
+            wrap_hi = __shfl_sync(FULL, X[0], 0, LPR);
+        }
+        // the lane's first face (low face of cell i0)
+        Real g_first = flux(left_nb, X[0], z[0]);
+        Real xl = left_nb;
+        if (first_sl) {
+            g_first = DIR ? g_low_amp * z[0] : flux(wrap_lo, X[0], z[0]);
+            xl = DIR ? Real(2) * wlo - X[0] : wrap_lo;
+        }
+        const Real g_zero = DIR ? Real(0) : __shfl_sync(FULL, g_first, 0, LPR);
+        Real g_prev = g_first;
+#pragma unroll
+        for (int j = 0; j + 1 < C; ++j) {
+            Real gf = flux(X[j], X[j + 1], z[j + 1]);   // face between cells j and j+1
+            Real tr = X[j + 1];
+            if (RAGGED && i0 + j + 1 == N) {            // ragged lane: the high face
+                gf = DIR ? g_high : g_zero;
+                tr = DIR ? Real(2) * whi - X[j] : wrap_hi;
+            }
+            inc[j] = r * (tr - Real(2) * X[j] + xl) + (gf - g_prev);
+            xl = X[j];
+            g_prev = gf;
+        }
+        // last cell of the lane: its high face is the next lane's first face,
+        // or the wall/wrap face when it is cell N-1
+        const Real g_next = __shfl_down_sync(FULL, g_first, 1, LPR);
+        Real tr = right_nb;
+        Real gr = g_next;
+        if ((!RAGGED && tail_sl) || (RAGGED && i0 + C - 1 == N - 1)) {
+            tr = DIR ? Real(2) * whi - X[C - 1] : wrap_hi;
+            gr = DIR ? g_high : g_zero;
+        }
+        inc[C - 1] = r * (tr - Real(2) * X[C - 1] + xl) + (gr - g_prev);
+    }
+
+    // advance the row T by the predictor-corrector step with absolute index
+    // n (Sec. 3): the step's normals are drawn once; the predictor is the
+    // forward-Euler step T* = T + inc(T); the corrector takes the face values
+    // and the stencil on T* with the same normals:
+    // T' = ((T + T*) + inc(T*)) / 2.
+    __device__ __forceinline__ void step_pc(Real (&T)[C], uint32_t n)
+    {
+        Real z[C];
+#pragma unroll
+        for (int g = 0; g < C / 4; ++g) {
+            Real v[4] = {Real(0), Real(0), Real(0), Real(0)};
+            if (stochastic) box_muller4(noise_block(make_uint4(q0 + (uint32_t)g, n, stream, 0u)), v);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) z[4 * g + t] = v[t];
+        }
+        const Real g_high = high_wall_flux(n);
+        Real Ts[C], inc[C];
+        increment(T, z, g_high, inc);
+#pragma unroll
+        for (int j = 0; j < C; ++j) Ts[j] = T[j] + inc[j];
+        increment(Ts, z, g_high, inc);
+#pragma unroll
+        for (int j = 0; j < C; ++j) T[j] = Real(0.5) * ((T[j] + Ts[j]) + inc[j]);
+    }
+
+    template <bool PC>
+    __device__ __forceinline__ void advance(Real (&T)[C], uint32_t n)
+    {
+        if constexpr (PC) step_pc(T, n);
+        else step(T, n);
     }
 };
 

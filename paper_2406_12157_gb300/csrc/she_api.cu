@@ -68,6 +68,7 @@ she_status convert(const she_params& p, she::Problem& out, std::string& msg)
         return SHE_ERR_INVALID_ARG;
     }
     if (p.equation != SHE_HEAT && p.equation != SHE_SPECIES) { msg = "she: bad equation"; return SHE_ERR_INVALID_ARG; }
+    if (p.scheme != SHE_FE && p.scheme != SHE_PC) { msg = "she: bad scheme"; return SHE_ERR_INVALID_ARG; }
     if (p.bc != SHE_PERIODIC && p.bc != SHE_DIRICHLET) { msg = "she: bad boundary"; return SHE_ERR_INVALID_ARG; }
     if (p.bc == SHE_DIRICHLET && p.dim > 1) {
         msg = "she: Dirichlet walls are supported in 1D only (2D/3D grids are periodic)";
@@ -107,6 +108,7 @@ she_status convert(const she_params& p, she::Problem& out, std::string& msg)
     out.bc = p.bc;
     out.r = r;
     out.eps = eps;
+    out.scheme = p.scheme;
     out.wall_lo = p.wall_lo;
     out.wall_hi = p.wall_hi;
     out.seed = p.seed;
@@ -208,7 +210,10 @@ she_status she_init(const she_params* p, she_handle** out)
     if (st == SHE_OK && p->precision != SHE_FP32 && p->precision != SHE_FP64) {
         st = SHE_ERR_INVALID_ARG; msg = "she: precision must be SHE_FP32 or SHE_FP64";
     }
-    if (st == SHE_OK && p->scheme != SHE_FE) { st = SHE_ERR_UNSUPPORTED; msg = "she: only the forward-Euler scheme"; }
+    if (st == SHE_OK && p->scheme == SHE_PC && (p->dim != 1 || p->kernel != SHE_KERNEL_AUTO || p->n[0] > 512)) {
+        st = SHE_ERR_UNSUPPORTED;
+        msg = "she: the predictor-corrector scheme runs on the fused 1D kernels (dim 1, kernel auto, N <= 512)";
+    }
     if (st == SHE_OK && p->kernel != SHE_KERNEL_AUTO && p->kernel != SHE_KERNEL_PLAIN) {
         st = SHE_ERR_INVALID_ARG; msg = "she: bad kernel selector";
     }
@@ -825,8 +830,9 @@ she_status she_step_plain_noalloc(const she_params* p, const double* T_in, doubl
         return st;
     }
     if (p->dim != 1 || p->realizations < 1 || p->precision != SHE_FP64 || step > (uint64_t)0xffffffffu ||
+        p->scheme != SHE_FE ||
         p->stream_offset < 0 || (int64_t)p->stream_offset + p->realizations > ((int64_t)1 << 32)) {
-        fprintf(stderr, "she_step_plain_noalloc: needs dim 1, FP64, realizations >= 1, step < 2^32\n");
+        fprintf(stderr, "she_step_plain_noalloc: needs dim 1, FP64, forward Euler, realizations >= 1, step < 2^32\n");
         return SHE_ERR_INVALID_ARG;
     }
     const int64_t faces = p->realizations * (int64_t)(prob.n[0] + 1);

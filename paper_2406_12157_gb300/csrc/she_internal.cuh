@@ -30,6 +30,7 @@ struct Problem {
     double eps = 0.0;     // k_B/(rho c_V dV)   (species: 1/(n0 dV))
     double wall_lo = 0.0, wall_hi = 0.0;
     uint64_t seed = 0;
+    int scheme = SHE_FE;  // SHE_FE or SHE_PC
 };
 
 // Arguments of the 1D step kernels (one realization per warp).

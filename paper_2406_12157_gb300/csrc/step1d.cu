@@ -39,7 +39,7 @@ namespace she {
 template <typename Real, int C>
 constexpr int step1d_smem_per_warp() { return 2 * C * 32 * (int)sizeof(Real); }
 
-template <typename Real, int C, int LPR, bool DIR, bool SPECIES, bool RAGGED, int MINB>
+template <typename Real, int C, int LPR, bool DIR, bool SPECIES, bool RAGGED, int MINB, bool PC>
 __global__ void __launch_bounds__(kWarpsPerBlock1D * 32, MINB)
 k_step1d(const __grid_constant__ Step1DArgs<Real> a)
 {
@@ -77,7 +77,7 @@ k_step1d(const __grid_constant__ Step1DArgs<Real> a)
     int nsamp = 0;
 
     for (int s = 0; s < a.nsteps; ++s) {
-        rowst.step(T, a.step0 + (uint32_t)s);
+        rowst.template advance<PC>(T, a.step0 + (uint32_t)s);
         if (s == next_s) {                 // sample after step m = n + 1 (Eq. (3.9))
             next_s += a.K;
             ++nsamp;
@@ -117,7 +117,7 @@ k_step1d(const __grid_constant__ Step1DArgs<Real> a)
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.flags, 1);
 }
 
-template <typename Real, int C, int LPR, bool DIR, bool SP, int MINB>
+template <typename Real, int C, int LPR, bool DIR, bool SP, int MINB, bool PC = false>
 static cudaError_t launch_layout(const Step1DArgs<Real>& a, cudaStream_t st)
 {
     constexpr int RPW = 32 / LPR;
@@ -126,11 +126,11 @@ static cudaError_t launch_layout(const Step1DArgs<Real>& a, cudaStream_t st)
     const dim3 grid((warps + kWarpsPerBlock1D - 1) / kWarpsPerBlock1D);
     const int smem = kWarpsPerBlock1D * step1d_smem_per_warp<Real, C>();
     if (a.N == LPR * C) {
-        auto k = k_step1d<Real, C, LPR, DIR, SP, false, MINB>;
+        auto k = k_step1d<Real, C, LPR, DIR, SP, false, MINB, PC>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         k<<<grid, block, smem, st>>>(a);
     } else {
-        auto k = k_step1d<Real, C, LPR, DIR, SP, true, MINB>;
+        auto k = k_step1d<Real, C, LPR, DIR, SP, true, MINB, PC>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         k<<<grid, block, smem, st>>>(a);
     }
@@ -161,6 +161,36 @@ static cudaError_t launch_ds(const Step1DArgs<Real>& a, int layout, cudaStream_t
     case 1632: return launch_layout_r<Real, 16, 32, DIR, SP, 4>(a, st);
     case 3208: return launch_layout_r<Real, 32, 8, DIR, SP, 2>(a, st);
     case 3232: return launch_layout_r<Real, 32, 32, DIR, SP, 1>(a, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// Predictor-corrector layouts: the step keeps the row, the predictor row, an
+// increment and the step's normals (4 C values per lane), so rows longer
+// than 128 cells use 8 or 16 cells per lane; rows of more than 512 cells are
+// not supported (0).
+static int pick_layout_pc(int N)
+{
+    if (N <= 16) return 404;
+    if (N <= 32) return 408;
+    if (N <= 64) return 416;
+    if (N <= 128) return 432;
+    if (N <= 256) return 832;
+    if (N <= 512) return 1632;
+    return 0;
+}
+
+template <typename Real, bool DIR, bool SP>
+static cudaError_t launch_ds_pc(const Step1DArgs<Real>& a, int layout, cudaStream_t st)
+{
+    constexpr bool F = sizeof(Real) == 4;
+    switch (layout) {
+    case 404: return launch_layout<Real, 4, 4, DIR, SP, F ? 8 : 4, true>(a, st);
+    case 408: return launch_layout<Real, 4, 8, DIR, SP, F ? 8 : 4, true>(a, st);
+    case 416: return launch_layout<Real, 4, 16, DIR, SP, F ? 8 : 4, true>(a, st);
+    case 432: return launch_layout<Real, 4, 32, DIR, SP, F ? 8 : 4, true>(a, st);
+    case 832: return launch_layout<Real, 8, 32, DIR, SP, F ? 6 : 3, true>(a, st);
+    case 1632: return launch_layout<Real, 16, 32, DIR, SP, F ? 3 : 2, true>(a, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -216,6 +246,15 @@ static cudaError_t launch_fused(Handle& h, uint32_t step0, int nsteps)
     a.stochastic = h.stochastic;
     const bool dir = h.prob.bc == SHE_DIRICHLET;
     const bool sp = h.prob.equation == SHE_SPECIES;
+    if (h.prob.scheme == SHE_PC) {
+        const int layout = pick_layout_pc(a.N);
+        if (dir) {
+            if (sp) return launch_ds_pc<Real, true, true>(a, layout, h.stream);
+            return launch_ds_pc<Real, true, false>(a, layout, h.stream);
+        }
+        if (sp) return launch_ds_pc<Real, false, true>(a, layout, h.stream);
+        return launch_ds_pc<Real, false, false>(a, layout, h.stream);
+    }
     const int layout = pick_layout(a.N);
     if (dir) {
         if (sp) return launch_ds<Real, true, true>(a, layout, h.stream);

@@ -86,7 +86,7 @@ __device__ __noinline__ int cov_mma_issue(unsigned char* base, uint64_t* full, u
     return ns;
 }
 
-template <int C, int LPR, bool DIR, bool SPECIES, bool RAGGED>
+template <int C, int LPR, bool DIR, bool SPECIES, bool RAGGED, bool PC>
 __global__ void __launch_bounds__(32 * LPR, 1)
 k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
 {
@@ -184,7 +184,7 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
         nsnap = __shfl_sync(FULL, nsnap, 0);
     } else
     for (int s = 0; s < a.nsteps; ++s) {
-        if (warp_active) rowst.step(T, a.step0 + (uint32_t)s);
+        if (warp_active) rowst.template advance<PC>(T, a.step0 + (uint32_t)s);
         if (s != next_s) continue;
         next_s += a.K;
         const int b = nsnap & 1;
@@ -308,38 +308,57 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
     }
 }
 
-template <int C, int LPR, bool DIR, bool SP>
+template <int C, int LPR, bool DIR, bool SP, bool PC>
 static cudaError_t launch_cov_layout(const Step1DArgs<float>& a, const CovArgs& c, int grid, cudaStream_t st)
 {
     const int smem = cov_smem_bytes<C>(LPR);
     if (a.N == C * LPR) {
-        auto k = k_step1d_cov<C, LPR, DIR, SP, false>;
+        auto k = k_step1d_cov<C, LPR, DIR, SP, false, PC>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         k<<<grid, 32 * LPR, smem, st>>>(a, c);
     } else {
-        auto k = k_step1d_cov<C, LPR, DIR, SP, true>;
+        auto k = k_step1d_cov<C, LPR, DIR, SP, true, PC>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         k<<<grid, 32 * LPR, smem, st>>>(a, c);
     }
     return cudaGetLastError();
 }
 
-// realization slots per CTA of the layout chosen for N: (warps - 1) x (32 / LPR)
-static int cov_slots_per_cta(int N)
+// Lanes per realization of the layout chosen for N: 4-cell layouts up to 128
+// cells, above 16 cells x 16 lanes (15 stepping warps per CTA, two
+// realizations each; measured faster than 32 cells x 8 lanes, whose 7
+// stepping warps leave one SMSP with a single warp: 3.99 vs 4.14 ms per
+// 2560-step launch at 256 x 4096, and the predictor-corrector step needs the
+// registers anyway).
+static int cov_lpr(int N, bool pc)
 {
-    const int lpr = N <= 16 ? 4 : N <= 32 ? 8 : N <= 64 ? 16 : N <= 128 ? 32 : 8;
+    (void)pc;
+    return N <= 16 ? 4 : N <= 32 ? 8 : N <= 64 ? 16 : N <= 128 ? 32 : 16;
+}
+
+// realization slots per CTA of that layout: (warps - 1) x (32 / LPR)
+static int cov_slots_per_cta(int N, bool pc)
+{
+    const int lpr = cov_lpr(N, pc);
     return (lpr - 1) * (32 / lpr);
 }
 
-template <bool DIR, bool SP>
+template <bool DIR, bool SP, bool PC>
 static cudaError_t launch_cov_ds(const Step1DArgs<float>& a, const CovArgs& c, int grid, cudaStream_t st)
 {
     const int N = a.N;
-    if (N <= 16) return launch_cov_layout<4, 4, DIR, SP>(a, c, grid, st);
-    if (N <= 32) return launch_cov_layout<4, 8, DIR, SP>(a, c, grid, st);
-    if (N <= 64) return launch_cov_layout<4, 16, DIR, SP>(a, c, grid, st);
-    if (N <= 128) return launch_cov_layout<4, 32, DIR, SP>(a, c, grid, st);
-    return launch_cov_layout<32, 8, DIR, SP>(a, c, grid, st);
+    if (N <= 16) return launch_cov_layout<4, 4, DIR, SP, PC>(a, c, grid, st);
+    if (N <= 32) return launch_cov_layout<4, 8, DIR, SP, PC>(a, c, grid, st);
+    if (N <= 64) return launch_cov_layout<4, 16, DIR, SP, PC>(a, c, grid, st);
+    if (N <= 128) return launch_cov_layout<4, 32, DIR, SP, PC>(a, c, grid, st);
+    return launch_cov_layout<16, 16, DIR, SP, PC>(a, c, grid, st);
+}
+
+template <bool DIR, bool SP>
+static cudaError_t launch_cov_scheme(const Step1DArgs<float>& a, const CovArgs& c, int grid, bool pc, cudaStream_t st)
+{
+    if (pc) return launch_cov_ds<DIR, SP, true>(a, c, grid, st);
+    return launch_cov_ds<DIR, SP, false>(a, c, grid, st);
 }
 
 cudaError_t launch_step1d_cov(Handle& h, uint32_t step0, int nsteps, bool has_samples)
@@ -368,7 +387,8 @@ cudaError_t launch_step1d_cov(Handle& h, uint32_t step0, int nsteps, bool has_sa
     const bool sp = h.prob.equation == SHE_SPECIES;
     // waves of at most (stepper warps x realizations per warp) per CTA
     const int G = h.cov_ctas;
-    const int64_t per_wave = (int64_t)cov_slots_per_cta(a.N) * G;
+    const bool pc = h.prob.scheme == SHE_PC;
+    const int64_t per_wave = (int64_t)cov_slots_per_cta(a.N, pc) * G;
     for (int64_t rb = 0; rb < h.R; rb += per_wave) {
         CovArgs c;
         c.partial = h.d_cov_partial;
@@ -377,8 +397,12 @@ cudaError_t launch_step1d_cov(Handle& h, uint32_t step0, int nsteps, bool has_sa
         c.has_samples = has_samples ? 1 : 0;
         const int grid = (int)std::min<int64_t>(G, c.r_count);
         cudaError_t e;
-        if (dir) e = sp ? launch_cov_ds<true, true>(a, c, grid, h.stream) : launch_cov_ds<true, false>(a, c, grid, h.stream);
-        else e = sp ? launch_cov_ds<false, true>(a, c, grid, h.stream) : launch_cov_ds<false, false>(a, c, grid, h.stream);
+        if (dir)
+            e = sp ? launch_cov_scheme<true, true>(a, c, grid, pc, h.stream)
+                   : launch_cov_scheme<true, false>(a, c, grid, pc, h.stream);
+        else
+            e = sp ? launch_cov_scheme<false, true>(a, c, grid, pc, h.stream)
+                   : launch_cov_scheme<false, false>(a, c, grid, pc, h.stream);
         h.launches += 1;
         if (e != cudaSuccess) return e;
     }
