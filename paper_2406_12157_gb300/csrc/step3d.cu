@@ -37,11 +37,10 @@ k_step3d(const __grid_constant__ Step3DArgs<Real> a)
 {
     static_assert(C % 4 == 0, "cells per lane must be a multiple of 4");
     constexpr unsigned FULL = 0xffffffffu;
-    // smem: 2 stages x [(Y + 2) rows of T + (Y + 1) rows of y-face flux] x nx
+    // smem: 3 stages x (Y + 2) rows of T + 2 stages x (Y + 1) rows of y-face flux, x nx
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Real* sm = reinterpret_cast<Real*>(smem_raw);
     const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const int stage_elems = (2 * kY3 + 3) * nx;
 
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
@@ -94,42 +93,71 @@ k_step3d(const __grid_constant__ Step3DArgs<Real> a)
         return (uint32_t)((((int64_t)wrap_once(zz, nz) * ny + yy) * nx) + i0);
     };
 
+    // Shared memory: the rows of plane p (halo y0-1, the tile's rows, halo
+    // y0+Y) in stage p % 3, the low y-face fluxes of plane p in stage p % 2.
+    // One CTA barrier per plane: iteration z publishes the rows of plane z+1,
+    // synchronises, computes the y-faces of plane z+1 and updates plane z with
+    // the y-faces computed in the previous iteration.  Three row stages keep
+    // a publication of plane z+1 off the rows of plane z-2, which a slower
+    // warp may still be reading (it has passed barrier z-1, so it is past
+    // iteration z-2, not necessarily past iteration z-1 -- which reads plane
+    // z-1, stage (z-1) % 3); two y-face stages suffice because the faces of
+    // plane z+1 are written after barrier z, which every reader of plane z-1's
+    // faces has passed.
+    const int rows_elems = (kY3 + 2) * nx, gy_elems = (kY3 + 1) * nx;
+    auto srow_of = [&](int p) { return sm + (size_t)(p % 3) * rows_elems; };
+    auto sgy_of = [&](int p) { return sm + (size_t)3 * rows_elems + (size_t)(p & 1) * gy_elems; };
+    // publish this warp's row v of plane p and, for warps 0 and 1, the halo row hv
+    auto publish = [&](int p, const Real (&v)[C], const Real (&hv)[C]) {
+        Real* srow = srow_of(p);
+        if (row_active) vstore<C>(srow + (size_t)(w + 1) * nx + i0, v);
+        if (w == 0 || w == 1) vstore<C>(srow + (size_t)(w == 0 ? 0 : nrows + 1) * nx + i0, hv);
+    };
+    // low y-face of this warp's row v of plane p (between y-1 and y); warp 0
+    // also does the top face of the tile (between the last row and the high halo)
+    auto yfaces = [&](int p, const Real (&v)[C]) {
+        const Real* srow = srow_of(p);
+        Real* sgy = sgy_of(p);
+        Real lo[C], g[C];
+        vload<C>(srow + (size_t)w * nx + i0, lo);
+        if (row_active) {
+            face_row(lo, v, (uint32_t)ncell + lin(y, p), g);
+            vstore<C>(sgy + (size_t)w * nx + i0, g);
+        }
+        if (w == 0) {
+            Real lo2[C], hi2[C];
+            vload<C>(srow + (size_t)nrows * nx + i0, lo2);
+            vload<C>(srow + (size_t)(nrows + 1) * nx + i0, hi2);
+            face_row(lo2, hi2, (uint32_t)ncell + lin(yh, p), g);
+            vstore<C>(sgy + (size_t)nrows * nx + i0, g);
+        }
+    };
+
     Real prev[C], cur[C], nxt[C], gz_cur[C], gz_nxt[C];
     load_row(yc, z0 - 1, prev);
     load_row(yc, z0, cur);
     face_row(prev, cur, (uint32_t)(2 * ncell) + lin(yc, z0), gz_cur);
+    {   // prologue: the rows and the y-faces of plane z0
+        Real hv[C];
+        if (w == 0 || w == 1) load_row(w == 0 ? yl : yh, z0, hv);
+        publish(z0, cur, hv);
+        __syncthreads();
+        yfaces(z0, cur);
+    }
 
     for (int z = z0; z < z1; ++z) {
-        Real* st = sm + (size_t)(z & 1) * stage_elems;
-        Real* srow = st;                                  // rows 0..Y+1: y0-1 .. y0+Y
-        Real* sgy = st + (kY3 + 2) * nx;                  // rows 0..Y: low y-faces of y0 .. y0+Y
-        // warps 0 and 1 fetch the halo rows first (their latency overlaps the z faces)
+        const bool more = z + 1 < z1;
+        // rows of plane z+1 (the warps 0 and 1 also fetch the halo rows; the
+        // latency overlaps the z faces)
         Real hv[C];
-        if (w == 0 || w == 1) load_row(w == 0 ? yl : yh, z, hv);
+        if (more && (w == 0 || w == 1)) load_row(w == 0 ? yl : yh, z + 1, hv);
         load_row(yc, z + 1, nxt);
         face_row(cur, nxt, (uint32_t)(2 * ncell) + lin(yc, z + 1), gz_nxt);
-        // publish this warp's row of plane z and the halo rows
-        if (row_active) vstore<C>(srow + (size_t)(w + 1) * nx + i0, cur);
-        if (w == 0 || w == 1) vstore<C>(srow + (size_t)(w == 0 ? 0 : nrows + 1) * nx + i0, hv);
+        if (more) publish(z + 1, nxt, hv);
         __syncthreads();
-        // low y-face of this row (between y-1 and y); warp 0 also does the
-        // top face of the tile (between the last row and the high halo)
-        {
-            Real lo[C], g[C];
-            vload<C>(srow + (size_t)w * nx + i0, lo);
-            if (row_active) {
-                face_row(lo, cur, (uint32_t)ncell + lin(y, z), g);
-                vstore<C>(sgy + (size_t)w * nx + i0, g);
-            }
-            if (w == 0) {
-                Real lo2[C], hi2[C];
-                vload<C>(srow + (size_t)nrows * nx + i0, lo2);
-                vload<C>(srow + (size_t)(nrows + 1) * nx + i0, hi2);
-                face_row(lo2, hi2, (uint32_t)ncell + lin(yh, z), g);
-                vstore<C>(sgy + (size_t)nrows * nx + i0, g);
-            }
-        }
-        __syncthreads();
+        if (more) yfaces(z + 1, nxt);
+        const Real* srow = srow_of(z);
+        const Real* sgy = sgy_of(z);
         if (row_active) {
             // x-direction (periodic, the warp holds the whole row)
             const Real left_nb = __shfl_up_sync(FULL, cur[C - 1], 1);
@@ -194,7 +222,7 @@ static cudaError_t launch3d_layout(const Step3DArgs<Real>& a, cudaStream_t st)
 {
     const int ytiles = (a.ny + kY3 - 1) / kY3, zbands = (a.nz + kH3 - 1) / kH3;
     const int64_t blocks = (int64_t)a.R * ytiles * zbands;
-    const int smem = 2 * (2 * kY3 + 3) * a.nx * (int)sizeof(Real);
+    const int smem = (3 * (kY3 + 2) + 2 * (kY3 + 1)) * a.nx * (int)sizeof(Real);
     auto k = k_step3d<Real, C, SP>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     k<<<(unsigned)blocks, kY3 * 32, smem, st>>>(a);
