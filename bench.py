@@ -133,7 +133,7 @@ WORKLOADS = {
               "(two-stage DFT-as-GEMM on tcgen05) every 10 steps after 1e4"),
         chunk=1000, ops=2 * (25.0 + 5.5 + 7.0) + 9.0, bytes=8.0 + 16.0 / 10,
         kernel="k_step2d<float,8,32,species>",
-        traffic=dict(bytes=74.679552e6 + 23.367168e6, realizations=256),   # profiles/k_step2d_species_2d.md
+        traffic=dict(bytes=74.257408e6 + 22.797312e6, realizations=256),   # profiles/k_step2d_species_2d.md
         # per realization and sample: row DFT (ny x nx x nx MAC) + column DFTs
         # for the 128 rows ky < 128 (2 x 128 x ny x nx MAC; the other rows
         # follow from the real-field symmetry), 3 split products, 2 flop per MAC
@@ -145,7 +145,7 @@ WORKLOADS = {
               "stencil, moments and S(k) along x, y, z (line covariance on tcgen05) every 10 steps"),
         chunk=100, ops=3 * (25.0 + 5.5 + 4.0) + 11.0, bytes=8.0 + 16.0 / 10,
         kernel="k_step3d<float,8,heat>",
-        traffic=None,    # to be recaptured after the one-barrier change (profiles/k_step3d_cube_3d.md)
+        traffic=dict(bytes=142.941184e6 + 92.432384e6, realizations=2),    # profiles/k_step3d_cube_3d.md
         # per realization and sample: for each axis a SYRK over all lines
         # (cells / n_a lines x n_a^2 MAC), 3 split products, 2 flop per MAC
         stats_kernel="k_axes_syrk", stats_flop=lambda p: 3 * 2 * sum(

@@ -24,11 +24,14 @@
 
 namespace she {
 
-// 6 resident blocks of 4 warps per SM for the FP32 8-cell layout (80
-// registers; measured faster than 7 blocks at 72 registers, which spill,
-// although the 256 x 256 x 256 ensemble then takes 1.1 waves)
+// One warp per CTA, 24 resident per SM for the FP32 8-cell layout (80
+// registers; 28 at 72 registers spill).  A one-warp CTA frees its slot when
+// its own warp finishes, so the warps of an SM need not wait for the slowest
+// of four: 68.4 -> 66.2 us per step of the 256 x 256 x 256 ensemble with the
+// same 24 warps per SM.
+constexpr int kWPB2 = 1;       // warps per CTA
 template <typename Real, int C, int LPR, bool SPECIES, bool RAGGED>
-__global__ void __launch_bounds__(128, (sizeof(Real) == 4 && C <= 8) ? 6 : 1)
+__global__ void __launch_bounds__(32 * kWPB2, (sizeof(Real) == 4 && C <= 8) ? 24 / kWPB2 : 1)
 k_step2d(const __grid_constant__ Step2DArgs<Real> a)
 {
     static_assert(C % 4 == 0, "cells per lane must be a multiple of 4");
@@ -36,7 +39,7 @@ k_step2d(const __grid_constant__ Step2DArgs<Real> a)
     constexpr int SPW = 32 / LPR;                     // segments per warp
     const int lane = threadIdx.x & 31;
     const int sl = lane % LPR;
-    const int warp = blockIdx.x * 4 + (threadIdx.x >> 5);
+    const int warp = blockIdx.x * kWPB2 + (threadIdx.x >> 5);
     // a.tiles > 0: segment = (realization, band of a.H rows); a.tiles == 0
     // (one segment per warp only): segment = a balanced run of the R * ny
     // realization-major rows, which may cross into the next realization
@@ -239,15 +242,17 @@ static int resident_warps(K kernel)
     int dev = 0, sms = 0, blocks = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, 128, 0) != cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, 32 * kWPB2, 0) != cudaSuccess)
         return 0;
-    return sms * blocks * 4;
+    return sms * blocks * kWPB2;
 }
 
 // One warp per segment (LPR = 32): the R * ny rows are split into as many
 // balanced runs as there are resident warps (but runs of at least 16 rows),
 // so the launch is a single full wave; a partial second wave of bands would
-// otherwise run at a fraction of the SM's issue rate.
+// otherwise run at a fraction of the SM's issue rate (and two or three
+// shorter runs per resident warp cost more in halo rows than they gain in
+// balance: 68.9 us per step against 66.2).
 template <typename Real, int C, int LPR, bool SP>
 static cudaError_t launch2d_layout(Step2DArgs<Real> a, cudaStream_t st)
 {
@@ -263,7 +268,7 @@ static cudaError_t launch2d_layout(Step2DArgs<Real> a, cudaStream_t st)
     }
     const int64_t segs = a.tiles > 0 ? (int64_t)a.R * a.tiles : a.nseg;
     const int64_t warps = (segs + SPW - 1) / SPW;
-    const dim3 grid((unsigned)((warps + 3) / 4)), block(128);
+    const dim3 grid((unsigned)((warps + kWPB2 - 1) / kWPB2)), block(32 * kWPB2);
     if (!ragged) k_step2d<Real, C, LPR, SP, false><<<grid, block, 0, st>>>(a);
     else k_step2d<Real, C, LPR, SP, true><<<grid, block, 0, st>>>(a);
     return cudaGetLastError();
