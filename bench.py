@@ -139,6 +139,19 @@ WORKLOADS = {
         # follow from the real-field symmetry), 3 split products, 2 flop per MAC
         stats_kernel="k_sk2d", stats_flop=lambda p: 3 * 2 * (p["n"][1] * p["n"][0] ** 2
                                                            + 2 * 128 * p["n"][1] * p["n"][0])),
+    "species_2d_pc": dict(
+        make=lambda W: W.species_2d(want_sk=1, scheme="pc"),
+        desc=("the species_2d configuration (2D species diffusion 256x256 periodic, 256 realizations, "
+              "FP32, moments and the full 2D S(k) every 10 steps after 1e4) stepped by the "
+              "predictor-corrector scheme of Sec. 3, run as a predictor pass and a corrector pass"),
+        # algorithmic: two normals per cell drawn once, the two face fluxes and
+        # the update twice, the trapezoid 3 (the two-pass kernels draw the
+        # normals again in the corrector; that work is not counted); bytes: the
+        # state read and written once plus the moments
+        chunk=1000, ops=2 * (25.0 + 5.5) + 2 * (2 * 7.0 + 9.0) + 3.0, bytes=8.0 + 16.0 / 10,
+        kernel="k_step2d<float,8,32,species> predictor + corrector", traffic=None,
+        stats_kernel="k_sk2d", stats_flop=lambda p: 3 * 2 * (p["n"][1] * p["n"][0] ** 2
+                                                           + 2 * 128 * p["n"][1] * p["n"][0])),
     "cube_3d": dict(
         make=lambda W: W.cube_3d(want_sk=2),
         desc=("3D SHE 256^3 periodic, T0=1, r=0.1, eps=1e-3, 8 realizations, FP32, HBM-streaming "

@@ -14,7 +14,9 @@
  *   - the predictor-corrector scheme, Sec. 3 (the trapezoidal scheme written
  *     after Eq. (3.3)): the forward-Euler step as predictor T*, then
  *     T' = (T + T* + D(T*) + div G(T*)) / 2 with the face values and the
- *     stencil on T* and the same face noise (1D, fused kernels only);
+ *     stencil on T* and the same face noise (1D rows up to 512 cells in one
+ *     fused pass; 2D/3D as a predictor pass and a corrector pass that draws
+ *     the same normals again);
  *   - Dirichlet walls: boundary stencil of Eq. (3.8) and the sqrt(2) factor on
  *     the wall-face noise (Sec. 3, text after Eq. (3.8)); periodic wrap;
  *   - stochastic species diffusion, Sec. 4, Eq. (4.7) (noise amplitude
@@ -112,7 +114,7 @@ typedef struct she_params {
     double dt;            /* time step */
     uint64_t seed;        /* Philox key */
     int64_t realizations; /* independent sample paths, >= 1 */
-    int32_t scheme;       /* SHE_FE, or SHE_PC (dim 1, kernel auto, N <= 512;
+    int32_t scheme;       /* SHE_FE, or SHE_PC (kernel auto; 1D N <= 512;
                              otherwise SHE_ERR_UNSUPPORTED) */
     int32_t stochastic;   /* 1: thermal noise on; 0: deterministic (alpha = 0) */
     int32_t perturb_ic;   /* 1: T_ref + sigma N(0,1) per cell, sigma^2 = eps T_mid^2

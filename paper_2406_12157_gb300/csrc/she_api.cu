@@ -210,9 +210,9 @@ she_status she_init(const she_params* p, she_handle** out)
     if (st == SHE_OK && p->precision != SHE_FP32 && p->precision != SHE_FP64) {
         st = SHE_ERR_INVALID_ARG; msg = "she: precision must be SHE_FP32 or SHE_FP64";
     }
-    if (st == SHE_OK && p->scheme == SHE_PC && (p->dim != 1 || p->kernel != SHE_KERNEL_AUTO || p->n[0] > 512)) {
+    if (st == SHE_OK && p->scheme == SHE_PC && (p->kernel != SHE_KERNEL_AUTO || (p->dim == 1 && p->n[0] > 512))) {
         st = SHE_ERR_UNSUPPORTED;
-        msg = "she: the predictor-corrector scheme runs on the fused 1D kernels (dim 1, kernel auto, N <= 512)";
+        msg = "she: the predictor-corrector scheme runs on the fused kernels (kernel auto; 1D rows of N <= 512)";
     }
     if (st == SHE_OK && p->kernel != SHE_KERNEL_AUTO && p->kernel != SHE_KERNEL_PLAIN) {
         st = SHE_ERR_INVALID_ARG; msg = "she: bad kernel selector";

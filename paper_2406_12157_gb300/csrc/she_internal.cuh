@@ -58,8 +58,9 @@ struct Step1DArgs {
 // Arguments of the 2D step kernel (one step per launch).
 template <typename Real>
 struct Step2DArgs {
-    const Real* T;        // [R][ny][nx] old state
-    Real* Tn;             // [R][ny][nx] new state
+    const Real* T;        // [R][ny][nx] old state (the corrector: the predictor state T*)
+    Real* Tn;             // [R][ny][nx] new state (the corrector: in place over Tc)
+    const Real* Tc;       // the corrector only: the state at the start of the step
     Real* m1;             // [R][cells] moment partial sums (FP32 partials, or the FP64 accumulators)
     Real* m2;
     int* flags;
@@ -77,8 +78,9 @@ struct Step2DArgs {
 // Arguments of the 3D step kernel (one step per launch).
 template <typename Real>
 struct Step3DArgs {
-    const Real* T;        // [R][nz][ny][nx] old state
-    Real* Tn;
+    const Real* T;        // [R][nz][ny][nx] old state (the corrector: the predictor state T*)
+    Real* Tn;             // new state (the corrector: in place over Tc)
+    const Real* Tc;       // the corrector only: the state at the start of the step
     Real* m1;             // [R][cells] moment partial sums
     Real* m2;
     int* flags;

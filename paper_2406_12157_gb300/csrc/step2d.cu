@@ -30,7 +30,7 @@ namespace she {
 // of four: 68.4 -> 66.2 us per step of the 256 x 256 x 256 ensemble with the
 // same 24 warps per SM.
 constexpr int kWPB2 = 1;       // warps per CTA
-template <typename Real, int C, int LPR, bool SPECIES, bool RAGGED>
+template <typename Real, int C, int LPR, bool SPECIES, bool RAGGED, bool CORR>
 __global__ void __launch_bounds__(32 * kWPB2, (sizeof(Real) == 4 && C <= 8) ? 24 / kWPB2 : 1)
 k_step2d(const __grid_constant__ Step2DArgs<Real> a)
 {
@@ -149,6 +149,15 @@ k_step2d(const __grid_constant__ Step2DArgs<Real> a)
             const Real g_next = __shfl_down_sync(FULL, gx[0], 1, LPR);
             const Real g_zero = __shfl_sync(FULL, gx[0], 0, LPR);
             Real out[C];
+            Real tc[C];                               // corrector: the state at the start of the step
+            if (CORR) {
+                const Real* pc = a.Tc + (size_t)rho * (size_t)ncell + (size_t)y * nx;
+                if (!RAGGED) vload<C>(pc + i0, tc);
+                else {
+#pragma unroll
+                    for (int j = 0; j < C; ++j) tc[j] = i0 + j < nx ? pc[i0 + j] : Real(0);
+                }
+            }
 #pragma unroll
             for (int j = 0; j < C; ++j) {
                 const int i = i0 + j;
@@ -161,8 +170,14 @@ k_step2d(const __grid_constant__ Step2DArgs<Real> a)
                     ghi = g_zero;
                 }
                 const Real c = cur[j];
-                out[j] = c + r * ((left + right) + (prev[j] + nxt[j]) - Real(4) * c) + (ghi - gx[j]) +
-                         (gy_nxt[j] - gy_cur[j]);
+                if (CORR) {   // predictor-corrector (Sec. 3): ((T + T*) + inc(T*)) / 2
+                    const Real inc = r * ((left + right) + (prev[j] + nxt[j]) - Real(4) * c) + (ghi - gx[j]) +
+                                     (gy_nxt[j] - gy_cur[j]);
+                    out[j] = half * ((tc[j] + c) + inc);
+                } else {
+                    out[j] = c + r * ((left + right) + (prev[j] + nxt[j]) - Real(4) * c) + (ghi - gx[j]) +
+                             (gy_nxt[j] - gy_cur[j]);
+                }
             }
             if (active) {
                 Real* po = Tout + (size_t)y * nx;
@@ -253,14 +268,14 @@ static int resident_warps(K kernel)
 // otherwise run at a fraction of the SM's issue rate (and two or three
 // shorter runs per resident warp cost more in halo rows than they gain in
 // balance: 68.9 us per step against 66.2).
-template <typename Real, int C, int LPR, bool SP>
+template <typename Real, int C, int LPR, bool SP, bool CORR>
 static cudaError_t launch2d_layout(Step2DArgs<Real> a, cudaStream_t st)
 {
     constexpr int SPW = 32 / LPR;
     const bool ragged = a.nx != C * LPR;
     if (LPR == 32) {
-        static const int slots[2] = {resident_warps(k_step2d<Real, C, LPR, SP, false>),
-                                     resident_warps(k_step2d<Real, C, LPR, SP, true>)};
+        static const int slots[2] = {resident_warps(k_step2d<Real, C, LPR, SP, false, CORR>),
+                                     resident_warps(k_step2d<Real, C, LPR, SP, true, CORR>)};
         const int64_t rows = (int64_t)a.R * a.ny;
         const int64_t runs = std::min<int64_t>(slots[ragged] > 0 ? slots[ragged] : 1, (rows + 15) / 16);
         a.tiles = 0;
@@ -269,21 +284,27 @@ static cudaError_t launch2d_layout(Step2DArgs<Real> a, cudaStream_t st)
     const int64_t segs = a.tiles > 0 ? (int64_t)a.R * a.tiles : a.nseg;
     const int64_t warps = (segs + SPW - 1) / SPW;
     const dim3 grid((unsigned)((warps + kWPB2 - 1) / kWPB2)), block(32 * kWPB2);
-    if (!ragged) k_step2d<Real, C, LPR, SP, false><<<grid, block, 0, st>>>(a);
-    else k_step2d<Real, C, LPR, SP, true><<<grid, block, 0, st>>>(a);
+    if (!ragged) k_step2d<Real, C, LPR, SP, false, CORR><<<grid, block, 0, st>>>(a);
+    else k_step2d<Real, C, LPR, SP, true, CORR><<<grid, block, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-template <typename Real, bool SP>
+template <typename Real, bool SP, bool CORR>
 static cudaError_t launch2d_sp(const Step2DArgs<Real>& a, cudaStream_t st)
 {
     const int nx = a.nx;
-    if (nx <= 16) return launch2d_layout<Real, 4, 4, SP>(a, st);
-    if (nx <= 32) return launch2d_layout<Real, 4, 8, SP>(a, st);
-    if (nx <= 64) return launch2d_layout<Real, 4, 16, SP>(a, st);
-    if (nx <= 128) return launch2d_layout<Real, 4, 32, SP>(a, st);
-    if (nx <= 256) return launch2d_layout<Real, 8, 32, SP>(a, st);
-    return launch2d_layout<Real, 16, 32, SP>(a, st);
+    if (nx <= 16) return launch2d_layout<Real, 4, 4, SP, CORR>(a, st);
+    if (nx <= 32) return launch2d_layout<Real, 4, 8, SP, CORR>(a, st);
+    if (nx <= 64) return launch2d_layout<Real, 4, 16, SP, CORR>(a, st);
+    if (nx <= 128) return launch2d_layout<Real, 4, 32, SP, CORR>(a, st);
+    if (nx <= 256) return launch2d_layout<Real, 8, 32, SP, CORR>(a, st);
+    return launch2d_layout<Real, 16, 32, SP, CORR>(a, st);
+}
+
+template <typename Real, bool CORR>
+static cudaError_t launch2d_eq(const Step2DArgs<Real>& a, bool sp, cudaStream_t st)
+{
+    return sp ? launch2d_sp<Real, true, CORR>(a, st) : launch2d_sp<Real, false, CORR>(a, st);
 }
 
 template <typename Real>
@@ -305,6 +326,7 @@ static cudaError_t launch2d_real(Handle& h, uint32_t step0, int nsteps)
     a.stream0 = h.stream0;
     a.stochastic = h.stochastic;
     a.flags = h.d_flags;
+    a.Tc = nullptr;
     const bool sp = h.prob.equation == SHE_SPECIES;
     for (int s = 0; s < nsteps; ++s) {
         const uint32_t n = step0 + (uint32_t)s;
@@ -320,10 +342,30 @@ static cudaError_t launch2d_real(Handle& h, uint32_t step0, int nsteps)
             a.m2 = (Real*)h.d_m2;
         }
         prof_mark(h, SHE_PROF_STEP);
-        cudaError_t e = sp ? launch2d_sp<Real, true>(a, h.stream) : launch2d_sp<Real, false>(a, h.stream);
-        h.launches += 1;
-        if (e != cudaSuccess) return e;
-        std::swap(h.d_state, h.d_state2);
+        cudaError_t e;
+        if (h.prob.scheme == SHE_PC) {
+            // predictor: the forward-Euler pass writes T* into the second
+            // buffer (no sampling); corrector: reads T* (neighbours, face
+            // values) and T (centre), draws the same normals (same step,
+            // stream, key) and writes ((T + T*) + inc(T*)) / 2 in place over T
+            const int sample = a.sample;
+            a.sample = 0;
+            e = launch2d_eq<Real, false>(a, sp, h.stream);
+            h.launches += 1;
+            if (e != cudaSuccess) return e;
+            a.T = (const Real*)h.d_state2;
+            a.Tc = (const Real*)h.d_state;
+            a.Tn = (Real*)h.d_state;
+            a.sample = sample;
+            e = launch2d_eq<Real, true>(a, sp, h.stream);
+            h.launches += 1;
+            if (e != cudaSuccess) return e;
+        } else {
+            e = launch2d_eq<Real, false>(a, sp, h.stream);
+            h.launches += 1;
+            if (e != cudaSuccess) return e;
+            std::swap(h.d_state, h.d_state2);
+        }
         if (a.sample && (h.want_sk & SHE_SK_AXES)) {
             prof_mark(h, SHE_PROF_STATS);
             e = launch_axes_syrk(h);

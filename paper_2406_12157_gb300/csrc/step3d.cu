@@ -31,7 +31,7 @@ namespace she {
 constexpr int kY3 = 8;          // x-rows (warps) per CTA
 constexpr int kH3 = 32;         // z-planes per band
 
-template <typename Real, int C, bool SPECIES>
+template <typename Real, int C, bool SPECIES, bool CORR>
 __global__ void __launch_bounds__(kY3 * 32, sizeof(Real) == 4 ? 3 : 1)
 k_step3d(const __grid_constant__ Step3DArgs<Real> a)
 {
@@ -184,8 +184,18 @@ k_step3d(const __grid_constant__ Step3DArgs<Real> a)
                 Real right = (j == C - 1) ? (lane == 31 ? wrap_hi : right_nb) : cur[j + 1];
                 Real ghi = (j == C - 1) ? (lane == 31 ? g_zero : g_next) : gx[j + 1];
                 const Real c = cur[j];
-                out[j] = c + r * ((left + right) + (down[j] + up[j]) + (prev[j] + nxt[j]) - Real(6) * c) +
-                         (ghi - gx[j]) + (gyh[j] - gyl[j]) + (gz_nxt[j] - gz_cur[j]);
+                if (CORR)   // the increment inc(T*); the trapezoid follows
+                    out[j] = r * ((left + right) + (down[j] + up[j]) + (prev[j] + nxt[j]) - Real(6) * c) +
+                             (ghi - gx[j]) + (gyh[j] - gyl[j]) + (gz_nxt[j] - gz_cur[j]);
+                else
+                    out[j] = c + r * ((left + right) + (down[j] + up[j]) + (prev[j] + nxt[j]) - Real(6) * c) +
+                             (ghi - gx[j]) + (gyh[j] - gyl[j]) + (gz_nxt[j] - gz_cur[j]);
+            }
+            if (CORR) {   // predictor-corrector (Sec. 3): ((T + T*) + inc(T*)) / 2
+                Real tc[C];
+                vload<C>(a.Tc + (size_t)rho * (size_t)ncell + ((size_t)z * ny + y) * nx + i0, tc);
+#pragma unroll
+                for (int j = 0; j < C; ++j) out[j] = half * ((tc[j] + cur[j]) + out[j]);
             }
             Real* po = Tout + ((size_t)z * ny + y) * nx + i0;
             vstore<C>(po, out);
@@ -217,27 +227,33 @@ k_step3d(const __grid_constant__ Step3DArgs<Real> a)
     }
 }
 
-template <typename Real, int C, bool SP>
+template <typename Real, int C, bool SP, bool CORR>
 static cudaError_t launch3d_layout(const Step3DArgs<Real>& a, cudaStream_t st)
 {
     const int ytiles = (a.ny + kY3 - 1) / kY3, zbands = (a.nz + kH3 - 1) / kH3;
     const int64_t blocks = (int64_t)a.R * ytiles * zbands;
     const int smem = (3 * (kY3 + 2) + 2 * (kY3 + 1)) * a.nx * (int)sizeof(Real);
-    auto k = k_step3d<Real, C, SP>;
+    auto k = k_step3d<Real, C, SP, CORR>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     k<<<(unsigned)blocks, kY3 * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <typename Real, bool SP>
+template <typename Real, bool SP, bool CORR>
 static cudaError_t launch3d_sp(const Step3DArgs<Real>& a, cudaStream_t st)
 {
     switch (a.nx) {
-    case 128: return launch3d_layout<Real, 4, SP>(a, st);
-    case 256: return launch3d_layout<Real, 8, SP>(a, st);
-    case 512: return launch3d_layout<Real, 16, SP>(a, st);
+    case 128: return launch3d_layout<Real, 4, SP, CORR>(a, st);
+    case 256: return launch3d_layout<Real, 8, SP, CORR>(a, st);
+    case 512: return launch3d_layout<Real, 16, SP, CORR>(a, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+template <typename Real, bool CORR>
+static cudaError_t launch3d_eq(const Step3DArgs<Real>& a, bool sp, cudaStream_t st)
+{
+    return sp ? launch3d_sp<Real, true, CORR>(a, st) : launch3d_sp<Real, false, CORR>(a, st);
 }
 
 template <typename Real>
@@ -257,6 +273,7 @@ static cudaError_t launch3d_real(Handle& h, uint32_t step0, int nsteps)
     a.stream0 = h.stream0;
     a.stochastic = h.stochastic;
     a.flags = h.d_flags;
+    a.Tc = nullptr;
     const bool sp = h.prob.equation == SHE_SPECIES;
     for (int s = 0; s < nsteps; ++s) {
         const uint32_t n = step0 + (uint32_t)s;
@@ -272,10 +289,28 @@ static cudaError_t launch3d_real(Handle& h, uint32_t step0, int nsteps)
             a.m2 = (Real*)h.d_m2;
         }
         prof_mark(h, SHE_PROF_STEP);
-        cudaError_t e = sp ? launch3d_sp<Real, true>(a, h.stream) : launch3d_sp<Real, false>(a, h.stream);
-        h.launches += 1;
-        if (e != cudaSuccess) return e;
-        std::swap(h.d_state, h.d_state2);
+        cudaError_t e;
+        if (h.prob.scheme == SHE_PC) {
+            // predictor pass into the second buffer, then the corrector in
+            // place over T (see the 2D step)
+            const int sample = a.sample;
+            a.sample = 0;
+            e = launch3d_eq<Real, false>(a, sp, h.stream);
+            h.launches += 1;
+            if (e != cudaSuccess) return e;
+            a.T = (const Real*)h.d_state2;
+            a.Tc = (const Real*)h.d_state;
+            a.Tn = (Real*)h.d_state;
+            a.sample = sample;
+            e = launch3d_eq<Real, true>(a, sp, h.stream);
+            h.launches += 1;
+            if (e != cudaSuccess) return e;
+        } else {
+            e = launch3d_eq<Real, false>(a, sp, h.stream);
+            h.launches += 1;
+            if (e != cudaSuccess) return e;
+            std::swap(h.d_state, h.d_state2);
+        }
         if (a.sample && (h.want_sk & SHE_SK_AXES)) {
             prof_mark(h, SHE_PROF_STATS);
             e = launch_axes_syrk(h);

@@ -11,6 +11,10 @@ oracle, through the C ABI.
 * About 10^6 realizations of 4-cell rods match the exact PC moment
   recursion (Gauss-Hermite quadrature over the face normals) within a few
   standard errors, independently of the oracle's sample paths.
+* 2D and 3D (a predictor pass and a corrector pass that draws the same
+  normals again): FP64 trajectories to 1e-12 over several bands, tiles and
+  ragged rows, FP32 one step within 2e-5, the full 2D S(k) on the
+  corrector's output.
 * Combinations outside the PC kernels are refused with SHE_ERR_UNSUPPORTED.
 """
 import numpy as np
@@ -152,11 +156,97 @@ def test_pc_million_realizations_match_exact_recursion(precision, bc, walls):
     assert np.mean(z * z) < 2.5, z
 
 
-@pytest.mark.parametrize("kw", [dict(dim=2, n=(8, 6, 1), bc="periodic"),
-                                dict(kernel="plain", precision="fp64"),
+@pytest.mark.parametrize("kw", [dict(kernel="plain", precision="fp64"),
                                 dict(n=(600, 1, 1))])
 def test_pc_outside_its_kernels_is_refused(kw):
     p = W.oracle_rod(scheme="pc", want_cov=0, want_sk=0, **kw)
     with pytest.raises(S.SheError) as e:
         S.Simulation(p)
     assert e.value.status == S._abi.SHE_ERR_UNSUPPORTED
+
+
+def _p2(nx, ny, eq, **kw):
+    kw.setdefault("realizations", 3)
+    kw.setdefault("stats_interval", 3)
+    kw.setdefault("relax_steps", 10)
+    kw.setdefault("want_sk", 0)
+    return W.species_2d(n=(nx, ny, 1), equation=eq, n0=200.0, kB=3e-3, wall_lo=1.3, wall_hi=1.3,
+                        scheme="pc", **kw)
+
+
+def _p3(shape, eq, **kw):
+    kw.setdefault("realizations", 2)
+    kw.setdefault("stats_interval", 2)
+    kw.setdefault("relax_steps", 3)
+    kw.setdefault("want_sk", 0)
+    return W.cube_3d(n=shape, equation=eq, n0=150.0, kB=4e-3, wall_lo=1.2, wall_hi=1.2, perturb_ic=1,
+                     scheme="pc", **kw)
+
+
+@pytest.mark.parametrize("nx,ny", [(8, 6), (20, 33), (64, 48), (132, 7), (256, 20)])
+@pytest.mark.parametrize("eq", ["species", "heat"])
+def test_pc_2d_fp64_trajectory_parity(nx, ny, eq):
+    p = _p2(nx, ny, eq, precision="fp64")
+    with S.Simulation(p) as sim:
+        sim.step(25)
+        st, _ = sim.state()
+        g = sim.stats(raw=True)
+    ref = O.run(p, 3, 25)
+    assert rel_err(st, ref["state"]) < 1e-12
+    assert g["n_samples"] == ref["n_samples"]
+    assert np.allclose(g["sum_d2"], ref["sum_d2"], rtol=1e-9, atol=1e-15)
+    fe = O.run(dict(p, scheme="fe"), 3, 25)["state"]
+    assert rel_err(st, fe) > 1e-7
+
+
+@pytest.mark.parametrize("nx,ny", [(8, 6), (132, 7), (256, 20)])
+def test_pc_2d_fp32_one_step_parity(nx, ny):
+    p = _p2(nx, ny, "species", precision="fp32")
+    x = W.random_states(p, 3, seed=nx * 7 + ny).astype(np.float32)
+    with S.Simulation(p) as sim:
+        for step in (0, 99, 123456):
+            sim.set_state(x, step)
+            sim.step(1)
+            got, _ = sim.state()
+            for rho in range(3):
+                ref = O.step(p, x[rho].astype(np.float64), step, rho)
+                assert rel_err(got[rho].astype(np.float64), ref) < 2e-5
+
+
+def test_pc_2d_full_structure_factor():
+    p = _p2(16, 12, "species", precision="fp32", want_sk=1, stats_interval=3, relax_steps=0, realizations=6)
+    with S.Simulation(p) as sim:
+        sim.step(12)
+        g = sim.stats(sk=True)
+    o = O.finalize(p, O.run(p, 6, 12, want_sk=1))
+    assert g["n_samples"] == o["n"]
+    scale = np.max(np.abs(o["sk_fluct"][1:]))
+    assert np.max(np.abs(g["sk_fluct"] - o["sk_fluct"])) < 2e-4 * scale
+
+
+@pytest.mark.parametrize("shape", [(128, 2, 2), (128, 9, 5), (128, 8, 40), (256, 16, 3)])
+@pytest.mark.parametrize("eq", ["heat", "species"])
+def test_pc_3d_fp64_trajectory_parity(shape, eq):
+    p = _p3(shape, eq, precision="fp64")
+    with S.Simulation(p) as sim:
+        sim.step(6)
+        st, _ = sim.state()
+        g = sim.stats(raw=True)
+    ref = O.run(p, 2, 6)
+    assert rel_err(st, ref["state"]) < 1e-12
+    assert g["n_samples"] == ref["n_samples"]
+    assert np.allclose(g["sum_d2"], ref["sum_d2"], rtol=1e-9, atol=1e-15)
+
+
+@pytest.mark.parametrize("shape", [(128, 2, 2), (128, 9, 5)])
+def test_pc_3d_fp32_one_step_parity(shape):
+    p = _p3(shape, "heat", precision="fp32")
+    x = W.random_states(p, 2, seed=sum(shape)).astype(np.float32)
+    with S.Simulation(p) as sim:
+        for step in (0, 77):
+            sim.set_state(x, step)
+            sim.step(1)
+            got, _ = sim.state()
+            for rho in range(2):
+                ref = O.step(p, x[rho].astype(np.float64), step, rho)
+                assert rel_err(got[rho].astype(np.float64), ref) < 2e-5
