@@ -428,8 +428,10 @@ def pooled_expectation_quadrature(prob_like, nsteps, K, relax, step0=0):
     nf = len(ops[2])
     W, Z = gauss_hermite(nf, 3)
     maps = [affine_step(prob_like, z, ops) for z in Z]
-    EF = sum(w * F for w, (F, g) in zip(W, maps))
-    Eg = sum(w * g for w, (F, g) in zip(W, maps))
+    F = np.stack([fg[0] for fg in maps])          # [Q, n, n]
+    G = np.stack([fg[1] for fg in maps])          # [Q, n]
+    EF = np.einsum("q,qij->ij", W, F)
+    Eg = W @ G
     m, C = initial_moments(prob_like, tref)
     S = C + np.outer(m, m)
     n = len(m)
@@ -437,10 +439,10 @@ def pooled_expectation_quadrature(prob_like, nsteps, K, relax, step0=0):
     s2 = np.zeros((n, n))
     cnt = 0
     for mstep in range(step0 + 1, step0 + nsteps + 1):
-        Sn = np.zeros((n, n))
-        for w, (F, g) in zip(W, maps):
-            Fm = F @ m
-            Sn += w * (F @ S @ F.T + np.outer(Fm, g) + np.outer(g, Fm) + np.outer(g, g))
+        Fm = F @ m                                 # [Q, n]
+        cross = np.einsum("q,qi,qj->ij", W, Fm, G)
+        Sn = (np.einsum("q,qij,jk,qlk->il", W, F, S, F, optimize=True) + cross + cross.T
+              + np.einsum("q,qi,qj->ij", W, G, G))
         m = EF @ m + Eg
         S = 0.5 * (Sn + Sn.T)
         if mstep % K == 0 and mstep > relax:

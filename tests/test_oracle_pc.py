@@ -181,3 +181,24 @@ def test_pc_structure_factor_matches_closed_form():
     k = N // 2
     assert ex[k] < flat < fe[k]
     assert abs(vals.mean(axis=0)[k] - ex[k]) < 0.2 * abs(fe[k] - ex[k])
+
+
+def test_pc_heat_2d_moments_match_exact_recursion():
+    # 2 x 2 periodic grid: 8 faces, 3^8 quadrature nodes; the quadrature
+    # reproduces the closed forward-Euler recursion in 2D as well
+    p = W.species_2d(n=(2, 2, 1), equation="heat", kB=0.01, wall_lo=1.0, wall_hi=1.0, stats_interval=1,
+                     relax_steps=10, perturb_ic=1, scheme="pc")
+    td = _td(p)
+    fe = theory.pooled_expectation(dict(td, scheme="fe"), 30, 1, 10)
+    feq = theory.pooled_expectation_quadrature(dict(td, scheme="fe"), 30, 1, 10)
+    assert np.max(np.abs(fe["second"] - feq["second"])) < 1e-9 * np.max(np.abs(fe["second"]))
+    ex = theory.pooled_expectation_quadrature(td, 30, 1, 10)
+    m1, m2 = _batched(p, 2000, 16, 30)
+    se1 = m1.std(axis=0, ddof=1) / np.sqrt(16)
+    se2 = m2.std(axis=0, ddof=1) / np.sqrt(16)
+    z1 = (m1.mean(axis=0) - ex["mean_delta"]) / np.maximum(se1, 1e-300)
+    z2 = (m2.mean(axis=0) - ex["second"]) / np.maximum(se2, 1e-300)
+    assert np.max(np.abs(z1)) < 4.5, z1
+    assert np.max(np.abs(z2)) < 4.5, z2
+    zfe = (m2.mean(axis=0) - fe["second"]) / np.maximum(se2, 1e-300)
+    assert np.max(np.abs(zfe)) > 10.0
