@@ -39,6 +39,8 @@ class OrcParams(ctypes.Structure):
         ("relax_steps", ctypes.c_int64),
         ("want_cov", ctypes.c_int32),
         ("want_sk", ctypes.c_int32),
+        ("tc_lags", ctypes.c_int32),
+        ("pad1", ctypes.c_int32),
     ]
 
 
@@ -71,7 +73,7 @@ def lib():
         L.orc_step.restype = ctypes.c_int
         L.orc_run.argtypes = [ctypes.POINTER(OrcParams), ctypes.c_int64, ctypes.c_uint32,
                               ctypes.c_uint32, ctypes.c_int64, dp, ctypes.c_int,
-                              ctypes.POINTER(ctypes.c_int64), dp, dp, dp, dp, dp]
+                              ctypes.POINTER(ctypes.c_int64), dp, dp, dp, dp, dp, dp]
         L.orc_run.restype = ctypes.c_int
         L.orc_num_threads.argtypes = []
         L.orc_num_threads.restype = ctypes.c_int
@@ -129,6 +131,7 @@ def to_params(prob):
     p.relax_steps = int(prob.get("relax_steps", 0))
     p.want_cov = int(prob.get("want_cov", 0))
     p.want_sk = int(prob.get("want_sk", 0))
+    p.tc_lags = int(prob.get("tc_lags", 0))
     return p
 
 
@@ -192,7 +195,7 @@ def step(prob, state, step_index, stream):
     return out
 
 
-def run(prob, R, nsteps, step0=0, stream0=0, state=None, want_cov=None, want_sk=None):
+def run(prob, R, nsteps, step0=0, stream0=0, state=None, want_cov=None, want_sk=None, tc_lags=None):
     """Run R realizations for nsteps steps; return the final states and the
     pooled accumulators of the sampling schedule (Eq. (3.9)).
 
@@ -204,6 +207,8 @@ def run(prob, R, nsteps, step0=0, stream0=0, state=None, want_cov=None, want_sk=
         p.want_cov = int(want_cov)
     if want_sk is not None:
         p.want_sk = int(want_sk)
+    if tc_lags is not None:
+        p.tc_lags = int(tc_lags)
     nc = cells(prob)
     if state is None:
         st = np.zeros((R, nc))
@@ -219,9 +224,11 @@ def run(prob, R, nsteps, step0=0, stream0=0, state=None, want_cov=None, want_sk=
     sum_sk = np.zeros(nc) if (p.want_sk & 1) else None
     axes_len = sum(prob["n"][: prob["dim"]])
     sum_ska = np.zeros(axes_len) if (p.want_sk & 2) else None
+    L = int(p.tc_lags)
+    sum_tc = np.zeros(L * nc) if L > 0 else None
     rc = lib().orc_run(ctypes.byref(p), R, stream0, step0, nsteps, _dp(st), init,
                        ctypes.byref(ns), _dp(sum_d), _dp(sum_d2), _dp(sum_dd),
-                       _dp(sum_sk), _dp(sum_ska))
+                       _dp(sum_sk), _dp(sum_ska), _dp(sum_tc))
     if rc != 0:
         raise RuntimeError("orc_run failed: %d" % rc)
     out = {
@@ -237,6 +244,11 @@ def run(prob, R, nsteps, step0=0, stream0=0, state=None, want_cov=None, want_sk=
         out["sum_sk"] = sum_sk
     if sum_ska is not None:
         out["sum_sk_axes"] = sum_ska
+    if sum_tc is not None:
+        # sample pairs l sampling intervals apart within this run, pooled over
+        # the realizations
+        out["sum_tc"] = sum_tc.reshape(L, nc)
+        out["n_tc"] = np.array([R * max(0, ns.value - l) for l in range(L)], dtype=np.int64)
     return out
 
 
@@ -259,6 +271,9 @@ def finalize(prob, acc):
         res["sk"] = np.abs(ref_hat) ** 2 + 2.0 * np.real(np.conj(ref_hat) * mu_hat) + dd
     if "sum_sk_axes" in acc:
         res["sk_axes"] = acc["sum_sk_axes"] / n
+    if "sum_tc" in acc:
+        # <delta_i(t + l K) delta_i(t)> per lag l and cell i (delta = T - T_ref)
+        res["time_corr"] = acc["sum_tc"] / np.maximum(acc["n_tc"], 1)[:, None]
     return res
 
 

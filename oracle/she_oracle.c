@@ -31,7 +31,10 @@
  *     pooled over realizations: sums of delta = T - T_ref, of delta^2, of
  *     delta_i*delta_j (equal-time covariance, generalising the one-point
  *     correlation the paper plots, Eq. (3.10)/(3.13)), and of |hat(delta)_k|^2
- *     with the unnormalised DFT of Eq. (3.11).
+ *     with the unnormalised DFT of Eq. (3.11); optionally the time
+ *     correlation sum delta_i(s) delta_i(s - l) over pairs of samples l
+ *     sampling intervals apart within one run (the exercise on
+ *     <dT_i^{n+m} dT_i^n>, Sec. 6).
  *
  * Counter layout (the paper leaves the random-number source open; this is
  * the reading both sides implement):
@@ -89,6 +92,8 @@ typedef struct {
     int64_t relax_steps;   /* sample at step m (1-based) iff m%K==0 && m>relax */
     int32_t want_cov;      /* accumulate sum delta_i delta_j */
     int32_t want_sk;       /* bit0: full DFT over the grid, bit1: per-axis lines */
+    int32_t tc_lags;       /* L > 0: accumulate the time correlation at lags 0..L-1 samples */
+    int32_t pad1;
 } orc_params;
 
 /* ---------------------------------------------------------------- RNG ---- */
@@ -387,6 +392,8 @@ typedef struct {
     double* sum_dd;        /* [cells*cells] or NULL */
     double* sum_sk;        /* [cells] |hat delta_k|^2 (full DFT, dim<=2) or NULL */
     double* sum_sk_axes;   /* [n0+n1+n2] line-averaged per-axis |hat delta|^2 or NULL */
+    double* sum_tc;        /* [L][cells] sum of delta_i(s) delta_i(s - l) or NULL */
+    double* ring;          /* [L][cells] the last L samples of delta (sample s in slot s % L) */
 } orc_acc;
 
 static void orc_sample(const orc_params* p, const double* T, const double* tref, orc_acc* acc,
@@ -395,6 +402,19 @@ static void orc_sample(const orc_params* p, const double* T, const double* tref,
     int64_t nc = orc_cells(p);
     double* d = work;                 /* [nc] */
     for (int64_t i = 0; i < nc; ++i) d[i] = T[i] - tref[i];
+    if (acc->sum_tc) {
+        /* time correlation <delta_i(t + l K) delta_i(t)> (the paper's exercise
+         * on <dT_i^{n+m} dT_i^n>, Sec. 6), lags in whole sampling intervals:
+         * pair this sample with each of the last L - 1 samples of this run */
+        const int L = p->tc_lags;
+        const int64_t s = acc->n_samples;
+        double* slot = acc->ring + (s % L) * nc;
+        for (int64_t i = 0; i < nc; ++i) slot[i] = d[i];
+        for (int l = 0; l < L && l <= s; ++l) {
+            const double* prev = acc->ring + ((s - l) % L) * nc;
+            for (int64_t i = 0; i < nc; ++i) acc->sum_tc[l * nc + i] += d[i] * prev[i];
+        }
+    }
     acc->n_samples += 1;
     for (int64_t i = 0; i < nc; ++i) {
         acc->sum_d[i] += d[i];
@@ -455,11 +475,12 @@ static void orc_sample(const orc_params* p, const double* T, const double* tref,
  */
 int orc_run(const orc_params* p, int64_t R, uint32_t stream0, uint32_t step0, int64_t nsteps,
             double* state, int init, int64_t* n_samples, double* sum_d, double* sum_d2,
-            double* sum_dd, double* sum_sk, double* sum_sk_axes)
+            double* sum_dd, double* sum_sk, double* sum_sk_axes, double* sum_tc)
 {
     if (p->dim < 1 || p->dim > 3 || R < 0 || nsteps < 0) return -2;
     if (p->dim > 1 && p->bc != ORC_PERIODIC) return -2;
     if (p->scheme != ORC_FE && p->scheme != ORC_PC) return -2;
+    if (sum_tc && p->tc_lags < 1) return -2;
     if (sum_sk && p->dim > 2) return -2;
     int64_t nc = orc_cells(p);
     int axes_len = p->n[0] + (p->dim >= 2 ? p->n[1] : 0) + (p->dim >= 3 ? p->n[2] : 0);
@@ -474,9 +495,11 @@ int orc_run(const orc_params* p, int64_t R, uint32_t stream0, uint32_t step0, in
     double* pdd = sum_dd ? (double*)calloc((size_t)(R * nc * nc), sizeof(double)) : NULL;
     double* psk = sum_sk ? (double*)calloc((size_t)(R * nc), sizeof(double)) : NULL;
     double* pska = sum_sk_axes ? (double*)calloc((size_t)(R * axes_len), sizeof(double)) : NULL;
+    const int64_t tcl = sum_tc ? (int64_t)p->tc_lags * nc : 0;
+    double* ptc = sum_tc ? (double*)calloc((size_t)(R * tcl), sizeof(double)) : NULL;
     if ((R > 0 && (!pd || !pd2)) || (sum_dd && R > 0 && !pdd) || (sum_sk && R > 0 && !psk) ||
-        (sum_sk_axes && R > 0 && !pska)) {
-        free(tref); free(pd); free(pd2); free(pdd); free(psk); free(pska);
+        (sum_sk_axes && R > 0 && !pska) || (sum_tc && R > 0 && !ptc)) {
+        free(tref); free(pd); free(pd2); free(pdd); free(psk); free(pska); free(ptc);
         return -1;
     }
     for (int64_t m = (int64_t)step0 + 1; m <= (int64_t)step0 + nsteps; ++m)
@@ -488,10 +511,11 @@ int orc_run(const orc_params* p, int64_t R, uint32_t stream0, uint32_t step0, in
         double* T = state + rr * nc;
         double* Tn = (double*)malloc(sizeof(double) * (size_t)nc);
         double* work = (double*)malloc(sizeof(double) * (size_t)(nc + 8192));
+        double* ring = sum_tc ? (double*)malloc(sizeof(double) * (size_t)tcl) : NULL;
         orc_work ws;
         int wrc = orc_work_alloc(p, &ws);
-        if (!Tn || !work || wrc != 0) {
-            free(Tn); free(work); orc_work_free(&ws);
+        if (!Tn || !work || wrc != 0 || (sum_tc && !ring)) {
+            free(Tn); free(work); free(ring); orc_work_free(&ws);
 #pragma omp atomic write
             err = -1;
             continue;
@@ -505,6 +529,8 @@ int orc_run(const orc_params* p, int64_t R, uint32_t stream0, uint32_t step0, in
         acc.sum_dd = pdd ? pdd + rr * nc * nc : NULL;
         acc.sum_sk = psk ? psk + rr * nc : NULL;
         acc.sum_sk_axes = pska ? pska + rr * axes_len : NULL;
+        acc.sum_tc = ptc ? ptc + rr * tcl : NULL;
+        acc.ring = ring;
         for (int64_t s = 0; s < nsteps; ++s) {
             uint32_t step = step0 + (uint32_t)s;
             orc_advance(p, step, stream, T, Tn, &ws);
@@ -513,7 +539,7 @@ int orc_run(const orc_params* p, int64_t R, uint32_t stream0, uint32_t step0, in
             if (p->stats_interval > 0 && m % p->stats_interval == 0 && m > p->relax_steps)
                 orc_sample(p, T, tref, &acc, work);
         }
-        free(Tn); free(work); orc_work_free(&ws);
+        free(Tn); free(work); free(ring); orc_work_free(&ws);
     }
     if (!err) {
         if (n_samples) *n_samples += samples_per_real;
@@ -527,9 +553,11 @@ int orc_run(const orc_params* p, int64_t R, uint32_t stream0, uint32_t step0, in
                 for (int64_t i = 0; i < nc * nc; ++i) sum_dd[i] += pdd[rr * nc * nc + i];
             if (sum_sk_axes)
                 for (int i = 0; i < axes_len; ++i) sum_sk_axes[i] += pska[rr * axes_len + i];
+            if (sum_tc)
+                for (int64_t i = 0; i < tcl; ++i) sum_tc[i] += ptc[rr * tcl + i];
         }
     }
-    free(tref); free(pd); free(pd2); free(pdd); free(psk); free(pska);
+    free(tref); free(pd); free(pd2); free(pdd); free(psk); free(pska); free(ptc);
     return err;
 }
 

@@ -466,3 +466,87 @@ def first_step_quadrature(prob_like, T0, npts):
     mean = W @ vals
     dev = vals - mean
     return mean, (dev * W[:, None]).T @ dev
+
+
+# ------------------------------------------------------- time correlation --
+
+def mean_map(prob_like, ops=None):
+    """(M, g0) with E[T' | T] = M T + g0 for one step: forward Euler A, b
+    (the face noise has mean zero and is independent of T); the heat
+    predictor-corrector step E[F], E[g] (exact by quadrature).  The
+    predictor-corrector species step has no affine conditional mean (the
+    corrector's noise amplitude depends on the predictor's noise)."""
+    ops = ops if ops is not None else scheme(prob_like)
+    A, b, faces = ops[0], ops[1], ops[2]
+    if prob_like.get("scheme", "fe") != "pc":
+        return A, b
+    assert prob_like.get("equation", "heat") == "heat"
+    W, Z = gauss_hermite(len(faces), 3)
+    maps = [affine_step(prob_like, z, ops) for z in Z]
+    return (np.einsum("q,qij->ij", W, np.stack([f for f, g in maps])),
+            W @ np.stack([g for f, g in maps]))
+
+
+def moment_path(prob_like, nsteps, step0=0):
+    """E[T] and E[T T^T] after each of nsteps steps (entry 0: the initial
+    state): the closed forward-Euler recursion, or for the heat
+    predictor-corrector scheme the quadrature recursion."""
+    ops = scheme(prob_like)
+    A, b, faces, tref, _ = ops
+    m, C = initial_moments(prob_like, tref)
+    path = [(m.copy(), C + np.outer(m, m))]
+    if prob_like.get("scheme", "fe") != "pc":
+        for _ in range(nsteps):
+            Q = noise_cov(prob_like, faces, m, C)
+            C = A @ C @ A.T + Q
+            m = A @ m + b
+            path.append((m.copy(), C + np.outer(m, m)))
+        return path
+    assert prob_like.get("equation", "heat") == "heat"
+    W, Z = gauss_hermite(len(faces), 3)
+    maps = [affine_step(prob_like, z, ops) for z in Z]
+    F = np.stack([f for f, g in maps])
+    G = np.stack([g for f, g in maps])
+    EF, Eg = np.einsum("q,qij->ij", W, F), W @ G
+    S = path[0][1]
+    for _ in range(nsteps):
+        Fm = F @ m
+        cross = np.einsum("q,qi,qj->ij", W, Fm, G)
+        Sn = (np.einsum("q,qij,jk,qlk->il", W, F, S, F, optimize=True) + cross + cross.T
+              + np.einsum("q,qi,qj->ij", W, G, G))
+        m = EF @ m + Eg
+        S = 0.5 * (Sn + Sn.T)
+        path.append((m.copy(), S.copy()))
+    return path
+
+
+def lagged_expectation(prob_like, nsteps, K, relax, L, step0=0):
+    """Exact expectation of the pooled time correlation
+    <delta_i(t + l K) delta_i(t)> (delta = T - T_ref) over the pairs of
+    sampling steps l K apart within one run of steps step0+1..step0+nsteps
+    (sample at step m iff m % K == 0 and m > relax), l = 0..L-1.  Because
+    E[T^{t+j} | T^t] = M^j T^t + c_j with c_j = sum_{i<j} M^i g0 (mean_map),
+    E[T^{t+j} (T^t)^T] = M^j E[T^t (T^t)^T] + c_j E[T^t]^T, whatever the
+    noise.  Returns (expectation [L, cells], pairs per realization [L])."""
+    ops = scheme(prob_like)
+    tref = ops[3]
+    n = len(tref)
+    M, g0 = mean_map(prob_like, ops)
+    path = moment_path(prob_like, nsteps, step0)
+    samples = [m for m in range(step0 + 1, step0 + nsteps + 1) if m % K == 0 and m > relax]
+    Mj, cj = [np.eye(n)], [np.zeros(n)]
+    for _ in range((L - 1) * K):
+        cj.append(M @ cj[-1] + g0)
+        Mj.append(M @ Mj[-1])
+    out = np.zeros((L, n))
+    cnt = np.zeros(L)
+    for s, ts in enumerate(samples):
+        m_s = path[ts - step0][0]
+        for l in range(min(L, s + 1)):
+            tp = samples[s - l]
+            j = ts - tp
+            m_p, S_p = path[tp - step0]
+            cross = Mj[j] @ S_p + np.outer(cj[j], m_p)
+            out[l] += np.diag(cross) - tref * m_p - m_s * tref + tref * tref
+            cnt[l] += 1
+    return out / np.maximum(cnt, 1)[:, None], cnt
