@@ -326,10 +326,11 @@ static cudaError_t launch_cov_layout(const Step1DArgs<float>& a, const CovArgs& 
 
 // Lanes per realization of the layout chosen for N: 4-cell layouts up to 128
 // cells, above 16 cells x 16 lanes (15 stepping warps per CTA, two
-// realizations each; measured faster than 32 cells x 8 lanes, whose 7
-// stepping warps leave one SMSP with a single warp: 3.99 vs 4.14 ms per
-// 2560-step launch at 256 x 4096, and the predictor-corrector step needs the
-// registers anyway).
+// realizations each).  Measured per 2560-step launch at 256 x 4096: 3.99 ms,
+// against 4.14 ms for 32 cells x 8 lanes (7 stepping warps leave one SMSP
+// with a single warp) and 4.10 ms for 8 cells x 32 lanes (31 stepping warps
+// at 64 registers); the predictor-corrector step needs the registers of the
+// 16 x 16 layout anyway.
 static int cov_lpr(int N, bool pc)
 {
     (void)pc;
