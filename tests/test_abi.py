@@ -66,3 +66,17 @@ def test_struct_layout_matches_header(cls, cname):
 def test_missing_library_fails_loudly(tmp_path):
     with pytest.raises(_abi.LibraryMissing):
         _abi.load(str(tmp_path / "nope.so"))
+
+
+def test_scheme_constants_and_marshalling():
+    # the enum values the header declares, and the binding's mapping of the
+    # problem's scheme (an unknown name is an error, not forward Euler)
+    text = open(HEADER).read()
+    assert re.search(r"SHE_FE\s*=\s*0\s*,\s*SHE_PC\s*=\s*1", text)
+    assert (_abi.SHE_FE, _abi.SHE_PC) == (0, 1)
+    import paper_2406_12157_gb300 as S
+    import she_workloads as W
+    assert S.params_from_problem(W.oracle_rod()).scheme == _abi.SHE_FE
+    assert S.params_from_problem(W.oracle_rod(scheme="pc")).scheme == _abi.SHE_PC
+    with pytest.raises(KeyError):
+        S.params_from_problem(W.oracle_rod(scheme="rk4"))
