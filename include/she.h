@@ -131,6 +131,11 @@ typedef struct she_params {
                               rho uses stream stream_offset + rho, so disjoint shards of
                               one ensemble can run in separate handles or processes */
     void* stream;         /* cudaStream_t */
+    int32_t tc_lags;      /* L > 0: accumulate the time correlation
+                             <delta_i(t + l K) delta_i(t)>, l = 0..L-1 sampling intervals,
+                             over the pairs of samples since the last reset (the exercise on
+                             <dT_i^{n+m} dT_i^n>, Sec. 6); L <= 64; 1D, kernel auto, FP64 or
+                             FP32 without the covariance (otherwise SHE_ERR_UNSUPPORTED) */
 } she_params;
 
 typedef struct she_handle she_handle;
@@ -162,6 +167,9 @@ typedef struct she_stats_out {
     double* sk_axes;      /* [n0+n1+n2]; needs want_sk & SHE_SK_AXES */
     double* sum_d;        /* [cells] raw pooled sum of delta */
     double* sum_d2;       /* [cells] raw pooled sum of delta^2 */
+    double* time_corr;    /* [tc_lags][cells]: <delta_i(t + l K) delta_i(t)>, the pooled sum
+                             over the pairs l sampling intervals apart divided by their count
+                             (NaN for a lag with no pair yet); needs tc_lags */
 } she_stats_out;
 
 typedef struct she_sizes {
@@ -172,6 +180,7 @@ typedef struct she_sizes {
     int64_t elem_bytes;   /* 4 (FP32) or 8 (FP64) */
     int64_t axes_len;     /* n[0] + n[1] + n[2] over used axes */
     uint64_t step;        /* absolute steps taken so far */
+    int64_t tc_lags;      /* lags of the time correlation (0: not accumulated) */
 } she_sizes;
 
 /*

@@ -93,6 +93,7 @@ def params_from_problem(prob, stream=None, **overrides):
     p.kernel = SHE_KERNEL_PLAIN if kern in ("plain", SHE_KERNEL_PLAIN) else SHE_KERNEL_AUTO
     p.steps_per_launch = int(q.get("steps_per_launch", 0))
     p.stream_offset = int(q.get("stream_offset", 0))
+    p.tc_lags = int(q.get("tc_lags", 0))
     sp = _stream_ptr(stream)
     p.stream = sp
     return p
@@ -125,7 +126,7 @@ def _ptr(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if a is not None else None
 
 
-def she_stats(h, cov=False, sk=False, sk_axes=False, raw=False):
+def she_stats(h, cov=False, sk=False, sk_axes=False, raw=False, time_corr=False):
     """Finalised statistics as numpy arrays (see she_stats_out in she.h)."""
     s = she_get_sizes(h)
     c = int(s.cells)
@@ -140,6 +141,9 @@ def she_stats(h, cov=False, sk=False, sk_axes=False, raw=False):
     if raw:
         out["sum_d"] = np.empty(c)
         out["sum_d2"] = np.empty(c)
+    L = int(s.tc_lags)
+    if time_corr and L > 0:
+        out["time_corr"] = np.empty(L * c)
     st = _abi.she_stats_out()
     for k, v in out.items():
         setattr(st, k, _ptr(v))
@@ -147,6 +151,8 @@ def she_stats(h, cov=False, sk=False, sk_axes=False, raw=False):
     out["n_samples"] = int(st.n_samples)
     if cov:
         out["cov"] = out["cov"].reshape(c, c)
+    if "time_corr" in out:
+        out["time_corr"] = out["time_corr"].reshape(L, c)
     return out
 
 

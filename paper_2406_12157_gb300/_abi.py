@@ -69,6 +69,7 @@ class she_params(ctypes.Structure):
         ("steps_per_launch", ctypes.c_int32),
         ("stream_offset", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
+        ("tc_lags", ctypes.c_int32),
     ]
 
 
@@ -87,6 +88,7 @@ class she_stats_out(ctypes.Structure):
         ("sk_axes", _dp),
         ("sum_d", _dp),
         ("sum_d2", _dp),
+        ("time_corr", _dp),
     ]
 
 
@@ -99,6 +101,7 @@ class she_sizes(ctypes.Structure):
         ("elem_bytes", ctypes.c_int64),
         ("axes_len", ctypes.c_int64),
         ("step", ctypes.c_uint64),
+        ("tc_lags", ctypes.c_int64),
     ]
 
 

@@ -122,6 +122,11 @@ void release(Handle* h)
     cudaFree(h->d_state2);
     cudaFree(h->d_acc1);
     cudaFree(h->d_acc2);
+    cudaFree(h->d_tc_ring);
+    cudaFree(h->d_tc_acc);
+    cudaFree(h->d_tc_red);
+    h->d_tc_ring = nullptr;
+    h->d_tc_acc = h->d_tc_red = nullptr;
     cudaFree(h->d_face);
     cudaFree(h->d_flags);
     cudaFree(h->d_red);
@@ -228,6 +233,14 @@ she_status she_init(const she_params* p, she_handle** out)
     // 1D: the structure factor is the DFT of the pooled covariance (exact), so
     // SHE_SK_FULL implies the covariance accumulation.
     const bool need_cov = p->want_cov || (p->dim == 1 && (p->want_sk & SHE_SK_FULL));
+    if (st == SHE_OK && (p->tc_lags < 0 || p->tc_lags > 64)) {
+        st = SHE_ERR_INVALID_ARG; msg = "she: tc_lags must be in [0, 64]";
+    }
+    if (st == SHE_OK && p->tc_lags > 0 &&
+        (p->dim != 1 || p->kernel != SHE_KERNEL_AUTO || (p->precision == SHE_FP32 && need_cov))) {
+        st = SHE_ERR_UNSUPPORTED;
+        msg = "she: the time correlation runs on the 1D row kernel (kernel auto; FP64, or FP32 without the covariance)";
+    }
     if (st == SHE_OK && need_cov && (p->dim != 1 || p->n[0] > 256)) {
         st = SHE_ERR_INVALID_ARG; msg = "she: the covariance needs a 1D grid of at most 256 cells";
     }
@@ -289,6 +302,14 @@ she_status she_init(const she_params* p, she_handle** out)
     const int batches = (int)std::min<int64_t>(32, h->R);
     h->red_bytes = 2 * (size_t)batches * cells * sizeof(double);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_red, h->red_bytes);
+    h->tc_lags = p->tc_lags;
+    if (e == cudaSuccess && h->tc_lags > 0) {
+        const size_t tcn = nstate * (size_t)h->tc_lags;
+        e = cudaMalloc(&h->d_tc_ring, tcn * elem);
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_tc_acc, tcn * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_tc_red, (size_t)h->tc_lags * cells * sizeof(double));
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->d_tc_acc, 0, tcn * sizeof(double), h->stream);
+    }
     if (e == cudaSuccess && h->prob.dim > 1) {
         e = cudaMalloc(&h->d_state2, nstate * elem);
         if (e == cudaSuccess && h->precision == SHE_FP32) {
@@ -381,7 +402,7 @@ she_status she_init_batch(const she_params* p, int64_t count, she_handle** out)
             q.precision != SHE_FP32 || q.stats_interval != p[0].stats_interval || q.stats_interval < 1 ||
             q.relax_steps != p[0].relax_steps || q.stochastic != p[0].stochastic ||
             q.perturb_ic != p[0].perturb_ic || q.kernel != SHE_KERNEL_AUTO || q.want_cov || q.want_sk ||
-            q.scheme != SHE_FE || pr.n[0] > 2048) {
+            q.scheme != SHE_FE || q.tc_lags != 0 || pr.n[0] > 2048) {
             st = SHE_ERR_INVALID_ARG;
             msg = "she_init_batch: instances must be 1D, FP32, one realization each, N <= 2048, and share "
                   "equation, boundary, stats_interval, relax_steps, stochastic and perturb_ic";
@@ -523,6 +544,7 @@ she_status she_get_sizes(const she_handle* hh, she_sizes* s)
     s->axes_len = 0;
     for (int a = 0; a < h->prob.dim; ++a) s->axes_len += h->prob.n[a];
     s->step = h->step;
+    s->tc_lags = h->tc_lags;
     return SHE_OK;
 }
 
@@ -590,6 +612,23 @@ she_status she_stats(she_handle* hh, she_stats_out* out)
             const double mv = sv / B;
             out->var_se[i] = (B >= 2) ? std::sqrt(std::max(0.0, (svv / B - mv * mv) * B / (B - 1)) / B)
                                       : std::numeric_limits<double>::quiet_NaN();
+        }
+    }
+    if (out->time_corr) {
+        // <delta_i(t + l K) delta_i(t)>: the per-realization sums added over the
+        // realizations, over the R (n - l) pairs l sampling intervals apart
+        if (h->tc_lags < 1) return fail(h, SHE_ERR_INVALID_ARG, "she: time_corr needs tc_lags > 0");
+        const int L = h->tc_lags;
+        e = she::launch_reduce_sum(h->d_tc_acc, (int64_t)L * cells, (int)h->R, h->d_tc_red, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        std::vector<double> tc((size_t)L * cells);
+        if (e == cudaSuccess) e = cudaMemcpy(tc.data(), h->d_tc_red, tc.size() * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(time_corr)");
+        for (int l = 0; l < L; ++l) {
+            const int64_t pairs = h->R * std::max<int64_t>(0, h->samples_per_real - l);
+            for (int64_t i = 0; i < cells; ++i)
+                out->time_corr[(size_t)l * cells + i] = pairs > 0 ? tc[(size_t)l * cells + i] / (double)pairs
+                                                              : std::numeric_limits<double>::quiet_NaN();
         }
     }
     if (out->sk_axes) {
@@ -721,6 +760,8 @@ she_status she_reset_stats(she_handle* hh)
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_acc2, 0, nstate * sizeof(double), h->stream);
     if (e == cudaSuccess && h->d_m1) e = cudaMemsetAsync(h->d_m1, 0, nstate * sizeof(float), h->stream);
     if (e == cudaSuccess && h->d_m2) e = cudaMemsetAsync(h->d_m2, 0, nstate * sizeof(float), h->stream);
+    if (e == cudaSuccess && h->d_tc_acc)
+        e = cudaMemsetAsync(h->d_tc_acc, 0, nstate * (size_t)h->tc_lags * sizeof(double), h->stream);
     h->partial_samples = 0;
     if (e == cudaSuccess && h->d_sk_partial)
         e = cudaMemsetAsync(h->d_sk_partial, 0, (size_t)h->sk_ctas * 256 * 129 * sizeof(float), h->stream);

@@ -53,6 +53,10 @@ struct Step1DArgs {
     long long relax;      // sample after step m (1-based) iff m % K == 0 && m > relax
     uint32_t stream0;     // noise stream of realization 0
     int stochastic;
+    int tc_lags;          // time correlation: lags (0: off)
+    long long tc_s0;      // samples taken before this launch (since the last reset)
+    Real* tc_ring;        // [R][tc_lags][N] the last tc_lags samples of delta (sample s in slot s % L)
+    double* tc_acc;       // [R][tc_lags][N] sum of delta_i(s) delta_i(s - l)
 };
 
 // Arguments of the 2D step kernel (one step per launch).
@@ -182,6 +186,10 @@ struct Handle {
     cudaStream_t stream = nullptr;
     uint64_t step = 0;             // absolute steps taken
     int64_t samples_per_real = 0;  // samples taken per realization
+    int tc_lags = 0;               // time correlation lags (0: off)
+    void* d_tc_ring = nullptr;     // [R][tc_lags][N] of the state's type
+    double* d_tc_acc = nullptr;    // [R][tc_lags][N]
+    double* d_tc_red = nullptr;    // [tc_lags][N] reduction over the realizations
     int64_t launches = 0;
     // device buffers
     void* d_state = nullptr;       // [R][cells] float or double
@@ -279,6 +287,7 @@ cudaError_t launch_plain_step_scratch(const Problem& p, int R, const double* T, 
                                       uint32_t n, uint32_t stream0, int stochastic, cudaStream_t st);
 cudaError_t launch_step1d_cov(Handle& h, uint32_t step0, int nsteps, bool has_samples);
 cudaError_t launch_reduce_cov(const Handle& h, double* d_out);
+cudaError_t launch_reduce_sum(const double* partial, int64_t n, int G, double* out, cudaStream_t st);
 cudaError_t launch_cov_fp64(Handle& h);
 cudaError_t launch_step2d(Handle& h, uint32_t step0, int nsteps);
 cudaError_t launch_step3d(Handle& h, uint32_t step0, int nsteps);

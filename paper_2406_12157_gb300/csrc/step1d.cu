@@ -80,6 +80,31 @@ k_step1d(const __grid_constant__ Step1DArgs<Real> a)
         rowst.template advance<PC>(T, a.step0 + (uint32_t)s);
         if (s == next_s) {                 // sample after step m = n + 1 (Eq. (3.9))
             next_s += a.K;
+            if (a.tc_lags > 0 && active) {
+                // time correlation (the exercise on <dT_i^{n+m} dT_i^n>, Sec. 6):
+                // store this sample of delta in the realization's ring, then add
+                // delta_i(s) delta_i(s - l) for every lag l with a partner; each
+                // element has one writer, so the fire-and-forget adds are exact
+                const int L = a.tc_lags;
+                const long long st = a.tc_s0 + nsamp;
+                Real* ring = a.tc_ring + (size_t)rho * (size_t)L * (size_t)N;
+                double* acc = a.tc_acc + (size_t)rho * (size_t)L * (size_t)N;
+                const int slot = (int)(st % L);
+                const int lmax = st < (long long)(L - 1) ? (int)st : L - 1;
+#pragma unroll
+                for (int j = 0; j < C; ++j) {
+                    const int i = i0 + j;
+                    if (RAGGED && i >= N) continue;
+                    const Real ref = DIR ? fma(dref, Real(i0 + j) + half, wlo) : wlo;
+                    const Real d = T[j] - ref;
+                    ring[(size_t)slot * N + i] = d;
+                    atomicAdd(&acc[i], (double)(d * d));
+                    for (int l = 1; l <= lmax; ++l) {
+                        const Real prev = ring[(size_t)((st - l) % L) * N + i];
+                        atomicAdd(&acc[(size_t)l * N + i], (double)(d * prev));
+                    }
+                }
+            }
             ++nsamp;
 #pragma unroll
             for (int j = 0; j < C; ++j) {
@@ -244,6 +269,10 @@ static cudaError_t launch_fused(Handle& h, uint32_t step0, int nsteps)
     a.relax = (long long)h.relax;
     a.stream0 = h.stream0;
     a.stochastic = h.stochastic;
+    a.tc_lags = h.tc_lags;
+    a.tc_s0 = (long long)h.samples_per_real;
+    a.tc_ring = (Real*)h.d_tc_ring;
+    a.tc_acc = h.d_tc_acc;
     const bool dir = h.prob.bc == SHE_DIRICHLET;
     const bool sp = h.prob.equation == SHE_SPECIES;
     if (h.prob.scheme == SHE_PC) {

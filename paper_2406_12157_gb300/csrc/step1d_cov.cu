@@ -420,6 +420,13 @@ __global__ void k_reduce_partials(const double* __restrict__ partial, int64_t n,
     out[i] = s;
 }
 
+// out[i] = sum_g partial[g][i] for i < n (any G arrays of n sums back to back)
+cudaError_t launch_reduce_sum(const double* partial, int64_t n, int G, double* out, cudaStream_t st)
+{
+    k_reduce_partials<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(partial, n, G, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_reduce_cov(const Handle& h, double* d_out)
 {
     const int64_t n = (int64_t)h.prob.n[0] * h.prob.n[0];
