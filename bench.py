@@ -139,6 +139,15 @@ WORKLOADS = {
         # follow from the real-field symmetry), 3 split products, 2 flop per MAC
         stats_kernel="k_sk2d", stats_flop=lambda p: 3 * 2 * (p["n"][1] * p["n"][0] ** 2
                                                            + 2 * 128 * p["n"][1] * p["n"][0])),
+    "gradient_rod_tc": dict(
+        make=lambda W: W.gradient_rod(want_cov=0, tc_lags=8),
+        desc=("the gradient_rod configuration without the covariance, with the time correlation "
+              "<delta_i(t + l K) delta_i(t)> at 8 lags accumulated every 10 steps after 1e5 (the "
+              "exercise on <dT_i^{n+m} dT_i^n>, Sec. 6)"),
+        # forward Euler plus one product and one add per lag and cell at
+        # every sample (8 lags / 10 steps)
+        chunk=10_000, ops=25.0 + 5.5 + 4.0 + 6.0 + 2 * 8 / 10.0, bytes=None,
+        kernel="k_step1d<float,32,8,dirichlet,heat> with the time correlation", traffic=None),
     "species_2d_pc": dict(
         make=lambda W: W.species_2d(want_sk=1, scheme="pc"),
         desc=("the species_2d configuration (2D species diffusion 256x256 periodic, 256 realizations, "
@@ -322,7 +331,7 @@ def run_ours(args):
     p64 = dict(p)
     # 1D: the plain three-launches-per-step FP64 form; 2D/3D (streaming
     # kernels already launch once per step): the same kernel in FP64
-    kind64 = "plain" if p["dim"] == 1 and p.get("scheme", "fe") == "fe" else "auto"
+    kind64 = "plain" if p["dim"] == 1 and p.get("scheme", "fe") == "fe" and not p.get("tc_lags") else "auto"
     if batch:     # same total cells as 256-cell rows in the plain FP64 form
         p64 = dict(p, n=(256, 1, 1), realizations=max(1, cells // 256))
     sim64 = she.Simulation(p64, stream=stream, precision="fp64", kernel=kind64, stream_offset=rank * R,
