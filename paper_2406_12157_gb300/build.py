@@ -1,9 +1,13 @@
 """Build ``libshe.so`` (the C-ABI library) for sm_103a with nvcc, in-tree.
 
 Each ``csrc/*.cu`` translation unit is compiled in parallel to an object
-file, then linked into ``paper_2406_12157_gb300/_build/libshe.so``.  One
-``-gencode`` (compute_103a -> sm_103a); no CMake.  Rebuilds only when a
-source or header is newer than the library.
+file, then linked into ``paper_2406_12157_gb300/_build/libshe.so``.  The
+fused 1D kernel's instantiation unit (``step1d_inst.cu``) is compiled once per
+(precision, wall, equation, scheme) variant, sixteen objects, so that its
+template instances compile in parallel too.  One ``-gencode``
+(compute_103a -> sm_103a); no CMake.  An object is recompiled only when its
+source or any header is newer than it; the library is relinked when an
+object changed.
 """
 import concurrent.futures
 import glob
@@ -39,20 +43,38 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _deps():
-    files = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
-    return files
+# Units compiled once per variant: file name -> list of (object tag, defines).
+VARIANTS = {
+    "step1d_inst.cu": [
+        ("%s_%s_%s_%s" % (real[0], "dir" if d else "per", "sp" if s else "heat", "pc" if pc else "fe"),
+         ["-DSHE_V_REAL=%s" % real, "-DSHE_V_DIR=%d" % d, "-DSHE_V_SP=%d" % s, "-DSHE_V_PC=%d" % pc])
+        for real in ("float", "double") for d in (0, 1) for s in (0, 1) for pc in (0, 1)],
+}
 
 
-def _stale():
-    if not os.path.exists(LIB):
+def jobs():
+    """(source, object path, extra defines) of every object of the library."""
+    out = []
+    for src in sources():
+        base = os.path.basename(src)
+        for tag, defs in VARIANTS.get(base, [("", [])]):
+            obj = os.path.join(OUT_DIR, base + ("." + tag if tag else "") + ".o")
+            out.append((src, obj, defs))
+    return out
+
+
+def _headers():
+    return glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+
+
+def _obj_stale(src, obj, newest_header):
+    if not os.path.exists(obj):
         return True
-    t = os.path.getmtime(LIB)
-    return any(os.path.getmtime(f) > t for f in _deps())
+    t = os.path.getmtime(obj)
+    return os.path.getmtime(src) > t or newest_header > t
 
 
-def _compile(src, extra):
-    obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
+def _compile(src, obj, extra):
     cmd = [nvcc()] + ARCH + NVCC_FLAGS + extra + ["-c", src, "-o", obj]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
@@ -61,14 +83,20 @@ def _compile(src, extra):
 
 
 def build(force=False, verbose=False, extra_flags=()):
-    """Compile every CUDA source and link libshe.so; return its path."""
+    """Compile every CUDA source (stale objects only, unless `force`) and
+    link libshe.so; return its path."""
     os.makedirs(OUT_DIR, exist_ok=True)
-    if not force and not _stale():
-        return LIB
     extra = list(extra_flags)
-    with concurrent.futures.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
-        results = list(ex.map(lambda s: _compile(s, extra), sources()))
-    objs = [o for o, _ in results]
+    newest_header = max([os.path.getmtime(f) for f in _headers()] + [0.0])
+    all_jobs = jobs()
+    todo = [j for j in all_jobs if force or extra or _obj_stale(j[0], j[1], newest_header)]
+    objs = [o for _, o, _ in all_jobs]
+    if not todo and os.path.exists(LIB) and all(os.path.getmtime(o) <= os.path.getmtime(LIB) for o in objs):
+        return LIB
+    # longest units first (the variant objects and the larger kernels)
+    todo.sort(key=lambda j: -os.path.getsize(j[0]) - (10 ** 6 if j[2] else 0))
+    with concurrent.futures.ThreadPoolExecutor(max_workers=max(1, os.cpu_count() or 1)) as ex:
+        results = list(ex.map(lambda j: _compile(j[0], j[1], j[2] + extra), todo))
     if verbose:
         for _, log in results:
             if log:

@@ -280,6 +280,11 @@ inline void prof_close(Handle& h)
 }
 
 // Launchers (return cudaSuccess or the launch error).
+// The fused 1D kernel of one (precision, wall, equation, scheme) variant at
+// the given layout (cells per lane * 100 + lanes per realization); defined
+// in step1d_kernel.cuh, instantiated by step1d_inst.cu.
+template <typename Real, bool DIR, bool SP, bool PC>
+cudaError_t launch_step1d_variant(const Step1DArgs<Real>& a, int layout, cudaStream_t st);
 cudaError_t launch_init_state(Handle& h);
 cudaError_t launch_step1d(Handle& h, uint32_t step0, int nsteps);
 cudaError_t launch_step1d_plain(Handle& h, uint32_t step0, int nsteps);

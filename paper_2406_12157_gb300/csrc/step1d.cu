@@ -2,7 +2,8 @@
 // diffusion equation over many realizations (Sec. 3, Eq. (3.3), Dirichlet
 // walls Eq. (3.8), species noise Eq. (4.7)).
 //
-// Fused kernel: one warp owns one realization for a whole launch of many
+// Fused kernel (step1d_kernel.cuh, instantiated per variant by
+// step1d_inst.cu): one warp owns one realization for a whole launch of many
 // steps.  Lane l keeps cells [l*C, l*C + C) of the row in registers; the only
 // inter-lane traffic per step is three shuffles (left/right neighbour value,
 // right-neighbour face flux) plus the periodic wrap or the wall-noise
@@ -23,172 +24,9 @@
 #include <cstdlib>
 
 #include "philox.cuh"
-#include "row1d.cuh"
 #include "she_internal.cuh"
 
 namespace she {
-
-// ---------------------------------------------------------------- fused ----
-//
-// Layout: a warp is split into 32/LPR segments of LPR lanes; each segment owns
-// one realization and lane l of a segment holds cells [l*C, l*C + C) in
-// registers.  Shuffles are segmented (width LPR).  Moment partials of the
-// launch live in shared memory, [C][32] per warp and moment (lane-contiguous,
-// conflict-free), so the registers hold only the row and the pipeline state.
-
-template <typename Real, int C>
-constexpr int step1d_smem_per_warp() { return 2 * C * 32 * (int)sizeof(Real); }
-
-template <typename Real, int C, int LPR, bool DIR, bool SPECIES, bool RAGGED, int MINB, bool PC>
-__global__ void __launch_bounds__(kWarpsPerBlock1D * 32, MINB)
-k_step1d(const __grid_constant__ Step1DArgs<Real> a)
-{
-    constexpr unsigned FULL = 0xffffffffu;
-    constexpr int RPW = 32 / LPR;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31;
-    const int sl = lane % LPR;
-    const int warp = blockIdx.x * kWarpsPerBlock1D + (threadIdx.x >> 5);
-    if (warp * RPW >= a.R) return;  // warp-uniform
-    const int rho_raw = warp * RPW + lane / LPR;
-    const bool active = rho_raw < a.R;
-    const int rho = active ? rho_raw : a.R - 1;   // idle segments shadow a real row, never store
-
-    Real* sm1 = reinterpret_cast<Real*>(smem_raw) + (threadIdx.x >> 5) * (2 * C * 32) + lane;
-    Real* sm2 = sm1 + C * 32;
-
-    Row1D<Real, C, LPR, DIR, SPECIES, RAGGED> rowst;
-    rowst.init(a, sl, rho);
-    const int N = a.N;
-    const int i0 = sl * C;
-    Real* row = a.state + (size_t)rho * (size_t)N;
-    Real T[C];
-#pragma unroll
-    for (int j = 0; j < C; ++j) {
-        const int i = i0 + j;
-        T[j] = (!RAGGED || i < N) ? row[i] : Real(0);
-        sm1[j * 32] = Real(0);
-        sm2[j * 32] = Real(0);
-    }
-    const Real half = Real(0.5);
-    const Real wlo = a.wall_lo;
-    const Real dref = DIR ? (a.wall_hi - a.wall_lo) / Real(N) : Real(0);
-    int next_s = first_sample_index(a.step0, a.relax, a.K, a.nsteps);
-    int nsamp = 0;
-
-    for (int s = 0; s < a.nsteps; ++s) {
-        rowst.template advance<PC>(T, a.step0 + (uint32_t)s);
-        if (s == next_s) {                 // sample after step m = n + 1 (Eq. (3.9))
-            next_s += a.K;
-            if (a.tc_lags > 0 && active) {
-                // time correlation (the exercise on <dT_i^{n+m} dT_i^n>, Sec. 6):
-                // store this sample of delta in the realization's ring, then add
-                // delta_i(s) delta_i(s - l) for every lag l with a partner; each
-                // element has one writer, so the fire-and-forget adds are exact
-                const int L = a.tc_lags;
-                const long long st = a.tc_s0 + nsamp;
-                Real* ring = a.tc_ring + (size_t)rho * (size_t)L * (size_t)N;
-                double* acc = a.tc_acc + (size_t)rho * (size_t)L * (size_t)N;
-                const int slot = (int)(st % L);
-                const int lmax = st < (long long)(L - 1) ? (int)st : L - 1;
-#pragma unroll
-                for (int j = 0; j < C; ++j) {
-                    const int i = i0 + j;
-                    if (RAGGED && i >= N) continue;
-                    const Real ref = DIR ? fma(dref, Real(i0 + j) + half, wlo) : wlo;
-                    const Real d = T[j] - ref;
-                    ring[(size_t)slot * N + i] = d;
-                    atomicAdd(&acc[i], (double)(d * d));
-                    for (int l = 1; l <= lmax; ++l) {
-                        const Real prev = ring[(size_t)((st - l) % L) * N + i];
-                        atomicAdd(&acc[(size_t)l * N + i], (double)(d * prev));
-                    }
-                }
-            }
-            ++nsamp;
-#pragma unroll
-            for (int j = 0; j < C; ++j) {
-                const Real ref = DIR ? fma(dref, Real(i0 + j) + half, wlo) : wlo;
-                const Real d = T[j] - ref;
-                sm1[j * 32] += d;
-                sm2[j * 32] = fma(d, d, sm2[j * 32]);
-            }
-        }
-    }
-
-    bool bad = false;
-    if (active) {
-#pragma unroll
-        for (int j = 0; j < C; ++j) {
-            const int i = i0 + j;
-            if (!RAGGED || i < N) {
-                row[i] = T[j];
-                bad |= !finite_any(T[j]);
-            }
-        }
-        if (nsamp > 0) {
-            double* p1 = a.acc1 + (size_t)rho * (size_t)N;
-            double* p2 = a.acc2 + (size_t)rho * (size_t)N;
-#pragma unroll
-            for (int j = 0; j < C; ++j) {
-                const int i = i0 + j;
-                if (!RAGGED || i < N) {
-                    atomicAdd(&p1[i], (double)sm1[j * 32]);
-                    atomicAdd(&p2[i], (double)sm2[j * 32]);
-                }
-            }
-        }
-    }
-    if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.flags, 1);
-}
-
-template <typename Real, int C, int LPR, bool DIR, bool SP, int MINB, bool PC = false>
-static cudaError_t launch_layout(const Step1DArgs<Real>& a, cudaStream_t st)
-{
-    constexpr int RPW = 32 / LPR;
-    const int warps = (a.R + RPW - 1) / RPW;
-    const dim3 block(kWarpsPerBlock1D * 32);
-    const dim3 grid((warps + kWarpsPerBlock1D - 1) / kWarpsPerBlock1D);
-    const int smem = kWarpsPerBlock1D * step1d_smem_per_warp<Real, C>();
-    if (a.N == LPR * C) {
-        auto k = k_step1d<Real, C, LPR, DIR, SP, false, MINB, PC>;
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k<<<grid, block, smem, st>>>(a);
-    } else {
-        auto k = k_step1d<Real, C, LPR, DIR, SP, true, MINB, PC>;
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k<<<grid, block, smem, st>>>(a);
-    }
-    return cudaGetLastError();
-}
-
-// Register budget per layout (min resident blocks of 128 threads): enough
-// warps per SM to hold the whole 4096-realization ensemble in one wave for
-// the 256-cell rows, without starving the compiler of registers for ILP.
-template <typename Real, int C, int LPR, bool DIR, bool SP, int MINB32>
-static cudaError_t launch_layout_r(const Step1DArgs<Real>& a, cudaStream_t st)
-{
-    constexpr int MINB = sizeof(Real) == 4 ? MINB32 : (MINB32 / 2 > 0 ? MINB32 / 2 : 1);
-    return launch_layout<Real, C, LPR, DIR, SP, MINB>(a, st);
-}
-
-template <typename Real, bool DIR, bool SP>
-static cudaError_t launch_ds(const Step1DArgs<Real>& a, int layout, cudaStream_t st)
-{
-    // layout = cells per lane * 100 + lanes per realization (see pick_layout)
-    switch (layout) {
-    case 404: return launch_layout_r<Real, 4, 4, DIR, SP, 8>(a, st);
-    case 408: return launch_layout_r<Real, 4, 8, DIR, SP, 8>(a, st);
-    case 416: return launch_layout_r<Real, 4, 16, DIR, SP, 8>(a, st);
-    case 432: return launch_layout_r<Real, 4, 32, DIR, SP, 8>(a, st);
-    case 832: return launch_layout_r<Real, 8, 32, DIR, SP, 7>(a, st);
-    case 1616: return launch_layout_r<Real, 16, 16, DIR, SP, 4>(a, st);
-    case 1632: return launch_layout_r<Real, 16, 32, DIR, SP, 4>(a, st);
-    case 3208: return launch_layout_r<Real, 32, 8, DIR, SP, 2>(a, st);
-    case 3232: return launch_layout_r<Real, 32, 32, DIR, SP, 1>(a, st);
-    default: return cudaErrorInvalidValue;
-    }
-}
 
 // Predictor-corrector layouts: the step keeps the row, the predictor row, an
 // increment and the step's normals (4 C values per lane), so rows longer
@@ -205,20 +43,6 @@ static int pick_layout_pc(int N)
     return 0;
 }
 
-template <typename Real, bool DIR, bool SP>
-static cudaError_t launch_ds_pc(const Step1DArgs<Real>& a, int layout, cudaStream_t st)
-{
-    constexpr bool F = sizeof(Real) == 4;
-    switch (layout) {
-    case 404: return launch_layout<Real, 4, 4, DIR, SP, F ? 8 : 4, true>(a, st);
-    case 408: return launch_layout<Real, 4, 8, DIR, SP, F ? 8 : 4, true>(a, st);
-    case 416: return launch_layout<Real, 4, 16, DIR, SP, F ? 8 : 4, true>(a, st);
-    case 432: return launch_layout<Real, 4, 32, DIR, SP, F ? 8 : 4, true>(a, st);
-    case 832: return launch_layout<Real, 8, 32, DIR, SP, F ? 6 : 3, true>(a, st);
-    case 1632: return launch_layout<Real, 16, 32, DIR, SP, F ? 3 : 2, true>(a, st);
-    default: return cudaErrorInvalidValue;
-    }
-}
 
 // Layout for a row of N cells: cells per lane C and lanes per realization
 // LPR with LPR*C >= N.  Rows of up to 128 cells use 4 cells per lane in the
@@ -278,19 +102,19 @@ static cudaError_t launch_fused(Handle& h, uint32_t step0, int nsteps)
     if (h.prob.scheme == SHE_PC) {
         const int layout = pick_layout_pc(a.N);
         if (dir) {
-            if (sp) return launch_ds_pc<Real, true, true>(a, layout, h.stream);
-            return launch_ds_pc<Real, true, false>(a, layout, h.stream);
+            if (sp) return launch_step1d_variant<Real, true, true, true>(a, layout, h.stream);
+            return launch_step1d_variant<Real, true, false, true>(a, layout, h.stream);
         }
-        if (sp) return launch_ds_pc<Real, false, true>(a, layout, h.stream);
-        return launch_ds_pc<Real, false, false>(a, layout, h.stream);
+        if (sp) return launch_step1d_variant<Real, false, true, true>(a, layout, h.stream);
+        return launch_step1d_variant<Real, false, false, true>(a, layout, h.stream);
     }
     const int layout = pick_layout(a.N);
     if (dir) {
-        if (sp) return launch_ds<Real, true, true>(a, layout, h.stream);
-        return launch_ds<Real, true, false>(a, layout, h.stream);
+        if (sp) return launch_step1d_variant<Real, true, true, false>(a, layout, h.stream);
+        return launch_step1d_variant<Real, true, false, false>(a, layout, h.stream);
     }
-    if (sp) return launch_ds<Real, false, true>(a, layout, h.stream);
-    return launch_ds<Real, false, false>(a, layout, h.stream);
+    if (sp) return launch_step1d_variant<Real, false, true, false>(a, layout, h.stream);
+    return launch_step1d_variant<Real, false, false, false>(a, layout, h.stream);
 }
 
 cudaError_t launch_step1d(Handle& h, uint32_t step0, int nsteps)
