@@ -230,12 +230,16 @@ she_status she_reset_stats(she_handle* h);
 she_status she_get_state(she_handle* h, void* host_buf, size_t bytes, uint64_t* step);
 
 /* Overwrite the state from `host_buf` (same layout as she_get_state) and set
- * the absolute step counter.  Accumulators are not touched. */
+ * the absolute step counter.  Accumulators are not touched, but the time
+ * correlation (tc_lags) pairs no sample taken after the overwrite with one
+ * taken before it: the two belong to different trajectories.  Its pair
+ * counts per lag account for that. */
 she_status she_set_state(she_handle* h, const void* host_buf, size_t bytes, uint64_t step);
 
 /* Device-resident variants for callers that keep the state in their own
  * device memory: `dev_buf` is a device pointer of state_bytes bytes; the
- * copy is enqueued on the handle's stream (no synchronisation). */
+ * copy is enqueued on the handle's stream (no synchronisation).  The set
+ * variant restarts the time correlation's pairs as she_set_state does. */
 she_status she_get_state_device(she_handle* h, void* dev_buf, size_t bytes);
 she_status she_set_state_device(she_handle* h, const void* dev_buf, size_t bytes, uint64_t step);
 
@@ -291,7 +295,10 @@ she_status she_syrk_probe(const float* X, int32_t K, int32_t N, double* C);
  * the same GPU, e.g. issued on different streams, race -- issue them on one
  * stream.  The first call on each device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  Asynchronous on
+ * make that first call before any stream capture.  The address is cached
+ * with the id of the CUDA context it belongs to: after that context is
+ * destroyed (cudaDeviceReset) the next call on the device looks it up again,
+ * so that call, too, belongs before any capture.  Asynchronous on
  * p->stream.  Errors: SHE_ERR_INVALID_ARG, SHE_ERR_UNSTABLE, SHE_ERR_CUDA.
  */
 #define SHE_NOALLOC_MAX_FACES (1 << 20)

@@ -30,6 +30,8 @@ SHE_FE = 0
 SHE_PC = 1
 SHE_SK_FULL, SHE_SK_AXES = 1, 2
 SHE_KERNEL_AUTO, SHE_KERNEL_PLAIN = 0, 1
+# face fluxes the fixed scratch array of she_step_plain_noalloc holds
+SHE_NOALLOC_MAX_FACES = 1 << 20
 
 # Every symbol include/she.h declares (checked by the CPU test suite).
 EXPORTS = ["she_init", "she_init_batch", "she_step_n", "she_get_sizes", "she_stats",

@@ -196,6 +196,60 @@ int default_steps_per_launch(const Handle& h)
     return (int)spl;
 }
 
+// Device address of g_noalloc_faces in the current device's context (the
+// host-side name of the array is only a stand-in for the symbol).  Looked up
+// with cudaGetSymbolAddress once per device and cached together with the
+// driver's unique id of the context it was looked up in (cuCtxGetId, reached
+// through the runtime's driver entry point, so the library does not link the
+// driver library); when the device's context was destroyed and re-created
+// (cudaDeviceReset), the id differs, or no context is current yet, and the
+// address is looked up again.  Without that driver entry point the first
+// address is kept.
+typedef int (*ctx_id_fn)(void* ctx, unsigned long long* id);
+
+// Id of the current context; 0 if none is current; ~0 if the driver entry
+// point is unavailable.
+unsigned long long current_ctx_id()
+{
+    static ctx_id_fn fn = []() -> ctx_id_fn {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<ctx_id_fn>(f);
+    }();
+    if (!fn) return ~0ull;
+    unsigned long long id = 0;
+    if (fn(nullptr, &id) != 0) return 0;
+    return id;
+}
+
+cudaError_t noalloc_scratch(double** out)
+{
+    static std::mutex mu;
+    static double* addr[64] = {nullptr};
+    static unsigned long long ctx[64] = {0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    const unsigned long long id = current_ctx_id();
+    if (!addr[dev] || id == 0 || id != ctx[dev]) {
+        double* a = nullptr;
+        e = cudaGetSymbolAddress((void**)&a, g_noalloc_faces);   // makes the primary context current
+        if (e != cudaSuccess) {
+            addr[dev] = nullptr;
+            return e;
+        }
+        addr[dev] = a;
+        ctx[dev] = current_ctx_id();
+    }
+    *out = addr[dev];
+    return cudaSuccess;
+}
+
 }  // namespace
 
 extern "C" {
@@ -303,6 +357,7 @@ she_status she_init(const she_params* p, she_handle** out)
     h->red_bytes = 2 * (size_t)batches * cells * sizeof(double);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_red, h->red_bytes);
     h->tc_lags = p->tc_lags;
+    h->tc_pairs.assign((size_t)std::max(0, h->tc_lags), 0);
     if (e == cudaSuccess && h->tc_lags > 0) {
         const size_t tcn = nstate * (size_t)h->tc_lags;
         e = cudaMalloc(&h->d_tc_ring, tcn * elem);
@@ -524,6 +579,12 @@ she_status she_step_n(she_handle* hh, uint64_t n)
             she::prof_close(*h);
             return cuda_fail(h, e, "she_step_n");
         }
+        // time correlation: samples s of this chunk pair with s - l for every
+        // lag l that stays on this trajectory (s - l >= tc_base)
+        for (int l = 0; l < h->tc_lags; ++l) {
+            const int64_t s0 = std::max<int64_t>(h->samples_per_real, h->tc_base + l);
+            h->tc_pairs[(size_t)l] += std::max<int64_t>(0, h->samples_per_real + ns - s0);
+        }
         h->samples_per_real += ns;
         h->step += (uint64_t)chunk;
         left -= (uint64_t)chunk;
@@ -616,7 +677,8 @@ she_status she_stats(she_handle* hh, she_stats_out* out)
     }
     if (out->time_corr) {
         // <delta_i(t + l K) delta_i(t)>: the per-realization sums added over the
-        // realizations, over the R (n - l) pairs l sampling intervals apart
+        // realizations, over the pairs l sampling intervals apart (R (n - l)
+        // without a state overwrite since the last reset)
         if (h->tc_lags < 1) return fail(h, SHE_ERR_INVALID_ARG, "she: time_corr needs tc_lags > 0");
         const int L = h->tc_lags;
         e = she::launch_reduce_sum(h->d_tc_acc, (int64_t)L * cells, (int)h->R, h->d_tc_red, h->stream);
@@ -625,7 +687,7 @@ she_status she_stats(she_handle* hh, she_stats_out* out)
         if (e == cudaSuccess) e = cudaMemcpy(tc.data(), h->d_tc_red, tc.size() * sizeof(double), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(time_corr)");
         for (int l = 0; l < L; ++l) {
-            const int64_t pairs = h->R * std::max<int64_t>(0, h->samples_per_real - l);
+            const int64_t pairs = h->R * h->tc_pairs[(size_t)l];
             for (int64_t i = 0; i < cells; ++i)
                 out->time_corr[(size_t)l * cells + i] = pairs > 0 ? tc[(size_t)l * cells + i] / (double)pairs
                                                               : std::numeric_limits<double>::quiet_NaN();
@@ -776,6 +838,8 @@ she_status she_reset_stats(she_handle* hh)
                             h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "she_reset_stats");
     h->samples_per_real = 0;
+    h->tc_base = 0;
+    std::fill(h->tc_pairs.begin(), h->tc_pairs.end(), 0);
     return SHE_OK;
 }
 
@@ -806,6 +870,7 @@ she_status she_set_state(she_handle* hh, const void* host_buf, size_t bytes, uin
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "she_set_state");
     h->step = step;
+    h->tc_base = h->samples_per_real;   // the time correlation restarts its pairs here
     return SHE_OK;
 }
 
@@ -836,6 +901,7 @@ she_status she_set_state_device(she_handle* hh, const void* dev_buf, size_t byte
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "she_set_state_device");
     h->step = step;
+    h->tc_base = h->samples_per_real;   // the time correlation restarts its pairs here
     return SHE_OK;
 }
 
@@ -858,10 +924,6 @@ void she_free(she_handle* hh)
 
 she_status she_step_plain_noalloc(const she_params* p, const double* T_in, double* T_out, uint64_t step)
 {
-    // Device address of the scratch array, looked up once per device (the
-    // host-side name g_noalloc_faces is only a stand-in for the symbol).
-    static std::mutex mu;
-    static double* addr[64] = {nullptr};
     if (!p || !T_in || !T_out || T_in == T_out) return SHE_ERR_INVALID_ARG;
     she::Problem prob;
     std::string msg;
@@ -884,24 +946,11 @@ she_status she_step_plain_noalloc(const she_params* p, const double* T_in, doubl
                 (long long)faces, (int)SHE_NOALLOC_MAX_FACES);
         return SHE_ERR_INVALID_ARG;
     }
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= 64) return SHE_ERR_CUDA;
     double* scratch = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(mu);
-        if (!addr[dev]) {
-            e = cudaGetSymbolAddress((void**)&addr[dev], g_noalloc_faces);
-            if (e != cudaSuccess) {
-                addr[dev] = nullptr;
-                return SHE_ERR_CUDA;
-            }
-        }
-        scratch = addr[dev];
-    }
-    e = she::launch_plain_step_scratch(prob, (int)p->realizations, T_in, T_out, scratch, (uint32_t)step,
-                                       (uint32_t)p->stream_offset, p->stochastic ? 1 : 0,
-                                       (cudaStream_t)p->stream);
+    if (noalloc_scratch(&scratch) != cudaSuccess) return SHE_ERR_CUDA;
+    cudaError_t e = she::launch_plain_step_scratch(prob, (int)p->realizations, T_in, T_out, scratch, (uint32_t)step,
+                                                   (uint32_t)p->stream_offset, p->stochastic ? 1 : 0,
+                                                   (cudaStream_t)p->stream);
     return e == cudaSuccess ? SHE_OK : SHE_ERR_CUDA;
 }
 

@@ -55,6 +55,8 @@ struct Step1DArgs {
     int stochastic;
     int tc_lags;          // time correlation: lags (0: off)
     long long tc_s0;      // samples taken before this launch (since the last reset)
+    long long tc_base;    // sample index of the last state overwrite: pairs never reach
+                          // back past it (the trajectory before it is another one)
     Real* tc_ring;        // [R][tc_lags][N] the last tc_lags samples of delta (sample s in slot s % L)
     double* tc_acc;       // [R][tc_lags][N] sum of delta_i(s) delta_i(s - l)
 };
@@ -187,6 +189,8 @@ struct Handle {
     uint64_t step = 0;             // absolute steps taken
     int64_t samples_per_real = 0;  // samples taken per realization
     int tc_lags = 0;               // time correlation lags (0: off)
+    int64_t tc_base = 0;           // samples_per_real at the last set_state (0 after a reset)
+    std::vector<int64_t> tc_pairs; // [tc_lags] sample pairs per realization at each lag
     void* d_tc_ring = nullptr;     // [R][tc_lags][N] of the state's type
     double* d_tc_acc = nullptr;    // [R][tc_lags][N]
     double* d_tc_red = nullptr;    // [tc_lags][N] reduction over the realizations

@@ -95,6 +95,7 @@ static cudaError_t launch_fused(Handle& h, uint32_t step0, int nsteps)
     a.stochastic = h.stochastic;
     a.tc_lags = h.tc_lags;
     a.tc_s0 = (long long)h.samples_per_real;
+    a.tc_base = (long long)h.tc_base;
     a.tc_ring = (Real*)h.d_tc_ring;
     a.tc_acc = h.d_tc_acc;
     const bool dir = h.prob.bc == SHE_DIRICHLET;

@@ -75,7 +75,8 @@ k_step1d(const __grid_constant__ Step1DArgs<Real> a)
                 Real* ring = a.tc_ring + (size_t)rho * (size_t)L * (size_t)N;
                 double* acc = a.tc_acc + (size_t)rho * (size_t)L * (size_t)N;
                 const int slot = (int)(st % L);
-                const int lmax = st < (long long)(L - 1) ? (int)st : L - 1;
+                const long long since = st - a.tc_base;   // samples of this trajectory before st
+                const int lmax = since < (long long)(L - 1) ? (int)since : L - 1;
 #pragma unroll
                 for (int j = 0; j < C; ++j) {
                     const int i = i0 + j;

@@ -80,3 +80,10 @@ def test_scheme_constants_and_marshalling():
     assert S.params_from_problem(W.oracle_rod(scheme="pc")).scheme == _abi.SHE_PC
     with pytest.raises(KeyError):
         S.params_from_problem(W.oracle_rod(scheme="rk4"))
+
+
+def test_noalloc_limit_matches_header():
+    # the binding's copy of the fixed scratch size of she_step_plain_noalloc
+    m = re.search(r"#define\s+SHE_NOALLOC_MAX_FACES\s+\(1\s*<<\s*(\d+)\)", open(HEADER).read())
+    assert m, "SHE_NOALLOC_MAX_FACES not found"
+    assert _abi.SHE_NOALLOC_MAX_FACES == 1 << int(m.group(1))

@@ -2,8 +2,8 @@
 exercise on <dT_i^{n+m} dT_i^n>, Sec. 6) against the FP64 oracle, through the
 C ABI: FP64 to 1e-9 relative across launch windows (forward Euler and
 predictor-corrector, with and without the FP64 covariance), FP32 within the
-single-precision trajectory error, the pairs restarting at she_reset_stats,
-and the unsupported combinations refused."""
+single-precision trajectory error, the pairs restarting at she_reset_stats
+and at a state overwrite, and the unsupported combinations refused."""
 import numpy as np
 import pytest
 
@@ -60,6 +60,36 @@ def test_pairs_restart_at_reset():
         g = sim.stats(time_corr=True)
     o = O.finalize(p, O.run(p, 4, 40, step0=step, state=st))
     assert np.allclose(g["time_corr"], o["time_corr"], rtol=1e-9, atol=1e-15)
+
+
+@pytest.mark.parametrize("device", [False, True])
+def test_pairs_restart_at_set_state(device):
+    # the statistics span two trajectories: 60 steps from the initial
+    # condition, then 44 steps from an overwritten state; the time
+    # correlation pairs samples within each of them only, so it is the sum of
+    # two oracle runs (each pairs within its own run) over their pair counts
+    p = W.oracle_rod(n=(24, 1, 1), wall_lo=1.0, wall_hi=1.5, realizations=4, stats_interval=2,
+                     relax_steps=0, tc_lags=5, want_cov=0, want_sk=0, precision="fp64")
+    x = W.random_states(p, 4, seed=3)
+    with S.Simulation(p, steps_per_launch=14) as sim:
+        sim.step(60)
+        if device:
+            d = torch.from_numpy(np.ascontiguousarray(x)).to("cuda")
+            torch.cuda.synchronize()
+            S.she_set_state_device(sim.h, d.data_ptr(), d.numel() * 8, 60)
+        else:
+            sim.set_state(x, 60)
+        sim.step(44)
+        g = sim.stats(time_corr=True)
+    a = O.run(p, 4, 60)
+    b = O.run(p, 4, 44, step0=60, state=x)
+    tc = (a["sum_tc"] + b["sum_tc"]) / (a["n_tc"] + b["n_tc"])[:, None]
+    assert np.allclose(g["time_corr"], tc, rtol=1e-9, atol=1e-15)
+    # the moments pool both trajectories
+    ref = O.reference_profile(p)
+    n = a["n_samples"] + b["n_samples"]
+    mu = (a["sum_d"] + b["sum_d"]) / n
+    assert np.allclose(g["mean"], ref + mu, rtol=1e-12)
 
 
 @pytest.mark.parametrize("kw,status", [(dict(precision="fp32", want_cov=1), "SHE_ERR_UNSUPPORTED"),

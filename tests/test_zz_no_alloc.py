@@ -66,15 +66,35 @@ def test_noalloc_step_matches_handle_path_twice(N, bc, eq):
     assert np.max(np.abs(got2 - ref2) / np.abs(ref2)) < 1e-12
 
 
+def test_noalloc_accepts_exactly_its_scratch_size():
+    # realizations * (N + 1) == the limit: 4096 rows of 255 cells fill the array
+    N = 255
+    R = _abi.SHE_NOALLOC_MAX_FACES // (N + 1)
+    assert R * (N + 1) == _abi.SHE_NOALLOC_MAX_FACES
+    prob = W.oracle_rod(n=(N, 1, 1), wall_lo=1.0, wall_hi=2.0, realizations=R, precision="fp64",
+                        kernel="plain", want_cov=0, want_sk=0)
+    x = W.random_states(prob, R, seed=7)
+    with S.Simulation(prob) as sim:
+        sim.set_state(x, 99)
+        sim.step(1)
+        ref, _ = sim.state()
+    params = S.params_from_problem(prob)
+    d_in = torch.from_numpy(x).to("cuda")
+    d_out = torch.empty_like(d_in)
+    torch.cuda.synchronize()
+    st = S.lib().she_step_plain_noalloc(ctypes.byref(params), d_in.data_ptr(), d_out.data_ptr(), 99)
+    assert st == _abi.SHE_OK
+    torch.cuda.synchronize()
+    got = d_out.cpu().numpy()
+    assert np.max(np.abs(got - ref) / np.abs(ref)) < 1e-12
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch():
-    R = (_abi_max() // 257) + 1          # realizations * (N + 1) just above the limit
+    R = (_abi.SHE_NOALLOC_MAX_FACES // 257) + 1     # realizations * (N + 1) just above the limit
+    assert R * 257 > _abi.SHE_NOALLOC_MAX_FACES
     prob = W.oracle_rod(n=(256, 1, 1), realizations=R, precision="fp64", want_cov=0, want_sk=0)
     params = S.params_from_problem(prob)
     d = torch.empty(1, dtype=torch.float64, device="cuda")
     e = torch.empty(1, dtype=torch.float64, device="cuda")
     st = S.lib().she_step_plain_noalloc(ctypes.byref(params), d.data_ptr(), e.data_ptr(), 0)
     assert st == _abi.SHE_ERR_INVALID_ARG
-
-
-def _abi_max():
-    return 1 << 20
