@@ -365,6 +365,139 @@ def structure_factor(shape, r, eps_amp, scheme="fe"):
     return S
 
 
+
+# ------------------------------------ structure factors pooled over samples --
+
+def _sample_steps(K, relax, nsteps, step0=0):
+    """Sampling steps m (1-based) of a run of steps step0+1..step0+nsteps:
+    m % K == 0 and m > relax (Sec. 3, Eq. (3.9), after relaxation)."""
+    lo = max(step0, relax) // K + 1
+    hi = (step0 + nsteps) // K
+    return np.arange(lo, hi + 1, dtype=np.float64) * K
+
+
+def _mean_power(lam2, ns):
+    """Mean over the sample times n of lam2^n (lam2 = lambda^2 in [0, 1]);
+    the times are an arithmetic progression n_1 + K j, j < M, so the mean is
+    the geometric sum lam2^{n_1} (1 - q^M) / (M (1 - q)), q = lam2^K (1 where
+    q = 1), with the ratio taken through expm1 for q near 1."""
+    ns = np.asarray(ns, dtype=np.float64)
+    M = len(ns)
+    if M == 0:
+        return np.zeros_like(lam2)
+    n1 = ns[0]
+    step = ns[1] - ns[0] if M > 1 else 1.0
+    assert M == 1 or np.all(np.diff(ns) == step)
+    lam2 = np.asarray(lam2, dtype=np.float64)
+    with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
+        lg = np.log(lam2)                       # -inf where lam2 = 0
+        first = np.exp(n1 * lg)
+        num = -np.expm1(M * step * lg)
+        den = -np.expm1(step * lg)
+        ratio = np.where(den > 0.0, num / np.where(den > 0.0, den, 1.0) / M, 1.0)
+    return np.where(lam2 > 0.0, first * ratio, 0.0)
+
+
+def fe_structure_factor_pooled(shape, r, eps_amp, s0, K, relax, nsteps, step0=0):
+    """Exact expectation of the structure factor <|hat delta_k|^2> pooled over
+    the sampling steps of a run (sample at m iff m % K == 0 and m > relax) on
+    a periodic grid stepped by forward Euler with noise of constant expected
+    strength -- species, whose face-noise variance 2 r eps_c E[c_f] is linear
+    in the state, so that with the conserved uniform mean c the per-mode
+    recursion S' = lambda^2 S + q is exact (eps_amp = eps_c c).  From S_k = s0
+    at step step0 (the seeded initial perturbation: s0 = sigma^2 x cells for
+    k != 0), S_k(n) = S_inf + (s0 - S_inf) lambda_k^{2 (n - step0)},
+    lambda_k = 1 - r mu_k, S_inf = eps_amp cells / (1 - r mu_k / 2)
+    (fe_structure_factor).  Cells order, axis 0 fastest; k = 0 set to 0."""
+    dims = list(shape)
+    grids = np.meshgrid(*[np.arange(n) for n in reversed(dims)], indexing="ij")
+    mu = np.zeros(grids[0].shape)
+    for g, n in zip(grids, reversed(dims)):
+        mu += 4.0 * np.sin(np.pi * g / n) ** 2
+    lam2 = ((1.0 - r * mu) ** 2).ravel()
+    S_inf = fe_structure_factor(shape, r, eps_amp)
+    ns = _sample_steps(K, relax, nsteps, step0) - step0
+    out = S_inf + (s0 - S_inf) * _mean_power(lam2, ns)
+    out[0] = 0.0
+    return out
+
+
+def _axis_mus(dims):
+    """Per-axis mu_a(k_a) = 4 sin^2(pi k_a / n_a)."""
+    return [4.0 * np.sin(np.pi * np.arange(n) / n) ** 2 for n in dims]
+
+
+def heat_face_variance(shape, r, eps, T0):
+    """Stationary variance v_a of a face value (T_i + T_{i - e_a}) / 2 along
+    each axis a on a periodic heat grid at uniform mean T0.  The heat face
+    noise has E[g_f^2] = 2 r eps E[T_f^2] = 2 r eps (T0^2 + v_a) (noise
+    proportional to the face temperature, Eq. (2.12)), so per Fourier mode
+    S_k = 2 r eps cells sum_a (T0^2 + v_a) mu_a(k) / (1 - lambda_k^2), while
+    v_a = (1/cells^2) sum_k S_k cos^2(pi k_a / n_a) (the face average's
+    transfer function): a linear system for v solved here.  Returns v (one
+    entry per axis)."""
+    dims = list(shape)
+    D = len(dims)
+    cells = float(np.prod(dims))
+    mus = _axis_mus(dims)
+    grids = np.meshgrid(*[np.arange(n) for n in dims], indexing="ij")
+    mu_a = [mus[a][grids[a]] for a in range(D)]
+    mu = sum(mu_a)
+    den = 1.0 - (1.0 - r * mu) ** 2
+    den[(0,) * D] = 1.0
+    M = np.zeros((D, D))
+    for a in range(D):
+        cos2 = 1.0 - mu_a[a] / 4.0
+        for b in range(D):
+            w = cos2 * mu_a[b] / den
+            w[(0,) * D] = 0.0
+            M[a, b] = 2.0 * r * eps / cells * w.sum()
+    return np.linalg.solve(np.eye(D) - M, M @ np.full(D, T0 * T0))
+
+
+def heat_axes_structure_factor_pooled(shape, r, eps, T0, K, relax, nsteps, step0=0):
+    """Expected per-axis structure factor of a periodic heat grid started
+    uniform at T0 (no perturbation), pooled over the sampling steps of a run
+    (sample at m iff m % K == 0 and m > relax): for each axis a the 1D DFT
+    along a, <|hat delta_line(k_a)|^2> averaged over all lines along a.  By
+    Parseval over the other axes this is (1/lines^2) sum over the other
+    wavenumbers of the full-grid <|hat delta_k|^2>, which from a uniform start
+    is S_inf,k (1 - lambda_k^{2 n}) with the face noise strength
+    2 r eps (T0^2 + v_b) on axis b (multiplicative noise, Eq. (2.12)):
+    S_inf,k = 2 r eps cells sum_b (T0^2 + v_b) mu_b(k) / (1 - lambda_k^2).
+    The face variance is taken at its stationary value v_b
+    (heat_face_variance) from the first step on: it relaxes within the
+    decay time of the high-wavenumber modes that carry it (tens of steps), so
+    the neglected part is of order v x (those steps) / (sampled steps)
+    relative.  Returns the axes back to back (n_0 + n_1 + ...)."""
+    dims = list(shape)
+    D = len(dims)
+    cells = float(np.prod(dims))
+    v = heat_face_variance(shape, r, eps, T0)
+    mus = _axis_mus(dims)
+    ns = _sample_steps(K, relax, nsteps, step0) - step0
+    out = []
+    for a in range(D):
+        lines = cells / dims[a]
+        acc = np.zeros(dims[a])
+        # sum over the other axes' wavenumbers, chunked over the outermost
+        other = [b for b in range(D) if b != a]
+        grids = np.meshgrid(*[mus[b] for b in other], indexing="ij") if other else []
+        mu_o = sum(grids) if other else np.zeros(())
+        noise_o = sum((T0 * T0 + v[b]) * grids[i] for i, b in enumerate(other)) if other else np.zeros(())
+        for ka in range(dims[a]):
+            mu = mus[a][ka] + mu_o
+            lam2 = (1.0 - r * mu) ** 2
+            num = 2.0 * r * eps * cells * ((T0 * T0 + v[a]) * mus[a][ka] + noise_o)
+            den = 1.0 - lam2
+            with np.errstate(divide="ignore", invalid="ignore"):
+                S_inf = np.where(mu > 0.0, num / np.where(mu > 0.0, den, 1.0), 0.0)
+            pooled = S_inf * (1.0 - _mean_power(lam2, ns))
+            acc[ka] = pooled.sum() / (lines * lines)
+        out.append(acc)
+    return np.concatenate(out)
+
+
 # ------------------------------------------- exact moments by quadrature --
 
 def gauss_hermite(nvars, npts):
