@@ -26,13 +26,67 @@ sys.path.insert(0, ROOT)
 METRIC = "SHE cell-updates/s incl. noise, FP32-batched vs FP64 plain, % of roofline"
 UNIT = "cell-updates/s"
 
-# Algorithmic lane-operations per 1D cell-update, counted from the source
-# algorithm (Philox-4x32-10: per round 2 x (32x32->64 product = hi + lo),
-# 4 two-input xors, 2 key adds = 10 ops, 10 rounds per 4 normals -> 25 per
-# normal; Box-Muller: 2 uniforms (convert + scale), log, sqrt, sin/cos,
-# 2 products per pair -> 5.5 per normal; heat face flux: mean (2), amplitude
-# (1), noise (1); cell update: stencil (4) + flux difference (2) -> 6).
-OPS_PER_CELL_UPDATE_1D = 25.0 + 5.5 + 4.0 + 6.0
+# Per-pipe roofline.  Algorithmic lane-operations per cell-update are counted
+# from the source algorithm (never from compiled code) and assigned to the
+# pipe the CUDA programming guide's throughput table puts them on; rates are
+# that table's results per clock per SM (FP32 add/multiply/FMA 128; 32-bit
+# integer multiply 64; 32-bit integer add, logic, compare and min/max 64;
+# transcendentals (MUFU) and 32-bit conversions 16), plus the issue limit of
+# one warp instruction per clock per SM sub-partition (4 x 32 lane-ops).
+# The bound is the slowest of these resources.
+PIPE_RATES = {"issue": 128.0, "fma": 128.0, "alu": 64.0, "imad": 64.0, "xu": 16.0}
+
+
+def noise_ops(nz):
+    """Lane-ops of nz normals.  Philox-4x32-10 per block of 4 normals: 10
+    rounds of two 32x32->64 products (hi and lo: 4 integer-multiply ops) and
+    four xors (the round keys are precomputed per launch, so the key
+    schedule's adds are not per-block work): 10 imad + 10 alu per normal.
+    Box-Muller per block: 4 integer-to-float conversions, 2 log2, 2 rsqrt,
+    2 sin, 2 cos (12 xu), 12 FP32 multiplies/FMAs (uniform scale, -2 ln 2,
+    radius, angle, the four products), 2 max and 2 sign-flip xors (4 alu):
+    per normal 3 xu, 3 fma, 1 alu."""
+    return {"imad": 10.0 * nz, "alu": 11.0 * nz, "xu": 3.0 * nz, "fma": 3.0 * nz}
+
+
+def flux_ops(nf, species):
+    """Face fluxes: heat mean, amplitude, noise (3 fma); species mean,
+    product, x*rsqrt(x), noise (4 fma), clamp (1 alu), rsqrt (1 xu)."""
+    if species:
+        return {"fma": 4.0 * nf, "alu": 1.0 * nf, "xu": 1.0 * nf}
+    return {"fma": 3.0 * nf}
+
+
+def add_ops(*parts):
+    out = {k: 0.0 for k in ("imad", "alu", "xu", "fma")}
+    for d in parts:
+        for k, v in d.items():
+            if k != "issue":
+                out[k] += v
+    out["issue"] = sum(out[k] for k in ("imad", "alu", "xu", "fma"))
+    return out
+
+
+# cell update: 1D stencil and flux difference 5, 2D 9, 3D 11 FP32 ops;
+# the predictor-corrector's trapezoid (T + T* + inc) / 2: 3
+OPS_1D = add_ops(noise_ops(257.0 / 256.0), flux_ops(257.0 / 256.0, False), {"fma": 5.0})
+OPS_1D_PC = add_ops(noise_ops(257.0 / 256.0), flux_ops(2 * 257.0 / 256.0, False), {"fma": 2 * 5.0 + 3.0})
+OPS_2D_SP = add_ops(noise_ops(2.0), flux_ops(2.0, True), {"fma": 9.0})
+OPS_2D_SP_PC = add_ops(noise_ops(2.0), flux_ops(4.0, True), {"fma": 2 * 9.0 + 3.0})
+OPS_3D = add_ops(noise_ops(3.0), flux_ops(3.0, False), {"fma": 11.0})
+
+
+def pipe_roofline(ops, cu_per_s, sm_mhz, sms=152):
+    """Per-pipe bounds (cell-updates/s) and the binding one."""
+    pipes = {}
+    for k, rate in PIPE_RATES.items():
+        if ops.get(k, 0.0) <= 0.0:
+            continue
+        bound = sms * sm_mhz * 1e6 * rate / ops[k]
+        pipes[k] = {"ops_per_cell_update": round(ops[k], 3), "rate_per_clk_per_sm": rate,
+                    "bound_cell_updates_per_s": bound, "frac": round(cu_per_s / bound, 4)}
+    binding = min(pipes, key=lambda k: pipes[k]["bound_cell_updates_per_s"])
+    return binding, pipes
 
 
 def _peaks():
@@ -100,38 +154,40 @@ class ClockSampler:
 
 # Per workload: problem, description, default time steps per bench step, the
 # dominant kernel, and its algorithmic work per cell-update counted from the
-# source algorithm: lane-ops (Philox 25 and Box-Muller 5.5 per normal; face
-# flux 4 heat / 7 species per face; update 6 (1D) / 9 (2D) / 11 (3D)) and
+# source algorithm: lane-ops per pipe (noise_ops, flux_ops, the update) and
 # HBM bytes (state read + write, 8 B, plus the FP32 moment read-modify-write,
 # 16 B per sample, on the streaming 2D/3D paths; the 1D path keeps its rows
 # on chip for a whole launch).
 WORKLOADS = {
     "gradient_rod": dict(
+        leg_chunk=10000, leg_steps=10,
         make=lambda W: W.gradient_rod(),
         desc=("1D SHE rod, 256 cells, Dirichlet walls T_L=1 T_R=2, eps=1e-3, r=0.2, 4096 "
               "realizations, FP32 state, moments and full 256x256 equal-time covariance "
               "(tcgen05) every 10 steps after 1e5 steps"),
-        chunk=10_000, ops=25.0 + 5.5 + 4.0 + 6.0, bytes=None,
+        chunk=10_000, ops=OPS_1D, bytes=None,
         kernel="k_step1d_cov<16,16,dirichlet,heat>",
         # DRAM read + write of one launch (2560 steps, mostly the per-CTA
         # covariance flush), ncu capture in profiles/k_step1d_cov_gradient_rod.md
         traffic=dict(bytes=100.734208e6 + 41.664512e6, realizations=4096)),
     "gradient_rod_pc": dict(
+        leg_chunk=10000, leg_steps=10,
         make=lambda W: W.gradient_rod(scheme="pc"),
         desc=("the gradient_rod configuration (1D SHE rod, 256 cells, walls 1 and 2, eps=1e-3, r=0.2, "
               "4096 realizations, FP32, moments and the 256x256 covariance on tcgen05 every 10 steps "
               "after 1e5) stepped by the predictor-corrector scheme of Sec. 3"),
         # one normal per face as forward Euler, the face flux and update twice
         # (predictor, corrector on T*), and the trapezoid (T + T* + inc) / 2
-        chunk=10_000, ops=25.0 + 5.5 + 2 * (4.0 + 6.0) + 3.0, bytes=None,
+        chunk=10_000, ops=OPS_1D_PC, bytes=None,
         kernel="k_step1d_cov<16,16,dirichlet,heat,pc>",
         traffic=dict(bytes=100.739072e6 + 41.579008e6, realizations=4096)),   # profiles/k_step1d_cov_pc_gradient_rod_pc.md
     "species_2d": dict(
+        leg_chunk=1000, leg_steps=10,
         make=lambda W: W.species_2d(want_sk=1),
         desc=("2D stochastic species diffusion, 256x256 periodic, D=1, r=0.1, eps_c=1e-3, c=1 + "
               "zero-sum perturbation, 256 realizations, FP32, moments and the full 2D S(k) "
               "(two-stage DFT-as-GEMM on tcgen05) every 10 steps after 1e4"),
-        chunk=1000, ops=2 * (25.0 + 5.5 + 7.0) + 9.0, bytes=8.0 + 16.0 / 10,
+        chunk=1000, ops=OPS_2D_SP, bytes=8.0 + 16.0 / 10,
         kernel="k_step2d<float,8,32,species>",
         traffic=dict(bytes=74.257408e6 + 22.797312e6, realizations=256),   # profiles/k_step2d_species_2d.md
         # per realization and sample: row DFT (ny x nx x nx MAC) + column DFTs
@@ -140,15 +196,19 @@ WORKLOADS = {
         stats_kernel="k_sk2d", stats_flop=lambda p: 3 * 2 * (p["n"][1] * p["n"][0] ** 2
                                                            + 2 * 128 * p["n"][1] * p["n"][0])),
     "gradient_rod_tc": dict(
+        leg_chunk=10000, leg_steps=10,
         make=lambda W: W.gradient_rod(want_cov=0, tc_lags=8),
         desc=("the gradient_rod configuration without the covariance, with the time correlation "
               "<delta_i(t + l K) delta_i(t)> at 8 lags accumulated every 10 steps after 1e5 (the "
               "exercise on <dT_i^{n+m} dT_i^n>, Sec. 6)"),
         # forward Euler plus one product and one add per lag and cell at
-        # every sample (8 lags / 10 steps)
-        chunk=10_000, ops=25.0 + 5.5 + 4.0 + 6.0 + 2 * 8 / 10.0, bytes=None,
+        # every sample (8 lags / 10 steps); memory per cell and sample: the
+        # ring store and L - 1 ring loads (4 B each) and L FP64 atomic adds
+        # (8 B each), every 10 steps
+        chunk=10_000, ops=add_ops(OPS_1D, {"fma": 2 * 8 / 10.0}), bytes=(4.0 * 8 + 8.0 * 8) / 10.0,
         kernel="k_step1d<float,32,8,dirichlet,heat> with the time correlation", traffic=None),
     "species_2d_pc": dict(
+        leg_chunk=1000, leg_steps=6,
         make=lambda W: W.species_2d(want_sk=1, scheme="pc"),
         desc=("the species_2d configuration (2D species diffusion 256x256 periodic, 256 realizations, "
               "FP32, moments and the full 2D S(k) every 10 steps after 1e4) stepped by the "
@@ -157,15 +217,16 @@ WORKLOADS = {
         # the update twice, the trapezoid 3 (the two-pass kernels draw the
         # normals again in the corrector; that work is not counted); bytes: the
         # state read and written once plus the moments
-        chunk=1000, ops=2 * (25.0 + 5.5) + 2 * (2 * 7.0 + 9.0) + 3.0, bytes=8.0 + 16.0 / 10,
+        chunk=1000, ops=OPS_2D_SP_PC, bytes=8.0 + 16.0 / 10,
         kernel="k_step2d<float,8,32,species> predictor + corrector", traffic=None,
         stats_kernel="k_sk2d", stats_flop=lambda p: 3 * 2 * (p["n"][1] * p["n"][0] ** 2
                                                            + 2 * 128 * p["n"][1] * p["n"][0])),
     "cube_3d": dict(
+        leg_chunk=100, leg_steps=10,
         make=lambda W: W.cube_3d(want_sk=2),
         desc=("3D SHE 256^3 periodic, T0=1, r=0.1, eps=1e-3, 8 realizations, FP32, HBM-streaming "
               "stencil, moments and S(k) along x, y, z (line covariance on tcgen05) every 10 steps"),
-        chunk=100, ops=3 * (25.0 + 5.5 + 4.0) + 11.0, bytes=8.0 + 16.0 / 10,
+        chunk=100, ops=OPS_3D, bytes=8.0 + 16.0 / 10,
         kernel="k_step3d<float,8,heat>",
         traffic=dict(bytes=142.941184e6 + 92.432384e6, realizations=2),    # profiles/k_step3d_cube_3d.md
         # per realization and sample: for each axis a SYRK over all lines
@@ -173,17 +234,25 @@ WORKLOADS = {
         stats_kernel="k_axes_syrk", stats_flop=lambda p: 3 * 2 * sum(
             (p["n"][0] * p["n"][1] * p["n"][2] // p["n"][a]) * p["n"][a] ** 2 for a in range(3))),
     "batched_rods": dict(
+        leg_chunk=2560, leg_steps=10,
         make=lambda W: W.batched_rods(count=10_000, seed=0),
         desc=("10,000 uneven 1D SHE rods, N log-uniform in [16, 2048], kappa U[0.5, 2], walls U[1, 3], "
               "r = 0.2 each, per-instance seeds, FP32, moments every 10 steps after 1e4, one CUDA-graph "
               "launch per step batch"),
-        chunk=2560, ops=25.0 + 5.5 + 4.0 + 6.0, bytes=None, kernel="k_step1d_batch<*>",
+        chunk=2560, ops=OPS_1D, bytes=None, kernel="k_step1d_batch<*>",
         traffic=dict(bytes=17.868800e6 + 0.052480e6, realizations=1)),    # profiles/k_step1d_batch_batched_rods.md
     "oracle_rod": dict(
+        leg_chunk=10000, leg_steps=3,
         make=lambda W: W.oracle_rod(want_cov=0, want_sk=0),
         desc="1D SHE rod, 32 cells, walls 1, 16 realizations, FP64",
-        chunk=10_000, ops=25.0 + 5.5 + 4.0 + 6.0, bytes=None, kernel="k_step1d<double,4,8>"),
+        chunk=10_000, ops=OPS_1D, bytes=None, kernel="k_step1d<double,4,8>"),
 }
+
+
+# the workloads timed in short legs beside the headline (the `workloads`
+# sub-object of the bench line)
+LEG_WORKLOADS = ["gradient_rod_pc", "gradient_rod_tc", "species_2d", "species_2d_pc", "cube_3d",
+                 "batched_rods"]
 
 
 def workload(name):
@@ -241,6 +310,124 @@ def oracle_sample_rate(p, seconds_hint=10.0):
 
 # --------------------------------------------------------------- our arm ----
 
+def _make_sim(she, args, name, rank, stream, realizations=None):
+    """Simulation of a workload (a batch of instances for a list), its
+    problem, cells per realization and realizations; every rank runs a full
+    ensemble on its own noise streams (weak scaling)."""
+    p, desc = workload(name)
+    if isinstance(p, list):
+        probs = [dict(q, relax_steps=args.relax) if args.relax is not None else q for q in p]
+        sim = she.BatchSimulation(probs, stream=stream, stream_offset=rank * len(probs))
+        return sim, probs[0], desc, sum(q["n"][0] for q in probs), 1, probs
+    if args.relax is not None:
+        p["relax_steps"] = args.relax
+    if realizations:
+        p["realizations"] = realizations
+    sim = she.Simulation(p, stream=stream, stream_offset=rank * p["realizations"])
+    return sim, p, desc, _cells(p), p["realizations"], None
+
+
+def _roofline(wl, p, R, batch, cu_per_launch, per_launch_ms, prof, ms, peaks, peak_src, sm_mhz):
+    """Per-pipe roofline of the dominant (step) kernel, plus the HBM and the
+    tensor-core statistics kernels where the workload has them."""
+    cu_rate = cu_per_launch / (per_launch_ms / 1e3)
+    ops = wl["ops"]
+    binding, pipes = pipe_roofline(ops, cu_rate, sm_mhz)
+    rate = PIPE_RATES[binding]
+    achieved = cu_rate * ops[binding] / 1e12                    # lane-op Tops/s on the binding pipe
+    peak = 152 * sm_mhz * 1e6 * rate / 1e12
+    traffic = None
+    if wl.get("traffic"):
+        traffic = wl["traffic"]["bytes"] * (R / wl["traffic"]["realizations"] if not batch else 1.0)
+    roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": wl["kernel"],
+            "binding_pipe": binding, "pipes": pipes,
+            "ms_per_launch": round(per_launch_ms, 5), "cell_updates_per_launch": cu_per_launch,
+            "launches": prof["step_launches"],
+            "share_of_timed_region": round(prof["step_ms"] / ms, 4) if ms > 0 and prof["step_launches"] else None,
+            "peak_source": ("min over pipes of (rate per clk per SM x 152 SMs x sampled SM clock %.0f MHz) / "
+                            "(lane-ops per cell-update); rates from the CUDA throughput table (%s peaks file "
+                            "for the other roofs)" % (sm_mhz, peak_src))}
+    if wl["bytes"]:
+        gbs = cu_rate * wl["bytes"] / 1e9
+        roof["hbm"] = {"achieved": round(gbs, 1), "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s",
+                       "frac": round(gbs / peaks.get("hbm_gbs", 6800.0), 4), "bytes_per_cell_update": wl["bytes"],
+                       "peak_source": "hbm_gbs (%s)" % peak_src}
+    if prof["stats_launches"] and wl.get("stats_flop"):
+        flop = wl["stats_flop"](p) * (R if not batch else 1)
+        tf = flop / (prof["stats_ms"] / prof["stats_launches"] / 1e3) / 1e12
+        bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0))
+        roof["stats"] = {"bound": "tensor", "kernel": wl["stats_kernel"], "achieved": round(tf, 2),
+                         "peak": bf16, "unit": "TFLOP/s", "frac": round(tf / bf16, 4),
+                         "flop_per_launch": flop, "launches": prof["stats_launches"],
+                         "ms_per_launch": round(prof["stats_ms"] / prof["stats_launches"], 5),
+                         "share_of_timed_region": round(prof["stats_ms"] / ms, 4) if ms > 0 else None,
+                         "peak_source": "bf16_tflops_sustained (%s); the BF16x3 split counts 3 products" % peak_src}
+    return roof
+
+
+def _time_leg(sim, stream, chunk, steps, flush, barrier):
+    """K timed bench steps (CUDA events on the simulation's stream, L2 flushed
+    between them outside the events) with the library's per-kernel device
+    timing; returns (ms, launches, prof)."""
+    import torch
+    launches0 = sim.launches()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    sim.profile(True)
+    barrier()
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.add_(1.0)                 # L2 flush (256 MB write) outside the timed events
+            ev[k][0].record(stream)
+        sim.step(chunk)
+        with torch.cuda.stream(stream):
+            ev[k][1].record(stream)
+    barrier()
+    prof = sim.profile_read()
+    sim.profile(False)
+    ms = sum(x.elapsed_time(y) for x, y in ev)
+    return ms, sim.launches() - launches0, prof
+
+
+def _relax(sim, p, chunk):
+    """Step past the relaxation so that every timed step is in the sampling
+    phase (the phase that holds nine tenths of a full run)."""
+    left = int(p.get("relax_steps", 0))
+    while left > 0:
+        n = min(left, 100 * chunk)
+        sim.step(n)
+        left -= n
+
+
+def run_workload_leg(she, args, name, stream, flush, barrier, peaks, peak_src):
+    """A short device-timed leg of another workload for the `workloads`
+    sub-object: relaxation untimed, one warm-up bench step, then its timed
+    bench steps; the per-kernel roofline as for the headline."""
+    import torch
+    wl = WORKLOADS[name]
+    sim, p, desc, cells, R, probs = _make_sim(she, args, name, 0, stream)
+    batch = probs is not None
+    chunk = wl["leg_chunk"]
+    try:
+        _relax(sim, p, chunk)
+        sim.step(chunk)
+        torch.cuda.synchronize()
+        clocks = ClockSampler(0)
+        clocks.start()
+        ms, launches, prof = _time_leg(sim, stream, chunk, wl["leg_steps"], flush, barrier)
+        clk = clocks.stop()
+    finally:
+        sim.close()
+    cu = R * cells * chunk * wl["leg_steps"]
+    sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    step_launches = max(1, prof["step_launches"])
+    per_launch_ms = prof["step_ms"] / step_launches if prof["step_launches"] else ms / max(1, launches)
+    roof = _roofline(wl, p, R, batch, cu / step_launches, per_launch_ms, prof, ms, peaks, peak_src, sm_mhz)
+    return {"value": cu / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / wl["leg_steps"],
+            "steps": wl["leg_steps"], "time_steps_per_bench_step": chunk, "description": desc,
+            "phase": "sampling", "roofline": roof, "gpu_launches": int(launches), "clocks": clk}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -256,26 +443,9 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     she.lib()
-    p, desc = workload(args.workload)
-    batch = isinstance(p, list)
-    if batch:
-        probs = [dict(q, relax_steps=args.relax) if args.relax is not None else q for q in p]
-        p = probs[0]
-        R = 1
-        cells = sum(q["n"][0] for q in probs)
-    else:
-        if args.relax is not None:          # profile the sampling phase from the start
-            p["relax_steps"] = args.relax
-        if args.realizations:
-            p["realizations"] = args.realizations
-        R = p["realizations"]
-        cells = _cells(p)
     stream = torch.cuda.Stream()
-    # weak scaling: every rank runs a full ensemble on its own noise streams
-    if batch:
-        sim = she.BatchSimulation(probs, stream=stream, stream_offset=rank * len(probs))
-    else:
-        sim = she.Simulation(p, stream=stream, stream_offset=rank * R)
+    sim, p, desc, cells, R, probs = _make_sim(she, args, args.workload, rank, stream, args.realizations)
+    batch = probs is not None
     wl = WORKLOADS[args.workload]
     chunk = args.chunk if args.chunk else wl["chunk"]
     cu_per_step = R * cells * chunk
@@ -287,35 +457,23 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    # relaxation untimed, then the warm-up steps: the timed steps are all in
+    # the sampling phase
+    if args.relax is None:
+        _relax(sim, p, chunk)
     for _ in range(args.warmup):
         sim.step(chunk)
     barrier()
-    launches0 = sim.launches()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
-    sim.profile(True)            # event pair around every library launch, on its stream
-    barrier()
     t_wall0 = time.perf_counter()
-    for k in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.add_(1.0)          # L2 flush (256 MB write) outside the timed events
-            ev[k][0].record(stream)
-        sim.step(chunk)
-        with torch.cuda.stream(stream):
-            ev[k][1].record(stream)
-    barrier()
+    ms, launches, prof = _time_leg(sim, stream, chunk, args.steps, flush, barrier)
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
-    prof = sim.profile_read()
-    sim.profile(False)
-    launches = sim.launches() - launches0
-    ms = sum(a.elapsed_time(b) for a, b in ev)
     if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
     total_cu = cu_per_step * args.steps * world
     value = total_cu / (ms / 1e3)
     try:
@@ -379,48 +537,25 @@ def run_ours(args):
                "d2h_bytes_per_step": int(d2h)}
     sim.close()
 
+    peaks, peak_src = _peaks()
+    # the other workloads: short device-timed legs, every rank (weak scaling
+    # runs them per GPU; rank 0 reports its own)
+    legs = {}
+    if not args.no_workloads and args.workload == "gradient_rod":
+        for name in LEG_WORKLOADS:
+            legs[name] = run_workload_leg(she, args, name, stream, flush, barrier, peaks, peak_src)
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
-    peaks, peak_src = _peaks()
-    # DRAM bytes per launch of the dominant kernel from its ncu capture;
-    # where the capture ran fewer realizations, scaled by the units a launch
-    # processes (the traffic grows in proportion)
-    traffic = None
-    if wl.get("traffic"):
-        traffic = wl["traffic"]["bytes"] * (R / wl["traffic"]["realizations"] if not batch else 1.0)
     # the dominant (step) kernel alone: its launches and their summed device
     # time, from the event pairs the library recorded in the timed region
     step_launches = max(1, prof["step_launches"])
     cu_per_launch = cu_per_step * args.steps / step_launches
     per_launch_ms = prof["step_ms"] / step_launches if prof["step_launches"] else ms / max(1, launches)
-    ops_per_launch = cu_per_launch * wl["ops"]
-    achieved = ops_per_launch / (per_launch_ms / 1e3) / 1e12          # Tops/s (lane-ops)
-    peak = 128 * 152 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
-            "unit": "Tops/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-            "kernel": wl["kernel"], "ops_per_cell_update": wl["ops"],
-            "launches": prof["step_launches"], "ms_per_launch": round(per_launch_ms, 5),
-            "cell_updates_per_launch": cu_per_launch,
-            "share_of_timed_region": round(prof["step_ms"] / ms, 4) if ms > 0 else None,
-            "peak_source": "128 lane-ops/clk/SM x 152 SMs x max SM clock (%s)" % peak_src}
-    if wl["bytes"]:
-        gbs = cu_per_launch * wl["bytes"] / (per_launch_ms / 1e3) / 1e9
-        roof["hbm"] = {"achieved": round(gbs, 1), "peak": peaks.get("hbm_gbs", 6800.0),
-                       "unit": "GB/s", "frac": round(gbs / peaks.get("hbm_gbs", 6800.0), 4),
-                       "bytes_per_cell_update": wl["bytes"]}
-    if prof["stats_launches"] and wl.get("stats_flop"):
-        # tensor-core statistics kernels (S(k)), one region per sampling step
-        flop = wl["stats_flop"](p) * (R if not batch else 1)
-        tf = flop / (prof["stats_ms"] / prof["stats_launches"] / 1e3) / 1e12
-        bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0))
-        roof["stats"] = {"bound": "tensor", "kernel": wl["stats_kernel"], "achieved": round(tf, 2),
-                         "peak": bf16, "unit": "TFLOP/s", "frac": round(tf / bf16, 4),
-                         "flop_per_launch": flop, "launches": prof["stats_launches"],
-                         "ms_per_launch": round(prof["stats_ms"] / prof["stats_launches"], 5),
-                         "share_of_timed_region": round(prof["stats_ms"] / ms, 4) if ms > 0 else None,
-                         "peak_source": "bf16_tflops_sustained (%s); the BF16x3 split counts 3 products" % peak_src}
+    sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    roof = _roofline(wl, p, R, batch, cu_per_launch, per_launch_ms, prof, ms, peaks, peak_src, sm_mhz)
     cpu = None
     if not args.no_cpu_baseline and world == 1:     # rank 0 at N = 1 only
         rate, cores, sample = oracle_sample_rate(probs if batch else p)
@@ -433,12 +568,15 @@ def run_ours(args):
         "config": {"workload": args.workload, "description": desc, "cells": cells,
                    "realizations_per_gpu": R, "time_steps_per_bench_step": chunk,
                    "stats_interval": p["stats_interval"], "relax_steps": p["relax_steps"],
+                   "phase": ("sampling: the relaxation steps run untimed before the warm-up"
+                             if args.relax is None else "relax overridden to %d" % args.relax),
                    "l2": "flushed between timed steps (256 MB write outside the events)"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clk,
         "fp64_plain": {"value": plain_rate, "unit": UNIT, "steps": plain_steps,
                        "form": "plain FP64 (3 launches/step)" if kind64 == "plain" else "same kernel in FP64",
                        "speedup_fp32_batched": value / world / plain_rate},
+        "workloads": legs or None,
         "wall_s": t_wall,
     }
     print(json.dumps(line))
@@ -494,6 +632,8 @@ def main():
                     help="time steps per bench step (default: per workload)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the short legs of the other workloads")
     ap.add_argument("--realizations", type=int, default=None,
                     help="override the workload's realizations (small ncu captures)")
     ap.add_argument("--relax", type=int, default=None,
