@@ -41,6 +41,9 @@ class OrcParams(ctypes.Structure):
         ("want_sk", ctypes.c_int32),
         ("tc_lags", ctypes.c_int32),
         ("pad1", ctypes.c_int32),
+        ("cond", ctypes.POINTER(ctypes.c_double)),
+        ("cap", ctypes.POINTER(ctypes.c_double)),
+        ("kB_dV", ctypes.c_double),
     ]
 
 
@@ -112,6 +115,21 @@ def dimensionless(prob):
     return prob["D"] * prob["dt"] / dx2, 1.0 / (prob["n0"] * dV)
 
 
+def material_arrays(prob):
+    """A rod of several materials (the iron / aluminium exercise, Sec. 6):
+    per cell the conductance number a_i = lambda_i dt / dx^2 and the heat
+    capacity per volume rho c_V,i, and k_B / dV; None for a uniform problem.
+    The problem gives ``lambda_cells`` (thermal conductivity per cell) and
+    ``rho_cv_cells``."""
+    lam = prob.get("lambda_cells")
+    if lam is None:
+        return None
+    lam = np.asarray(lam, dtype=np.float64)
+    cap = np.ascontiguousarray(prob["rho_cv_cells"], dtype=np.float64)
+    cond = np.ascontiguousarray(lam * prob["dt"] / prob["dx"] ** 2)
+    return cond, cap, prob["kB"] / cell_volume(prob)
+
+
 def to_params(prob):
     p = OrcParams()
     dim = prob["dim"]
@@ -132,6 +150,13 @@ def to_params(prob):
     p.want_cov = int(prob.get("want_cov", 0))
     p.want_sk = int(prob.get("want_sk", 0))
     p.tc_lags = int(prob.get("tc_lags", 0))
+    mat = material_arrays(prob)
+    if mat is not None:
+        cond, cap, kb_dv = mat
+        p._keep = (cond, cap)              # the struct holds pointers into these
+        p.cond = _dp(cond)
+        p.cap = _dp(cap)
+        p.kB_dV = kb_dv
     return p
 
 

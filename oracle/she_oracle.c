@@ -50,6 +50,17 @@
  *   th_a = 2 pi U(u1), R_b = sqrt(-2 ln U(u2)), th_b = 2 pi U(u3);
  *   slots 0..3 = R_a cos th_a, R_a sin th_a, R_b cos th_b, R_b sin th_b.
  *
+ *   - a rod of two (or more) materials (the iron / aluminium exercise of
+ *     Sec. 6): per-cell conductivity lambda_i and heat capacity rho c_V,i in
+ *     the conservation form of the SHE, rho c_V dT/dt = div(lambda grad T +
+ *     sqrt(2 k_B lambda T^2) Z) (Sec. 2), discretised as Eq. (3.3): face
+ *     conductance = the harmonic mean of the two cells' (the series
+ *     conductance of two half cells; the paper is silent), a Dirichlet wall
+ *     face at half a cell with the edge cell's conductivity (as the wall
+ *     stencil of Eq. (3.8)), face noise sqrt(2 k_B a_f / dV) T_f N_f with
+ *     a_f = lambda_f dt / dx^2 (sqrt(2) more at a wall), and the face
+ *     balance divided by the cell's rho c_V.
+ *
  * Parity pins: see tests/test_oracle_*.py (Philox statistical tests, the
  * deterministic sine/Fourier-mode limit, the exact first/second-moment
  * recursion of the discrete scheme, closed forms of Eq. (3.10), (3.12),
@@ -94,6 +105,13 @@ typedef struct {
     int32_t want_sk;       /* bit0: full DFT over the grid, bit1: per-axis lines */
     int32_t tc_lags;       /* L > 0: accumulate the time correlation at lags 0..L-1 samples */
     int32_t pad1;
+    /* Variable material (1D heat; NULL for a uniform rod): per cell the
+     * conductance number a_i = lambda_i dt / dx^2 and the heat capacity per
+     * volume rho c_V,i, plus k_B / dV.  The rod of the exercise on an
+     * iron / aluminium rod (Sec. 6); r and eps are then unused. */
+    const double* cond;
+    const double* cap;
+    double kB_dV;
 } orc_params;
 
 /* ---------------------------------------------------------------- RNG ---- */
@@ -171,9 +189,46 @@ static int64_t orc_cells(const orc_params* p)
 
 /* Deterministic steady profile T_ref (Sec. 3: linear profile between the
  * walls for Dirichlet, uniform for periodic). */
+/* Face conductance numbers of a variable rod, a[f] for the low face of cell
+ * f (f = 0..n; face n is the high wall, or face 0 again when periodic):
+ * the harmonic mean of the two cells' a_i (series conductance of two half
+ * cells), the edge cell's a_i at a Dirichlet wall (a half cell away; the
+ * factor 2 of that half distance is applied where the flux is formed). */
+static void orc_face_conductance(const orc_params* p, double* a)
+{
+    const int n = p->n[0];
+    for (int f = 1; f < n; ++f) {
+        const double l = p->cond[f - 1], r = p->cond[f];
+        a[f] = 2.0 * l * r / (l + r);
+    }
+    if (p->bc == ORC_DIRICHLET) {
+        a[0] = p->cond[0];
+        a[n] = p->cond[n - 1];
+    } else {
+        const double l = p->cond[n - 1], r = p->cond[0];
+        a[0] = 2.0 * l * r / (l + r);
+        a[n] = a[0];
+    }
+}
+
 void orc_reference_profile(const orc_params* p, double* tref)
 {
     int64_t nc = orc_cells(p);
+    if (p->dim == 1 && p->bc == ORC_DIRICHLET && p->cond) {
+        /* steady conduction through resistances in series: half a cell to
+         * each wall (1 / (2 a)), 1 / a_f across each interior face; the heat
+         * flow q is the same through all of them */
+        int n = p->n[0];
+        double* a = (double*)malloc(sizeof(double) * (size_t)(n + 1));
+        orc_face_conductance(p, a);
+        double rtot = 0.5 / a[0] + 0.5 / a[n];
+        for (int f = 1; f < n; ++f) rtot += 1.0 / a[f];
+        const double q = (p->wall_hi - p->wall_lo) / rtot;
+        tref[0] = p->wall_lo + q * 0.5 / a[0];
+        for (int i = 1; i < n; ++i) tref[i] = tref[i - 1] + q / a[i];
+        free(a);
+        return;
+    }
     if (p->dim == 1 && p->bc == ORC_DIRICHLET) {
         int n = p->n[0];
         for (int i = 0; i < n; ++i)
@@ -195,12 +250,18 @@ void orc_initial_state(const orc_params* p, uint32_t stream, double* T)
     double mid = 0.5 * (p->wall_lo + p->wall_hi);
     double sigma = (p->equation == ORC_HEAT) ? sqrt(p->eps) * fabs(mid) : sqrt(p->eps * fabs(mid));
     double* pert = (double*)malloc(sizeof(double) * (size_t)nc);
-    double mean = 0.0;
+    double mean = 0.0, wsum = 0.0;
     for (int64_t i = 0; i < nc; ++i) {
-        pert[i] = sigma * orc_normal(p->seed, (uint64_t)i, 0u, stream, ORC_TAG_IC);
-        mean += pert[i];
+        /* a variable rod: each cell's own equilibrium variance k_B T^2 / (rho c_V,i dV) */
+        const double s = p->cond ? sqrt(p->kB_dV / p->cap[i]) * fabs(mid) : sigma;
+        const double w = p->cond ? p->cap[i] : 1.0;
+        pert[i] = s * orc_normal(p->seed, (uint64_t)i, 0u, stream, ORC_TAG_IC);
+        mean += w * pert[i];
+        wsum += w;
     }
-    mean /= (double)nc;
+    /* the conserved total of a periodic grid is sum rho c_V,i T_i (energy):
+     * project the perturbation to zero weighted sum */
+    mean /= wsum;
     int periodic = (p->bc == ORC_PERIODIC);
     for (int64_t i = 0; i < nc; ++i) T[i] += pert[i] - (periodic ? mean : 0.0);
     free(pert);
@@ -297,6 +358,38 @@ static void orc_increment_1d(const orc_params* p, const double* T, const double*
     }
 }
 
+/* Increment of a variable rod (Eq. (3.3) in conservation form with per-cell
+ * rho c_V,i and per-face conductance): the net conducted heat into cell i,
+ * a_{i+1/2} (T_{i+1} - T_i) - a_{i-1/2} (T_i - T_{i-1}) (a Dirichlet wall
+ * face conducts 2 a_w (T_wall - T_edge) over its half cell, Eq. (3.8)), plus
+ * the stochastic face flux difference G_{i+1/2} - G_{i-1/2},
+ * G_f = sqrt(2 k_B a_f / dV) T_f Z_f (the sqrt(2) of a wall face is in Z),
+ * all divided by rho c_V,i. */
+static void orc_increment_1d_var(const orc_params* p, const double* T, const double* Z, double* G, double* inc)
+{
+    const int n = p->n[0];
+    const int dir = (p->bc == ORC_DIRICHLET);
+    double* a = (double*)malloc(sizeof(double) * (size_t)(n + 1));
+    orc_face_conductance(p, a);
+    for (int f = 0; f < n; ++f) {
+        double tface;
+        if (f == 0) tface = dir ? p->wall_lo : 0.5 * (T[n - 1] + T[0]);
+        else tface = 0.5 * (T[f - 1] + T[f]);
+        G[f] = p->stochastic ? sqrt(2.0 * p->kB_dV * a[f]) * tface * Z[f] : 0.0;
+    }
+    if (dir) G[n] = p->stochastic ? sqrt(2.0 * p->kB_dV * a[n]) * p->wall_hi * Z[n] : 0.0;
+    else G[n] = G[0];
+    for (int i = 0; i < n; ++i) {
+        double q_lo, q_hi;            /* conducted heat in through the low and high faces */
+        if (dir && i == 0) q_lo = 2.0 * a[0] * (p->wall_lo - T[0]);
+        else q_lo = a[i] * (T[(i - 1 + n) % n] - T[i]);
+        if (dir && i == n - 1) q_hi = 2.0 * a[n] * (p->wall_hi - T[n - 1]);
+        else q_hi = a[i + 1] * (T[(i + 1) % n] - T[i]);
+        inc[i] = (q_lo + q_hi + (G[i + 1] - G[i])) / p->cap[i];
+    }
+    free(a);
+}
+
 /* The same in 2D/3D, periodic on every axis: per axis the 1D stencil and an
  * independent face noise (Eq. (2.11)), summed over the axes. */
 static void orc_increment_nd(const orc_params* p, const double* T, const double* Z, double* G, double* inc)
@@ -331,7 +424,8 @@ static void orc_increment_nd(const orc_params* p, const double* T, const double*
 
 static void orc_increment(const orc_params* p, const double* T, orc_work* w)
 {
-    if (p->dim == 1) orc_increment_1d(p, T, w->Z, w->G, w->inc);
+    if (p->dim == 1 && p->cond) orc_increment_1d_var(p, T, w->Z, w->G, w->inc);
+    else if (p->dim == 1) orc_increment_1d(p, T, w->Z, w->G, w->inc);
     else orc_increment_nd(p, T, w->Z, w->G, w->inc);
 }
 
@@ -478,6 +572,7 @@ int orc_run(const orc_params* p, int64_t R, uint32_t stream0, uint32_t step0, in
             double* sum_dd, double* sum_sk, double* sum_sk_axes, double* sum_tc)
 {
     if (p->dim < 1 || p->dim > 3 || R < 0 || nsteps < 0) return -2;
+    if (p->cond && (p->dim != 1 || p->equation != ORC_HEAT || !p->cap)) return -2;
     if (p->dim > 1 && p->bc != ORC_PERIODIC) return -2;
     if (p->scheme != ORC_FE && p->scheme != ORC_PC) return -2;
     if (sum_tc && p->tc_lags < 1) return -2;

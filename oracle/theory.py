@@ -136,9 +136,102 @@ def faces_nd_periodic(shape):
     return out
 
 
+def face_conductance(cond, bc):
+    """Face conductance numbers of a rod of several materials, a[f] for the
+    low face of cell f (f = 0..N): the harmonic mean of the two cells' (two
+    half-cell resistances in series), the edge cell's own at a Dirichlet wall,
+    and face N = face 0 on a periodic rod."""
+    c = np.asarray(cond, dtype=float)
+    N = len(c)
+    a = np.empty(N + 1)
+    a[1:N] = 2.0 * c[:-1] * c[1:] / (c[:-1] + c[1:])
+    if bc == "dirichlet":
+        a[0], a[N] = c[0], c[-1]
+    else:
+        a[0] = a[N] = 2.0 * c[-1] * c[0] / (c[-1] + c[0])
+    return a
+
+
+def conductance_matrix(a, bc):
+    """Matrix L of the conducted heat, (L T)_i = sum over the faces of cell i
+    of a_f (T_neighbour - T_i); a Dirichlet wall face conducts over half a
+    cell, 2 a_w (T_wall - T_edge), whose T_edge part is on the diagonal."""
+    N = len(a) - 1
+    L = np.zeros((N, N))
+    for f in range(N + 1 if bc == "dirichlet" else N):
+        if bc == "dirichlet" and f in (0, N):
+            i = 0 if f == 0 else N - 1
+            L[i, i] -= 2.0 * a[f]
+            continue
+        lo, hi = (f - 1) % N, f % N
+        L[lo, lo] -= a[f]
+        L[hi, hi] -= a[f]
+        L[lo, hi] += a[f]
+        L[hi, lo] += a[f]
+    return L
+
+
+def _scheme_var(prob_like):
+    """(A, b, faces, tref, L) of a rod of several materials (the iron /
+    aluminium exercise, Sec. 6): T' = T + C^{-1} (L T + b_w + sum_f g_f N_f
+    D_f) with C = diag(rho c_V,i), L the conductance matrix, b_w the walls'
+    conducted heat and E[g_f^2] = 2 k_B a_f / dV x E[T_f^2] (x 2 at a wall:
+    its half-cell conductance is 2 a_w).  Faces carry that full coefficient
+    in place of the squared wall weight."""
+    N = prob_like["n"][0]
+    bc = prob_like["bc"]
+    cond = np.asarray(prob_like["cond"], dtype=float)
+    cap = np.asarray(prob_like["cap"], dtype=float)
+    kb_dv = prob_like["kB_dV"]
+    a = face_conductance(cond, bc)
+    L = conductance_matrix(a, bc)
+    bw = np.zeros(N)
+    if bc == "dirichlet":
+        bw[0] = 2.0 * a[0] * prob_like["wall_lo"]
+        bw[-1] = 2.0 * a[N] * prob_like["wall_hi"]
+    A = np.eye(N) + L / cap[:, None]
+    b = bw / cap
+    faces = []
+    for P, q, w2, d in faces_1d(N, bc, prob_like["wall_lo"], prob_like["wall_hi"]):
+        f = len(faces)
+        faces.append((P, q, 2.0 * kb_dv * a[f] * w2, d / cap))
+    if bc == "dirichlet":
+        tref = np.linalg.solve(np.eye(N) - A, b)
+    else:
+        tref = np.full(N, float(prob_like["wall_lo"]))
+    return A, b, faces, tref, L
+
+
+def variable_equilibrium_cov(cond, cap, kb_dv, bc, T):
+    """Forward-Euler equilibrium covariance of a rod of several materials at
+    uniform temperature T with the noise linearised about T:
+    k_B T^2 / dV (C - L/2)^{-1}, C = diag(rho c_V,i), L the conductance
+    matrix (negative semi-definite).  Derivation: with A = I + C^{-1} L and
+    Q = 2 k_B T^2 / dV C^{-1} (-L) C^{-1} (the fluctuation-dissipation
+    balance of each face), X = (C + L/2)^{-1} solves
+    X = A X A^T + 2 C^{-1} (-L) C^{-1}, because with B = C + L/2,
+    (B + L/2) B^{-1} (B + L/2) = (B - L/2) B^{-1} (B - L/2) - 2 L.  Its
+    r -> 0 limit is k_B T^2 / (rho c_V,i dV) per cell and no correlation
+    (Eq. (3.10) per material).  Periodic rods conserve the energy
+    sum rho c_V,i T_i, and X + alpha 1 1^T solves the same equation; since
+    1^T (C + L/2) = c^T, c^T X = 1^T, and the solution with no energy
+    fluctuation (c^T S = 0) is X - 1 1^T / sum_i rho c_V,i."""
+    a = face_conductance(cond, bc)
+    L = conductance_matrix(a, bc)
+    c = np.asarray(cap, dtype=float)
+    X = np.linalg.inv(np.diag(c) + 0.5 * L)
+    if bc != "dirichlet":
+        n = len(c)
+        X = X - np.ones((n, n)) / c.sum()
+    return kb_dv * T * T * X
+
+
 def scheme(prob_like):
     """(A, b, faces, tref) of one forward-Euler step for a problem given as a
-    dict with dim, n, bc, r, eps, wall_lo, wall_hi, equation."""
+    dict with dim, n, bc, r, eps, wall_lo, wall_hi, equation (and, for a rod
+    of several materials, cond, cap and kB_dV in place of r and eps)."""
+    if prob_like.get("cond") is not None:
+        return _scheme_var(prob_like)
     dim = prob_like["dim"]
     r = prob_like["r"]
     if dim == 1:
@@ -166,7 +259,8 @@ def scheme(prob_like):
 
 def noise_cov(prob_like, faces, m, C):
     """sum_f E[g_f^2] d_f d_f^T for mean m and covariance C of the state."""
-    r, eps = prob_like["r"], prob_like["eps"]
+    var = prob_like.get("cond") is not None
+    r, eps = (1.0, 0.5) if var else (prob_like["r"], prob_like["eps"])   # var: the face holds 2 r eps w2
     heat = prob_like.get("equation", "heat") == "heat"
     n = len(m)
     Q = np.zeros((n, n))
@@ -186,6 +280,16 @@ def initial_moments(prob_like, tref):
     to zero sum on periodic grids."""
     n = len(tref)
     C = np.zeros((n, n))
+    if prob_like.get("perturb_ic", 1) and prob_like.get("cond") is not None:
+        # each cell's own equilibrium variance k_B T_mid^2 / (rho c_V,i dV);
+        # periodic: projected to zero energy sum rho c_V,i delta_i
+        mid = 0.5 * (prob_like["wall_lo"] + prob_like["wall_hi"])
+        cap = np.asarray(prob_like["cap"], dtype=float)
+        C = np.diag(prob_like["kB_dV"] * mid * mid / cap)
+        if prob_like["bc"] == "periodic":
+            Pr = np.eye(n) - np.outer(np.ones(n), cap) / cap.sum()
+            C = Pr @ C @ Pr.T
+        return tref.copy(), C
     if prob_like.get("perturb_ic", 1):
         mid = 0.5 * (prob_like["wall_lo"] + prob_like["wall_hi"])
         if prob_like.get("equation", "heat") == "heat":
@@ -231,7 +335,11 @@ def stationary(prob_like, iters=50):
     A, b, faces, tref, L = scheme(prob_like)
     n = len(tref)
     periodic = prob_like["dim"] > 1 or prob_like["bc"] == "periodic"
-    if periodic:
+    if periodic and prob_like.get("cond") is not None:
+        m = tref.copy()
+        cap = np.asarray(prob_like["cap"], dtype=float)
+        Pr = np.eye(n) - np.outer(np.ones(n), cap) / cap.sum()
+    elif periodic:
         m = tref.copy()
         Pr = np.eye(n) - np.ones((n, n)) / n
     else:
@@ -241,7 +349,7 @@ def stationary(prob_like, iters=50):
     # project the zero mode out (the total is conserved on periodic grids)
     Ap = Pr @ A @ Pr
     for _ in range(iters):
-        Q = Pr @ noise_cov(prob_like, faces, m, C) @ Pr
+        Q = Pr @ noise_cov(prob_like, faces, m, C) @ Pr.T
         Cn = scipy.linalg.solve_discrete_lyapunov(Ap, Q)
         Cn = 0.5 * (Cn + Cn.T)
         if np.max(np.abs(Cn - C)) <= 1e-15 * max(1.0, np.max(np.abs(Cn))):

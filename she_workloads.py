@@ -30,6 +30,17 @@ configurations this library is measured on):
 * ``iron_rod``       the paper's own physical rod: iron, l = 20 nm,
                      A = 4 nm^2, 32 cells, a = 0.1 (r = 0.05), 300 K
                      equilibrium or 100 K / 500 K walls.
+* ``two_material_rod`` the iron / aluminium rod of the exercise (Sec. 6) in
+                     the units of ``gradient_rod``: 256 cells, iron (rho c_V
+                     1, conductivity 1) on the left half, aluminium (rho c_V
+                     0.684, conductivity 3.386: the ratios of aluminium's
+                     2700 kg/m^3 x 897 J/(kg K) and 237 W/(m K) to the
+                     paper's iron) on the right, walls 1 and 2, dt 0.08
+                     (r = 0.08 in iron, 0.396 in aluminium), k_B = 1e-3,
+                     4096 realizations, FP32, covariance.
+* ``iron_aluminium_rod`` the paper's physical rod (l = 20 nm, A = 4 nm^2,
+                     32 cells, the iron time step a = 0.1) with its right half
+                     aluminium.
 """
 import numpy as np
 
@@ -131,3 +142,35 @@ def random_states(prob, R, seed, spread=0.05):
     lo = min(prob["wall_lo"], prob["wall_hi"]) * (1.0 - spread)
     hi = max(prob["wall_lo"], prob["wall_hi"]) * (1.0 + spread)
     return rng.uniform(lo, hi, size=(R, cells))
+
+
+# Material data: the paper's iron (Sec. 3) and aluminium (standard values).
+IRON = dict(rho=7870.0, c_v=450.0, lam=70.0)
+ALUMINIUM = dict(rho=2700.0, c_v=897.0, lam=237.0)
+
+
+def two_material_rod(**kw):
+    """Iron / aluminium rod (the exercise of Sec. 6) in nondimensional units:
+    per-cell conductivity ``lambda_cells`` and heat capacity ``rho_cv_cells``,
+    iron (1, 1) left of the middle, aluminium (the ratios to iron) right."""
+    n = int(kw.pop("cells", 256))
+    rcv_al = ALUMINIUM["rho"] * ALUMINIUM["c_v"] / (IRON["rho"] * IRON["c_v"])
+    lam_al = ALUMINIUM["lam"] / IRON["lam"]
+    half = n // 2
+    p = _base(n=(n, 1, 1), wall_lo=1.0, wall_hi=2.0, dt=0.08, realizations=4096, steps=1_000_000,
+              relax_steps=100_000, precision="fp32", want_cov=1, kB=1e-3)
+    p["lambda_cells"] = np.r_[np.full(half, 1.0), np.full(n - half, lam_al)]
+    p["rho_cv_cells"] = np.r_[np.full(half, 1.0), np.full(n - half, rcv_al)]
+    p.update(kw)
+    return p
+
+
+def iron_aluminium_rod(noneq=False, **kw):
+    """The paper's rod (l = 20 nm, A = 4 nm^2, 32 cells) with aluminium from
+    l/2 to l, dt = 0.1 dx^2 / (2 kappa_iron) (the paper's a = 0.1 for iron)."""
+    p = iron_rod(noneq=noneq, **kw)
+    n = p["n"][0]
+    p["lambda_cells"] = np.r_[np.full(n // 2, IRON["lam"]), np.full(n - n // 2, ALUMINIUM["lam"])]
+    p["rho_cv_cells"] = np.r_[np.full(n // 2, IRON["rho"] * IRON["c_v"]),
+                              np.full(n - n // 2, ALUMINIUM["rho"] * ALUMINIUM["c_v"])]
+    return p
