@@ -74,6 +74,9 @@ OPS_1D_PC = add_ops(noise_ops(257.0 / 256.0), flux_ops(2 * 257.0 / 256.0, False)
 OPS_2D_SP = add_ops(noise_ops(2.0), flux_ops(2.0, True), {"fma": 9.0})
 OPS_2D_SP_PC = add_ops(noise_ops(2.0), flux_ops(4.0, True), {"fma": 2 * 9.0 + 3.0})
 OPS_3D = add_ops(noise_ops(3.0), flux_ops(3.0, False), {"fma": 11.0})
+# a rod of several materials: the update ic (a_hi (T_r - T) + a_lo (T_l - T) + dG) + T,
+# 6 FP32 ops, its coefficients read from a shared-memory table
+OPS_1D_VAR = add_ops(noise_ops(257.0 / 256.0), flux_ops(257.0 / 256.0, False), {"fma": 6.0})
 
 
 def pipe_roofline(ops, cu_per_s, sm_mhz, sms=152):
@@ -241,6 +244,15 @@ WORKLOADS = {
               "launch per step batch"),
         chunk=2560, ops=OPS_1D, bytes=None, kernel="k_step1d_batch<*>",
         traffic=dict(bytes=17.868800e6 + 0.052480e6, realizations=1)),    # profiles/k_step1d_batch_batched_rods.md
+    "two_material_rod": dict(
+        leg_chunk=10000, leg_steps=10,
+        make=lambda W: W.two_material_rod(),
+        desc=("1D SHE rod of two materials (the iron / aluminium exercise, Sec. 6): 256 cells, iron "
+              "(rho c_V 1, lambda 1) left, aluminium (0.684, 3.386) right, walls 1 and 2, dt 0.08, "
+              "k_B 1e-3, 4096 realizations, FP32, moments and the 256x256 covariance (tcgen05) every 10 "
+              "steps after 1e5"),
+        chunk=10_000, ops=OPS_1D_VAR, bytes=None,
+        kernel="k_step1d_cov<16,16,dirichlet,heat,var>", traffic=None),
     "oracle_rod": dict(
         leg_chunk=10000, leg_steps=3,
         make=lambda W: W.oracle_rod(want_cov=0, want_sk=0),
@@ -251,8 +263,8 @@ WORKLOADS = {
 
 # the workloads timed in short legs beside the headline (the `workloads`
 # sub-object of the bench line)
-LEG_WORKLOADS = ["gradient_rod_pc", "gradient_rod_tc", "species_2d", "species_2d_pc", "cube_3d",
-                 "batched_rods"]
+LEG_WORKLOADS = ["gradient_rod_pc", "gradient_rod_tc", "two_material_rod", "species_2d", "species_2d_pc",
+                 "cube_3d", "batched_rods"]
 
 
 def workload(name):
@@ -489,7 +501,8 @@ def run_ours(args):
     p64 = dict(p)
     # 1D: the plain three-launches-per-step FP64 form; 2D/3D (streaming
     # kernels already launch once per step): the same kernel in FP64
-    kind64 = "plain" if p["dim"] == 1 and p.get("scheme", "fe") == "fe" and not p.get("tc_lags") else "auto"
+    kind64 = ("plain" if p["dim"] == 1 and p.get("scheme", "fe") == "fe" and not p.get("tc_lags")
+              and p.get("lambda_cells") is None else "auto")
     if batch:     # same total cells as 256-cell rows in the plain FP64 form
         p64 = dict(p, n=(256, 1, 1), realizations=max(1, cells // 256))
     sim64 = she.Simulation(p64, stream=stream, precision="fp64", kernel=kind64, stream_offset=rank * R,

@@ -136,6 +136,30 @@ typedef struct she_params {
                              over the pairs of samples since the last reset (the exercise on
                              <dT_i^{n+m} dT_i^n>, Sec. 6); L <= 64; 1D, kernel auto, FP64 or
                              FP32 without the covariance (otherwise SHE_ERR_UNSUPPORTED) */
+    /* A rod of several materials (the iron / aluminium exercise, Sec. 6):
+     * host arrays of n[0] values, read during she_init only, both NULL for a
+     * uniform rod (kappa and rho_cv) or both set (kappa and rho_cv are then
+     * ignored).  lambda_cells[i] is cell i's thermal conductivity lambda
+     * and rho_cv_cells[i] its rho c_V (> 0, finite).  The step is the
+     * conservation form of the SHE (Sec. 2),
+     *   T_i' = T_i + [a_{i+1/2} (T_{i+1} - T_i) - a_{i-1/2} (T_i - T_{i-1})
+     *                 + G_{i+1/2} - G_{i-1/2}] / rho c_V,i,
+     * with the face conductance number a_f = lambda_f dt / dx^2, lambda_f the
+     * harmonic mean of the face's two cells (series conductance of two half
+     * cells; a Dirichlet wall face is half a cell from the edge cell and
+     * conducts 2 a_w (T_wall - T_edge) with the edge cell's lambda, as the
+     * wall stencil of Eq. (3.8)), and G_f = sqrt(2 k_B a_f / dV) T_f N_f
+     * (sqrt(2) more at a wall).  T_ref (the centre of delta) is the exact
+     * steady profile, piecewise linear through the materials' resistances in
+     * series; the initial perturbation of cell i has its own equilibrium
+     * variance k_B T_mid^2 / (rho c_V,i dV), zero energy sum on a periodic
+     * rod.  1D heat, kernel auto, not in a batch (otherwise
+     * SHE_ERR_UNSUPPORTED); stability: every cell's Gershgorin radius of the
+     * symmetrised step, (a_lo + a_hi) / c_i + a_lo / sqrt(c_i c_lo) +
+     * a_hi / sqrt(c_i c_hi) <= 2 (r <= 1/2 for a uniform rod), else
+     * SHE_ERR_UNSTABLE. */
+    const double* lambda_cells;
+    const double* rho_cv_cells;
 } she_params;
 
 typedef struct she_handle she_handle;

@@ -94,6 +94,14 @@ def params_from_problem(prob, stream=None, **overrides):
     p.steps_per_launch = int(q.get("steps_per_launch", 0))
     p.stream_offset = int(q.get("stream_offset", 0))
     p.tc_lags = int(q.get("tc_lags", 0))
+    if q.get("lambda_cells") is not None:
+        # a rod of several materials: the arrays are read during she_init only;
+        # the struct keeps them alive as long as it lives
+        lam = np.ascontiguousarray(q["lambda_cells"], dtype=np.float64)
+        rcv = np.ascontiguousarray(q["rho_cv_cells"], dtype=np.float64)
+        p._keep = (lam, rcv)
+        p.lambda_cells = _ptr(lam)
+        p.rho_cv_cells = _ptr(rcv)
     sp = _stream_ptr(stream)
     p.stream = sp
     return p

@@ -72,6 +72,8 @@ class she_params(ctypes.Structure):
         ("stream_offset", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
         ("tc_lags", ctypes.c_int32),
+        ("lambda_cells", ctypes.POINTER(ctypes.c_double)),
+        ("rho_cv_cells", ctypes.POINTER(ctypes.c_double)),
     ]
 
 

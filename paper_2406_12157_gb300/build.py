@@ -3,8 +3,8 @@
 Each ``csrc/*.cu`` translation unit is compiled in parallel to an object
 file, then linked into ``paper_2406_12157_gb300/_build/libshe.so``.  The
 fused 1D kernel's instantiation unit (``step1d_inst.cu``) is compiled once per
-(precision, wall, equation, scheme) variant, sixteen objects, so that its
-template instances compile in parallel too.  One ``-gencode``
+(precision, wall, equation, scheme, material table) variant, 24 objects, so
+that its template instances compile in parallel too.  One ``-gencode``
 (compute_103a -> sm_103a); no CMake.  An object is recompiled only when its
 source or any header is newer than it; the library is relinked when an
 object changed.
@@ -46,9 +46,12 @@ def sources():
 # Units compiled once per variant: file name -> list of (object tag, defines).
 VARIANTS = {
     "step1d_inst.cu": [
-        ("%s_%s_%s_%s" % (real[0], "dir" if d else "per", "sp" if s else "heat", "pc" if pc else "fe"),
-         ["-DSHE_V_REAL=%s" % real, "-DSHE_V_DIR=%d" % d, "-DSHE_V_SP=%d" % s, "-DSHE_V_PC=%d" % pc])
-        for real in ("float", "double") for d in (0, 1) for s in (0, 1) for pc in (0, 1)],
+        ("%s_%s_%s_%s%s" % (real[0], "dir" if d else "per", "sp" if s else "heat", "pc" if pc else "fe",
+                            "_var" if v else ""),
+         ["-DSHE_V_REAL=%s" % real, "-DSHE_V_DIR=%d" % d, "-DSHE_V_SP=%d" % s, "-DSHE_V_PC=%d" % pc,
+          "-DSHE_V_VAR=%d" % v])
+        for real in ("float", "double") for d in (0, 1) for s in (0, 1) for pc in (0, 1) for v in (0, 1)
+        if not (v and s)],       # the material table is for heat rods
 }
 
 

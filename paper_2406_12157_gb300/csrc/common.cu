@@ -56,9 +56,80 @@ __global__ void k_init_state(Real* state, int64_t cells, int dim_is_1d_dirichlet
     }
 }
 
+// Initial condition of a rod of several materials (one block per
+// realization): T_ref,i + sigma_i N(0,1), sigma_i^2 = k_B T_mid^2 /
+// (rho c_V,i dV) (each material's equilibrium variance, Eq. (3.10)); a
+// periodic rod conserves the energy sum rho c_V,i T_i, so its perturbation
+// is projected to zero weighted sum (two passes over the row).
+template <typename Real>
+__global__ void k_init_state_var(Real* state, int N, const double* __restrict__ ref,
+                                 const double* __restrict__ sigma, const double* __restrict__ cap, int perturb,
+                                 int periodic, uint32_t key0, uint32_t key1, uint32_t stream0)
+{
+    const int rho = blockIdx.x;
+    const uint32_t stream = stream0 + (uint32_t)rho;
+    Real* row = state + (size_t)rho * (size_t)N;
+    __shared__ double red[2][32];
+    double local = 0.0, wlocal = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        double z = 0.0;
+        if (perturb) {
+            double zz[4];
+            box_muller4(philox4x32_10(make_uint4((uint32_t)(i >> 2), 0u, stream, 1u), key0, key1), zz);
+            z = sigma[i] * zz[i & 3];
+            local += cap[i] * z;
+            wlocal += cap[i];
+        }
+        row[i] = (Real)(ref[i] + z);
+    }
+    if (!(perturb && periodic)) return;
+    for (int o = 16; o > 0; o >>= 1) {
+        local += __shfl_xor_sync(0xffffffffu, local, o);
+        wlocal += __shfl_xor_sync(0xffffffffu, wlocal, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = local;
+        red[1][threadIdx.x >> 5] = wlocal;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const bool in = threadIdx.x < (blockDim.x >> 5);
+        double v = in ? red[0][threadIdx.x] : 0.0, w = in ? red[1][threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            v += __shfl_xor_sync(0xffffffffu, v, o);
+            w += __shfl_xor_sync(0xffffffffu, w, o);
+        }
+        if (threadIdx.x == 0) {
+            red[0][0] = v;
+            red[1][0] = w;
+        }
+    }
+    __syncthreads();
+    const double mean = red[0][0] / red[1][0];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        double zz[4];
+        box_muller4(philox4x32_10(make_uint4((uint32_t)(i >> 2), 0u, stream, 1u), key0, key1), zz);
+        row[i] = (Real)(ref[i] + (sigma[i] * zz[i & 3] - mean));
+    }
+}
+
 cudaError_t launch_init_state(Handle& h)
 {
     const Problem& p = h.prob;
+    if (h.var) {
+        const uint32_t key0 = (uint32_t)(p.seed & 0xffffffffu), key1 = (uint32_t)(p.seed >> 32);
+        const int N = p.n[0];
+        const double* sigma = h.d_sigma;
+        const double* cap = h.d_sigma + N;
+        h.launches += 1;
+        if (h.precision == SHE_FP64)
+            k_init_state_var<double><<<(unsigned)h.R, 256, 0, h.stream>>>(
+                (double*)h.d_state, N, h.d_ref, sigma, cap, h.perturb_ic, p.bc == SHE_PERIODIC, key0, key1, h.stream0);
+        else
+            k_init_state_var<float><<<(unsigned)h.R, 256, 0, h.stream>>>(
+                (float*)h.d_state, N, h.d_ref, sigma, cap, h.perturb_ic, p.bc == SHE_PERIODIC, key0, key1, h.stream0);
+        return cudaGetLastError();
+    }
     const bool dir1d = (p.dim == 1 && p.bc == SHE_DIRICHLET);
     const double mid = 0.5 * (p.wall_lo + p.wall_hi);
     const double sigma = (p.equation == SHE_HEAT) ? sqrt(p.eps) * fabs(mid) : sqrt(p.eps * fabs(mid));

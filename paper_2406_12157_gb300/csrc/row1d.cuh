@@ -78,7 +78,10 @@ __device__ __forceinline__ Real face_amp(Real face_value, Real amp2, Real s_heat
 // RK: the noise key comes as precomputed round keys (a kernel parameter of
 // the single-problem kernels); otherwise as (key0, key1) (per-instance keys
 // of the batch kernel).
-template <typename Real, int C, int LPR, bool DIR, bool SPECIES, bool RAGGED, bool RK = true>
+// VAR: a rod of several materials (heat): the face conductances, the face
+// noise amplitudes and the cells' 1 / (rho c_V) come from a material table
+// in shared memory (Coef1D, index = face / cell), set by init_var.
+template <typename Real, int C, int LPR, bool DIR, bool SPECIES, bool RAGGED, bool RK = true, bool VAR = false>
 struct Row1D {
     static_assert(C % 4 == 0, "cells per lane must be a multiple of 4");
     static_assert(LPR == 4 || LPR == 8 || LPR == 16 || LPR == 32, "segment width");
@@ -92,6 +95,7 @@ struct Row1D {
     int stochastic;
     Real wz[4];
     uint32_t wwin;
+    const Coef1D<Real>* cf = nullptr;   // VAR: the material table
 
     // per-row problem: cells, diffusion number, squared noise amplitude per
     // unit face value (2 r eps), wall values, noise stream and key
@@ -127,6 +131,18 @@ struct Row1D {
         init_vals(a.N, a.r, a.amp2, a.wall_lo, a.wall_hi, a.stream0 + (uint32_t)rho, a.key0, a.key1, a.stochastic, sl);
         if constexpr (RK) rk = &a.rk;
     }
+
+    // VAR: the material table (shared memory, N + 1 entries); the wall
+    // faces' noise amplitudes sqrt(2) x sqrt(2 k_B a_w / dV) x T_wall
+    __device__ __forceinline__ void init_var(const Coef1D<Real>* table)
+    {
+        cf = table;
+        const Real sq2 = Real(1.41421356237309504880);
+        g_low_amp = sq2 * Real(2) * cf[0].sh * wlo;
+        g_wall_amp = sq2 * Real(2) * cf[N].sh * whi;
+    }
+
+    __device__ __forceinline__ const Coef1D<Real>& coef_at(int k) const { return cf[k < N ? k : N]; }
 
     __device__ __forceinline__ uint4 noise_block(uint4 ctr) const
     {
@@ -165,9 +181,90 @@ struct Row1D {
         return g_high;
     }
 
+    // advance the row T of a rod of several materials by the forward-Euler
+    // step with absolute index n: the pipeline of step() with the face
+    // conductances a_f, the face noise amplitudes and 1 / (rho c_V) of the
+    // cells from the material table:
+    // T_i' = T_i + ic_i (a_hi (T_{i+1} - T_i) + a_lo (T_{i-1} - T_i) + G_hi - G_lo)
+    // (a wall's ghost cell 2 T_wall - T_edge makes a_w (ghost - T_edge) the
+    // half-cell conduction 2 a_w (T_wall - T_edge))
+    __device__ __forceinline__ void step_var(Real (&T)[C], uint32_t n)
+    {
+        const Real left_nb = __shfl_up_sync(FULL, T[C - 1], 1, LPR);
+        const Real right_nb = __shfl_down_sync(FULL, T[0], 1, LPR);
+        Real wrap_lo = Real(0), wrap_hi = Real(0);
+        if (!DIR) {
+            Real mine = T[C - 1];
+            if (RAGGED) {
+#pragma unroll
+                for (int j = 0; j < C; ++j)
+                    if (j == jlast) mine = T[j];
+            }
+            wrap_lo = __shfl_sync(FULL, mine, last_sl, LPR);
+            wrap_hi = __shfl_sync(FULL, T[0], 0, LPR);
+        }
+        const Real g_high = high_wall_flux(n);
+        const Coef1D<Real> c0 = coef_at(i0);
+        Real a_prev = c0.a, ic_prev = c0.ic;        // low face and capacity of the cell to update
+        Real g_first = Real(0), g_prev = Real(0), g_zero = Real(0);
+        Real old_prev = left_nb;
+        if (first_sl) old_prev = DIR ? Real(2) * wlo - T[0] : wrap_lo;
+        Real old_cur = T[0];
+#pragma unroll
+        for (int g = 0; g < C / 4; ++g) {
+            Real z[4] = {Real(0), Real(0), Real(0), Real(0)};
+            if (stochastic) {
+                const uint4 u = noise_block(make_uint4(q0 + (uint32_t)g, n, stream, 0u));
+                box_muller4(u, z);
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int j = 4 * g + t;
+                Real gf;
+                if (j == 0) {
+                    gf = c0.sh * (left_nb + T[0]) * z[0];
+                    if (first_sl) gf = DIR ? g_low_amp * z[0] : c0.sh * (wrap_lo + T[0]) * z[0];
+                    g_first = gf;
+                    if (!DIR) g_zero = __shfl_sync(FULL, g_first, 0, LPR);
+                } else {
+                    const Coef1D<Real> cj = coef_at(i0 + j);   // face i0 + j, cell i0 + j
+                    gf = cj.sh * (old_cur + T[j]) * z[t];
+                    Real tr = T[j];
+                    if (RAGGED && i0 + j == N) {            // ragged lane: the high face
+                        gf = DIR ? g_high : g_zero;
+                        tr = DIR ? Real(2) * whi - old_cur : wrap_hi;
+                    }
+                    const Real tc = old_cur;
+                    T[j - 1] = tc + ic_prev * (cj.a * (tr - tc) + a_prev * (old_prev - tc) + (gf - g_prev));
+                    old_prev = tc;
+                    old_cur = T[j];
+                    a_prev = cj.a;
+                    ic_prev = cj.ic;
+                }
+                g_prev = gf;
+            }
+        }
+        {
+            const Real g_next = __shfl_down_sync(FULL, g_first, 1, LPR);
+            const Real a_hi = coef_at(i0 + C).a;
+            const Real tc = old_cur;
+            Real tr = right_nb;
+            Real gr = g_next;
+            if ((!RAGGED && tail_sl) || (RAGGED && i0 + C - 1 == N - 1)) {
+                tr = DIR ? Real(2) * whi - tc : wrap_hi;
+                gr = DIR ? g_high : g_zero;
+            }
+            T[C - 1] = tc + ic_prev * (a_hi * (tr - tc) + a_prev * (old_prev - tc) + (gr - g_prev));
+        }
+    }
+
     // advance the row T by the forward-Euler step with absolute index n
     __device__ __forceinline__ void step(Real (&T)[C], uint32_t n)
     {
+        if constexpr (VAR) {
+            step_var(T, n);
+            return;
+        }
         const Real left_nb = __shfl_up_sync(FULL, T[C - 1], 1, LPR);
         const Real right_nb = __shfl_down_sync(FULL, T[0], 1, LPR);
         Real wrap_lo = Real(0), wrap_hi = Real(0);   // periodic: T_{N-1}, T_0
@@ -241,9 +338,65 @@ struct Row1D {
     // fluxes built from X with this step's normals z (the wall fluxes g_low
     // at the left Dirichlet wall and g_high at the right one do not depend on
     // X).  Cells of a ragged lane beyond N get values that are never used.
+    // inc of a rod of several materials (see step_var)
+    __device__ __forceinline__ void increment_var(const Real (&X)[C], const Real (&z)[C], Real g_high,
+                                                  Real (&inc)[C]) const
+    {
+        const Real left_nb = __shfl_up_sync(FULL, X[C - 1], 1, LPR);
+        const Real right_nb = __shfl_down_sync(FULL, X[0], 1, LPR);
+        Real wrap_lo = Real(0), wrap_hi = Real(0);
+        if (!DIR) {
+            Real mine = X[C - 1];
+            if (RAGGED) {
+#pragma unroll
+                for (int j = 0; j < C; ++j)
+                    if (j == jlast) mine = X[j];
+            }
+            wrap_lo = __shfl_sync(FULL, mine, last_sl, LPR);
+            wrap_hi = __shfl_sync(FULL, X[0], 0, LPR);
+        }
+        const Coef1D<Real> c0 = coef_at(i0);
+        Real g_first = c0.sh * (left_nb + X[0]) * z[0];
+        Real xl = left_nb;
+        if (first_sl) {
+            g_first = DIR ? g_low_amp * z[0] : c0.sh * (wrap_lo + X[0]) * z[0];
+            xl = DIR ? Real(2) * wlo - X[0] : wrap_lo;
+        }
+        const Real g_zero = DIR ? Real(0) : __shfl_sync(FULL, g_first, 0, LPR);
+        Real g_prev = g_first, a_lo = c0.a, ic = c0.ic;
+#pragma unroll
+        for (int j = 0; j + 1 < C; ++j) {
+            const Coef1D<Real> cj = coef_at(i0 + j + 1);   // face between cells j and j+1, cell j+1
+            Real gf = cj.sh * (X[j] + X[j + 1]) * z[j + 1];
+            Real tr = X[j + 1];
+            if (RAGGED && i0 + j + 1 == N) {
+                gf = DIR ? g_high : g_zero;
+                tr = DIR ? Real(2) * whi - X[j] : wrap_hi;
+            }
+            inc[j] = ic * (cj.a * (tr - X[j]) + a_lo * (xl - X[j]) + (gf - g_prev));
+            xl = X[j];
+            g_prev = gf;
+            a_lo = cj.a;
+            ic = cj.ic;
+        }
+        const Real g_next = __shfl_down_sync(FULL, g_first, 1, LPR);
+        const Real a_hi = coef_at(i0 + C).a;
+        Real tr = right_nb;
+        Real gr = g_next;
+        if ((!RAGGED && tail_sl) || (RAGGED && i0 + C - 1 == N - 1)) {
+            tr = DIR ? Real(2) * whi - X[C - 1] : wrap_hi;
+            gr = DIR ? g_high : g_zero;
+        }
+        inc[C - 1] = ic * (a_hi * (tr - X[C - 1]) + a_lo * (xl - X[C - 1]) + (gr - g_prev));
+    }
+
     __device__ __forceinline__ void increment(const Real (&X)[C], const Real (&z)[C], Real g_high,
                                               Real (&inc)[C]) const
     {
+        if constexpr (VAR) {
+            increment_var(X, z, g_high, inc);
+            return;
+        }
         const Real left_nb = __shfl_up_sync(FULL, X[C - 1], 1, LPR);
         const Real right_nb = __shfl_down_sync(FULL, X[0], 1, LPR);
         Real wrap_lo = Real(0), wrap_hi = Real(0);   // periodic: X_{N-1}, X_0

@@ -47,6 +47,82 @@ double cell_volume(const she_params& p)
     return p.dx * p.dx * p.dx;
 }
 
+// A rod of several materials (the iron / aluminium exercise, Sec. 6), in
+// FP64 on the host: face conductance numbers a_f = lambda_f dt / dx^2
+// (lambda_f the harmonic mean of the face's two cells: two half-cell
+// resistances in series; a Dirichlet wall face takes the edge cell's
+// lambda), half the face noise amplitude per unit face temperature
+// sqrt(2 k_B a_f / dV) / 2, the cells' rho c_V, the exact steady profile
+// T_ref (resistances in series between the walls) and each cell's
+// equilibrium perturbation width sqrt(k_B / (rho c_V,i dV)) |T_mid|.
+struct Materials {
+    std::vector<double> a, sh;        // [N + 1] by face (face N: the high wall, or face 0 again)
+    std::vector<double> cap, ref, sigma;   // [N] by cell
+};
+
+she_status build_materials(const she_params& p, Materials& m, std::string& msg)
+{
+    const int N = p.n[0];
+    const bool dir = p.bc == SHE_DIRICHLET;
+    const double dV = p.area * p.dx;
+    const double kb_dv = p.kB / dV;
+    const double g = p.dt / (p.dx * p.dx);
+    std::vector<double> cond((size_t)N);
+    m.cap.assign((size_t)N, 0.0);
+    for (int i = 0; i < N; ++i) {
+        const double lam = p.lambda_cells[i], c = p.rho_cv_cells[i];
+        if (!(lam > 0.0) || !(c > 0.0) || !std::isfinite(lam) || !std::isfinite(c)) {
+            msg = "she: lambda_cells and rho_cv_cells must be positive and finite";
+            return SHE_ERR_INVALID_ARG;
+        }
+        cond[(size_t)i] = lam * g;
+        m.cap[(size_t)i] = c;
+    }
+    m.a.assign((size_t)N + 1, 0.0);
+    for (int f = 1; f < N; ++f)
+        m.a[(size_t)f] = 2.0 * cond[(size_t)f - 1] * cond[(size_t)f] / (cond[(size_t)f - 1] + cond[(size_t)f]);
+    if (dir) {
+        m.a[0] = cond[0];
+        m.a[(size_t)N] = cond[(size_t)N - 1];
+    } else {
+        m.a[0] = m.a[(size_t)N] = 2.0 * cond[(size_t)N - 1] * cond[0] / (cond[(size_t)N - 1] + cond[0]);
+    }
+    m.sh.assign((size_t)N + 1, 0.0);
+    for (int f = 0; f <= N; ++f) m.sh[(size_t)f] = 0.5 * std::sqrt(2.0 * kb_dv * m.a[(size_t)f]);
+    // stability: Gershgorin radius of the symmetrised step C^{-1/2} L C^{-1/2}
+    // (a wall face conducts 2 a_w to a fixed value: diagonal only)
+    double worst = 0.0;
+    for (int i = 0; i < N; ++i) {
+        const double ci = m.cap[(size_t)i];
+        const bool wl = dir && i == 0, wr = dir && i == N - 1;
+        const double lo = m.a[(size_t)i], hi = m.a[(size_t)i + 1];
+        const double cl = m.cap[(size_t)((i - 1 + N) % N)], cr = m.cap[(size_t)((i + 1) % N)];
+        const double rad = ((wl ? 2.0 : 1.0) * lo + (wr ? 2.0 : 1.0) * hi) / ci + (wl ? 0.0 : lo / std::sqrt(ci * cl)) +
+                           (wr ? 0.0 : hi / std::sqrt(ci * cr));
+        worst = std::max(worst, rad);
+    }
+    if (worst > 2.0 * (1.0 + 1e-12)) {
+        char buf[200];
+        snprintf(buf, sizeof buf,
+                 "she: forward Euler is unstable for these materials: the largest Gershgorin radius of the "
+                 "step is %g > 2 (r <= 1/2 for a uniform rod)", worst);
+        msg = buf;
+        return SHE_ERR_UNSTABLE;
+    }
+    m.ref.assign((size_t)N, p.wall_lo);
+    if (dir) {
+        double rtot = 0.5 / m.a[0] + 0.5 / m.a[(size_t)N];
+        for (int f = 1; f < N; ++f) rtot += 1.0 / m.a[(size_t)f];
+        const double q = (p.wall_hi - p.wall_lo) / rtot;
+        m.ref[0] = p.wall_lo + 0.5 * q / m.a[0];
+        for (int i = 1; i < N; ++i) m.ref[(size_t)i] = m.ref[(size_t)i - 1] + q / m.a[(size_t)i];
+    }
+    const double mid = 0.5 * (p.wall_lo + p.wall_hi);
+    m.sigma.assign((size_t)N, 0.0);
+    for (int i = 0; i < N; ++i) m.sigma[(size_t)i] = std::sqrt(kb_dv / m.cap[(size_t)i]) * std::fabs(mid);
+    return SHE_OK;
+}
+
 // Validate and convert the physical parameters to the dimensionless pair
 // (r, eps) of Eq. (3.3)/(3.7).
 she_status convert(const she_params& p, she::Problem& out, std::string& msg)
@@ -81,7 +157,28 @@ she_status convert(const she_params& p, she::Problem& out, std::string& msg)
     if (!std::isfinite(p.wall_lo) || !std::isfinite(p.wall_hi)) { msg = "she: walls must be finite"; return SHE_ERR_INVALID_ARG; }
     const double dV = cell_volume(p);
     double r, eps;
-    if (p.equation == SHE_HEAT) {
+    const bool var = p.lambda_cells || p.rho_cv_cells;
+    if (var) {
+        if (!p.lambda_cells || !p.rho_cv_cells) {
+            msg = "she: lambda_cells and rho_cv_cells go together";
+            return SHE_ERR_INVALID_ARG;
+        }
+        if (p.dim != 1 || p.equation != SHE_HEAT) {
+            msg = "she: a rod of several materials is a 1D heat problem";
+            return SHE_ERR_UNSUPPORTED;
+        }
+        if (!(p.kB >= 0.0)) { msg = "she: kB must be non-negative"; return SHE_ERR_INVALID_ARG; }
+        Materials m;
+        const she_status st = build_materials(p, m, msg);
+        if (st != SHE_OK) return st;
+        // largest diffusion number and relative variance (informational)
+        r = 0.0;
+        eps = 0.0;
+        for (int i = 0; i < p.n[0]; ++i) {
+            r = std::max(r, 0.5 * (m.a[(size_t)i] + m.a[(size_t)i + 1]) / m.cap[(size_t)i]);
+            eps = std::max(eps, p.kB / (m.cap[(size_t)i] * dV));
+        }
+    } else if (p.equation == SHE_HEAT) {
         if (!(p.kappa > 0.0) || !(p.rho_cv > 0.0) || !(p.kB >= 0.0)) {
             msg = "she: kappa, rho_cv must be positive and kB non-negative";
             return SHE_ERR_INVALID_ARG;
@@ -94,7 +191,7 @@ she_status convert(const she_params& p, she::Problem& out, std::string& msg)
         eps = 1.0 / (p.n0 * dV);
     }
     if (!std::isfinite(r) || !std::isfinite(eps)) { msg = "she: non-finite r or eps"; return SHE_ERR_INVALID_ARG; }
-    if (r > 1.0 / (2.0 * p.dim)) {
+    if (!var && r > 1.0 / (2.0 * p.dim)) {
         char buf[160];
         snprintf(buf, sizeof buf, "she: forward Euler is unstable: r = kappa dt/dx^2 = %g > 1/(2 dim) = %g", r,
                  1.0 / (2.0 * p.dim));
@@ -128,6 +225,11 @@ void release(Handle* h)
     h->d_tc_ring = nullptr;
     h->d_tc_acc = h->d_tc_red = nullptr;
     cudaFree(h->d_face);
+    cudaFree(h->d_coef);
+    cudaFree(h->d_ref);
+    cudaFree(h->d_sigma);
+    h->d_coef = nullptr;
+    h->d_ref = h->d_sigma = nullptr;
     cudaFree(h->d_flags);
     cudaFree(h->d_red);
     cudaFree(h->d_cov_partial);
@@ -327,6 +429,9 @@ she_status she_init(const she_params* p, she_handle** out)
     if (st == SHE_OK && p->dim > 1 && p->kernel != SHE_KERNEL_AUTO) {
         st = SHE_ERR_UNSUPPORTED; msg = "she: the plain form is 1D";
     }
+    if (st == SHE_OK && p->lambda_cells && p->kernel != SHE_KERNEL_AUTO) {
+        st = SHE_ERR_UNSUPPORTED; msg = "she: a rod of several materials runs on the fused kernels (kernel auto)";
+    }
     if (st != SHE_OK) {
         fprintf(stderr, "%s\n", msg.c_str());
         delete h;
@@ -420,6 +525,38 @@ she_status she_init(const she_params* p, she_handle** out)
         if (e == cudaSuccess)
             e = cudaMemsetAsync(h->d_cov_partial, 0, (size_t)h->cov_ctas * nn * sizeof(double), h->stream);
     }
+    if (e == cudaSuccess && p->lambda_cells) {
+        // a rod of several materials: the material table in the state's
+        // precision, T_ref and the perturbation widths in FP64
+        Materials m;
+        std::string m_msg;
+        build_materials(*p, m, m_msg);           // validated by convert
+        h->var = true;
+        h->ref_cells = m.ref;
+        h->cap_cells = m.cap;
+        const int N = h->prob.n[0];
+        if (h->precision == SHE_FP64) {
+            std::vector<she::Coef1D<double>> tab((size_t)N + 1);
+            for (int k = 0; k <= N; ++k)
+                tab[(size_t)k] = {m.a[(size_t)k], m.sh[(size_t)k], k < N ? 1.0 / m.cap[(size_t)k] : 0.0,
+                                  k < N ? m.ref[(size_t)k] : 0.0};
+            e = cudaMalloc(&h->d_coef, tab.size() * sizeof(tab[0]));
+            if (e == cudaSuccess) e = cudaMemcpy(h->d_coef, tab.data(), tab.size() * sizeof(tab[0]), cudaMemcpyHostToDevice);
+        } else {
+            std::vector<she::Coef1D<float>> tab((size_t)N + 1);
+            for (int k = 0; k <= N; ++k)
+                tab[(size_t)k] = {(float)m.a[(size_t)k], (float)m.sh[(size_t)k],
+                                  k < N ? (float)(1.0 / m.cap[(size_t)k]) : 0.0f, k < N ? (float)m.ref[(size_t)k] : 0.0f};
+            e = cudaMalloc(&h->d_coef, tab.size() * sizeof(tab[0]));
+            if (e == cudaSuccess) e = cudaMemcpy(h->d_coef, tab.data(), tab.size() * sizeof(tab[0]), cudaMemcpyHostToDevice);
+        }
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_ref, (size_t)N * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_sigma, 2 * (size_t)N * sizeof(double));
+        if (e == cudaSuccess) e = cudaMemcpy(h->d_ref, m.ref.data(), (size_t)N * sizeof(double), cudaMemcpyHostToDevice);
+        std::vector<double> sc(m.sigma);
+        sc.insert(sc.end(), m.cap.begin(), m.cap.end());
+        if (e == cudaSuccess) e = cudaMemcpy(h->d_sigma, sc.data(), sc.size() * sizeof(double), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_acc1, 0, nstate * sizeof(double), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_acc2, 0, nstate * sizeof(double), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flags, 0, sizeof(int), h->stream);
@@ -457,10 +594,10 @@ she_status she_init_batch(const she_params* p, int64_t count, she_handle** out)
             q.precision != SHE_FP32 || q.stats_interval != p[0].stats_interval || q.stats_interval < 1 ||
             q.relax_steps != p[0].relax_steps || q.stochastic != p[0].stochastic ||
             q.perturb_ic != p[0].perturb_ic || q.kernel != SHE_KERNEL_AUTO || q.want_cov || q.want_sk ||
-            q.scheme != SHE_FE || q.tc_lags != 0 || pr.n[0] > 2048) {
+            q.scheme != SHE_FE || q.tc_lags != 0 || pr.n[0] > 2048 || q.lambda_cells || q.rho_cv_cells) {
             st = SHE_ERR_INVALID_ARG;
-            msg = "she_init_batch: instances must be 1D, FP32, one realization each, N <= 2048, and share "
-                  "equation, boundary, stats_interval, relax_steps, stochastic and perturb_ic";
+            msg = "she_init_batch: instances must be uniform 1D rods, FP32, one realization each, N <= 2048, "
+                  "and share equation, boundary, stats_interval, relax_steps, stochastic and perturb_ic";
             break;
         }
         she::InstanceDesc& d = desc[(size_t)i];
@@ -652,6 +789,7 @@ she_status she_stats(she_handle* hh, she_stats_out* out)
         double ref_i = dir ? h->prob.wall_lo + (h->prob.wall_hi - h->prob.wall_lo) * ((double)i + 0.5) / (double)cells
                            : h->prob.wall_lo;
         if (h->is_batch) ref_i = batch_ref(*h, i);
+        if (h->var) ref_i = h->ref_cells[(size_t)i];
         const double mu_i = s1 / n;
         mu[(size_t)i] = mu_i;
         ref[(size_t)i] = ref_i;
@@ -933,9 +1071,10 @@ she_status she_step_plain_noalloc(const she_params* p, const double* T_in, doubl
         return st;
     }
     if (p->dim != 1 || p->realizations < 1 || p->precision != SHE_FP64 || step > (uint64_t)0xffffffffu ||
-        p->scheme != SHE_FE ||
+        p->scheme != SHE_FE || p->lambda_cells || p->rho_cv_cells ||
         p->stream_offset < 0 || (int64_t)p->stream_offset + p->realizations > ((int64_t)1 << 32)) {
-        fprintf(stderr, "she_step_plain_noalloc: needs dim 1, FP64, forward Euler, realizations >= 1, step < 2^32\n");
+        fprintf(stderr, "she_step_plain_noalloc: needs a uniform 1D rod, FP64, forward Euler, realizations >= 1, "
+                        "step < 2^32\n");
         return SHE_ERR_INVALID_ARG;
     }
     const int64_t faces = p->realizations * (int64_t)(prob.n[0] + 1);

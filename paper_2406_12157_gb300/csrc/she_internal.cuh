@@ -33,6 +33,18 @@ struct Problem {
     int scheme = SHE_FE;  // SHE_FE or SHE_PC
 };
 
+// One entry of the material table of a rod of several materials (the iron /
+// aluminium exercise, Sec. 6), index k = 0..N: `a` the conductance number
+// lambda_f dt / dx^2 of the low face of cell k (k = N: the high wall, or
+// face 0 again on a periodic rod), `sh` half the noise amplitude per unit
+// face temperature of that face, sqrt(2 k_B a / dV) / 2 (so that
+// G_f = sh (T_l + T_r) N_f), `ic` = 1 / (rho c_V) of cell k (0 for k = N),
+// `ref` = T_ref of cell k (the exact steady profile).
+template <typename Real>
+struct __align__(4 * sizeof(Real)) Coef1D {
+    Real a, sh, ic, ref;
+};
+
 // Arguments of the 1D step kernels (one realization per warp).
 template <typename Real>
 struct Step1DArgs {
@@ -59,6 +71,7 @@ struct Step1DArgs {
                           // back past it (the trajectory before it is another one)
     Real* tc_ring;        // [R][tc_lags][N] the last tc_lags samples of delta (sample s in slot s % L)
     double* tc_acc;       // [R][tc_lags][N] sum of delta_i(s) delta_i(s - l)
+    const Coef1D<Real>* coef;   // [N + 1] material table of a rod of several materials (else null)
 };
 
 // Arguments of the 2D step kernel (one step per launch).
@@ -191,6 +204,13 @@ struct Handle {
     int tc_lags = 0;               // time correlation lags (0: off)
     int64_t tc_base = 0;           // samples_per_real at the last set_state (0 after a reset)
     std::vector<int64_t> tc_pairs; // [tc_lags] sample pairs per realization at each lag
+    // rod of several materials (lambda_cells / rho_cv_cells given at init)
+    bool var = false;
+    void* d_coef = nullptr;        // [N + 1] Coef1D of the state's precision
+    double* d_ref = nullptr;       // [N] T_ref (FP64)
+    double* d_sigma = nullptr;     // [N] initial perturbation sd per cell
+    std::vector<double> ref_cells; // host copy of T_ref
+    std::vector<double> cap_cells; // rho c_V per cell (the energy weights of a periodic rod)
     void* d_tc_ring = nullptr;     // [R][tc_lags][N] of the state's type
     double* d_tc_acc = nullptr;    // [R][tc_lags][N]
     double* d_tc_red = nullptr;    // [tc_lags][N] reduction over the realizations
@@ -284,10 +304,10 @@ inline void prof_close(Handle& h)
 }
 
 // Launchers (return cudaSuccess or the launch error).
-// The fused 1D kernel of one (precision, wall, equation, scheme) variant at
+// The fused 1D kernel of one (precision, wall, equation, scheme, material table) variant at
 // the given layout (cells per lane * 100 + lanes per realization); defined
 // in step1d_kernel.cuh, instantiated by step1d_inst.cu.
-template <typename Real, bool DIR, bool SP, bool PC>
+template <typename Real, bool DIR, bool SP, bool PC, bool VAR>
 cudaError_t launch_step1d_variant(const Step1DArgs<Real>& a, int layout, cudaStream_t st);
 cudaError_t launch_init_state(Handle& h);
 cudaError_t launch_step1d(Handle& h, uint32_t step0, int nsteps);

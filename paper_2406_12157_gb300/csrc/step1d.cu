@@ -98,24 +98,31 @@ static cudaError_t launch_fused(Handle& h, uint32_t step0, int nsteps)
     a.tc_base = (long long)h.tc_base;
     a.tc_ring = (Real*)h.d_tc_ring;
     a.tc_acc = h.d_tc_acc;
+    a.coef = (const Coef1D<Real>*)h.d_coef;
     const bool dir = h.prob.bc == SHE_DIRICHLET;
     const bool sp = h.prob.equation == SHE_SPECIES;
     if (h.prob.scheme == SHE_PC) {
         const int layout = pick_layout_pc(a.N);
+        if (h.var)         // a rod of several materials (heat)
+            return dir ? launch_step1d_variant<Real, true, false, true, true>(a, layout, h.stream)
+                       : launch_step1d_variant<Real, false, false, true, true>(a, layout, h.stream);
         if (dir) {
-            if (sp) return launch_step1d_variant<Real, true, true, true>(a, layout, h.stream);
-            return launch_step1d_variant<Real, true, false, true>(a, layout, h.stream);
+            if (sp) return launch_step1d_variant<Real, true, true, true, false>(a, layout, h.stream);
+            return launch_step1d_variant<Real, true, false, true, false>(a, layout, h.stream);
         }
-        if (sp) return launch_step1d_variant<Real, false, true, true>(a, layout, h.stream);
-        return launch_step1d_variant<Real, false, false, true>(a, layout, h.stream);
+        if (sp) return launch_step1d_variant<Real, false, true, true, false>(a, layout, h.stream);
+        return launch_step1d_variant<Real, false, false, true, false>(a, layout, h.stream);
     }
     const int layout = pick_layout(a.N);
+    if (h.var)
+        return dir ? launch_step1d_variant<Real, true, false, false, true>(a, layout, h.stream)
+                   : launch_step1d_variant<Real, false, false, false, true>(a, layout, h.stream);
     if (dir) {
-        if (sp) return launch_step1d_variant<Real, true, true, false>(a, layout, h.stream);
-        return launch_step1d_variant<Real, true, false, false>(a, layout, h.stream);
+        if (sp) return launch_step1d_variant<Real, true, true, false, false>(a, layout, h.stream);
+        return launch_step1d_variant<Real, true, false, false, false>(a, layout, h.stream);
     }
-    if (sp) return launch_step1d_variant<Real, false, true, false>(a, layout, h.stream);
-    return launch_step1d_variant<Real, false, false, false>(a, layout, h.stream);
+    if (sp) return launch_step1d_variant<Real, false, true, false, false>(a, layout, h.stream);
+    return launch_step1d_variant<Real, false, false, false, false>(a, layout, h.stream);
 }
 
 cudaError_t launch_step1d(Handle& h, uint32_t step0, int nsteps)
@@ -265,14 +272,16 @@ cudaError_t launch_step1d_plain(Handle& h, uint32_t step0, int nsteps)
 // tensor-core partials ([j][i]; symmetric), one partial.
 
 __global__ void __launch_bounds__(256) k_cov_fp64(const double* __restrict__ T, int R, int N, double wlo,
-                                                  double dref, int dir, double* __restrict__ C)
+                                                  double dref, int dir, const double* __restrict__ ref,
+                                                  double* __restrict__ C)
 {
     __shared__ double si[16][17], sj[16][17];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int i = blockIdx.y * 16 + ty, j = blockIdx.x * 16 + tx;
     const int li = blockIdx.y * 16 + tx, lj = blockIdx.x * 16 + tx;   // columns this thread loads
-    const double refi = dir ? fma(dref, (double)li + 0.5, wlo) : wlo;
-    const double refj = dir ? fma(dref, (double)lj + 0.5, wlo) : wlo;
+    // T_ref: a rod of several materials passes its profile (ref), else linear / uniform
+    const double refi = ref ? (li < N ? ref[li] : 0.0) : dir ? fma(dref, (double)li + 0.5, wlo) : wlo;
+    const double refj = ref ? (lj < N ? ref[lj] : 0.0) : dir ? fma(dref, (double)lj + 0.5, wlo) : wlo;
     double acc = 0.0;
     for (int r0 = 0; r0 < R; r0 += 16) {
         const int r = r0 + ty;
@@ -293,7 +302,7 @@ cudaError_t launch_cov_fp64(Handle& h)
     const double dref = dir ? (h.prob.wall_hi - h.prob.wall_lo) / (double)N : 0.0;
     const dim3 grid((unsigned)((N + 15) / 16), (unsigned)((N + 15) / 16)), block(16, 16);
     k_cov_fp64<<<grid, block, 0, h.stream>>>((const double*)h.d_state, (int)h.R, N, h.prob.wall_lo, dref,
-                                             dir ? 1 : 0, h.d_cov_partial);
+                                             dir ? 1 : 0, h.var ? h.d_ref : nullptr, h.d_cov_partial);
     h.launches += 1;
     return cudaGetLastError();
 }

@@ -86,7 +86,9 @@ __device__ __noinline__ int cov_mma_issue(unsigned char* base, uint64_t* full, u
     return ns;
 }
 
-template <int C, int LPR, bool DIR, bool SPECIES, bool RAGGED, bool PC>
+// VAR: a rod of several materials; its material table (N + 1 entries) is
+// copied into shared memory after the moment partials.
+template <int C, int LPR, bool DIR, bool SPECIES, bool RAGGED, bool PC, bool VAR>
 __global__ void __launch_bounds__(32 * LPR, 1)
 k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
 {
@@ -103,6 +105,7 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
     uint32_t* tslot = reinterpret_cast<uint32_t*>(empty + 2);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
     float* mom = reinterpret_cast<float*>(base + 4 * kOpBytes + 64);
+    Coef1D<float>* tab = reinterpret_cast<Coef1D<float>*>(mom + LPR * 2 * C * 32);
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -128,6 +131,8 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
     // zero both operand stages (rows of absent realizations stay zero)
     for (int i = threadIdx.x; i < 4 * kOpBytes / 16; i += blockDim.x)
         reinterpret_cast<uint4*>(base)[i] = make_uint4(0u, 0u, 0u, 0u);
+    if constexpr (VAR)
+        for (int k = threadIdx.x; k <= a.N; k += blockDim.x) tab[k] = a.coef[k];
 
     const int N = a.N;
     const int Mh = (N + 127) / 128;
@@ -154,8 +159,9 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
     fence_after_sync();
     const uint32_t tbase = use_tc ? *tslot : 0u;
 
-    Row1D<float, C, LPR, DIR, SPECIES, RAGGED, false> rowst;   // keys in registers: measured faster here
+    Row1D<float, C, LPR, DIR, SPECIES, RAGGED, false, VAR> rowst;   // keys in registers: measured faster here
     rowst.init(a, sl, rho);
+    if constexpr (VAR) rowst.init_var(tab);
     const int i0 = sl * C;
     float* row = a.state + (size_t)rho * (size_t)N;
     float T[C];
@@ -207,7 +213,8 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
 #pragma unroll
                 for (int t = 0; t < G8; ++t) {
                     const int j = j0 + t;
-                    const float ref = DIR ? fmaf(dref, (float)(i0 + j) + 0.5f, wlo) : wlo;
+                    const float ref = VAR ? tab[i0 + j < N ? i0 + j : N].ref
+                                          : DIR ? fmaf(dref, (float)(i0 + j) + 0.5f, wlo) : wlo;
                     d[t] = T[j] - ref;
                     sm1[j * 32] += d[t];
                     sm2[j * 32] = fmaf(d[t], d[t], sm2[j * 32]);
@@ -308,16 +315,16 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
     }
 }
 
-template <int C, int LPR, bool DIR, bool SP, bool PC>
+template <int C, int LPR, bool DIR, bool SP, bool PC, bool VAR>
 static cudaError_t launch_cov_layout(const Step1DArgs<float>& a, const CovArgs& c, int grid, cudaStream_t st)
 {
-    const int smem = cov_smem_bytes<C>(LPR);
+    const int smem = cov_smem_bytes<C>(LPR) + (VAR ? (a.N + 1) * (int)sizeof(Coef1D<float>) : 0);
     if (a.N == C * LPR) {
-        auto k = k_step1d_cov<C, LPR, DIR, SP, false, PC>;
+        auto k = k_step1d_cov<C, LPR, DIR, SP, false, PC, VAR>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         k<<<grid, 32 * LPR, smem, st>>>(a, c);
     } else {
-        auto k = k_step1d_cov<C, LPR, DIR, SP, true, PC>;
+        auto k = k_step1d_cov<C, LPR, DIR, SP, true, PC, VAR>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         k<<<grid, 32 * LPR, smem, st>>>(a, c);
     }
@@ -344,22 +351,29 @@ static int cov_slots_per_cta(int N, bool pc)
     return (lpr - 1) * (32 / lpr);
 }
 
-template <bool DIR, bool SP, bool PC>
+template <bool DIR, bool SP, bool PC, bool VAR>
 static cudaError_t launch_cov_ds(const Step1DArgs<float>& a, const CovArgs& c, int grid, cudaStream_t st)
 {
     const int N = a.N;
-    if (N <= 16) return launch_cov_layout<4, 4, DIR, SP, PC>(a, c, grid, st);
-    if (N <= 32) return launch_cov_layout<4, 8, DIR, SP, PC>(a, c, grid, st);
-    if (N <= 64) return launch_cov_layout<4, 16, DIR, SP, PC>(a, c, grid, st);
-    if (N <= 128) return launch_cov_layout<4, 32, DIR, SP, PC>(a, c, grid, st);
-    return launch_cov_layout<16, 16, DIR, SP, PC>(a, c, grid, st);
+    if (N <= 16) return launch_cov_layout<4, 4, DIR, SP, PC, VAR>(a, c, grid, st);
+    if (N <= 32) return launch_cov_layout<4, 8, DIR, SP, PC, VAR>(a, c, grid, st);
+    if (N <= 64) return launch_cov_layout<4, 16, DIR, SP, PC, VAR>(a, c, grid, st);
+    if (N <= 128) return launch_cov_layout<4, 32, DIR, SP, PC, VAR>(a, c, grid, st);
+    return launch_cov_layout<16, 16, DIR, SP, PC, VAR>(a, c, grid, st);
 }
 
 template <bool DIR, bool SP>
-static cudaError_t launch_cov_scheme(const Step1DArgs<float>& a, const CovArgs& c, int grid, bool pc, cudaStream_t st)
+static cudaError_t launch_cov_scheme(const Step1DArgs<float>& a, const CovArgs& c, int grid, bool pc, bool var,
+                                     cudaStream_t st)
 {
-    if (pc) return launch_cov_ds<DIR, SP, true>(a, c, grid, st);
-    return launch_cov_ds<DIR, SP, false>(a, c, grid, st);
+    if constexpr (!SP) {
+        if (var) {        // a rod of several materials (heat)
+            if (pc) return launch_cov_ds<DIR, SP, true, true>(a, c, grid, st);
+            return launch_cov_ds<DIR, SP, false, true>(a, c, grid, st);
+        }
+    }
+    if (pc) return launch_cov_ds<DIR, SP, true, false>(a, c, grid, st);
+    return launch_cov_ds<DIR, SP, false, false>(a, c, grid, st);
 }
 
 cudaError_t launch_step1d_cov(Handle& h, uint32_t step0, int nsteps, bool has_samples)
@@ -384,6 +398,7 @@ cudaError_t launch_step1d_cov(Handle& h, uint32_t step0, int nsteps, bool has_sa
     a.relax = (long long)h.relax;
     a.stream0 = h.stream0;
     a.stochastic = h.stochastic;
+    a.coef = (const Coef1D<float>*)h.d_coef;
     const bool dir = h.prob.bc == SHE_DIRICHLET;
     const bool sp = h.prob.equation == SHE_SPECIES;
     // waves of at most (stepper warps x realizations per warp) per CTA
@@ -399,11 +414,11 @@ cudaError_t launch_step1d_cov(Handle& h, uint32_t step0, int nsteps, bool has_sa
         const int grid = (int)std::min<int64_t>(G, c.r_count);
         cudaError_t e;
         if (dir)
-            e = sp ? launch_cov_scheme<true, true>(a, c, grid, pc, h.stream)
-                   : launch_cov_scheme<true, false>(a, c, grid, pc, h.stream);
+            e = sp ? launch_cov_scheme<true, true>(a, c, grid, pc, false, h.stream)
+                   : launch_cov_scheme<true, false>(a, c, grid, pc, h.var, h.stream);
         else
-            e = sp ? launch_cov_scheme<false, true>(a, c, grid, pc, h.stream)
-                   : launch_cov_scheme<false, false>(a, c, grid, pc, h.stream);
+            e = sp ? launch_cov_scheme<false, true>(a, c, grid, pc, false, h.stream)
+                   : launch_cov_scheme<false, false>(a, c, grid, pc, h.var, h.stream);
         h.launches += 1;
         if (e != cudaSuccess) return e;
     }

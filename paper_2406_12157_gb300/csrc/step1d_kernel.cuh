@@ -24,7 +24,9 @@ namespace she {
 template <typename Real, int C>
 constexpr int step1d_smem_per_warp() { return 2 * C * 32 * (int)sizeof(Real); }
 
-template <typename Real, int C, int LPR, bool DIR, bool SPECIES, bool RAGGED, int MINB, bool PC>
+// VAR: a rod of several materials; its material table (N + 1 entries) is
+// copied into shared memory after the moment partials.
+template <typename Real, int C, int LPR, bool DIR, bool SPECIES, bool RAGGED, int MINB, bool PC, bool VAR>
 __global__ void __launch_bounds__(kWarpsPerBlock1D * 32, MINB)
 k_step1d(const __grid_constant__ Step1DArgs<Real> a)
 {
@@ -34,6 +36,13 @@ k_step1d(const __grid_constant__ Step1DArgs<Real> a)
     const int lane = threadIdx.x & 31;
     const int sl = lane % LPR;
     const int warp = blockIdx.x * kWarpsPerBlock1D + (threadIdx.x >> 5);
+    Coef1D<Real>* tab = reinterpret_cast<Coef1D<Real>*>(
+        smem_raw + (size_t)kWarpsPerBlock1D * step1d_smem_per_warp<Real, C>());
+    if constexpr (VAR) {
+        // every thread of the block helps, before any warp leaves
+        for (int k = threadIdx.x; k <= a.N; k += blockDim.x) tab[k] = a.coef[k];
+        __syncthreads();
+    }
     if (warp * RPW >= a.R) return;  // warp-uniform
     const int rho_raw = warp * RPW + lane / LPR;
     const bool active = rho_raw < a.R;
@@ -42,8 +51,9 @@ k_step1d(const __grid_constant__ Step1DArgs<Real> a)
     Real* sm1 = reinterpret_cast<Real*>(smem_raw) + (threadIdx.x >> 5) * (2 * C * 32) + lane;
     Real* sm2 = sm1 + C * 32;
 
-    Row1D<Real, C, LPR, DIR, SPECIES, RAGGED> rowst;
+    Row1D<Real, C, LPR, DIR, SPECIES, RAGGED, true, VAR> rowst;
     rowst.init(a, sl, rho);
+    if constexpr (VAR) rowst.init_var(tab);
     const int N = a.N;
     const int i0 = sl * C;
     Real* row = a.state + (size_t)rho * (size_t)N;
@@ -81,7 +91,7 @@ k_step1d(const __grid_constant__ Step1DArgs<Real> a)
                 for (int j = 0; j < C; ++j) {
                     const int i = i0 + j;
                     if (RAGGED && i >= N) continue;
-                    const Real ref = DIR ? fma(dref, Real(i0 + j) + half, wlo) : wlo;
+                    const Real ref = VAR ? tab[i].ref : DIR ? fma(dref, Real(i0 + j) + half, wlo) : wlo;
                     const Real d = T[j] - ref;
                     ring[(size_t)slot * N + i] = d;
                     atomicAdd(&acc[i], (double)(d * d));
@@ -94,7 +104,8 @@ k_step1d(const __grid_constant__ Step1DArgs<Real> a)
             ++nsamp;
 #pragma unroll
             for (int j = 0; j < C; ++j) {
-                const Real ref = DIR ? fma(dref, Real(i0 + j) + half, wlo) : wlo;
+                const Real ref = VAR ? tab[i0 + j < N ? i0 + j : N].ref
+                                     : DIR ? fma(dref, Real(i0 + j) + half, wlo) : wlo;
                 const Real d = T[j] - ref;
                 sm1[j * 32] += d;
                 sm2[j * 32] = fma(d, d, sm2[j * 32]);
@@ -128,20 +139,21 @@ k_step1d(const __grid_constant__ Step1DArgs<Real> a)
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.flags, 1);
 }
 
-template <typename Real, int C, int LPR, bool DIR, bool SP, int MINB, bool PC = false>
+template <typename Real, int C, int LPR, bool DIR, bool SP, int MINB, bool PC = false, bool VAR = false>
 inline cudaError_t launch_layout(const Step1DArgs<Real>& a, cudaStream_t st)
 {
     constexpr int RPW = 32 / LPR;
     const int warps = (a.R + RPW - 1) / RPW;
     const dim3 block(kWarpsPerBlock1D * 32);
     const dim3 grid((warps + kWarpsPerBlock1D - 1) / kWarpsPerBlock1D);
-    const int smem = kWarpsPerBlock1D * step1d_smem_per_warp<Real, C>();
+    const int smem = kWarpsPerBlock1D * step1d_smem_per_warp<Real, C>() +
+                     (VAR ? (a.N + 1) * (int)sizeof(Coef1D<Real>) : 0);
     if (a.N == LPR * C) {
-        auto k = k_step1d<Real, C, LPR, DIR, SP, false, MINB, PC>;
+        auto k = k_step1d<Real, C, LPR, DIR, SP, false, MINB, PC, VAR>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         k<<<grid, block, smem, st>>>(a);
     } else {
-        auto k = k_step1d<Real, C, LPR, DIR, SP, true, MINB, PC>;
+        auto k = k_step1d<Real, C, LPR, DIR, SP, true, MINB, PC, VAR>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         k<<<grid, block, smem, st>>>(a);
     }
@@ -151,54 +163,55 @@ inline cudaError_t launch_layout(const Step1DArgs<Real>& a, cudaStream_t st)
 // Register budget per layout (min resident blocks of 128 threads): enough
 // warps per SM to hold the whole 4096-realization ensemble in one wave for
 // the 256-cell rows, without starving the compiler of registers for ILP.
-template <typename Real, int C, int LPR, bool DIR, bool SP, int MINB32>
+template <typename Real, int C, int LPR, bool DIR, bool SP, int MINB32, bool VAR = false>
 inline cudaError_t launch_layout_r(const Step1DArgs<Real>& a, cudaStream_t st)
 {
     constexpr int MINB = sizeof(Real) == 4 ? MINB32 : (MINB32 / 2 > 0 ? MINB32 / 2 : 1);
-    return launch_layout<Real, C, LPR, DIR, SP, MINB>(a, st);
+    return launch_layout<Real, C, LPR, DIR, SP, MINB, false, VAR>(a, st);
 }
 
-template <typename Real, bool DIR, bool SP>
+template <typename Real, bool DIR, bool SP, bool VAR = false>
 inline cudaError_t launch_ds(const Step1DArgs<Real>& a, int layout, cudaStream_t st)
 {
     // layout = cells per lane * 100 + lanes per realization (see pick_layout)
     switch (layout) {
-    case 404: return launch_layout_r<Real, 4, 4, DIR, SP, 8>(a, st);
-    case 408: return launch_layout_r<Real, 4, 8, DIR, SP, 8>(a, st);
-    case 416: return launch_layout_r<Real, 4, 16, DIR, SP, 8>(a, st);
-    case 432: return launch_layout_r<Real, 4, 32, DIR, SP, 8>(a, st);
-    case 832: return launch_layout_r<Real, 8, 32, DIR, SP, 7>(a, st);
-    case 1616: return launch_layout_r<Real, 16, 16, DIR, SP, 4>(a, st);
-    case 1632: return launch_layout_r<Real, 16, 32, DIR, SP, 4>(a, st);
-    case 3208: return launch_layout_r<Real, 32, 8, DIR, SP, 2>(a, st);
-    case 3232: return launch_layout_r<Real, 32, 32, DIR, SP, 1>(a, st);
+    case 404: return launch_layout_r<Real, 4, 4, DIR, SP, 8, VAR>(a, st);
+    case 408: return launch_layout_r<Real, 4, 8, DIR, SP, 8, VAR>(a, st);
+    case 416: return launch_layout_r<Real, 4, 16, DIR, SP, 8, VAR>(a, st);
+    case 432: return launch_layout_r<Real, 4, 32, DIR, SP, 8, VAR>(a, st);
+    case 832: return launch_layout_r<Real, 8, 32, DIR, SP, 7, VAR>(a, st);
+    case 1616: return launch_layout_r<Real, 16, 16, DIR, SP, 4, VAR>(a, st);
+    case 1632: return launch_layout_r<Real, 16, 32, DIR, SP, 4, VAR>(a, st);
+    case 3208: return launch_layout_r<Real, 32, 8, DIR, SP, 2, VAR>(a, st);
+    case 3232: return launch_layout_r<Real, 32, 32, DIR, SP, 1, VAR>(a, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
-template <typename Real, bool DIR, bool SP>
+template <typename Real, bool DIR, bool SP, bool VAR = false>
 inline cudaError_t launch_ds_pc(const Step1DArgs<Real>& a, int layout, cudaStream_t st)
 {
     constexpr bool F = sizeof(Real) == 4;
     switch (layout) {
-    case 404: return launch_layout<Real, 4, 4, DIR, SP, F ? 8 : 4, true>(a, st);
-    case 408: return launch_layout<Real, 4, 8, DIR, SP, F ? 8 : 4, true>(a, st);
-    case 416: return launch_layout<Real, 4, 16, DIR, SP, F ? 8 : 4, true>(a, st);
-    case 432: return launch_layout<Real, 4, 32, DIR, SP, F ? 8 : 4, true>(a, st);
-    case 832: return launch_layout<Real, 8, 32, DIR, SP, F ? 6 : 3, true>(a, st);
-    case 1632: return launch_layout<Real, 16, 32, DIR, SP, F ? 3 : 2, true>(a, st);
+    case 404: return launch_layout<Real, 4, 4, DIR, SP, F ? 8 : 4, true, VAR>(a, st);
+    case 408: return launch_layout<Real, 4, 8, DIR, SP, F ? 8 : 4, true, VAR>(a, st);
+    case 416: return launch_layout<Real, 4, 16, DIR, SP, F ? 8 : 4, true, VAR>(a, st);
+    case 432: return launch_layout<Real, 4, 32, DIR, SP, F ? 8 : 4, true, VAR>(a, st);
+    case 832: return launch_layout<Real, 8, 32, DIR, SP, F ? 6 : 3, true, VAR>(a, st);
+    case 1632: return launch_layout<Real, 16, 32, DIR, SP, F ? 3 : 2, true, VAR>(a, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
 // The forward-Euler (PC = false) or predictor-corrector layouts of one
-// (precision, wall, equation) combination; layout = cells per lane * 100 +
-// lanes per realization.
-template <typename Real, bool DIR, bool SP, bool PC>
+// (precision, wall, equation) combination, with the material table of a rod
+// of several materials (VAR); layout = cells per lane * 100 + lanes per
+// realization.
+template <typename Real, bool DIR, bool SP, bool PC, bool VAR>
 cudaError_t launch_step1d_variant(const Step1DArgs<Real>& a, int layout, cudaStream_t st)
 {
-    if constexpr (PC) return launch_ds_pc<Real, DIR, SP>(a, layout, st);
-    else return launch_ds<Real, DIR, SP>(a, layout, st);
+    if constexpr (PC) return launch_ds_pc<Real, DIR, SP, VAR>(a, layout, st);
+    else return launch_ds<Real, DIR, SP, VAR>(a, layout, st);
 }
 
 }  // namespace she
