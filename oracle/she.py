@@ -18,7 +18,7 @@ from . import build as _build
 
 HEAT, SPECIES = 0, 1
 PERIODIC, DIRICHLET = 0, 1
-FE, PC = 0, 1
+FE, PC, BE, CN = 0, 1, 2, 3
 
 
 class OrcParams(ctypes.Structure):
@@ -145,7 +145,7 @@ def to_params(prob):
     p.stochastic = int(prob.get("stochastic", 1))
     p.perturb_ic = int(prob.get("perturb_ic", 1))
     p.stats_interval = int(prob.get("stats_interval", 10))
-    p.scheme = PC if prob.get("scheme", "fe") == "pc" else FE
+    p.scheme = {"fe": FE, "pc": PC, "be": BE, "cn": CN}[prob.get("scheme", "fe")]
     p.relax_steps = int(prob.get("relax_steps", 0))
     p.want_cov = int(prob.get("want_cov", 0))
     p.want_sk = int(prob.get("want_sk", 0))
@@ -209,8 +209,10 @@ def initial_state(prob, stream):
 
 
 def step(prob, state, step_index, stream):
-    """One step of one realization from `state`: forward Euler (Eq. (3.3)) or,
-    with ``prob["scheme"] == "pc"``, the predictor-corrector scheme of Sec. 3."""
+    """One step of one realization from `state`: forward Euler (Eq. (3.3)),
+    the predictor-corrector scheme of Sec. 3 (``prob["scheme"] == "pc"``), or
+    backward Euler / Crank-Nicolson ("be" / "cn", the implicit exercise of
+    Sec. 6)."""
     p = to_params(prob)
     T = np.ascontiguousarray(state, dtype=np.float64)
     out = np.zeros_like(T)

@@ -50,6 +50,16 @@
  *   th_a = 2 pi U(u1), R_b = sqrt(-2 ln U(u2)), th_b = 2 pi U(u3);
  *   slots 0..3 = R_a cos th_a, R_a sin th_a, R_b cos th_b, R_b sin th_b.
  *
+ *   - or one step of an implicit scheme (the exercise on backward Euler and
+ *     Crank-Nicolson, Sec. 6), 1D: the diffusion term implicit with weight
+ *     theta (1 backward Euler, 1/2 Crank-Nicolson) and the stochastic flux
+ *     explicit from the state at the start of the step (noise constant over
+ *     the step, as in the predictor-corrector scheme):
+ *       (I - theta r L) T' = T + (1 - theta) r L T + r b + div G(T),
+ *     L the second-difference matrix with the Dirichlet ghost of Eq. (3.8)
+ *     (b its wall terms), solved by the Thomas algorithm (tridiagonal
+ *     elimination; periodic rods: its cyclic form by the Sherman-Morrison
+ *     formula);
  *   - a rod of two (or more) materials (the iron / aluminium exercise of
  *     Sec. 6): per-cell conductivity lambda_i and heat capacity rho c_V,i in
  *     the conservation form of the SHE, rho c_V dT/dt = div(lambda grad T +
@@ -82,6 +92,8 @@
 
 #define ORC_FE 0
 #define ORC_PC 1
+#define ORC_BE 2
+#define ORC_CN 3
 
 #define ORC_TAG_STEP 0u
 #define ORC_TAG_IC 1u
@@ -429,6 +441,89 @@ static void orc_increment(const orc_params* p, const double* T, orc_work* w)
     else orc_increment_nd(p, T, w->Z, w->G, w->inc);
 }
 
+/* Solve the tridiagonal system sub[i] x[i-1] + dia[i] x[i] + sup[i] x[i+1] =
+ * rhs[i], i = 0..n-1 (sub[0], sup[n-1] unused) by the Thomas algorithm
+ * (forward elimination, back substitution); work: n doubles. */
+static void orc_thomas(int n, const double* sub, const double* dia, const double* sup, const double* rhs,
+                       double* x, double* work)
+{
+    double* cp = work;
+    double piv = dia[0];
+    cp[0] = sup[0] / piv;
+    x[0] = rhs[0] / piv;
+    for (int i = 1; i < n; ++i) {
+        piv = dia[i] - sub[i] * cp[i - 1];
+        cp[i] = (i < n - 1) ? sup[i] / piv : 0.0;
+        x[i] = (rhs[i] - sub[i] * x[i - 1]) / piv;
+    }
+    for (int i = n - 2; i >= 0; --i) x[i] -= cp[i] * x[i + 1];
+}
+
+/* One step of the implicit scheme with weight theta (1D): the right-hand
+ * side T + (1 - theta) r L T + r b + (G_{i+1} - G_i) with the face fluxes of
+ * the state at the start of the step, then (I - theta r L) T' = rhs.  A
+ * periodic rod's matrix is cyclic: with A = A' + u v^T (u = (g, 0, .., 0, c)^T,
+ * v = (1, 0, .., 0, c/g)^T, g = -dia[0], c the corner entries -theta r) the
+ * Sherman-Morrison formula gives T' = y - (v.y) / (1 + v.z) z, A' y = rhs,
+ * A' z = u, A' the tridiagonal part with dia[0] - g and dia[n-1] - c^2/g. */
+static void orc_implicit_1d(const orc_params* p, double theta, const double* T, const double* Z, double* G,
+                            double* Tn)
+{
+    const int n = p->n[0];
+    const double r = p->r;
+    const int dir = (p->bc == ORC_DIRICHLET);
+    double* rhs = (double*)calloc((size_t)n * 7, sizeof(double));
+    double* sub = rhs + n;
+    double* dia = sub + n;
+    double* sup = dia + n;
+    double* y = sup + n;
+    double* z = y + n;
+    double* work = z + n;
+    /* explicit part: the stochastic face fluxes of T (as forward Euler) */
+    for (int f = 0; f < n; ++f) {
+        double tface;
+        if (f == 0) tface = dir ? p->wall_lo : 0.5 * (T[n - 1] + T[0]);
+        else tface = 0.5 * (T[f - 1] + T[f]);
+        G[f] = orc_flux_amp(p, tface) * Z[f];
+    }
+    G[n] = dir ? orc_flux_amp(p, p->wall_hi) * Z[n] : G[0];
+    for (int i = 0; i < n; ++i) {
+        double lap, wall = 0.0;
+        if (dir && i == 0) {
+            lap = T[1] - 3.0 * T[0];
+            wall = 2.0 * p->wall_lo;
+        } else if (dir && i == n - 1) {
+            lap = T[n - 2] - 3.0 * T[n - 1];
+            wall = 2.0 * p->wall_hi;
+        } else {
+            lap = T[(i + 1) % n] - 2.0 * T[i] + T[(i - 1 + n) % n];
+        }
+        rhs[i] = T[i] + (1.0 - theta) * r * lap + r * wall + (G[i + 1] - G[i]);
+        sub[i] = -theta * r;
+        sup[i] = -theta * r;
+        dia[i] = 1.0 + 2.0 * theta * r;
+    }
+    if (dir) {
+        dia[0] = 1.0 + 3.0 * theta * r;
+        dia[n - 1] = 1.0 + 3.0 * theta * r;
+        orc_thomas(n, sub, dia, sup, rhs, Tn, work);
+    } else {
+        const double c = -theta * r;            /* the corner entries A[0][n-1] = A[n-1][0] */
+        const double g = -dia[0];
+        dia[0] -= g;
+        dia[n - 1] -= c * c / g;
+        orc_thomas(n, sub, dia, sup, rhs, y, work);
+        for (int i = 0; i < n; ++i) rhs[i] = 0.0;
+        rhs[0] = g;
+        rhs[n - 1] = c;
+        orc_thomas(n, sub, dia, sup, rhs, z, work);
+        const double vy = y[0] + (c / g) * y[n - 1];
+        const double vz = z[0] + (c / g) * z[n - 1];
+        for (int i = 0; i < n; ++i) Tn[i] = y[i] - vy / (1.0 + vz) * z[i];
+    }
+    free(rhs);
+}
+
 /* One step at absolute index `step`.  Forward Euler (Eq. (3.3)):
  * Tn = T + inc(T).  Predictor-corrector (Sec. 3): the predictor
  * T* = T + inc(T) and the corrector Tn = (T + T* + inc(T*)) / 2, where
@@ -439,6 +534,10 @@ static void orc_advance(const orc_params* p, uint32_t step, uint32_t stream, con
 {
     const int64_t nc = orc_cells(p);
     orc_step_normals(p, step, stream, w->Z);
+    if (p->scheme == ORC_BE || p->scheme == ORC_CN) {
+        orc_implicit_1d(p, p->scheme == ORC_BE ? 1.0 : 0.5, T, w->Z, w->G, Tn);
+        return;
+    }
     orc_increment(p, T, w);
     if (p->scheme != ORC_PC) {
         for (int64_t i = 0; i < nc; ++i) Tn[i] = T[i] + w->inc[i];
@@ -574,7 +673,8 @@ int orc_run(const orc_params* p, int64_t R, uint32_t stream0, uint32_t step0, in
     if (p->dim < 1 || p->dim > 3 || R < 0 || nsteps < 0) return -2;
     if (p->cond && (p->dim != 1 || p->equation != ORC_HEAT || !p->cap)) return -2;
     if (p->dim > 1 && p->bc != ORC_PERIODIC) return -2;
-    if (p->scheme != ORC_FE && p->scheme != ORC_PC) return -2;
+    if (p->scheme != ORC_FE && p->scheme != ORC_PC && p->scheme != ORC_BE && p->scheme != ORC_CN) return -2;
+    if ((p->scheme == ORC_BE || p->scheme == ORC_CN) && (p->dim != 1 || p->cond)) return -2;
     if (sum_tc && p->tc_lags < 1) return -2;
     if (sum_sk && p->dim > 2) return -2;
     int64_t nc = orc_cells(p);

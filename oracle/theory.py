@@ -254,6 +254,15 @@ def scheme(prob_like):
         tref = np.full(L.shape[0], float(prob_like["wall_lo"]))
         faces = faces_nd_periodic(shape)
     A = np.eye(L.shape[0]) + r * L
+    theta = {"be": 1.0, "cn": 0.5}.get(prob_like.get("scheme", "fe"))
+    if theta is not None:
+        # implicit diffusion with weight theta, explicit noise (the implicit
+        # exercise of Sec. 6): T' = M^{-1} ((I + (1 - theta) r L) T + b + sum_f g_f d_f),
+        # M = I - theta r L; the face values are still those of T
+        Minv = np.linalg.inv(np.eye(L.shape[0]) - theta * r * L)
+        A = Minv @ (np.eye(L.shape[0]) + (1.0 - theta) * r * L)
+        b = Minv @ b
+        faces = [(P, q, w2, Minv @ d) for P, q, w2, d in faces]
     return A, b, faces, tref, L
 
 
@@ -421,8 +430,14 @@ def long_range_correlation(N, eps, dT):
 
 def amplification(x, scheme="fe"):
     """Deterministic factor per step of a mode with eigenvalue -x of r L:
-    forward Euler 1 - x; predictor-corrector (Heun) 1 - x + x^2/2."""
+    forward Euler 1 - x; predictor-corrector (Heun) 1 - x + x^2/2; the
+    implicit theta scheme (1 - (1 - theta) x) / (1 + theta x), theta = 1
+    backward Euler, 1/2 Crank-Nicolson (|factor| <= 1 for every x >= 0: both
+    unconditionally stable)."""
     x = np.asarray(x, dtype=float)
+    theta = {"be": 1.0, "cn": 0.5}.get(scheme)
+    if theta is not None:
+        return (1.0 - (1.0 - theta) * x) / (1.0 + theta * x)
     return 1.0 - x + (0.5 * x * x if scheme == "pc" else 0.0)
 
 
@@ -454,7 +469,8 @@ def structure_factor(shape, r, eps_amp, scheme="fe"):
     """Periodic structure factor for k != 0 with additive noise (the
     linearised heat equation; exact for species): forward Euler
     eps_amp N / (1 - x/2), predictor-corrector eps_amp N (2 - x) /
-    (2 - x + x^2/2), x = r mu_k (derivation: per mode T' = g T + h eta with
+    (2 - x + x^2/2), backward Euler eps_amp N / (1 + x/2), Crank-Nicolson
+    eps_amp N, x = r mu_k (derivation: per mode T' = g T + h eta with
     g = 1 - x + x^2/2 and h = 1 - x/2, so S = h^2 sigma^2 / (1 - g^2)).
     Entry k = 0 is set to 0; cells ordered with axis 0 fastest."""
     dims = list(shape)
@@ -466,6 +482,13 @@ def structure_factor(shape, r, eps_amp, scheme="fe"):
     x = r * mu
     if scheme == "pc":
         S = eps_amp * ncell * (2.0 - x) / (2.0 - x + 0.5 * x * x)
+    elif scheme in ("be", "cn"):
+        # implicit theta scheme: per mode S = q / ((1 + theta x)^2 - (1 - (1 - theta) x)^2)
+        # with the forward-Euler noise q = 2 x eps_amp N, i.e.
+        # eps_amp N / (1 + (theta - 1/2) x): Crank-Nicolson gives the flat value
+        # at every time step, backward Euler falls below it
+        theta = 1.0 if scheme == "be" else 0.5
+        S = eps_amp * ncell / (1.0 + (theta - 0.5) * x)
     else:
         S = eps_amp * ncell / (1.0 - 0.5 * x)
     S = S.ravel()
