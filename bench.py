@@ -74,6 +74,12 @@ OPS_1D_PC = add_ops(noise_ops(257.0 / 256.0), flux_ops(2 * 257.0 / 256.0, False)
 OPS_2D_SP = add_ops(noise_ops(2.0), flux_ops(2.0, True), {"fma": 9.0})
 OPS_2D_SP_PC = add_ops(noise_ops(2.0), flux_ops(4.0, True), {"fma": 2 * 9.0 + 3.0})
 OPS_3D = add_ops(noise_ops(3.0), flux_ops(3.0, False), {"fma": 11.0})
+# implicit theta scheme: the explicit right-hand side (stencil and flux
+# difference 5), the block LU (forward 1, backward 2: FMA and multiply), the
+# correction by the neighbouring values (2) and the reduced solve (4 FMAs per
+# source lane per lane, LPR / C = 1/4 of a source lane per cell at 32 x 8: 1);
+# its factors are read from a shared-memory table
+OPS_1D_THETA = add_ops(noise_ops(257.0 / 256.0), flux_ops(257.0 / 256.0, False), {"fma": 5.0 + 6.0})
 # a rod of several materials: the update ic (a_hi (T_r - T) + a_lo (T_l - T) + dG) + T,
 # 6 FP32 ops, its coefficients read from a shared-memory table
 OPS_1D_VAR = add_ops(noise_ops(257.0 / 256.0), flux_ops(257.0 / 256.0, False), {"fma": 6.0})
@@ -253,6 +259,15 @@ WORKLOADS = {
               "steps after 1e5"),
         chunk=10_000, ops=OPS_1D_VAR, bytes=None,
         kernel="k_step1d_cov<16,16,dirichlet,heat,var>", traffic=None),
+    "gradient_rod_cn": dict(
+        leg_chunk=10000, leg_steps=10,
+        make=lambda W: W.gradient_rod(scheme="cn", dt=2.0, want_cov=0),
+        desc=("the gradient_rod configuration (1D SHE rod, 256 cells, walls 1 and 2, eps=1e-3, 4096 "
+              "realizations, FP32, moments every 10 steps after 1e5) stepped by Crank-Nicolson (the implicit "
+              "exercise of Sec. 6) at r = 2, ten times forward Euler's stability limit; a partitioned "
+              "tridiagonal solve per realization and step"),
+        chunk=10_000, ops=OPS_1D_THETA, bytes=None,
+        kernel="k_step1d<float,32,8,dirichlet,heat,theta>", traffic=None),
     "oracle_rod": dict(
         leg_chunk=10000, leg_steps=3,
         make=lambda W: W.oracle_rod(want_cov=0, want_sk=0),
@@ -263,8 +278,8 @@ WORKLOADS = {
 
 # the workloads timed in short legs beside the headline (the `workloads`
 # sub-object of the bench line)
-LEG_WORKLOADS = ["gradient_rod_pc", "gradient_rod_tc", "two_material_rod", "species_2d", "species_2d_pc",
-                 "cube_3d", "batched_rods"]
+LEG_WORKLOADS = ["gradient_rod_pc", "gradient_rod_cn", "gradient_rod_tc", "two_material_rod", "species_2d",
+                 "species_2d_pc", "cube_3d", "batched_rods"]
 
 
 def workload(name):

@@ -73,7 +73,7 @@ extern "C" {
 typedef enum she_status {
     SHE_OK = 0,
     SHE_ERR_INVALID_ARG = 1,  /* bad parameter, size or pointer */
-    SHE_ERR_UNSTABLE = 2,     /* r = kappa dt/dx^2 > 1/(2 dim): FE unstable (Sec. 3) */
+    SHE_ERR_UNSTABLE = 2,     /* r = kappa dt/dx^2 > 1/(2 dim): FE / PC unstable (Sec. 3) */
     SHE_ERR_OOM = 3,          /* device allocation failed */
     SHE_ERR_CUDA = 4,         /* a CUDA runtime call failed */
     SHE_ERR_NONFINITE = 5,    /* the state holds NaN/Inf after a step batch */
@@ -85,7 +85,8 @@ typedef enum she_status {
 enum { SHE_HEAT = 0, SHE_SPECIES = 1 };        /* equation */
 enum { SHE_PERIODIC = 0, SHE_DIRICHLET = 1 };  /* boundary */
 enum { SHE_FP32 = 0, SHE_FP64 = 1 };           /* state/step precision */
-enum { SHE_FE = 0, SHE_PC = 1 };               /* scheme: forward Euler, predictor-corrector */
+enum { SHE_FE = 0, SHE_PC = 1,                /* scheme: forward Euler, predictor-corrector, */
+       SHE_BE = 2, SHE_CN = 3 };               /* backward Euler, Crank-Nicolson (implicit) */
 enum { SHE_SK_FULL = 1, SHE_SK_AXES = 2 };     /* want_sk bits */
 enum { SHE_KERNEL_AUTO = 0,                    /* fused on-chip / streaming kernels */
        SHE_KERNEL_PLAIN = 1 };                 /* plain one-launch-per-step form */
@@ -114,8 +115,16 @@ typedef struct she_params {
     double dt;            /* time step */
     uint64_t seed;        /* Philox key */
     int64_t realizations; /* independent sample paths, >= 1 */
-    int32_t scheme;       /* SHE_FE, or SHE_PC (kernel auto; 1D N <= 512;
-                             otherwise SHE_ERR_UNSUPPORTED) */
+    int32_t scheme;       /* SHE_FE; SHE_PC (kernel auto; 1D N <= 512); SHE_BE or
+                             SHE_CN, the implicit exercise of Sec. 6: the diffusion
+                             implicit with weight theta (1 backward Euler, 1/2
+                             Crank-Nicolson), the stochastic flux explicit,
+                               (I - theta r L) T' = T + (1 - theta) r L T + r b + div G(T),
+                             L the second difference with the wall stencil of
+                             Eq. (3.8), b its wall terms; no time-step limit
+                             (unconditionally stable); 1D, kernel auto, N <= 1024,
+                             a uniform rod, FP64 or FP32 without the covariance
+                             (otherwise SHE_ERR_UNSUPPORTED) */
     int32_t stochastic;   /* 1: thermal noise on; 0: deterministic (alpha = 0) */
     int32_t perturb_ic;   /* 1: T_ref + sigma N(0,1) per cell, sigma^2 = eps T_mid^2
                              (heat) or eps_c c_mid (species); zero-sum on periodic grids */

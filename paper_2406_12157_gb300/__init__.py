@@ -14,7 +14,8 @@ import ctypes
 import numpy as np
 
 from . import _abi
-from ._abi import (LibraryMissing, SHE_DIRICHLET, SHE_FE, SHE_PC, SHE_FP32, SHE_FP64, SHE_HEAT,  # noqa: F401
+from ._abi import (LibraryMissing, SHE_BE, SHE_CN, SHE_DIRICHLET, SHE_FE, SHE_PC, SHE_FP32, SHE_FP64,  # noqa: F401
+                   SHE_HEAT,
                    SHE_KERNEL_AUTO, SHE_KERNEL_PLAIN, SHE_PERIODIC, SHE_SK_AXES, SHE_SK_FULL,
                    SHE_SPECIES)
 
@@ -80,7 +81,8 @@ def params_from_problem(prob, stream=None, **overrides):
     p.dt = float(q["dt"])
     p.seed = int(q.get("seed", 0))
     p.realizations = int(q.get("realizations", 1))
-    p.scheme = {"fe": SHE_FE, "pc": SHE_PC, SHE_FE: SHE_FE, SHE_PC: SHE_PC}[q.get("scheme", "fe")]
+    p.scheme = {"fe": SHE_FE, "pc": SHE_PC, "be": SHE_BE, "cn": SHE_CN, SHE_FE: SHE_FE, SHE_PC: SHE_PC,
+                SHE_BE: SHE_BE, SHE_CN: SHE_CN}[q.get("scheme", "fe")]
     p.stochastic = int(q.get("stochastic", 1))
     p.perturb_ic = int(q.get("perturb_ic", 1))
     prec = q.get("precision", "fp32")

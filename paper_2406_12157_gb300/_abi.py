@@ -28,6 +28,8 @@ SHE_PERIODIC, SHE_DIRICHLET = 0, 1
 SHE_FP32, SHE_FP64 = 0, 1
 SHE_FE = 0
 SHE_PC = 1
+SHE_BE = 2
+SHE_CN = 3
 SHE_SK_FULL, SHE_SK_AXES = 1, 2
 SHE_KERNEL_AUTO, SHE_KERNEL_PLAIN = 0, 1
 # face fluxes the fixed scratch array of she_step_plain_noalloc holds

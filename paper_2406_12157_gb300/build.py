@@ -3,8 +3,9 @@
 Each ``csrc/*.cu`` translation unit is compiled in parallel to an object
 file, then linked into ``paper_2406_12157_gb300/_build/libshe.so``.  The
 fused 1D kernel's instantiation unit (``step1d_inst.cu``) is compiled once per
-(precision, wall, equation, scheme, material table) variant, 24 objects, so
-that its template instances compile in parallel too.  One ``-gencode``
+(precision, wall, equation, scheme, material table) variant, and once per
+(precision, wall, equation) for the implicit schemes, 32 objects, so that its
+template instances compile in parallel too.  One ``-gencode``
 (compute_103a -> sm_103a); no CMake.  An object is recompiled only when its
 source or any header is newer than it; the library is relinked when an
 object changed.
@@ -51,7 +52,10 @@ VARIANTS = {
          ["-DSHE_V_REAL=%s" % real, "-DSHE_V_DIR=%d" % d, "-DSHE_V_SP=%d" % s, "-DSHE_V_PC=%d" % pc,
           "-DSHE_V_VAR=%d" % v])
         for real in ("float", "double") for d in (0, 1) for s in (0, 1) for pc in (0, 1) for v in (0, 1)
-        if not (v and s)],       # the material table is for heat rods
+        if not (v and s)] + [    # the material table is for heat rods
+        ("%s_%s_%s_theta" % (real[0], "dir" if d else "per", "sp" if s else "heat"),
+         ["-DSHE_V_REAL=%s" % real, "-DSHE_V_DIR=%d" % d, "-DSHE_V_SP=%d" % s, "-DSHE_V_IMP=1"])
+        for real in ("float", "double") for d in (0, 1) for s in (0, 1)],
 }
 
 

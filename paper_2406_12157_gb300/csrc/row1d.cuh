@@ -393,10 +393,15 @@ struct Row1D {
     __device__ __forceinline__ void increment(const Real (&X)[C], const Real (&z)[C], Real g_high,
                                               Real (&inc)[C]) const
     {
-        if constexpr (VAR) {
-            increment_var(X, z, g_high, inc);
-            return;
-        }
+        if constexpr (VAR) increment_var(X, z, g_high, inc);
+        else increment_rate(X, z, g_high, inc, r);
+    }
+
+    // increment() with the stencil's rate rr in place of r (the implicit
+    // schemes take its explicit part (1 - theta) r)
+    __device__ __forceinline__ void increment_rate(const Real (&X)[C], const Real (&z)[C], Real g_high,
+                                                   Real (&inc)[C], Real rr) const
+    {
         const Real left_nb = __shfl_up_sync(FULL, X[C - 1], 1, LPR);
         const Real right_nb = __shfl_down_sync(FULL, X[0], 1, LPR);
         Real wrap_lo = Real(0), wrap_hi = Real(0);   // periodic: X_{N-1}, X_0
@@ -427,7 +432,7 @@ struct Row1D {
                 gf = DIR ? g_high : g_zero;
                 tr = DIR ? Real(2) * whi - X[j] : wrap_hi;
             }
-            inc[j] = r * (tr - Real(2) * X[j] + xl) + (gf - g_prev);
+            inc[j] = rr * (tr - Real(2) * X[j] + xl) + (gf - g_prev);
             xl = X[j];
             g_prev = gf;
         }
@@ -440,7 +445,7 @@ struct Row1D {
             tr = DIR ? Real(2) * whi - X[C - 1] : wrap_hi;
             gr = DIR ? g_high : g_zero;
         }
-        inc[C - 1] = r * (tr - Real(2) * X[C - 1] + xl) + (gr - g_prev);
+        inc[C - 1] = rr * (tr - Real(2) * X[C - 1] + xl) + (gr - g_prev);
     }
 
     // advance the row T by the predictor-corrector step with absolute index
@@ -466,6 +471,78 @@ struct Row1D {
         increment(Ts, z, g_high, inc);
 #pragma unroll
         for (int j = 0; j < C; ++j) T[j] = Real(0.5) * ((T[j] + Ts[j]) + inc[j]);
+    }
+
+    // advance the row T by one step of the implicit theta scheme with
+    // absolute index n (backward Euler theta = 1, Crank-Nicolson 1/2; the
+    // implicit exercise of Sec. 6): the right-hand side
+    // T + (1 - theta) r L T + r b + div G(T) with this step's normals (the
+    // stochastic flux explicit), then (I - theta r L) T' = rhs by a
+    // partitioned solve: each lane solves its block of C rows with the
+    // block's LU factors, the values left and right of every block follow
+    // from all lanes' first and last block values through the inverse of the
+    // reduced system (shuffles within the segment), and the block values are
+    // corrected by the block's responses to them.  A periodic rod's cyclic
+    // matrix is its tridiagonal part plus a rank-one term, removed by the
+    // Sherman-Morrison formula.  Rows past N are identity rows (rhs 0).
+    template <bool PERIODIC_SM>
+    __device__ __forceinline__ void step_theta(Real (&T)[C], uint32_t n, const Solve1D<Real>* sc,
+                                               const Reduced1D<Real>* red, Real omt, Real th2r_lo, Real th2r_hi,
+                                               Real cg, Real inv_den)
+    {
+        Real z[C];
+#pragma unroll
+        for (int g = 0; g < C / 4; ++g) {
+            Real v[4] = {Real(0), Real(0), Real(0), Real(0)};
+            if (stochastic) box_muller4(noise_block(make_uint4(q0 + (uint32_t)g, n, stream, 0u)), v);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) z[4 * g + t] = v[t];
+        }
+        const Real g_high = high_wall_flux(n);
+        Real x[C];
+        increment_rate(T, z, g_high, x, r * omt);
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            x[j] += T[j];
+            if (DIR && first_sl && j == 0) x[j] += th2r_lo;
+            if (DIR && i0 + j == N - 1) x[j] += th2r_hi;
+            if (RAGGED && i0 + j >= N) x[j] = Real(0);
+        }
+        const Solve1D<Real>* s = sc + i0;
+        // block LU: forward elimination, back substitution
+#pragma unroll
+        for (int j = 1; j < C; ++j) x[j] -= s[j].m * x[j - 1];
+        x[C - 1] *= s[C - 1].ip;
+#pragma unroll
+        for (int j = C - 2; j >= 0; --j) x[j] = (x[j] - s[j].sup * x[j + 1]) * s[j].ip;
+        // the values left and right of this block
+        Real xl = Real(0), xr = Real(0);
+        const Reduced1D<Real>* rr = red + (i0 / C) * LPR;
+#pragma unroll
+        for (int m = 0; m < LPR; ++m) {
+            const Real yf = __shfl_sync(FULL, x[0], m, LPR);
+            const Real yl = __shfl_sync(FULL, x[C - 1], m, LPR);
+            const Reduced1D<Real> q = rr[m];
+            xl = fma(q.lf, yf, fma(q.ll, yl, xl));
+            xr = fma(q.rf, yf, fma(q.rl, yl, xr));
+        }
+#pragma unroll
+        for (int j = 0; j < C; ++j) x[j] -= xl * s[j].v + xr * s[j].w;
+        if constexpr (PERIODIC_SM) {
+            Real mine = x[C - 1];
+            if (RAGGED) {
+#pragma unroll
+                for (int j = 0; j < C; ++j)
+                    if (j == jlast) mine = x[j];
+            }
+            const Real x_last = __shfl_sync(FULL, mine, last_sl, LPR);
+            const Real x_first = __shfl_sync(FULL, x[0], 0, LPR);
+            const Real sf = (x_first + cg * x_last) * inv_den;
+#pragma unroll
+            for (int j = 0; j < C; ++j) x[j] -= sf * s[j].z;
+        }
+#pragma unroll
+        for (int j = 0; j < C; ++j) T[j] = x[j];
     }
 
     template <bool PC>

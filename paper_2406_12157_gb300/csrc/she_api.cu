@@ -144,7 +144,11 @@ she_status convert(const she_params& p, she::Problem& out, std::string& msg)
         return SHE_ERR_INVALID_ARG;
     }
     if (p.equation != SHE_HEAT && p.equation != SHE_SPECIES) { msg = "she: bad equation"; return SHE_ERR_INVALID_ARG; }
-    if (p.scheme != SHE_FE && p.scheme != SHE_PC) { msg = "she: bad scheme"; return SHE_ERR_INVALID_ARG; }
+    if (p.scheme != SHE_FE && p.scheme != SHE_PC && p.scheme != SHE_BE && p.scheme != SHE_CN) {
+        msg = "she: bad scheme";
+        return SHE_ERR_INVALID_ARG;
+    }
+    const bool implicit = p.scheme == SHE_BE || p.scheme == SHE_CN;
     if (p.bc != SHE_PERIODIC && p.bc != SHE_DIRICHLET) { msg = "she: bad boundary"; return SHE_ERR_INVALID_ARG; }
     if (p.bc == SHE_DIRICHLET && p.dim > 1) {
         msg = "she: Dirichlet walls are supported in 1D only (2D/3D grids are periodic)";
@@ -191,7 +195,7 @@ she_status convert(const she_params& p, she::Problem& out, std::string& msg)
         eps = 1.0 / (p.n0 * dV);
     }
     if (!std::isfinite(r) || !std::isfinite(eps)) { msg = "she: non-finite r or eps"; return SHE_ERR_INVALID_ARG; }
-    if (!var && r > 1.0 / (2.0 * p.dim)) {
+    if (!var && !implicit && r > 1.0 / (2.0 * p.dim)) {
         char buf[160];
         snprintf(buf, sizeof buf, "she: forward Euler is unstable: r = kappa dt/dx^2 = %g > 1/(2 dim) = %g", r,
                  1.0 / (2.0 * p.dim));
@@ -228,6 +232,9 @@ void release(Handle* h)
     cudaFree(h->d_coef);
     cudaFree(h->d_ref);
     cudaFree(h->d_sigma);
+    cudaFree(h->d_solve);
+    cudaFree(h->d_theta_red);
+    h->d_solve = h->d_theta_red = nullptr;
     h->d_coef = nullptr;
     h->d_ref = h->d_sigma = nullptr;
     cudaFree(h->d_flags);
@@ -429,6 +436,15 @@ she_status she_init(const she_params* p, she_handle** out)
     if (st == SHE_OK && p->dim > 1 && p->kernel != SHE_KERNEL_AUTO) {
         st = SHE_ERR_UNSUPPORTED; msg = "she: the plain form is 1D";
     }
+    if (st == SHE_OK && p->dim == 1 && p->kernel == SHE_KERNEL_AUTO && p->n[0] > 1024) {
+        st = SHE_ERR_UNSUPPORTED; msg = "she: the fused 1D kernels take rows of at most 1024 cells (the plain form any)";
+    }
+    if (st == SHE_OK && (p->scheme == SHE_BE || p->scheme == SHE_CN) &&
+        (p->dim != 1 || p->kernel != SHE_KERNEL_AUTO || p->lambda_cells || (need_cov && p->precision == SHE_FP32))) {
+        st = SHE_ERR_UNSUPPORTED;
+        msg = "she: the implicit schemes run on the fused 1D kernel (kernel auto, a uniform rod; FP64, or FP32 "
+              "without the covariance)";
+    }
     if (st == SHE_OK && p->lambda_cells && p->kernel != SHE_KERNEL_AUTO) {
         st = SHE_ERR_UNSUPPORTED; msg = "she: a rod of several materials runs on the fused kernels (kernel auto)";
     }
@@ -557,6 +573,7 @@ she_status she_init(const she_params* p, she_handle** out)
         sc.insert(sc.end(), m.cap.begin(), m.cap.end());
         if (e == cudaSuccess) e = cudaMemcpy(h->d_sigma, sc.data(), sc.size() * sizeof(double), cudaMemcpyHostToDevice);
     }
+    if (e == cudaSuccess && (h->prob.scheme == SHE_BE || h->prob.scheme == SHE_CN)) e = she::setup_implicit(*h);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_acc1, 0, nstate * sizeof(double), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_acc2, 0, nstate * sizeof(double), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flags, 0, sizeof(int), h->stream);

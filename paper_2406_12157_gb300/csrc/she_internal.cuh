@@ -45,6 +45,25 @@ struct __align__(4 * sizeof(Real)) Coef1D {
     Real a, sh, ic, ref;
 };
 
+// Factor table of the implicit schemes' tridiagonal solve (backward Euler /
+// Crank-Nicolson), one entry per padded row: the forward multiplier m, the
+// reciprocal pivot ip and the super-diagonal sup of the row's block LU, the
+// block's responses v (to the value left of the block) and w (to the value
+// right of it), and z, the Sherman-Morrison vector of a periodic rod.
+template <typename Real>
+struct __align__(4 * sizeof(Real)) Solve1D {
+    Real m, ip, sup, v;
+    Real w, z, pad0, pad1;
+};
+
+// Row of the inverse of the implicit solve's reduced (lane-interface) system:
+// for lane k and source lane m, the weights of lane m's first and last block
+// values in the value left of lane k's block (lf, ll) and right of it (rf, rl).
+template <typename Real>
+struct __align__(4 * sizeof(Real)) Reduced1D {
+    Real lf, ll, rf, rl;
+};
+
 // Arguments of the 1D step kernels (one realization per warp).
 template <typename Real>
 struct Step1DArgs {
@@ -72,6 +91,12 @@ struct Step1DArgs {
     Real* tc_ring;        // [R][tc_lags][N] the last tc_lags samples of delta (sample s in slot s % L)
     double* tc_acc;       // [R][tc_lags][N] sum of delta_i(s) delta_i(s - l)
     const Coef1D<Real>* coef;   // [N + 1] material table of a rod of several materials (else null)
+    // implicit schemes (theta = 1 backward Euler, 1/2 Crank-Nicolson)
+    const Solve1D<Real>* solve; // [C x LPR] factor table of the layout
+    const Reduced1D<Real>* red; // [LPR][LPR] reduced-system inverse
+    Real omt;                   // 1 - theta
+    Real th2r_lo, th2r_hi;      // theta 2 r T_wall: the walls' implicit share of the ghost term
+    Real sm_cg, sm_inv;         // periodic: Sherman-Morrison c / g and 1 / (1 + v.z)
 };
 
 // Arguments of the 2D step kernel (one step per launch).
@@ -211,6 +236,11 @@ struct Handle {
     double* d_sigma = nullptr;     // [N] initial perturbation sd per cell
     std::vector<double> ref_cells; // host copy of T_ref
     std::vector<double> cap_cells; // rho c_V per cell (the energy weights of a periodic rod)
+    // implicit schemes: factor tables of the chosen layout
+    int imp_layout = 0;
+    void* d_solve = nullptr;       // [C x LPR] Solve1D of the state's precision
+    void* d_theta_red = nullptr;   // [LPR][LPR] Reduced1D
+    double sm_cg = 0.0, sm_inv = 0.0;
     void* d_tc_ring = nullptr;     // [R][tc_lags][N] of the state's type
     double* d_tc_acc = nullptr;    // [R][tc_lags][N]
     double* d_tc_red = nullptr;    // [tc_lags][N] reduction over the realizations
@@ -309,6 +339,12 @@ inline void prof_close(Handle& h)
 // in step1d_kernel.cuh, instantiated by step1d_inst.cu.
 template <typename Real, bool DIR, bool SP, bool PC, bool VAR>
 cudaError_t launch_step1d_variant(const Step1DArgs<Real>& a, int layout, cudaStream_t st);
+// The fused 1D kernel stepping an implicit scheme (backward Euler /
+// Crank-Nicolson) at the given layout; instantiated by step1d_inst.cu.
+template <typename Real, bool DIR, bool SP>
+cudaError_t launch_step1d_theta(const Step1DArgs<Real>& a, int layout, cudaStream_t st);
+// Layout and factor tables of the implicit solve (host, at init).
+cudaError_t setup_implicit(Handle& h);
 cudaError_t launch_init_state(Handle& h);
 cudaError_t launch_step1d(Handle& h, uint32_t step0, int nsteps);
 cudaError_t launch_step1d_plain(Handle& h, uint32_t step0, int nsteps);

@@ -21,7 +21,10 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <cmath>
 #include <cstdlib>
+#include <utility>
+#include <vector>
 
 #include "philox.cuh"
 #include "she_internal.cuh"
@@ -43,6 +46,163 @@ static int pick_layout_pc(int N)
     return 0;
 }
 
+
+// Implicit-scheme layouts: 4 x 4 up to 16 cells, then at least 8 cells per
+// lane in segments of 4 to 32 lanes (rows of up to 1024 cells).
+static int pick_layout_theta(int N)
+{
+    if (N <= 16) return 404;
+    if (N <= 32) return 804;
+    if (N <= 64) return 808;
+    if (N <= 128) return 1608;
+    if (N <= 256) return 3208;
+    if (N <= 512) return 3216;
+    if (N <= 1024) return 3232;
+    return 0;
+}
+
+// Factor tables of the implicit theta scheme (host, FP64, then the state's
+// precision): the matrix M = I - theta r L (Dirichlet rows of the wall
+// stencil 1 + 3 theta r; a periodic rod's tridiagonal part, its corners
+// moved into a rank-one term, Sherman-Morrison), padded to C x LPR rows with
+// identity rows; per block of C rows its LU factors and its responses v, w
+// to the values next to it; the inverse of the reduced system that couples
+// the blocks' first and last values.
+template <typename Real>
+static cudaError_t upload_theta_tables(Handle& h, int C, int LPR, const std::vector<double>& m,
+                                       const std::vector<double>& ip, const std::vector<double>& sup,
+                                       const std::vector<double>& v, const std::vector<double>& w,
+                                       const std::vector<double>& z, const std::vector<double>& Rinv)
+{
+    const int Np = C * LPR, P2 = 2 * LPR;
+    std::vector<Solve1D<Real>> s((size_t)Np);
+    for (int i = 0; i < Np; ++i)
+        s[(size_t)i] = {(Real)m[(size_t)i], (Real)ip[(size_t)i], (Real)sup[(size_t)i], (Real)v[(size_t)i],
+                        (Real)w[(size_t)i], (Real)z[(size_t)i], Real(0), Real(0)};
+    std::vector<Reduced1D<Real>> red((size_t)LPR * LPR);
+    for (int k = 0; k < LPR; ++k)
+        for (int q = 0; q < LPR; ++q) {
+            // left of block k: last value of block k - 1 (row 2k - 1 of the
+            // reduced unknowns); right: first value of block k + 1 (row 2k + 2)
+            const double lf = k >= 1 ? Rinv[(size_t)(2 * k - 1) * P2 + 2 * q] : 0.0;
+            const double ll = k >= 1 ? Rinv[(size_t)(2 * k - 1) * P2 + 2 * q + 1] : 0.0;
+            const double rf = k + 1 < LPR ? Rinv[(size_t)(2 * k + 2) * P2 + 2 * q] : 0.0;
+            const double rl = k + 1 < LPR ? Rinv[(size_t)(2 * k + 2) * P2 + 2 * q + 1] : 0.0;
+            red[(size_t)k * LPR + q] = {(Real)lf, (Real)ll, (Real)rf, (Real)rl};
+        }
+    cudaError_t e = cudaMalloc(&h.d_solve, s.size() * sizeof(s[0]));
+    if (e == cudaSuccess) e = cudaMalloc(&h.d_theta_red, red.size() * sizeof(red[0]));
+    if (e == cudaSuccess) e = cudaMemcpy(h.d_solve, s.data(), s.size() * sizeof(s[0]), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h.d_theta_red, red.data(), red.size() * sizeof(red[0]), cudaMemcpyHostToDevice);
+    return e;
+}
+
+cudaError_t setup_implicit(Handle& h)
+{
+    const int N = h.prob.n[0];
+    const bool dir = h.prob.bc == SHE_DIRICHLET;
+    const double theta = h.prob.scheme == SHE_BE ? 1.0 : 0.5;
+    const double r = h.prob.r;
+    const int layout = pick_layout_theta(N);
+    if (layout == 0) return cudaErrorInvalidValue;
+    const int C = layout / 100, LPR = layout % 100, Np = C * LPR;
+    h.imp_layout = layout;
+    std::vector<double> sub((size_t)Np, 0.0), dia((size_t)Np, 1.0), sup((size_t)Np, 0.0);
+    for (int i = 0; i < N; ++i) {
+        sub[(size_t)i] = i > 0 ? -theta * r : 0.0;
+        sup[(size_t)i] = i < N - 1 ? -theta * r : 0.0;
+        dia[(size_t)i] = 1.0 + 2.0 * theta * r;
+    }
+    const double corner = -theta * r;
+    double gam = 0.0;
+    if (dir) {
+        dia[0] = 1.0 + 3.0 * theta * r;
+        dia[(size_t)N - 1] = 1.0 + 3.0 * theta * r;
+    } else {
+        gam = -dia[0];
+        dia[0] -= gam;
+        dia[(size_t)N - 1] -= corner * corner / gam;
+    }
+    std::vector<double> m((size_t)Np, 0.0), ip((size_t)Np, 0.0), v((size_t)Np, 0.0), w((size_t)Np, 0.0),
+        z((size_t)Np, 0.0);
+    // block LU and the responses to the neighbouring values
+    auto solve_block = [&](int b, std::vector<double>& x) {   // x[b..b+C) in place
+        for (int j = 1; j < C; ++j) x[(size_t)b + j] -= m[(size_t)b + j] * x[(size_t)b + j - 1];
+        x[(size_t)b + C - 1] *= ip[(size_t)b + C - 1];
+        for (int j = C - 2; j >= 0; --j)
+            x[(size_t)b + j] = (x[(size_t)b + j] - sup[(size_t)b + j] * x[(size_t)b + j + 1]) * ip[(size_t)b + j];
+    };
+    for (int k = 0; k < LPR; ++k) {
+        const int b = k * C;
+        double piv = dia[(size_t)b];
+        ip[(size_t)b] = 1.0 / piv;
+        for (int j = 1; j < C; ++j) {
+            m[(size_t)b + j] = sub[(size_t)b + j] / piv;
+            piv = dia[(size_t)b + j] - m[(size_t)b + j] * sup[(size_t)b + j - 1];
+            ip[(size_t)b + j] = 1.0 / piv;
+        }
+        v[(size_t)b] = sub[(size_t)b];
+        solve_block(b, v);
+        w[(size_t)b + C - 1] = sup[(size_t)b + C - 1];
+        solve_block(b, w);
+    }
+    // reduced system of the blocks' first and last values, and its inverse
+    const int P2 = 2 * LPR;
+    std::vector<double> M((size_t)P2 * P2, 0.0), Rinv((size_t)P2 * P2, 0.0);
+    for (int k = 0; k < LPR; ++k) {
+        const int b = k * C;
+        for (int e2 = 0; e2 < 2; ++e2) {
+            const int row = 2 * k + e2;
+            const int cell = e2 == 0 ? b : b + C - 1;
+            M[(size_t)row * P2 + row] = 1.0;
+            if (k >= 1) M[(size_t)row * P2 + 2 * k - 1] += v[(size_t)cell];
+            if (k + 1 < LPR) M[(size_t)row * P2 + 2 * k + 2] += w[(size_t)cell];
+        }
+    }
+    for (int i = 0; i < P2; ++i) Rinv[(size_t)i * P2 + i] = 1.0;
+    for (int c = 0; c < P2; ++c) {                 // Gauss-Jordan with partial pivoting
+        int piv = c;
+        for (int i = c + 1; i < P2; ++i)
+            if (std::fabs(M[(size_t)i * P2 + c]) > std::fabs(M[(size_t)piv * P2 + c])) piv = i;
+        for (int j = 0; j < P2; ++j) {
+            std::swap(M[(size_t)c * P2 + j], M[(size_t)piv * P2 + j]);
+            std::swap(Rinv[(size_t)c * P2 + j], Rinv[(size_t)piv * P2 + j]);
+        }
+        const double d = 1.0 / M[(size_t)c * P2 + c];
+        for (int j = 0; j < P2; ++j) {
+            M[(size_t)c * P2 + j] *= d;
+            Rinv[(size_t)c * P2 + j] *= d;
+        }
+        for (int i = 0; i < P2; ++i) {
+            if (i == c) continue;
+            const double f = M[(size_t)i * P2 + c];
+            if (f == 0.0) continue;
+            for (int j = 0; j < P2; ++j) {
+                M[(size_t)i * P2 + j] -= f * M[(size_t)c * P2 + j];
+                Rinv[(size_t)i * P2 + j] -= f * Rinv[(size_t)c * P2 + j];
+            }
+        }
+    }
+    if (!dir) {
+        // Sherman-Morrison: M = M' + u v^T, u = (g, 0, .., c)^T, v = (1, 0, .., c / g)^T;
+        // z = M'^{-1} u by the plain Thomas algorithm on the padded tridiagonal part
+        std::vector<double> cp((size_t)Np, 0.0);
+        double pv = dia[0];
+        cp[0] = sup[0] / pv;
+        z[0] = gam / pv;
+        for (int i = 1; i < Np; ++i) {
+            pv = dia[(size_t)i] - sub[(size_t)i] * cp[(size_t)i - 1];
+            cp[(size_t)i] = sup[(size_t)i] / pv;
+            const double ui = i == N - 1 ? corner : 0.0;
+            z[(size_t)i] = (ui - sub[(size_t)i] * z[(size_t)i - 1]) / pv;
+        }
+        for (int i = Np - 2; i >= 0; --i) z[(size_t)i] -= cp[(size_t)i] * z[(size_t)i + 1];
+        h.sm_cg = corner / gam;
+        h.sm_inv = 1.0 / (1.0 + z[0] + h.sm_cg * z[(size_t)N - 1]);
+    }
+    if (h.precision == SHE_FP64) return upload_theta_tables<double>(h, C, LPR, m, ip, sup, v, w, z, Rinv);
+    return upload_theta_tables<float>(h, C, LPR, m, ip, sup, v, w, z, Rinv);
+}
 
 // Layout for a row of N cells: cells per lane C and lanes per realization
 // LPR with LPR*C >= N.  Rows of up to 128 cells use 4 cells per lane in the
@@ -101,6 +261,21 @@ static cudaError_t launch_fused(Handle& h, uint32_t step0, int nsteps)
     a.coef = (const Coef1D<Real>*)h.d_coef;
     const bool dir = h.prob.bc == SHE_DIRICHLET;
     const bool sp = h.prob.equation == SHE_SPECIES;
+    if (h.prob.scheme == SHE_BE || h.prob.scheme == SHE_CN) {
+        const double theta = h.prob.scheme == SHE_BE ? 1.0 : 0.5;
+        a.solve = (const Solve1D<Real>*)h.d_solve;
+        a.red = (const Reduced1D<Real>*)h.d_theta_red;
+        a.omt = (Real)(1.0 - theta);
+        a.th2r_lo = (Real)(dir ? theta * 2.0 * h.prob.r * h.prob.wall_lo : 0.0);
+        a.th2r_hi = (Real)(dir ? theta * 2.0 * h.prob.r * h.prob.wall_hi : 0.0);
+        a.sm_cg = (Real)h.sm_cg;
+        a.sm_inv = (Real)h.sm_inv;
+        const int layout = h.imp_layout;
+        if (dir) return sp ? launch_step1d_theta<Real, true, true>(a, layout, h.stream)
+                           : launch_step1d_theta<Real, true, false>(a, layout, h.stream);
+        return sp ? launch_step1d_theta<Real, false, true>(a, layout, h.stream)
+                  : launch_step1d_theta<Real, false, false>(a, layout, h.stream);
+    }
     if (h.prob.scheme == SHE_PC) {
         const int layout = pick_layout_pc(a.N);
         if (h.var)         // a rod of several materials (heat)

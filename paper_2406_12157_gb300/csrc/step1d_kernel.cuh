@@ -26,7 +26,10 @@ constexpr int step1d_smem_per_warp() { return 2 * C * 32 * (int)sizeof(Real); }
 
 // VAR: a rod of several materials; its material table (N + 1 entries) is
 // copied into shared memory after the moment partials.
-template <typename Real, int C, int LPR, bool DIR, bool SPECIES, bool RAGGED, int MINB, bool PC, bool VAR>
+// IMP: an implicit scheme (backward Euler / Crank-Nicolson); its factor
+// tables (C x LPR rows, LPR x LPR reduced weights) are copied there instead.
+template <typename Real, int C, int LPR, bool DIR, bool SPECIES, bool RAGGED, int MINB, bool PC, bool VAR,
+          bool IMP = false>
 __global__ void __launch_bounds__(kWarpsPerBlock1D * 32, MINB)
 k_step1d(const __grid_constant__ Step1DArgs<Real> a)
 {
@@ -38,9 +41,16 @@ k_step1d(const __grid_constant__ Step1DArgs<Real> a)
     const int warp = blockIdx.x * kWarpsPerBlock1D + (threadIdx.x >> 5);
     Coef1D<Real>* tab = reinterpret_cast<Coef1D<Real>*>(
         smem_raw + (size_t)kWarpsPerBlock1D * step1d_smem_per_warp<Real, C>());
+    Solve1D<Real>* stab = reinterpret_cast<Solve1D<Real>*>(tab);
+    Reduced1D<Real>* rtab = reinterpret_cast<Reduced1D<Real>*>(stab + C * LPR);
     if constexpr (VAR) {
         // every thread of the block helps, before any warp leaves
         for (int k = threadIdx.x; k <= a.N; k += blockDim.x) tab[k] = a.coef[k];
+        __syncthreads();
+    }
+    if constexpr (IMP) {
+        for (int k = threadIdx.x; k < C * LPR; k += blockDim.x) stab[k] = a.solve[k];
+        for (int k = threadIdx.x; k < LPR * LPR; k += blockDim.x) rtab[k] = a.red[k];
         __syncthreads();
     }
     if (warp * RPW >= a.R) return;  // warp-uniform
@@ -72,7 +82,11 @@ k_step1d(const __grid_constant__ Step1DArgs<Real> a)
     int nsamp = 0;
 
     for (int s = 0; s < a.nsteps; ++s) {
-        rowst.template advance<PC>(T, a.step0 + (uint32_t)s);
+        if constexpr (IMP)
+            rowst.template step_theta<!DIR>(T, a.step0 + (uint32_t)s, stab, rtab, a.omt, a.th2r_lo, a.th2r_hi,
+                                            a.sm_cg, a.sm_inv);
+        else
+            rowst.template advance<PC>(T, a.step0 + (uint32_t)s);
         if (s == next_s) {                 // sample after step m = n + 1 (Eq. (3.9))
             next_s += a.K;
             if (a.tc_lags > 0 && active) {
@@ -139,7 +153,8 @@ k_step1d(const __grid_constant__ Step1DArgs<Real> a)
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.flags, 1);
 }
 
-template <typename Real, int C, int LPR, bool DIR, bool SP, int MINB, bool PC = false, bool VAR = false>
+template <typename Real, int C, int LPR, bool DIR, bool SP, int MINB, bool PC = false, bool VAR = false,
+          bool IMP = false>
 inline cudaError_t launch_layout(const Step1DArgs<Real>& a, cudaStream_t st)
 {
     constexpr int RPW = 32 / LPR;
@@ -147,13 +162,14 @@ inline cudaError_t launch_layout(const Step1DArgs<Real>& a, cudaStream_t st)
     const dim3 block(kWarpsPerBlock1D * 32);
     const dim3 grid((warps + kWarpsPerBlock1D - 1) / kWarpsPerBlock1D);
     const int smem = kWarpsPerBlock1D * step1d_smem_per_warp<Real, C>() +
-                     (VAR ? (a.N + 1) * (int)sizeof(Coef1D<Real>) : 0);
+                     (VAR ? (a.N + 1) * (int)sizeof(Coef1D<Real>) : 0) +
+                     (IMP ? C * LPR * (int)sizeof(Solve1D<Real>) + LPR * LPR * (int)sizeof(Reduced1D<Real>) : 0);
     if (a.N == LPR * C) {
-        auto k = k_step1d<Real, C, LPR, DIR, SP, false, MINB, PC, VAR>;
+        auto k = k_step1d<Real, C, LPR, DIR, SP, false, MINB, PC, VAR, IMP>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         k<<<grid, block, smem, st>>>(a);
     } else {
-        auto k = k_step1d<Real, C, LPR, DIR, SP, true, MINB, PC, VAR>;
+        auto k = k_step1d<Real, C, LPR, DIR, SP, true, MINB, PC, VAR, IMP>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         k<<<grid, block, smem, st>>>(a);
     }
@@ -207,6 +223,25 @@ inline cudaError_t launch_ds_pc(const Step1DArgs<Real>& a, int layout, cudaStrea
 // (precision, wall, equation) combination, with the material table of a rod
 // of several materials (VAR); layout = cells per lane * 100 + lanes per
 // realization.
+// Implicit-scheme layouts (see pick_layout_theta): at least 8 cells per lane
+// where the row allows, since the reduced solve costs LPR shuffle pairs per
+// lane and step.
+template <typename Real, bool DIR, bool SP>
+cudaError_t launch_step1d_theta(const Step1DArgs<Real>& a, int layout, cudaStream_t st)
+{
+    constexpr bool F = sizeof(Real) == 4;
+    switch (layout) {
+    case 404: return launch_layout<Real, 4, 4, DIR, SP, F ? 8 : 4, false, false, true>(a, st);
+    case 804: return launch_layout<Real, 8, 4, DIR, SP, F ? 8 : 4, false, false, true>(a, st);
+    case 808: return launch_layout<Real, 8, 8, DIR, SP, F ? 8 : 4, false, false, true>(a, st);
+    case 1608: return launch_layout<Real, 16, 8, DIR, SP, F ? 4 : 2, false, false, true>(a, st);
+    case 3208: return launch_layout<Real, 32, 8, DIR, SP, F ? 2 : 1, false, false, true>(a, st);
+    case 3216: return launch_layout<Real, 32, 16, DIR, SP, F ? 2 : 1, false, false, true>(a, st);
+    case 3232: return launch_layout<Real, 32, 32, DIR, SP, 1, false, false, true>(a, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 template <typename Real, bool DIR, bool SP, bool PC, bool VAR>
 cudaError_t launch_step1d_variant(const Step1DArgs<Real>& a, int layout, cudaStream_t st)
 {
