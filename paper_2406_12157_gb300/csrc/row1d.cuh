@@ -138,11 +138,19 @@ struct Row1D {
     {
         cf = table;
         const Real sq2 = Real(1.41421356237309504880);
-        g_low_amp = sq2 * Real(2) * cf[0].sh * wlo;
-        g_wall_amp = sq2 * Real(2) * cf[N].sh * whi;
+        g_low_amp = sq2 * Real(2) * cf[tpos(0)].sh * wlo;
+        g_wall_amp = sq2 * Real(2) * cf[tpos(N)].sh * whi;
     }
 
-    __device__ __forceinline__ const Coef1D<Real>& coef_at(int k) const { return cf[k < N ? k : N]; }
+    // Shared-memory tables (the material table, the implicit solve's
+    // factors) hold logical row k = 0..NP (NP = C x LPR; rows past N repeat
+    // row N) transposed: row j of lane block s at j * LPR + s, so that the
+    // lanes of a segment read consecutive entries (row-major, a segment's
+    // lanes are C rows apart: the same bank for every lane).
+    static constexpr int NP = C * LPR;
+    __device__ __forceinline__ static int tpos(int k) { return k < NP ? (k % C) * LPR + k / C : NP; }
+
+    __device__ __forceinline__ const Coef1D<Real>& coef_at(int k) const { return cf[tpos(k)]; }
 
     __device__ __forceinline__ uint4 noise_block(uint4 ctr) const
     {
@@ -508,26 +516,27 @@ struct Row1D {
             if (DIR && i0 + j == N - 1) x[j] += th2r_hi;
             if (RAGGED && i0 + j >= N) x[j] = Real(0);
         }
-        const Solve1D<Real>* s = sc + i0;
+        const Solve1D<Real>* s = sc + i0 / C;          // row j of this block at s[j * LPR]
         // block LU: forward elimination, back substitution
 #pragma unroll
-        for (int j = 1; j < C; ++j) x[j] -= s[j].m * x[j - 1];
-        x[C - 1] *= s[C - 1].ip;
+        for (int j = 1; j < C; ++j) x[j] -= s[j * LPR].m * x[j - 1];
+        x[C - 1] *= s[(C - 1) * LPR].ip;
 #pragma unroll
-        for (int j = C - 2; j >= 0; --j) x[j] = (x[j] - s[j].sup * x[j + 1]) * s[j].ip;
-        // the values left and right of this block
+        for (int j = C - 2; j >= 0; --j) x[j] = (x[j] - s[j * LPR].sup * x[j + 1]) * s[j * LPR].ip;
+        // the values left and right of this block (reduced weights stored
+        // transposed: source lane m of block k at m * LPR + k)
         Real xl = Real(0), xr = Real(0);
-        const Reduced1D<Real>* rr = red + (i0 / C) * LPR;
+        const Reduced1D<Real>* rr = red + i0 / C;
 #pragma unroll
         for (int m = 0; m < LPR; ++m) {
             const Real yf = __shfl_sync(FULL, x[0], m, LPR);
             const Real yl = __shfl_sync(FULL, x[C - 1], m, LPR);
-            const Reduced1D<Real> q = rr[m];
+            const Reduced1D<Real> q = rr[m * LPR];
             xl = fma(q.lf, yf, fma(q.ll, yl, xl));
             xr = fma(q.rf, yf, fma(q.rl, yl, xr));
         }
 #pragma unroll
-        for (int j = 0; j < C; ++j) x[j] -= xl * s[j].v + xr * s[j].w;
+        for (int j = 0; j < C; ++j) x[j] -= xl * s[j * LPR].v + xr * s[j * LPR].w;
         if constexpr (PERIODIC_SM) {
             Real mine = x[C - 1];
             if (RAGGED) {
@@ -539,7 +548,7 @@ struct Row1D {
             const Real x_first = __shfl_sync(FULL, x[0], 0, LPR);
             const Real sf = (x_first + cg * x_last) * inv_den;
 #pragma unroll
-            for (int j = 0; j < C; ++j) x[j] -= sf * s[j].z;
+            for (int j = 0; j < C; ++j) x[j] -= sf * s[j * LPR].z;
         }
 #pragma unroll
         for (int j = 0; j < C; ++j) T[j] = x[j];

@@ -131,8 +131,9 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
     // zero both operand stages (rows of absent realizations stay zero)
     for (int i = threadIdx.x; i < 4 * kOpBytes / 16; i += blockDim.x)
         reinterpret_cast<uint4*>(base)[i] = make_uint4(0u, 0u, 0u, 0u);
-    if constexpr (VAR)
-        for (int k = threadIdx.x; k <= a.N; k += blockDim.x) tab[k] = a.coef[k];
+    using RowT = Row1D<float, C, LPR, DIR, SPECIES, RAGGED, false, VAR>;
+    if constexpr (VAR)     // rows past N repeat row N; stored transposed (RowT::tpos)
+        for (int k = threadIdx.x; k <= C * LPR; k += blockDim.x) tab[RowT::tpos(k)] = a.coef[k < a.N ? k : a.N];
 
     const int N = a.N;
     const int Mh = (N + 127) / 128;
@@ -159,7 +160,7 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
     fence_after_sync();
     const uint32_t tbase = use_tc ? *tslot : 0u;
 
-    Row1D<float, C, LPR, DIR, SPECIES, RAGGED, false, VAR> rowst;   // keys in registers: measured faster here
+    RowT rowst;   // keys in registers: measured faster here
     rowst.init(a, sl, rho);
     if constexpr (VAR) rowst.init_var(tab);
     const int i0 = sl * C;
@@ -213,7 +214,7 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
 #pragma unroll
                 for (int t = 0; t < G8; ++t) {
                     const int j = j0 + t;
-                    const float ref = VAR ? tab[i0 + j < N ? i0 + j : N].ref
+                    const float ref = VAR ? tab[RowT::tpos(i0 + j)].ref
                                           : DIR ? fmaf(dref, (float)(i0 + j) + 0.5f, wlo) : wlo;
                     d[t] = T[j] - ref;
                     sm1[j * 32] += d[t];
@@ -318,7 +319,7 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
 template <int C, int LPR, bool DIR, bool SP, bool PC, bool VAR>
 static cudaError_t launch_cov_layout(const Step1DArgs<float>& a, const CovArgs& c, int grid, cudaStream_t st)
 {
-    const int smem = cov_smem_bytes<C>(LPR) + (VAR ? (a.N + 1) * (int)sizeof(Coef1D<float>) : 0);
+    const int smem = cov_smem_bytes<C>(LPR) + (VAR ? (C * LPR + 1) * (int)sizeof(Coef1D<float>) : 0);
     if (a.N == C * LPR) {
         auto k = k_step1d_cov<C, LPR, DIR, SP, false, PC, VAR>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

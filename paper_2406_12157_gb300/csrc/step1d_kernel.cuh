@@ -41,16 +41,18 @@ k_step1d(const __grid_constant__ Step1DArgs<Real> a)
     const int warp = blockIdx.x * kWarpsPerBlock1D + (threadIdx.x >> 5);
     Coef1D<Real>* tab = reinterpret_cast<Coef1D<Real>*>(
         smem_raw + (size_t)kWarpsPerBlock1D * step1d_smem_per_warp<Real, C>());
+    using RowT = Row1D<Real, C, LPR, DIR, SPECIES, RAGGED, true, VAR>;
     Solve1D<Real>* stab = reinterpret_cast<Solve1D<Real>*>(tab);
     Reduced1D<Real>* rtab = reinterpret_cast<Reduced1D<Real>*>(stab + C * LPR);
     if constexpr (VAR) {
-        // every thread of the block helps, before any warp leaves
-        for (int k = threadIdx.x; k <= a.N; k += blockDim.x) tab[k] = a.coef[k];
+        // every thread of the block helps, before any warp leaves; rows past
+        // N repeat row N; stored transposed (RowT::tpos)
+        for (int k = threadIdx.x; k <= C * LPR; k += blockDim.x) tab[RowT::tpos(k)] = a.coef[k < a.N ? k : a.N];
         __syncthreads();
     }
     if constexpr (IMP) {
-        for (int k = threadIdx.x; k < C * LPR; k += blockDim.x) stab[k] = a.solve[k];
-        for (int k = threadIdx.x; k < LPR * LPR; k += blockDim.x) rtab[k] = a.red[k];
+        for (int k = threadIdx.x; k < C * LPR; k += blockDim.x) stab[RowT::tpos(k)] = a.solve[k];
+        for (int k = threadIdx.x; k < LPR * LPR; k += blockDim.x) rtab[(k % LPR) * LPR + k / LPR] = a.red[k];
         __syncthreads();
     }
     if (warp * RPW >= a.R) return;  // warp-uniform
@@ -61,7 +63,7 @@ k_step1d(const __grid_constant__ Step1DArgs<Real> a)
     Real* sm1 = reinterpret_cast<Real*>(smem_raw) + (threadIdx.x >> 5) * (2 * C * 32) + lane;
     Real* sm2 = sm1 + C * 32;
 
-    Row1D<Real, C, LPR, DIR, SPECIES, RAGGED, true, VAR> rowst;
+    RowT rowst;
     rowst.init(a, sl, rho);
     if constexpr (VAR) rowst.init_var(tab);
     const int N = a.N;
@@ -105,7 +107,7 @@ k_step1d(const __grid_constant__ Step1DArgs<Real> a)
                 for (int j = 0; j < C; ++j) {
                     const int i = i0 + j;
                     if (RAGGED && i >= N) continue;
-                    const Real ref = VAR ? tab[i].ref : DIR ? fma(dref, Real(i0 + j) + half, wlo) : wlo;
+                    const Real ref = VAR ? tab[RowT::tpos(i)].ref : DIR ? fma(dref, Real(i0 + j) + half, wlo) : wlo;
                     const Real d = T[j] - ref;
                     ring[(size_t)slot * N + i] = d;
                     atomicAdd(&acc[i], (double)(d * d));
@@ -118,7 +120,7 @@ k_step1d(const __grid_constant__ Step1DArgs<Real> a)
             ++nsamp;
 #pragma unroll
             for (int j = 0; j < C; ++j) {
-                const Real ref = VAR ? tab[i0 + j < N ? i0 + j : N].ref
+                const Real ref = VAR ? tab[RowT::tpos(i0 + j)].ref
                                      : DIR ? fma(dref, Real(i0 + j) + half, wlo) : wlo;
                 const Real d = T[j] - ref;
                 sm1[j * 32] += d;
@@ -162,7 +164,7 @@ inline cudaError_t launch_layout(const Step1DArgs<Real>& a, cudaStream_t st)
     const dim3 block(kWarpsPerBlock1D * 32);
     const dim3 grid((warps + kWarpsPerBlock1D - 1) / kWarpsPerBlock1D);
     const int smem = kWarpsPerBlock1D * step1d_smem_per_warp<Real, C>() +
-                     (VAR ? (a.N + 1) * (int)sizeof(Coef1D<Real>) : 0) +
+                     (VAR ? (C * LPR + 1) * (int)sizeof(Coef1D<Real>) : 0) +
                      (IMP ? C * LPR * (int)sizeof(Solve1D<Real>) + LPR * LPR * (int)sizeof(Reduced1D<Real>) : 0);
     if (a.N == LPR * C) {
         auto k = k_step1d<Real, C, LPR, DIR, SP, false, MINB, PC, VAR, IMP>;
