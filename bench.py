@@ -30,11 +30,13 @@ UNIT = "cell-updates/s"
 # from the source algorithm (never from compiled code) and assigned to the
 # pipe the CUDA programming guide's throughput table puts them on; rates are
 # that table's results per clock per SM (FP32 add/multiply/FMA 128; 32-bit
-# integer multiply 64; 32-bit integer add, logic, compare and min/max 64;
-# transcendentals (MUFU) and 32-bit conversions 16), plus the issue limit of
-# one warp instruction per clock per SM sub-partition (4 x 32 lane-ops).
-# The bound is the slowest of these resources.
-PIPE_RATES = {"issue": 128.0, "fma": 128.0, "alu": 64.0, "imad": 64.0, "xu": 16.0}
+# integer multiply 64; 32-bit integer add, logic, compare, min/max and
+# conversions 64) except the transcendentals (MUFU), which run at 32 per clock
+# per SM on GB300 (twice the table's 16: Blackwell Ultra doubled the special
+# function units; the XU pipe counters of the covariance kernel's capture
+# agree), plus the issue limit of one warp instruction per clock per SM
+# sub-partition (4 x 32 lane-ops).  The bound is the slowest resource.
+PIPE_RATES = {"issue": 128.0, "fma": 128.0, "alu": 64.0, "imad": 64.0, "xu": 32.0}
 
 
 def noise_ops(nz):
@@ -42,19 +44,20 @@ def noise_ops(nz):
     rounds of two 32x32->64 products (hi and lo: 4 integer-multiply ops) and
     four xors (the round keys are precomputed per launch, so the key
     schedule's adds are not per-block work): 10 imad + 10 alu per normal.
-    Box-Muller per block: 4 integer-to-float conversions, 2 log2, 2 rsqrt,
-    2 sin, 2 cos (12 xu), 12 FP32 multiplies/FMAs (uniform scale, -2 ln 2,
-    radius, angle, the four products), 2 max and 2 sign-flip xors (4 alu):
-    per normal 3 xu, 3 fma, 1 alu."""
-    return {"imad": 10.0 * nz, "alu": 11.0 * nz, "xu": 3.0 * nz, "fma": 3.0 * nz}
+    Box-Muller per block: 2 log2, 2 rsqrt, 2 sin, 2 cos (8 xu), 4
+    integer-to-float conversions, 2 max and 2 sign-flip xors (8 alu), 12
+    FP32 multiplies/FMAs (uniform scale, -2 ln 2, radius, angle, the four
+    products): per normal 2 xu, 2 alu, 3 fma."""
+    return {"imad": 10.0 * nz, "alu": 12.0 * nz, "xu": 2.0 * nz, "fma": 3.0 * nz}
 
 
 def flux_ops(nf, species):
-    """Face fluxes: heat mean, amplitude, noise (3 fma); species mean,
-    product, x*rsqrt(x), noise (4 fma), clamp (1 alu), rsqrt (1 xu)."""
+    """Face fluxes: heat, the face sum T_l + T_r and its product with the
+    normal that carries the amplitude (2 fma); species mean, product,
+    x*rsqrt(x), noise (4 fma), clamp (1 alu), rsqrt (1 xu)."""
     if species:
         return {"fma": 4.0 * nf, "alu": 1.0 * nf, "xu": 1.0 * nf}
-    return {"fma": 3.0 * nf}
+    return {"fma": 2.0 * nf}
 
 
 def add_ops(*parts):
@@ -67,10 +70,10 @@ def add_ops(*parts):
     return out
 
 
-# cell update: 1D stencil and flux difference 5, 2D 9, 3D 11 FP32 ops;
-# the predictor-corrector's trapezoid (T + T* + inc) / 2: 3
-OPS_1D = add_ops(noise_ops(257.0 / 256.0), flux_ops(257.0 / 256.0, False), {"fma": 5.0})
-OPS_1D_PC = add_ops(noise_ops(257.0 / 256.0), flux_ops(2 * 257.0 / 256.0, False), {"fma": 2 * 5.0 + 3.0})
+# cell update: 1D with the face sums, (1 - 4 r) T + r (s_hi + s_lo) + G_hi - G_lo,
+# 4 FP32 ops; 2D 9, 3D 11; the predictor-corrector's trapezoid (T + T* + inc) / 2: 3
+OPS_1D = add_ops(noise_ops(257.0 / 256.0), flux_ops(257.0 / 256.0, False), {"fma": 4.0})
+OPS_1D_PC = add_ops(noise_ops(257.0 / 256.0), flux_ops(2 * 257.0 / 256.0, False), {"fma": 2 * 4.0 + 3.0})
 OPS_2D_SP = add_ops(noise_ops(2.0), flux_ops(2.0, True), {"fma": 9.0})
 OPS_2D_SP_PC = add_ops(noise_ops(2.0), flux_ops(4.0, True), {"fma": 2 * 9.0 + 3.0})
 OPS_3D = add_ops(noise_ops(3.0), flux_ops(3.0, False), {"fma": 11.0})
@@ -79,10 +82,10 @@ OPS_3D = add_ops(noise_ops(3.0), flux_ops(3.0, False), {"fma": 11.0})
 # correction by the neighbouring values (2) and the reduced solve (4 FMAs per
 # source lane per lane, LPR / C = 1/4 of a source lane per cell at 32 x 8: 1);
 # its factors are read from a shared-memory table
-OPS_1D_THETA = add_ops(noise_ops(257.0 / 256.0), flux_ops(257.0 / 256.0, False), {"fma": 5.0 + 6.0})
+OPS_1D_THETA = add_ops(noise_ops(257.0 / 256.0), flux_ops(257.0 / 256.0, False), {"fma": 4.0 + 6.0})
 # a rod of several materials: the update ic (a_hi (T_r - T) + a_lo (T_l - T) + dG) + T,
-# 6 FP32 ops, its coefficients read from a shared-memory table
-OPS_1D_VAR = add_ops(noise_ops(257.0 / 256.0), flux_ops(257.0 / 256.0, False), {"fma": 6.0})
+# 5 FP32 ops beyond the face sums, its coefficients read from a shared-memory table
+OPS_1D_VAR = add_ops(noise_ops(257.0 / 256.0), flux_ops(257.0 / 256.0, False), {"fma": 5.0})
 
 
 def pipe_roofline(ops, cu_per_s, sm_mhz, sms=152):

@@ -65,6 +65,41 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
+// B independent blocks at once, round by round (round-outer order: the B
+// chains interleave, and each round's key serves all of them); the same
+// results as B calls of philox4x32_10.
+template <int B>
+__device__ __forceinline__ void philox4x32_10_batch(uint4 (&c)[B], const RoundKeys& rk)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c[b].x;
+            const uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c[b].z;
+            c[b] = make_uint4((uint32_t)(p1 >> 32) ^ c[b].y ^ rk.k0[round], (uint32_t)p1,
+                              (uint32_t)(p0 >> 32) ^ c[b].w ^ rk.k1[round], (uint32_t)p0);
+        }
+    }
+}
+
+template <int B>
+__device__ __forceinline__ void philox4x32_10_batch(uint4 (&c)[B], uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c[b].x;
+            const uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c[b].z;
+            c[b] = make_uint4((uint32_t)(p1 >> 32) ^ c[b].y ^ k0, (uint32_t)p1,
+                              (uint32_t)(p0 >> 32) ^ c[b].w ^ k1, (uint32_t)p0);
+        }
+        k0 += kPhiloxW0;
+        k1 += kPhiloxW1;
+    }
+}
+
 // Four normals from one block, double precision: U = (u + 1/2) 2^-32,
 // z0,z1 = sqrt(-2 ln U(u0)) (cos, sin)(2 pi U(u1)); z2,z3 likewise (u2, u3).
 __device__ __forceinline__ void box_muller4(uint4 u, double z[4])
@@ -109,6 +144,40 @@ __device__ __forceinline__ void box_muller4(uint4 u, float z[4])
     z[1] = ra * sa;
     z[2] = rb * cb;
     z[3] = rb * sb;
+}
+
+// The same single-precision deviates times a factor a > 0, free of cost: the
+// radius sqrt(-2 ln U) a is sqrt(x') with x' = (-2 ln 2 a^2) log2 U, so a^2
+// goes into the constant c2 = -2 ln 2 a^2 that multiplies log2 U anyway (the
+// heat step takes the face noise amplitude this way).  c2 < 0.
+__device__ __forceinline__ void box_muller4_scaled(uint4 u, float c2, float z[4])
+{
+    const float scale = 2.3283064365386963e-10f;          // 2^-32
+    const float ang = 1.46291807926715968105e-09f;        // 2 pi 2^-32
+    const float ang0 = 7.31459039633579840525e-10f;       // pi 2^-32
+    float xa = c2 * __log2f(fmaf((float)u.x, scale, 0.5f * scale));
+    float xb = c2 * __log2f(fmaf((float)u.z, scale, 0.5f * scale));
+    xa = fmaxf(xa, 1e-30f);
+    xb = fmaxf(xb, 1e-30f);
+    const float ra = -(xa * rsqrtf(xa));
+    const float rb = -(xb * rsqrtf(xb));
+    const float ta = fmaf((float)(int32_t)(u.y ^ 0x80000000u), ang, ang0);
+    const float tb = fmaf((float)(int32_t)(u.w ^ 0x80000000u), ang, ang0);
+    float sa, ca, sb, cb;
+    __sincosf(ta, &sa, &ca);
+    __sincosf(tb, &sb, &cb);
+    z[0] = ra * ca;
+    z[1] = ra * sa;
+    z[2] = rb * cb;
+    z[3] = rb * sb;
+}
+
+// double precision: the deviates times a (one product each)
+__device__ __forceinline__ void box_muller4_scaled(uint4 u, double a, double z[4])
+{
+    box_muller4(u, z);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) z[k] *= a;
 }
 
 }  // namespace she

@@ -96,6 +96,9 @@ struct Row1D {
     Real wz[4];
     uint32_t wwin;
     const Coef1D<Real>* cf = nullptr;   // VAR: the material table
+    Real a4;                            // heat: 1 - 4 r (the centre weight of step_heat)
+    Real ncoef;                         // heat: the noise factor s_half (FP32: -2 ln 2 s_half^2)
+    Real gl_heat;                       // heat: 2 sqrt(2) T_L, the left wall face's flux per scaled normal
 
     // per-row problem: cells, diffusion number, squared noise amplitude per
     // unit face value (2 r eps), wall values, noise stream and key
@@ -124,6 +127,12 @@ struct Row1D {
         stochastic = stochastic_;
         wz[0] = wz[1] = wz[2] = wz[3] = Real(0);
         wwin = 0xffffffffu;
+        a4 = Real(1) - Real(4) * r;
+        gl_heat = Real(2.82842712474619009760) * wlo;
+        if constexpr (sizeof(Real) == 4) ncoef = Real(-1.38629436111989061883) * s_half * s_half;
+        else ncoef = s_half;
+        if (!SPECIES && !(s_half > Real(0)) && !(g_wall_amp > Real(0)) && !(g_low_amp > Real(0)))
+            stochastic = 0;   // no noise at all (k_B = 0): none is drawn
     }
 
     __device__ __forceinline__ void init(const Step1DArgs<Real>& a, int sl, int rho)
@@ -266,11 +275,107 @@ struct Row1D {
         }
     }
 
+    // advance the row T of a uniform heat rod by the forward-Euler step with
+    // absolute index n, the update of step() rewritten with the face sums
+    // s_f = T_l + T_r:  r (T_{i+1} - 2 T_i + T_{i-1}) = r (s_hi + s_lo) - 4 r T_i
+    // (a Dirichlet wall's ghost 2 T_wall - T_edge makes s_wall = 2 T_wall), so
+    // T_i' = (1 - 4 r) T_i + r (s_hi + s_lo) + G_hi - G_lo, and the face flux
+    // G_f = s_half s_f N_f with s_half folded into the normals (one product
+    // per face, four operations per cell)
+    __device__ __forceinline__ void step_heat(Real (&T)[C], uint32_t n)
+    {
+        const Real left_nb = __shfl_up_sync(FULL, T[C - 1], 1, LPR);
+        const Real right_nb = __shfl_down_sync(FULL, T[0], 1, LPR);
+        Real wrap_lo = Real(0), wrap_hi = Real(0);   // periodic: T_{N-1}, T_0
+        if (!DIR) {
+            Real mine = T[C - 1];
+            if (RAGGED) {
+#pragma unroll
+                for (int j = 0; j < C; ++j)
+                    if (j == jlast) mine = T[j];
+            }
+            wrap_lo = __shfl_sync(FULL, mine, last_sl, LPR);
+            wrap_hi = __shfl_sync(FULL, T[0], 0, LPR);
+        }
+        const Real g_high = high_wall_flux(n);
+        // the lane's C / 4 Philox blocks together, round by round, then their
+        // normals: independent chains side by side for the scheduler
+        Real zz[C];
+        if (stochastic) {
+            uint4 blk[C / 4];
+#pragma unroll
+            for (int g = 0; g < C / 4; ++g) blk[g] = make_uint4(q0 + (uint32_t)g, n, stream, 0u);
+            if constexpr (RK) philox4x32_10_batch<C / 4>(blk, *rk);
+            else philox4x32_10_batch<C / 4>(blk, key0, key1);
+#pragma unroll
+            for (int g = 0; g < C / 4; ++g) {
+                Real v[4];
+                box_muller4_scaled(blk[g], ncoef, v);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) zz[4 * g + t] = v[t];
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < C; ++j) zz[j] = Real(0);
+        }
+        Real g_first = Real(0), g_prev = Real(0), g_zero = Real(0);
+        Real s_prev = Real(0);
+        Real old_cur = T[0];
+#pragma unroll
+        for (int g = 0; g < C / 4; ++g) {
+            const Real* z = zz + 4 * g;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int j = 4 * g + t;
+                if (j == 0) {
+                    // face i0: between cell i0-1 (neighbour lane, or wall/wrap) and i0
+                    Real s0 = left_nb + T[0];
+                    Real g0;
+                    if (first_sl) s0 = DIR ? Real(2) * wlo : wrap_lo + T[0];
+                    g0 = s0 * z[0];
+                    if (DIR && first_sl) g0 = gl_heat * z[0];   // sqrt(2) s_half 2 T_L N_0
+                    g_first = g0;
+                    if (!DIR) g_zero = __shfl_sync(FULL, g_first, 0, LPR);
+                    s_prev = s0;
+                    g_prev = g0;
+                } else {
+                    Real sf = old_cur + T[j];
+                    Real gf = sf * z[t];
+                    if (RAGGED && i0 + j == N) {            // ragged lane: the high face
+                        sf = DIR ? Real(2) * whi : old_cur + wrap_hi;
+                        gf = DIR ? g_high : g_zero;
+                    }
+                    const Real tc = old_cur;
+                    old_cur = T[j];
+                    T[j - 1] = fma(a4, tc, fma(r, s_prev + sf, gf) - g_prev);
+                    s_prev = sf;
+                    g_prev = gf;
+                }
+            }
+        }
+        // last cell of the lane: its high face is the neighbour lane's first
+        // face, or the wall/wrap face when it is cell N-1
+        {
+            const Real g_next = __shfl_down_sync(FULL, g_first, 1, LPR);
+            const Real tc = old_cur;
+            Real sr = tc + right_nb;
+            Real gr = g_next;
+            if ((!RAGGED && tail_sl) || (RAGGED && i0 + C - 1 == N - 1)) {
+                sr = DIR ? Real(2) * whi : tc + wrap_hi;
+                gr = DIR ? g_high : g_zero;
+            }
+            T[C - 1] = fma(a4, tc, fma(r, s_prev + sr, gr) - g_prev);
+        }
+    }
+
     // advance the row T by the forward-Euler step with absolute index n
     __device__ __forceinline__ void step(Real (&T)[C], uint32_t n)
     {
         if constexpr (VAR) {
             step_var(T, n);
+            return;
+        } else if constexpr (!SPECIES) {
+            step_heat(T, n);
             return;
         }
         const Real left_nb = __shfl_up_sync(FULL, T[C - 1], 1, LPR);

@@ -88,6 +88,7 @@ struct Step1DArgs {
     long long tc_s0;      // samples taken before this launch (since the last reset)
     long long tc_base;    // sample index of the last state overwrite: pairs never reach
                           // back past it (the trajectory before it is another one)
+    int tc_onchip;        // 1: lag sums in per-warp shared-memory partials, flushed per launch
     Real* tc_ring;        // [R][tc_lags][N] the last tc_lags samples of delta (sample s in slot s % L)
     double* tc_acc;       // [R][tc_lags][N] sum of delta_i(s) delta_i(s - l)
     const Coef1D<Real>* coef;   // [N + 1] material table of a rod of several materials (else null)

@@ -259,8 +259,15 @@ static cudaError_t launch_fused(Handle& h, uint32_t step0, int nsteps)
     a.tc_ring = (Real*)h.d_tc_ring;
     a.tc_acc = h.d_tc_acc;
     a.coef = (const Coef1D<Real>*)h.d_coef;
+    a.tc_onchip = 0;
     const bool dir = h.prob.bc == SHE_DIRICHLET;
     const bool sp = h.prob.equation == SHE_SPECIES;
+    // the time correlation's lag sums go to per-warp shared-memory partials
+    // when they fit (4 warps x L x C x 32 values within 64 KB)
+    auto tc_fits = [&](int layout) {
+        const int C = layout / 100;
+        return h.tc_lags > 0 && kWarpsPerBlock1D * h.tc_lags * C * 32 * (int)sizeof(Real) <= 64 * 1024;
+    };
     if (h.prob.scheme == SHE_BE || h.prob.scheme == SHE_CN) {
         const double theta = h.prob.scheme == SHE_BE ? 1.0 : 0.5;
         a.solve = (const Solve1D<Real>*)h.d_solve;
@@ -271,6 +278,7 @@ static cudaError_t launch_fused(Handle& h, uint32_t step0, int nsteps)
         a.sm_cg = (Real)h.sm_cg;
         a.sm_inv = (Real)h.sm_inv;
         const int layout = h.imp_layout;
+        a.tc_onchip = tc_fits(layout) ? 1 : 0;
         if (dir) return sp ? launch_step1d_theta<Real, true, true>(a, layout, h.stream)
                            : launch_step1d_theta<Real, true, false>(a, layout, h.stream);
         return sp ? launch_step1d_theta<Real, false, true>(a, layout, h.stream)
@@ -278,6 +286,7 @@ static cudaError_t launch_fused(Handle& h, uint32_t step0, int nsteps)
     }
     if (h.prob.scheme == SHE_PC) {
         const int layout = pick_layout_pc(a.N);
+        a.tc_onchip = tc_fits(layout) ? 1 : 0;
         if (h.var)         // a rod of several materials (heat)
             return dir ? launch_step1d_variant<Real, true, false, true, true>(a, layout, h.stream)
                        : launch_step1d_variant<Real, false, false, true, true>(a, layout, h.stream);
@@ -288,7 +297,11 @@ static cudaError_t launch_fused(Handle& h, uint32_t step0, int nsteps)
         if (sp) return launch_step1d_variant<Real, false, true, true, false>(a, layout, h.stream);
         return launch_step1d_variant<Real, false, false, true, false>(a, layout, h.stream);
     }
-    const int layout = pick_layout(a.N);
+    int layout = pick_layout(a.N);
+    // with the time correlation, at most 16 cells per lane so that its
+    // partials fit beside the moments at two blocks per SM
+    if (h.tc_lags > 0 && layout / 100 > 16) layout = a.N <= 256 ? 1616 : a.N <= 512 ? 1632 : layout;
+    a.tc_onchip = tc_fits(layout) ? 1 : 0;
     if (h.var)
         return dir ? launch_step1d_variant<Real, true, false, false, true>(a, layout, h.stream)
                    : launch_step1d_variant<Real, false, false, false, true>(a, layout, h.stream);

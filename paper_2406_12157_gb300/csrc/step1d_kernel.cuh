@@ -62,6 +62,13 @@ k_step1d(const __grid_constant__ Step1DArgs<Real> a)
 
     Real* sm1 = reinterpret_cast<Real*>(smem_raw) + (threadIdx.x >> 5) * (2 * C * 32) + lane;
     Real* sm2 = sm1 + C * 32;
+    // time correlation on chip: per warp [L][C][32] partial lag sums after
+    // the tables (lane-contiguous like the moments)
+    constexpr int kTabBytes = (VAR ? (C * LPR + 1) * (int)sizeof(Coef1D<Real>) : 0) +
+                              (IMP ? C * LPR * (int)sizeof(Solve1D<Real>) + LPR * LPR * (int)sizeof(Reduced1D<Real>) : 0);
+    Real* tcp = reinterpret_cast<Real*>(smem_raw + (size_t)kWarpsPerBlock1D * step1d_smem_per_warp<Real, C>() +
+                                        kTabBytes) +
+                (size_t)(threadIdx.x >> 5) * a.tc_lags * C * 32 + lane;
 
     RowT rowst;
     rowst.init(a, sl, rho);
@@ -77,6 +84,8 @@ k_step1d(const __grid_constant__ Step1DArgs<Real> a)
         sm1[j * 32] = Real(0);
         sm2[j * 32] = Real(0);
     }
+    if (a.tc_onchip)
+        for (int k = 0; k < a.tc_lags * C; ++k) tcp[k * 32] = Real(0);
     const Real half = Real(0.5);
     const Real wlo = a.wall_lo;
     const Real dref = DIR ? (a.wall_hi - a.wall_lo) / Real(N) : Real(0);
@@ -94,8 +103,10 @@ k_step1d(const __grid_constant__ Step1DArgs<Real> a)
             if (a.tc_lags > 0 && active) {
                 // time correlation (the exercise on <dT_i^{n+m} dT_i^n>, Sec. 6):
                 // store this sample of delta in the realization's ring, then add
-                // delta_i(s) delta_i(s - l) for every lag l with a partner; each
-                // element has one writer, so the fire-and-forget adds are exact
+                // delta_i(s) delta_i(s - l) for every lag l with a partner, into
+                // the warp's shared-memory partials (flushed at launch end) or,
+                // where they do not fit, straight into the FP64 sums (one writer
+                // per element, so the fire-and-forget adds are exact)
                 const int L = a.tc_lags;
                 const long long st = a.tc_s0 + nsamp;
                 Real* ring = a.tc_ring + (size_t)rho * (size_t)L * (size_t)N;
@@ -110,10 +121,18 @@ k_step1d(const __grid_constant__ Step1DArgs<Real> a)
                     const Real ref = VAR ? tab[RowT::tpos(i)].ref : DIR ? fma(dref, Real(i0 + j) + half, wlo) : wlo;
                     const Real d = T[j] - ref;
                     ring[(size_t)slot * N + i] = d;
-                    atomicAdd(&acc[i], (double)(d * d));
-                    for (int l = 1; l <= lmax; ++l) {
-                        const Real prev = ring[(size_t)((st - l) % L) * N + i];
-                        atomicAdd(&acc[(size_t)l * N + i], (double)(d * prev));
+                    if (a.tc_onchip) {
+                        tcp[j * 32] = fma(d, d, tcp[j * 32]);
+                        for (int l = 1; l <= lmax; ++l) {
+                            const Real prev = ring[(size_t)((st - l) % L) * N + i];
+                            tcp[(l * C + j) * 32] = fma(d, prev, tcp[(l * C + j) * 32]);
+                        }
+                    } else {
+                        atomicAdd(&acc[i], (double)(d * d));
+                        for (int l = 1; l <= lmax; ++l) {
+                            const Real prev = ring[(size_t)((st - l) % L) * N + i];
+                            atomicAdd(&acc[(size_t)l * N + i], (double)(d * prev));
+                        }
                     }
                 }
             }
@@ -150,6 +169,15 @@ k_step1d(const __grid_constant__ Step1DArgs<Real> a)
                     atomicAdd(&p2[i], (double)sm2[j * 32]);
                 }
             }
+            if (a.tc_onchip) {
+                double* acc = a.tc_acc + (size_t)rho * (size_t)a.tc_lags * (size_t)N;
+                for (int l = 0; l < a.tc_lags; ++l)
+#pragma unroll
+                    for (int j = 0; j < C; ++j) {
+                        const int i = i0 + j;
+                        if (!RAGGED || i < N) atomicAdd(&acc[(size_t)l * N + i], (double)tcp[(l * C + j) * 32]);
+                    }
+            }
         }
     }
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.flags, 1);
@@ -165,7 +193,8 @@ inline cudaError_t launch_layout(const Step1DArgs<Real>& a, cudaStream_t st)
     const dim3 grid((warps + kWarpsPerBlock1D - 1) / kWarpsPerBlock1D);
     const int smem = kWarpsPerBlock1D * step1d_smem_per_warp<Real, C>() +
                      (VAR ? (C * LPR + 1) * (int)sizeof(Coef1D<Real>) : 0) +
-                     (IMP ? C * LPR * (int)sizeof(Solve1D<Real>) + LPR * LPR * (int)sizeof(Reduced1D<Real>) : 0);
+                     (IMP ? C * LPR * (int)sizeof(Solve1D<Real>) + LPR * LPR * (int)sizeof(Reduced1D<Real>) : 0) +
+                     (a.tc_onchip ? kWarpsPerBlock1D * a.tc_lags * C * 32 * (int)sizeof(Real) : 0);
     if (a.N == LPR * C) {
         auto k = k_step1d<Real, C, LPR, DIR, SP, false, MINB, PC, VAR, IMP>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
