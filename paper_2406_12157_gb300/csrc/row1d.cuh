@@ -167,6 +167,29 @@ struct Row1D {
         else return philox4x32_10(ctr, key0, key1);
     }
 
+    // the C normals of the lane's faces at step n (C / 4 Philox blocks run
+    // together, round by round), or zeros without noise
+    __device__ __forceinline__ void draw_normals(uint32_t n, Real (&z)[C]) const
+    {
+        if (!stochastic) {
+#pragma unroll
+            for (int j = 0; j < C; ++j) z[j] = Real(0);
+            return;
+        }
+        uint4 blk[C / 4];
+#pragma unroll
+        for (int g = 0; g < C / 4; ++g) blk[g] = make_uint4(q0 + (uint32_t)g, n, stream, 0u);
+        if constexpr (RK) philox4x32_10_batch<C / 4>(blk, *rk);
+        else philox4x32_10_batch<C / 4>(blk, key0, key1);
+#pragma unroll
+        for (int g = 0; g < C / 4; ++g) {
+            Real v[4];
+            box_muller4(blk[g], v);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) z[4 * g + t] = v[t];
+        }
+    }
+
     __device__ __forceinline__ Real flux(Real lo, Real hi, Real z) const
     {
         if (SPECIES) {
@@ -227,13 +250,11 @@ struct Row1D {
         Real old_prev = left_nb;
         if (first_sl) old_prev = DIR ? Real(2) * wlo - T[0] : wrap_lo;
         Real old_cur = T[0];
+        Real zz[C];
+        draw_normals(n, zz);
 #pragma unroll
         for (int g = 0; g < C / 4; ++g) {
-            Real z[4] = {Real(0), Real(0), Real(0), Real(0)};
-            if (stochastic) {
-                const uint4 u = noise_block(make_uint4(q0 + (uint32_t)g, n, stream, 0u));
-                box_muller4(u, z);
-            }
+            const Real* z = zz + 4 * g;
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 const int j = 4 * g + t;
@@ -400,13 +421,11 @@ struct Row1D {
         Real old_prev = left_nb;
         if (first_sl) old_prev = DIR ? Real(2) * wlo - T[0] : wrap_lo;
         Real old_cur = T[0];
+        Real zz[C];
+        draw_normals(n, zz);
 #pragma unroll
         for (int g = 0; g < C / 4; ++g) {
-            Real z[4] = {Real(0), Real(0), Real(0), Real(0)};
-            if (stochastic) {
-                const uint4 u = noise_block(make_uint4(q0 + (uint32_t)g, n, stream, 0u));
-                box_muller4(u, z);
-            }
+            const Real* z = zz + 4 * g;
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 const int j = 4 * g + t;
@@ -569,13 +588,7 @@ struct Row1D {
     __device__ __forceinline__ void step_pc(Real (&T)[C], uint32_t n)
     {
         Real z[C];
-#pragma unroll
-        for (int g = 0; g < C / 4; ++g) {
-            Real v[4] = {Real(0), Real(0), Real(0), Real(0)};
-            if (stochastic) box_muller4(noise_block(make_uint4(q0 + (uint32_t)g, n, stream, 0u)), v);
-#pragma unroll
-            for (int t = 0; t < 4; ++t) z[4 * g + t] = v[t];
-        }
+        draw_normals(n, z);
         const Real g_high = high_wall_flux(n);
         Real Ts[C], inc[C];
         increment(T, z, g_high, inc);
@@ -604,13 +617,7 @@ struct Row1D {
                                                Real cg, Real inv_den)
     {
         Real z[C];
-#pragma unroll
-        for (int g = 0; g < C / 4; ++g) {
-            Real v[4] = {Real(0), Real(0), Real(0), Real(0)};
-            if (stochastic) box_muller4(noise_block(make_uint4(q0 + (uint32_t)g, n, stream, 0u)), v);
-#pragma unroll
-            for (int t = 0; t < 4; ++t) z[4 * g + t] = v[t];
-        }
+        draw_normals(n, z);
         const Real g_high = high_wall_flux(n);
         Real x[C];
         increment_rate(T, z, g_high, x, r * omt);

@@ -114,25 +114,50 @@ k_step1d(const __grid_constant__ Step1DArgs<Real> a)
                 const int slot = (int)(st % L);
                 const long long since = st - a.tc_base;   // samples of this trajectory before st
                 const int lmax = since < (long long)(L - 1) ? (int)since : L - 1;
+                Real d[C];
 #pragma unroll
                 for (int j = 0; j < C; ++j) {
                     const int i = i0 + j;
-                    if (RAGGED && i >= N) continue;
                     const Real ref = VAR ? tab[RowT::tpos(i)].ref : DIR ? fma(dref, Real(i0 + j) + half, wlo) : wlo;
-                    const Real d = T[j] - ref;
-                    ring[(size_t)slot * N + i] = d;
-                    if (a.tc_onchip) {
-                        tcp[j * 32] = fma(d, d, tcp[j * 32]);
-                        for (int l = 1; l <= lmax; ++l) {
-                            const Real prev = ring[(size_t)((st - l) % L) * N + i];
-                            tcp[(l * C + j) * 32] = fma(d, prev, tcp[(l * C + j) * 32]);
-                        }
+                    d[j] = (RAGGED && i >= N) ? Real(0) : T[j] - ref;
+                }
+                // the lane's C cells are contiguous: 16-byte moves when the
+                // ring rows are aligned (N a multiple of 4, a full row)
+                const bool vec = !RAGGED && (N % 4 == 0);
+                Real* srow = ring + (size_t)slot * N + i0;
+                if (vec) {
+                    vstore<C>(srow, d);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < C; ++j)
+                        if (!RAGGED || i0 + j < N) srow[j] = d[j];
+                }
+                if (a.tc_onchip) {
+#pragma unroll
+                    for (int j = 0; j < C; ++j) tcp[j * 32] = fma(d[j], d[j], tcp[j * 32]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < C; ++j)
+                        if (!RAGGED || i0 + j < N) atomicAdd(&acc[i0 + j], (double)(d[j] * d[j]));
+                }
+                int ps = slot;                            // slot of sample st - l, (st - l) % L
+                for (int l = 1; l <= lmax; ++l) {
+                    ps = ps == 0 ? L - 1 : ps - 1;
+                    const Real* prow = ring + (size_t)ps * N + i0;
+                    Real pv[C];
+                    if (vec) {
+                        vload<C>(prow, pv);
                     } else {
-                        atomicAdd(&acc[i], (double)(d * d));
-                        for (int l = 1; l <= lmax; ++l) {
-                            const Real prev = ring[(size_t)((st - l) % L) * N + i];
-                            atomicAdd(&acc[(size_t)l * N + i], (double)(d * prev));
-                        }
+#pragma unroll
+                        for (int j = 0; j < C; ++j) pv[j] = (!RAGGED || i0 + j < N) ? prow[j] : Real(0);
+                    }
+                    if (a.tc_onchip) {
+#pragma unroll
+                        for (int j = 0; j < C; ++j) tcp[(l * C + j) * 32] = fma(d[j], pv[j], tcp[(l * C + j) * 32]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < C; ++j)
+                            if (!RAGGED || i0 + j < N) atomicAdd(&acc[(size_t)l * N + i0 + j], (double)(d[j] * pv[j]));
                     }
                 }
             }
