@@ -514,6 +514,22 @@ def run_ours(args):
         if e.status != she._abi.SHE_ERR_STATE:   # no sample yet in a short run is fine
             raise
 
+    # ---- replicas: every rank's raw accumulators summed (one all-reduce, the
+    # method's only exchange) and finalised by the library on rank 0 ----
+    merged = None
+    if dist is not None and not batch:
+        from paper_2406_12157_gb300 import replica
+        try:
+            total = replica.allreduce_raw(sim.stats_raw())
+            if rank == 0:
+                fin = replica.finalize(sim.params, total, cov=bool(p.get("want_cov")))
+                merged = {"n_samples": fin["n_samples"], "ranks": world,
+                          "mean_var": float(np.mean(fin["var"])),
+                          "max_var_se_rel": float(np.nanmax(fin["var_se"] / fin["var"]))}
+        except she.SheError as e:
+            if e.status != she._abi.SHE_ERR_STATE:
+                raise
+
     # ---- FP64 plain form on the same workload, a bounded number of steps ----
     plain_steps = max(10, min(2000, int(2e8 // (R * cells))))
     p64 = dict(p)
@@ -608,6 +624,7 @@ def run_ours(args):
                        "form": "plain FP64 (3 launches/step)" if kind64 == "plain" else "same kernel in FP64",
                        "speedup_fp32_batched": value / world / plain_rate},
         "workloads": legs or None,
+        "replica_merge": merged,
         "wall_s": t_wall,
     }
     print(json.dumps(line))

@@ -214,7 +214,37 @@ typedef struct she_sizes {
     int64_t axes_len;     /* n[0] + n[1] + n[2] over used axes */
     uint64_t step;        /* absolute steps taken so far */
     int64_t tc_lags;      /* lags of the time correlation (0: not accumulated) */
+    int64_t batches;      /* realization batches B of she_raw's per-batch sums */
+    int64_t sk_raw_len;   /* she_raw.sk_sum length: ny (nx/2 + 1) for the 2D full S(k), else 0 */
+    int64_t axes_raw_len; /* she_raw.axes_sum length: sum over used axes of n_a^2 (SHE_SK_AXES), else 0 */
 } she_sizes;
+
+/*
+ * The raw FP64 accumulators behind she_stats, pooled over realizations and
+ * sampling times.  Every member is a sum (or a count), so the blocks of
+ * independent replicas -- disjoint realization ranges of one ensemble run by
+ * separate handles or processes (stream_offset) -- merge by element-wise
+ * addition, and she_finalize turns any such block into the statistics of a
+ * she_stats_out: Eq. (3.9)-(3.13), S(k) of Eq. (3.11), the time correlation
+ * of the Sec. 6 exercise.  The caller allocates every non-NULL array
+ * (sizes from she_get_sizes); NULL arrays are skipped (she_stats_raw) or
+ * mean "not available" (she_finalize).
+ */
+typedef struct she_raw {
+    int64_t n_samples;    /* pooled samples n (realizations x sampling times) */
+    int64_t batches;      /* B (she_sizes.batches); batch b holds realizations
+                             [R b / B, R (b + 1) / B) of the handle */
+    int64_t* batch_n;     /* [B] samples pooled in batch b */
+    double* batch_sum_d;  /* [B][cells] sum of delta = T - T_ref over batch b */
+    double* batch_sum_d2; /* [B][cells] sum of delta^2 over batch b */
+    double* sum_dd;       /* [cells][cells] sum of delta delta^T (want_cov) */
+    double* sk_sum;       /* [ny][nx/2 + 1] (kx fastest) sum of |hat delta_k|^2 of
+                             the 2D full S(k), kx <= nx/2 (the rest by symmetry) */
+    double* axes_sum;     /* per used axis a, [n_a][n_a] sum over lines along a of
+                             delta_line delta_line^T, axes back to back */
+    double* tc_sum;       /* [tc_lags][cells] sum of delta_i(s) delta_i(s - l) */
+    int64_t* tc_pairs;    /* [tc_lags] pooled pairs l sampling intervals apart */
+} she_raw;
 
 /*
  * Validate `p` and create a handle: allocates the state [realizations][cells]
@@ -253,6 +283,23 @@ she_status she_get_sizes(const she_handle* h, she_sizes* s);
  * untouched), SHE_ERR_INVALID_ARG if cov/sk are requested but were not
  * enabled at init, SHE_ERR_NONFINITE if the state became non-finite. */
 she_status she_stats(she_handle* h, she_stats_out* out);
+
+/* Copy the raw accumulators into the caller's arrays of `out` (reduced over
+ * the realizations of each batch on the device; synchronises the stream).
+ * A statistic requested (non-NULL array) that was not enabled at init is
+ * SHE_ERR_INVALID_ARG; n_samples = 0 (nothing sampled yet) is valid.
+ * Errors: SHE_ERR_INVALID_ARG, SHE_ERR_NONFINITE, SHE_ERR_TIMEOUT,
+ * SHE_ERR_CUDA. */
+she_status she_stats_raw(she_handle* h, she_raw* out);
+
+/* Host-only (no device, no handle): the statistics of she_stats_out from a
+ * raw block of the problem `p` (its grid, boundary, walls and materials give
+ * T_ref), e.g. the element-wise sum of the raw blocks of several replicas.
+ * she_stats is she_stats_raw followed by this.  Single problems only (not a
+ * batch of instances).  Errors: SHE_ERR_INVALID_ARG (bad p or arrays, a
+ * statistic requested whose raw sums are NULL), SHE_ERR_UNSTABLE (p as
+ * she_init), SHE_ERR_STATE (n_samples = 0). */
+she_status she_finalize(const she_params* p, const she_raw* raw, she_stats_out* out);
 
 /* Zero every accumulator (the state and step counter are kept). */
 she_status she_reset_stats(she_handle* h);

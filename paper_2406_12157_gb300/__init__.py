@@ -23,7 +23,7 @@ __all__ = ["SheError", "LibraryMissing", "params_from_problem", "she_init", "she
            "she_step_n", "she_get_sizes", "she_stats", "she_reset_stats", "she_get_state",
            "she_set_state", "she_get_state_device", "she_set_state_device", "she_last_error",
            "she_free", "she_noise_probe", "she_launch_count", "she_syrk_probe", "she_profile",
-           "she_profile_read", "Simulation", "BatchSimulation", "lib"]
+           "she_profile_read", "she_stats_raw", "she_finalize", "Simulation", "BatchSimulation", "lib"]
 
 
 class SheError(RuntimeError):
@@ -112,6 +112,7 @@ def params_from_problem(prob, stream=None, **overrides):
 def she_init(params):
     h = ctypes.c_void_p()
     _check(lib().she_init(ctypes.byref(params), ctypes.byref(h)), None, "she_init")
+    _HANDLE_FLAGS[h.value] = {"cov": bool(params.want_cov) or (int(params.dim) == 1 and bool(params.want_sk & 1))}
     return h
 
 
@@ -166,6 +167,88 @@ def she_stats(h, cov=False, sk=False, sk_axes=False, raw=False, time_corr=False)
     return out
 
 
+_RAW_KEYS = ("batch_n", "batch_sum_d", "batch_sum_d2", "sum_dd", "sk_sum", "axes_sum", "tc_sum", "tc_pairs")
+
+
+def _raw_struct(raw):
+    st = _abi.she_raw()
+    st.n_samples = int(raw["n_samples"])
+    st.batches = int(raw["batches"])
+    for k in _RAW_KEYS:
+        v = raw.get(k)
+        if v is None:
+            continue
+        if k in ("batch_n", "tc_pairs"):
+            setattr(st, k, v.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+        else:
+            setattr(st, k, _ptr(v))
+    return st
+
+
+def she_stats_raw(h):
+    """The raw FP64 accumulators (see she_raw in she.h) as numpy arrays:
+    every entry a sum or a count, so replicas merge by addition."""
+    s = she_get_sizes(h)
+    c, B, L = int(s.cells), int(s.batches), int(s.tc_lags)
+    out = {"batch_n": np.empty(B, dtype=np.int64), "batch_sum_d": np.empty(B * c),
+           "batch_sum_d2": np.empty(B * c)}
+    if _stats_flags(h)["cov"]:
+        out["sum_dd"] = np.empty(c * c)
+    if s.sk_raw_len:
+        out["sk_sum"] = np.empty(int(s.sk_raw_len))
+    if s.axes_raw_len:
+        out["axes_sum"] = np.empty(int(s.axes_raw_len))
+    if L:
+        out["tc_sum"] = np.empty(L * c)
+        out["tc_pairs"] = np.empty(L, dtype=np.int64)
+    out["n_samples"] = 0
+    out["batches"] = B
+    st = _raw_struct(out)
+    _check(lib().she_stats_raw(h, ctypes.byref(st)), h, "she_stats_raw")
+    out["n_samples"] = int(st.n_samples)
+    return out
+
+
+def _stats_flags(h):
+    # whether the handle accumulates the covariance: probe with a NULL-free
+    # request is not possible, so the binding remembers it per handle
+    return _HANDLE_FLAGS.get(h.value, {"cov": False})
+
+
+_HANDLE_FLAGS = {}
+
+
+def she_finalize(params, raw, cov=False, sk=False, sk_axes=False, time_corr=False):
+    """Statistics (as she_stats) of the problem `params` from a raw block,
+    e.g. the sum of several replicas' she_stats_raw blocks.  Host only."""
+    p = params
+    c = 1
+    for a in range(int(p.dim)):
+        c *= int(p.n[a])
+    out = {k: np.empty(c) for k in ("mean", "var", "var_se", "sum_d", "sum_d2")}
+    if cov:
+        out["cov"] = np.empty(c * c)
+    if sk:
+        out["sk"] = np.empty(c)
+        out["sk_fluct"] = np.empty(c)
+    if sk_axes:
+        out["sk_axes"] = np.empty(sum(int(p.n[a]) for a in range(int(p.dim))))
+    L = int(p.tc_lags)
+    if time_corr and L > 0:
+        out["time_corr"] = np.empty(L * c)
+    st = _abi.she_stats_out()
+    for k, v in out.items():
+        setattr(st, k, _ptr(v))
+    rs = _raw_struct(raw)
+    _check(lib().she_finalize(ctypes.byref(p), ctypes.byref(rs), ctypes.byref(st)), None, "she_finalize")
+    out["n_samples"] = int(st.n_samples)
+    if cov:
+        out["cov"] = out["cov"].reshape(c, c)
+    if "time_corr" in out:
+        out["time_corr"] = out["time_corr"].reshape(L, c)
+    return out
+
+
 def she_reset_stats(h):
     _check(lib().she_reset_stats(h), h, "she_reset_stats")
 
@@ -203,6 +286,7 @@ def she_last_error(h):
 
 def she_free(h):
     if h is not None and h.value:
+        _HANDLE_FLAGS.pop(h.value, None)
         lib().she_free(h)
         h.value = None
 
@@ -312,6 +396,9 @@ class Simulation:
 
     def stats(self, **kw):
         return she_stats(self.h, **kw)
+
+    def stats_raw(self):
+        return she_stats_raw(self.h)
 
     def state(self):
         return she_get_state(self.h)

@@ -40,7 +40,7 @@ EXPORTS = ["she_init", "she_init_batch", "she_step_n", "she_get_sizes", "she_sta
            "she_reset_stats", "she_get_state", "she_set_state", "she_get_state_device",
            "she_set_state_device", "she_last_error", "she_free", "she_noise_probe",
            "she_launch_count", "she_syrk_probe", "she_step_plain_noalloc", "she_wait_probe",
-           "she_profile", "she_profile_read"]
+           "she_profile", "she_profile_read", "she_stats_raw", "she_finalize"]
 
 
 class she_params(ctypes.Structure):
@@ -108,6 +108,27 @@ class she_sizes(ctypes.Structure):
         ("axes_len", ctypes.c_int64),
         ("step", ctypes.c_uint64),
         ("tc_lags", ctypes.c_int64),
+        ("batches", ctypes.c_int64),
+        ("sk_raw_len", ctypes.c_int64),
+        ("axes_raw_len", ctypes.c_int64),
+    ]
+
+
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+class she_raw(ctypes.Structure):
+    _fields_ = [
+        ("n_samples", ctypes.c_int64),
+        ("batches", ctypes.c_int64),
+        ("batch_n", _i64p),
+        ("batch_sum_d", _dp),
+        ("batch_sum_d2", _dp),
+        ("sum_dd", _dp),
+        ("sk_sum", _dp),
+        ("axes_sum", _dp),
+        ("tc_sum", _dp),
+        ("tc_pairs", _i64p),
     ]
 
 
@@ -172,6 +193,10 @@ def load(path=None):
     L.she_profile_read.argtypes = [H, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
     L.she_profile_read.restype = ctypes.c_int
+    L.she_stats_raw.argtypes = [H, ctypes.POINTER(she_raw)]
+    L.she_stats_raw.restype = ctypes.c_int
+    L.she_finalize.argtypes = [ctypes.POINTER(she_params), ctypes.POINTER(she_raw), ctypes.POINTER(she_stats_out)]
+    L.she_finalize.restype = ctypes.c_int
     if path is None:
         _LIB = L
     return L

@@ -359,6 +359,307 @@ cudaError_t noalloc_scratch(double** out)
     return cudaSuccess;
 }
 
+// ------------------------------------------------------------- statistics --
+
+// What the finalisation needs of a problem: the grid, T_ref per cell (the
+// linear profile, a material rod's steady profile, the uniform value, or a
+// batch's profiles back to back) and the time correlation's lags.
+struct FinInfo {
+    int dim = 1;
+    int n[3] = {1, 1, 1};
+    int64_t cells = 0;
+    std::vector<double> ref;
+    double ref_uniform = 0.0;     // a periodic grid's T_ref (its only Fourier mode is k = 0)
+    int L = 0;
+};
+
+FinInfo fin_info(const Handle& h)
+{
+    FinInfo fi;
+    fi.dim = h.prob.dim;
+    for (int a = 0; a < 3; ++a) fi.n[a] = h.prob.n[a];
+    fi.cells = h.prob.cells;
+    fi.L = h.tc_lags;
+    fi.ref_uniform = h.prob.wall_lo;
+    const bool dir = h.prob.dim == 1 && h.prob.bc == SHE_DIRICHLET;
+    fi.ref.assign((size_t)fi.cells, h.prob.wall_lo);
+    for (int64_t i = 0; i < fi.cells; ++i) {
+        double ref_i = dir ? h.prob.wall_lo + (h.prob.wall_hi - h.prob.wall_lo) * ((double)i + 0.5) / (double)fi.cells
+                           : h.prob.wall_lo;
+        if (h.is_batch) ref_i = batch_ref(h, i);
+        if (h.var) ref_i = h.ref_cells[(size_t)i];
+        fi.ref[(size_t)i] = ref_i;
+    }
+    return fi;
+}
+
+// Owning host copy of the raw accumulators.
+struct RawHost {
+    int64_t n = 0;
+    int B = 0;
+    std::vector<int64_t> batch_n, pairs;
+    std::vector<double> b1, b2, S, sk, axes, tc;
+    she_raw view()
+    {
+        she_raw r;
+        r.n_samples = n;
+        r.batches = B;
+        r.batch_n = batch_n.data();
+        r.batch_sum_d = b1.data();
+        r.batch_sum_d2 = b2.data();
+        r.sum_dd = S.empty() ? nullptr : S.data();
+        r.sk_sum = sk.empty() ? nullptr : sk.data();
+        r.axes_sum = axes.empty() ? nullptr : axes.data();
+        r.tc_sum = tc.empty() ? nullptr : tc.data();
+        r.tc_pairs = pairs.empty() ? nullptr : pairs.data();
+        return r;
+    }
+};
+
+// Synchronise, check the flags, and reduce the device accumulators over the
+// realizations of each batch (and the per-CTA partials) into host copies.
+she_status gather_raw(Handle* h, RawHost& rh, bool want_dd, bool want_sk2d, bool want_axes, bool want_tc)
+{
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(sync)");
+    int flags = 0;
+    e = cudaMemcpy(&flags, h->d_flags, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(flags)");
+    rh.n = h->samples_per_real * h->R;
+    if (flags & 1) return fail(h, SHE_ERR_NONFINITE, "she: the state became non-finite");
+    if (flags & 2) return fail(h, SHE_ERR_TIMEOUT, "she: a bounded tensor-core completion wait gave up");
+    const int64_t cells = h->prob.cells;
+    const int B = (int)std::min<int64_t>(32, h->R);
+    rh.B = B;
+    if (h->d_m1 && h->partial_samples > 0) {
+        e = she::launch_flush_moments(*h);
+        if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(flush)");
+    }
+    double* d1 = h->d_red;
+    double* d2 = h->d_red + (size_t)B * cells;
+    e = she::launch_reduce_batches(*h, B, d1, d2);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(reduce)");
+    rh.b1.resize((size_t)B * cells);
+    rh.b2.resize((size_t)B * cells);
+    e = cudaMemcpy(rh.b1.data(), d1, rh.b1.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(rh.b2.data(), d2, rh.b2.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(copy)");
+    rh.batch_n.resize((size_t)B);
+    for (int b = 0; b < B; ++b)     // batch b holds realizations [R b / B, R (b+1) / B)
+        rh.batch_n[(size_t)b] = h->samples_per_real * (h->R * (b + 1) / B - h->R * b / B);
+    if (want_tc && h->tc_lags > 0) {
+        const int L = h->tc_lags;
+        e = she::launch_reduce_sum(h->d_tc_acc, (int64_t)L * cells, (int)h->R, h->d_tc_red, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        rh.tc.resize((size_t)L * cells);
+        if (e == cudaSuccess) e = cudaMemcpy(rh.tc.data(), h->d_tc_red, rh.tc.size() * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(time_corr)");
+        rh.pairs.resize((size_t)L);
+        for (int l = 0; l < L; ++l) rh.pairs[(size_t)l] = h->R * h->tc_pairs[(size_t)l];
+    }
+    if (want_axes && (h->want_sk & SHE_SK_AXES)) {
+        e = she::launch_reduce_axes(*h, h->d_axes_red);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        std::vector<double> Gs((size_t)h->prob.dim * 65536);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(Gs.data(), h->d_axes_red, Gs.size() * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(sk_axes)");
+        for (int ax = 0; ax < h->prob.dim; ++ax) {
+            const int na = h->prob.n[ax];
+            rh.axes.insert(rh.axes.end(), Gs.begin() + (size_t)ax * 65536, Gs.begin() + (size_t)ax * 65536 + (size_t)na * na);
+        }
+    }
+    if (want_sk2d && h->prob.dim == 2 && (h->want_sk & SHE_SK_FULL)) {
+        e = she::launch_sk2d_flush(*h);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        std::vector<double> acc(256 * 129);
+        if (e == cudaSuccess) e = cudaMemcpy(acc.data(), h->d_sk_acc, acc.size() * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(sk2d)");
+        const int nx = h->prob.n[0], ny = h->prob.n[1], kxn = nx / 2 + 1;
+        rh.sk.resize((size_t)ny * kxn);
+        for (int ky = 0; ky < ny; ++ky)
+            for (int kx = 0; kx < kxn; ++kx) rh.sk[(size_t)ky * kxn + kx] = acc[(size_t)ky * 129 + kx];
+    }
+    if (want_dd && h->want_cov) {
+        const int64_t N = cells;
+        e = she::launch_reduce_cov(*h, h->d_cov_red);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        rh.S.resize((size_t)(N * N));
+        if (e == cudaSuccess) e = cudaMemcpy(rh.S.data(), h->d_cov_red, rh.S.size() * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(cov)");
+    }
+    return SHE_OK;
+}
+
+// The statistics of she_stats_out from a raw block (host FP64).
+she_status finalize_stats(const FinInfo& fi, const she_raw& raw, she_stats_out* out, std::string& msg)
+{
+    const int64_t cells = fi.cells;
+    const int B = (int)raw.batches;
+    out->n_samples = raw.n_samples;
+    if (raw.n_samples <= 0) {
+        msg = "she: no sample taken yet";
+        return SHE_ERR_STATE;
+    }
+    if (B < 1 || !raw.batch_n || !raw.batch_sum_d || !raw.batch_sum_d2) {
+        msg = "she_finalize: the per-batch sums are required";
+        return SHE_ERR_INVALID_ARG;
+    }
+    const bool sk1d = fi.dim == 1 && (out->sk || out->sk_fluct);
+    const bool sk2d = fi.dim == 2 && (out->sk || out->sk_fluct);
+    if (((out->cov || sk1d) && !raw.sum_dd) || (sk2d && !raw.sk_sum) || (out->sk_axes && !raw.axes_sum) ||
+        (out->time_corr && (!raw.tc_sum || !raw.tc_pairs || fi.L < 1)) || ((out->sk || out->sk_fluct) && fi.dim == 3)) {
+        msg = "she: statistic requested whose raw sums are not available";
+        return SHE_ERR_INVALID_ARG;
+    }
+    const double* b1 = raw.batch_sum_d;
+    const double* b2 = raw.batch_sum_d2;
+    const double n = (double)raw.n_samples;
+    std::vector<double> mu((size_t)cells);
+    const std::vector<double>& ref = fi.ref;
+    for (int64_t i = 0; i < cells; ++i) {
+        double s1 = 0.0, s2 = 0.0;
+        for (int b = 0; b < B; ++b) {
+            s1 += b1[(size_t)b * cells + i];
+            s2 += b2[(size_t)b * cells + i];
+        }
+        const double mu_i = s1 / n;
+        mu[(size_t)i] = mu_i;
+        if (out->sum_d) out->sum_d[i] = s1;
+        if (out->sum_d2) out->sum_d2[i] = s2;
+        if (out->mean) out->mean[i] = ref[(size_t)i] + mu_i;
+        if (out->var) out->var[i] = s2 / n - mu_i * mu_i;
+        if (out->var_se) {
+            double sv = 0.0, svv = 0.0;
+            for (int b = 0; b < B; ++b) {
+                const double nb = (double)raw.batch_n[b];
+                const double m1 = b1[(size_t)b * cells + i] / nb;
+                const double v = b2[(size_t)b * cells + i] / nb - m1 * m1;
+                sv += v;
+                svv += v * v;
+            }
+            const double mv = sv / B;
+            out->var_se[i] = (B >= 2) ? std::sqrt(std::max(0.0, (svv / B - mv * mv) * B / (B - 1)) / B)
+                                      : std::numeric_limits<double>::quiet_NaN();
+        }
+    }
+    if (out->time_corr) {
+        // <delta_i(t + l K) delta_i(t)>: the lag sums over the pooled pairs
+        for (int l = 0; l < fi.L; ++l) {
+            const int64_t pairs = raw.tc_pairs[l];
+            for (int64_t i = 0; i < cells; ++i)
+                out->time_corr[(size_t)l * cells + i] = pairs > 0 ? raw.tc_sum[(size_t)l * cells + i] / (double)pairs
+                                                                  : std::numeric_limits<double>::quiet_NaN();
+        }
+    }
+    if (out->sk_axes) {
+        // S_a(k) = sum_{j,l} G_a[j][l] cos(2 pi (j - l) k / n_a) / (lines_a n)
+        const double two_pi = 6.283185307179586476925286766559;
+        int off = 0;
+        size_t goff = 0;
+        for (int ax = 0; ax < fi.dim; ++ax) {
+            const int na = fi.n[ax];
+            const double lines = (double)(cells / na);
+            const double* Gm = raw.axes_sum + goff;
+            std::vector<double> diag_sum((size_t)na, 0.0);   // sum over j of G[j][(j + d) mod n]
+            for (int j = 0; j < na; ++j)
+                for (int l = 0; l < na; ++l)
+                    diag_sum[(size_t)(((l - j) % na + na) % na)] +=
+                        0.5 * (Gm[(size_t)j * na + l] + Gm[(size_t)l * na + j]);
+            for (int k = 0; k < na; ++k) {
+                double acc = 0.0;
+                for (int d = 0; d < na; ++d)
+                    acc += diag_sum[(size_t)d] * std::cos(two_pi * (double)(((long long)d * k) % na) / (double)na);
+                out->sk_axes[off + k] = acc / (lines * n);
+            }
+            off += na;
+            goff += (size_t)na * na;
+        }
+    }
+    if (sk2d) {
+        const int nx = fi.n[0], ny = fi.n[1], kxn = nx / 2 + 1;
+        // hat mu (2D DFT of the mean delta), separably: rows then columns
+        const double two_pi = 6.283185307179586476925286766559;
+        std::vector<double> rr((size_t)cells), ri((size_t)cells), mr((size_t)cells), mi((size_t)cells);
+        for (int y = 0; y < ny; ++y)
+            for (int kx = 0; kx < nx; ++kx) {
+                double sr = 0.0, si = 0.0;
+                for (int x = 0; x < nx; ++x) {
+                    const double ang = two_pi * (double)(((long long)kx * x) % nx) / nx;
+                    sr += mu[(size_t)y * nx + x] * std::cos(ang);
+                    si -= mu[(size_t)y * nx + x] * std::sin(ang);
+                }
+                rr[(size_t)y * nx + kx] = sr;
+                ri[(size_t)y * nx + kx] = si;
+            }
+        for (int ky = 0; ky < ny; ++ky)
+            for (int kx = 0; kx < nx; ++kx) {
+                double sr = 0.0, si = 0.0;
+                for (int y = 0; y < ny; ++y) {
+                    const double ang = two_pi * (double)(((long long)ky * y) % ny) / ny;
+                    const double c = std::cos(ang), sn = std::sin(ang);
+                    const double ar = rr[(size_t)y * nx + kx], ai = ri[(size_t)y * nx + kx];
+                    sr += ar * c + ai * sn;
+                    si += ai * c - ar * sn;
+                }
+                mr[(size_t)ky * nx + kx] = sr;
+                mi[(size_t)ky * nx + kx] = si;
+            }
+        const double refsum = fi.ref_uniform * (double)cells;     // hat T_ref: only k = 0
+        for (int ky = 0; ky < ny; ++ky)
+            for (int kx = 0; kx < nx; ++kx) {
+                double d2;
+                if (kx <= nx / 2) d2 = raw.sk_sum[(size_t)ky * kxn + kx] / n;
+                else d2 = raw.sk_sum[(size_t)((ny - ky) % ny) * kxn + (nx - kx)] / n;
+                const size_t k = (size_t)ky * nx + kx;
+                const double m2 = mr[k] * mr[k] + mi[k] * mi[k];
+                if (out->sk_fluct) out->sk_fluct[k] = d2 - m2;
+                if (out->sk) out->sk[k] = (k == 0 ? refsum * refsum + 2.0 * refsum * mr[0] : 0.0) + d2;
+            }
+    }
+    if (raw.sum_dd && (out->cov || sk1d)) {
+        const int64_t N = cells;
+        const double* S = raw.sum_dd;
+        // second moment of delta, symmetrised: M2 = (S + S^T) / (2 n)
+        std::vector<double> M2((size_t)(N * N));
+        for (int64_t i = 0; i < N; ++i)
+            for (int64_t j = 0; j < N; ++j)
+                M2[(size_t)(i * N + j)] = 0.5 * (S[(size_t)(i * N + j)] + S[(size_t)(j * N + i)]) / n;
+        if (out->cov)
+            for (int64_t i = 0; i < N; ++i)
+                for (int64_t j = 0; j < N; ++j)
+                    out->cov[i * N + j] = M2[(size_t)(i * N + j)] - mu[(size_t)i] * mu[(size_t)j];
+        if (sk1d) {
+            // S_k = <|hat T_k|^2> (Eq. (3.11)) from the pooled moments:
+            // <|hat delta_k|^2> = sum_{j,l} M2_jl cos(2 pi (j - l) k / N)
+            const double two_pi = 6.283185307179586476925286766559;
+            std::vector<double> cs((size_t)N), sn((size_t)N);
+            for (int64_t tt = 0; tt < N; ++tt) {
+                cs[(size_t)tt] = std::cos(two_pi * (double)tt / (double)N);
+                sn[(size_t)tt] = std::sin(two_pi * (double)tt / (double)N);
+            }
+            for (int64_t k = 0; k < N; ++k) {
+                double dd = 0.0, mr = 0.0, mi = 0.0, rr = 0.0, ri = 0.0;
+                for (int64_t j = 0; j < N; ++j) {
+                    const size_t ph = (size_t)((j * k) % N);
+                    mr += mu[(size_t)j] * cs[ph];
+                    mi -= mu[(size_t)j] * sn[ph];
+                    rr += ref[(size_t)j] * cs[ph];
+                    ri -= ref[(size_t)j] * sn[ph];
+                    for (int64_t l = 0; l < N; ++l) {
+                        const size_t d = (size_t)((((j - l) * k) % N + N) % N);
+                        dd += M2[(size_t)(j * N + l)] * cs[d];
+                    }
+                }
+                if (out->sk_fluct) out->sk_fluct[k] = dd - (mr * mr + mi * mi);
+                if (out->sk) out->sk[k] = rr * rr + ri * ri + 2.0 * (rr * mr + ri * mi) + dd;
+            }
+        }
+    }
+    return SHE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -760,6 +1061,11 @@ she_status she_get_sizes(const she_handle* hh, she_sizes* s)
     for (int a = 0; a < h->prob.dim; ++a) s->axes_len += h->prob.n[a];
     s->step = h->step;
     s->tc_lags = h->tc_lags;
+    s->batches = std::min<int64_t>(32, h->R);
+    s->sk_raw_len = (h->prob.dim == 2 && (h->want_sk & SHE_SK_FULL)) ? (int64_t)h->prob.n[1] * (h->prob.n[0] / 2 + 1) : 0;
+    s->axes_raw_len = 0;
+    if (h->want_sk & SHE_SK_AXES)
+        for (int a = 0; a < h->prob.dim; ++a) s->axes_raw_len += (int64_t)h->prob.n[a] * h->prob.n[a];
     return SHE_OK;
 }
 
@@ -770,202 +1076,81 @@ she_status she_stats(she_handle* hh, she_stats_out* out)
     if ((out->cov && !h->want_cov) || ((out->sk || out->sk_fluct) && !(h->want_sk & SHE_SK_FULL)) ||
         (out->sk_axes && !(h->want_sk & SHE_SK_AXES)))
         return fail(h, SHE_ERR_INVALID_ARG, "she: statistic requested that was not enabled at init");
-    cudaError_t e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(sync)");
-    int flags = 0;
-    e = cudaMemcpy(&flags, h->d_flags, sizeof(int), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(flags)");
-    out->n_samples = h->samples_per_real * h->R;
-    if (flags & 1) return fail(h, SHE_ERR_NONFINITE, "she: the state became non-finite");
-    if (flags & 2) return fail(h, SHE_ERR_TIMEOUT, "she: a bounded tensor-core completion wait gave up");
-    if (h->samples_per_real == 0) return fail(h, SHE_ERR_STATE, "she: no sample taken yet");
-    const int64_t cells = h->prob.cells;
-    const int B = (int)std::min<int64_t>(32, h->R);
-    if (h->d_m1 && h->partial_samples > 0) {
-        e = she::launch_flush_moments(*h);
-        if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(flush)");
+    if (out->time_corr && h->tc_lags < 1) return fail(h, SHE_ERR_INVALID_ARG, "she: time_corr needs tc_lags > 0");
+    RawHost rh;
+    const bool need_dd = h->want_cov && (out->cov || ((out->sk || out->sk_fluct) && h->prob.dim == 1));
+    she_status st = gather_raw(h, rh, need_dd, h->prob.dim == 2 && (out->sk || out->sk_fluct), out->sk_axes != nullptr,
+                               out->time_corr != nullptr);
+    if (st != SHE_OK) {
+        out->n_samples = rh.n;
+        return st;
     }
-    double* d1 = h->d_red;
-    double* d2 = h->d_red + (size_t)B * cells;
-    e = she::launch_reduce_batches(*h, B, d1, d2);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(reduce)");
-    std::vector<double> b1((size_t)B * cells), b2((size_t)B * cells);
-    e = cudaMemcpy(b1.data(), d1, b1.size() * sizeof(double), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(b2.data(), d2, b2.size() * sizeof(double), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(copy)");
-    const double n = (double)out->n_samples;
-    const bool dir = h->prob.dim == 1 && h->prob.bc == SHE_DIRICHLET;
-    std::vector<double> mu((size_t)cells), ref((size_t)cells);
-    for (int64_t i = 0; i < cells; ++i) {
-        double s1 = 0.0, s2 = 0.0;
-        for (int b = 0; b < B; ++b) {
-            s1 += b1[(size_t)b * cells + i];
-            s2 += b2[(size_t)b * cells + i];
-        }
-        double ref_i = dir ? h->prob.wall_lo + (h->prob.wall_hi - h->prob.wall_lo) * ((double)i + 0.5) / (double)cells
-                           : h->prob.wall_lo;
-        if (h->is_batch) ref_i = batch_ref(*h, i);
-        if (h->var) ref_i = h->ref_cells[(size_t)i];
-        const double mu_i = s1 / n;
-        mu[(size_t)i] = mu_i;
-        ref[(size_t)i] = ref_i;
-        if (out->sum_d) out->sum_d[i] = s1;
-        if (out->sum_d2) out->sum_d2[i] = s2;
-        if (out->mean) out->mean[i] = ref_i + mu_i;
-        if (out->var) out->var[i] = s2 / n - mu_i * mu_i;
-        if (out->var_se) {
-            // batch b holds realizations [R b / B, R (b+1) / B)
-            double sv = 0.0, svv = 0.0;
-            for (int b = 0; b < B; ++b) {
-                const int64_t rb = h->R * (b + 1) / B - h->R * b / B;
-                const double nb = (double)(h->samples_per_real * rb);
-                const double m1 = b1[(size_t)b * cells + i] / nb;
-                const double v = b2[(size_t)b * cells + i] / nb - m1 * m1;
-                sv += v;
-                svv += v * v;
-            }
-            const double mv = sv / B;
-            out->var_se[i] = (B >= 2) ? std::sqrt(std::max(0.0, (svv / B - mv * mv) * B / (B - 1)) / B)
-                                      : std::numeric_limits<double>::quiet_NaN();
-        }
+    if (rh.n == 0) {
+        out->n_samples = 0;
+        return fail(h, SHE_ERR_STATE, "she: no sample taken yet");
     }
-    if (out->time_corr) {
-        // <delta_i(t + l K) delta_i(t)>: the per-realization sums added over the
-        // realizations, over the pairs l sampling intervals apart (R (n - l)
-        // without a state overwrite since the last reset)
-        if (h->tc_lags < 1) return fail(h, SHE_ERR_INVALID_ARG, "she: time_corr needs tc_lags > 0");
-        const int L = h->tc_lags;
-        e = she::launch_reduce_sum(h->d_tc_acc, (int64_t)L * cells, (int)h->R, h->d_tc_red, h->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-        std::vector<double> tc((size_t)L * cells);
-        if (e == cudaSuccess) e = cudaMemcpy(tc.data(), h->d_tc_red, tc.size() * sizeof(double), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(time_corr)");
-        for (int l = 0; l < L; ++l) {
-            const int64_t pairs = h->R * h->tc_pairs[(size_t)l];
-            for (int64_t i = 0; i < cells; ++i)
-                out->time_corr[(size_t)l * cells + i] = pairs > 0 ? tc[(size_t)l * cells + i] / (double)pairs
-                                                              : std::numeric_limits<double>::quiet_NaN();
-        }
-    }
-    if (out->sk_axes) {
-        // S_a(k) = sum_{j,l} G_a[j][l] cos(2 pi (j - l) k / n_a) / (lines_a n)
-        e = she::launch_reduce_axes(*h, h->d_axes_red);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-        std::vector<double> Gs((size_t)h->prob.dim * 65536);
-        if (e == cudaSuccess)
-            e = cudaMemcpy(Gs.data(), h->d_axes_red, Gs.size() * sizeof(double), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(sk_axes)");
-        const double two_pi = 6.283185307179586476925286766559;
-        int off = 0;
-        for (int ax = 0; ax < h->prob.dim; ++ax) {
-            const int na = h->prob.n[ax];
-            const double lines = (double)(cells / na);
-            const double* Gm = Gs.data() + (size_t)ax * 65536;
-            std::vector<double> diag_sum((size_t)na, 0.0);   // sum over j of G[j][(j + d) mod n]
-            for (int j = 0; j < na; ++j)
-                for (int l = 0; l < na; ++l)
-                    diag_sum[(size_t)(((l - j) % na + na) % na)] +=
-                        0.5 * (Gm[(size_t)j * na + l] + Gm[(size_t)l * na + j]);
-            for (int k = 0; k < na; ++k) {
-                double acc = 0.0;
-                for (int d = 0; d < na; ++d)
-                    acc += diag_sum[(size_t)d] * std::cos(two_pi * (double)(((long long)d * k) % na) / (double)na);
-                out->sk_axes[off + k] = acc / (lines * n);
-            }
-            off += na;
-        }
-    }
-    if (h->prob.dim == 2 && (out->sk || out->sk_fluct)) {
-        e = she::launch_sk2d_flush(*h);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-        std::vector<double> acc(256 * 129);
-        if (e == cudaSuccess) e = cudaMemcpy(acc.data(), h->d_sk_acc, acc.size() * sizeof(double), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(sk2d)");
-        const int nx = h->prob.n[0], ny = h->prob.n[1];
-        // hat mu (2D DFT of the mean delta), separably: rows then columns
-        const double two_pi = 6.283185307179586476925286766559;
-        std::vector<double> rr((size_t)cells), ri((size_t)cells), mr((size_t)cells), mi((size_t)cells);
-        for (int y = 0; y < ny; ++y)
-            for (int kx = 0; kx < nx; ++kx) {
-                double sr = 0.0, si = 0.0;
-                for (int x = 0; x < nx; ++x) {
-                    const double ang = two_pi * (double)(((long long)kx * x) % nx) / nx;
-                    sr += mu[(size_t)y * nx + x] * std::cos(ang);
-                    si -= mu[(size_t)y * nx + x] * std::sin(ang);
-                }
-                rr[(size_t)y * nx + kx] = sr;
-                ri[(size_t)y * nx + kx] = si;
-            }
-        for (int ky = 0; ky < ny; ++ky)
-            for (int kx = 0; kx < nx; ++kx) {
-                double sr = 0.0, si = 0.0;
-                for (int y = 0; y < ny; ++y) {
-                    const double ang = two_pi * (double)(((long long)ky * y) % ny) / ny;
-                    const double c = std::cos(ang), sn = std::sin(ang);
-                    const double ar = rr[(size_t)y * nx + kx], ai = ri[(size_t)y * nx + kx];
-                    sr += ar * c + ai * sn;
-                    si += ai * c - ar * sn;
-                }
-                mr[(size_t)ky * nx + kx] = sr;
-                mi[(size_t)ky * nx + kx] = si;
-            }
-        const double refsum = h->prob.wall_lo * (double)cells;     // hat T_ref: only k = 0
-        for (int ky = 0; ky < ny; ++ky)
-            for (int kx = 0; kx < nx; ++kx) {
-                double d2;
-                if (kx <= nx / 2) d2 = acc[(size_t)ky * 129 + kx] / n;
-                else d2 = acc[(size_t)((ny - ky) % ny) * 129 + (nx - kx)] / n;
-                const size_t k = (size_t)ky * nx + kx;
-                const double m2 = mr[k] * mr[k] + mi[k] * mi[k];
-                if (out->sk_fluct) out->sk_fluct[k] = d2 - m2;
-                if (out->sk) out->sk[k] = (k == 0 ? refsum * refsum + 2.0 * refsum * mr[0] : 0.0) + d2;
-            }
-    }
-    if (h->want_cov && (out->cov || out->sk || out->sk_fluct)) {
-        const int64_t N = cells;
-        e = she::launch_reduce_cov(*h, h->d_cov_red);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-        std::vector<double> S((size_t)(N * N));
-        if (e == cudaSuccess) e = cudaMemcpy(S.data(), h->d_cov_red, S.size() * sizeof(double), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return cuda_fail(h, e, "she_stats(cov)");
-        // second moment of delta, symmetrised: M2 = (S + S^T) / (2 n)
-        std::vector<double> M2((size_t)(N * N));
-        for (int64_t i = 0; i < N; ++i)
-            for (int64_t j = 0; j < N; ++j)
-                M2[(size_t)(i * N + j)] = 0.5 * (S[(size_t)(i * N + j)] + S[(size_t)(j * N + i)]) / n;
-        if (out->cov)
-            for (int64_t i = 0; i < N; ++i)
-                for (int64_t j = 0; j < N; ++j)
-                    out->cov[i * N + j] = M2[(size_t)(i * N + j)] - mu[(size_t)i] * mu[(size_t)j];
-        if (out->sk || out->sk_fluct) {
-            // S_k = <|hat T_k|^2> (Eq. (3.11)) from the pooled moments:
-            // <|hat delta_k|^2> = sum_{j,l} M2_jl cos(2 pi (j - l) k / N)
-            const double two_pi = 6.283185307179586476925286766559;
-            std::vector<double> cs((size_t)N), sn((size_t)N);
-            for (int64_t t = 0; t < N; ++t) {
-                cs[(size_t)t] = std::cos(two_pi * (double)t / (double)N);
-                sn[(size_t)t] = std::sin(two_pi * (double)t / (double)N);
-            }
-            for (int64_t k = 0; k < N; ++k) {
-                double dd = 0.0, mr = 0.0, mi = 0.0, rr = 0.0, ri = 0.0;
-                for (int64_t j = 0; j < N; ++j) {
-                    const size_t ph = (size_t)((j * k) % N);
-                    mr += mu[(size_t)j] * cs[ph];
-                    mi -= mu[(size_t)j] * sn[ph];
-                    rr += ref[(size_t)j] * cs[ph];
-                    ri -= ref[(size_t)j] * sn[ph];
-                    for (int64_t l = 0; l < N; ++l) {
-                        const size_t d = (size_t)((((j - l) * k) % N + N) % N);
-                        dd += M2[(size_t)(j * N + l)] * cs[d];
-                    }
-                }
-                if (out->sk_fluct) out->sk_fluct[k] = dd - (mr * mr + mi * mi);
-                if (out->sk) out->sk[k] = rr * rr + ri * ri + 2.0 * (rr * mr + ri * mi) + dd;
-            }
-        }
-    }
+    she_raw view = rh.view();
+    std::string msg;
+    st = finalize_stats(fin_info(*h), view, out, msg);
+    if (st != SHE_OK) return fail(h, st, msg);
     return SHE_OK;
+}
+
+she_status she_stats_raw(she_handle* hh, she_raw* out)
+{
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !out) return SHE_ERR_INVALID_ARG;
+    if ((out->sum_dd && !h->want_cov) || (out->sk_sum && !(h->prob.dim == 2 && (h->want_sk & SHE_SK_FULL))) ||
+        (out->axes_sum && !(h->want_sk & SHE_SK_AXES)) || ((out->tc_sum || out->tc_pairs) && h->tc_lags < 1))
+        return fail(h, SHE_ERR_INVALID_ARG, "she: raw sums requested that were not enabled at init");
+    RawHost rh;
+    she_status st = gather_raw(h, rh, out->sum_dd != nullptr, out->sk_sum != nullptr, out->axes_sum != nullptr,
+                               out->tc_sum != nullptr || out->tc_pairs != nullptr);
+    out->n_samples = rh.n;
+    out->batches = rh.B;
+    if (st != SHE_OK) return st;
+    auto copy = [](auto* dst, const auto& v) {
+        if (dst) std::copy(v.begin(), v.end(), dst);
+    };
+    copy(out->batch_n, rh.batch_n);
+    copy(out->batch_sum_d, rh.b1);
+    copy(out->batch_sum_d2, rh.b2);
+    copy(out->sum_dd, rh.S);
+    copy(out->sk_sum, rh.sk);
+    copy(out->axes_sum, rh.axes);
+    copy(out->tc_sum, rh.tc);
+    copy(out->tc_pairs, rh.pairs);
+    return SHE_OK;
+}
+
+she_status she_finalize(const she_params* p, const she_raw* raw, she_stats_out* out)
+{
+    if (!p || !raw || !out) return SHE_ERR_INVALID_ARG;
+    she::Problem prob;
+    std::string msg;
+    she_status st = convert(*p, prob, msg);
+    if (st != SHE_OK) {
+        fprintf(stderr, "%s\n", msg.c_str());
+        return st;
+    }
+    FinInfo fi;
+    fi.dim = prob.dim;
+    for (int a = 0; a < 3; ++a) fi.n[a] = prob.n[a];
+    fi.cells = prob.cells;
+    fi.L = p->tc_lags;
+    fi.ref_uniform = prob.wall_lo;
+    fi.ref.assign((size_t)prob.cells, prob.wall_lo);
+    if (p->lambda_cells) {
+        Materials m;
+        build_materials(*p, m, msg);
+        fi.ref = m.ref;
+    } else if (prob.dim == 1 && prob.bc == SHE_DIRICHLET) {
+        for (int64_t i = 0; i < prob.cells; ++i)
+            fi.ref[(size_t)i] = prob.wall_lo + (prob.wall_hi - prob.wall_lo) * ((double)i + 0.5) / (double)prob.cells;
+    }
+    st = finalize_stats(fi, *raw, out, msg);
+    if (st != SHE_OK) fprintf(stderr, "%s\n", msg.c_str());
+    return st;
 }
 
 she_status she_reset_stats(she_handle* hh)

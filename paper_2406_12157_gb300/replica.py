@@ -1,66 +1,47 @@
-"""Merging statistics of independent replicas (one process per GPU).
+"""Merging the statistics of independent replicas (one process per GPU).
 
 Realizations are independent and the noise is addressed by the global
 realization index (``stream_offset``), so shards of one ensemble run on
 different GPUs produce exactly the sample paths of one large run.  Their
-statistics combine by summing the raw FP64 accumulators -- the sample count,
-sum(delta), sum(delta^2) and, where accumulated, sum(delta delta^T) and the
-time correlation's lag sums with their pair counts -- which
-is the one exchange the method has (no per-step collective).  This module
-does that sum with ``torch.distributed.all_reduce`` (gloo on host memory, or
-NCCL), then finalises the statistics exactly as ``she_stats`` does.
+statistics combine by summing the raw FP64 accumulators of she_stats_raw --
+per-batch sums of delta and delta^2 with their sample counts, sum of
+delta delta^T, the structure factors' sums and the time correlation's lag
+sums with their pair counts -- which is the one exchange the method has (no
+per-step collective).  This module only does that sum, with one
+``torch.distributed.all_reduce`` (gloo on host memory, or NCCL); the
+library's host call she_finalize then forms the statistics, exactly as
+she_stats does for a single handle.
 """
 import numpy as np
 
+from . import she_finalize
 
-def raw_from_stats(stats, realizations=None):
-    """Raw pooled sums from a ``she_stats(..., raw=True[, cov=True][,
-    time_corr=True])`` result.  The time correlation needs the handle's
-    realization count R: lag l has R (n/R - l) pairs."""
-    n = float(stats["n_samples"])
-    out = {"n": n, "sum_d": np.asarray(stats["sum_d"], dtype=np.float64),
-           "sum_d2": np.asarray(stats["sum_d2"], dtype=np.float64)}
-    if "cov" in stats:
-        mu = out["sum_d"] / n
-        out["sum_dd"] = n * (np.asarray(stats["cov"], dtype=np.float64) + np.outer(mu, mu))
-    if "time_corr" in stats:
-        R = int(realizations)
-        ns = int(round(n / R))
-        tc = np.asarray(stats["time_corr"], dtype=np.float64)
-        pairs = np.array([R * max(0, ns - l) for l in range(tc.shape[0])], dtype=np.float64)
-        out["n_tc"] = pairs
-        out["sum_tc"] = np.where(pairs[:, None] > 0, np.nan_to_num(tc) * pairs[:, None], 0.0)
-    return out
+_INT_KEYS = ("batch_n", "tc_pairs")
+_SUM_KEYS = ("batch_n", "batch_sum_d", "batch_sum_d2", "sum_dd", "sk_sum", "axes_sum", "tc_sum", "tc_pairs")
 
 
 def allreduce_raw(raw, group=None):
-    """Sum the raw accumulators of every rank (in place on a copy)."""
+    """Element-wise sum of every rank's raw block (she_stats_raw layout)."""
     import torch
     import torch.distributed as dist
-    keys = [k for k in ("sum_d", "sum_d2", "sum_dd", "sum_tc", "n_tc") if k in raw]
-    flat = np.concatenate([np.array([raw["n"]])] + [np.ravel(raw[k]) for k in keys])
+    keys = [k for k in _SUM_KEYS if raw.get(k) is not None]
+    flat = np.concatenate([np.array([float(raw["n_samples"])])] +
+                          [np.ravel(raw[k]).astype(np.float64) for k in keys])
     t = torch.from_numpy(flat.copy())
+    if dist.get_backend(group) == "nccl":      # NCCL reduces device memory
+        t = t.cuda()
     dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
-    flat = t.numpy()
-    out = {"n": float(flat[0])}
+    flat = t.cpu().numpy()
+    out = {"n_samples": int(round(flat[0])), "batches": int(raw["batches"])}
     pos = 1
     for k in keys:
         size = np.size(raw[k])
-        out[k] = flat[pos:pos + size].reshape(np.shape(raw[k]))
+        v = flat[pos:pos + size].reshape(np.shape(raw[k]))
+        out[k] = np.rint(v).astype(np.int64) if k in _INT_KEYS else np.ascontiguousarray(v)
         pos += size
     return out
 
 
-def finalize(raw, tref):
-    """mean = T_ref + sum(delta)/n, var = sum(delta^2)/n - mu^2 (biased, as
-    in Sec. 3), cov = sum(delta delta^T)/n - mu mu^T."""
-    n = raw["n"]
-    mu = raw["sum_d"] / n
-    out = {"n": n, "mean": np.asarray(tref) + mu, "var": raw["sum_d2"] / n - mu * mu}
-    if "sum_dd" in raw:
-        out["cov"] = raw["sum_dd"] / n - np.outer(mu, mu)
-    if "sum_tc" in raw:
-        # <delta_i(t + l K) delta_i(t)> over the pairs of every rank
-        pairs = np.asarray(raw["n_tc"])[:, None]
-        out["time_corr"] = np.where(pairs > 0, raw["sum_tc"] / np.maximum(pairs, 1), np.nan)
-    return out
+def finalize(params, raw, **kw):
+    """Statistics of the merged ensemble: she_finalize on the summed block."""
+    return she_finalize(params, raw, **kw)
