@@ -209,10 +209,10 @@ WORKLOADS = {
                                                            + 2 * 128 * p["n"][1] * p["n"][0])),
     "gradient_rod_tc": dict(
         leg_chunk=10000, leg_steps=10,
-        make=lambda W: W.gradient_rod(want_cov=0, tc_lags=8),
+        make=lambda W: W.gradient_rod(want_cov=0, tc_lags=8, tune=1),
         desc=("the gradient_rod configuration without the covariance, with the time correlation "
               "<delta_i(t + l K) delta_i(t)> at 8 lags accumulated every 10 steps after 1e5 (the "
-              "exercise on <dT_i^{n+m} dT_i^n>, Sec. 6)"),
+              "exercise on <dT_i^{n+m} dT_i^n>, Sec. 6); layout picked by the autotuner"),
         # forward Euler plus one product and one add per lag and cell at
         # every sample (8 lags / 10 steps); memory per cell and sample: the
         # ring store and L - 1 ring loads (4 B each) and L FP64 atomic adds
@@ -437,6 +437,7 @@ def run_workload_leg(she, args, name, stream, flush, barrier, peaks, peak_src):
     wl = WORKLOADS[name]
     sim, p, desc, cells, R, probs = _make_sim(she, args, name, 0, stream)
     batch = probs is not None
+    layout = int(she.she_get_sizes(sim.h).layout)
     chunk = wl["leg_chunk"]
     try:
         _relax(sim, p, chunk)
@@ -453,7 +454,7 @@ def run_workload_leg(she, args, name, stream, flush, barrier, peaks, peak_src):
     step_launches = max(1, prof["step_launches"])
     per_launch_ms = prof["step_ms"] / step_launches if prof["step_launches"] else ms / max(1, launches)
     roof = _roofline(wl, p, R, batch, cu / step_launches, per_launch_ms, prof, ms, peaks, peak_src, sm_mhz)
-    return {"value": cu / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / wl["leg_steps"],
+    return {"value": cu / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / wl["leg_steps"], "layout": layout,
             "steps": wl["leg_steps"], "time_steps_per_bench_step": chunk, "description": desc,
             "phase": "sampling", "roofline": roof, "gpu_launches": int(launches), "clocks": clk}
 
@@ -476,6 +477,7 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     sim, p, desc, cells, R, probs = _make_sim(she, args, args.workload, rank, stream, args.realizations)
     batch = probs is not None
+    layout = int(she.she_get_sizes(sim.h).layout)
     wl = WORKLOADS[args.workload]
     chunk = args.chunk if args.chunk else wl["chunk"]
     cu_per_step = R * cells * chunk
@@ -615,6 +617,7 @@ def run_ours(args):
         "config": {"workload": args.workload, "description": desc, "cells": cells,
                    "realizations_per_gpu": R, "time_steps_per_bench_step": chunk,
                    "stats_interval": p["stats_interval"], "relax_steps": p["relax_steps"],
+                   "fused_1d_layout": layout,
                    "phase": ("sampling: the relaxation steps run untimed before the warm-up"
                              if args.relax is None else "relax overridden to %d" % args.relax),
                    "l2": "flushed between timed steps (256 MB write outside the events)"},

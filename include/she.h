@@ -169,6 +169,15 @@ typedef struct she_params {
      * SHE_ERR_UNSTABLE. */
     const double* lambda_cells;
     const double* rho_cv_cells;
+    int32_t tune;         /* 1: she_init picks the fused 1D kernel's layout (cells per lane x
+                             lanes per realization; forward Euler, predictor-corrector, material
+                             rods, the time correlation) by timing every candidate on a scratch
+                             copy of the state, or takes it from the cache file (the environment
+                             variable SHE_TUNE_CACHE, else $HOME/.cache/libshe_tune.txt; one line
+                             per GPU model, library build and problem shape); 0: the built-in
+                             table.  SHE_TUNE_1D = "C,LPR" overrides both.  The chosen layout is
+                             she_sizes.layout; results are the same for every layout (the noise
+                             is addressed by face, step and realization). */
 } she_params;
 
 typedef struct she_handle she_handle;
@@ -217,6 +226,8 @@ typedef struct she_sizes {
     int64_t batches;      /* realization batches B of she_raw's per-batch sums */
     int64_t sk_raw_len;   /* she_raw.sk_sum length: ny (nx/2 + 1) for the 2D full S(k), else 0 */
     int64_t axes_raw_len; /* she_raw.axes_sum length: sum over used axes of n_a^2 (SHE_SK_AXES), else 0 */
+    int64_t layout;       /* the fused 1D kernel's layout, cells per lane x 100 + lanes per
+                             realization (0: the handle steps with another kernel) */
 } she_sizes;
 
 /*

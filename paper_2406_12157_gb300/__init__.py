@@ -96,6 +96,7 @@ def params_from_problem(prob, stream=None, **overrides):
     p.steps_per_launch = int(q.get("steps_per_launch", 0))
     p.stream_offset = int(q.get("stream_offset", 0))
     p.tc_lags = int(q.get("tc_lags", 0))
+    p.tune = int(q.get("tune", 0))
     if q.get("lambda_cells") is not None:
         # a rod of several materials: the arrays are read during she_init only;
         # the struct keeps them alive as long as it lives

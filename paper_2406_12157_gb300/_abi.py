@@ -76,6 +76,7 @@ class she_params(ctypes.Structure):
         ("tc_lags", ctypes.c_int32),
         ("lambda_cells", ctypes.POINTER(ctypes.c_double)),
         ("rho_cv_cells", ctypes.POINTER(ctypes.c_double)),
+        ("tune", ctypes.c_int32),
     ]
 
 
@@ -111,6 +112,7 @@ class she_sizes(ctypes.Structure):
         ("batches", ctypes.c_int64),
         ("sk_raw_len", ctypes.c_int64),
         ("axes_raw_len", ctypes.c_int64),
+        ("layout", ctypes.c_int64),
     ]
 
 

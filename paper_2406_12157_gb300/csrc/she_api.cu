@@ -14,6 +14,11 @@
 
 #include <mutex>
 
+#include <dlfcn.h>
+#include <fstream>
+#include <sstream>
+#include <sys/stat.h>
+
 #include "she_internal.cuh"
 
 using she::Handle;
@@ -660,6 +665,92 @@ she_status finalize_stats(const FinInfo& fi, const she_raw& raw, she_stats_out* 
     return SHE_OK;
 }
 
+// ---------------------------------------------------------------- tuning --
+
+// Identity of the loaded library: FNV-1a 64 of the shared object's bytes
+// (so a cache entry never outlives the build that measured it).
+std::string build_id()
+{
+    static std::string id = []() -> std::string {
+        Dl_info info;
+        if (!dladdr(reinterpret_cast<void*>(&she_init), &info) || !info.dli_fname) return "unknown";
+        std::ifstream f(info.dli_fname, std::ios::binary);
+        uint64_t hsh = 1469598103934665603ull;
+        char buf[1 << 16];
+        while (f) {
+            f.read(buf, sizeof buf);
+            for (std::streamsize i = 0; i < f.gcount(); ++i) {
+                hsh ^= (unsigned char)buf[i];
+                hsh *= 1099511628211ull;
+            }
+        }
+        char out[32];
+        snprintf(out, sizeof out, "%016llx", (unsigned long long)hsh);
+        return out;
+    }();
+    return id;
+}
+
+std::string tune_cache_path()
+{
+    if (const char* e = getenv("SHE_TUNE_CACHE")) return e;
+    const char* home = getenv("HOME");
+    if (!home) return "";
+    const std::string dir = std::string(home) + "/.cache";
+    mkdir(dir.c_str(), 0755);          // may exist already
+    return dir + "/libshe_tune.txt";
+}
+
+std::string tune_key(const Handle& h)
+{
+    char buf[160];
+    snprintf(buf, sizeof buf, "fused1d N=%d R=%lld prec=%d scheme=%d eq=%d bc=%d var=%d tc=%d", h.prob.n[0],
+             (long long)h.R, h.precision, h.prob.scheme, h.prob.equation, h.prob.bc, h.var ? 1 : 0, h.tc_lags);
+    return buf;
+}
+
+// The tuned layout of the handle: from the cache file when a line matches
+// (GPU model, library build, problem shape), else measured and appended.
+cudaError_t apply_tuning(Handle& h)
+{
+    if (getenv("SHE_TUNE_1D")) return cudaSuccess;       // the explicit override wins
+    if (she::fused_layout(h) == 0) return cudaSuccess;
+    int dev = 0;
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaGetDeviceProperties(&prop, dev);
+    if (e != cudaSuccess) return e;
+    const std::string gpu = prop.name, build = build_id(), key = tune_key(h);
+    const std::string path = tune_cache_path();
+    if (!path.empty()) {
+        std::ifstream f(path);
+        std::string line;
+        while (std::getline(f, line)) {
+            std::istringstream ss(line);
+            std::string g, b, k, v;
+            if (std::getline(ss, g, '\t') && std::getline(ss, b, '\t') && std::getline(ss, k, '\t') &&
+                std::getline(ss, v, '\t') && g == gpu && b == build && k == key) {
+                const int code = atoi(v.c_str());
+                if (she::layout_valid(h, code)) {
+                    h.layout_override = code;
+                    return cudaSuccess;
+                }
+            }
+        }
+    }
+    int best = 0;
+    e = she::tune_step1d(h, &best);
+    if (e != cudaSuccess) return e;
+    if (best > 0) {
+        h.layout_override = best;
+        if (!path.empty()) {
+            std::ofstream f(path, std::ios::app);
+            f << gpu << '\t' << build << '\t' << key << '\t' << best << '\n';
+        }
+    }
+    return cudaSuccess;
+}
+
 }  // namespace
 
 extern "C" {
@@ -880,6 +971,7 @@ she_status she_init(const she_params* p, she_handle** out)
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flags, 0, sizeof(int), h->stream);
     if (e == cudaSuccess) e = she::launch_init_state(*h);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess && p->tune) e = apply_tuning(*h);
     if (e != cudaSuccess) {
         she_status s2 = cuda_fail(h, e, "she_init");
         fprintf(stderr, "%s\n", h->err.c_str());
@@ -1063,6 +1155,7 @@ she_status she_get_sizes(const she_handle* hh, she_sizes* s)
     s->tc_lags = h->tc_lags;
     s->batches = std::min<int64_t>(32, h->R);
     s->sk_raw_len = (h->prob.dim == 2 && (h->want_sk & SHE_SK_FULL)) ? (int64_t)h->prob.n[1] * (h->prob.n[0] / 2 + 1) : 0;
+    s->layout = she::fused_layout(*h);
     s->axes_raw_len = 0;
     if (h->want_sk & SHE_SK_AXES)
         for (int a = 0; a < h->prob.dim; ++a) s->axes_raw_len += (int64_t)h->prob.n[a] * h->prob.n[a];

@@ -237,6 +237,7 @@ struct Handle {
     double* d_sigma = nullptr;     // [N] initial perturbation sd per cell
     std::vector<double> ref_cells; // host copy of T_ref
     std::vector<double> cap_cells; // rho c_V per cell (the energy weights of a periodic rod)
+    int layout_override = 0;       // fused 1D layout chosen by the tuner (0: the table)
     // implicit schemes: factor tables of the chosen layout
     int imp_layout = 0;
     void* d_solve = nullptr;       // [C x LPR] Solve1D of the state's precision
@@ -346,6 +347,15 @@ template <typename Real, bool DIR, bool SP>
 cudaError_t launch_step1d_theta(const Step1DArgs<Real>& a, int layout, cudaStream_t st);
 // Layout and factor tables of the implicit solve (host, at init).
 cudaError_t setup_implicit(Handle& h);
+// The fused 1D layout (cells per lane * 100 + lanes per realization) the
+// handle's steps launch with (0: the handle has no fused 1D kernel).
+int fused_layout(const Handle& h);
+// Time every fused 1D layout that fits the handle's rows on a scratch copy
+// of the state and return the fastest in *best (0 if none applies); the
+// handle's state and accumulators are untouched.
+cudaError_t tune_step1d(Handle& h, int* best);
+// Whether `code` is a fused 1D layout of the handle's scheme that holds its rows.
+bool layout_valid(const Handle& h, int code);
 cudaError_t launch_init_state(Handle& h);
 cudaError_t launch_step1d(Handle& h, uint32_t step0, int nsteps);
 cudaError_t launch_step1d_plain(Handle& h, uint32_t step0, int nsteps);

@@ -230,11 +230,53 @@ static int pick_layout(int N)
     return 3232;
 }
 
+static bool in_list(int code, const int* list, int n)
+{
+    for (int i = 0; i < n; ++i)
+        if (list[i] == code) return true;
+    return false;
+}
+static const int kLayoutsFE[] = {404, 408, 416, 432, 832, 1616, 1632, 3208, 3232};
+static const int kLayoutsPC[] = {404, 408, 416, 432, 832, 1632};
+
+bool layout_valid(const Handle& h, int code)
+{
+    const int N = h.prob.n[0];
+    if ((code / 100) * (code % 100) < N) return false;
+    if (h.prob.scheme == SHE_PC) return in_list(code, kLayoutsPC, (int)(sizeof(kLayoutsPC) / sizeof(int)));
+    return in_list(code, kLayoutsFE, (int)(sizeof(kLayoutsFE) / sizeof(int)));
+}
+
+// The layout the fused kernel of the handle takes: the implicit schemes'
+// own (their factor tables belong to it), the tuner's choice, or the table
+// (with the time correlation, at most 16 cells per lane up to 512 cells).
+static int choose_layout(const Handle& h)
+{
+    const int N = h.prob.n[0];
+    if (h.prob.scheme == SHE_BE || h.prob.scheme == SHE_CN) return h.imp_layout;
+    if (h.prob.scheme == SHE_PC) return h.layout_override ? h.layout_override : pick_layout_pc(N);
+    if (h.layout_override) return h.layout_override;
+    int layout = pick_layout(N);
+    if (h.tc_lags > 0 && layout / 100 > 16 && !getenv("SHE_TUNE_1D"))
+        layout = N <= 256 ? 1616 : N <= 512 ? 1632 : layout;
+    return layout;
+}
+
+int fused_layout(const Handle& h)
+{
+    if (h.prob.dim != 1 || h.is_batch || h.kernel != SHE_KERNEL_AUTO) return 0;
+    if (h.want_cov && h.precision == SHE_FP32) return 0;     // the covariance kernel's own layout
+    return choose_layout(h);
+}
+
+// state_alt: run on another state buffer (the tuner's scratch copy);
+// no_samples: take no sample in this launch (timing runs)
 template <typename Real>
-static cudaError_t launch_fused(Handle& h, uint32_t step0, int nsteps)
+static cudaError_t launch_fused(Handle& h, uint32_t step0, int nsteps, int layout_force = 0,
+                                Real* state_alt = nullptr, bool no_samples = false)
 {
     Step1DArgs<Real> a;
-    a.state = (Real*)h.d_state;
+    a.state = state_alt ? state_alt : (Real*)h.d_state;
     a.acc1 = h.d_acc1;
     a.acc2 = h.d_acc2;
     a.flags = h.d_flags;
@@ -250,10 +292,10 @@ static cudaError_t launch_fused(Handle& h, uint32_t step0, int nsteps)
     a.step0 = step0;
     a.nsteps = nsteps;
     a.K = h.K;
-    a.relax = (long long)h.relax;
+    a.relax = no_samples ? (long long)step0 + nsteps : (long long)h.relax;
     a.stream0 = h.stream0;
     a.stochastic = h.stochastic;
-    a.tc_lags = h.tc_lags;
+    a.tc_lags = no_samples ? 0 : h.tc_lags;
     a.tc_s0 = (long long)h.samples_per_real;
     a.tc_base = (long long)h.tc_base;
     a.tc_ring = (Real*)h.d_tc_ring;
@@ -278,15 +320,15 @@ static cudaError_t launch_fused(Handle& h, uint32_t step0, int nsteps)
         a.sm_cg = (Real)h.sm_cg;
         a.sm_inv = (Real)h.sm_inv;
         const int layout = h.imp_layout;
-        a.tc_onchip = tc_fits(layout) ? 1 : 0;
+        a.tc_onchip = (a.tc_lags > 0 && tc_fits(layout)) ? 1 : 0;
         if (dir) return sp ? launch_step1d_theta<Real, true, true>(a, layout, h.stream)
                            : launch_step1d_theta<Real, true, false>(a, layout, h.stream);
         return sp ? launch_step1d_theta<Real, false, true>(a, layout, h.stream)
                   : launch_step1d_theta<Real, false, false>(a, layout, h.stream);
     }
     if (h.prob.scheme == SHE_PC) {
-        const int layout = pick_layout_pc(a.N);
-        a.tc_onchip = tc_fits(layout) ? 1 : 0;
+        const int layout = layout_force ? layout_force : choose_layout(h);
+        a.tc_onchip = (a.tc_lags > 0 && tc_fits(layout)) ? 1 : 0;
         if (h.var)         // a rod of several materials (heat)
             return dir ? launch_step1d_variant<Real, true, false, true, true>(a, layout, h.stream)
                        : launch_step1d_variant<Real, false, false, true, true>(a, layout, h.stream);
@@ -297,11 +339,8 @@ static cudaError_t launch_fused(Handle& h, uint32_t step0, int nsteps)
         if (sp) return launch_step1d_variant<Real, false, true, true, false>(a, layout, h.stream);
         return launch_step1d_variant<Real, false, false, true, false>(a, layout, h.stream);
     }
-    int layout = pick_layout(a.N);
-    // with the time correlation, at most 16 cells per lane so that its
-    // partials fit beside the moments at two blocks per SM
-    if (h.tc_lags > 0 && layout / 100 > 16) layout = a.N <= 256 ? 1616 : a.N <= 512 ? 1632 : layout;
-    a.tc_onchip = tc_fits(layout) ? 1 : 0;
+    const int layout = layout_force ? layout_force : choose_layout(h);
+    a.tc_onchip = (a.tc_lags > 0 && tc_fits(layout)) ? 1 : 0;
     if (h.var)
         return dir ? launch_step1d_variant<Real, true, false, false, true>(a, layout, h.stream)
                    : launch_step1d_variant<Real, false, false, false, true>(a, layout, h.stream);
@@ -311,6 +350,59 @@ static cudaError_t launch_fused(Handle& h, uint32_t step0, int nsteps)
     }
     if (sp) return launch_step1d_variant<Real, false, true, false, false>(a, layout, h.stream);
     return launch_step1d_variant<Real, false, false, false, false>(a, layout, h.stream);
+}
+
+// Autotuner of the fused 1D kernel: every layout with C x LPR in [N, 2N]
+// (and >= the row) of the scheme's table, three timed launches of 256 steps
+// each on a scratch copy of the state, no samples; the fastest wins.
+template <typename Real>
+static cudaError_t tune_fused(Handle& h, int* best)
+{
+    *best = 0;
+    const int N = h.prob.n[0];
+    const bool pc = h.prob.scheme == SHE_PC;
+    const int* list = pc ? kLayoutsPC : kLayoutsFE;
+    const int nlist = pc ? (int)(sizeof(kLayoutsPC) / sizeof(int)) : (int)(sizeof(kLayoutsFE) / sizeof(int));
+    const size_t bytes = (size_t)h.R * (size_t)N * sizeof(Real);
+    Real* scratch = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&scratch, bytes);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    for (int i = 0; i < nlist && e == cudaSuccess; ++i) {
+        const int code = list[i];
+        const int cells = (code / 100) * (code % 100);
+        if (cells < N || cells > 2 * N + 32) continue;
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {      // the first run warms up
+            e = cudaMemcpyAsync(scratch, h.d_state, bytes, cudaMemcpyDeviceToDevice, h.stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, h.stream);
+            if (e == cudaSuccess) e = launch_fused<Real>(h, (uint32_t)h.step, 256, code, scratch, true);
+            h.launches += 1;
+            if (e == cudaSuccess) e = cudaEventRecord(e1, h.stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) ms_min = std::min(ms_min, ms);
+        }
+        if (e == cudaSuccess && ms_min < best_ms) {
+            best_ms = ms_min;
+            *best = code;
+        }
+    }
+    cudaFree(scratch);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return e;
+}
+
+cudaError_t tune_step1d(Handle& h, int* best)
+{
+    *best = 0;
+    if (fused_layout(h) == 0 || h.prob.scheme == SHE_BE || h.prob.scheme == SHE_CN) return cudaSuccess;
+    if (h.precision == SHE_FP64) return tune_fused<double>(h, best);
+    return tune_fused<float>(h, best);
 }
 
 cudaError_t launch_step1d(Handle& h, uint32_t step0, int nsteps)
