@@ -297,12 +297,14 @@ struct Row1D {
     }
 
     // advance the row T of a uniform heat rod by the forward-Euler step with
-    // absolute index n, the update of step() rewritten with the face sums
-    // s_f = T_l + T_r:  r (T_{i+1} - 2 T_i + T_{i-1}) = r (s_hi + s_lo) - 4 r T_i
-    // (a Dirichlet wall's ghost 2 T_wall - T_edge makes s_wall = 2 T_wall), so
-    // T_i' = (1 - 4 r) T_i + r (s_hi + s_lo) + G_hi - G_lo, and the face flux
-    // G_f = s_half s_f N_f with s_half folded into the normals (one product
-    // per face, four operations per cell)
+    // absolute index n, the update of step() written per face: with the
+    // face difference d_f = T_r - T_l (exact for neighbouring values; a
+    // Dirichlet wall's ghost 2 T_wall - T_edge gives 2 (T_edge - T_wall) at
+    // the low wall and 2 (T_wall - T_edge) at the high one) and the face flux
+    // G_f = s_half (T_l + T_r) N_f, the face carries q_f = r d_f + G_f and
+    // T_i' = T_i + (q_hi - q_lo).  Every quantity but T is small, so the step
+    // rounds once at the scale of T, as the stencil form does, in six
+    // operations per cell (s_half folded into the normals).
     __device__ __forceinline__ void step_heat(Real (&T)[C], uint32_t n)
     {
         const Real left_nb = __shfl_up_sync(FULL, T[C - 1], 1, LPR);
@@ -339,53 +341,39 @@ struct Row1D {
 #pragma unroll
             for (int j = 0; j < C; ++j) zz[j] = Real(0);
         }
-        Real g_first = Real(0), g_prev = Real(0), g_zero = Real(0);
-        Real s_prev = Real(0);
+        // face i0 (between cell i0 - 1 -- the neighbour lane, the wall or the
+        // wrap -- and cell i0)
+        Real q_first;
+        {
+            const Real lo = first_sl ? (DIR ? Real(0) : wrap_lo) : left_nb;
+            Real d0 = T[0] - lo, g0 = (lo + T[0]) * zz[0];
+            if (DIR && first_sl) {
+                d0 = Real(2) * (T[0] - wlo);
+                g0 = gl_heat * zz[0];                 // sqrt(2) s_half 2 T_L N_0
+            }
+            q_first = fma(r, d0, g0);
+        }
+        const Real q_zero = DIR ? Real(0) : __shfl_sync(FULL, q_first, 0, LPR);
+        Real q_prev = q_first;
         Real old_cur = T[0];
 #pragma unroll
-        for (int g = 0; g < C / 4; ++g) {
-            const Real* z = zz + 4 * g;
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int j = 4 * g + t;
-                if (j == 0) {
-                    // face i0: between cell i0-1 (neighbour lane, or wall/wrap) and i0
-                    Real s0 = left_nb + T[0];
-                    Real g0;
-                    if (first_sl) s0 = DIR ? Real(2) * wlo : wrap_lo + T[0];
-                    g0 = s0 * z[0];
-                    if (DIR && first_sl) g0 = gl_heat * z[0];   // sqrt(2) s_half 2 T_L N_0
-                    g_first = g0;
-                    if (!DIR) g_zero = __shfl_sync(FULL, g_first, 0, LPR);
-                    s_prev = s0;
-                    g_prev = g0;
-                } else {
-                    Real sf = old_cur + T[j];
-                    Real gf = sf * z[t];
-                    if (RAGGED && i0 + j == N) {            // ragged lane: the high face
-                        sf = DIR ? Real(2) * whi : old_cur + wrap_hi;
-                        gf = DIR ? g_high : g_zero;
-                    }
-                    const Real tc = old_cur;
-                    old_cur = T[j];
-                    T[j - 1] = fma(a4, tc, fma(r, s_prev + sf, gf) - g_prev);
-                    s_prev = sf;
-                    g_prev = gf;
-                }
-            }
+        for (int j = 1; j < C; ++j) {
+            // face i0 + j between cells i0 + j - 1 and i0 + j; then cell i0 + j - 1
+            Real qf = fma(r, T[j] - old_cur, (old_cur + T[j]) * zz[j]);
+            if (RAGGED && i0 + j == N)               // ragged lane: the high face
+                qf = DIR ? fma(r, Real(2) * (whi - old_cur), g_high) : q_zero;
+            const Real tc = old_cur;
+            old_cur = T[j];
+            T[j - 1] = tc + (qf - q_prev);
+            q_prev = qf;
         }
         // last cell of the lane: its high face is the neighbour lane's first
         // face, or the wall/wrap face when it is cell N-1
         {
-            const Real g_next = __shfl_down_sync(FULL, g_first, 1, LPR);
-            const Real tc = old_cur;
-            Real sr = tc + right_nb;
-            Real gr = g_next;
-            if ((!RAGGED && tail_sl) || (RAGGED && i0 + C - 1 == N - 1)) {
-                sr = DIR ? Real(2) * whi : tc + wrap_hi;
-                gr = DIR ? g_high : g_zero;
-            }
-            T[C - 1] = fma(a4, tc, fma(r, s_prev + sr, gr) - g_prev);
+            Real q_hi = __shfl_down_sync(FULL, q_first, 1, LPR);
+            if ((!RAGGED && tail_sl) || (RAGGED && i0 + C - 1 == N - 1))
+                q_hi = DIR ? fma(r, Real(2) * (whi - old_cur), g_high) : q_zero;
+            T[C - 1] = old_cur + (q_hi - q_prev);
         }
     }
 

@@ -120,7 +120,31 @@ k_step2d(const __grid_constant__ Step2DArgs<Real> a)
 
         for (int y = y0; y < y1; ++y) {
             load_row(y + 2, nn);                          // prefetch, used next row
-            yflux(y + 1, cur, nxt, gy_nxt);
+            // this row's normals: the low y-faces of row y + 1 and the low
+            // x-faces of row y, C / 4 Philox blocks each, run together round
+            // by round (independent chains side by side)
+            Real zy[C], zx[C];
+            if (a.stochastic) {
+                uint4 blk[C / 2];
+                const uint32_t gyb = (uint32_t)(ncell + (int64_t)nx * wrap_once(y + 1, ny) + i0) / 4u;
+                const uint32_t gxb = (uint32_t)((int64_t)nx * y + i0) / 4u;
+#pragma unroll
+                for (int q = 0; q < C / 4; ++q) {
+                    blk[q] = make_uint4(gyb + (uint32_t)q, n, stream, 0u);
+                    blk[C / 4 + q] = make_uint4(gxb + (uint32_t)q, n, stream, 0u);
+                }
+                philox4x32_10_batch<C / 2>(blk, a.rk);
+#pragma unroll
+                for (int q = 0; q < C / 4; ++q) {
+                    box_muller4(blk[q], zy + 4 * q);
+                    box_muller4(blk[C / 4 + q], zx + 4 * q);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < C; ++j) zy[j] = zx[j] = Real(0);
+            }
+#pragma unroll
+            for (int j = 0; j < C; ++j) gy_nxt[j] = flux(cur[j], nxt[j], zy[j]);
             // x-direction of row y (periodic): neighbours and low x-face fluxes
             const Real left_nb = __shfl_up_sync(FULL, cur[C - 1], 1, LPR);
             const Real right_nb = __shfl_down_sync(FULL, cur[0], 1, LPR);
@@ -133,18 +157,11 @@ k_step2d(const __grid_constant__ Step2DArgs<Real> a)
             const Real wrap_lo = __shfl_sync(FULL, mine, last_sl, LPR);     // T(nx-1, y)
             const Real wrap_hi = __shfl_sync(FULL, cur[0], 0, LPR);         // T(0, y)
             Real gx[C];
-            const uint32_t gxbase = (uint32_t)((int64_t)nx * y + i0);
 #pragma unroll
-            for (int q = 0; q < C / 4; ++q) {
-                Real z[4] = {Real(0), Real(0), Real(0), Real(0)};
-                if (a.stochastic) box_muller4(philox4x32_10(make_uint4(gxbase / 4u + (uint32_t)q, n, stream, 0u), a.rk), z);
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int j = 4 * q + t;
-                    Real lo = (j == 0) ? left_nb : cur[j - 1];
-                    if (j == 0 && sl == 0) lo = wrap_lo;
-                    gx[j] = flux(lo, cur[j], z[t]);
-                }
+            for (int j = 0; j < C; ++j) {
+                Real lo = (j == 0) ? left_nb : cur[j - 1];
+                if (j == 0 && sl == 0) lo = wrap_lo;
+                gx[j] = flux(lo, cur[j], zx[j]);
             }
             const Real g_next = __shfl_down_sync(FULL, gx[0], 1, LPR);
             const Real g_zero = __shfl_sync(FULL, gx[0], 0, LPR);
