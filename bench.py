@@ -70,8 +70,9 @@ def add_ops(*parts):
     return out
 
 
-# cell update: 1D with the face sums, (1 - 4 r) T + r (s_hi + s_lo) + G_hi - G_lo,
-# 4 FP32 ops; 2D 9, 3D 11; the predictor-corrector's trapezoid (T + T* + inc) / 2: 3
+# cell update: 1D per face q_f = r (T_r - T_l) + G_f (a difference and an FMA)
+# and T + (q_hi - q_lo) (two adds): 4 FP32 ops per cell-update beside the
+# face flux; 2D 9, 3D 11; the predictor-corrector's trapezoid (T + T* + inc) / 2: 3
 OPS_1D = add_ops(noise_ops(257.0 / 256.0), flux_ops(257.0 / 256.0, False), {"fma": 4.0})
 OPS_1D_PC = add_ops(noise_ops(257.0 / 256.0), flux_ops(2 * 257.0 / 256.0, False), {"fma": 2 * 4.0 + 3.0})
 OPS_2D_SP = add_ops(noise_ops(2.0), flux_ops(2.0, True), {"fma": 9.0})
