@@ -182,7 +182,7 @@ WORKLOADS = {
         kernel="k_step1d_cov<16,16,dirichlet,heat>",
         # DRAM read + write of one launch (2560 steps, mostly the per-CTA
         # covariance flush), ncu capture in profiles/k_step1d_cov_gradient_rod.md
-        traffic=dict(bytes=100.734208e6 + 41.664512e6, realizations=4096)),
+        traffic=dict(bytes=100.868864e6 + 41.249536e6, realizations=4096)),
     "gradient_rod_pc": dict(
         leg_chunk=10000, leg_steps=10,
         make=lambda W: W.gradient_rod(scheme="pc"),
@@ -193,7 +193,7 @@ WORKLOADS = {
         # (predictor, corrector on T*), and the trapezoid (T + T* + inc) / 2
         chunk=10_000, ops=OPS_1D_PC, bytes=None,
         kernel="k_step1d_cov<16,16,dirichlet,heat,pc>",
-        traffic=dict(bytes=100.739072e6 + 41.579008e6, realizations=4096)),   # profiles/k_step1d_cov_pc_gradient_rod_pc.md
+        traffic=None),     # the kernel changed since profiles/k_step1d_cov_pc_gradient_rod_pc.md
     "species_2d": dict(
         leg_chunk=1000, leg_steps=10,
         make=lambda W: W.species_2d(want_sk=1),
@@ -202,7 +202,7 @@ WORKLOADS = {
               "(two-stage DFT-as-GEMM on tcgen05) every 10 steps after 1e4"),
         chunk=1000, ops=OPS_2D_SP, bytes=8.0 + 16.0 / 10,
         kernel="k_step2d<float,8,32,species>",
-        traffic=dict(bytes=74.257408e6 + 22.797312e6, realizations=256),   # profiles/k_step2d_species_2d.md
+        traffic=dict(bytes=74.259456e6 + 22.635008e6, realizations=256),   # profiles/k_step2d_species_2d.md
         # per realization and sample: row DFT (ny x nx x nx MAC) + column DFTs
         # for the 128 rows ky < 128 (2 x 128 x ny x nx MAC; the other rows
         # follow from the real-field symmetry), 3 split products, 2 flop per MAC
@@ -253,7 +253,7 @@ WORKLOADS = {
               "r = 0.2 each, per-instance seeds, FP32, moments every 10 steps after 1e4, one CUDA-graph "
               "launch per step batch"),
         chunk=2560, ops=OPS_1D, bytes=None, kernel="k_step1d_batch<*>",
-        traffic=dict(bytes=17.868800e6 + 0.052480e6, realizations=1)),    # profiles/k_step1d_batch_batched_rods.md
+        traffic=None),     # the row step changed since profiles/k_step1d_batch_batched_rods.md
     "two_material_rod": dict(
         leg_chunk=10000, leg_steps=10,
         make=lambda W: W.two_material_rod(),
@@ -262,7 +262,8 @@ WORKLOADS = {
               "k_B 1e-3, 4096 realizations, FP32, moments and the 256x256 covariance (tcgen05) every 10 "
               "steps after 1e5"),
         chunk=10_000, ops=OPS_1D_VAR, bytes=None,
-        kernel="k_step1d_cov<16,16,dirichlet,heat,var>", traffic=None),
+        kernel="k_step1d_cov<16,16,dirichlet,heat,var>",
+        traffic=dict(bytes=100.739584e6 + 40.971264e6, realizations=4096)),   # profiles/k_step1d_cov_var_two_material_rod.md
     "gradient_rod_cn": dict(
         leg_chunk=10000, leg_steps=10,
         make=lambda W: W.gradient_rod(scheme="cn", dt=2.0, want_cov=0),
