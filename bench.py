@@ -225,13 +225,13 @@ WORKLOADS = {
         make=lambda W: W.species_2d(want_sk=1, scheme="pc"),
         desc=("the species_2d configuration (2D species diffusion 256x256 periodic, 256 realizations, "
               "FP32, moments and the full 2D S(k) every 10 steps after 1e4) stepped by the "
-              "predictor-corrector scheme of Sec. 3, run as a predictor pass and a corrector pass"),
-        # algorithmic: two normals per cell drawn once, the two face fluxes and
-        # the update twice, the trapezoid 3 (the two-pass kernels draw the
-        # normals again in the corrector; that work is not counted); bytes: the
-        # state read and written once plus the moments
+              "predictor-corrector scheme of Sec. 3 in one pass (the predictor state carried one row "
+              "ahead of the corrector)"),
+        # two normals per cell drawn once, the two face fluxes and the update
+        # twice, the trapezoid 3; bytes: the state read and written once plus
+        # the moments
         chunk=1000, ops=OPS_2D_SP_PC, bytes=8.0 + 16.0 / 10,
-        kernel="k_step2d<float,8,32,species> predictor + corrector", traffic=None,
+        kernel="k_step2d_pc<float,8,32,species>", traffic=None,
         stats_kernel="k_sk2d", stats_flop=lambda p: 3 * 2 * (p["n"][1] * p["n"][0] ** 2
                                                            + 2 * 128 * p["n"][1] * p["n"][0])),
     "cube_3d": dict(

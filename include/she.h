@@ -171,7 +171,8 @@ typedef struct she_params {
     const double* rho_cv_cells;
     int32_t tune;         /* 1: she_init picks the fused 1D kernel's layout (cells per lane x
                              lanes per realization; forward Euler, predictor-corrector, material
-                             rods, the time correlation) by timing every candidate on a scratch
+                             rods, the time correlation, and the implicit schemes, whose factor
+                             tables are set up per candidate) by timing every candidate on a scratch
                              copy of the state, or takes it from the cache file (the environment
                              variable SHE_TUNE_CACHE, else $HOME/.cache/libshe_tune.txt; one line
                              per GPU model, library build and problem shape); 0: the built-in

@@ -711,6 +711,17 @@ std::string tune_key(const Handle& h)
 
 // The tuned layout of the handle: from the cache file when a line matches
 // (GPU model, library build, problem shape), else measured and appended.
+bool implicit_scheme(const Handle& h) { return h.prob.scheme == SHE_BE || h.prob.scheme == SHE_CN; }
+
+// Take a fused layout: the implicit schemes set up that layout's factor
+// tables, the others run it in place of the table's choice.
+cudaError_t use_layout(Handle& h, int code)
+{
+    if (implicit_scheme(h)) return she::setup_implicit(h, code);
+    h.layout_override = code;
+    return cudaSuccess;
+}
+
 cudaError_t apply_tuning(Handle& h)
 {
     if (getenv("SHE_TUNE_1D")) return cudaSuccess;       // the explicit override wins
@@ -731,18 +742,16 @@ cudaError_t apply_tuning(Handle& h)
             if (std::getline(ss, g, '\t') && std::getline(ss, b, '\t') && std::getline(ss, k, '\t') &&
                 std::getline(ss, v, '\t') && g == gpu && b == build && k == key) {
                 const int code = atoi(v.c_str());
-                if (she::layout_valid(h, code)) {
-                    h.layout_override = code;
-                    return cudaSuccess;
-                }
+                if (she::layout_valid(h, code)) return use_layout(h, code);
             }
         }
     }
     int best = 0;
     e = she::tune_step1d(h, &best);
+    if (e == cudaSuccess && best > 0) e = use_layout(h, best);
+    else if (e == cudaSuccess && implicit_scheme(h)) e = she::setup_implicit(h);   // no candidate: the table's
     if (e != cudaSuccess) return e;
     if (best > 0) {
-        h.layout_override = best;
         if (!path.empty()) {
             std::ofstream f(path, std::ios::app);
             f << gpu << '\t' << build << '\t' << key << '\t' << best << '\n';

@@ -346,7 +346,9 @@ cudaError_t launch_step1d_variant(const Step1DArgs<Real>& a, int layout, cudaStr
 template <typename Real, bool DIR, bool SP>
 cudaError_t launch_step1d_theta(const Step1DArgs<Real>& a, int layout, cudaStream_t st);
 // Layout and factor tables of the implicit solve (host, at init).
-cudaError_t setup_implicit(Handle& h);
+// factor tables of the implicit theta scheme for a layout (0: the table's
+// choice for the row length), replacing any earlier ones
+cudaError_t setup_implicit(Handle& h, int layout = 0);
 // The fused 1D layout (cells per lane * 100 + lanes per realization) the
 // handle's steps launch with (0: the handle has no fused 1D kernel).
 int fused_layout(const Handle& h);

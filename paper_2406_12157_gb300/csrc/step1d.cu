@@ -51,6 +51,15 @@ static int pick_layout_pc(int N)
 // lane in segments of 4 to 32 lanes (rows of up to 1024 cells).
 static int pick_layout_theta(int N)
 {
+    if (const char* e = getenv("SHE_TUNE_1D")) {       // "C,LPR", honoured when it is a theta layout that fits
+        int c = 0, l = 0;
+        if (sscanf(e, "%d,%d", &c, &l) == 2 && c * l >= N) {
+            const int code = c * 100 + l;
+            if (code == 404 || code == 804 || code == 808 || code == 832 || code == 1608 || code == 1616 ||
+                code == 3208 || code == 3216 || code == 3232)
+                return code;
+        }
+    }
     if (N <= 16) return 404;
     if (N <= 32) return 804;
     if (N <= 64) return 808;
@@ -90,6 +99,11 @@ static cudaError_t upload_theta_tables(Handle& h, int C, int LPR, const std::vec
             const double rl = k + 1 < LPR ? Rinv[(size_t)(2 * k + 2) * P2 + 2 * q + 1] : 0.0;
             red[(size_t)k * LPR + q] = {(Real)lf, (Real)ll, (Real)rf, (Real)rl};
         }
+    // a new layout replaces the tables of the previous one (the autotuner)
+    cudaFree(h.d_solve);
+    cudaFree(h.d_theta_red);
+    h.d_solve = nullptr;
+    h.d_theta_red = nullptr;
     cudaError_t e = cudaMalloc(&h.d_solve, s.size() * sizeof(s[0]));
     if (e == cudaSuccess) e = cudaMalloc(&h.d_theta_red, red.size() * sizeof(red[0]));
     if (e == cudaSuccess) e = cudaMemcpy(h.d_solve, s.data(), s.size() * sizeof(s[0]), cudaMemcpyHostToDevice);
@@ -97,14 +111,14 @@ static cudaError_t upload_theta_tables(Handle& h, int C, int LPR, const std::vec
     return e;
 }
 
-cudaError_t setup_implicit(Handle& h)
+cudaError_t setup_implicit(Handle& h, int layout)
 {
     const int N = h.prob.n[0];
     const bool dir = h.prob.bc == SHE_DIRICHLET;
     const double theta = h.prob.scheme == SHE_BE ? 1.0 : 0.5;
     const double r = h.prob.r;
-    const int layout = pick_layout_theta(N);
-    if (layout == 0) return cudaErrorInvalidValue;
+    if (layout == 0) layout = pick_layout_theta(N);
+    if (layout == 0 || (layout / 100) * (layout % 100) < N) return cudaErrorInvalidValue;
     const int C = layout / 100, LPR = layout % 100, Np = C * LPR;
     h.imp_layout = layout;
     std::vector<double> sub((size_t)Np, 0.0), dia((size_t)Np, 1.0), sup((size_t)Np, 0.0);
@@ -238,12 +252,15 @@ static bool in_list(int code, const int* list, int n)
 }
 static const int kLayoutsFE[] = {404, 408, 416, 432, 832, 1616, 1632, 3208, 3232};
 static const int kLayoutsPC[] = {404, 408, 416, 432, 832, 1632};
+static const int kLayoutsTheta[] = {404, 804, 808, 832, 1608, 1616, 3208, 3216, 3232};
 
 bool layout_valid(const Handle& h, int code)
 {
     const int N = h.prob.n[0];
     if ((code / 100) * (code % 100) < N) return false;
     if (h.prob.scheme == SHE_PC) return in_list(code, kLayoutsPC, (int)(sizeof(kLayoutsPC) / sizeof(int)));
+    if (h.prob.scheme == SHE_BE || h.prob.scheme == SHE_CN)
+        return in_list(code, kLayoutsTheta, (int)(sizeof(kLayoutsTheta) / sizeof(int)));
     return in_list(code, kLayoutsFE, (int)(sizeof(kLayoutsFE) / sizeof(int)));
 }
 
@@ -361,8 +378,13 @@ static cudaError_t tune_fused(Handle& h, int* best)
     *best = 0;
     const int N = h.prob.n[0];
     const bool pc = h.prob.scheme == SHE_PC;
-    const int* list = pc ? kLayoutsPC : kLayoutsFE;
-    const int nlist = pc ? (int)(sizeof(kLayoutsPC) / sizeof(int)) : (int)(sizeof(kLayoutsFE) / sizeof(int));
+    // the implicit schemes' factor tables belong to a layout: each candidate
+    // gets its own, and the caller sets up the winner's
+    const bool imp = h.prob.scheme == SHE_BE || h.prob.scheme == SHE_CN;
+    const int* list = imp ? kLayoutsTheta : pc ? kLayoutsPC : kLayoutsFE;
+    const int nlist = imp  ? (int)(sizeof(kLayoutsTheta) / sizeof(int))
+                      : pc ? (int)(sizeof(kLayoutsPC) / sizeof(int))
+                           : (int)(sizeof(kLayoutsFE) / sizeof(int));
     const size_t bytes = (size_t)h.R * (size_t)N * sizeof(Real);
     Real* scratch = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -374,6 +396,10 @@ static cudaError_t tune_fused(Handle& h, int* best)
         const int code = list[i];
         const int cells = (code / 100) * (code % 100);
         if (cells < N || cells > 2 * N + 32) continue;
+        if (imp) {
+            e = setup_implicit(h, code);
+            if (e != cudaSuccess) break;
+        }
         float ms_min = 1e30f;
         for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {      // the first run warms up
             e = cudaMemcpyAsync(scratch, h.d_state, bytes, cudaMemcpyDeviceToDevice, h.stream);
@@ -400,7 +426,7 @@ static cudaError_t tune_fused(Handle& h, int* best)
 cudaError_t tune_step1d(Handle& h, int* best)
 {
     *best = 0;
-    if (fused_layout(h) == 0 || h.prob.scheme == SHE_BE || h.prob.scheme == SHE_CN) return cudaSuccess;
+    if (fused_layout(h) == 0) return cudaSuccess;
     if (h.precision == SHE_FP64) return tune_fused<double>(h, best);
     return tune_fused<float>(h, best);
 }

@@ -279,9 +279,10 @@ inline cudaError_t launch_ds_pc(const Step1DArgs<Real>& a, int layout, cudaStrea
 // (precision, wall, equation) combination, with the material table of a rod
 // of several materials (VAR); layout = cells per lane * 100 + lanes per
 // realization.
-// Implicit-scheme layouts (see pick_layout_theta): at least 8 cells per lane
-// where the row allows, since the reduced solve costs LPR shuffle pairs per
-// lane and step.
+// Implicit-scheme layouts (see pick_layout_theta): the reduced solve costs
+// LPR shuffle pairs per lane and step, so few lanes per realization save
+// work while more warps per SM hide latency; 8 x 32 and 16 x 16 are the
+// autotuner's alternatives to 32 x 8 for rows of up to 256 cells.
 template <typename Real, bool DIR, bool SP>
 cudaError_t launch_step1d_theta(const Step1DArgs<Real>& a, int layout, cudaStream_t st)
 {
@@ -290,7 +291,9 @@ cudaError_t launch_step1d_theta(const Step1DArgs<Real>& a, int layout, cudaStrea
     case 404: return launch_layout<Real, 4, 4, DIR, SP, F ? 8 : 4, false, false, true>(a, st);
     case 804: return launch_layout<Real, 8, 4, DIR, SP, F ? 8 : 4, false, false, true>(a, st);
     case 808: return launch_layout<Real, 8, 8, DIR, SP, F ? 8 : 4, false, false, true>(a, st);
+    case 832: return launch_layout<Real, 8, 32, DIR, SP, F ? 6 : 3, false, false, true>(a, st);
     case 1608: return launch_layout<Real, 16, 8, DIR, SP, F ? 4 : 2, false, false, true>(a, st);
+    case 1616: return launch_layout<Real, 16, 16, DIR, SP, F ? 4 : 2, false, false, true>(a, st);
     case 3208: return launch_layout<Real, 32, 8, DIR, SP, F ? 2 : 1, false, false, true>(a, st);
     case 3216: return launch_layout<Real, 32, 16, DIR, SP, F ? 2 : 1, false, false, true>(a, st);
     case 3232: return launch_layout<Real, 32, 32, DIR, SP, 1, false, false, true>(a, st);

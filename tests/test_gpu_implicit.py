@@ -7,7 +7,7 @@ realization and step by the kernel's partitioned tridiagonal solve.
 * FP64 trajectories within 1e-12 of the oracle (the Thomas algorithm, cyclic
   by Sherman-Morrison): both schemes, Dirichlet and periodic, heat and
   species, ragged rows, every implicit layout (4 x 4 ... 32 x 32 cells x
-  lanes), time steps below and far above forward Euler's limit, several
+  lanes; 8 x 32, 16 x 16 and 32 x 8 for the same 256-cell row), time steps below and far above forward Euler's limit, several
   launch windows; moments, the FP64 covariance and the time correlation.
 * FP32: one step from a shared state within 2e-5.
 * Deterministic limit at r = 30: every sine mode multiplied per step by
@@ -62,6 +62,23 @@ def test_fp64_trajectory_matches_oracle(N, bc, scheme, r, eq, kB):
     assert np.max(np.abs(x - o["state"]) / np.maximum(np.abs(o["state"]), 1.0)) < 1e-12
     assert g["n_samples"] == o["n_samples"]
     assert np.allclose(g["sum_d2"], o["sum_d2"], rtol=1e-9, atol=1e-15)
+
+
+@pytest.mark.parametrize("layout", ["8,32", "16,16", "32,8"])
+@pytest.mark.parametrize("N,bc,scheme,eq", [(256, "dirichlet", "cn", "heat"), (200, "periodic", "be", "heat"),
+                                            (250, "dirichlet", "be", "species")])
+def test_forced_layouts_match_oracle(monkeypatch, layout, N, bc, scheme, eq):
+    """Every implicit layout of a 256-cell row (SHE_TUNE_1D picks it, as the
+    autotuner does) keeps the trajectories within 1e-12."""
+    monkeypatch.setenv("SHE_TUNE_1D", layout)
+    p = _rod(N, bc, scheme, 3.0, eq, R=9)
+    with S.Simulation(p, steps_per_launch=37) as sim:
+        c, l = (int(v) for v in layout.split(","))
+        assert int(sim.sizes().layout) == 100 * c + l
+        sim.step(80)
+        x, _ = sim.state()
+    o = O.run(p, p["realizations"], 80)
+    assert np.max(np.abs(x - o["state"]) / np.maximum(np.abs(o["state"]), 1.0)) < 1e-12
 
 
 @pytest.mark.parametrize("scheme", ["be", "cn"])

@@ -11,9 +11,12 @@ oracle, through the C ABI.
 * About 10^6 realizations of 4-cell rods match the exact PC moment
   recursion (Gauss-Hermite quadrature over the face normals) within a few
   standard errors, independently of the oracle's sample paths.
-* 2D and 3D (a predictor pass and a corrector pass that draws the same
-  normals again): FP64 trajectories to 1e-12 over several bands, tiles and
-  ragged rows, FP32 one step within 2e-5, the full 2D S(k) on the
+* 2D (one pass: the predictor state carried one row ahead of the corrector,
+  each normal drawn once) and 3D (a predictor pass and a corrector pass that
+  draws the same normals again): FP64 trajectories to 1e-12 over several
+  bands, tiles, ragged rows, a 2-row grid and row runs that cross
+  realizations; FP32 one step within 2e-5, also at the full 256^2 x 256
+  benchmark shape on sampled realizations; the full 2D S(k) on the
   corrector's output.
 * Combinations outside the PC kernels are refused with SHE_ERR_UNSUPPORTED.
 """
@@ -183,20 +186,37 @@ def _p3(shape, eq, **kw):
                      scheme="pc", **kw)
 
 
-@pytest.mark.parametrize("nx,ny", [(8, 6), (20, 33), (64, 48), (132, 7), (256, 20)])
+@pytest.mark.parametrize("nx,ny,R", [(8, 6, 3), (20, 33, 3), (64, 48, 3), (132, 7, 3), (256, 20, 3), (64, 2, 3),
+                                      (256, 64, 20), (40, 3, 5)])
 @pytest.mark.parametrize("eq", ["species", "heat"])
-def test_pc_2d_fp64_trajectory_parity(nx, ny, eq):
-    p = _p2(nx, ny, eq, precision="fp64")
+def test_pc_2d_fp64_trajectory_parity(nx, ny, R, eq):
+    p = _p2(nx, ny, eq, precision="fp64", realizations=R)
     with S.Simulation(p) as sim:
         sim.step(25)
         st, _ = sim.state()
         g = sim.stats(raw=True)
-    ref = O.run(p, 3, 25)
+    ref = O.run(p, R, 25)
     assert rel_err(st, ref["state"]) < 1e-12
     assert g["n_samples"] == ref["n_samples"]
     assert np.allclose(g["sum_d2"], ref["sum_d2"], rtol=1e-9, atol=1e-15)
-    fe = O.run(dict(p, scheme="fe"), 3, 25)["state"]
+    fe = O.run(dict(p, scheme="fe"), R, 25)["state"]
     assert rel_err(st, fe) > 1e-7
+
+
+def test_pc_2d_fp32_one_step_full_size():
+    """The benchmark shape (256 x 256 species, 256 realizations) in the
+    launch configuration the bench times: one step from a shared state,
+    sampled realizations against the oracle."""
+    p = W.species_2d(scheme="pc", want_sk=0)
+    R = p["realizations"]
+    x = W.random_states(p, R, seed=5).astype(np.float32)
+    with S.Simulation(p) as sim:
+        sim.set_state(x, 777)
+        sim.step(1)
+        got, _ = sim.state()
+    for rho in (0, 101, 255):
+        ref = O.step(p, x[rho].astype(np.float64), 777, rho)
+        assert rel_err(got[rho].astype(np.float64), ref) < 2e-5
 
 
 @pytest.mark.parametrize("nx,ny", [(8, 6), (132, 7), (256, 20)])

@@ -3,7 +3,9 @@ the layout it picks (cells per lane x lanes per realization) is one of the
 scheme's layouts that holds the row, keeps the FP64 trajectories within
 1e-12 of the oracle, is written to the cache file keyed by GPU model,
 library build and problem shape, and is read back (no timing runs) by the
-next handle of the same shape; SHE_TUNE_1D still overrides."""
+next handle of the same shape; SHE_TUNE_1D still overrides.  The implicit
+schemes (backward Euler, Crank-Nicolson) are tuned the same way, each
+candidate with its own factor tables."""
 import numpy as np
 import pytest
 
@@ -20,6 +22,7 @@ import paper_2406_12157_gb300 as S  # noqa: E402
 
 FE = {404, 408, 416, 432, 832, 1616, 1632, 3208, 3232}
 PC = {404, 408, 416, 432, 832, 1632}
+THETA = {404, 804, 808, 832, 1608, 1616, 3208, 3216, 3232}
 
 
 @pytest.fixture
@@ -31,7 +34,7 @@ def cache(tmp_path, monkeypatch):
 
 
 @pytest.mark.parametrize("N,scheme,bc", [(130, "fe", "dirichlet"), (256, "fe", "periodic"), (64, "pc", "dirichlet"),
-                                         (500, "pc", "periodic")])
+                                         (500, "pc", "periodic"), (256, "cn", "dirichlet"), (200, "be", "periodic")])
 def test_tuned_layout_keeps_parity_and_is_cached(cache, N, scheme, bc):
     walls = (1.0, 2.0) if bc == "dirichlet" else (1.4, 1.4)
     p = W.oracle_rod(n=(N, 1, 1), bc=bc, wall_lo=walls[0], wall_hi=walls[1], realizations=96, relax_steps=20,
@@ -41,7 +44,7 @@ def test_tuned_layout_keeps_parity_and_is_cached(cache, N, scheme, bc):
         tuning_launches = sim.launches()
         sim.step(150)
         x, _ = sim.state()
-    assert layout in (PC if scheme == "pc" else FE)
+    assert layout in (PC if scheme == "pc" else THETA if scheme in ("be", "cn") else FE)
     assert (layout // 100) * (layout % 100) >= N
     o = O.run(p, 96, 150)
     assert np.max(np.abs(x - o["state"]) / np.abs(o["state"])) < 1e-12
