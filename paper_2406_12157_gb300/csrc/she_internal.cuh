@@ -118,6 +118,8 @@ struct Step2DArgs {
     RoundKeys rk;         // round keys of (key0, key1)
     int stochastic;
     int sample;           // this step is a sampling step
+    int check;            // test the new state for NaN / Inf (the last step of a step batch: once
+                          // non-finite, a cell stays so, since its new value includes its old one)
 };
 
 // Arguments of the 3D step kernel (one step per launch).
@@ -135,6 +137,7 @@ struct Step3DArgs {
     RoundKeys rk;         // round keys of (key0, key1)
     int stochastic;
     int sample;
+    int check;            // as for the 2D step
 };
 
 // Arguments of the per-axis line-covariance kernel (S(k) along each axis).

@@ -63,16 +63,14 @@ k_step3d(const __grid_constant__ Step3DArgs<Real> a)
     const uint32_t stream = a.stream0 + (uint32_t)rho;
     const Real r = a.r, amp2 = a.amp2, half = Real(0.5);
     const Real s_half = fsqrt_any(amp2) * half;
+    const Real hamp2 = half * amp2;                   // species: r eps_c
     const uint32_t n = a.step;
     const int yl = (y0 - 1 + ny) % ny;                 // halo rows
     const int yh = min(y0 + kY3, ny) % ny;
     const int nrows = min(kY3, ny - y0);               // rows of this tile
 
     auto flux = [&](Real lo, Real hi, Real z) -> Real {
-        if (SPECIES) {
-            const Real c = half * (lo + hi);
-            return fsqrt_any(amp2 * (c > Real(0) ? c : Real(0))) * z;
-        }
+        if (SPECIES) return species_flux(lo, hi, hamp2, z);
         return (s_half * (lo + hi)) * z;
     };
     auto row_ptr = [&](int yy, int zz) -> const Real* {
@@ -201,7 +199,8 @@ k_step3d(const __grid_constant__ Step3DArgs<Real> a)
             vstore<C>(po, out);
             bool bad = false;
 #pragma unroll
-            for (int j = 0; j < C; ++j) bad |= !finite_any(out[j]);
+            for (int j = 0; j < C; ++j)
+                if (a.check) bad |= !finite_any(out[j]);
             if (bad) atomicOr(a.flags, 1);
             if (a.sample) {
                 const size_t off = (size_t)rho * (size_t)ncell + ((size_t)z * ny + y) * nx + i0;
@@ -281,6 +280,7 @@ static cudaError_t launch3d_real(Handle& h, uint32_t step0, int nsteps)
         a.Tn = (Real*)h.d_state2;
         a.step = n;
         a.sample = sample_step((int64_t)n + 1, h.K, h.relax) ? 1 : 0;
+        a.check = s == nsteps - 1 ? 1 : 0;
         if (sizeof(Real) == 8) {
             a.m1 = (Real*)h.d_acc1;
             a.m2 = (Real*)h.d_acc2;
@@ -293,8 +293,9 @@ static cudaError_t launch3d_real(Handle& h, uint32_t step0, int nsteps)
         if (h.prob.scheme == SHE_PC) {
             // predictor pass into the second buffer, then the corrector in
             // place over T (see the 2D step)
-            const int sample = a.sample;
+            const int sample = a.sample, check = a.check;
             a.sample = 0;
+            a.check = 0;
             e = launch3d_eq<Real, false>(a, sp, h.stream);
             h.launches += 1;
             if (e != cudaSuccess) return e;
@@ -302,6 +303,7 @@ static cudaError_t launch3d_real(Handle& h, uint32_t step0, int nsteps)
             a.Tc = (const Real*)h.d_state;
             a.Tn = (Real*)h.d_state;
             a.sample = sample;
+            a.check = check;
             e = launch3d_eq<Real, true>(a, sp, h.stream);
             h.launches += 1;
             if (e != cudaSuccess) return e;

@@ -115,3 +115,19 @@ def test_full_structure_factor_2d(nx, ny, R):
     assert np.max(np.abs(g["sk_fluct"] - o["sk_fluct"])) < 2e-4 * scale
     assert np.allclose(g["sk"][1:], o["sk"][1:], rtol=0, atol=2e-4 * scale)
     assert abs(g["sk"][0] - o["sk"][0]) < 1e-6 * abs(o["sk"][0])
+
+
+@pytest.mark.parametrize("scheme", ["fe", "pc"])
+@pytest.mark.parametrize("steps", [1, 7])
+def test_nonfinite_state_is_reported_2d(scheme, steps):
+    """A NaN in the state is reported (SHE_ERR_NONFINITE) after the step
+    batch, whichever step of the batch checks it."""
+    p = _p(32, 24, "species", precision="fp32", scheme=scheme, relax_steps=0, stats_interval=1)
+    with S.Simulation(p) as sim:
+        x, _ = sim.state()
+        x[1, 100] = np.nan
+        sim.set_state(x, 0)
+        sim.step(steps)
+        with pytest.raises(S.SheError) as e:
+            sim.stats()
+        assert e.value.status == S._abi.SHE_ERR_NONFINITE

@@ -102,3 +102,17 @@ def test_per_axis_structure_factor_3d(shape):
     ref = o["sk_axes"]
     scale = np.max(np.abs(ref))
     assert np.max(np.abs(g["sk_axes"] - ref)) < 2e-4 * scale
+
+
+@pytest.mark.parametrize("steps", [1, 5])
+def test_nonfinite_state_is_reported_3d(steps):
+    """A NaN in the state is reported (SHE_ERR_NONFINITE) after the step batch."""
+    p = _p((128, 8, 4), "heat", precision="fp32", relax_steps=0, stats_interval=1)
+    with S.Simulation(p) as sim:
+        x, _ = sim.state()
+        x[0, 1000] = np.inf
+        sim.set_state(x, 0)
+        sim.step(steps)
+        with pytest.raises(S.SheError) as e:
+            sim.stats()
+        assert e.value.status == S._abi.SHE_ERR_NONFINITE
