@@ -44,19 +44,21 @@ def noise_ops(nz):
     rounds of two 32x32->64 products (hi and lo: 4 integer-multiply ops) and
     four xors (the round keys are precomputed per launch, so the key
     schedule's adds are not per-block work): 10 imad + 10 alu per normal.
-    Box-Muller per block: 2 log2, 2 rsqrt, 2 sin, 2 cos (8 xu), 4
-    integer-to-float conversions, 2 max and 2 sign-flip xors (8 alu), 12
-    FP32 multiplies/FMAs (uniform scale, -2 ln 2, radius, angle, the four
-    products): per normal 2 xu, 2 alu, 3 fma."""
-    return {"imad": 10.0 * nz, "alu": 12.0 * nz, "xu": 2.0 * nz, "fma": 3.0 * nz}
+    Box-Muller per block: 2 log2, 2 square roots, 2 sin, 2 cos (8 xu), 4
+    integer-to-float conversions and 2 sign-flip xors (6 alu), 10 FP32
+    multiplies/FMAs (the two uniforms' scale, -2 ln 2 times the logarithm,
+    the two angles, the four products): per normal 2 xu, 1.5 alu, 2.5 fma."""
+    return {"imad": 10.0 * nz, "alu": 11.5 * nz, "xu": 2.0 * nz, "fma": 2.5 * nz}
 
 
 def flux_ops(nf, species):
     """Face fluxes: heat, the face sum T_l + T_r and its product with the
-    normal that carries the amplitude (2 fma); species mean, product,
-    x*rsqrt(x), noise (4 fma), clamp (1 alu), rsqrt (1 xu)."""
+    normal that carries the amplitude (2 fma); species, the face sum, its
+    clamp at 0 (1 alu), the product with r eps_c (the halving of the mean
+    folded into the constant), the square root (1 xu) and the product with
+    the normal (3 fma)."""
     if species:
-        return {"fma": 4.0 * nf, "alu": 1.0 * nf, "xu": 1.0 * nf}
+        return {"fma": 3.0 * nf, "alu": 1.0 * nf, "xu": 1.0 * nf}
     return {"fma": 2.0 * nf}
 
 

@@ -116,6 +116,15 @@ __device__ __forceinline__ void box_muller4(uint4 u, double z[4])
     z[3] = rb * sb;
 }
 
+// Square root of x >= 0 by the approximate hardware instruction (relative
+// error about 2^-23, sqrt(0) = 0): one instruction, no guard against x = 0.
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Same deviates in single precision.  The radius uses the hardware base-2
 // logarithm (ln U = ln 2 * log2 U); the angle is taken as
 // 2 pi U - pi = 2 pi (u - 2^31 + 1/2) 2^-32, inside (-pi, pi) where the fast
@@ -129,12 +138,8 @@ __device__ __forceinline__ void box_muller4(uint4 u, float z[4])
     const float m2ln2 = -1.38629436111989061883f;         // -2 ln 2
     const float ang = 1.46291807926715968105e-09f;        // 2 pi 2^-32
     const float ang0 = 7.31459039633579840525e-10f;       // pi 2^-32
-    float xa = m2ln2 * __log2f(fmaf((float)u.x, scale, 0.5f * scale));
-    float xb = m2ln2 * __log2f(fmaf((float)u.z, scale, 0.5f * scale));
-    xa = fmaxf(xa, 1e-30f);
-    xb = fmaxf(xb, 1e-30f);
-    const float ra = -(xa * rsqrtf(xa));
-    const float rb = -(xb * rsqrtf(xb));
+    const float ra = -sqrt_approx(m2ln2 * __log2f(fmaf((float)u.x, scale, 0.5f * scale)));
+    const float rb = -sqrt_approx(m2ln2 * __log2f(fmaf((float)u.z, scale, 0.5f * scale)));
     const float ta = fmaf((float)(int32_t)(u.y ^ 0x80000000u), ang, ang0);
     const float tb = fmaf((float)(int32_t)(u.w ^ 0x80000000u), ang, ang0);
     float sa, ca, sb, cb;
@@ -155,12 +160,8 @@ __device__ __forceinline__ void box_muller4_scaled(uint4 u, float c2, float z[4]
     const float scale = 2.3283064365386963e-10f;          // 2^-32
     const float ang = 1.46291807926715968105e-09f;        // 2 pi 2^-32
     const float ang0 = 7.31459039633579840525e-10f;       // pi 2^-32
-    float xa = c2 * __log2f(fmaf((float)u.x, scale, 0.5f * scale));
-    float xb = c2 * __log2f(fmaf((float)u.z, scale, 0.5f * scale));
-    xa = fmaxf(xa, 1e-30f);
-    xb = fmaxf(xb, 1e-30f);
-    const float ra = -(xa * rsqrtf(xa));
-    const float rb = -(xb * rsqrtf(xb));
+    const float ra = -sqrt_approx(c2 * __log2f(fmaf((float)u.x, scale, 0.5f * scale)));
+    const float rb = -sqrt_approx(c2 * __log2f(fmaf((float)u.z, scale, 0.5f * scale)));
     const float ta = fmaf((float)(int32_t)(u.y ^ 0x80000000u), ang, ang0);
     const float tb = fmaf((float)(int32_t)(u.w ^ 0x80000000u), ang, ang0);
     float sa, ca, sb, cb;

@@ -17,18 +17,11 @@
 
 namespace she {
 
-// Square root of a noise amplitude.  Single precision takes x * rsqrt(x)
-// (relative error a few 1e-7, far inside the FP32 step tolerance, and a
-// fraction of the instructions of the correctly rounded sqrtf), with an exact
-// 0 at x <= 0; double precision keeps the correctly rounded sqrt.
-// square root of x >= 0: FP32 by the approximate hardware square root (one
-// instruction; relative error about 2^-23, sqrt(0) = 0), FP64 correctly rounded
-__device__ __forceinline__ float fsqrt_any(float x)
-{
-    float y;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
+// Square root of a noise amplitude x >= 0: single precision by the
+// approximate hardware square root (one instruction, relative error about
+// 2^-23, far inside the FP32 step tolerance; sqrt(0) = 0), double precision
+// correctly rounded.
+__device__ __forceinline__ float fsqrt_any(float x) { return sqrt_approx(x); }
 __device__ __forceinline__ double fsqrt_any(double x) { return sqrt(x); }
 
 // Species face flux sqrt(2 r eps_c max(c_f, 0)) N_f with c_f = (lo + hi) / 2

@@ -77,11 +77,18 @@ k_step2d(const __grid_constant__ Step2DArgs<Real> a)
     const Real r = a.r, amp2 = a.amp2, half = Real(0.5);
     const Real s_half = fsqrt_any(amp2) * half;
     const Real hamp2 = half * amp2;                   // species: r eps_c
+    // heat: the amplitude s_half rides on the normals (box_muller4_scaled;
+    // FP32: -2 ln 2 s_half^2 multiplies log2 U), the flux is (lo + hi) z
+    const Real ncoef = sizeof(Real) == 4 ? Real(-1.38629436111989061883) * s_half * s_half : s_half;
+    auto normals4 = [&](uint4 blk, Real* z) {
+        if (SPECIES) box_muller4(blk, z);
+        else box_muller4_scaled(blk, ncoef, z);
+    };
     const uint32_t n = a.step;
 
     auto flux = [&](Real lo, Real hi, Real z) -> Real {
         if (SPECIES) return species_flux(lo, hi, hamp2, z);
-        return (s_half * (lo + hi)) * z;
+        return (lo + hi) * z;
     };
     auto load_row = [&](int y, Real (&v)[C]) {
         const int yy = wrap_once(y, ny);
@@ -100,7 +107,7 @@ k_step2d(const __grid_constant__ Step2DArgs<Real> a)
 #pragma unroll
         for (int q = 0; q < C / 4; ++q) {
             Real z[4] = {Real(0), Real(0), Real(0), Real(0)};
-            if (a.stochastic) box_muller4(philox4x32_10(make_uint4(gbase / 4u + (uint32_t)q, n, stream, 0u), a.rk), z);
+            if (a.stochastic) normals4(philox4x32_10(make_uint4(gbase / 4u + (uint32_t)q, n, stream, 0u), a.rk), z);
 #pragma unroll
             for (int t = 0; t < 4; ++t) g[4 * q + t] = flux(lo[4 * q + t], hi[4 * q + t], z[t]);
         }
@@ -139,8 +146,8 @@ k_step2d(const __grid_constant__ Step2DArgs<Real> a)
                 philox4x32_10_batch<C / 2>(blk, a.rk);
 #pragma unroll
                 for (int q = 0; q < C / 4; ++q) {
-                    box_muller4(blk[q], zy + 4 * q);
-                    box_muller4(blk[C / 4 + q], zx + 4 * q);
+                    normals4(blk[q], zy + 4 * q);
+                    normals4(blk[C / 4 + q], zx + 4 * q);
                 }
             } else {
 #pragma unroll
@@ -289,11 +296,18 @@ k_step2d_pc(const __grid_constant__ Step2DArgs<Real> a)
     const Real r = a.r, amp2 = a.amp2, half = Real(0.5);
     const Real s_half = fsqrt_any(amp2) * half;
     const Real hamp2 = half * amp2;                   // species: r eps_c
+    // heat: the amplitude s_half rides on the normals (box_muller4_scaled;
+    // FP32: -2 ln 2 s_half^2 multiplies log2 U), the flux is (lo + hi) z
+    const Real ncoef = sizeof(Real) == 4 ? Real(-1.38629436111989061883) * s_half * s_half : s_half;
+    auto normals4 = [&](uint4 blk, Real* z) {
+        if (SPECIES) box_muller4(blk, z);
+        else box_muller4_scaled(blk, ncoef, z);
+    };
     const uint32_t n = a.step;
 
     auto flux = [&](Real lo, Real hi, Real z) -> Real {
         if (SPECIES) return species_flux(lo, hi, hamp2, z);
-        return (s_half * (lo + hi)) * z;
+        return (lo + hi) * z;
     };
     auto load_row = [&](int y, Real (&v)[C]) {
         const Real* p = Tin + (size_t)wrap_row(y, ny) * nx;
@@ -323,8 +337,8 @@ k_step2d_pc(const __grid_constant__ Step2DArgs<Real> a)
         philox4x32_10_batch<C / 2>(blk, a.rk);
 #pragma unroll
         for (int q = 0; q < C / 4; ++q) {
-            box_muller4(blk[q], zy + 4 * q);
-            box_muller4(blk[C / 4 + q], zx + 4 * q);
+            normals4(blk[q], zy + 4 * q);
+            normals4(blk[C / 4 + q], zx + 4 * q);
         }
     };
     auto draw1 = [&](int yz, Real (&zy)[C]) {          // the low y-faces of row yz only
@@ -339,7 +353,7 @@ k_step2d_pc(const __grid_constant__ Step2DArgs<Real> a)
         for (int q = 0; q < C / 4; ++q) blk[q] = make_uint4(gyb + (uint32_t)q, n, stream, 0u);
         philox4x32_10_batch<C / 4>(blk, a.rk);
 #pragma unroll
-        for (int q = 0; q < C / 4; ++q) box_muller4(blk[q], zy + 4 * q);
+        for (int q = 0; q < C / 4; ++q) normals4(blk[q], zy + 4 * q);
     };
     // x-direction of one row v (periodic): lx = left + right neighbour,
     // dgx = G(high x-face) - G(low x-face), the fluxes from the row's values

@@ -64,6 +64,13 @@ k_step3d(const __grid_constant__ Step3DArgs<Real> a)
     const Real r = a.r, amp2 = a.amp2, half = Real(0.5);
     const Real s_half = fsqrt_any(amp2) * half;
     const Real hamp2 = half * amp2;                   // species: r eps_c
+    // heat: the amplitude s_half rides on the normals (box_muller4_scaled;
+    // FP32: -2 ln 2 s_half^2 multiplies log2 U), the flux is (lo + hi) z
+    const Real ncoef = sizeof(Real) == 4 ? Real(-1.38629436111989061883) * s_half * s_half : s_half;
+    auto normals4 = [&](uint4 blk, Real* z) {
+        if (SPECIES) box_muller4(blk, z);
+        else box_muller4_scaled(blk, ncoef, z);
+    };
     const uint32_t n = a.step;
     const int yl = (y0 - 1 + ny) % ny;                 // halo rows
     const int yh = min(y0 + kY3, ny) % ny;
@@ -71,7 +78,7 @@ k_step3d(const __grid_constant__ Step3DArgs<Real> a)
 
     auto flux = [&](Real lo, Real hi, Real z) -> Real {
         if (SPECIES) return species_flux(lo, hi, hamp2, z);
-        return (s_half * (lo + hi)) * z;
+        return (lo + hi) * z;
     };
     auto row_ptr = [&](int yy, int zz) -> const Real* {
         return Tin + ((size_t)wrap_once(zz, nz) * ny + (size_t)yy) * nx;
@@ -82,7 +89,7 @@ k_step3d(const __grid_constant__ Step3DArgs<Real> a)
 #pragma unroll
         for (int q = 0; q < C / 4; ++q) {
             Real z[4] = {Real(0), Real(0), Real(0), Real(0)};
-            if (a.stochastic) box_muller4(philox4x32_10(make_uint4(g0 / 4u + (uint32_t)q, n, stream, 0u), a.rk), z);
+            if (a.stochastic) normals4(philox4x32_10(make_uint4(g0 / 4u + (uint32_t)q, n, stream, 0u), a.rk), z);
 #pragma unroll
             for (int t = 0; t < 4; ++t) g[4 * q + t] = flux(lo[4 * q + t], hi[4 * q + t], z[t]);
         }
