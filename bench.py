@@ -184,7 +184,7 @@ WORKLOADS = {
         kernel="k_step1d_cov<16,16,dirichlet,heat>",
         # DRAM read + write of one launch (2560 steps, mostly the per-CTA
         # covariance flush), ncu capture in profiles/k_step1d_cov_gradient_rod.md
-        traffic=dict(bytes=100.868864e6 + 41.249536e6, realizations=4096)),
+        traffic=dict(bytes=100.731136e6 + 40.777216e6, realizations=4096)),
     "gradient_rod_pc": dict(
         leg_chunk=10000, leg_steps=10,
         make=lambda W: W.gradient_rod(scheme="pc"),
@@ -195,7 +195,7 @@ WORKLOADS = {
         # (predictor, corrector on T*), and the trapezoid (T + T* + inc) / 2
         chunk=10_000, ops=OPS_1D_PC, bytes=None,
         kernel="k_step1d_cov<16,16,dirichlet,heat,pc>",
-        traffic=None),     # the kernel changed since profiles/k_step1d_cov_pc_gradient_rod_pc.md
+        traffic=dict(bytes=100.738816e6 + 41.408256e6, realizations=4096)),   # profiles/k_step1d_cov_pc_gradient_rod_pc.md
     "species_2d": dict(
         leg_chunk=1000, leg_steps=10,
         make=lambda W: W.species_2d(want_sk=1),
@@ -204,7 +204,7 @@ WORKLOADS = {
               "(two-stage DFT-as-GEMM on tcgen05) every 10 steps after 1e4"),
         chunk=1000, ops=OPS_2D_SP, bytes=8.0 + 16.0 / 10,
         kernel="k_step2d<float,8,32,species>",
-        traffic=dict(bytes=74.259456e6 + 22.635008e6, realizations=256),   # profiles/k_step2d_species_2d.md
+        traffic=dict(bytes=74.895872e6 + 21.625600e6, realizations=256),   # profiles/k_step2d_species_2d.md
         # per realization and sample: row DFT (ny x nx x nx MAC) + column DFTs
         # for the 128 rows ky < 128 (2 x 128 x ny x nx MAC; the other rows
         # follow from the real-field symmetry), 3 split products, 2 flop per MAC
@@ -218,10 +218,11 @@ WORKLOADS = {
               "exercise on <dT_i^{n+m} dT_i^n>, Sec. 6); layout picked by the autotuner"),
         # forward Euler plus one product and one add per lag and cell at
         # every sample (8 lags / 10 steps); memory per cell and sample: the
-        # ring store and L - 1 ring loads (4 B each) and L FP64 atomic adds
-        # (8 B each), every 10 steps
-        chunk=10_000, ops=add_ops(OPS_1D, {"fma": 2 * 8 / 10.0}), bytes=(4.0 * 8 + 8.0 * 8) / 10.0,
-        kernel="k_step1d<float,32,8,dirichlet,heat> with the time correlation", traffic=None),
+        # ring store and L - 1 ring loads (4 B each), every 10 steps (the lag
+        # sums are shared-memory partials, flushed once per launch)
+        chunk=10_000, ops=add_ops(OPS_1D, {"fma": 2 * 8 / 10.0}), bytes=(4.0 * 8) / 10.0,
+        kernel="k_step1d<float,8,32,dirichlet,heat> with the time correlation",
+        traffic=dict(bytes=117.473024e6 + 66.203904e6, realizations=4096)),   # profiles/k_step1d_tc_gradient_rod_tc.md
     "species_2d_pc": dict(
         leg_chunk=1000, leg_steps=6,
         make=lambda W: W.species_2d(want_sk=1, scheme="pc"),
@@ -233,7 +234,8 @@ WORKLOADS = {
         # twice, the trapezoid 3; bytes: the state read and written once plus
         # the moments
         chunk=1000, ops=OPS_2D_SP_PC, bytes=8.0 + 16.0 / 10,
-        kernel="k_step2d_pc<float,8,32,species>", traffic=None,
+        kernel="k_step2d_pc<float,8,32,species>",
+        traffic=dict(bytes=75.952384e6 + 23.411968e6, realizations=256),   # profiles/k_step2d_pc_species_2d_pc.md
         stats_kernel="k_sk2d", stats_flop=lambda p: 3 * 2 * (p["n"][1] * p["n"][0] ** 2
                                                            + 2 * 128 * p["n"][1] * p["n"][0])),
     "cube_3d": dict(
@@ -243,7 +245,7 @@ WORKLOADS = {
               "stencil, moments and S(k) along x, y, z (line covariance on tcgen05) every 10 steps"),
         chunk=100, ops=OPS_3D, bytes=8.0 + 16.0 / 10,
         kernel="k_step3d<float,8,heat>",
-        traffic=dict(bytes=142.941184e6 + 92.432384e6, realizations=2),    # profiles/k_step3d_cube_3d.md
+        traffic=dict(bytes=576.138240e6 + 499.718656e6, realizations=8),    # profiles/k_step3d_cube_3d.md
         # per realization and sample: for each axis a SYRK over all lines
         # (cells / n_a lines x n_a^2 MAC), 3 split products, 2 flop per MAC
         stats_kernel="k_axes_syrk", stats_flop=lambda p: 3 * 2 * sum(
@@ -255,7 +257,7 @@ WORKLOADS = {
               "r = 0.2 each, per-instance seeds, FP32, moments every 10 steps after 1e4, one CUDA-graph "
               "launch per step batch"),
         chunk=2560, ops=OPS_1D, bytes=None, kernel="k_step1d_batch<*>",
-        traffic=None),     # the row step changed since profiles/k_step1d_batch_batched_rods.md
+        traffic=dict(bytes=83.965184e6 + 42.347520e6, realizations=1)),    # profiles/k_step1d_batch_batched_rods.md
     "two_material_rod": dict(
         leg_chunk=10000, leg_steps=10,
         make=lambda W: W.two_material_rod(),
@@ -265,7 +267,7 @@ WORKLOADS = {
               "steps after 1e5"),
         chunk=10_000, ops=OPS_1D_VAR, bytes=None,
         kernel="k_step1d_cov<16,16,dirichlet,heat,var>",
-        traffic=dict(bytes=100.739584e6 + 40.971264e6, realizations=4096)),   # profiles/k_step1d_cov_var_two_material_rod.md
+        traffic=dict(bytes=100.738048e6 + 41.069824e6, realizations=4096)),   # profiles/k_step1d_cov_var_two_material_rod.md
     "gradient_rod_cn": dict(
         leg_chunk=10000, leg_steps=10,
         make=lambda W: W.gradient_rod(scheme="cn", dt=2.0, want_cov=0),
