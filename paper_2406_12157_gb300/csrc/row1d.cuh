@@ -238,8 +238,7 @@ struct Row1D {
     __device__ __forceinline__ void step_var(Real (&T)[C], uint32_t n)
     {
         const Real left_nb = __shfl_up_sync(FULL, T[C - 1], 1, LPR);
-        const Real right_nb = __shfl_down_sync(FULL, T[0], 1, LPR);
-        Real wrap_lo = Real(0), wrap_hi = Real(0);
+        Real wrap_lo = Real(0);
         if (!DIR) {
             Real mine = T[C - 1];
             if (RAGGED) {
@@ -248,58 +247,48 @@ struct Row1D {
                     if (j == jlast) mine = T[j];
             }
             wrap_lo = __shfl_sync(FULL, mine, last_sl, LPR);
-            wrap_hi = __shfl_sync(FULL, T[0], 0, LPR);
         }
         const Real g_high = high_wall_flux(n);
-        const Coef1D<Real> c0 = coef_at(i0);
-        Real a_prev = c0.a, ic_prev = c0.ic;        // low face and capacity of the cell to update
-        Real g_first = Real(0), g_prev = Real(0), g_zero = Real(0);
-        Real old_prev = left_nb;
-        if (first_sl) old_prev = DIR ? Real(2) * wlo - T[0] : wrap_lo;
-        Real old_cur = T[0];
         Real zz[C];
         draw_normals(n, zz);
-#pragma unroll
-        for (int g = 0; g < C / 4; ++g) {
-            const Real* z = zz + 4 * g;
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int j = 4 * g + t;
-                Real gf;
-                if (j == 0) {
-                    gf = c0.sh * (left_nb + T[0]) * z[0];
-                    if (first_sl) gf = DIR ? g_low_amp * z[0] : c0.sh * (wrap_lo + T[0]) * z[0];
-                    g_first = gf;
-                    if (!DIR) g_zero = __shfl_sync(FULL, g_first, 0, LPR);
-                } else {
-                    const Coef1D<Real> cj = coef_at(i0 + j);   // face i0 + j, cell i0 + j
-                    gf = cj.sh * (old_cur + T[j]) * z[t];
-                    Real tr = T[j];
-                    if (RAGGED && i0 + j == N) {            // ragged lane: the high face
-                        gf = DIR ? g_high : g_zero;
-                        tr = DIR ? Real(2) * whi - old_cur : wrap_hi;
-                    }
-                    const Real tc = old_cur;
-                    T[j - 1] = tc + ic_prev * (cj.a * (tr - tc) + a_prev * (old_prev - tc) + (gf - g_prev));
-                    old_prev = tc;
-                    old_cur = T[j];
-                    a_prev = cj.a;
-                    ic_prev = cj.ic;
-                }
-                g_prev = gf;
-            }
-        }
+        // per face f: q_f = a_f (T_r - T_l) + sh_f (T_l + T_r) N_f; per cell
+        // T_i' = T_i + ic_i (q_hi - q_lo), the increment formed at the scale
+        // of the fluctuation.  Face i0 first (the wall's ghost 2 T_L - T_0
+        // gives T_r - T_l = 2 (T_0 - T_L)).
+        const Coef1D<Real> c0 = coef_at(i0);
+        Real q_first;
         {
-            const Real g_next = __shfl_down_sync(FULL, g_first, 1, LPR);
-            const Real a_hi = coef_at(i0 + C).a;
-            const Real tc = old_cur;
-            Real tr = right_nb;
-            Real gr = g_next;
-            if ((!RAGGED && tail_sl) || (RAGGED && i0 + C - 1 == N - 1)) {
-                tr = DIR ? Real(2) * whi - tc : wrap_hi;
-                gr = DIR ? g_high : g_zero;
+            const Real lo = first_sl ? (DIR ? Real(0) : wrap_lo) : left_nb;
+            Real d0 = T[0] - lo, g0 = c0.sh * (lo + T[0]) * zz[0];
+            if (DIR && first_sl) {
+                d0 = Real(2) * (T[0] - wlo);
+                g0 = g_low_amp * zz[0];
             }
-            T[C - 1] = tc + ic_prev * (a_hi * (tr - tc) + a_prev * (old_prev - tc) + (gr - g_prev));
+            q_first = fma(c0.a, d0, g0);
+        }
+        const Real q_zero = DIR ? Real(0) : __shfl_sync(FULL, q_first, 0, LPR);
+        Real q_prev = q_first, ic_prev = c0.ic;
+        Real old_cur = T[0];
+#pragma unroll
+        for (int j = 1; j < C; ++j) {
+            // face i0 + j between cells i0 + j - 1 and i0 + j; then cell i0 + j - 1
+            const Coef1D<Real> cj = coef_at(i0 + j);      // face i0 + j, cell i0 + j
+            Real qf = fma(cj.a, T[j] - old_cur, cj.sh * (old_cur + T[j]) * zz[j]);
+            if (RAGGED && i0 + j == N)                    // ragged lane: the high face
+                qf = DIR ? fma(cj.a, Real(2) * (whi - old_cur), g_high) : q_zero;
+            const Real tc = old_cur;
+            old_cur = T[j];
+            T[j - 1] = fma(ic_prev, qf - q_prev, tc);
+            q_prev = qf;
+            ic_prev = cj.ic;
+        }
+        // last cell of the lane: its high face is the neighbour lane's first
+        // face, or the wall/wrap face when it is cell N-1
+        {
+            Real q_hi = __shfl_down_sync(FULL, q_first, 1, LPR);
+            if ((!RAGGED && tail_sl) || (RAGGED && i0 + C - 1 == N - 1))
+                q_hi = DIR ? fma(coef_at(i0 + C).a, Real(2) * (whi - old_cur), g_high) : q_zero;
+            T[C - 1] = fma(ic_prev, q_hi - q_prev, old_cur);
         }
     }
 
