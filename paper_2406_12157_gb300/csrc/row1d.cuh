@@ -200,6 +200,28 @@ struct Row1D {
         }
     }
 
+    // the same normals times the heat amplitude s_half (box_muller4_scaled)
+    __device__ __forceinline__ void draw_normals_scaled(uint32_t n, Real (&z)[C]) const
+    {
+        if (!stochastic) {
+#pragma unroll
+            for (int j = 0; j < C; ++j) z[j] = Real(0);
+            return;
+        }
+        uint4 blk[C / 4];
+#pragma unroll
+        for (int g = 0; g < C / 4; ++g) blk[g] = make_uint4(q0 + (uint32_t)g, n, stream, 0u);
+        if constexpr (RK) philox4x32_10_batch<C / 4>(blk, *rk);
+        else philox4x32_10_batch<C / 4>(blk, key0, key1);
+#pragma unroll
+        for (int g = 0; g < C / 4; ++g) {
+            Real v[4];
+            box_muller4_scaled(blk[g], ncoef, v);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) z[4 * g + t] = v[t];
+        }
+    }
+
     __device__ __forceinline__ Real flux(Real lo, Real hi, Real z) const
     {
         if (SPECIES) return species_flux(lo, hi, Real(0.5) * amp2, z);
@@ -506,6 +528,49 @@ struct Row1D {
         inc[C - 1] = ic * (a_hi * (tr - X[C - 1]) + a_lo * (xl - X[C - 1]) + (gr - g_prev));
     }
 
+    // inc of a uniform heat rod in the per-face form of step_heat: q_f =
+    // r (X_r - X_l) + (X_l + X_r) zs_f with the normals zs carrying s_half,
+    // inc_i = q_hi - q_lo
+    __device__ __forceinline__ void increment_heat(const Real (&X)[C], const Real (&zs)[C], Real g_high,
+                                                   Real (&inc)[C]) const
+    {
+        const Real left_nb = __shfl_up_sync(FULL, X[C - 1], 1, LPR);
+        Real wrap_lo = Real(0);
+        if (!DIR) {
+            Real mine = X[C - 1];
+            if (RAGGED) {
+#pragma unroll
+                for (int j = 0; j < C; ++j)
+                    if (j == jlast) mine = X[j];
+            }
+            wrap_lo = __shfl_sync(FULL, mine, last_sl, LPR);
+        }
+        Real q_first;
+        {
+            const Real lo = first_sl ? (DIR ? Real(0) : wrap_lo) : left_nb;
+            Real d0 = X[0] - lo, g0 = (lo + X[0]) * zs[0];
+            if (DIR && first_sl) {
+                d0 = Real(2) * (X[0] - wlo);
+                g0 = gl_heat * zs[0];
+            }
+            q_first = fma(r, d0, g0);
+        }
+        const Real q_zero = DIR ? Real(0) : __shfl_sync(FULL, q_first, 0, LPR);
+        Real q_prev = q_first;
+#pragma unroll
+        for (int j = 1; j < C; ++j) {
+            Real qf = fma(r, X[j] - X[j - 1], (X[j - 1] + X[j]) * zs[j]);
+            if (RAGGED && i0 + j == N)
+                qf = DIR ? fma(r, Real(2) * (whi - X[j - 1]), g_high) : q_zero;
+            inc[j - 1] = qf - q_prev;
+            q_prev = qf;
+        }
+        Real q_hi = __shfl_down_sync(FULL, q_first, 1, LPR);
+        if ((!RAGGED && tail_sl) || (RAGGED && i0 + C - 1 == N - 1))
+            q_hi = DIR ? fma(r, Real(2) * (whi - X[C - 1]), g_high) : q_zero;
+        inc[C - 1] = q_hi - q_prev;
+    }
+
     __device__ __forceinline__ void increment(const Real (&X)[C], const Real (&z)[C], Real g_high,
                                               Real (&inc)[C]) const
     {
@@ -572,13 +637,22 @@ struct Row1D {
     __device__ __forceinline__ void step_pc(Real (&T)[C], uint32_t n)
     {
         Real z[C];
-        draw_normals(n, z);
         const Real g_high = high_wall_flux(n);
         Real Ts[C], inc[C];
-        increment(T, z, g_high, inc);
+        if constexpr (!SPECIES && !VAR) {
+            // uniform heat rod: the per-face form, the amplitude on the normals
+            draw_normals_scaled(n, z);
+            increment_heat(T, z, g_high, inc);
 #pragma unroll
-        for (int j = 0; j < C; ++j) Ts[j] = T[j] + inc[j];
-        increment(Ts, z, g_high, inc);
+            for (int j = 0; j < C; ++j) Ts[j] = T[j] + inc[j];
+            increment_heat(Ts, z, g_high, inc);
+        } else {
+            draw_normals(n, z);
+            increment(T, z, g_high, inc);
+#pragma unroll
+            for (int j = 0; j < C; ++j) Ts[j] = T[j] + inc[j];
+            increment(Ts, z, g_high, inc);
+        }
 #pragma unroll
         for (int j = 0; j < C; ++j) T[j] = Real(0.5) * ((T[j] + Ts[j]) + inc[j]);
     }
