@@ -118,8 +118,11 @@ k_step3d(const __grid_constant__ Step3DArgs<Real> a)
         if (row_active) vstore<C>(srow + (size_t)(w + 1) * nx + i0, v);
         if (w == 0 || w == 1) vstore<C>(srow + (size_t)(w == 0 ? 0 : nrows + 1) * nx + i0, hv);
     };
-    // low y-face of this warp's row v of plane p (between y-1 and y); warp 0
-    // also does the top face of the tile (between the last row and the high halo)
+    // low y-face of this warp's row v of plane p (between y-1 and y); warps
+    // 0 .. C/4 - 1 also share the top face of the tile (between the last row
+    // and the high halo), one Philox block (four faces) per lane each, so that
+    // no warp draws more than one block beyond its own three rows of faces
+    // (the plane's barrier waits for the busiest warp)
     auto yfaces = [&](int p, const Real (&v)[C]) {
         const Real* srow = srow_of(p);
         Real* sgy = sgy_of(p);
@@ -129,12 +132,16 @@ k_step3d(const __grid_constant__ Step3DArgs<Real> a)
             face_row(lo, v, (uint32_t)ncell + lin(y, p), g);
             vstore<C>(sgy + (size_t)w * nx + i0, g);
         }
-        if (w == 0) {
-            Real lo2[C], hi2[C];
-            vload<C>(srow + (size_t)nrows * nx + i0, lo2);
-            vload<C>(srow + (size_t)(nrows + 1) * nx + i0, hi2);
-            face_row(lo2, hi2, (uint32_t)ncell + lin(yh, p), g);
-            vstore<C>(sgy + (size_t)nrows * nx + i0, g);
+        if (w < C / 4) {
+            const int xq = (w * 32 + lane) * 4;          // this lane's four faces
+            Real lo4[4], hi4[4], g4[4], z[4] = {Real(0), Real(0), Real(0), Real(0)};
+            vload<4>(srow + (size_t)nrows * nx + xq, lo4);
+            vload<4>(srow + (size_t)(nrows + 1) * nx + xq, hi4);
+            const uint32_t gq = (uint32_t)ncell + (uint32_t)(((int64_t)wrap_once(p, nz) * ny + yh) * nx + xq);
+            if (a.stochastic) normals4(philox4x32_10(make_uint4(gq / 4u, n, stream, 0u), a.rk), z);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) g4[t] = flux(lo4[t], hi4[t], z[t]);
+            vstore<4>(sgy + (size_t)nrows * nx + xq, g4);
         }
     };
 
