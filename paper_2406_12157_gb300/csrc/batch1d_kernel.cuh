@@ -26,9 +26,11 @@ namespace she {
 
 // Layout classes: instances with N <= max_n (and above the previous class)
 // use C cells per lane and LPR lanes; the table is shared with the host
-// planner through these macros so that both sides agree.
+// planner through these macros so that both sides agree.  Short rows take
+// the narrowest segments with at least 8 cells per lane where they can: a
+// lane's Philox blocks per step are its independent dependency chains.
 #define SHE_BATCH_CLASSES(X)                                                                 \
-    X(0, 16, 4, 4) X(1, 32, 4, 8) X(2, 64, 4, 16) X(3, 128, 4, 32) X(4, 160, 20, 8)         \
+    X(0, 16, 4, 4) X(1, 32, 8, 4) X(2, 64, 16, 4) X(3, 128, 16, 8) X(4, 160, 20, 8)         \
     X(5, 192, 24, 8) X(6, 224, 28, 8) X(7, 256, 32, 8) X(8, 384, 12, 32) X(9, 512, 16, 32)  \
     X(10, 640, 20, 32) X(11, 768, 24, 32) X(12, 896, 28, 32) X(13, 1024, 32, 32)             \
     X(14, 1280, 40, 32) X(15, 1536, 48, 32) X(16, 1792, 56, 32) X(17, 2048, 64, 32)
