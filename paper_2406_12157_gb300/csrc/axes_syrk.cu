@@ -16,11 +16,13 @@
 // into an FP32 tensor-memory accumulator; full/empty mbarriers (bounded,
 // sleeping waits) hand the buffers over.  After each axis the accumulator is
 // added into the CTA's FP64 partial.
+#include <cuda.h>   // CUtensorMap and its encoder's types (the encoder is reached through the runtime)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
 
 #include "she_internal.cuh"
 #include "tc05.cuh"
@@ -35,6 +37,8 @@ constexpr uint32_t kSBO = 4096;
 constexpr int kOpB = 16384;                 // 32 lines x 256 cells x bf16
 constexpr int kProducers = 8;               // producer warps
 constexpr uint32_t kTries = 1u << 20;
+constexpr int kStg = 32768;                 // one FP32 tile: 32 lines x 256 cells
+constexpr int kStages = 3;                  // FP32 tiles in flight (TMA path)
 }  // namespace
 
 // Tiles of axis a: 32 lines each.  Axis 0 (x): lines are rows, consecutive
@@ -65,16 +69,25 @@ __device__ __forceinline__ AxisGeom axis_geom(int axis, int nx, int ny, int nz)
     return g;
 }
 
+// TMA: the tiles reach shared memory as FP32 by tiled tensor copies (one per
+// tile, issued two tiles ahead into a ring of three stages), and the
+// producers split them from shared memory; otherwise the producers load
+// their part of each tile from device memory themselves.
+template <bool TMA>
 __global__ void __launch_bounds__((kProducers + 1) * 32, 1)
-k_axes_syrk(const AxesArgs a)
+k_axes_syrk(const __grid_constant__ AxesArgs a)
 {
+    constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     auto op_hi = [&](int b) { return base + 2 * b * kOpB; };
     auto op_lo = [&](int b) { return base + (2 * b + 1) * kOpB; };
-    uint64_t* full = reinterpret_cast<uint64_t*>(base + 4 * kOpB);
+    auto stage = [&](int s3) { return reinterpret_cast<float*>(base + 4 * kOpB + s3 * kStg); };
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + 4 * kOpB + (TMA ? kStages * kStg : 0));
     uint64_t* empty = full + 2;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(empty + 2);
+    uint64_t* fpf = empty + 2;               // [kStages] FP32 tile landed (TMA)
+    uint64_t* fpe = fpf + kStages;           // [kStages] every producer read it
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(fpe + kStages);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
 
     const int lane = threadIdx.x & 31;
@@ -91,6 +104,10 @@ k_axes_syrk(const AxesArgs a)
         for (int b = 0; b < 2; ++b) {
             mbar_init(&full[b], kProducers);
             mbar_init(&empty[b], 1);
+        }
+        for (int s3 = 0; s3 < kStages; ++s3) {
+            mbar_init(&fpf[s3], 1);
+            mbar_init(&fpe[s3], kProducers);
         }
         fence_mbar_init();
     }
@@ -141,6 +158,111 @@ k_axes_syrk(const AxesArgs a)
                     mma_commit(&empty[b]);
                 }
             }
+        } else if constexpr (TMA) {
+            const uint32_t tile_bytes = (uint32_t)(axis == 0 ? nx : n) * 32u * 4u;
+            const void* map = &a.map[axis];
+            const int ntx = (nx + 31) / 32;
+            const bool issuer = threadIdx.x == 0;            // producer warp 0, lane 0
+            auto issue = [&](int t) {
+                const int s3 = t % kStages;
+                const int64_t tile = t0 + t;
+                const int rho = (int)(tile / ge.tiles);
+                const int64_t lt = tile % ge.tiles;
+                mbar_arrive_expect_tx(&fpf[s3], tile_bytes);
+                if (axis == 0) {
+                    tma_load_2d(stage(s3), map, 0, (int)((int64_t)rho * ny * nz + lt * 32), &fpf[s3]);
+                } else {
+                    const int x0 = (int)(lt % ntx) * 32, other = (int)(lt / ntx);
+                    if (axis == 1) tma_load_4d(stage(s3), map, x0, 0, other, rho, &fpf[s3]);
+                    else tma_load_4d(stage(s3), map, x0, other, 0, rho, &fpf[s3]);
+                }
+            };
+            int issued = 0, consumed = 0;
+            if (issuer)
+                for (; issued < 2 && issued < ntiles; ++issued) issue(issued);
+            for (int t = 0; t < ntiles; ++t) {
+                const int b = t & 1, s3 = t % kStages;
+                if (*abort_flag) break;
+                bool ok = true;
+                if (issuer && t + 2 < ntiles) {
+                    // stage (t + 2) % 3 last held tile t - 1, read by every producer
+                    if (t + 2 >= kStages)
+                        ok = mbar_wait_sleep_bounded(&fpe[(t + 2) % kStages], (uint32_t)(((t + 2) / kStages - 1) & 1),
+                                                     kTries);
+                    if (ok) {
+                        issue(t + 2);
+                        issued = t + 3;
+                    }
+                }
+                if (ok && lane == 0) ok = mbar_wait_sleep_bounded(&fpf[s3], (uint32_t)((t / kStages) & 1), kTries);
+                if (ok && lane == 0 && t >= 2)
+                    ok = mbar_wait_sleep_bounded(&empty[b], (uint32_t)(((t >> 1) - 1) & 1), kTries);
+                ok = __shfl_sync(FULL, ok ? 1 : 0, 0) != 0;
+                if (!ok) {
+                    if (lane == 0) {
+                        *abort_flag = 1;
+                        atomicOr(a.flags, 2);
+                    }
+                    break;
+                }
+                if (warp == 0) consumed = t + 1;
+                const int64_t lt = (t0 + t) % ge.tiles;
+                const float* st = stage(s3);
+                unsigned char* dh = op_hi(b);
+                unsigned char* dl = op_lo(b);
+                if (axis == 0) {
+                    // tile [32 rows][nx]: this warp's rows 4 warp .. + 3, eight
+                    // consecutive cells per lane (all 256 columns written, zero
+                    // past the row)
+                    const int p0 = 8 * lane;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int k = 4 * warp + i;
+                        const bool rowok = lt * 32 + k < (int64_t)ny * nz;
+                        const float4 f0 = *reinterpret_cast<const float4*>(st + k * nx + p0);
+                        const float4 f1 = *reinterpret_cast<const float4*>(st + k * nx + p0 + 4);
+                        float v[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) v[q] = (rowok && p0 + q < n) ? v[q] - a.ref : 0.0f;
+                        uint32_t hw[4], lw[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) split_bf16x2(v[2 * q], v[2 * q + 1], hw[q], lw[q]);
+                        const uint32_t off = sw128_mn_offset(k, p0, kLBO, kSBO);
+                        *reinterpret_cast<uint4*>(dh + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        *reinterpret_cast<uint4*>(dl + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    }
+                } else {
+                    // tile [n positions][32 lines]: line = lane, positions
+                    // [32 warp, +32) along the axis
+                    const bool xin = (int)(lt % ntx) * 32 + lane < nx;
+                    const int p0 = 32 * warp;
+                    float v[32];
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        const int pp = p0 + q;
+                        v[q] = (xin && pp < n) ? st[pp * 32 + lane] - a.ref : 0.0f;
+                    }
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        uint32_t hw[4], lw[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) split_bf16x2(v[8 * c + 2 * q], v[8 * c + 2 * q + 1], hw[q], lw[q]);
+                        const uint32_t off = sw128_mn_offset(lane, p0 + 8 * c, kLBO, kSBO);
+                        *reinterpret_cast<uint4*>(dh + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        *reinterpret_cast<uint4*>(dl + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    }
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&full[b]);
+                    mbar_arrive(&fpe[s3]);
+                }
+            }
+            // after an abort, let the tensor copies still in flight land
+            if (issuer)
+                for (int t = consumed; t < issued; ++t)
+                    mbar_wait_bounded(&fpf[t % kStages], (uint32_t)((t / kStages) & 1), kTries);
         } else {
             for (int t = 0; t < ntiles; ++t) {
                 const int u = t, b = u & 1;
@@ -148,7 +270,7 @@ k_axes_syrk(const AxesArgs a)
                 if (u >= 2) {
                     bool ok = true;
                     if (lane == 0) ok = mbar_wait_sleep_bounded(&empty[b], (uint32_t)(((u >> 1) - 1) & 1), kTries);
-                    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                    ok = __shfl_sync(FULL, ok ? 1 : 0, 0) != 0;
                     if (!ok) {
                         if (lane == 0) {
                             *abort_flag = 1;
@@ -275,6 +397,12 @@ k_axes_syrk(const AxesArgs a)
                 mbar_init(&full[b], kProducers);
                 mbar_init(&empty[b], 1);
             }
+            for (int s3 = 0; s3 < kStages; ++s3) {
+                mbar_inval(&fpf[s3]);
+                mbar_inval(&fpe[s3]);
+                mbar_init(&fpf[s3], 1);
+                mbar_init(&fpe[s3], kProducers);
+            }
             fence_mbar_init();
         }
         __syncthreads();
@@ -284,9 +412,67 @@ k_axes_syrk(const AxesArgs a)
     if (warp == 0) tmem_dealloc(tbase, 512);
 }
 
+// The driver's tiled tensor-map encoder, reached through the runtime's
+// driver entry point (the library does not link the driver library); null
+// if unavailable.
+typedef CUresult (*encode_tiled_fn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static encode_tiled_fn tensor_map_encoder()
+{
+    static encode_tiled_fn fn = []() -> encode_tiled_fn {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<encode_tiled_fn>(f);
+    }();
+    return fn;
+}
+
+// FP32 tensor map of `rank` dimensions (dims[0] innermost, strides in bytes
+// of dims 1 .. rank-1), plain (unswizzled) boxes, zeros outside the tensor
+static bool encode_map(TensorMap128& out, const float* base, int rank, const cuuint64_t* dims,
+                       const cuuint64_t* strides, const cuuint32_t* box)
+{
+    static_assert(sizeof(TensorMap128) == sizeof(CUtensorMap), "tensor map size");
+    encode_tiled_fn enc = tensor_map_encoder();
+    if (!enc) return false;
+    CUtensorMap m;
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<float*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    memcpy(&out, &m, sizeof(m));
+    return true;
+}
+
+// The tensor maps of the TMA path for the current state buffer: axis 0 the
+// [R ny nz][nx] rows in boxes of 32 rows, axes 1 and 2 the [R][nz][ny][nx]
+// grid in boxes of 32 x positions by the whole line.  Needs rows of a
+// multiple of 4 cells (16-byte row pitch) and lines of at most 256 cells.
+static bool axes_tensor_maps(const Handle& h, AxesArgs& a)
+{
+    const cuuint64_t nx = (cuuint64_t)a.nx, ny = (cuuint64_t)a.ny, nz = (cuuint64_t)a.nz, R = (cuuint64_t)a.R;
+    if (nx % 4 != 0 || nx > 256 || ny > 256 || nz > 256) return false;
+    const cuuint64_t d0[2] = {nx, R * ny * nz}, s0[1] = {nx * 4};
+    const cuuint32_t b0[2] = {(cuuint32_t)nx, 32};
+    if (!encode_map(a.map[0], a.T, 2, d0, s0, b0)) return false;
+    const cuuint64_t d4[4] = {nx, ny, nz, R}, s4[3] = {nx * 4, nx * ny * 4, nx * ny * nz * 4};
+    const cuuint32_t b1[4] = {32, (cuuint32_t)ny, 1, 1}, b2[4] = {32, 1, (cuuint32_t)nz, 1};
+    if (h.prob.dim >= 2 && !encode_map(a.map[1], a.T, 4, d4, s4, b1)) return false;
+    if (h.prob.dim >= 3 && !encode_map(a.map[2], a.T, 4, d4, s4, b2)) return false;
+    return true;
+}
+
 cudaError_t launch_axes_syrk(Handle& h)
 {
     AxesArgs a;
+    memset(&a, 0, sizeof(a));
     a.T = (const float*)h.d_state;
     a.partial = h.d_axes_partial;
     a.flags = h.d_flags;
@@ -296,9 +482,15 @@ cudaError_t launch_axes_syrk(Handle& h)
     a.naxes = h.prob.dim;
     a.R = (int)h.R;
     a.ref = (float)h.prob.wall_lo;
-    const int smem = 1024 + 4 * kOpB + 64;
-    cudaFuncSetAttribute(k_axes_syrk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_axes_syrk<<<h.cov_ctas, (kProducers + 1) * 32, smem, h.stream>>>(a);
+    if (axes_tensor_maps(h, a)) {
+        const int smem = 1024 + 4 * kOpB + kStages * kStg + 128;
+        cudaFuncSetAttribute(k_axes_syrk<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_axes_syrk<true><<<h.cov_ctas, (kProducers + 1) * 32, smem, h.stream>>>(a);
+    } else {
+        const int smem = 1024 + 4 * kOpB + 128;
+        cudaFuncSetAttribute(k_axes_syrk<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_axes_syrk<false><<<h.cov_ctas, (kProducers + 1) * 32, smem, h.stream>>>(a);
+    }
     h.launches += 1;
     return cudaGetLastError();
 }

@@ -141,12 +141,22 @@ struct Step3DArgs {
 };
 
 // Arguments of the per-axis line-covariance kernel (S(k) along each axis).
+// An encoded tensor map (the driver's 128-byte CUtensorMap) for tiled TMA
+// copies, kept opaque here so that only the unit that encodes it needs the
+// driver API header.
+struct alignas(64) TensorMap128 {
+    unsigned long long w[16];
+};
+
 struct AxesArgs {
     const float* T;       // [R][nz][ny][nx] state after the sampling step
     double* partial;      // [naxes][G][256*256] per-CTA FP64 partial line covariances
     int* flags;
     int nx, ny, nz, naxes, R;
     float ref;
+    // TMA path: axis 0 tiles of 32 rows from the [R ny nz][nx] view, axes 1
+    // and 2 tiles of 32 lines from the [R][nz][ny][nx] view
+    TensorMap128 map[3];
 };
 
 // Arguments of the full 2D structure-factor kernel.
