@@ -195,7 +195,7 @@ WORKLOADS = {
         # (predictor, corrector on T*), and the trapezoid (T + T* + inc) / 2
         chunk=10_000, ops=OPS_1D_PC, bytes=None,
         kernel="k_step1d_cov<16,16,dirichlet,heat,pc>",
-        traffic=dict(bytes=100.738816e6 + 41.408256e6, realizations=4096)),   # profiles/k_step1d_cov_pc_gradient_rod_pc.md
+        traffic=dict(bytes=100.735744e6 + 41.127936e6, realizations=4096)),   # profiles/k_step1d_cov_pc_gradient_rod_pc.md
     "species_2d": dict(
         leg_chunk=1000, leg_steps=10,
         make=lambda W: W.species_2d(want_sk=1),
@@ -245,7 +245,7 @@ WORKLOADS = {
               "stencil, moments and S(k) along x, y, z (line covariance on tcgen05) every 10 steps"),
         chunk=100, ops=OPS_3D, bytes=8.0 + 16.0 / 10,
         kernel="k_step3d<float,8,heat>",
-        traffic=dict(bytes=576.138240e6 + 499.718656e6, realizations=8),    # profiles/k_step3d_cube_3d.md
+        traffic=dict(bytes=576.348416e6 + 499.231488e6, realizations=8),    # profiles/k_step3d_cube_3d.md
         # per realization and sample: for each axis a SYRK over all lines
         # (cells / n_a lines x n_a^2 MAC), 3 split products, 2 flop per MAC
         stats_kernel="k_axes_syrk", stats_flop=lambda p: 3 * 2 * sum(
@@ -257,7 +257,7 @@ WORKLOADS = {
               "r = 0.2 each, per-instance seeds, FP32, moments every 10 steps after 1e4, one CUDA-graph "
               "launch per step batch"),
         chunk=2560, ops=OPS_1D, bytes=None, kernel="k_step1d_batch<*>",
-        traffic=dict(bytes=83.965184e6 + 42.347520e6, realizations=1)),    # profiles/k_step1d_batch_batched_rods.md
+        traffic=dict(bytes=83.822336e6 + 42.458624e6, realizations=1)),    # profiles/k_step1d_batch_batched_rods.md
     "two_material_rod": dict(
         leg_chunk=10000, leg_steps=10,
         make=lambda W: W.two_material_rod(),
@@ -267,7 +267,7 @@ WORKLOADS = {
               "steps after 1e5"),
         chunk=10_000, ops=OPS_1D_VAR, bytes=None,
         kernel="k_step1d_cov<16,16,dirichlet,heat,var>",
-        traffic=dict(bytes=100.738048e6 + 41.069824e6, realizations=4096)),   # profiles/k_step1d_cov_var_two_material_rod.md
+        traffic=dict(bytes=100.736512e6 + 40.870400e6, realizations=4096)),   # profiles/k_step1d_cov_var_two_material_rod.md
     "gradient_rod_cn": dict(
         leg_chunk=10000, leg_steps=10,
         make=lambda W: W.gradient_rod(scheme="cn", dt=2.0, want_cov=0),
@@ -276,7 +276,8 @@ WORKLOADS = {
               "exercise of Sec. 6) at r = 2, ten times forward Euler's stability limit; a partitioned "
               "tridiagonal solve per realization and step"),
         chunk=10_000, ops=OPS_1D_THETA, bytes=None,
-        kernel="k_step1d<float,32,8,dirichlet,heat,theta>", traffic=None),
+        kernel="k_step1d<float,32,8,dirichlet,heat,theta>",
+        traffic=dict(bytes=21.046272e6, realizations=4096)),   # profiles/k_step1d_theta_gradient_rod_cn.md
     "oracle_rod": dict(
         leg_chunk=10000, leg_steps=3,
         make=lambda W: W.oracle_rod(want_cov=0, want_sk=0),
