@@ -435,8 +435,8 @@ static encode_tiled_fn tensor_map_encoder()
 
 // FP32 tensor map of `rank` dimensions (dims[0] innermost, strides in bytes
 // of dims 1 .. rank-1), plain (unswizzled) boxes, zeros outside the tensor
-static bool encode_map(TensorMap128& out, const float* base, int rank, const cuuint64_t* dims,
-                       const cuuint64_t* strides, const cuuint32_t* box)
+bool encode_tensor_map_f32(TensorMap128& out, const float* base, int rank, const uint64_t* dims,
+                           const uint64_t* strides, const uint32_t* box)
 {
     static_assert(sizeof(TensorMap128) == sizeof(CUtensorMap), "tensor map size");
     encode_tiled_fn enc = tensor_map_encoder();
@@ -461,11 +461,11 @@ static bool axes_tensor_maps(const Handle& h, AxesArgs& a)
     if (nx % 4 != 0 || nx > 256 || ny > 256 || nz > 256) return false;
     const cuuint64_t d0[2] = {nx, R * ny * nz}, s0[1] = {nx * 4};
     const cuuint32_t b0[2] = {(cuuint32_t)nx, 32};
-    if (!encode_map(a.map[0], a.T, 2, d0, s0, b0)) return false;
+    if (!encode_tensor_map_f32(a.map[0], a.T, 2, d0, s0, b0)) return false;
     const cuuint64_t d4[4] = {nx, ny, nz, R}, s4[3] = {nx * 4, nx * ny * 4, nx * ny * nz * 4};
     const cuuint32_t b1[4] = {32, (cuuint32_t)ny, 1, 1}, b2[4] = {32, 1, (cuuint32_t)nz, 1};
-    if (h.prob.dim >= 2 && !encode_map(a.map[1], a.T, 4, d4, s4, b1)) return false;
-    if (h.prob.dim >= 3 && !encode_map(a.map[2], a.T, 4, d4, s4, b2)) return false;
+    if (h.prob.dim >= 2 && !encode_tensor_map_f32(a.map[1], a.T, 4, d4, s4, b1)) return false;
+    if (h.prob.dim >= 3 && !encode_tensor_map_f32(a.map[2], a.T, 4, d4, s4, b2)) return false;
     return true;
 }
 

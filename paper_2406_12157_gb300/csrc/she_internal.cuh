@@ -148,6 +148,13 @@ struct alignas(64) TensorMap128 {
     unsigned long long w[16];
 };
 
+// Encode an FP32 tensor map (rank <= 4; dims[0] innermost, strides in
+// bytes of dims 1 .. rank-1, box sizes per dimension) for tiled TMA copies:
+// unswizzled boxes, zeros outside the tensor.  False if the driver's encoder
+// is unavailable or refuses the shape.
+bool encode_tensor_map_f32(TensorMap128& out, const float* base, int rank, const uint64_t* dims,
+                           const uint64_t* strides, const uint32_t* box);
+
 struct AxesArgs {
     const float* T;       // [R][nz][ny][nx] state after the sampling step
     double* partial;      // [naxes][G][256*256] per-CTA FP64 partial line covariances
@@ -169,6 +176,7 @@ struct Sk2dArgs {
     int* flags;
     int nx, ny, R;
     float ref;
+    TensorMap128 map;     // TMA path: the [R ny][nx] state in boxes of 16 columns x ny rows
 };
 
 // One instance of a batch of uneven 1D problems.

@@ -35,6 +35,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 
 #include "she_internal.cuh"
 #include "tc05.cuh"
@@ -144,9 +145,15 @@ __device__ __forceinline__ bool named_and(int id, int n, bool p)
 // Every wait is bounded and gives up when another thread has; the kernel then
 // lets its copies and MMAs finish (bounded), frees its tensor memory, sets
 // the error flag and returns.
+// TMA: delta reaches shared memory as FP32 tiles of 16 columns x ny rows by
+// tiled tensor copies (two tiles in flight, in the workers' staging area,
+// which the split does not share with the drain), and the workers split it
+// from there; otherwise they load it from device memory themselves.
+template <bool TMA>
 __global__ void __launch_bounds__(288, 1)
 k_sk2d(const __grid_constant__ Sk2dArgs a)
 {
+    constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* bufs = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* stage = bufs + kStages * kChunk;                          // [8 workers][kStage]
@@ -158,7 +165,8 @@ k_sk2d(const __grid_constant__ Sk2dArgs a)
     uint64_t* row_done = tmem_free + 1;
     uint64_t* col_done = row_done + 1;
     uint64_t* fin = col_done + 1;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 1);
+    uint64_t* fpf = fin + 1;                         // [2] FP32 delta tile landed (TMA)
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(fpf + 2);
     volatile int* s_abort = reinterpret_cast<volatile int*>(tslot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nx = a.nx, ny = a.ny;
@@ -177,7 +185,7 @@ k_sk2d(const __grid_constant__ Sk2dArgs a)
             mbar_init(&full[b], 1);
             mbar_init(&empty[b], 1);
         }
-        for (uint64_t* b = x_ready; b <= fin; ++b) mbar_init(b, 1);
+        for (uint64_t* b = x_ready; b <= fin + 2; ++b) mbar_init(b, 1);     // ... fin, fpf[2]
         *s_abort = 0;
         fence_mbar_init();
     }
@@ -266,6 +274,13 @@ k_sk2d(const __grid_constant__ Sk2dArgs a)
         const int wt = tid - 32;                     // 0 .. 255
         const int q4 = warp & 3;                     // tensor-memory lane quarter of this warp
         const int hh = (warp - 1) >> 2;              // which half of the work
+        // all workers: a bounded wait, agreed on by all of them
+        auto wait_all = [&](uint64_t* bar, uint32_t parity) -> bool {
+            const bool done = wait(bar, parity);
+            const bool all = named_and(kWorkBar, kWorkers, done);
+            fence_after_sync();
+            return all;
+        };
         // split delta of realization rho into the scratch (k = x, mn = y).
         // Lane (a, b) = (lane / 8, lane % 8) of a warp tile owns x = x0 + a and
         // the eight rows 64 Y + 8 b .. + 7: the eight lanes of one x then write
@@ -274,7 +289,7 @@ k_sk2d(const __grid_constant__ Sk2dArgs a)
         // half-written per instruction).  A warp takes 8 columns x 256 rows per
         // pass (two x0, four Y: 64 loads per lane in flight); the second x0
         // reads the other half of the first one's 32-byte sectors from L1.
-        auto split = [&](int rho) {
+        auto split_ldg = [&](int rho) -> bool {
             const float* X = a.T + (size_t)rho * (size_t)ncell;
             const int la = lane >> 3, lb = lane & 7;
             for (int x8 = 8 * (warp - 1); x8 < 16 * n1; x8 += 64) {
@@ -308,13 +323,77 @@ k_sk2d(const __grid_constant__ Sk2dArgs a)
                     }
                 }
             }
+            return true;
         };
-        // all workers: a bounded wait, agreed on by all of them
-        auto wait_all = [&](uint64_t* bar, uint32_t parity) -> bool {
-            const bool done = wait(bar, parity);
-            const bool all = named_and(kWorkBar, kWorkers, done);
-            fence_after_sync();
-            return all;
+        // TMA path: chunk c of the split (x in [16 c, 16 c + 16)) arrives as an
+        // FP32 tile [ny][16] in half g & 1 of the staging area (g: the CTA's
+        // running tile count, the same in every worker).  A warp takes blocks
+        // of 16 rows: lane (x, p) = (lane % 16, lane / 16) reads rows 2 r + p of
+        // the block (two rows are 32 consecutive words: no bank conflicts),
+        // then the partner lanes (x, 0) and (x, 1) swap four values, so that
+        // lane (x, 0) holds rows 0 .. 7 and lane (x, 1) rows 8 .. 15 of column
+        // x: one 16-byte chunk of the image each.
+        uint32_t tile_g = 0, tile_issued = 0;
+        auto issue_tile = [&](int rho, int c) {        // thread wt == 0
+            const uint32_t g = tile_issued++;
+            uint64_t* bar = &fpf[g & 1];
+            mbar_arrive_expect_tx(bar, (uint32_t)ny * 16u * 4u);
+            tma_load_2d(stage + (size_t)(g & 1) * 16384, &a.map, 16 * c, rho * ny, bar);
+        };
+        auto split_tma = [&](int rho) -> bool {
+            // the staging area was last used by the drain (generic proxy)
+            fence_proxy_async_smem();
+            named_sync(kWorkBar, kWorkers);
+            if (wt == 0) {
+                issue_tile(rho, 0);
+                if (n1 > 1) issue_tile(rho, 1);
+            }
+            const int x = lane & 15, p = lane >> 4;
+            const int nb = (ny + 15) / 16;
+            for (int c = 0; c < n1; ++c) {
+                const uint32_t g = tile_g + (uint32_t)c;
+                if (!wait_all(&fpf[g & 1], (g >> 1) & 1u)) {
+                    tile_g = g;                     // tiles from g on may still be in flight
+                    return false;
+                }
+                const float* st = reinterpret_cast<const float*>(stage + (size_t)(g & 1) * 16384);
+                const bool xin = 16 * c + x < nx;
+                unsigned char* dh = xs + (size_t)c * 2 * kImg;
+                for (int blk = warp - 1; blk < nb; blk += kWorkers / 32) {
+                    const int y0 = 16 * blk;
+                    float v[8];
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) {
+                        const int y = y0 + 2 * r + p;
+                        v[r] = (xin && y < ny) ? st[y * 16 + x] - a.ref : 0.0f;
+                    }
+                    float rv[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) rv[q] = __shfl_xor_sync(FULL, p ? v[q] : v[4 + q], 16);
+                    float o[8];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        o[2 * q] = p ? rv[q] : v[q];
+                        o[2 * q + 1] = p ? v[4 + q] : rv[q];
+                    }
+                    uint32_t hw[4], lw[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) split_bf16x2(o[2 * q], o[2 * q + 1], hw[q], lw[q]);
+                    const uint32_t off = sw128_mn_offset(x, y0 + 8 * p, kLBO, kSBO);
+                    *reinterpret_cast<uint4*>(dh + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    *reinterpret_cast<uint4*>(dh + kImg + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                }
+                // every worker has read this half: the copy of chunk c + 2 may take it
+                fence_proxy_async_smem();
+                named_sync(kWorkBar, kWorkers);
+                if (wt == 0 && c + 2 < n1) issue_tile(rho, c + 2);
+            }
+            tile_g += (uint32_t)n1;
+            return true;
+        };
+        auto split = [&](int rho) -> bool {
+            if constexpr (TMA) return split_tma(rho);
+            else return split_ldg(rho);
         };
         // all workers: publish their writes, then one arrival
         auto publish = [&](uint64_t* bar) {
@@ -324,12 +403,13 @@ k_sk2d(const __grid_constant__ Sk2dArgs a)
             if (wt == 0) mbar_arrive(bar);
         };
 
+        bool split_ok = true;
         if (nr > 0) {
-            split((int)blockIdx.x);
-            publish(x_ready);
+            split_ok = split((int)blockIdx.x);
+            if (split_ok) publish(x_ready);
         }
         float* P = a.partial + (size_t)blockIdx.x * 256 * 129;          // [kx][ky]
-        for (int i = 0; i < nr; ++i) {
+        for (int i = 0; i < nr && split_ok; ++i) {
             // ---------- drain D1 -> split Y in the scratch (k = y, mn = p) ----------
             // A thread holds row y (its tensor-memory lane); its 32 columns go
             // through the warp's staging area so that the copy-out writes whole
@@ -365,7 +445,7 @@ k_sk2d(const __grid_constant__ Sk2dArgs a)
             publish(y_ready);
             // ---------- split the next realization meanwhile ----------
             if (i + 1 < nr) {
-                split((int)blockIdx.x + (i + 1) * (int)gridDim.x);
+                if (!split((int)blockIdx.x + (i + 1) * (int)gridDim.x)) break;
                 publish(x_ready);
             }
             // ---------- epilogue: |hat delta|^2 into P[kx][ky] ----------
@@ -415,6 +495,11 @@ k_sk2d(const __grid_constant__ Sk2dArgs a)
             }
             publish(tmem_free);
         }
+        if constexpr (TMA) {
+            // after an abort, let the tensor copies still in flight land
+            if (wt == 0)
+                for (uint32_t g = tile_g; g < tile_issued; ++g) mbar_wait_bounded(&fpf[g & 1], (g >> 1) & 1u, kTries2);
+        }
     }
     fence_before_sync();
     __syncthreads();
@@ -449,6 +534,7 @@ cudaError_t launch_sk2d_tables(Handle& h)
 cudaError_t launch_sk2d(Handle& h)
 {
     Sk2dArgs a;
+    memset(&a, 0, sizeof(a));
     a.T = (const float*)h.d_state;
     a.partial = h.d_sk_partial;
     a.wimg = h.d_sk_w;
@@ -460,8 +546,17 @@ cudaError_t launch_sk2d(Handle& h)
     a.R = (int)h.R;
     a.ref = (float)h.prob.wall_lo;
     const int smem = 1024 + kStages * kChunk + 8 * kStage + 256;
-    cudaFuncSetAttribute(k_sk2d, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_sk2d<<<h.sk_ctas, 288, smem, h.stream>>>(a);
+    // the TMA path: the [R ny][nx] state (rows of a multiple of 4 cells) in
+    // boxes of 16 columns x ny rows
+    const uint64_t dims[2] = {(uint64_t)a.nx, (uint64_t)a.R * (uint64_t)a.ny}, strides[1] = {(uint64_t)a.nx * 4};
+    const uint32_t box[2] = {16, (uint32_t)a.ny};
+    if (a.nx % 4 == 0 && a.ny <= 256 && encode_tensor_map_f32(a.map, a.T, 2, dims, strides, box)) {
+        cudaFuncSetAttribute(k_sk2d<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_sk2d<true><<<h.sk_ctas, 288, smem, h.stream>>>(a);
+    } else {
+        cudaFuncSetAttribute(k_sk2d<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_sk2d<false><<<h.sk_ctas, 288, smem, h.stream>>>(a);
+    }
     h.launches += 1;
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && ++h.sk_partial_samples >= 64) e = launch_sk2d_flush(h);
