@@ -143,8 +143,9 @@ typedef struct she_params {
     int32_t tc_lags;      /* L > 0: accumulate the time correlation
                              <delta_i(t + l K) delta_i(t)>, l = 0..L-1 sampling intervals,
                              over the pairs of samples since the last reset (the exercise on
-                             <dT_i^{n+m} dT_i^n>, Sec. 6); L <= 64; 1D, kernel auto, FP64 or
-                             FP32 without the covariance (otherwise SHE_ERR_UNSUPPORTED) */
+                             <dT_i^{n+m} dT_i^n>, Sec. 6); L <= 64; 1D, kernel auto
+                             (otherwise SHE_ERR_UNSUPPORTED); beside the FP32 tensor-core
+                             covariance the lag sums go straight to FP64 device memory */
     /* A rod of several materials (the iron / aluminium exercise, Sec. 6):
      * host arrays of n[0] values, read during she_init only, both NULL for a
      * uniform rod (kappa and rho_cv) or both set (kappa and rho_cv are then

@@ -85,6 +85,67 @@ __device__ __forceinline__ Real face_amp(Real face_value, Real amp2, Real s_heat
     return s_heat * face_value;
 }
 
+// Time correlation at one sample (the exercise on <dT_i^{n+m} dT_i^n>,
+// Sec. 6) for the lane's C cells of realization rho, with this sample's
+// delta d: store d in the realization's ring of the last L samples, then add
+// d x (the sample l back) for every lag l with a partner in this trajectory,
+// into the warp's shared-memory partials tcp ([L][C][32] lane-contiguous,
+// flushed at launch end) or, with tcp null, straight into the FP64 sums
+// (one writer per element, so the fire-and-forget adds are exact).  nsamp:
+// the samples taken earlier in this launch.
+template <typename Real, int C, bool RAGGED>
+__device__ __forceinline__ void time_corr_sample(const Step1DArgs<Real>& a, int rho, int i0, const Real (&d)[C],
+                                                 int nsamp, Real* tcp)
+{
+    const int N = a.N;
+    const int L = a.tc_lags;
+    const long long st = a.tc_s0 + nsamp;
+    Real* ring = a.tc_ring + (size_t)rho * (size_t)L * (size_t)N;
+    double* acc = a.tc_acc + (size_t)rho * (size_t)L * (size_t)N;
+    const int slot = (int)(st % L);
+    const long long since = st - a.tc_base;     // samples of this trajectory before st
+    const int lmax = since < (long long)(L - 1) ? (int)since : L - 1;
+    // the lane's C cells are contiguous: 16-byte moves when the
+    // ring rows are aligned (N a multiple of 4, a full row)
+    const bool vec = !RAGGED && (N % 4 == 0);
+    Real* srow = ring + (size_t)slot * N + i0;
+    if (vec) {
+        vstore<C>(srow, d);
+    } else {
+#pragma unroll
+        for (int j = 0; j < C; ++j)
+            if (!RAGGED || i0 + j < N) srow[j] = d[j];
+    }
+    if (tcp) {
+#pragma unroll
+        for (int j = 0; j < C; ++j) tcp[j * 32] = fma(d[j], d[j], tcp[j * 32]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < C; ++j)
+            if (!RAGGED || i0 + j < N) atomicAdd(&acc[i0 + j], (double)(d[j] * d[j]));
+    }
+    int ps = slot;                            // slot of sample st - l, (st - l) % L
+    for (int l = 1; l <= lmax; ++l) {
+        ps = ps == 0 ? L - 1 : ps - 1;
+        const Real* prow = ring + (size_t)ps * N + i0;
+        Real pv[C];
+        if (vec) {
+            vload<C>(prow, pv);
+        } else {
+#pragma unroll
+            for (int j = 0; j < C; ++j) pv[j] = (!RAGGED || i0 + j < N) ? prow[j] : Real(0);
+        }
+        if (tcp) {
+#pragma unroll
+            for (int j = 0; j < C; ++j) tcp[(l * C + j) * 32] = fma(d[j], pv[j], tcp[(l * C + j) * 32]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < C; ++j)
+                if (!RAGGED || i0 + j < N) atomicAdd(&acc[(size_t)l * N + i0 + j], (double)(d[j] * pv[j]));
+        }
+    }
+}
+
 // RK: the noise key comes as precomputed round keys (a kernel parameter of
 // the single-problem kernels); otherwise as (key0, key1) (per-instance keys
 // of the batch kernel).

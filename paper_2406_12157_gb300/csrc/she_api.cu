@@ -800,10 +800,9 @@ she_status she_init(const she_params* p, she_handle** out)
     if (st == SHE_OK && (p->tc_lags < 0 || p->tc_lags > 64)) {
         st = SHE_ERR_INVALID_ARG; msg = "she: tc_lags must be in [0, 64]";
     }
-    if (st == SHE_OK && p->tc_lags > 0 &&
-        (p->dim != 1 || p->kernel != SHE_KERNEL_AUTO || (p->precision == SHE_FP32 && need_cov))) {
+    if (st == SHE_OK && p->tc_lags > 0 && (p->dim != 1 || p->kernel != SHE_KERNEL_AUTO)) {
         st = SHE_ERR_UNSUPPORTED;
-        msg = "she: the time correlation runs on the 1D row kernel (kernel auto; FP64, or FP32 without the covariance)";
+        msg = "she: the time correlation runs on the fused 1D kernels (kernel auto)";
     }
     if (st == SHE_OK && need_cov && (p->dim != 1 || p->n[0] > 256)) {
         st = SHE_ERR_INVALID_ARG; msg = "she: the covariance needs a 1D grid of at most 256 cells";

@@ -385,6 +385,10 @@ cudaError_t launch_step1d_plain(Handle& h, uint32_t step0, int nsteps);
 cudaError_t launch_plain_step_scratch(const Problem& p, int R, const double* T, double* Tn, double* G,
                                       uint32_t n, uint32_t stream0, int stochastic, cudaStream_t st);
 cudaError_t launch_step1d_cov(Handle& h, uint32_t step0, int nsteps, bool has_samples);
+// the fused covariance kernels that also sample the time correlation (their
+// own object of step1d_cov.cu)
+cudaError_t launch_cov_with_time_corr(const Step1DArgs<float>& a, const CovArgs& c, int grid, bool dir, bool sp,
+                                      bool pc, bool var, cudaStream_t st);
 cudaError_t launch_reduce_cov(const Handle& h, double* d_out);
 cudaError_t launch_reduce_sum(const double* partial, int64_t n, int G, double* out, cudaStream_t st);
 cudaError_t launch_cov_fp64(Handle& h);

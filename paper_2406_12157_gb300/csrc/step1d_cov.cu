@@ -48,7 +48,7 @@ constexpr int cov_smem_bytes(int warps)
 // Returns the number of snapshots.  Kept out of line so that the stepping
 // loop of the kernel compiles as it does without the tensor-core code
 // (measured: inlined, the sampling launches are about 1 % slower).
-__device__ __noinline__ int cov_mma_issue(unsigned char* base, uint64_t* full, uint64_t* empty,
+static __device__ __noinline__ int cov_mma_issue(unsigned char* base, uint64_t* full, uint64_t* empty,
                                           volatile int* abort_flag, int* flags, uint32_t tbase, int Mh, int Nm,
                                           uint32_t idesc, uint32_t idesc1, int next_s, int nsteps, int K)
 {
@@ -88,7 +88,9 @@ __device__ __noinline__ int cov_mma_issue(unsigned char* base, uint64_t* full, u
 
 // VAR: a rod of several materials; its material table (N + 1 entries) is
 // copied into shared memory after the moment partials.
-template <int C, int LPR, bool DIR, bool SPECIES, bool RAGGED, bool PC, bool VAR>
+// TC: the time correlation is sampled too (its code stays out of the other
+// instances, whose register allocation it would change).
+template <int C, int LPR, bool DIR, bool SPECIES, bool RAGGED, bool PC, bool VAR, bool TC>
 __global__ void __launch_bounds__(32 * LPR, 1)
 k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
 {
@@ -244,6 +246,19 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&full[b]);
             }
+            // the time correlation (its FP64 lag sums in device memory: the
+            // per-warp partials of the row kernel do not fit beside the
+            // operand buffers), after the hand-off so that the MMAs start
+            if (TC && active) {
+                float d[C];
+#pragma unroll
+                for (int j = 0; j < C; ++j) {
+                    const float ref = VAR ? tab[RowT::tpos(i0 + j)].ref
+                                          : DIR ? fmaf(dref, (float)(i0 + j) + 0.5f, wlo) : wlo;
+                    d[j] = (RAGGED && i0 + j >= N) ? 0.0f : T[j] - ref;
+                }
+                time_corr_sample<float, C, RAGGED>(a, rho, i0, d, nsnap, nullptr);
+            }
         }
         ++nsnap;
     }
@@ -316,21 +331,22 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
     }
 }
 
-template <int C, int LPR, bool DIR, bool SP, bool PC, bool VAR>
+template <int C, int LPR, bool DIR, bool SP, bool PC, bool VAR, bool TC>
 static cudaError_t launch_cov_layout(const Step1DArgs<float>& a, const CovArgs& c, int grid, cudaStream_t st)
 {
     const int smem = cov_smem_bytes<C>(LPR) + (VAR ? (C * LPR + 1) * (int)sizeof(Coef1D<float>) : 0);
     if (a.N == C * LPR) {
-        auto k = k_step1d_cov<C, LPR, DIR, SP, false, PC, VAR>;
+        auto k = k_step1d_cov<C, LPR, DIR, SP, false, PC, VAR, TC>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         k<<<grid, 32 * LPR, smem, st>>>(a, c);
     } else {
-        auto k = k_step1d_cov<C, LPR, DIR, SP, true, PC, VAR>;
+        auto k = k_step1d_cov<C, LPR, DIR, SP, true, PC, VAR, TC>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         k<<<grid, 32 * LPR, smem, st>>>(a, c);
     }
     return cudaGetLastError();
 }
+
 
 // Lanes per realization of the layout chosen for N: 4-cell layouts up to 128
 // cells, above 16 cells x 16 lanes (15 stepping warps per CTA, two
@@ -352,31 +368,54 @@ static int cov_slots_per_cta(int N, bool pc)
     return (lpr - 1) * (32 / lpr);
 }
 
-template <bool DIR, bool SP, bool PC, bool VAR>
+template <bool DIR, bool SP, bool PC, bool VAR, bool TC>
 static cudaError_t launch_cov_ds(const Step1DArgs<float>& a, const CovArgs& c, int grid, cudaStream_t st)
 {
     const int N = a.N;
-    if (N <= 16) return launch_cov_layout<4, 4, DIR, SP, PC, VAR>(a, c, grid, st);
-    if (N <= 32) return launch_cov_layout<4, 8, DIR, SP, PC, VAR>(a, c, grid, st);
-    if (N <= 64) return launch_cov_layout<4, 16, DIR, SP, PC, VAR>(a, c, grid, st);
-    if (N <= 128) return launch_cov_layout<4, 32, DIR, SP, PC, VAR>(a, c, grid, st);
-    return launch_cov_layout<16, 16, DIR, SP, PC, VAR>(a, c, grid, st);
+    if (N <= 16) return launch_cov_layout<4, 4, DIR, SP, PC, VAR, TC>(a, c, grid, st);
+    if (N <= 32) return launch_cov_layout<4, 8, DIR, SP, PC, VAR, TC>(a, c, grid, st);
+    if (N <= 64) return launch_cov_layout<4, 16, DIR, SP, PC, VAR, TC>(a, c, grid, st);
+    if (N <= 128) return launch_cov_layout<4, 32, DIR, SP, PC, VAR, TC>(a, c, grid, st);
+    return launch_cov_layout<16, 16, DIR, SP, PC, VAR, TC>(a, c, grid, st);
 }
 
-template <bool DIR, bool SP>
+template <bool DIR, bool SP, bool TC>
 static cudaError_t launch_cov_scheme(const Step1DArgs<float>& a, const CovArgs& c, int grid, bool pc, bool var,
                                      cudaStream_t st)
 {
     if constexpr (!SP) {
         if (var) {        // a rod of several materials (heat)
-            if (pc) return launch_cov_ds<DIR, SP, true, true>(a, c, grid, st);
-            return launch_cov_ds<DIR, SP, false, true>(a, c, grid, st);
+            if (pc) return launch_cov_ds<DIR, SP, true, true, TC>(a, c, grid, st);
+            return launch_cov_ds<DIR, SP, false, true, TC>(a, c, grid, st);
         }
     }
-    if (pc) return launch_cov_ds<DIR, SP, true, false>(a, c, grid, st);
-    return launch_cov_ds<DIR, SP, false, false>(a, c, grid, st);
+    if (pc) return launch_cov_ds<DIR, SP, true, false, TC>(a, c, grid, st);
+    return launch_cov_ds<DIR, SP, false, false, TC>(a, c, grid, st);
 }
 
+template <bool TC>
+static cudaError_t launch_cov_all(const Step1DArgs<float>& a, const CovArgs& c, int grid, bool dir, bool sp,
+                                  bool pc, bool var, cudaStream_t st)
+{
+    if (dir)
+        return sp ? launch_cov_scheme<true, true, TC>(a, c, grid, pc, false, st)
+                  : launch_cov_scheme<true, false, TC>(a, c, grid, pc, var, st);
+    return sp ? launch_cov_scheme<false, true, TC>(a, c, grid, pc, false, st)
+              : launch_cov_scheme<false, false, TC>(a, c, grid, pc, var, st);
+}
+
+// The unit compiles once per value of SHE_COV_TC (the kernels with the time
+// correlation in one object, the others in the second, so that the two
+// halves build in parallel); without the macro it holds both.
+#if !defined(SHE_COV_TC) || SHE_COV_TC == 1
+cudaError_t launch_cov_with_time_corr(const Step1DArgs<float>& a, const CovArgs& c, int grid, bool dir, bool sp,
+                                      bool pc, bool var, cudaStream_t st)
+{
+    return launch_cov_all<true>(a, c, grid, dir, sp, pc, var, st);
+}
+#endif
+
+#if !defined(SHE_COV_TC) || SHE_COV_TC == 0
 cudaError_t launch_step1d_cov(Handle& h, uint32_t step0, int nsteps, bool has_samples)
 {
     Step1DArgs<float> a;
@@ -400,6 +439,12 @@ cudaError_t launch_step1d_cov(Handle& h, uint32_t step0, int nsteps, bool has_sa
     a.stream0 = h.stream0;
     a.stochastic = h.stochastic;
     a.coef = (const Coef1D<float>*)h.d_coef;
+    a.tc_lags = has_samples ? h.tc_lags : 0;
+    a.tc_s0 = (long long)h.samples_per_real;
+    a.tc_base = (long long)h.tc_base;
+    a.tc_ring = (float*)h.d_tc_ring;
+    a.tc_acc = h.d_tc_acc;
+    a.tc_onchip = 0;
     const bool dir = h.prob.bc == SHE_DIRICHLET;
     const bool sp = h.prob.equation == SHE_SPECIES;
     // waves of at most (stepper warps x realizations per warp) per CTA
@@ -413,13 +458,9 @@ cudaError_t launch_step1d_cov(Handle& h, uint32_t step0, int nsteps, bool has_sa
         c.r_count = (int)std::min<int64_t>(per_wave, h.R - rb);
         c.has_samples = has_samples ? 1 : 0;
         const int grid = (int)std::min<int64_t>(G, c.r_count);
-        cudaError_t e;
-        if (dir)
-            e = sp ? launch_cov_scheme<true, true>(a, c, grid, pc, false, h.stream)
-                   : launch_cov_scheme<true, false>(a, c, grid, pc, h.var, h.stream);
-        else
-            e = sp ? launch_cov_scheme<false, true>(a, c, grid, pc, false, h.stream)
-                   : launch_cov_scheme<false, false>(a, c, grid, pc, h.var, h.stream);
+        const cudaError_t e = a.tc_lags > 0
+                                  ? launch_cov_with_time_corr(a, c, grid, dir, sp, pc, h.var, h.stream)
+                                  : launch_cov_all<false>(a, c, grid, dir, sp, pc, h.var, h.stream);
         h.launches += 1;
         if (e != cudaSuccess) return e;
     }
@@ -449,5 +490,7 @@ cudaError_t launch_reduce_cov(const Handle& h, double* d_out)
     k_reduce_partials<<<(unsigned)((n + 255) / 256), 256, 0, h.stream>>>(h.d_cov_partial, n, h.cov_ctas, d_out);
     return cudaGetLastError();
 }
+
+#endif  // SHE_COV_TC == 0
 
 }  // namespace she

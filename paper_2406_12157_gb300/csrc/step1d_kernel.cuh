@@ -101,19 +101,6 @@ k_step1d(const __grid_constant__ Step1DArgs<Real> a)
         if (s == next_s) {                 // sample after step m = n + 1 (Eq. (3.9))
             next_s += a.K;
             if (a.tc_lags > 0 && active) {
-                // time correlation (the exercise on <dT_i^{n+m} dT_i^n>, Sec. 6):
-                // store this sample of delta in the realization's ring, then add
-                // delta_i(s) delta_i(s - l) for every lag l with a partner, into
-                // the warp's shared-memory partials (flushed at launch end) or,
-                // where they do not fit, straight into the FP64 sums (one writer
-                // per element, so the fire-and-forget adds are exact)
-                const int L = a.tc_lags;
-                const long long st = a.tc_s0 + nsamp;
-                Real* ring = a.tc_ring + (size_t)rho * (size_t)L * (size_t)N;
-                double* acc = a.tc_acc + (size_t)rho * (size_t)L * (size_t)N;
-                const int slot = (int)(st % L);
-                const long long since = st - a.tc_base;   // samples of this trajectory before st
-                const int lmax = since < (long long)(L - 1) ? (int)since : L - 1;
                 Real d[C];
 #pragma unroll
                 for (int j = 0; j < C; ++j) {
@@ -121,45 +108,7 @@ k_step1d(const __grid_constant__ Step1DArgs<Real> a)
                     const Real ref = VAR ? tab[RowT::tpos(i)].ref : DIR ? fma(dref, Real(i0 + j) + half, wlo) : wlo;
                     d[j] = (RAGGED && i >= N) ? Real(0) : T[j] - ref;
                 }
-                // the lane's C cells are contiguous: 16-byte moves when the
-                // ring rows are aligned (N a multiple of 4, a full row)
-                const bool vec = !RAGGED && (N % 4 == 0);
-                Real* srow = ring + (size_t)slot * N + i0;
-                if (vec) {
-                    vstore<C>(srow, d);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < C; ++j)
-                        if (!RAGGED || i0 + j < N) srow[j] = d[j];
-                }
-                if (a.tc_onchip) {
-#pragma unroll
-                    for (int j = 0; j < C; ++j) tcp[j * 32] = fma(d[j], d[j], tcp[j * 32]);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < C; ++j)
-                        if (!RAGGED || i0 + j < N) atomicAdd(&acc[i0 + j], (double)(d[j] * d[j]));
-                }
-                int ps = slot;                            // slot of sample st - l, (st - l) % L
-                for (int l = 1; l <= lmax; ++l) {
-                    ps = ps == 0 ? L - 1 : ps - 1;
-                    const Real* prow = ring + (size_t)ps * N + i0;
-                    Real pv[C];
-                    if (vec) {
-                        vload<C>(prow, pv);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < C; ++j) pv[j] = (!RAGGED || i0 + j < N) ? prow[j] : Real(0);
-                    }
-                    if (a.tc_onchip) {
-#pragma unroll
-                        for (int j = 0; j < C; ++j) tcp[(l * C + j) * 32] = fma(d[j], pv[j], tcp[(l * C + j) * 32]);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < C; ++j)
-                            if (!RAGGED || i0 + j < N) atomicAdd(&acc[(size_t)l * N + i0 + j], (double)(d[j] * pv[j]));
-                    }
-                }
+                time_corr_sample<Real, C, RAGGED>(a, rho, i0, d, nsamp, a.tc_onchip ? tcp : nullptr);
             }
             ++nsamp;
 #pragma unroll

@@ -2,8 +2,9 @@
 exercise on <dT_i^{n+m} dT_i^n>, Sec. 6) against the FP64 oracle, through the
 C ABI: FP64 to 1e-9 relative across launch windows (forward Euler and
 predictor-corrector, with and without the FP64 covariance), FP32 within the
-single-precision trajectory error, the pairs restarting at she_reset_stats
-and at a state overwrite, and the unsupported combinations refused."""
+single-precision trajectory error, also beside the tensor-core covariance,
+the pairs restarting at she_reset_stats and at a state overwrite, and the
+unsupported combinations refused."""
 import numpy as np
 import pytest
 
@@ -49,6 +50,25 @@ def test_fp32_time_corr_matches_oracle():
     assert np.max(np.abs(g["time_corr"] - o["time_corr"])) < 1e-3 * scale
 
 
+@pytest.mark.parametrize("N,scheme,var", [(256, "fe", False), (200, "pc", False), (256, "fe", True), (100, "fe", False)])
+def test_fp32_time_corr_beside_the_tensor_core_covariance(N, scheme, var):
+    """FP32 with the covariance: the fused tensor-core kernel takes the time
+    correlation too (its lag sums in FP64 device memory); both statistics
+    against the oracle, the time correlation within the FP32 bar above, the
+    covariance within the bar of the covariance tests."""
+    kw = dict(n=(N, 1, 1), realizations=64, relax_steps=0, stats_interval=10, want_cov=1, tc_lags=6,
+              scheme=scheme)
+    p = W.two_material_rod(cells=N, **kw) if var else W.gradient_rod(**kw)
+    with S.Simulation(p) as sim:
+        sim.step(300)
+        g = sim.stats(time_corr=True, cov=True)
+    o = O.finalize(p, O.run(p, 64, 300, want_cov=1))
+    scale = np.max(np.abs(o["time_corr"]))
+    assert np.max(np.abs(g["time_corr"] - o["time_corr"])) < 1e-3 * scale
+    assert np.max(np.abs(g["cov"] - o["cov"])) < 2e-4 * np.max(np.diag(o["cov"]))
+    assert np.allclose(g["time_corr"][0], g["var"] + (g["mean"] - O.reference_profile(p)) ** 2, rtol=1e-4)
+
+
 def test_pairs_restart_at_reset():
     p = W.oracle_rod(n=(16, 1, 1), realizations=4, stats_interval=2, relax_steps=0, tc_lags=4, want_cov=0,
                      want_sk=0, precision="fp64")
@@ -92,8 +112,7 @@ def test_pairs_restart_at_set_state(device):
     assert np.allclose(g["mean"], ref + mu, rtol=1e-12)
 
 
-@pytest.mark.parametrize("kw,status", [(dict(precision="fp32", want_cov=1), "SHE_ERR_UNSUPPORTED"),
-                                       (dict(kernel="plain"), "SHE_ERR_UNSUPPORTED"),
+@pytest.mark.parametrize("kw,status", [(dict(kernel="plain"), "SHE_ERR_UNSUPPORTED"),
                                        (dict(tc_lags=65), "SHE_ERR_INVALID_ARG")])
 def test_time_corr_outside_its_kernel_is_refused(kw, status):
     q = dict(dict(tc_lags=4, want_cov=0, want_sk=0), **kw)
