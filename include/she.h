@@ -14,9 +14,10 @@
  *   - the predictor-corrector scheme, Sec. 3 (the trapezoidal scheme written
  *     after Eq. (3.3)): the forward-Euler step as predictor T*, then
  *     T' = (T + T* + D(T*) + div G(T*)) / 2 with the face values and the
- *     stencil on T* and the same face noise (1D rows up to 512 cells in one
- *     fused pass; 2D/3D as a predictor pass and a corrector pass that draws
- *     the same normals again);
+ *     stencil on T* and the same face noise (1D rows up to 512 cells and 2D
+ *     grids in one pass, 2D with the predictor one row ahead of the
+ *     corrector; 3D as a predictor pass and a corrector pass that draws the
+ *     same normals again);
  *   - Dirichlet walls: boundary stencil of Eq. (3.8) and the sqrt(2) factor on
  *     the wall-face noise (Sec. 3, text after Eq. (3.8)); periodic wrap;
  *   - stochastic species diffusion, Sec. 4, Eq. (4.7) (noise amplitude
