@@ -495,22 +495,15 @@ cudaError_t launch_axes_syrk(Handle& h)
     return cudaGetLastError();
 }
 
-__global__ void k_reduce_axes(const double* __restrict__ partial, int G, int naxes, double* __restrict__ out)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)naxes * 65536) return;
-    const int axis = (int)(i / 65536);
-    const int64_t e = i % 65536;
-    double s = 0.0;
-    for (int g = 0; g < G; ++g) s += partial[((int64_t)axis * G + g) * 65536 + e];
-    out[i] = s;
-}
-
+// Sum of the per-CTA partial line covariances of each axis (the row
+// reduction of common.cu, one call per axis).
 cudaError_t launch_reduce_axes(const Handle& h, double* d_out)
 {
-    const int64_t n = (int64_t)h.prob.dim * 65536;
-    k_reduce_axes<<<(unsigned)((n + 255) / 256), 256, 0, h.stream>>>(h.d_axes_partial, h.cov_ctas, h.prob.dim, d_out);
-    return cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    for (int axis = 0; axis < h.prob.dim && e == cudaSuccess; ++axis)
+        e = launch_reduce_rows(h.d_axes_partial + (size_t)axis * h.cov_ctas * 65536, 65536, h.cov_ctas, 1,
+                               d_out + (size_t)axis * 65536, h.stream);
+    return e;
 }
 
 }  // namespace she

@@ -149,30 +149,48 @@ cudaError_t launch_init_state(Handle& h)
 
 // Sum the per-realization FP64 accumulators over `batches` contiguous
 // realization batches: out[b][i] = sum over realizations of batch b.
-__global__ void k_reduce_batches(const double* __restrict__ acc1, const double* __restrict__ acc2,
-                                 int64_t cells, int64_t R, int batches, double* out1, double* out2)
+// out[p][i] = sum of in[g][i] over the source rows g of part p, [G p / P,
+// G (p + 1) / P), for i < n (in: G rows of n values).  Deterministic: a
+// block takes a tile of 32 values of one part, its 32 x 32 threads read the
+// part's rows 32 apart (thread row ty from row ty on; coalesced 256-byte
+// rows), then a fixed tree over the 32 thread rows in shared memory.
+__global__ void __launch_bounds__(1024) k_reduce_rows(const double* __restrict__ in, int64_t n, int64_t G, int P,
+                                                      double* __restrict__ out)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= cells) return;
-    for (int b = 0; b < batches; ++b) {
-        const int64_t r0 = R * b / batches, r1 = R * (b + 1) / batches;
-        double a1 = 0.0, a2 = 0.0;
-        for (int64_t r = r0; r < r1; ++r) {
-            a1 += acc1[r * cells + i];
-            a2 += acc2[r * cells + i];
-        }
-        out1[(int64_t)b * cells + i] = a1;
-        out2[(int64_t)b * cells + i] = a2;
+    __shared__ double s[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * 32 + tx;
+    const int p = blockIdx.y;
+    const int64_t g0 = G * p / P, g1 = G * (p + 1) / P;
+    double a = 0.0;
+    if (i < n)
+        for (int64_t g = g0 + ty; g < g1; g += 32) a += in[g * n + i];
+    s[ty][tx] = a;
+    __syncthreads();
+#pragma unroll
+    for (int k = 16; k > 0; k >>= 1) {
+        if (ty < k) s[ty][tx] += s[ty + k][tx];
+        __syncthreads();
     }
+    if (ty == 0 && i < n) out[(int64_t)p * n + i] = s[0][tx];
 }
 
+cudaError_t launch_reduce_rows(const double* in, int64_t n, int64_t G, int P, double* out, cudaStream_t st)
+{
+    if (n <= 0 || P <= 0) return cudaSuccess;
+    const dim3 grid((unsigned)((n + 31) / 32), (unsigned)P);
+    k_reduce_rows<<<grid, 1024, 0, st>>>(in, n, G, P, out);
+    return cudaGetLastError();
+}
+
+// Per-batch sums of the per-realization moment accumulators: batch b holds
+// realizations [R b / B, R (b + 1) / B).
 cudaError_t launch_reduce_batches(const Handle& h, int batches, double* d_out1, double* d_out2)
 {
-    const int tpb = 256;
     const int64_t cells = h.prob.cells;
-    k_reduce_batches<<<(unsigned)((cells + tpb - 1) / tpb), tpb, 0, h.stream>>>(
-        h.d_acc1, h.d_acc2, cells, h.R, batches, d_out1, d_out2);
-    return cudaGetLastError();
+    cudaError_t e = launch_reduce_rows(h.d_acc1, cells, h.R, batches, d_out1, h.stream);
+    if (e == cudaSuccess) e = launch_reduce_rows(h.d_acc2, cells, h.R, batches, d_out2, h.stream);
+    return e;
 }
 
 __global__ void k_noise_probe(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,

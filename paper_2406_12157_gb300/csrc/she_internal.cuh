@@ -408,6 +408,9 @@ cudaError_t launch_init_batch(Handle& h, const float* d_sigma);
 void destroy_batch_graphs(Handle& h);
 cudaError_t launch_reduce_axes(const Handle& h, double* d_out);
 cudaError_t launch_reduce_batches(const Handle& h, int batches, double* d_out1, double* d_out2);
+// out[p][i] = sum of in[g][i] over the rows g of part p ([G p / P, G (p + 1) / P)), i < n;
+// deterministic (a fixed summation tree)
+cudaError_t launch_reduce_rows(const double* in, int64_t n, int64_t G, int P, double* out, cudaStream_t st);
 cudaError_t launch_wait_probe(uint32_t max_tries, int* d_result);
 cudaError_t launch_syrk_probe(const float* d_X, int K, int N, double* d_C, int* d_err);
 cudaError_t launch_noise_probe(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,

@@ -467,28 +467,17 @@ cudaError_t launch_step1d_cov(Handle& h, uint32_t step0, int nsteps, bool has_sa
     return cudaSuccess;
 }
 
-// Sum the per-CTA FP64 partial covariances: out[i] = sum_g partial[g][i].
-__global__ void k_reduce_partials(const double* __restrict__ partial, int64_t n, int G, double* __restrict__ out)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double s = 0.0;
-    for (int g = 0; g < G; ++g) s += partial[(int64_t)g * n + i];
-    out[i] = s;
-}
-
-// out[i] = sum_g partial[g][i] for i < n (any G arrays of n sums back to back)
+// The per-CTA FP64 partial covariances summed (the row reduction of
+// common.cu); any G arrays of n sums back to back the same way.
 cudaError_t launch_reduce_sum(const double* partial, int64_t n, int G, double* out, cudaStream_t st)
 {
-    k_reduce_partials<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(partial, n, G, out);
-    return cudaGetLastError();
+    return launch_reduce_rows(partial, n, G, 1, out, st);
 }
 
 cudaError_t launch_reduce_cov(const Handle& h, double* d_out)
 {
     const int64_t n = (int64_t)h.prob.n[0] * h.prob.n[0];
-    k_reduce_partials<<<(unsigned)((n + 255) / 256), 256, 0, h.stream>>>(h.d_cov_partial, n, h.cov_ctas, d_out);
-    return cudaGetLastError();
+    return launch_reduce_rows(h.d_cov_partial, n, h.cov_ctas, 1, d_out, h.stream);
 }
 
 #endif  // SHE_COV_TC == 0
