@@ -124,8 +124,8 @@ typedef struct she_params {
                              L the second difference with the wall stencil of
                              Eq. (3.8), b its wall terms; no time-step limit
                              (unconditionally stable); 1D, kernel auto, N <= 1024,
-                             a uniform rod, FP64 or FP32 without the covariance
-                             (otherwise SHE_ERR_UNSUPPORTED) */
+                             a uniform rod (otherwise SHE_ERR_UNSUPPORTED); with the
+                             FP32 covariance the tensor-core kernel steps it */
     int32_t stochastic;   /* 1: thermal noise on; 0: deterministic (alpha = 0) */
     int32_t perturb_ic;   /* 1: T_ref + sigma N(0,1) per cell, sigma^2 = eps T_mid^2
                              (heat) or eps_c c_mid (species); zero-sum on periodic grids */

@@ -56,8 +56,10 @@ VARIANTS = {
         ("%s_%s_%s_theta" % (real[0], "dir" if d else "per", "sp" if s else "heat"),
          ["-DSHE_V_REAL=%s" % real, "-DSHE_V_DIR=%d" % d, "-DSHE_V_SP=%d" % s, "-DSHE_V_IMP=1"])
         for real in ("float", "double") for d in (0, 1) for s in (0, 1)],
-    # the fused covariance kernels without and with the time correlation
-    "step1d_cov.cu": [("notc", ["-DSHE_COV_TC=0"]), ("tc", ["-DSHE_COV_TC=1"])],
+    # the fused covariance kernels: explicit or implicit step, without and with the time correlation
+    "step1d_cov.cu": [("fe", ["-DSHE_COV_TC=0", "-DSHE_COV_IMP=0"]), ("tc", ["-DSHE_COV_TC=1", "-DSHE_COV_IMP=0"]),
+                      ("imp", ["-DSHE_COV_TC=0", "-DSHE_COV_IMP=1"]),
+                      ("imp_tc", ["-DSHE_COV_TC=1", "-DSHE_COV_IMP=1"])],
 }
 
 

@@ -840,10 +840,9 @@ she_status she_init(const she_params* p, she_handle** out)
         st = SHE_ERR_UNSUPPORTED; msg = "she: the fused 1D kernels take rows of at most 1024 cells (the plain form any)";
     }
     if (st == SHE_OK && (p->scheme == SHE_BE || p->scheme == SHE_CN) &&
-        (p->dim != 1 || p->kernel != SHE_KERNEL_AUTO || p->lambda_cells || (need_cov && p->precision == SHE_FP32))) {
+        (p->dim != 1 || p->kernel != SHE_KERNEL_AUTO || p->lambda_cells)) {
         st = SHE_ERR_UNSUPPORTED;
-        msg = "she: the implicit schemes run on the fused 1D kernel (kernel auto, a uniform rod; FP64, or FP32 "
-              "without the covariance)";
+        msg = "she: the implicit schemes run on the fused 1D kernels (kernel auto, a uniform rod)";
     }
     if (st == SHE_OK && p->lambda_cells && p->kernel != SHE_KERNEL_AUTO) {
         st = SHE_ERR_UNSUPPORTED; msg = "she: a rod of several materials runs on the fused kernels (kernel auto)";
@@ -973,7 +972,8 @@ she_status she_init(const she_params* p, she_handle** out)
         sc.insert(sc.end(), m.cap.begin(), m.cap.end());
         if (e == cudaSuccess) e = cudaMemcpy(h->d_sigma, sc.data(), sc.size() * sizeof(double), cudaMemcpyHostToDevice);
     }
-    if (e == cudaSuccess && (h->prob.scheme == SHE_BE || h->prob.scheme == SHE_CN)) e = she::setup_implicit(*h);
+    if (e == cudaSuccess && (h->prob.scheme == SHE_BE || h->prob.scheme == SHE_CN))   // the factor tables of the
+        e = she::setup_implicit(*h, h->want_cov && h->precision == SHE_FP32 ? she::cov_layout(h->prob.n[0]) : 0);  // kernel's layout
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_acc1, 0, nstate * sizeof(double), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_acc2, 0, nstate * sizeof(double), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flags, 0, sizeof(int), h->stream);

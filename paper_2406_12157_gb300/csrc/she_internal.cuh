@@ -389,6 +389,16 @@ cudaError_t launch_step1d_cov(Handle& h, uint32_t step0, int nsteps, bool has_sa
 // own object of step1d_cov.cu)
 cudaError_t launch_cov_with_time_corr(const Step1DArgs<float>& a, const CovArgs& c, int grid, bool dir, bool sp,
                                       bool pc, bool var, cudaStream_t st);
+// the fused covariance kernels with the implicit step (backward Euler /
+// Crank-Nicolson; uniform rod), without and with the time correlation (their
+// own objects of step1d_cov.cu)
+cudaError_t launch_cov_implicit(const Step1DArgs<float>& a, const CovArgs& c, int grid, bool dir, bool sp,
+                                cudaStream_t st);
+cudaError_t launch_cov_implicit_time_corr(const Step1DArgs<float>& a, const CovArgs& c, int grid, bool dir,
+                                          bool sp, cudaStream_t st);
+// layout code (cells per lane x 100 + lanes per realization) of the FP32
+// covariance kernel for rows of N cells
+int cov_layout(int N);
 cudaError_t launch_reduce_cov(const Handle& h, double* d_out);
 cudaError_t launch_reduce_sum(const double* partial, int64_t n, int G, double* out, cudaStream_t st);
 cudaError_t launch_cov_fp64(Handle& h);

@@ -89,8 +89,11 @@ static __device__ __noinline__ int cov_mma_issue(unsigned char* base, uint64_t* 
 // VAR: a rod of several materials; its material table (N + 1 entries) is
 // copied into shared memory after the moment partials.
 // TC: the time correlation is sampled too (its code stays out of the other
-// instances, whose register allocation it would change).
-template <int C, int LPR, bool DIR, bool SPECIES, bool RAGGED, bool PC, bool VAR, bool TC>
+// instances, whose register allocation it would change).  IMP: the step is
+// the implicit theta scheme (backward Euler / Crank-Nicolson); its factor
+// tables (C x LPR rows, LPR x LPR reduced weights) are copied into shared
+// memory after the moment partials.
+template <int C, int LPR, bool DIR, bool SPECIES, bool RAGGED, bool PC, bool VAR, bool TC, bool IMP>
 __global__ void __launch_bounds__(32 * LPR, 1)
 k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
 {
@@ -108,6 +111,8 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
     float* mom = reinterpret_cast<float*>(base + 4 * kOpBytes + 64);
     Coef1D<float>* tab = reinterpret_cast<Coef1D<float>*>(mom + LPR * 2 * C * 32);
+    Solve1D<float>* stab = reinterpret_cast<Solve1D<float>*>(mom + LPR * 2 * C * 32);
+    Reduced1D<float>* rtab = reinterpret_cast<Reduced1D<float>*>(stab + C * LPR);
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -134,6 +139,10 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
     for (int i = threadIdx.x; i < 4 * kOpBytes / 16; i += blockDim.x)
         reinterpret_cast<uint4*>(base)[i] = make_uint4(0u, 0u, 0u, 0u);
     using RowT = Row1D<float, C, LPR, DIR, SPECIES, RAGGED, false, VAR>;
+    if constexpr (IMP) {   // stored transposed (RowT::tpos; source lane m of block k at m * LPR + k)
+        for (int k = threadIdx.x; k < C * LPR; k += blockDim.x) stab[RowT::tpos(k)] = a.solve[k];
+        for (int k = threadIdx.x; k < LPR * LPR; k += blockDim.x) rtab[(k % LPR) * LPR + k / LPR] = a.red[k];
+    }
     if constexpr (VAR)     // rows past N repeat row N; stored transposed (RowT::tpos)
         for (int k = threadIdx.x; k <= C * LPR; k += blockDim.x) tab[RowT::tpos(k)] = a.coef[k < a.N ? k : a.N];
 
@@ -193,7 +202,13 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
         nsnap = __shfl_sync(FULL, nsnap, 0);
     } else
     for (int s = 0; s < a.nsteps; ++s) {
-        if (warp_active) rowst.template advance<PC>(T, a.step0 + (uint32_t)s);
+        if (warp_active) {
+            if constexpr (IMP)
+                rowst.template step_theta<!DIR>(T, a.step0 + (uint32_t)s, stab, rtab, a.omt, a.th2r_lo, a.th2r_hi,
+                                                a.sm_cg, a.sm_inv);
+            else
+                rowst.template advance<PC>(T, a.step0 + (uint32_t)s);
+        }
         if (s != next_s) continue;
         next_s += a.K;
         const int b = nsnap & 1;
@@ -331,16 +346,17 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
     }
 }
 
-template <int C, int LPR, bool DIR, bool SP, bool PC, bool VAR, bool TC>
+template <int C, int LPR, bool DIR, bool SP, bool PC, bool VAR, bool TC, bool IMP>
 static cudaError_t launch_cov_layout(const Step1DArgs<float>& a, const CovArgs& c, int grid, cudaStream_t st)
 {
-    const int smem = cov_smem_bytes<C>(LPR) + (VAR ? (C * LPR + 1) * (int)sizeof(Coef1D<float>) : 0);
+    const int smem = cov_smem_bytes<C>(LPR) + (VAR ? (C * LPR + 1) * (int)sizeof(Coef1D<float>) : 0) +
+                     (IMP ? C * LPR * (int)sizeof(Solve1D<float>) + LPR * LPR * (int)sizeof(Reduced1D<float>) : 0);
     if (a.N == C * LPR) {
-        auto k = k_step1d_cov<C, LPR, DIR, SP, false, PC, VAR, TC>;
+        auto k = k_step1d_cov<C, LPR, DIR, SP, false, PC, VAR, TC, IMP>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         k<<<grid, 32 * LPR, smem, st>>>(a, c);
     } else {
-        auto k = k_step1d_cov<C, LPR, DIR, SP, true, PC, VAR, TC>;
+        auto k = k_step1d_cov<C, LPR, DIR, SP, true, PC, VAR, TC, IMP>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         k<<<grid, 32 * LPR, smem, st>>>(a, c);
     }
@@ -368,54 +384,89 @@ static int cov_slots_per_cta(int N, bool pc)
     return (lpr - 1) * (32 / lpr);
 }
 
-template <bool DIR, bool SP, bool PC, bool VAR, bool TC>
+template <bool DIR, bool SP, bool PC, bool VAR, bool TC, bool IMP>
 static cudaError_t launch_cov_ds(const Step1DArgs<float>& a, const CovArgs& c, int grid, cudaStream_t st)
 {
     const int N = a.N;
-    if (N <= 16) return launch_cov_layout<4, 4, DIR, SP, PC, VAR, TC>(a, c, grid, st);
-    if (N <= 32) return launch_cov_layout<4, 8, DIR, SP, PC, VAR, TC>(a, c, grid, st);
-    if (N <= 64) return launch_cov_layout<4, 16, DIR, SP, PC, VAR, TC>(a, c, grid, st);
-    if (N <= 128) return launch_cov_layout<4, 32, DIR, SP, PC, VAR, TC>(a, c, grid, st);
-    return launch_cov_layout<16, 16, DIR, SP, PC, VAR, TC>(a, c, grid, st);
+    if (N <= 16) return launch_cov_layout<4, 4, DIR, SP, PC, VAR, TC, IMP>(a, c, grid, st);
+    if (N <= 32) return launch_cov_layout<4, 8, DIR, SP, PC, VAR, TC, IMP>(a, c, grid, st);
+    if (N <= 64) return launch_cov_layout<4, 16, DIR, SP, PC, VAR, TC, IMP>(a, c, grid, st);
+    if (N <= 128) return launch_cov_layout<4, 32, DIR, SP, PC, VAR, TC, IMP>(a, c, grid, st);
+    return launch_cov_layout<16, 16, DIR, SP, PC, VAR, TC, IMP>(a, c, grid, st);
 }
 
-template <bool DIR, bool SP, bool TC>
+template <bool DIR, bool SP, bool TC, bool IMP>
 static cudaError_t launch_cov_scheme(const Step1DArgs<float>& a, const CovArgs& c, int grid, bool pc, bool var,
                                      cudaStream_t st)
 {
-    if constexpr (!SP) {
-        if (var) {        // a rod of several materials (heat)
-            if (pc) return launch_cov_ds<DIR, SP, true, true, TC>(a, c, grid, st);
-            return launch_cov_ds<DIR, SP, false, true, TC>(a, c, grid, st);
+    if constexpr (IMP) {       // the implicit schemes: a uniform rod, no predictor-corrector
+        (void)pc;
+        (void)var;
+        return launch_cov_ds<DIR, SP, false, false, TC, true>(a, c, grid, st);
+    } else {
+        if constexpr (!SP) {
+            if (var) {        // a rod of several materials (heat)
+                if (pc) return launch_cov_ds<DIR, SP, true, true, TC, false>(a, c, grid, st);
+                return launch_cov_ds<DIR, SP, false, true, TC, false>(a, c, grid, st);
+            }
         }
+        if (pc) return launch_cov_ds<DIR, SP, true, false, TC, false>(a, c, grid, st);
+        return launch_cov_ds<DIR, SP, false, false, TC, false>(a, c, grid, st);
     }
-    if (pc) return launch_cov_ds<DIR, SP, true, false, TC>(a, c, grid, st);
-    return launch_cov_ds<DIR, SP, false, false, TC>(a, c, grid, st);
 }
 
-template <bool TC>
+template <bool TC, bool IMP>
 static cudaError_t launch_cov_all(const Step1DArgs<float>& a, const CovArgs& c, int grid, bool dir, bool sp,
                                   bool pc, bool var, cudaStream_t st)
 {
     if (dir)
-        return sp ? launch_cov_scheme<true, true, TC>(a, c, grid, pc, false, st)
-                  : launch_cov_scheme<true, false, TC>(a, c, grid, pc, var, st);
-    return sp ? launch_cov_scheme<false, true, TC>(a, c, grid, pc, false, st)
-              : launch_cov_scheme<false, false, TC>(a, c, grid, pc, var, st);
+        return sp ? launch_cov_scheme<true, true, TC, IMP>(a, c, grid, pc, false, st)
+                  : launch_cov_scheme<true, false, TC, IMP>(a, c, grid, pc, var, st);
+    return sp ? launch_cov_scheme<false, true, TC, IMP>(a, c, grid, pc, false, st)
+              : launch_cov_scheme<false, false, TC, IMP>(a, c, grid, pc, var, st);
 }
 
-// The unit compiles once per value of SHE_COV_TC (the kernels with the time
-// correlation in one object, the others in the second, so that the two
-// halves build in parallel); without the macro it holds both.
-#if !defined(SHE_COV_TC) || SHE_COV_TC == 1
+// The unit compiles once per (SHE_COV_TC, SHE_COV_IMP) pair, each object
+// holding the kernels of one combination (with or without the time
+// correlation, explicit or implicit step), so that they build in parallel;
+// without the macros it holds all.
+#if defined(SHE_COV_TC) && defined(SHE_COV_IMP)
+#define SHE_COV_PART(tc, imp) (SHE_COV_TC == (tc) && SHE_COV_IMP == (imp))
+#else
+#define SHE_COV_PART(tc, imp) 1
+#endif
+
+#if SHE_COV_PART(1, 0)
 cudaError_t launch_cov_with_time_corr(const Step1DArgs<float>& a, const CovArgs& c, int grid, bool dir, bool sp,
                                       bool pc, bool var, cudaStream_t st)
 {
-    return launch_cov_all<true>(a, c, grid, dir, sp, pc, var, st);
+    return launch_cov_all<true, false>(a, c, grid, dir, sp, pc, var, st);
+}
+#endif
+#if SHE_COV_PART(0, 1)
+cudaError_t launch_cov_implicit(const Step1DArgs<float>& a, const CovArgs& c, int grid, bool dir, bool sp,
+                                cudaStream_t st)
+{
+    return launch_cov_all<false, true>(a, c, grid, dir, sp, false, false, st);
+}
+#endif
+#if SHE_COV_PART(1, 1)
+cudaError_t launch_cov_implicit_time_corr(const Step1DArgs<float>& a, const CovArgs& c, int grid, bool dir,
+                                          bool sp, cudaStream_t st)
+{
+    return launch_cov_all<true, true>(a, c, grid, dir, sp, false, false, st);
 }
 #endif
 
-#if !defined(SHE_COV_TC) || SHE_COV_TC == 0
+#if SHE_COV_PART(0, 0)
+// The layout code (cells per lane x 100 + lanes per realization) of the
+// covariance kernel for rows of N cells: the implicit schemes set up their
+// factor tables for it.
+int cov_layout(int N)
+{
+    return (N <= 128 ? 4 : 16) * 100 + cov_lpr(N, false);
+}
+
 cudaError_t launch_step1d_cov(Handle& h, uint32_t step0, int nsteps, bool has_samples)
 {
     Step1DArgs<float> a;
@@ -447,6 +498,17 @@ cudaError_t launch_step1d_cov(Handle& h, uint32_t step0, int nsteps, bool has_sa
     a.tc_onchip = 0;
     const bool dir = h.prob.bc == SHE_DIRICHLET;
     const bool sp = h.prob.equation == SHE_SPECIES;
+    const bool imp = h.prob.scheme == SHE_BE || h.prob.scheme == SHE_CN;
+    if (imp) {
+        const double theta = h.prob.scheme == SHE_BE ? 1.0 : 0.5;
+        a.solve = (const Solve1D<float>*)h.d_solve;
+        a.red = (const Reduced1D<float>*)h.d_theta_red;
+        a.omt = (float)(1.0 - theta);
+        a.th2r_lo = (float)(dir ? theta * 2.0 * h.prob.r * h.prob.wall_lo : 0.0);
+        a.th2r_hi = (float)(dir ? theta * 2.0 * h.prob.r * h.prob.wall_hi : 0.0);
+        a.sm_cg = (float)h.sm_cg;
+        a.sm_inv = (float)h.sm_inv;
+    }
     // waves of at most (stepper warps x realizations per warp) per CTA
     const int G = h.cov_ctas;
     const bool pc = h.prob.scheme == SHE_PC;
@@ -458,9 +520,11 @@ cudaError_t launch_step1d_cov(Handle& h, uint32_t step0, int nsteps, bool has_sa
         c.r_count = (int)std::min<int64_t>(per_wave, h.R - rb);
         c.has_samples = has_samples ? 1 : 0;
         const int grid = (int)std::min<int64_t>(G, c.r_count);
-        const cudaError_t e = a.tc_lags > 0
-                                  ? launch_cov_with_time_corr(a, c, grid, dir, sp, pc, h.var, h.stream)
-                                  : launch_cov_all<false>(a, c, grid, dir, sp, pc, h.var, h.stream);
+        const cudaError_t e =
+            imp ? (a.tc_lags > 0 ? launch_cov_implicit_time_corr(a, c, grid, dir, sp, h.stream)
+                                 : launch_cov_implicit(a, c, grid, dir, sp, h.stream))
+                : (a.tc_lags > 0 ? launch_cov_with_time_corr(a, c, grid, dir, sp, pc, h.var, h.stream)
+                                 : launch_cov_all<false, false>(a, c, grid, dir, sp, pc, h.var, h.stream));
         h.launches += 1;
         if (e != cudaSuccess) return e;
     }
@@ -480,6 +544,6 @@ cudaError_t launch_reduce_cov(const Handle& h, double* d_out)
     return launch_reduce_rows(h.d_cov_partial, n, h.cov_ctas, 1, d_out, h.stream);
 }
 
-#endif  // SHE_COV_TC == 0
+#endif  // SHE_COV_PART(0, 0)
 
 }  // namespace she

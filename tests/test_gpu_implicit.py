@@ -9,13 +9,15 @@ realization and step by the kernel's partitioned tridiagonal solve.
   species, ragged rows, every implicit layout (4 x 4 ... 32 x 32 cells x
   lanes; 8 x 32, 16 x 16 and 32 x 8 for the same 256-cell row), time steps below and far above forward Euler's limit, several
   launch windows; moments, the FP64 covariance and the time correlation.
-* FP32: one step from a shared state within 2e-5.
+* FP32: one step from a shared state within 2e-5; with the covariance (the
+  tensor-core kernel stepping the implicit scheme), the mean, the covariance
+  and the time correlation of whole runs against the oracle.
 * Deterministic limit at r = 30: every sine mode multiplied per step by
   (1 - (1 - theta) x) / (1 + theta x).
 * About 10^6 realizations of 4- and 5-cell rods within 4.5 batch SE of the
   exact moment recursion of the theta scheme.
-* Refusals: FP32 with the covariance, 2D, the plain form, a rod of several
-  materials, 1D rows longer than 1024 cells on the fused kernels.
+* Refusals: 2D, the plain form, a rod of several materials, 1D rows longer
+  than 1024 cells on the fused kernels.
 """
 import numpy as np
 import pytest
@@ -104,6 +106,30 @@ def test_fp32_one_step_from_shared_state(N, bc, scheme):
     assert rel_err(got.astype(np.float64), ref) < 2e-5
 
 
+@pytest.mark.parametrize("N,bc,scheme,eq,lags", [(256, "dirichlet", "cn", "heat", 0), (200, "periodic", "be", "heat", 4),
+                                                 (100, "dirichlet", "be", "species", 0),
+                                                 (30, "periodic", "cn", "heat", 3), (16, "dirichlet", "cn", "heat", 0),
+                                                 (13, "periodic", "be", "species", 2), (64, "dirichlet", "be", "heat", 5)])
+def test_fp32_covariance_on_the_tensor_cores(N, bc, scheme, eq, lags):
+    """FP32 with the covariance: the fused tensor-core kernel steps the
+    implicit scheme with the factor tables of its own layout (4 cells per lane
+    up to 128 cells, 16 x 16 above); whole runs against the FP64 oracle, the
+    covariance within the bar of the explicit FP32 covariance tests."""
+    R, steps = 64, 240
+    p = _rod(N, bc, scheme, 2.5, eq, R=R, precision="fp32", want_cov=1, tc_lags=lags, stats_interval=6)
+    with S.Simulation(p, steps_per_launch=70) as sim:
+        sim.step(steps)
+        g = sim.stats(cov=True, time_corr=lags > 0)
+    o = O.finalize(p, O.run(p, R, steps, want_cov=1))
+    tref = O.reference_profile(p)
+    assert np.max(np.abs(g["mean"] - o["mean"])) < 1e-5 * np.max(np.abs(o["mean"]))
+    assert np.max(np.abs(g["cov"] - o["cov"])) < 2e-4 * np.max(np.diag(o["cov"]))
+    assert np.max(np.abs(g["var"] - np.diag(o["cov"]))) < 2e-4 * np.max(np.diag(o["cov"]))
+    if lags:
+        assert np.max(np.abs(g["time_corr"] - o["time_corr"])) < 1e-3 * np.max(np.abs(o["time_corr"]))
+        assert np.allclose(g["time_corr"][0], g["var"] + (g["mean"] - tref) ** 2, rtol=1e-4)
+
+
 @pytest.mark.parametrize("scheme", ["be", "cn"])
 def test_deterministic_modes_at_large_time_step(scheme):
     N, r, steps = 100, 30.0, 25
@@ -150,7 +176,6 @@ def test_moments_match_exact_recursion(N, bc, eq, scheme, r, precision):
 
 
 @pytest.mark.parametrize("kw,status", [
-    (dict(precision="fp32", want_cov=1), "SHE_ERR_UNSUPPORTED"),
     (dict(kernel="plain"), "SHE_ERR_UNSUPPORTED"),
     (dict(n=(1025, 1, 1)), "SHE_ERR_UNSUPPORTED"),
 ])
