@@ -86,90 +86,32 @@ static __device__ __noinline__ int cov_mma_issue(unsigned char* base, uint64_t* 
     return ns;
 }
 
-// VAR: a rod of several materials; its material table (N + 1 entries) is
-// copied into shared memory after the moment partials.
-// TC: the time correlation is sampled too (its code stays out of the other
-// instances, whose register allocation it would change).  IMP: the step is
-// the implicit theta scheme (backward Euler / Crank-Nicolson); its factor
-// tables (C x LPR rows, LPR x LPR reduced weights) are copied into shared
-// memory after the moment partials.
+// The stepping warps' part of k_step1d_cov.  This warp's realizations are
+// the CTA's slots slot0 + lane / LPR (those below count), each on LPR lanes
+// of C cells: it steps them through the launch, writes every snapshot into
+// operand buffer nsnap & 1 and arrives on that buffer's full barrier, and at
+// the end stores the state and adds its moment partials (wmom: 2 x C x 32
+// floats) into the FP64 accumulators.  Returns the number of snapshots.
 template <int C, int LPR, bool DIR, bool SPECIES, bool RAGGED, bool PC, bool VAR, bool TC, bool IMP>
-__global__ void __launch_bounds__(32 * LPR, 1)
-k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
+__device__ __forceinline__ int cov_step_warp(const Step1DArgs<float>& a, unsigned char* base, uint64_t* full,
+                                             uint64_t* empty, volatile int* abort_flag, float* wmom,
+                                             const Coef1D<float>* tab, const Solve1D<float>* stab,
+                                             const Reduced1D<float>* rtab, int rb, int count, int slot0,
+                                             bool use_tc)
 {
     constexpr unsigned FULL = 0xffffffffu;
-    constexpr int RPW = 32 / LPR;
-    constexpr int NBUF = 2;
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    // stage b: hi at base + 2b * kOpBytes, lo right after it
+    using RowT = Row1D<float, C, LPR, DIR, SPECIES, RAGGED, false, VAR>;
     auto op_hi = [&](int b) { return base + 2 * b * kOpBytes; };
     auto op_lo = [&](int b) { return base + (2 * b + 1) * kOpBytes; };
-    uint64_t* full = reinterpret_cast<uint64_t*>(base + 4 * kOpBytes);   // [2]: snapshot written
-    uint64_t* empty = full + 2;                                           // [2]: MMAs done reading
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(empty + 2);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
-    float* mom = reinterpret_cast<float*>(base + 4 * kOpBytes + 64);
-    Coef1D<float>* tab = reinterpret_cast<Coef1D<float>*>(mom + LPR * 2 * C * 32);
-    Solve1D<float>* stab = reinterpret_cast<Solve1D<float>*>(mom + LPR * 2 * C * 32);
-    Reduced1D<float>* rtab = reinterpret_cast<Reduced1D<float>*>(stab + C * LPR);
-
     const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
     const int sl = lane % LPR;
-    const int g = blockIdx.x;
-    // realizations of this CTA inside the wave [r_begin, r_begin + r_count)
-    const int rb = c.r_begin + (int)((long long)c.r_count * g / gridDim.x);
-    const int re = c.r_begin + (int)((long long)c.r_count * (g + 1) / gridDim.x);
-    const int count = re - rb;
-    // warps 0..LPR-2 step realizations (slots warp*RPW + segment); the last
-    // warp issues the MMAs
-    constexpr int MMA_WARP = LPR - 1;
-    const bool is_mma_warp = (warp == MMA_WARP);
-    const int slot = warp * RPW + lane / LPR;
-    const bool active = !is_mma_warp && slot < count;
-    const bool warp_active = !is_mma_warp && warp * RPW < count;
-    const int active_warps = (count + RPW - 1) / RPW;
+    const int slot = slot0 + lane / LPR;
+    const bool active = slot < count;
+    const bool warp_active = slot0 < count;
     const int rho = active ? rb + slot : (count > 0 ? rb : 0);
-
-    float* sm1 = mom + warp * (2 * C * 32) + lane;
-    float* sm2 = sm1 + C * 32;
-
-    // zero both operand stages (rows of absent realizations stay zero)
-    for (int i = threadIdx.x; i < 4 * kOpBytes / 16; i += blockDim.x)
-        reinterpret_cast<uint4*>(base)[i] = make_uint4(0u, 0u, 0u, 0u);
-    using RowT = Row1D<float, C, LPR, DIR, SPECIES, RAGGED, false, VAR>;
-    if constexpr (IMP) {   // stored transposed (RowT::tpos; source lane m of block k at m * LPR + k)
-        for (int k = threadIdx.x; k < C * LPR; k += blockDim.x) stab[RowT::tpos(k)] = a.solve[k];
-        for (int k = threadIdx.x; k < LPR * LPR; k += blockDim.x) rtab[(k % LPR) * LPR + k / LPR] = a.red[k];
-    }
-    if constexpr (VAR)     // rows past N repeat row N; stored transposed (RowT::tpos)
-        for (int k = threadIdx.x; k <= C * LPR; k += blockDim.x) tab[RowT::tpos(k)] = a.coef[k < a.N ? k : a.N];
-
     const int N = a.N;
-    const int Mh = (N + 127) / 128;
-    const int Nm = ((N + 15) / 16) * 16;
-    uint32_t ncols = 32;
-    while ((int)ncols < Mh * Nm) ncols <<= 1;
-    const bool use_tc = c.has_samples != 0;
-    if (threadIdx.x == 0) {
-        *abort_flag = 0;
-        if (use_tc) {
-            for (int b = 0; b < NBUF; ++b) {
-                mbar_init(&full[b], (uint32_t)active_warps);
-                mbar_init(&empty[b], 1);
-            }
-            fence_mbar_init();
-        }
-    }
-    if (use_tc && warp == 0) {
-        tmem_alloc(tslot, ncols);
-        tmem_relinquish();
-    }
-    fence_before_sync();
-    __syncthreads();
-    fence_after_sync();
-    const uint32_t tbase = use_tc ? *tslot : 0u;
+    float* sm1 = wmom + lane;
+    float* sm2 = sm1 + C * 32;
 
     RowT rowst;   // keys in registers: measured faster here
     rowst.init(a, sl, rho);
@@ -188,19 +130,6 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
     const float dref = DIR ? (a.wall_hi - a.wall_lo) / (float)N : 0.0f;
     int next_s = first_sample_index(a.step0, a.relax, a.K, a.nsteps);
     int nsnap = 0;
-    const uint32_t idesc = idesc_bf16_f32(128, Nm, true, true);
-    // C is symmetric: the second 128-row half (rows 128..) needs only columns
-    // 128.. (N = Nm - 128, whose B operand is the A operand itself); the
-    // lower-left block is the transpose of the first half's upper-right one
-    const uint32_t idesc1 = Mh > 1 ? idesc_bf16_f32(128, Nm - 128, true, true) : idesc;
-
-    if (is_mma_warp) {
-        // MMA issue: one thread, once every stepping warp wrote the snapshot
-        if (use_tc && lane == 0)
-            nsnap = cov_mma_issue(base, full, empty, abort_flag, a.flags, tbase, Mh, Nm, idesc, idesc1, next_s,
-                                  a.nsteps, a.K);
-        nsnap = __shfl_sync(FULL, nsnap, 0);
-    } else
     for (int s = 0; s < a.nsteps; ++s) {
         if (warp_active) {
             if constexpr (IMP)
@@ -303,6 +232,119 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
         }
     }
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.flags, 1);
+    return nsnap;
+}
+
+// VAR: a rod of several materials; its material table (N + 1 entries) is
+// copied into shared memory after the moment partials.
+// TC: the time correlation is sampled too (its code stays out of the other
+// instances, whose register allocation it would change).  IMP: the step is
+// the implicit theta scheme (backward Euler / Crank-Nicolson); its factor
+// tables (C x LPR rows, LPR x LPR reduced weights) are copied into shared
+// memory after the moment partials.
+// MIX (16 cells x 16 lanes, FE / PC on a uniform rod): a CTA holds at most
+// 30 realizations on 15 stepping warps, two per warp; since a scheduler's
+// share of the launch is set by the instructions of its warps, a CTA with
+// fewer realizations gives count - 15 warps two of them and the others one
+// each on 32 lanes of 8 cells (half a pair-warp's instructions): 27
+// realizations take 3.5 pair-warp loads on the busiest scheduler instead of
+// 4 (warp w runs on scheduler w mod 4).
+template <int C, int LPR, bool DIR, bool SPECIES, bool RAGGED, bool PC, bool VAR, bool TC, bool IMP>
+__global__ void __launch_bounds__(32 * LPR, 1)
+k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int RPW = 32 / LPR;
+    constexpr int NBUF = 2;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // stage b: hi at base + 2b * kOpBytes, lo right after it
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + 4 * kOpBytes);   // [2]: snapshot written
+    uint64_t* empty = full + 2;                                           // [2]: MMAs done reading
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(empty + 2);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+    float* mom = reinterpret_cast<float*>(base + 4 * kOpBytes + 64);
+    Coef1D<float>* tab = reinterpret_cast<Coef1D<float>*>(mom + LPR * 2 * C * 32);
+    Solve1D<float>* stab = reinterpret_cast<Solve1D<float>*>(mom + LPR * 2 * C * 32);
+    Reduced1D<float>* rtab = reinterpret_cast<Reduced1D<float>*>(stab + C * LPR);
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int g = blockIdx.x;
+    // realizations of this CTA inside the wave [r_begin, r_begin + r_count)
+    const int rb = c.r_begin + (int)((long long)c.r_count * g / gridDim.x);
+    const int re = c.r_begin + (int)((long long)c.r_count * (g + 1) / gridDim.x);
+    const int count = re - rb;
+    // warps 0..LPR-2 step realizations; the last warp issues the MMAs
+    constexpr int MMA_WARP = LPR - 1;
+    const bool is_mma_warp = (warp == MMA_WARP);
+    constexpr bool MIX = C == 16 && LPR == 16 && !VAR && !IMP;
+    const int npair = MIX ? (count > MMA_WARP ? count - MMA_WARP : 0) : 0;   // MIX: warps with two
+    const int active_warps = MIX ? count - npair : (count + RPW - 1) / RPW;
+    using RowT = Row1D<float, C, LPR, DIR, SPECIES, RAGGED, false, VAR>;     // the tables' layout
+
+    // zero both operand stages (rows of absent realizations stay zero)
+    for (int i = threadIdx.x; i < 4 * kOpBytes / 16; i += blockDim.x)
+        reinterpret_cast<uint4*>(base)[i] = make_uint4(0u, 0u, 0u, 0u);
+    if constexpr (IMP) {   // stored transposed (RowT::tpos; source lane m of block k at m * LPR + k)
+        for (int k = threadIdx.x; k < C * LPR; k += blockDim.x) stab[RowT::tpos(k)] = a.solve[k];
+        for (int k = threadIdx.x; k < LPR * LPR; k += blockDim.x) rtab[(k % LPR) * LPR + k / LPR] = a.red[k];
+    }
+    if constexpr (VAR)     // rows past N repeat row N; stored transposed (RowT::tpos)
+        for (int k = threadIdx.x; k <= C * LPR; k += blockDim.x) tab[RowT::tpos(k)] = a.coef[k < a.N ? k : a.N];
+
+    const int N = a.N;
+    const int Mh = (N + 127) / 128;
+    const int Nm = ((N + 15) / 16) * 16;
+    uint32_t ncols = 32;
+    while ((int)ncols < Mh * Nm) ncols <<= 1;
+    const bool use_tc = c.has_samples != 0;
+    if (threadIdx.x == 0) {
+        *abort_flag = 0;
+        if (use_tc) {
+            for (int b = 0; b < NBUF; ++b) {
+                mbar_init(&full[b], (uint32_t)active_warps);
+                mbar_init(&empty[b], 1);
+            }
+            fence_mbar_init();
+        }
+    }
+    if (use_tc && warp == 0) {
+        tmem_alloc(tslot, ncols);
+        tmem_relinquish();
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tbase = use_tc ? *tslot : 0u;
+
+    int nsnap = 0;
+    if (is_mma_warp) {
+        const uint32_t idesc = idesc_bf16_f32(128, Nm, true, true);
+        // C is symmetric: the second 128-row half (rows 128..) needs only columns
+        // 128.. (N = Nm - 128, whose B operand is the A operand itself); the
+        // lower-left block is the transpose of the first half's upper-right one
+        const uint32_t idesc1 = Mh > 1 ? idesc_bf16_f32(128, Nm - 128, true, true) : idesc;
+        // MMA issue: one thread, once every stepping warp wrote the snapshot
+        if (use_tc && lane == 0)
+            nsnap = cov_mma_issue(base, full, empty, abort_flag, a.flags, tbase, Mh, Nm, idesc, idesc1,
+                                  first_sample_index(a.step0, a.relax, a.K, a.nsteps), a.nsteps, a.K);
+        nsnap = __shfl_sync(FULL, nsnap, 0);
+    } else {
+        float* wmom = mom + warp * (2 * C * 32);
+        if constexpr (MIX) {
+            if (warp >= npair)
+                nsnap = cov_step_warp<C / 2, 2 * LPR, DIR, SPECIES, RAGGED, PC, VAR, TC, IMP>(
+                    a, base, full, empty, abort_flag, wmom, tab, stab, rtab, rb, count, 2 * npair + (warp - npair),
+                    use_tc);
+            else
+                nsnap = cov_step_warp<C, LPR, DIR, SPECIES, RAGGED, PC, VAR, TC, IMP>(
+                    a, base, full, empty, abort_flag, wmom, tab, stab, rtab, rb, count, 2 * warp, use_tc);
+        } else {
+            nsnap = cov_step_warp<C, LPR, DIR, SPECIES, RAGGED, PC, VAR, TC, IMP>(
+                a, base, full, empty, abort_flag, wmom, tab, stab, rtab, rb, count, warp * RPW, use_tc);
+        }
+    }
 
     if (use_tc) {
         __syncthreads();
