@@ -184,7 +184,7 @@ WORKLOADS = {
         kernel="k_step1d_cov<16,16,dirichlet,heat>",
         # DRAM read + write of one launch (2560 steps, mostly the per-CTA
         # covariance flush), ncu capture in profiles/k_step1d_cov_gradient_rod.md
-        traffic=dict(bytes=100.731136e6 + 40.777216e6, realizations=4096)),
+        traffic=dict(bytes=100.741376e6 + 41.261312e6, realizations=4096)),
     "gradient_rod_pc": dict(
         leg_chunk=10000, leg_steps=10,
         make=lambda W: W.gradient_rod(scheme="pc"),
@@ -195,7 +195,7 @@ WORKLOADS = {
         # (predictor, corrector on T*), and the trapezoid (T + T* + inc) / 2
         chunk=10_000, ops=OPS_1D_PC, bytes=None,
         kernel="k_step1d_cov<16,16,dirichlet,heat,pc>",
-        traffic=dict(bytes=100.735744e6 + 41.127936e6, realizations=4096)),   # profiles/k_step1d_cov_pc_gradient_rod_pc.md
+        traffic=dict(bytes=100.781824e6 + 41.127168e6, realizations=4096)),   # profiles/k_step1d_cov_pc_gradient_rod_pc.md
     "species_2d": dict(
         leg_chunk=1000, leg_steps=10,
         make=lambda W: W.species_2d(want_sk=1),
@@ -267,7 +267,7 @@ WORKLOADS = {
               "steps after 1e5"),
         chunk=10_000, ops=OPS_1D_VAR, bytes=None,
         kernel="k_step1d_cov<16,16,dirichlet,heat,var>",
-        traffic=dict(bytes=100.736512e6 + 40.870400e6, realizations=4096)),   # profiles/k_step1d_cov_var_two_material_rod.md
+        traffic=dict(bytes=100.737280e6 + 41.548288e6, realizations=4096)),   # profiles/k_step1d_cov_var_two_material_rod.md
     "gradient_rod_cn": dict(
         leg_chunk=10000, leg_steps=10,
         make=lambda W: W.gradient_rod(scheme="cn", dt=2.0, want_cov=0),
