@@ -267,7 +267,7 @@ WORKLOADS = {
               "steps after 1e5"),
         chunk=10_000, ops=OPS_1D_VAR, bytes=None,
         kernel="k_step1d_cov<16,16,dirichlet,heat,var>",
-        traffic=dict(bytes=100.737280e6 + 41.548288e6, realizations=4096)),   # profiles/k_step1d_cov_var_two_material_rod.md
+        traffic=dict(bytes=100.785664e6 + 41.385216e6, realizations=4096)),   # profiles/k_step1d_cov_var_two_material_rod.md
     "gradient_rod_cn": dict(
         leg_chunk=10000, leg_steps=10,
         make=lambda W: W.gradient_rod(scheme="cn", dt=2.0, want_cov=0),

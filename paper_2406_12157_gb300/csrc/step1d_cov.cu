@@ -242,13 +242,14 @@ __device__ __forceinline__ int cov_step_warp(const Step1DArgs<float>& a, unsigne
 // the implicit theta scheme (backward Euler / Crank-Nicolson); its factor
 // tables (C x LPR rows, LPR x LPR reduced weights) are copied into shared
 // memory after the moment partials.
-// MIX (16 cells x 16 lanes, FE / PC on a uniform rod): a CTA holds at most
+// MIX (16 cells x 16 lanes, the explicit schemes): a CTA holds at most
 // 30 realizations on 15 stepping warps, two per warp; since a scheduler's
 // share of the launch is set by the instructions of its warps, a CTA with
 // fewer realizations gives count - 15 warps two of them and the others one
 // each on 32 lanes of 8 cells (half a pair-warp's instructions): 27
 // realizations take 3.5 pair-warp loads on the busiest scheduler instead of
-// 4 (warp w runs on scheduler w mod 4).
+// 4 (warp w runs on scheduler w mod 4).  A rod of several materials keeps a
+// second copy of its table in the single warps' transposed layout.
 template <int C, int LPR, bool DIR, bool SPECIES, bool RAGGED, bool PC, bool VAR, bool TC, bool IMP>
 __global__ void __launch_bounds__(32 * LPR, 1)
 k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
@@ -278,7 +279,7 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
     // warps 0..LPR-2 step realizations; the last warp issues the MMAs
     constexpr int MMA_WARP = LPR - 1;
     const bool is_mma_warp = (warp == MMA_WARP);
-    constexpr bool MIX = C == 16 && LPR == 16 && !VAR && !IMP;
+    constexpr bool MIX = C == 16 && LPR == 16 && !IMP;
     const int npair = MIX ? (count > MMA_WARP ? count - MMA_WARP : 0) : 0;   // MIX: warps with two
     const int active_warps = MIX ? count - npair : (count + RPW - 1) / RPW;
     using RowT = Row1D<float, C, LPR, DIR, SPECIES, RAGGED, false, VAR>;     // the tables' layout
@@ -290,8 +291,16 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
         for (int k = threadIdx.x; k < C * LPR; k += blockDim.x) stab[RowT::tpos(k)] = a.solve[k];
         for (int k = threadIdx.x; k < LPR * LPR; k += blockDim.x) rtab[(k % LPR) * LPR + k / LPR] = a.red[k];
     }
-    if constexpr (VAR)     // rows past N repeat row N; stored transposed (RowT::tpos)
+    // rows past N repeat row N; stored transposed (RowT::tpos), and MIX a
+    // second copy in the single-realization warps' layout after it
+    Coef1D<float>* tab2 = tab + (C * LPR + 1);
+    if constexpr (VAR) {
         for (int k = threadIdx.x; k <= C * LPR; k += blockDim.x) tab[RowT::tpos(k)] = a.coef[k < a.N ? k : a.N];
+        if constexpr (MIX) {
+            using RowS = Row1D<float, C / 2, 2 * LPR, DIR, SPECIES, RAGGED, false, VAR>;
+            for (int k = threadIdx.x; k <= C * LPR; k += blockDim.x) tab2[RowS::tpos(k)] = a.coef[k < a.N ? k : a.N];
+        }
+    }
 
     const int N = a.N;
     const int Mh = (N + 127) / 128;
@@ -335,7 +344,7 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
         if constexpr (MIX) {
             if (warp >= npair)
                 nsnap = cov_step_warp<C / 2, 2 * LPR, DIR, SPECIES, RAGGED, PC, VAR, TC, IMP>(
-                    a, base, full, empty, abort_flag, wmom, tab, stab, rtab, rb, count, 2 * npair + (warp - npair),
+                    a, base, full, empty, abort_flag, wmom, tab2, stab, rtab, rb, count, 2 * npair + (warp - npair),
                     use_tc);
             else
                 nsnap = cov_step_warp<C, LPR, DIR, SPECIES, RAGGED, PC, VAR, TC, IMP>(
@@ -391,7 +400,8 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
 template <int C, int LPR, bool DIR, bool SP, bool PC, bool VAR, bool TC, bool IMP>
 static cudaError_t launch_cov_layout(const Step1DArgs<float>& a, const CovArgs& c, int grid, cudaStream_t st)
 {
-    const int smem = cov_smem_bytes<C>(LPR) + (VAR ? (C * LPR + 1) * (int)sizeof(Coef1D<float>) : 0) +
+    constexpr bool MIX = C == 16 && LPR == 16 && !IMP;       // two copies of a material table
+    const int smem = cov_smem_bytes<C>(LPR) + (VAR ? (MIX ? 2 : 1) * (C * LPR + 1) * (int)sizeof(Coef1D<float>) : 0) +
                      (IMP ? C * LPR * (int)sizeof(Solve1D<float>) + LPR * LPR * (int)sizeof(Reduced1D<float>) : 0);
     if (a.N == C * LPR) {
         auto k = k_step1d_cov<C, LPR, DIR, SP, false, PC, VAR, TC, IMP>;
