@@ -32,7 +32,7 @@ constexpr int kY3 = 8;          // x-rows (warps) per CTA
 constexpr int kH3 = 32;         // z-planes per band
 
 template <typename Real, int C, bool SPECIES, bool CORR>
-__global__ void __launch_bounds__(kY3 * 32, sizeof(Real) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(kY3 * 32, sizeof(Real) == 4 ? 2 : 1)
 k_step3d(const __grid_constant__ Step3DArgs<Real> a)
 {
     static_assert(C % 4 == 0, "cells per lane must be a multiple of 4");
@@ -80,22 +80,25 @@ k_step3d(const __grid_constant__ Step3DArgs<Real> a)
         if (SPECIES) return species_flux(lo, hi, hamp2, z);
         return (lo + hi) * z;
     };
+    // offsets inside a realization in 32 bits (3 x cells < 2^32 is checked at init)
     auto row_ptr = [&](int yy, int zz) -> const Real* {
-        return Tin + ((size_t)wrap_once(zz, nz) * ny + (size_t)yy) * nx;
+        return Tin + (((uint32_t)wrap_once(zz, nz) * (uint32_t)ny + (uint32_t)yy) * (uint32_t)nx);
     };
     auto load_row = [&](int yy, int zz, Real (&v)[C]) { vload<C>(row_ptr(yy, zz) + i0, v); };
-    // fluxes of C faces from two rows of values, noise block base g0 (multiple of 4)
+    // fluxes of C faces from two rows of values, noise block base g0 (multiple
+    // of 4); without noise the amplitude is 0 and so is every flux (the
+    // normals are still drawn: no branch per block)
     auto face_row = [&](const Real (&lo)[C], const Real (&hi)[C], uint32_t g0, Real (&g)[C]) {
 #pragma unroll
         for (int q = 0; q < C / 4; ++q) {
             Real z[4] = {Real(0), Real(0), Real(0), Real(0)};
-            if (a.stochastic) normals4(philox4x32_10(make_uint4(g0 / 4u + (uint32_t)q, n, stream, 0u), a.rk), z);
+            normals4(philox4x32_10(make_uint4(g0 / 4u + (uint32_t)q, n, stream, 0u), a.rk), z);
 #pragma unroll
             for (int t = 0; t < 4; ++t) g[4 * q + t] = flux(lo[4 * q + t], hi[4 * q + t], z[t]);
         }
     };
     auto lin = [&](int yy, int zz) -> uint32_t {
-        return (uint32_t)((((int64_t)wrap_once(zz, nz) * ny + yy) * nx) + i0);
+        return ((uint32_t)wrap_once(zz, nz) * (uint32_t)ny + (uint32_t)yy) * (uint32_t)nx + (uint32_t)i0;
     };
 
     // Shared memory: the rows of plane p (halo y0-1, the tile's rows, halo
@@ -123,13 +126,18 @@ k_step3d(const __grid_constant__ Step3DArgs<Real> a)
     // and the high halo), one Philox block (four faces) per lane each, so that
     // no warp draws more than one block beyond its own three rows of faces
     // (the plane's barrier waits for the busiest warp)
-    auto yfaces = [&](int p, const Real (&v)[C]) {
+    auto yfaces = [&](int p, const Real (&v)[C], const Real* zpre) {
         const Real* srow = srow_of(p);
         Real* sgy = sgy_of(p);
         Real lo[C], g[C];
         vload<C>(srow + (size_t)w * nx + i0, lo);
         if (row_active) {
-            face_row(lo, v, (uint32_t)ncell + lin(y, p), g);
+            if (zpre) {
+#pragma unroll
+                for (int j = 0; j < C; ++j) g[j] = flux(lo[j], v[j], zpre[j]);
+            } else {
+                face_row(lo, v, (uint32_t)ncell + lin(y, p), g);
+            }
             vstore<C>(sgy + (size_t)w * nx + i0, g);
         }
         if (w < C / 4) {
@@ -137,8 +145,9 @@ k_step3d(const __grid_constant__ Step3DArgs<Real> a)
             Real lo4[4], hi4[4], g4[4], z[4] = {Real(0), Real(0), Real(0), Real(0)};
             vload<4>(srow + (size_t)nrows * nx + xq, lo4);
             vload<4>(srow + (size_t)(nrows + 1) * nx + xq, hi4);
-            const uint32_t gq = (uint32_t)ncell + (uint32_t)(((int64_t)wrap_once(p, nz) * ny + yh) * nx + xq);
-            if (a.stochastic) normals4(philox4x32_10(make_uint4(gq / 4u, n, stream, 0u), a.rk), z);
+            const uint32_t gq = (uint32_t)ncell + ((uint32_t)wrap_once(p, nz) * (uint32_t)ny + (uint32_t)yh) * (uint32_t)nx +
+                                (uint32_t)xq;
+            normals4(philox4x32_10(make_uint4(gq / 4u, n, stream, 0u), a.rk), z);
 #pragma unroll
             for (int t = 0; t < 4; ++t) g4[t] = flux(lo4[t], hi4[t], z[t]);
             vstore<4>(sgy + (size_t)nrows * nx + xq, g4);
@@ -154,7 +163,7 @@ k_step3d(const __grid_constant__ Step3DArgs<Real> a)
         if (w == 0 || w == 1) load_row(w == 0 ? yl : yh, z0, hv);
         publish(z0, cur, hv);
         __syncthreads();
-        yfaces(z0, cur);
+        yfaces(z0, cur, nullptr);
     }
 
     for (int z = z0; z < z1; ++z) {
@@ -164,10 +173,33 @@ k_step3d(const __grid_constant__ Step3DArgs<Real> a)
         Real hv[C];
         if (more && (w == 0 || w == 1)) load_row(w == 0 ? yl : yh, z + 1, hv);
         load_row(yc, z + 1, nxt);
-        face_row(cur, nxt, (uint32_t)(2 * ncell) + lin(yc, z + 1), gz_nxt);
+        // the normals of this row's faces: the low z-faces of plane z + 1, its
+        // low y-faces of plane z + 1 and its x-faces of plane z; 3 C / 4 Philox
+        // blocks run together round by round
+        Real zz[C], zy[C], zx[C];
+        {
+            uint4 blk[3 * C / 4];
+            const uint32_t gzb = (2u * (uint32_t)ncell + lin(yc, z + 1)) / 4u;
+            const uint32_t gyb = ((uint32_t)ncell + lin(yc, z + 1)) / 4u, gxb = lin(yc, z) / 4u;
+#pragma unroll
+            for (int q = 0; q < C / 4; ++q) {
+                blk[q] = make_uint4(gzb + (uint32_t)q, n, stream, 0u);
+                blk[C / 4 + q] = make_uint4(gyb + (uint32_t)q, n, stream, 0u);
+                blk[C / 2 + q] = make_uint4(gxb + (uint32_t)q, n, stream, 0u);
+            }
+            philox4x32_10_batch<3 * C / 4>(blk, a.rk);
+#pragma unroll
+            for (int q = 0; q < C / 4; ++q) {
+                normals4(blk[q], zz + 4 * q);
+                normals4(blk[C / 4 + q], zy + 4 * q);
+                normals4(blk[C / 2 + q], zx + 4 * q);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < C; ++j) gz_nxt[j] = flux(cur[j], nxt[j], zz[j]);
         if (more) publish(z + 1, nxt, hv);
         __syncthreads();
-        if (more) yfaces(z + 1, nxt);
+        if (more) yfaces(z + 1, nxt, zy);
         const Real* srow = srow_of(z);
         const Real* sgy = sgy_of(z);
         if (row_active) {
@@ -181,7 +213,8 @@ k_step3d(const __grid_constant__ Step3DArgs<Real> a)
                 Real lo[C];
 #pragma unroll
                 for (int j = 0; j < C; ++j) lo[j] = (j == 0) ? (lane == 0 ? wrap_lo : left_nb) : cur[j - 1];
-                face_row(lo, cur, lin(y, z), gx);
+#pragma unroll
+                for (int j = 0; j < C; ++j) gx[j] = flux(lo[j], cur[j], zx[j]);
             }
             const Real g_next = __shfl_down_sync(FULL, gx[0], 1);
             const Real g_zero = __shfl_sync(FULL, gx[0], 0);
@@ -205,11 +238,11 @@ k_step3d(const __grid_constant__ Step3DArgs<Real> a)
             }
             if (CORR) {   // predictor-corrector (Sec. 3): ((T + T*) + inc(T*)) / 2
                 Real tc[C];
-                vload<C>(a.Tc + (size_t)rho * (size_t)ncell + ((size_t)z * ny + y) * nx + i0, tc);
+                vload<C>(a.Tc + (size_t)rho * (size_t)ncell + lin(y, z), tc);
 #pragma unroll
                 for (int j = 0; j < C; ++j) out[j] = half * ((tc[j] + cur[j]) + out[j]);
             }
-            Real* po = Tout + ((size_t)z * ny + y) * nx + i0;
+            Real* po = Tout + lin(y, z);
             vstore<C>(po, out);
             bool bad = false;
 #pragma unroll
@@ -217,7 +250,7 @@ k_step3d(const __grid_constant__ Step3DArgs<Real> a)
                 if (a.check) bad |= !finite_any(out[j]);
             if (bad) atomicOr(a.flags, 1);
             if (a.sample) {
-                const size_t off = (size_t)rho * (size_t)ncell + ((size_t)z * ny + y) * nx + i0;
+                const size_t off = (size_t)rho * (size_t)ncell + lin(y, z);
                 Real s1[C], s2[C];
                 vload<C>(a.m1 + off, s1);
                 vload<C>(a.m2 + off, s2);
