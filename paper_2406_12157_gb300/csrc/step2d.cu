@@ -29,14 +29,15 @@
 
 namespace she {
 
-// One warp per CTA, 24 resident per SM for the FP32 8-cell layout (80
-// registers; 28 at 72 registers spill).  A one-warp CTA frees its slot when
-// its own warp finishes, so the warps of an SM need not wait for the slowest
-// of four: 68.4 -> 66.2 us per step of the 256 x 256 x 256 ensemble with the
-// same 24 warps per SM.
+// One warp per CTA, 20 resident per SM for the FP32 8-cell layout (up to 102
+// registers; measured per step of the 256 x 256 x 256 species ensemble:
+// 56.6 us at 24 warps and 80 registers, 54.7 at 20, 55.7 at 16, 55.1 at 12;
+// 28 at 72 registers spill).  A one-warp CTA frees its slot when its own
+// warp finishes, so the warps of an SM need not wait for the slowest of
+// four: 68.4 -> 66.2 us per step with the same 24 warps per SM.
 constexpr int kWPB2 = 1;       // warps per CTA
 template <typename Real, int C, int LPR, bool SPECIES, bool RAGGED>
-__global__ void __launch_bounds__(32 * kWPB2, (sizeof(Real) == 4 && C <= 8) ? 24 / kWPB2 : 1)
+__global__ void __launch_bounds__(32 * kWPB2, (sizeof(Real) == 4 && C <= 8) ? 20 / kWPB2 : 1)
 k_step2d(const __grid_constant__ Step2DArgs<Real> a)
 {
     static_assert(C % 4 == 0, "cells per lane must be a multiple of 4");
