@@ -204,7 +204,7 @@ WORKLOADS = {
               "(two-stage DFT-as-GEMM on tcgen05) every 10 steps after 1e4"),
         chunk=1000, ops=OPS_2D_SP, bytes=8.0 + 16.0 / 10,
         kernel="k_step2d<float,8,32,species>",
-        traffic=dict(bytes=74.895872e6 + 21.625600e6, realizations=256),   # profiles/k_step2d_species_2d.md
+        traffic=dict(bytes=72.756736e6 + 21.945344e6, realizations=256),   # profiles/k_step2d_species_2d.md
         # per realization and sample: row DFT (ny x nx x nx MAC) + column DFTs
         # for the 128 rows ky < 128 (2 x 128 x ny x nx MAC; the other rows
         # follow from the real-field symmetry), 3 split products, 2 flop per MAC
@@ -245,7 +245,7 @@ WORKLOADS = {
               "stencil, moments and S(k) along x, y, z (line covariance on tcgen05) every 10 steps"),
         chunk=100, ops=OPS_3D, bytes=8.0 + 16.0 / 10,
         kernel="k_step3d<float,8,heat>",
-        traffic=dict(bytes=576.348416e6 + 499.231488e6, realizations=8),    # profiles/k_step3d_cube_3d.md
+        traffic=dict(bytes=574.792192e6 + 494.729216e6, realizations=8),    # profiles/k_step3d_cube_3d.md
         # per realization and sample: for each axis a SYRK over all lines
         # (cells / n_a lines x n_a^2 MAC), 3 split products, 2 flop per MAC
         stats_kernel="k_axes_syrk", stats_flop=lambda p: 3 * 2 * sum(
