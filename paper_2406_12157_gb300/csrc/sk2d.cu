@@ -26,8 +26,8 @@
 //
 // Both B-side operands that change per realization (the split delta and
 // the split D1) go through a per-CTA global scratch, so every operand chunk
-// reaches shared memory by bulk asynchronous copy through a ring of six
-// 32 KB stages and up to five copies are in flight while the tensor core
+// reaches shared memory by bulk asynchronous copy through a ring of five
+// 32 KB stages and up to four copies are in flight while the tensor core
 // works.  Operands are MN-major, 128-byte swizzled (the layout validated by
 // she_syrk_probe): LBO = 1 KB between 64-element atoms, SBO = 4 KB between
 // K groups of 8.
@@ -48,8 +48,11 @@ namespace {
 constexpr int kK = 16;                 // K rows per chunk: one MMA K step
 constexpr int kImg = 8192;             // one bf16 image of 256 (MN) x 16 (K)
 constexpr int kChunk = 4 * kImg;       // A hi, A lo, B hi, B lo: 32 KB
-constexpr int kStages = 6;             // shared-memory ring of chunks
+constexpr int kStages = 5;             // shared-memory ring of chunks
 constexpr int kStage = 4096;           // per-worker-warp staging of 32 rows x 32 columns, hi and lo
+constexpr int kTiles = 4;              // FP32 delta tiles (16 columns x ny <= 256 rows) in flight (TMA)
+constexpr int kTileBytes = 16384;
+constexpr int kStaging = kTiles * kTileBytes > 8 * kStage ? kTiles * kTileBytes : 8 * kStage;
 constexpr int kKC = 256 / kK;          // K chunks of a full 256-long axis
 constexpr uint32_t kLBO = 1024;
 constexpr uint32_t kSBO = 4096;        // 4 atoms (256 MN) per K group of 8
@@ -146,9 +149,11 @@ __device__ __forceinline__ bool named_and(int id, int n, bool p)
 // lets its copies and MMAs finish (bounded), frees its tensor memory, sets
 // the error flag and returns.
 // TMA: delta reaches shared memory as FP32 tiles of 16 columns x ny rows by
-// tiled tensor copies (two tiles in flight, in the workers' staging area,
-// which the split does not share with the drain), and the workers split it
-// from there; otherwise they load it from device memory themselves.
+// tiled tensor copies (four tiles in flight, in the workers' staging area,
+// which the drain uses at other times), and the workers split it from
+// there; otherwise they load it from device memory themselves.  With two
+// tiles in flight the split of one realization took 16.5 us, longer than the
+// column stage it overlaps; five ring stages instead of six make the room.
 template <bool TMA>
 __global__ void __launch_bounds__(288, 1)
 k_sk2d(const __grid_constant__ Sk2dArgs a)
@@ -156,8 +161,8 @@ k_sk2d(const __grid_constant__ Sk2dArgs a)
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* bufs = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* stage = bufs + kStages * kChunk;                          // [8 workers][kStage]
-    uint64_t* full = reinterpret_cast<uint64_t*>(stage + 8 * kStage);         // [kStages] chunk landed
+    unsigned char* stage = bufs + kStages * kChunk;     // [8 workers][kStage] or [kTiles][kTileBytes]
+    uint64_t* full = reinterpret_cast<uint64_t*>(stage + kStaging);           // [kStages] chunk landed
     uint64_t* empty = full + kStages;                                          // [kStages] MMAs done reading
     uint64_t* x_ready = empty + kStages;
     uint64_t* y_ready = x_ready + 1;
@@ -165,8 +170,8 @@ k_sk2d(const __grid_constant__ Sk2dArgs a)
     uint64_t* row_done = tmem_free + 1;
     uint64_t* col_done = row_done + 1;
     uint64_t* fin = col_done + 1;
-    uint64_t* fpf = fin + 1;                         // [2] FP32 delta tile landed (TMA)
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(fpf + 2);
+    uint64_t* fpf = fin + 1;                         // [kTiles] FP32 delta tile landed (TMA)
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(fpf + kTiles);
     volatile int* s_abort = reinterpret_cast<volatile int*>(tslot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nx = a.nx, ny = a.ny;
@@ -185,7 +190,7 @@ k_sk2d(const __grid_constant__ Sk2dArgs a)
             mbar_init(&full[b], 1);
             mbar_init(&empty[b], 1);
         }
-        for (uint64_t* b = x_ready; b <= fin + 2; ++b) mbar_init(b, 1);     // ... fin, fpf[2]
+        for (uint64_t* b = x_ready; b <= fin + kTiles; ++b) mbar_init(b, 1);     // ... fin, fpf[kTiles]
         *s_abort = 0;
         fence_mbar_init();
     }
@@ -326,7 +331,7 @@ k_sk2d(const __grid_constant__ Sk2dArgs a)
             return true;
         };
         // TMA path: chunk c of the split (x in [16 c, 16 c + 16)) arrives as an
-        // FP32 tile [ny][16] in half g & 1 of the staging area (g: the CTA's
+        // FP32 tile [ny][16] in slot g % kTiles of the staging area (g: the CTA's
         // running tile count, the same in every worker).  A warp takes blocks
         // of 16 rows: lane (x, p) = (lane % 16, lane / 16) reads rows 2 r + p of
         // the block (two rows are 32 consecutive words: no bank conflicts),
@@ -336,27 +341,26 @@ k_sk2d(const __grid_constant__ Sk2dArgs a)
         uint32_t tile_g = 0, tile_issued = 0;
         auto issue_tile = [&](int rho, int c) {        // thread wt == 0
             const uint32_t g = tile_issued++;
-            uint64_t* bar = &fpf[g & 1];
+            uint64_t* bar = &fpf[g % kTiles];
             mbar_arrive_expect_tx(bar, (uint32_t)ny * 16u * 4u);
-            tma_load_2d(stage + (size_t)(g & 1) * 16384, &a.map, 16 * c, rho * ny, bar);
+            tma_load_2d(stage + (size_t)(g % kTiles) * kTileBytes, &a.map, 16 * c, rho * ny, bar);
         };
         auto split_tma = [&](int rho) -> bool {
             // the staging area was last used by the drain (generic proxy)
             fence_proxy_async_smem();
             named_sync(kWorkBar, kWorkers);
             if (wt == 0) {
-                issue_tile(rho, 0);
-                if (n1 > 1) issue_tile(rho, 1);
+                for (int c = 0; c < kTiles && c < n1; ++c) issue_tile(rho, c);
             }
             const int x = lane & 15, p = lane >> 4;
             const int nb = (ny + 15) / 16;
             for (int c = 0; c < n1; ++c) {
                 const uint32_t g = tile_g + (uint32_t)c;
-                if (!wait_all(&fpf[g & 1], (g >> 1) & 1u)) {
+                if (!wait_all(&fpf[g % kTiles], (g / kTiles) & 1u)) {
                     tile_g = g;                     // tiles from g on may still be in flight
                     return false;
                 }
-                const float* st = reinterpret_cast<const float*>(stage + (size_t)(g & 1) * 16384);
+                const float* st = reinterpret_cast<const float*>(stage + (size_t)(g % kTiles) * kTileBytes);
                 const bool xin = 16 * c + x < nx;
                 unsigned char* dh = xs + (size_t)c * 2 * kImg;
                 for (int blk = warp - 1; blk < nb; blk += kWorkers / 32) {
@@ -383,10 +387,10 @@ k_sk2d(const __grid_constant__ Sk2dArgs a)
                     *reinterpret_cast<uint4*>(dh + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
                     *reinterpret_cast<uint4*>(dh + kImg + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
                 }
-                // every worker has read this half: the copy of chunk c + 2 may take it
+                // every worker has read this tile: the copy of chunk c + kTiles may take it
                 fence_proxy_async_smem();
                 named_sync(kWorkBar, kWorkers);
-                if (wt == 0 && c + 2 < n1) issue_tile(rho, c + 2);
+                if (wt == 0 && c + kTiles < n1) issue_tile(rho, c + kTiles);
             }
             tile_g += (uint32_t)n1;
             return true;
@@ -498,7 +502,8 @@ k_sk2d(const __grid_constant__ Sk2dArgs a)
         if constexpr (TMA) {
             // after an abort, let the tensor copies still in flight land
             if (wt == 0)
-                for (uint32_t g = tile_g; g < tile_issued; ++g) mbar_wait_bounded(&fpf[g & 1], (g >> 1) & 1u, kTries2);
+                for (uint32_t g = tile_g; g < tile_issued; ++g)
+                    mbar_wait_bounded(&fpf[g % kTiles], (g / kTiles) & 1u, kTries2);
         }
     }
     fence_before_sync();
@@ -545,7 +550,7 @@ cudaError_t launch_sk2d(Handle& h)
     a.ny = h.prob.n[1];
     a.R = (int)h.R;
     a.ref = (float)h.prob.wall_lo;
-    const int smem = 1024 + kStages * kChunk + 8 * kStage + 256;
+    const int smem = 1024 + kStages * kChunk + kStaging + 256;
     // the TMA path: the [R ny][nx] state (rows of a multiple of 4 cells) in
     // boxes of 16 columns x ny rows
     const uint64_t dims[2] = {(uint64_t)a.nx, (uint64_t)a.R * (uint64_t)a.ny}, strides[1] = {(uint64_t)a.nx * 4};
