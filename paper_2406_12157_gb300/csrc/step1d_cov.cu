@@ -416,26 +416,6 @@ static cudaError_t launch_cov_layout(const Step1DArgs<float>& a, const CovArgs& 
 }
 
 
-// Lanes per realization of the layout chosen for N: 4-cell layouts up to 128
-// cells, above 16 cells x 16 lanes (15 stepping warps per CTA, two
-// realizations each).  Measured per 2560-step launch at 256 x 4096: 3.99 ms,
-// against 4.14 ms for 32 cells x 8 lanes (7 stepping warps leave one SMSP
-// with a single warp) and 4.10 ms for 8 cells x 32 lanes (31 stepping warps
-// at 64 registers); the predictor-corrector step needs the registers of the
-// 16 x 16 layout anyway.
-static int cov_lpr(int N, bool pc)
-{
-    (void)pc;
-    return N <= 16 ? 4 : N <= 32 ? 8 : N <= 64 ? 16 : N <= 128 ? 32 : 16;
-}
-
-// realization slots per CTA of that layout: (warps - 1) x (32 / LPR)
-static int cov_slots_per_cta(int N, bool pc)
-{
-    const int lpr = cov_lpr(N, pc);
-    return (lpr - 1) * (32 / lpr);
-}
-
 template <bool DIR, bool SP, bool PC, bool VAR, bool TC, bool IMP>
 static cudaError_t launch_cov_ds(const Step1DArgs<float>& a, const CovArgs& c, int grid, cudaStream_t st)
 {
@@ -511,6 +491,27 @@ cudaError_t launch_cov_implicit_time_corr(const Step1DArgs<float>& a, const CovA
 #endif
 
 #if SHE_COV_PART(0, 0)
+// Lanes per realization of the layout chosen for N (launch_cov_ds): 4-cell
+// layouts up to 128 cells, above 16 cells x 16 lanes (15 stepping warps per
+// CTA, up to two realizations each).  Measured per 2560-step launch at 256 x 4096: 3.99 ms,
+// against 4.14 ms for 32 cells x 8 lanes (7 stepping warps leave one SMSP
+// with a single warp) and 4.10 ms for 8 cells x 32 lanes (31 stepping warps
+// at 64 registers); the predictor-corrector step needs the registers of the
+// 16 x 16 layout anyway.
+static int cov_lpr(int N, bool pc)
+{
+    (void)pc;
+    return N <= 16 ? 4 : N <= 32 ? 8 : N <= 64 ? 16 : N <= 128 ? 32 : 16;
+}
+
+// realization slots per CTA of that layout: (warps - 1) x (32 / LPR); at
+// 16 x 16 a CTA with fewer realizations spreads them over more warps
+static int cov_slots_per_cta(int N, bool pc)
+{
+    const int lpr = cov_lpr(N, pc);
+    return (lpr - 1) * (32 / lpr);
+}
+
 // The layout code (cells per lane x 100 + lanes per realization) of the
 // covariance kernel for rows of N cells: the implicit schemes set up their
 // factor tables for it.
