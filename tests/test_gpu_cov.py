@@ -71,6 +71,34 @@ def test_full_size_covariance_matches_oracle():
     assert np.max(np.abs(g["cov"] - o["cov"])) < 2e-4 * scale
 
 
+@pytest.mark.parametrize("N,R,kw", [(200, 4600, {}), (256, 3000, {"scheme": "pc"}), (256, 4096, {"var": True}),
+                                   (160, 2300, {"tc_lags": 3}), (256, 1200, {"species": True})])
+def test_covariance_warp_mix_matches_oracle(N, R, kw):
+    """Above 128 cells (16 x 16) a CTA's realizations go to warps of two and
+    warps of one (count - 15 warps of two, the others of one on 32 lanes of
+    8 cells): R = 4600 fills a first wave with 30 per CTA (all warps of two)
+    and leaves 40 for a second, 3000 gives 19-20 per CTA, 4096 26-27 (with
+    the material table's second layout), 2300 15-16 (with the time
+    correlation), 1200 7-8 (species, all warps of one)."""
+    kw = dict(kw)
+    var, species = kw.pop("var", False), kw.pop("species", False)
+    base = dict(n=(N, 1, 1), realizations=R, relax_steps=0, stats_interval=10, want_cov=1, want_sk=0, **kw)
+    if species:
+        base.update(equation="species", wall_lo=1.0, wall_hi=1.5, n0=300.0)
+    p = W.two_material_rod(cells=N, **base) if var else W.gradient_rod(**base)
+    steps = 40
+    with S.Simulation(p) as sim:
+        sim.step(steps)
+        g = sim.stats(cov=True, time_corr=bool(kw.get("tc_lags")))
+    o = O.finalize(p, O.run(p, R, steps, want_cov=1))
+    assert g["n_samples"] == o["n"]
+    scale = np.max(np.diag(o["cov"]))
+    assert np.max(np.abs(g["cov"] - o["cov"])) < 2e-4 * scale
+    assert np.max(np.abs(g["mean"] - o["mean"])) < 1e-5 * np.max(np.abs(o["mean"]))
+    if kw.get("tc_lags"):
+        assert np.max(np.abs(g["time_corr"] - o["time_corr"])) < 1e-3 * np.max(np.abs(o["time_corr"]))
+
+
 def test_bounded_wait_times_out_and_context_survives():
     # a wait on a barrier nothing completes gives up and reports it
     assert S.lib().she_wait_probe(64) == S._abi.SHE_ERR_TIMEOUT
