@@ -638,12 +638,16 @@ she_status finalize_stats(const FinInfo& fi, const she_raw& raw, she_stats_out* 
         if (sk1d) {
             // S_k = <|hat T_k|^2> (Eq. (3.11)) from the pooled moments:
             // <|hat delta_k|^2> = sum_{j,l} M2_jl cos(2 pi (j - l) k / N)
+            //                   = sum_d D_d cos(2 pi d k / N), D_d the sum of
+            // M2 over the wrapped diagonal j - l = d (mod N): O(N^2)
             const double two_pi = 6.283185307179586476925286766559;
-            std::vector<double> cs((size_t)N), sn((size_t)N);
+            std::vector<double> cs((size_t)N), sn((size_t)N), D((size_t)N, 0.0);
             for (int64_t tt = 0; tt < N; ++tt) {
                 cs[(size_t)tt] = std::cos(two_pi * (double)tt / (double)N);
                 sn[(size_t)tt] = std::sin(two_pi * (double)tt / (double)N);
             }
+            for (int64_t j = 0; j < N; ++j)
+                for (int64_t l = 0; l < N; ++l) D[(size_t)((j - l + N) % N)] += M2[(size_t)(j * N + l)];
             for (int64_t k = 0; k < N; ++k) {
                 double dd = 0.0, mr = 0.0, mi = 0.0, rr = 0.0, ri = 0.0;
                 for (int64_t j = 0; j < N; ++j) {
@@ -652,10 +656,7 @@ she_status finalize_stats(const FinInfo& fi, const she_raw& raw, she_stats_out* 
                     mi -= mu[(size_t)j] * sn[ph];
                     rr += ref[(size_t)j] * cs[ph];
                     ri -= ref[(size_t)j] * sn[ph];
-                    for (int64_t l = 0; l < N; ++l) {
-                        const size_t d = (size_t)((((j - l) * k) % N + N) % N);
-                        dd += M2[(size_t)(j * N + l)] * cs[d];
-                    }
+                    dd += D[(size_t)j] * cs[ph];
                 }
                 if (out->sk_fluct) out->sk_fluct[k] = dd - (mr * mr + mi * mi);
                 if (out->sk) out->sk[k] = rr * rr + ri * ri + 2.0 * (rr * mr + ri * mi) + dd;
@@ -804,8 +805,12 @@ she_status she_init(const she_params* p, she_handle** out)
         st = SHE_ERR_UNSUPPORTED;
         msg = "she: the time correlation runs on the fused 1D kernels (kernel auto)";
     }
-    if (st == SHE_OK && need_cov && (p->dim != 1 || p->n[0] > 256)) {
-        st = SHE_ERR_INVALID_ARG; msg = "she: the covariance needs a 1D grid of at most 256 cells";
+    if (st == SHE_OK && need_cov && (p->dim != 1 || p->n[0] > 2048)) {
+        st = SHE_ERR_INVALID_ARG; msg = "she: the covariance needs a 1D grid of at most 2048 cells";
+    }
+    if (st == SHE_OK && need_cov && p->precision == SHE_FP32 && p->n[0] > 256) {
+        st = SHE_ERR_UNSUPPORTED;
+        msg = "she: the FP32 covariance (tensor cores) takes rows of at most 256 cells; FP64 up to 2048";
     }
     if (st == SHE_OK && need_cov && p->precision == SHE_FP32 && p->kernel != SHE_KERNEL_AUTO) {
         st = SHE_ERR_UNSUPPORTED; msg = "she: the FP32 covariance runs on the fused tensor-core path";

@@ -99,6 +99,18 @@ def test_covariance_warp_mix_matches_oracle(N, R, kw):
         assert np.max(np.abs(g["time_corr"] - o["time_corr"])) < 1e-3 * np.max(np.abs(o["time_corr"]))
 
 
+@pytest.mark.parametrize("N,precision,status", [(300, "fp32", "SHE_ERR_UNSUPPORTED"),
+                                               (2049, "fp64", "SHE_ERR_INVALID_ARG")])
+def test_covariance_row_limits(N, precision, status):
+    # FP32: the tensor-core accumulator holds rows of at most 256 cells; FP64
+    # (CUDA cores) up to 2048
+    p = W.gradient_rod(n=(N, 1, 1), realizations=4, precision=precision, want_cov=1, want_sk=0,
+                       kernel="plain" if N > 1024 else "auto")
+    with pytest.raises(S.SheError) as e:
+        S.Simulation(p)
+    assert e.value.status == getattr(S._abi, status)
+
+
 def test_bounded_wait_times_out_and_context_survives():
     # a wait on a barrier nothing completes gives up and reports it
     assert S.lib().she_wait_probe(64) == S._abi.SHE_ERR_TIMEOUT
@@ -108,7 +120,8 @@ def test_bounded_wait_times_out_and_context_survives():
 
 
 @pytest.mark.parametrize("N,R,steps,bc,kernel", [(16, 40, 203, "dirichlet", "auto"), (130, 70, 157, "dirichlet", "auto"),
-                                                 (256, 33, 90, "periodic", "auto"), (48, 20, 95, "dirichlet", "plain")])
+                                                 (256, 33, 90, "periodic", "auto"), (48, 20, 95, "dirichlet", "plain"),
+                                                 (600, 12, 41, "dirichlet", "auto"), (1100, 5, 30, "periodic", "plain")])
 def test_fp64_covariance_matches_oracle_exactly(N, R, steps, bc, kernel):
     # FP64 state and FP64 covariance (CUDA cores): the same sample paths as
     # the oracle, so the pooled covariance and S(k) agree to rounding order
