@@ -132,8 +132,10 @@ typedef struct she_params {
     int32_t precision;    /* SHE_FP32 or SHE_FP64 */
     int32_t stats_interval; /* K: sample every K steps (>= 1) */
     int32_t want_cov;     /* 1: accumulate the full equal-time covariance
-                             (1D; FP32 N <= 256 on the tensor cores, FP64
-                             N <= 2048 on the CUDA cores) */
+                             (1D, N <= 2048: FP32 rows of at most 256 cells
+                             on the tensor cores, fused into the step; longer
+                             FP32 rows (fused kernels, N <= 1024) and FP64 by
+                             an FP64 SYRK on the CUDA cores at every sample) */
     int64_t relax_steps;  /* sample after step m (1-based) iff m % K == 0 and m > relax */
     int32_t want_sk;      /* SHE_SK_FULL (1D, 2D) and/or SHE_SK_AXES (any dim) */
     int32_t kernel;       /* SHE_KERNEL_AUTO or SHE_KERNEL_PLAIN */
@@ -269,8 +271,8 @@ typedef struct she_raw {
  * range, non-positive dx/dt/coefficients, periodic grid with
  * wall_lo != wall_hi -- the paper's program rejects that combination too --,
  * Dirichlet on dim > 1, want_cov with N > 2048 or dim > 1, SHE_SK_FULL on
- * dim 3), SHE_ERR_UNSUPPORTED (among others: the FP32 covariance with
- * N > 256), SHE_ERR_UNSTABLE (r > 1/(2 dim)), SHE_ERR_OOM, SHE_ERR_CUDA.
+ * dim 3), SHE_ERR_UNSUPPORTED (among others: the FP32 covariance on the
+ * plain form), SHE_ERR_UNSTABLE (r > 1/(2 dim)), SHE_ERR_OOM, SHE_ERR_CUDA.
  * On error *out is NULL.
  */
 she_status she_init(const she_params* p, she_handle** out);

@@ -808,12 +808,8 @@ she_status she_init(const she_params* p, she_handle** out)
     if (st == SHE_OK && need_cov && (p->dim != 1 || p->n[0] > 2048)) {
         st = SHE_ERR_INVALID_ARG; msg = "she: the covariance needs a 1D grid of at most 2048 cells";
     }
-    if (st == SHE_OK && need_cov && p->precision == SHE_FP32 && p->n[0] > 256) {
-        st = SHE_ERR_UNSUPPORTED;
-        msg = "she: the FP32 covariance (tensor cores) takes rows of at most 256 cells; FP64 up to 2048";
-    }
     if (st == SHE_OK && need_cov && p->precision == SHE_FP32 && p->kernel != SHE_KERNEL_AUTO) {
-        st = SHE_ERR_UNSUPPORTED; msg = "she: the FP32 covariance runs on the fused tensor-core path";
+        st = SHE_ERR_UNSUPPORTED; msg = "she: the FP32 covariance runs on the fused kernels (kernel auto)";
     }
     if (st == SHE_OK && (p->want_sk & SHE_SK_AXES) && p->dim == 1) {
         st = SHE_ERR_INVALID_ARG; msg = "she: SHE_SK_AXES is for 2D/3D grids (use SHE_SK_FULL in 1D)";
@@ -937,8 +933,8 @@ she_status she_init(const she_params* p, she_handle** out)
         int dev = 0, sms = 0;
         e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        // FP32: one partial per CTA of the fused kernel; FP64: one partial
-        h->cov_ctas = h->precision == SHE_FP64 ? 1 : (sms > 0 ? sms : 1);
+        // the tensor-core kernel: one partial per CTA; the CUDA-core SYRK: one
+        h->cov_ctas = she::cov_on_tensor_cores(*h) ? (sms > 0 ? sms : 1) : 1;
         const size_t nn = cells * cells;
         if (e == cudaSuccess) e = cudaMalloc(&h->d_cov_partial, (size_t)h->cov_ctas * nn * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc(&h->d_cov_red, nn * sizeof(double));
@@ -978,7 +974,7 @@ she_status she_init(const she_params* p, she_handle** out)
         if (e == cudaSuccess) e = cudaMemcpy(h->d_sigma, sc.data(), sc.size() * sizeof(double), cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess && (h->prob.scheme == SHE_BE || h->prob.scheme == SHE_CN))   // the factor tables of the
-        e = she::setup_implicit(*h, h->want_cov && h->precision == SHE_FP32 ? she::cov_layout(h->prob.n[0]) : 0);  // kernel's layout
+        e = she::setup_implicit(*h, she::cov_on_tensor_cores(*h) ? she::cov_layout(h->prob.n[0]) : 0);  // kernel's layout
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_acc1, 0, nstate * sizeof(double), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_acc2, 0, nstate * sizeof(double), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flags, 0, sizeof(int), h->stream);
@@ -1106,7 +1102,7 @@ she_status she_step_n(she_handle* hh, uint64_t n)
     uint64_t left = n;
     // FP64 with the covariance: every launch ends at a sampling step, after
     // which the FP64 covariance kernel reads the state
-    const bool cov64 = h->want_cov && h->precision == SHE_FP64 && !h->is_batch;
+    const bool cov64 = h->want_cov && !h->is_batch && !she::cov_on_tensor_cores(*h);   // the CUDA-core SYRK
     while (left > 0) {
         int chunk = (int)std::min<uint64_t>(left, (uint64_t)spl);
         bool ends_on_sample = false;

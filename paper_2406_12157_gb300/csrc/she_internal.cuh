@@ -316,6 +316,14 @@ struct Handle {
     std::string err;
 };
 
+// Whether the handle's covariance is accumulated by the fused tensor-core
+// kernel (FP32 state, rows of at most 256 cells); otherwise (FP64, or FP32
+// rows of 257..1024 cells) an FP64 CUDA-core SYRK runs at every sampling step.
+inline bool cov_on_tensor_cores(const Handle& h)
+{
+    return h.want_cov && h.precision == SHE_FP32 && h.prob.n[0] <= 256 && !h.is_batch;
+}
+
 // Timeline helpers of she_profile.  prof_mark(h, kind) precedes every launch
 // of the given kind (SHE_PROF_STEP / SHE_PROF_STATS); an event is recorded
 // only when the kind differs from the open interval's.  prof_close ends the

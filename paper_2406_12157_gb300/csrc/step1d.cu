@@ -282,7 +282,7 @@ static int choose_layout(const Handle& h)
 int fused_layout(const Handle& h)
 {
     if (h.prob.dim != 1 || h.is_batch || h.kernel != SHE_KERNEL_AUTO) return 0;
-    if (h.want_cov && h.precision == SHE_FP32) return 0;     // the covariance kernel's own layout
+    if (cov_on_tensor_cores(h)) return 0;     // the covariance kernel's own layout
     return choose_layout(h);
 }
 
@@ -577,7 +577,8 @@ cudaError_t launch_step1d_plain(Handle& h, uint32_t step0, int nsteps)
 // slices of delta in shared memory.  C is stored column-major like the FP32
 // tensor-core partials ([j][i]; symmetric), one partial.
 
-__global__ void __launch_bounds__(256) k_cov_fp64(const double* __restrict__ T, int R, int N, double wlo,
+template <typename Real>
+__global__ void __launch_bounds__(256) k_cov_fp64(const Real* __restrict__ T, int R, int N, double wlo,
                                                   double dref, int dir, const double* __restrict__ ref,
                                                   double* __restrict__ C)
 {
@@ -591,8 +592,8 @@ __global__ void __launch_bounds__(256) k_cov_fp64(const double* __restrict__ T, 
     double acc = 0.0;
     for (int r0 = 0; r0 < R; r0 += 16) {
         const int r = r0 + ty;
-        si[ty][tx] = (r < R && li < N) ? T[(size_t)r * N + li] - refi : 0.0;
-        sj[ty][tx] = (r < R && lj < N) ? T[(size_t)r * N + lj] - refj : 0.0;
+        si[ty][tx] = (r < R && li < N) ? (double)T[(size_t)r * N + li] - refi : 0.0;
+        sj[ty][tx] = (r < R && lj < N) ? (double)T[(size_t)r * N + lj] - refj : 0.0;
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < 16; ++k) acc = fma(si[k][ty], sj[k][tx], acc);
@@ -607,8 +608,12 @@ cudaError_t launch_cov_fp64(Handle& h)
     const bool dir = h.prob.bc == SHE_DIRICHLET;
     const double dref = dir ? (h.prob.wall_hi - h.prob.wall_lo) / (double)N : 0.0;
     const dim3 grid((unsigned)((N + 15) / 16), (unsigned)((N + 15) / 16)), block(16, 16);
-    k_cov_fp64<<<grid, block, 0, h.stream>>>((const double*)h.d_state, (int)h.R, N, h.prob.wall_lo, dref,
-                                             dir ? 1 : 0, h.var ? h.d_ref : nullptr, h.d_cov_partial);
+    if (h.precision == SHE_FP64)
+        k_cov_fp64<double><<<grid, block, 0, h.stream>>>((const double*)h.d_state, (int)h.R, N, h.prob.wall_lo, dref,
+                                                         dir ? 1 : 0, h.var ? h.d_ref : nullptr, h.d_cov_partial);
+    else   // FP32 rows above the tensor-core kernel's 256 cells: the deltas in FP64 from the FP32 state
+        k_cov_fp64<float><<<grid, block, 0, h.stream>>>((const float*)h.d_state, (int)h.R, N, h.prob.wall_lo, dref,
+                                                        dir ? 1 : 0, h.var ? h.d_ref : nullptr, h.d_cov_partial);
     h.launches += 1;
     return cudaGetLastError();
 }

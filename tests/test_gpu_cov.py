@@ -57,6 +57,18 @@ def test_fused_covariance_matches_oracle(N, R, steps):
     assert np.allclose(g["sk"], o["sk"], rtol=1e-6, atol=2e-4 * np.max(o["sk_fluct"]))
 
 
+@pytest.mark.parametrize("N,R,steps", [(300, 64, 120), (700, 24, 80)])
+def test_fp32_long_rows_covariance_on_cuda_cores(N, R, steps):
+    # FP32 rows above the tensor-core kernel's 256 cells: the fused row
+    # kernel steps them and an FP64 SYRK on the CUDA cores takes each sample
+    p, g, o = _cov_case(N, R, steps)
+    assert g["n_samples"] == o["n"]
+    scale = np.max(np.diag(o["cov"]))
+    assert np.max(np.abs(g["cov"] - o["cov"])) < 2e-4 * scale
+    assert np.max(np.abs(np.diag(g["cov"]) - g["var"])) < 1e-5 * scale
+    assert np.max(np.abs(g["sk_fluct"] - o["sk_fluct"])) < 2e-4 * np.max(o["sk_fluct"])
+
+
 def test_fused_covariance_periodic():
     p, g, o = _cov_case(64, 300, 200, walls=(1.0, 1.0), bc="periodic")
     scale = np.max(np.diag(o["cov"]))
@@ -102,10 +114,9 @@ def test_covariance_warp_mix_matches_oracle(N, R, kw):
 @pytest.mark.parametrize("N,precision,status", [(300, "fp32", "SHE_ERR_UNSUPPORTED"),
                                                (2049, "fp64", "SHE_ERR_INVALID_ARG")])
 def test_covariance_row_limits(N, precision, status):
-    # FP32: the tensor-core accumulator holds rows of at most 256 cells; FP64
-    # (CUDA cores) up to 2048
-    p = W.gradient_rod(n=(N, 1, 1), realizations=4, precision=precision, want_cov=1, want_sk=0,
-                       kernel="plain" if N > 1024 else "auto")
+    # the FP32 covariance runs on the fused kernels only; rows of at most
+    # 2048 cells (the plain form)
+    p = W.gradient_rod(n=(N, 1, 1), realizations=4, precision=precision, want_cov=1, want_sk=0, kernel="plain")
     with pytest.raises(S.SheError) as e:
         S.Simulation(p)
     assert e.value.status == getattr(S._abi, status)
