@@ -257,7 +257,7 @@ WORKLOADS = {
               "r = 0.2 each, per-instance seeds, FP32, moments every 10 steps after 1e4, one CUDA-graph "
               "launch per step batch"),
         chunk=2560, ops=OPS_1D, bytes=None, kernel="k_step1d_batch<*>",
-        traffic=dict(bytes=83.822336e6 + 42.458624e6, realizations=1)),    # profiles/k_step1d_batch_batched_rods.md
+        traffic=dict(bytes=84.418304e6 + 44.954112e6, realizations=1)),    # profiles/k_step1d_batch_batched_rods.md
     "two_material_rod": dict(
         leg_chunk=10000, leg_steps=10,
         make=lambda W: W.two_material_rod(),

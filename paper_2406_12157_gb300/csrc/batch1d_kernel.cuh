@@ -31,9 +31,12 @@ namespace she {
 // lane's Philox blocks per step are its independent dependency chains.
 #define SHE_BATCH_CLASSES(X)                                                                 \
     X(0, 16, 4, 4) X(1, 32, 8, 4) X(2, 64, 16, 4) X(3, 128, 16, 8) X(4, 160, 20, 8)         \
-    X(5, 192, 24, 8) X(6, 224, 28, 8) X(7, 256, 32, 8) X(8, 384, 12, 32) X(9, 512, 16, 32)  \
-    X(10, 640, 20, 32) X(11, 768, 24, 32) X(12, 896, 28, 32) X(13, 1024, 32, 32)             \
-    X(14, 1280, 40, 32) X(15, 1536, 48, 32) X(16, 1792, 56, 32) X(17, 2048, 64, 32)
+    X(5, 192, 24, 8) X(6, 224, 28, 8) X(7, 256, 32, 8) X(8, 320, 20, 16) X(9, 384, 12, 32)  \
+    X(10, 448, 28, 16) X(11, 512, 16, 32) X(12, 576, 36, 16) X(13, 640, 20, 32)              \
+    X(14, 704, 44, 16) X(15, 768, 24, 32) X(16, 832, 52, 16) X(17, 896, 28, 32)              \
+    X(18, 960, 60, 16) X(19, 1024, 32, 32) X(20, 1152, 36, 32) X(21, 1280, 40, 32)           \
+    X(22, 1408, 44, 32) X(23, 1536, 48, 32) X(24, 1664, 52, 32) X(25, 1792, 56, 32)          \
+    X(26, 1920, 60, 32) X(27, 2048, 64, 32)
 
 template <int C, int LPR, bool DIR, bool SPECIES>
 __device__ __forceinline__ void batch_unit(const BatchArgs& a, int first, int count, float* smw, int lane,

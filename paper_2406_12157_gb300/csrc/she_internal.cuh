@@ -215,7 +215,7 @@ struct BatchArgs {
     int stochastic;
 };
 
-constexpr int kNumBatchClasses = 18;
+constexpr int kNumBatchClasses = 28;
 constexpr int kBatchMaxC = 64;        // cells per lane of the largest class
 constexpr int kBatchWarps = 8;        // warps per block of the batch kernel (one block per SM)
 

@@ -30,7 +30,8 @@ def _batch(ns, steps=300, relax=40, K=4):
 
 
 # one or more instances of every layout class, full and ragged rows
-NS = [2, 5, 16, 17, 32, 33, 64, 100, 128, 129, 255, 256, 300, 512, 513, 1000, 1024, 1500, 2048]
+NS = [2, 5, 16, 17, 32, 33, 64, 100, 128, 129, 170, 200, 255, 256, 300, 350, 420, 512, 513, 600, 700, 740, 800,
+      880, 950, 1000, 1024, 1100, 1250, 1400, 1500, 1650, 1700, 1900, 2048]
 
 
 def test_batch_matches_oracle_per_instance():
