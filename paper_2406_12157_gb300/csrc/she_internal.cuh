@@ -49,11 +49,13 @@ struct __align__(4 * sizeof(Real)) Coef1D {
 // Crank-Nicolson), one entry per padded row: the forward multiplier m, the
 // reciprocal pivot ip and the super-diagonal sup of the row's block LU, the
 // block's responses v (to the value left of the block) and w (to the value
-// right of it), and z, the Sherman-Morrison vector of a periodic rod.
+// right of it), and z, the Sherman-Morrison vector of a periodic rod.  The
+// pairs read together (ip, sup in the back substitution; v, w in the
+// correction) sit on 8-byte boundaries: one load each.
 template <typename Real>
 struct __align__(4 * sizeof(Real)) Solve1D {
-    Real m, ip, sup, v;
-    Real w, z, pad0, pad1;
+    Real m, z, ip, sup;
+    Real v, w, pad0, pad1;
 };
 
 // Row of the inverse of the implicit solve's reduced (lane-interface) system:

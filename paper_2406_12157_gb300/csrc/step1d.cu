@@ -86,8 +86,8 @@ static cudaError_t upload_theta_tables(Handle& h, int C, int LPR, const std::vec
     const int Np = C * LPR, P2 = 2 * LPR;
     std::vector<Solve1D<Real>> s((size_t)Np);
     for (int i = 0; i < Np; ++i)
-        s[(size_t)i] = {(Real)m[(size_t)i], (Real)ip[(size_t)i], (Real)sup[(size_t)i], (Real)v[(size_t)i],
-                        (Real)w[(size_t)i], (Real)z[(size_t)i], Real(0), Real(0)};
+        s[(size_t)i] = {(Real)m[(size_t)i], (Real)z[(size_t)i], (Real)ip[(size_t)i], (Real)sup[(size_t)i],
+                        (Real)v[(size_t)i], (Real)w[(size_t)i], Real(0), Real(0)};
     std::vector<Reduced1D<Real>> red((size_t)LPR * LPR);
     for (int k = 0; k < LPR; ++k)
         for (int q = 0; q < LPR; ++q) {
