@@ -731,8 +731,8 @@ struct Row1D {
     // matrix is its tridiagonal part plus a rank-one term, removed by the
     // Sherman-Morrison formula.  Rows past N are identity rows (rhs 0).
     template <bool PERIODIC_SM>
-    __device__ __forceinline__ void step_theta(Real (&T)[C], uint32_t n, const Solve1D<Real>* sc,
-                                               const Reduced1D<Real>* red, Real omt, Real th2r_lo, Real th2r_hi,
+    __device__ __forceinline__ void step_theta(Real (&T)[C], uint32_t n, const SolveLU<Real>* sc,
+                                               const SolveResp<Real>* sresp, const Reduced1D<Real>* red, Real omt, Real th2r_lo, Real th2r_hi,
                                                Real cg, Real inv_den)
     {
         Real z[C];
@@ -747,7 +747,8 @@ struct Row1D {
             if (DIR && i0 + j == N - 1) x[j] += th2r_hi;
             if (RAGGED && i0 + j >= N) x[j] = Real(0);
         }
-        const Solve1D<Real>* s = sc + i0 / C;          // row j of this block at s[j * LPR]
+        const SolveLU<Real>* s = sc + i0 / C;          // row j of this block at s[j * LPR]
+        const SolveResp<Real>* sv = sresp + i0 / C;
         // block LU: forward elimination, back substitution
 #pragma unroll
         for (int j = 1; j < C; ++j) x[j] -= s[j * LPR].m * x[j - 1];
@@ -767,7 +768,7 @@ struct Row1D {
             xr = fma(q.rf, yf, fma(q.rl, yl, xr));
         }
 #pragma unroll
-        for (int j = 0; j < C; ++j) x[j] -= xl * s[j * LPR].v + xr * s[j * LPR].w;
+        for (int j = 0; j < C; ++j) x[j] -= xl * sv[j * LPR].v + xr * sv[j * LPR].w;
         if constexpr (PERIODIC_SM) {
             Real mine = x[C - 1];
             if (RAGGED) {

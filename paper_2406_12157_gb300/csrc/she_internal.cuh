@@ -58,6 +58,18 @@ struct __align__(4 * sizeof(Real)) Solve1D {
     Real v, w, pad0, pad1;
 };
 
+// The same table as the kernels hold it in shared memory, in two arrays:
+// 16-byte (FP32) rows {m, z, ip, sup} and 8-byte rows {v, w}, so that the
+// lanes of a segment read consecutive rows without bank conflicts.
+template <typename Real>
+struct __align__(4 * sizeof(Real)) SolveLU {
+    Real m, z, ip, sup;
+};
+template <typename Real>
+struct __align__(2 * sizeof(Real)) SolveResp {
+    Real v, w;
+};
+
 // Row of the inverse of the implicit solve's reduced (lane-interface) system:
 // for lane k and source lane m, the weights of lane m's first and last block
 // values in the value left of lane k's block (lf, ll) and right of it (rf, rl).
@@ -65,6 +77,13 @@ template <typename Real>
 struct __align__(4 * sizeof(Real)) Reduced1D {
     Real lf, ll, rf, rl;
 };
+
+// bytes of shared memory of the factor tables of a C x LPR layout
+template <typename Real>
+constexpr int solve_smem_bytes(int C, int LPR)
+{
+    return C * LPR * (int)(sizeof(SolveLU<Real>) + sizeof(SolveResp<Real>)) + LPR * LPR * (int)sizeof(Reduced1D<Real>);
+}
 
 // Arguments of the 1D step kernels (one realization per warp).
 template <typename Real>

@@ -95,8 +95,9 @@ static __device__ __noinline__ int cov_mma_issue(unsigned char* base, uint64_t* 
 template <int C, int LPR, bool DIR, bool SPECIES, bool RAGGED, bool PC, bool VAR, bool TC, bool IMP>
 __device__ __forceinline__ int cov_step_warp(const Step1DArgs<float>& a, unsigned char* base, uint64_t* full,
                                              uint64_t* empty, volatile int* abort_flag, float* wmom,
-                                             const Coef1D<float>* tab, const Solve1D<float>* stab,
-                                             const Reduced1D<float>* rtab, int rb, int count, int slot0,
+                                             const Coef1D<float>* tab, const SolveLU<float>* stab,
+                                             const SolveResp<float>* srsp, const Reduced1D<float>* rtab, int rb,
+                                             int count, int slot0,
                                              bool use_tc)
 {
     constexpr unsigned FULL = 0xffffffffu;
@@ -133,7 +134,7 @@ __device__ __forceinline__ int cov_step_warp(const Step1DArgs<float>& a, unsigne
     for (int s = 0; s < a.nsteps; ++s) {
         if (warp_active) {
             if constexpr (IMP)
-                rowst.template step_theta<!DIR>(T, a.step0 + (uint32_t)s, stab, rtab, a.omt, a.th2r_lo, a.th2r_hi,
+                rowst.template step_theta<!DIR>(T, a.step0 + (uint32_t)s, stab, srsp, rtab, a.omt, a.th2r_lo, a.th2r_hi,
                                                 a.sm_cg, a.sm_inv);
             else
                 rowst.template advance<PC>(T, a.step0 + (uint32_t)s);
@@ -240,7 +241,7 @@ __device__ __forceinline__ int cov_step_warp(const Step1DArgs<float>& a, unsigne
 // TC: the time correlation is sampled too (its code stays out of the other
 // instances, whose register allocation it would change).  IMP: the step is
 // the implicit theta scheme (backward Euler / Crank-Nicolson); its factor
-// tables (C x LPR rows, LPR x LPR reduced weights) are copied into shared
+// tables (C x LPR rows in two arrays, LPR x LPR reduced weights) are copied into shared
 // memory after the moment partials.
 // MIX (16 cells x 16 lanes, the explicit schemes): a CTA holds at most
 // 30 realizations on 15 stepping warps, two per warp; since a scheduler's
@@ -266,8 +267,9 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
     float* mom = reinterpret_cast<float*>(base + 4 * kOpBytes + 64);
     Coef1D<float>* tab = reinterpret_cast<Coef1D<float>*>(mom + LPR * 2 * C * 32);
-    Solve1D<float>* stab = reinterpret_cast<Solve1D<float>*>(mom + LPR * 2 * C * 32);
-    Reduced1D<float>* rtab = reinterpret_cast<Reduced1D<float>*>(stab + C * LPR);
+    SolveLU<float>* stab = reinterpret_cast<SolveLU<float>*>(mom + LPR * 2 * C * 32);
+    SolveResp<float>* srsp = reinterpret_cast<SolveResp<float>*>(stab + C * LPR);
+    Reduced1D<float>* rtab = reinterpret_cast<Reduced1D<float>*>(srsp + C * LPR);
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -288,7 +290,11 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
     for (int i = threadIdx.x; i < 4 * kOpBytes / 16; i += blockDim.x)
         reinterpret_cast<uint4*>(base)[i] = make_uint4(0u, 0u, 0u, 0u);
     if constexpr (IMP) {   // stored transposed (RowT::tpos; source lane m of block k at m * LPR + k)
-        for (int k = threadIdx.x; k < C * LPR; k += blockDim.x) stab[RowT::tpos(k)] = a.solve[k];
+        for (int k = threadIdx.x; k < C * LPR; k += blockDim.x) {
+            const Solve1D<float> e = a.solve[k];
+            stab[RowT::tpos(k)] = {e.m, e.z, e.ip, e.sup};
+            srsp[RowT::tpos(k)] = {e.v, e.w};
+        }
         for (int k = threadIdx.x; k < LPR * LPR; k += blockDim.x) rtab[(k % LPR) * LPR + k / LPR] = a.red[k];
     }
     // rows past N repeat row N; stored transposed (RowT::tpos), and MIX a
@@ -344,14 +350,14 @@ k_step1d_cov(const __grid_constant__ Step1DArgs<float> a, const CovArgs c)
         if constexpr (MIX) {
             if (warp >= npair)
                 nsnap = cov_step_warp<C / 2, 2 * LPR, DIR, SPECIES, RAGGED, PC, VAR, TC, IMP>(
-                    a, base, full, empty, abort_flag, wmom, tab2, stab, rtab, rb, count, 2 * npair + (warp - npair),
+                    a, base, full, empty, abort_flag, wmom, tab2, stab, srsp, rtab, rb, count, 2 * npair + (warp - npair),
                     use_tc);
             else
                 nsnap = cov_step_warp<C, LPR, DIR, SPECIES, RAGGED, PC, VAR, TC, IMP>(
-                    a, base, full, empty, abort_flag, wmom, tab, stab, rtab, rb, count, 2 * warp, use_tc);
+                    a, base, full, empty, abort_flag, wmom, tab, stab, srsp, rtab, rb, count, 2 * warp, use_tc);
         } else {
             nsnap = cov_step_warp<C, LPR, DIR, SPECIES, RAGGED, PC, VAR, TC, IMP>(
-                a, base, full, empty, abort_flag, wmom, tab, stab, rtab, rb, count, warp * RPW, use_tc);
+                a, base, full, empty, abort_flag, wmom, tab, stab, srsp, rtab, rb, count, warp * RPW, use_tc);
         }
     }
 
@@ -402,7 +408,7 @@ static cudaError_t launch_cov_layout(const Step1DArgs<float>& a, const CovArgs& 
 {
     constexpr bool MIX = C == 16 && LPR == 16 && !IMP;       // two copies of a material table
     const int smem = cov_smem_bytes<C>(LPR) + (VAR ? (MIX ? 2 : 1) * (C * LPR + 1) * (int)sizeof(Coef1D<float>) : 0) +
-                     (IMP ? C * LPR * (int)sizeof(Solve1D<float>) + LPR * LPR * (int)sizeof(Reduced1D<float>) : 0);
+                     (IMP ? solve_smem_bytes<float>(C, LPR) : 0);
     if (a.N == C * LPR) {
         auto k = k_step1d_cov<C, LPR, DIR, SP, false, PC, VAR, TC, IMP>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

@@ -27,7 +27,8 @@ constexpr int step1d_smem_per_warp() { return 2 * C * 32 * (int)sizeof(Real); }
 // VAR: a rod of several materials; its material table (N + 1 entries) is
 // copied into shared memory after the moment partials.
 // IMP: an implicit scheme (backward Euler / Crank-Nicolson); its factor
-// tables (C x LPR rows, LPR x LPR reduced weights) are copied there instead.
+// tables (C x LPR rows split into {m, z, ip, sup} and {v, w} arrays, LPR x
+// LPR reduced weights) are copied there instead.
 template <typename Real, int C, int LPR, bool DIR, bool SPECIES, bool RAGGED, int MINB, bool PC, bool VAR,
           bool IMP = false>
 __global__ void __launch_bounds__(kWarpsPerBlock1D * 32, MINB)
@@ -42,8 +43,9 @@ k_step1d(const __grid_constant__ Step1DArgs<Real> a)
     Coef1D<Real>* tab = reinterpret_cast<Coef1D<Real>*>(
         smem_raw + (size_t)kWarpsPerBlock1D * step1d_smem_per_warp<Real, C>());
     using RowT = Row1D<Real, C, LPR, DIR, SPECIES, RAGGED, true, VAR>;
-    Solve1D<Real>* stab = reinterpret_cast<Solve1D<Real>*>(tab);
-    Reduced1D<Real>* rtab = reinterpret_cast<Reduced1D<Real>*>(stab + C * LPR);
+    SolveLU<Real>* stab = reinterpret_cast<SolveLU<Real>*>(tab);
+    SolveResp<Real>* srsp = reinterpret_cast<SolveResp<Real>*>(stab + C * LPR);
+    Reduced1D<Real>* rtab = reinterpret_cast<Reduced1D<Real>*>(srsp + C * LPR);
     if constexpr (VAR) {
         // every thread of the block helps, before any warp leaves; rows past
         // N repeat row N; stored transposed (RowT::tpos)
@@ -51,7 +53,11 @@ k_step1d(const __grid_constant__ Step1DArgs<Real> a)
         __syncthreads();
     }
     if constexpr (IMP) {
-        for (int k = threadIdx.x; k < C * LPR; k += blockDim.x) stab[RowT::tpos(k)] = a.solve[k];
+        for (int k = threadIdx.x; k < C * LPR; k += blockDim.x) {
+            const Solve1D<Real> e = a.solve[k];
+            stab[RowT::tpos(k)] = {e.m, e.z, e.ip, e.sup};
+            srsp[RowT::tpos(k)] = {e.v, e.w};
+        }
         for (int k = threadIdx.x; k < LPR * LPR; k += blockDim.x) rtab[(k % LPR) * LPR + k / LPR] = a.red[k];
         __syncthreads();
     }
@@ -65,7 +71,7 @@ k_step1d(const __grid_constant__ Step1DArgs<Real> a)
     // time correlation on chip: per warp [L][C][32] partial lag sums after
     // the tables (lane-contiguous like the moments)
     constexpr int kTabBytes = (VAR ? (C * LPR + 1) * (int)sizeof(Coef1D<Real>) : 0) +
-                              (IMP ? C * LPR * (int)sizeof(Solve1D<Real>) + LPR * LPR * (int)sizeof(Reduced1D<Real>) : 0);
+                              (IMP ? solve_smem_bytes<Real>(C, LPR) : 0);
     Real* tcp = reinterpret_cast<Real*>(smem_raw + (size_t)kWarpsPerBlock1D * step1d_smem_per_warp<Real, C>() +
                                         kTabBytes) +
                 (size_t)(threadIdx.x >> 5) * a.tc_lags * C * 32 + lane;
@@ -94,7 +100,7 @@ k_step1d(const __grid_constant__ Step1DArgs<Real> a)
 
     for (int s = 0; s < a.nsteps; ++s) {
         if constexpr (IMP)
-            rowst.template step_theta<!DIR>(T, a.step0 + (uint32_t)s, stab, rtab, a.omt, a.th2r_lo, a.th2r_hi,
+            rowst.template step_theta<!DIR>(T, a.step0 + (uint32_t)s, stab, srsp, rtab, a.omt, a.th2r_lo, a.th2r_hi,
                                             a.sm_cg, a.sm_inv);
         else
             rowst.template advance<PC>(T, a.step0 + (uint32_t)s);
@@ -167,7 +173,7 @@ inline cudaError_t launch_layout(const Step1DArgs<Real>& a, cudaStream_t st)
     const dim3 grid((warps + kWarpsPerBlock1D - 1) / kWarpsPerBlock1D);
     const int smem = kWarpsPerBlock1D * step1d_smem_per_warp<Real, C>() +
                      (VAR ? (C * LPR + 1) * (int)sizeof(Coef1D<Real>) : 0) +
-                     (IMP ? C * LPR * (int)sizeof(Solve1D<Real>) + LPR * LPR * (int)sizeof(Reduced1D<Real>) : 0) +
+                     (IMP ? solve_smem_bytes<Real>(C, LPR) : 0) +
                      (a.tc_onchip ? kWarpsPerBlock1D * a.tc_lags * C * 32 * (int)sizeof(Real) : 0);
     if (a.N == LPR * C) {
         auto k = k_step1d<Real, C, LPR, DIR, SP, false, MINB, PC, VAR, IMP>;
